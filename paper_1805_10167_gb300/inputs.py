@@ -1,0 +1,215 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the benchmark.
+
+This module holds no arithmetic of the multigrid method itself: it only makes
+macro meshes, random right-hand sides and random coefficient fields.
+
+* ``unit_square_mesh``: the unit square cut into 2x2 quads, each split along
+  its (x0,y0)-(x1,y1) diagonal (8 macro-triangles).
+* ``annulus_mesh``: the straight-edged annulus r in [0.55, 1] meshed as
+  n_ang x n_rad quads, each split along its (i,j)-(i+1,j+1) diagonal.  Its
+  shape follows the annulus of the paper's energy-transport example (Sec. 5.2).
+* ``random_square_mesh``: a seeded random valid triangulation of the unit
+  square (point insertion, boundary splits, Lawson flips with a min-angle test).
+* ``splitmix64`` / ``uniform_pm1``: Vigna's SplitMix64 counter generator and
+  its map to uniform doubles in [-1, 1); the value for canonical DoF p is drawn
+  from ``splitmix64(seed ^ p)``.
+* ``grf_coefficient``: k = exp(g) with g a Gaussian random field of
+  squared-exponential covariance sigma^2 exp(-d^2 / (2 l^2)), drawn by random
+  Fourier features (Rahimi & Recht 2007) and sampled at element centroids.
+* ``element_centroids``: centroids of the fine micro-triangles of every face in
+  the library's canonical element order (per face: upward triangles row by row,
+  then downward triangles row by row) -- the sampling points of k.
+
+Every mesh is returned with counter-clockwise triangles.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+MASK64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def _ccw(xy: np.ndarray, tri: np.ndarray) -> np.ndarray:
+    tri = np.array(tri, dtype=np.int32, copy=True)
+    a, b, c = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    cross = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    flip = cross < 0
+    tri[flip, 1], tri[flip, 2] = tri[flip, 2].copy(), tri[flip, 1].copy()
+    return tri
+
+
+def unit_square_mesh(nq: int = 2):
+    """Unit square, nq x nq quads, each cut along its (x0,y0)-(x1,y1) diagonal."""
+    g = np.linspace(0.0, 1.0, nq + 1)
+    xy = np.array([[g[i], g[j]] for j in range(nq + 1) for i in range(nq + 1)], dtype=np.float64)
+    vid = lambda i, j: j * (nq + 1) + i
+    tri = []
+    for j in range(nq):
+        for i in range(nq):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            tri.append((a, b, c))
+            tri.append((a, c, d))
+    return xy, _ccw(xy, np.array(tri))
+
+
+def annulus_mesh(n_ang: int = 32, n_rad: int = 2, r0: float = 0.55, r1: float = 1.0):
+    """Straight-edged annulus: vertices at r_j = r0 + (r1-r0) j / n_rad and
+    theta_i = 2 pi i / n_ang (vertex id j*n_ang + i); quad (i,j),(i+1,j),
+    (i+1,j+1),(i,j+1) split along its (i,j)-(i+1,j+1) diagonal."""
+    xy = []
+    for j in range(n_rad + 1):
+        r = r0 + (r1 - r0) * j / n_rad
+        for i in range(n_ang):
+            th = 2.0 * np.pi * i / n_ang
+            xy.append((r * np.cos(th), r * np.sin(th)))
+    xy = np.array(xy, dtype=np.float64)
+    vid = lambda i, j: j * n_ang + (i % n_ang)
+    tri = []
+    for j in range(n_rad):
+        for i in range(n_ang):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            tri.append((a, b, c))
+            tri.append((a, c, d))
+    return xy, _ccw(xy, np.array(tri))
+
+
+def _min_angle(p, q, r):
+    def ang(a, b, c):
+        u, v = b - a, c - a
+        cu = float(np.dot(u, v) / (np.linalg.norm(u) * np.linalg.norm(v)))
+        return np.degrees(np.arccos(np.clip(cu, -1.0, 1.0)))
+    return min(ang(p, q, r), ang(q, r, p), ang(r, p, q))
+
+
+def random_square_mesh(seed: int, n_faces: int):
+    """Seeded random valid triangulation of the unit square with n_faces >= 2
+    triangles: start from the square cut by one diagonal; repeat interior point
+    insertion (+2 faces; barycentric weights drawn from [0.2, 0.6] and
+    normalised) or a boundary-edge split at t in [0.3, 0.7] (+1 face) until the
+    count is reached; then up to n_faces random Lawson flips, each kept only if
+    both new triangles have a minimum angle of at least 20 degrees."""
+    if n_faces < 2:
+        raise ValueError("n_faces must be >= 2")
+    rng = np.random.default_rng(seed)
+    pts = [np.array(p, dtype=np.float64) for p in ((0, 0), (1, 0), (1, 1), (0, 1))]
+    tris = [[0, 1, 2], [0, 2, 3]]
+
+    def edge_faces():
+        m = {}
+        for f, t in enumerate(tris):
+            for s in range(3):
+                a, b = t[s], t[(s + 1) % 3]
+                m.setdefault((min(a, b), max(a, b)), []).append(f)
+        return m
+
+    while len(tris) < n_faces:
+        need = n_faces - len(tris)
+        if need >= 2 and rng.random() < 0.6:
+            f = int(rng.integers(len(tris)))
+            w = rng.uniform(0.2, 0.6, size=3)
+            w /= w.sum()
+            a, b, c = tris[f]
+            p = w[0] * pts[a] + w[1] * pts[b] + w[2] * pts[c]
+            pts.append(p)
+            n = len(pts) - 1
+            tris[f] = [a, b, n]
+            tris.append([b, c, n])
+            tris.append([c, a, n])
+        else:
+            em = edge_faces()
+            bnd = [e for e, fs in em.items() if len(fs) == 1]
+            e = bnd[int(rng.integers(len(bnd)))]
+            f = em[e][0]
+            t = rng.uniform(0.3, 0.7)
+            a, b = e
+            p = (1 - t) * pts[a] + t * pts[b]
+            pts.append(p)
+            n = len(pts) - 1
+            tri = tris[f]
+            # rotate so that (tri[0], tri[1]) is the split edge
+            for s in range(3):
+                if {tri[s], tri[(s + 1) % 3]} == {a, b}:
+                    u, v, w_ = tri[s], tri[(s + 1) % 3], tri[(s + 2) % 3]
+                    break
+            tris[f] = [u, n, w_]
+            tris.append([n, v, w_])
+    for _ in range(n_faces):
+        em = edge_faces()
+        inner = [e for e, fs in em.items() if len(fs) == 2]
+        if not inner:
+            break
+        e = inner[int(rng.integers(len(inner)))]
+        f1, f2 = em[e]
+        a, b = e
+        c = [v for v in tris[f1] if v not in e][0]
+        d = [v for v in tris[f2] if v not in e][0]
+        t1, t2 = [c, d, a], [d, c, b]
+        P = lambda t: [pts[v] for v in t]
+
+        def area2(t):
+            p, q, r = P(t)
+            return (q[0] - p[0]) * (r[1] - p[1]) - (q[1] - p[1]) * (r[0] - p[0])
+        if abs(area2(t1)) < 1e-12 or abs(area2(t2)) < 1e-12:
+            continue
+        # the flip is valid only if the quad a,c,b,d is convex: the new
+        # triangles then have opposite orientations relative to segment cd
+        if np.sign(area2([c, d, a])) == np.sign(area2([c, d, b])):
+            continue
+        if _min_angle(*P(t1)) >= 20.0 and _min_angle(*P(t2)) >= 20.0:
+            tris[f1], tris[f2] = t1, t2
+    xy = np.array(pts, dtype=np.float64)
+    return xy, _ccw(xy, np.array(tris))
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function (Vigna 2015; Steele, Lea & Flood 2014)
+    applied to 64-bit states ``x`` (uint64 array)."""
+    with np.errstate(over="ignore"):
+        z = (x.astype(np.uint64) + np.uint64(0x9E3779B97F4A7C15)) & MASK64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & MASK64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & MASK64
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform_pm1(n: int, seed: int) -> np.ndarray:
+    """n doubles uniform in [-1, 1): value p = (top 53 bits of
+    splitmix64(seed ^ p)) * 2^-52 - 1."""
+    p = np.arange(n, dtype=np.uint64)
+    z = splitmix64(np.uint64(seed) ^ p)
+    u = (z >> np.uint64(11)).astype(np.float64)
+    return u * (2.0 ** -52) - 1.0
+
+
+def element_centroids(xy: np.ndarray, tri: np.ndarray, level: int) -> np.ndarray:
+    """Centroids (n_faces * N^2, 2) of the level-``level`` micro-triangles in
+    canonical element order.  Face frame: x = v0 + (i/N)(v1-v0) + (j/N)(v2-v0),
+    (v0,v1,v2) the counter-clockwise face.  Upward triangle (i,j): lattice
+    points (i,j),(i+1,j),(i,j+1), i+j <= N-1; downward triangle (i,j):
+    (i+1,j),(i,j+1),(i+1,j+1), i+j <= N-2; both row by row (j outer)."""
+    tri = _ccw(xy, tri)
+    N = 1 << level
+    up = [(i, j) for j in range(N) for i in range(N - j)]
+    dn = [(i, j) for j in range(N - 1) for i in range(N - 1 - j)]
+    cu = np.array([(i + 1.0 / 3.0, j + 1.0 / 3.0) for i, j in up]).reshape(-1, 2) / N
+    cd = np.array([(i + 2.0 / 3.0, j + 2.0 / 3.0) for i, j in dn]).reshape(-1, 2) / N
+    loc = np.concatenate([cu, cd], axis=0)  # (N^2, 2) in (s,t) frame coordinates
+    v0, v1, v2 = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    out = (v0[:, None, :] + loc[None, :, 0:1] * (v1 - v0)[:, None, :]
+           + loc[None, :, 1:2] * (v2 - v0)[:, None, :])
+    return out.reshape(-1, 2)
+
+
+def grf_coefficient(points: np.ndarray, seed: int = 42, length: float = 0.1,
+                    sigma: float = 1.0, n_features: int = 512) -> np.ndarray:
+    """k = exp(g(points)), g(x) = sigma sqrt(2/M) sum_m cos(w_m . x + phi_m),
+    w_m ~ N(0, length^-2 I), phi_m ~ U[0, 2 pi): a random-Fourier-feature draw
+    of a zero-mean Gaussian field with covariance sigma^2 exp(-d^2/(2 l^2))."""
+    rng = np.random.default_rng(seed)
+    w = rng.normal(0.0, 1.0 / length, size=(n_features, 2))
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=n_features)
+    out = np.empty(points.shape[0], dtype=np.float64)
+    step = 1 << 20
+    for s in range(0, points.shape[0], step):
+        pr = points[s:s + step] @ w.T + phi[None, :]
+        out[s:s + step] = sigma * np.sqrt(2.0 / n_features) * np.cos(pr).sum(axis=1)
+    return np.exp(out)
