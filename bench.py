@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Benchmark of the HHG P1 multigrid V-cycle on one GB300 (per process).
+
+Workload (default): P1 Poisson on the straight-edged annulus r in [0.55, 1],
+32 angular x 2 radial quads cut into 128 macro-triangles, refined to level 10
+(1025 lattice points per macro-edge, 67.1 M free unknowns), homogeneous
+Dirichlet conditions on both circles, b uniform in [-1, 1) from SplitMix64
+(seed 1234), FP64.  One step = one V(3,3) cycle (3-colour Gauss-Seidel, full
+weighting, linear prolongation, CG on level 0) plus the FP64 residual and its
+norm (the solver's convergence test), all on the device.
+
+Printed (one JSON line, rank 0): GDoF/s per V-cycle = free DoFs x cycles /
+seconds / 1e9 over all ranks (independent replicas, weak scaling), with
+  e2e          the same through the public API from pinned host memory
+               (b copied host->device each step, norm read back);
+  roofline     the dominant kernel (face Gauss-Seidel) timed by CUDA events
+               inside the timed region, against the FP64 ALU peak;
+  cpu_baseline the FP64 oracle timed on the host cores on a bounded sample;
+  time_to_tol  wall time to a 1e-10 relative FP64 residual: FP64 V-cycles
+               and FP32 V-cycles inside FP64 iterative refinement.
+``--impl reference`` times the oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GDoF/s per V-cycle & time to 1e-10 FP64 residual: mixed/learned vs FP64 (1 GB300)"
+UNIT = "GDoF/s"
+FP64_FLOP_PER_CLK_SM = 4          # 2 DFMA per clock per SM (probe: 598 GFMA/s at 1995 MHz, 152 SMs)
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--level", type=int, default=10)
+    ap.add_argument("--cpu-level", type=int, default=8, help="level of the oracle's bounded sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    return ap.parse_args()
+
+
+def workload(level):
+    from paper_1805_10167_gb300 import inputs
+    xy, tri = inputs.annulus_mesh(32, 2)
+    return xy, tri, f"annulus-32x2-128faces-L{level}-P1-Poisson-fp64-V(3,3)"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_rate(level, cycles, warmup=0):
+    """The FP64 oracle (as it stands) on the same annulus at a lower level:
+    returns (GDoF/s, seconds per cycle, free DoFs)."""
+    from oracle import mesh as om
+    from oracle import multigrid as mg
+    from paper_1805_10167_gb300 import inputs
+    xy, tri = inputs.annulus_mesh(32, 2)
+    H = mg.Hierarchy(om.MacroMesh(xy, tri), level)
+    lv = H.levels[level]
+    b = inputs.uniform_pm1(lv.n, 1234)
+    x = np.zeros(lv.n)
+    for l in range(1, level + 1):          # assemble the smoother sets and transfers once
+        H.sets(l)
+        H.P(l)
+    for _ in range(warmup):
+        mg.vcycle(H, level, x, b, 3, 3)
+    t0 = time.perf_counter()
+    for _ in range(cycles):
+        mg.vcycle(H, level, x, b, 3, 3)
+        r = H.residual(level, x, b)
+        mg.norm_free(H, level, r)
+    dt = time.perf_counter() - t0
+    n_free = int(lv.free.sum())
+    return n_free * cycles / dt / 1e9, dt / cycles, n_free
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = max(1, min(args.steps, 4))
+    rate, spc, n_free = oracle_rate(args.cpu_level, steps, warmup=min(args.warmup, 1))
+    sample = (f"annulus 32x2 (128 faces) at level {args.cpu_level} ({n_free} free DoFs), FP64 V(3,3) + "
+              f"residual norm, {steps} cycles after {min(args.warmup, 1)} warm-up; numpy/scipy oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": spc * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload(args.level)[2], "level": args.level},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1805_10167_gb300 import hhg, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    L = args.level
+    xy, tri, wname = workload(L)
+    g = hhg.Mesh(xy, tri, L)
+    info = g.info(L)
+    n_free = info.n_free
+    st = torch.cuda.current_stream()
+    b_canon = torch.tensor(inputs.uniform_pm1(info.n_nodes, 1234), dtype=torch.float64, device=dev)
+    b = torch.zeros(info.vec_len, dtype=torch.float64, device=dev)
+    x = torch.zeros_like(b)
+    r = torch.zeros_like(b)
+    nrm = torch.zeros(1, dtype=torch.float64, device=dev)
+    g.from_canonical(L, b_canon, b, stream=st)
+
+    def step():
+        g.vcycle(L, x, b, nu1=3, nu2=3, stream=st)
+        g.residual(L, x, b, r, nrm, stream=st)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    hhg.profile_begin(1 << hhg.K_FACE_GS, L)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    launches, kms = hhg.profile_end()
+    clk = clocks.stop()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    value = world * n_free * args.steps / (ms / 1e3) / 1e9
+
+    # dominant kernel: the face-interior Gauss-Seidel colour phase on level L
+    gs_launches_L = 6 * 3 * args.steps            # V(3,3): 6 sweeps x 3 colours per cycle
+    gs_ms = kms[hhg.K_FACE_GS] / gs_launches_L
+    nfi = info.n_faces * (info.N - 1) * (info.N - 2) // 2
+    pts = nfi / 3.0                               # one colour per launch
+    flops = 10.0 * pts                            # 3 adds + 3 muls + 2 adds + 1 sub + 1 div per point
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e9        # GFLOP/s at the sampled clock
+    achieved = flops / (gs_ms / 1e3) / 1e9
+    bytes_alg = 24.0 * pts                        # read x, b; write x of the colour's points
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roofline = {"bound": "alu", "kernel": "k_face<double,GS> (one colour phase, level %d)" % L,
+                "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
+                "traffic": None, "flops_per_launch": flops, "ms_per_launch": gs_ms,
+                "peak_basis": f"FP64: {N_SM} SMs x {FP64_FLOP_PER_CLK_SM} flop/clk x {sm_mhz:.0f} MHz (sampled)",
+                "hbm": {"achieved_gbs": bytes_alg / (gs_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
+                        "frac": bytes_alg / (gs_ms / 1e3) / 1e9 / hbm_peak,
+                        "algorithmic_bytes_per_launch": bytes_alg}}
+
+    # end to end through the public API from pinned host memory
+    b_host = b_canon.cpu().pin_memory()
+    nrm_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+    b_stage = torch.empty_like(b_canon)
+    x.zero_()
+
+    def e2e_step():
+        b_stage.copy_(b_host, non_blocking=True)
+        g.from_canonical(L, b_stage, b, stream=st)
+        step()
+        nrm_host.copy_(nrm, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(st)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+    e2e = {"value": world * n_free * args.steps / (ms_e2e / 1e3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(b_host.numel() * 8), "d2h_bytes_per_step": 8,
+           "ms_per_step": ms_e2e / args.steps}
+
+    # time to a 1e-10 relative FP64 residual: FP64 MG vs FP32-in-FP64 IR
+    solve = None
+    if not args.no_solve:
+        solve = {}
+        for name, mode in (("fp64_mg", hhg.SOLVE_MG), ("fp32_ir", hhg.SOLVE_IR)):
+            x.zero_()
+            g.solve(L, x, b, mode=mode, stream=st)          # warm-up
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, rep = g.solve(L, x, b, mode=mode, stream=st)
+            torch.cuda.synchronize()
+            solve[name] = {"seconds": time.perf_counter() - t0, "cycles": rep["iterations"],
+                           "rel_residual": rep["r_final"] / rep["r0"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, spc, nf = oracle_rate(args.cpu_level, 8)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"annulus 32x2 at level {args.cpu_level} ({nf} free DoFs), FP64 V(3,3) + residual norm, "
+                         f"8 cycles, numpy/scipy oracle (single thread), {spc:.2f} s/cycle"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "level": L, "macro_faces": info.n_faces, "free_dofs": n_free,
+                       "cycle": "V(3,3), 3-colour GS, CG on level 0", "rhs": "SplitMix64 seed 1234",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (%.2f GB per level-%d vector)" % (info.vec_len * 8 / 1e9, L)},
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(launches)),
+            "launches_by_class": dict(zip(hhg.K_NAMES, launches)),
+            "roofline": roofline, "cpu_baseline": cpu, "time_to_tol": solve,
+        }), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,222 @@
+/*
+ * hhg.h -- C-ABI of libhhg: a matrix-free geometric-multigrid V-cycle for P1
+ * finite elements on hierarchical hybrid grids, on one GB300 GPU.
+ *
+ * Method: Kohl, Thoennes, Drzisga, Bartuschat, Ruede, "A Scalable and Modular
+ * Software Architecture for Finite Elements on Hierarchical Hybrid Grids"
+ * (2018).  The mesh is a 2D unstructured triangulation of macro-triangles
+ * (Sec. 2.1) refined uniformly to level L (Sec. 3.1: N = 2^L intervals per
+ * macro-edge, N^2 congruent micro-triangles per macro-face).  The operator is
+ * the P1 stiffness matrix of -div(k grad u) (Sec. 4.1), applied matrix-free
+ * with one constant stencil per macro-face for k = 1 or assembled on the fly
+ * from a per-micro-triangle coefficient k (Sec. 4.2, Alg. 3).  Multigrid
+ * (Sec. 4.3) is the solver.
+ *
+ * Conventions shared by every call
+ *  - All pointers named *_dev or typed as vectors (x, y, b, r, src, dst) are
+ *    DEVICE pointers on the current CUDA device, owned by the caller.  Host
+ *    arrays (xy, tri, dirichlet_vertex) are copied; the caller keeps them.
+ *  - A "level vector" has hhg_info.vec_len elements of the precision given
+ *    (double for HHG_F64, float for HHG_F32) in the library's internal layout:
+ *    [vertex block | edge block | face block]; every macro-edge stores its N+1
+ *    lattice points (both end points are copies of the vertices), every
+ *    macro-face its closed triangle (i, j >= 0, i + j <= N) with row stride
+ *    info.row_stride (slot j * row_stride + i); lattice points on a face's
+ *    boundary are copies of the edge/vertex values (ghost layers, Sec. 2.2).
+ *    Padding slots are never read.  Use hhg_from_canonical/hhg_to_canonical
+ *    to cross to the canonical order (macro-vertices in input order; each
+ *    macro-edge, edges sorted by (min id, max id), interior points from the
+ *    low-id end; each macro-face in input order, interior points row by row).
+ *  - Calls that read neighbour values of a vector first refresh its ghost
+ *    slots from the owners (the communication steps of Alg. 3); the values it
+ *    represents do not change.  Inputs are otherwise left untouched.
+ *  - Dirichlet DoFs keep the values held in x and are never modified; b at
+ *    Dirichlet DoFs is ignored; operator outputs are 0 there.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream) unless stated otherwise.  One mesh owns one set of
+ *    workspaces: calls on the same mesh must not overlap in time.
+ *  - No exception crosses the ABI; on failure the call returns a status and
+ *    hhg_last_error() gives a message (thread-local).
+ */
+#ifndef HHG_H
+#define HHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hhg_mesh_s* hhg_mesh;
+
+typedef enum {
+  HHG_OK = 0,
+  HHG_ERR_ARG = 1,            /* bad argument (NULL, level out of range, size) */
+  HHG_ERR_MESH = 2,           /* invalid macro mesh */
+  HHG_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  HHG_ERR_OOM = 4,            /* device allocation failed */
+  HHG_ERR_NOT_CONVERGED = 5,  /* max_iter reached; x holds the last iterate */
+  HHG_ERR_NAN = 6,            /* non-finite residual norm */
+  HHG_ERR_TIMEOUT = 7,        /* a bounded device-side wait ran out */
+  HHG_ERR_BREAKDOWN = 8       /* Krylov breakdown */
+} hhg_status;
+
+typedef enum { HHG_F64 = 0, HHG_F32 = 1 } hhg_prec;
+
+typedef enum {
+  HHG_GS_FWD = 0,   /* multi-colour Gauss-Seidel, forward colour order    */
+  HHG_GS_BWD = 1,   /* the exact reverse order                            */
+  HHG_JACOBI = 2    /* damped Jacobi x <- x + omega D^-1 (b - A x)        */
+} hhg_smoother;
+
+typedef struct {
+  int32_t N;              /* intervals per macro-edge, 2^level             */
+  int32_t n_edge_colours; /* Gauss-Seidel colours of the edge-interior DoFs */
+  int64_t n_nodes;        /* unknowns incl. Dirichlet (canonical length)    */
+  int64_t n_free;         /* unknowns without Dirichlet ones               */
+  int64_t vec_len;        /* elements of an internal level vector          */
+  int64_t n_elems;        /* micro-triangles: n_faces * N^2                */
+  int64_t row_stride;     /* face row stride S                             */
+  int64_t v_off, e_off, f_off;   /* block offsets in the level vector      */
+  int64_t edge_stride, face_stride;
+  int32_t n_vertices, n_edges, n_faces, max_level;
+} hhg_info;
+
+typedef struct {
+  int32_t nu1;            /* pre-smoothing sweeps (forward GS)  default 3  */
+  int32_t nu2;            /* post-smoothing sweeps (backward GS) default 3 */
+} hhg_vcycle_opts;
+
+typedef enum {
+  HHG_SOLVE_MG = 0,       /* V-cycles in the precision of x (FP64)          */
+  HHG_SOLVE_IR = 1        /* FP32 V-cycle inside FP64 iterative refinement  */
+} hhg_solve_mode;
+
+typedef struct {
+  int32_t mode;           /* hhg_solve_mode                                  */
+  int32_t nu1, nu2;       /* V(nu1, nu2)                                     */
+  int32_t max_iter;       /* cycles / outer iterations, default 100          */
+  double tol;             /* stop at ||r|| <= tol ||r0||, default 1e-10       */
+} hhg_solve_opts;
+
+typedef struct {
+  int32_t iterations;     /* V-cycles (MG) or outer iterations (IR) run      */
+  int32_t status;         /* hhg_status of the solve                         */
+  double r0;              /* ||b - A x0||_2 over free DoFs                   */
+  double r_final;         /* final residual norm                             */
+  double* history;        /* optional HOST array: residual norm per cycle    */
+  int32_t history_cap;    /* its capacity (entries written: min(cap, it+1))   */
+} hhg_solve_report;
+
+/* Build the macro-primitive graph (Sec. 2.1), the level hierarchy 0..max_level
+ * (Sec. 3.1) and all device workspaces.  xy: nv x 2 doubles (host); tri: nt x 3
+ * vertex ids (host), any orientation (made counter-clockwise); dirichlet_vertex:
+ * nv flags (host) or NULL = every vertex on the boundary.  A macro-edge's
+ * interior DoFs are Dirichlet when the edge lies on the boundary and both end
+ * vertices are Dirichlet.  Errors: HHG_ERR_MESH for out-of-range ids,
+ * degenerate triangles or an edge shared by more than two triangles;
+ * HHG_ERR_ARG for max_level outside 1..12; HHG_ERR_OOM. */
+hhg_status hhg_mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                           const uint8_t* dirichlet_vertex, int32_t max_level, hhg_mesh* out);
+hhg_status hhg_mesh_destroy(hhg_mesh mesh);
+hhg_status hhg_mesh_info(hhg_mesh mesh, int32_t level, hhg_info* out);
+
+/* Coefficient k of -div(k grad u), one value per finest micro-triangle in the
+ * canonical element order (per macro-face in input order: upward triangles
+ * (i,j),(i+1,j),(i,j+1) row by row, then downward ones (i+1,j),(i,j+1),
+ * (i+1,j+1) row by row; n_faces * N^2 values), as a DEVICE array of doubles.
+ * Coarser levels take the mean of the four children of each element
+ * (rediscretisation, Sec. 4.3).  NULL restores k = 1 (one constant stencil
+ * per macro-face, Sec. 4.2).  Synchronises the stream once (the level-0
+ * matrix is assembled on the host). */
+hhg_status hhg_set_coefficient(hhg_mesh mesh, const double* k_elem_dev, void* stream);
+
+/* Canonical <-> internal layout of one level.  src/dst in the precision
+ * `prec`; canonical vectors have n_nodes elements. from_canonical fills the
+ * ghost copies too. */
+hhg_status hhg_from_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* src,
+                              void* dst, void* stream);
+hhg_status hhg_to_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* src,
+                            void* dst, void* stream);
+
+/* y = A x on free DoFs, 0 on Dirichlet DoFs (Alg. 3). */
+hhg_status hhg_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x, void* y,
+                     void* stream);
+
+/* r = b - A x on free DoFs (0 on Dirichlet); if norm_dev != NULL, writes
+ * ||r||_2 over free DoFs (double, device) there. */
+hhg_status hhg_residual(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x,
+                        const void* b, void* r, double* norm_dev, void* stream);
+
+/* Alg. 1: dst = alpha * x1 + beta * x2 (all slots; dst may alias x1 or x2). */
+hhg_status hhg_assign(hhg_mesh mesh, int32_t level, hhg_prec prec, double alpha, const void* x1,
+                      double beta, const void* x2, void* dst, void* stream);
+
+/* Alg. 2: *result_dev = sum over owned free DoFs of x1 * x2 (double, device),
+ * reduced in a fixed order (bitwise reproducible). */
+hhg_status hhg_dot(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1, const void* x2,
+                   double* result_dev, void* stream);
+
+/* Restriction (Sec. 4.3, a non-square matrix-vector product): b_coarse =
+ * P^T r_fine on the free coarse DoFs (full weighting: the fine value at the
+ * coarse point plus half of each of its six fine neighbours, summed over all
+ * primitives), 0 on coarse Dirichlet DoFs.  r_fine: level fine_level with 0
+ * at fine Dirichlet DoFs; b_coarse: level fine_level - 1. */
+hhg_status hhg_restrict(hhg_mesh mesh, int32_t fine_level, hhg_prec prec, const void* r_fine,
+                        void* b_coarse, void* stream);
+
+/* Prolongation and correction: x_fine += P x_coarse (linear interpolation
+ * of the nested P1 spaces: coarse points copied, edge midpoints averaged)
+ * on free fine DoFs.  x_coarse must be 0 at its Dirichlet DoFs. */
+hhg_status hhg_prolongate_add(hhg_mesh mesh, int32_t fine_level, hhg_prec prec,
+                              const void* x_coarse, void* x_fine, void* stream);
+
+/* `sweeps` smoothing sweeps in place on x (Sec. 4.3; multi-colour order: free
+ * macro-vertices, edge-interior colours, face colours (i + 2j) mod 3 = 0,1,2;
+ * HHG_GS_BWD runs the exact reverse).  omega is used by HHG_JACOBI only. */
+hhg_status hhg_smooth(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, const void* b,
+                      int32_t smoother, int32_t sweeps, double omega, void* stream);
+
+/* One V(nu1, nu2) cycle on A x = b at `level` (Sec. 4.3): forward GS
+ * pre-smoothing, residual, full-weighting restriction, recursion with zero
+ * initial guess, CG on level 0, linear prolongation and correction, backward
+ * GS post-smoothing.  opts may be NULL (V(3,3)). */
+hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, const void* b,
+                      const hhg_vcycle_opts* opts, void* stream);
+
+/* Solve A x = b (FP64 vectors) from the initial guess in x until
+ * ||b - A x||_2 <= tol * ||b - A x0||_2 (free DoFs).  Synchronous: reads one
+ * residual norm back per cycle.  Returns HHG_ERR_NOT_CONVERGED after max_iter
+ * (x holds the last iterate) and HHG_ERR_NAN on a non-finite norm.  opts may
+ * be NULL (MG, V(3,3), 1e-10, 100); rep may be NULL. */
+hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
+                     const hhg_solve_opts* opts, hhg_solve_report* rep, void* stream);
+
+/* Diagnostics.  The library counts every kernel it launches, by class; while
+ * profiling is on it also brackets each launch of the classes in `mask`
+ * (bit c = class c) on level `level` with CUDA events on the launching
+ * stream.  hhg_profile_end synchronises those events and returns, per class,
+ * the launches counted since hhg_profile_begin (all levels) and the summed
+ * event time in milliseconds (timed level only).  Arrays have
+ * HHG_K_COUNT entries.  Process-wide; not for concurrent use. */
+typedef enum {
+  HHG_K_FACE_GS = 0,      /* face-interior Gauss-Seidel                      */
+  HHG_K_FACE_ROWS = 1,    /* face-interior apply / residual / Jacobi          */
+  HHG_K_EDGE_VERTEX = 2,  /* edge and vertex rows (all modes)                 */
+  HHG_K_TRANSFER = 3,     /* restriction and prolongation                     */
+  HHG_K_GHOST = 4,        /* ghost-layer updates                              */
+  HHG_K_OTHER = 5,        /* BLAS-1, reductions, coarse solve, conversions    */
+  HHG_K_COUNT = 6
+} hhg_kernel_class;
+hhg_status hhg_profile_begin(uint32_t mask, int32_t level);
+hhg_status hhg_profile_end(int64_t* launches, double* ms);
+
+/* Message of the last failed call on this thread ('\0'-terminated, truncated
+ * to n bytes).  Returns the full message length. */
+size_t hhg_last_error(char* buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HHG_H */

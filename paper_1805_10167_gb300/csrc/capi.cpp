@@ -1,0 +1,395 @@
+// C-ABI entry points of libhhg and the host-side multigrid drivers (V-cycle
+// recursion, solver loop, iterative refinement).  See include/hhg.h for the
+// contract of every call.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+
+#include "hhg_internal.h"
+
+struct hhg_mesh_s {
+  hhg::Mesh* m;
+};
+
+namespace hhg {
+Mesh* mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                  const uint8_t* dirichlet_vertex, int max_level);
+void mesh_destroy(Mesh* m);
+void set_coefficient(Mesh& m, const double* k_dev, cudaStream_t st);
+}  // namespace hhg
+
+namespace {
+
+thread_local std::string g_error;
+
+hhg_status fail(hhg_status s, const std::string& msg) {
+  g_error = msg;
+  return s;
+}
+
+struct ArgError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+template <typename F>
+hhg_status guarded(F&& f) {
+  try {
+    return f();
+  } catch (const ArgError& e) {
+    return fail(HHG_ERR_ARG, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(HHG_ERR_OOM, "device or host allocation failed");
+  } catch (const std::invalid_argument& e) {
+    return fail(HHG_ERR_ARG, e.what());
+  } catch (const hhg::MeshError& e) {
+    return fail(HHG_ERR_MESH, e.what());
+  } catch (const std::runtime_error& e) {
+    return fail(HHG_ERR_CUDA, e.what());
+  } catch (...) {
+    return fail(HHG_ERR_CUDA, "unknown error");
+  }
+}
+
+hhg::Mesh& get(hhg_mesh h) {
+  if (!h || !h->m) throw ArgError("NULL mesh");
+  return *h->m;
+}
+
+void check_level(const hhg::Mesh& m, int level, int min_level = 0) {
+  if (level < min_level || level > m.max_level) throw ArgError("level out of range");
+}
+
+void check_prec(int prec) {
+  if (prec != HHG_F64 && prec != HHG_F32) throw ArgError("bad precision");
+}
+
+void need(const void* p, const char* name) {
+  if (!p) throw ArgError(std::string("NULL ") + name);
+}
+
+cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+// One V(nu1, nu2) cycle on level l (Sec. 4.3).  x, b belong to the caller on
+// the top level and to the library below it.  Ghost copies of x are
+// consistent on entry and on exit.
+void vcycle_rec(const hhg::Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2,
+                cudaStream_t st) {
+  using namespace hhg;
+  if (l == 0) {
+    coarse_solve(m, prec, b, x, st);
+    return;
+  }
+  for (int s = 0; s < nu1; ++s) gs_sweep(m, l, prec, x, b, true, st);
+  const LevelData& ld = m.levels[l];
+  const LevelData& lc = m.levels[l - 1];
+  residual_op(m, l, prec, x, b, ld.r[prec], nullptr, st);
+  restrict_op(m, l, prec, ld.r[prec], lc.b[prec], st);
+  zero_vec(m, l - 1, prec, lc.x[prec], st);
+  vcycle_rec(m, l - 1, prec, lc.x[prec], lc.b[prec], nu1, nu2, st);
+  prolongate_add(m, l, prec, lc.x[prec], x, st);
+  for (int s = 0; s < nu2; ++s) gs_sweep(m, l, prec, x, b, false, st);
+}
+
+double read_scalar(const double* dev, cudaStream_t st) {
+  double h = 0.0;
+  hhg::check_cuda(cudaMemcpyAsync(&h, dev, sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
+  hhg::check_cuda(cudaStreamSynchronize(st), "sync");
+  return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+hhg_status hhg_mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                           const uint8_t* dirichlet_vertex, int32_t max_level, hhg_mesh* out) {
+  return guarded([&]() {
+    need(out, "out");
+    *out = nullptr;
+    if (max_level < 1 || max_level > 12) throw ArgError("max_level must be in 1..12");
+    hhg::Mesh* m = hhg::mesh_create(xy, nv, tri, nt, dirichlet_vertex, max_level);
+    *out = new hhg_mesh_s{m};
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_mesh_destroy(hhg_mesh mesh) {
+  return guarded([&]() {
+    if (!mesh) return HHG_OK;
+    hhg::mesh_destroy(mesh->m);
+    delete mesh;
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_mesh_info(hhg_mesh mesh, int32_t level, hhg_info* out) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    need(out, "out");
+    const hhg::LevelData& ld = m.levels[level];
+    hhg_info& I = *out;
+    std::memset(&I, 0, sizeof(I));
+    I.N = ld.lv.N;
+    I.n_edge_colours = ld.n_colours;
+    I.n_nodes = ld.n_nodes;
+    I.n_free = ld.n_free;
+    I.vec_len = ld.lv.len;
+    I.n_elems = (int64_t)m.nf * ld.lv.N * ld.lv.N;
+    I.row_stride = ld.lv.S;
+    I.v_off = ld.lv.v_off;
+    I.e_off = ld.lv.e_off;
+    I.f_off = ld.lv.f_off;
+    I.edge_stride = ld.lv.ES;
+    I.face_stride = ld.lv.FS;
+    I.n_vertices = m.nv;
+    I.n_edges = m.ne;
+    I.n_faces = m.nf;
+    I.max_level = m.max_level;
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_set_coefficient(hhg_mesh mesh, const double* k_elem_dev, void* stream) {
+  return guarded([&]() {
+    hhg::set_coefficient(get(mesh), k_elem_dev, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_from_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* src,
+                              void* dst, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    check_prec(prec);
+    need(src, "src");
+    need(dst, "dst");
+    hhg::canonical_op(m, level, prec, src, dst, false, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_to_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* src,
+                            void* dst, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    check_prec(prec);
+    need(src, "src");
+    need(dst, "dst");
+    hhg::canonical_op(m, level, prec, src, dst, true, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x, void* y,
+                     void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    check_prec(prec);
+    need(x, "x");
+    need(y, "y");
+    hhg::ghost_fill(m, level, prec, const_cast<void*>(x), S(stream));
+    hhg::apply_op(m, level, prec, x, y, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_residual(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x,
+                        const void* b, void* r, double* norm_dev, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    check_prec(prec);
+    need(x, "x");
+    need(b, "b");
+    need(r, "r");
+    hhg::ghost_fill(m, level, prec, const_cast<void*>(x), S(stream));
+    hhg::residual_op(m, level, prec, x, b, r, norm_dev, S(stream));
+    if (norm_dev) hhg::sqrt_scalar(norm_dev, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_assign(hhg_mesh mesh, int32_t level, hhg_prec prec, double alpha, const void* x1,
+                      double beta, const void* x2, void* dst, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    check_prec(prec);
+    need(x1, "x1");
+    need(x2, "x2");
+    need(dst, "dst");
+    hhg::assign_op(m, level, prec, alpha, x1, beta, x2, dst, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_dot(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1, const void* x2,
+                   double* result_dev, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    check_prec(prec);
+    need(x1, "x1");
+    need(x2, "x2");
+    need(result_dev, "result_dev");
+    hhg::dot_op(m, level, prec, x1, x2, result_dev, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_restrict(hhg_mesh mesh, int32_t fine_level, hhg_prec prec, const void* r_fine,
+                        void* b_coarse, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, fine_level, 1);
+    check_prec(prec);
+    need(r_fine, "r_fine");
+    need(b_coarse, "b_coarse");
+    hhg::restrict_op(m, fine_level, prec, r_fine, b_coarse, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_prolongate_add(hhg_mesh mesh, int32_t fine_level, hhg_prec prec,
+                              const void* x_coarse, void* x_fine, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, fine_level, 1);
+    check_prec(prec);
+    need(x_coarse, "x_coarse");
+    need(x_fine, "x_fine");
+    hhg::ghost_fill(m, fine_level - 1, prec, const_cast<void*>(x_coarse), S(stream));
+    hhg::ghost_fill(m, fine_level, prec, x_fine, S(stream));
+    hhg::prolongate_add(m, fine_level, prec, x_coarse, x_fine, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_smooth(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, const void* b,
+                      int32_t smoother, int32_t sweeps, double omega, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level, 1);
+    check_prec(prec);
+    need(x, "x");
+    need(b, "b");
+    if (sweeps < 0) throw ArgError("sweeps < 0");
+    if (smoother < HHG_GS_FWD || smoother > HHG_JACOBI) throw ArgError("bad smoother");
+    hhg::ghost_fill(m, level, prec, x, S(stream));
+    for (int s = 0; s < sweeps; ++s) {
+      if (smoother == HHG_JACOBI)
+        hhg::jacobi_sweep(m, level, prec, x, b, omega, m.levels[level].r[prec], S(stream));
+      else
+        hhg::gs_sweep(m, level, prec, x, b, smoother == HHG_GS_FWD, S(stream));
+    }
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, const void* b,
+                      const hhg_vcycle_opts* opts, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    check_prec(prec);
+    need(x, "x");
+    need(b, "b");
+    const int nu1 = opts ? opts->nu1 : 3, nu2 = opts ? opts->nu2 : 3;
+    if (nu1 < 0 || nu2 < 0) throw ArgError("negative sweep count");
+    hhg::ghost_fill(m, level, prec, x, S(stream));
+    vcycle_rec(m, level, prec, x, b, nu1, nu2, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
+                     const hhg_solve_opts* opts, hhg_solve_report* rep, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    need(x, "x");
+    need(b, "b");
+    hhg_solve_opts o{HHG_SOLVE_MG, 3, 3, 100, 1e-10};
+    if (opts) o = *opts;
+    if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 0 || !(o.tol >= 0.0)) throw ArgError("bad solve options");
+    if (o.mode != HHG_SOLVE_MG && o.mode != HHG_SOLVE_IR) throw ArgError("bad solve mode");
+    cudaStream_t st = S(stream);
+    const hhg::LevelData& ld = m.levels[level];
+    double* nrm = m.scalars;
+    hhg::ghost_fill(m, level, 0, x, st);
+    // initial residual (IR: written in FP32 as the first inner right-hand side)
+    if (o.mode == HHG_SOLVE_IR)
+      hhg::residual_f64_to_f32(m, level, x, b, (float*)ld.b[1], nrm, st);
+    else
+      hhg::residual_op(m, level, 0, x, b, ld.r[0], nrm, st);
+    double r0 = std::sqrt(read_scalar(nrm, st));
+    double r = r0;
+    int it = 0;
+    hhg_status status = HHG_OK;
+    auto record = [&](int k, double v) {
+      if (rep && rep->history && k < rep->history_cap) rep->history[k] = v;
+    };
+    record(0, r0);
+    if (!std::isfinite(r0)) status = HHG_ERR_NAN;
+    while (status == HHG_OK && r > o.tol * r0 && r0 > 0.0) {
+      if (it >= o.max_iter) {
+        status = HHG_ERR_NOT_CONVERGED;
+        break;
+      }
+      if (o.mode == HHG_SOLVE_IR) {
+        // inner FP32 V-cycle on A d = r from d = 0, then x += d in FP64
+        hhg::zero_vec(m, level, 1, ld.x[1], st);
+        vcycle_rec(m, level, 1, ld.x[1], ld.b[1], o.nu1, o.nu2, st);
+        hhg::update_f64_from_f32(m, level, x, (const float*)ld.x[1], st);
+        hhg::residual_f64_to_f32(m, level, x, b, (float*)ld.b[1], nrm, st);
+      } else {
+        vcycle_rec(m, level, 0, x, b, o.nu1, o.nu2, st);
+        hhg::residual_op(m, level, 0, x, b, ld.r[0], nrm, st);
+      }
+      ++it;
+      r = std::sqrt(read_scalar(nrm, st));
+      record(it, r);
+      if (!std::isfinite(r)) status = HHG_ERR_NAN;
+    }
+    if (rep) {
+      rep->iterations = it;
+      rep->status = status;
+      rep->r0 = r0;
+      rep->r_final = r;
+    }
+    if (status == HHG_ERR_NAN) return fail(status, "non-finite residual norm");
+    if (status == HHG_ERR_NOT_CONVERGED) return fail(status, "max_iter reached");
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_profile_begin(uint32_t mask, int32_t level) {
+  return guarded([&]() {
+    hhg::profile_begin(mask, level);
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_profile_end(int64_t* launches, double* ms) {
+  return guarded([&]() {
+    hhg::profile_end(launches, ms);
+    return HHG_OK;
+  });
+}
+
+size_t hhg_last_error(char* buf, size_t n) {
+  if (buf && n) {
+    const size_t k = g_error.size() < n - 1 ? g_error.size() : n - 1;
+    std::memcpy(buf, g_error.data(), k);
+    buf[k] = '\0';
+  }
+  return g_error.size();
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Internal data structures of libhhg (host and device).
+//
+// Layout of one level vector (Sec. 3.2: an indexing function maps the
+// topological index of an unknown to memory; here one function per primitive
+// type, chosen for coalesced row access on the GPU):
+//   vertex block  v_off + v                              (macro-vertex v)
+//   edge block    e_off + e * ES + t,   t = 0..N          (t from the low-id end;
+//                                                          t = 0, N are vertex copies)
+//   face block    f_off + f * FS + j * S + i, i,j >= 0, i + j <= N
+//                 (S = row stride, FS = (N + 1) * S; boundary points are copies)
+// Micro-triangle coefficients use the same face slots: upward triangle (i,j)
+// in the "up" array, downward (i,j) in the "down" array.
+#pragma once
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hhg.h"
+
+namespace hhg {
+
+// Invalid macro mesh (reported as HHG_ERR_MESH).
+struct MeshError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+struct LevelView {
+  int N;
+  int64_t S, ES, FS;
+  int64_t v_off, e_off, f_off, len;
+};
+
+inline LevelView make_level_view(int nv, int ne, int nf, int level) {
+  LevelView L;
+  L.N = 1 << level;
+  auto up = [](int64_t a, int64_t m) { return (a + m - 1) / m * m; };
+  L.S = up(L.N + 1, 8);
+  L.ES = up(L.N + 1, 8);
+  L.FS = (int64_t)(L.N + 1) * L.S;
+  L.v_off = 0;
+  L.e_off = up(nv, 64);
+  L.f_off = up(L.e_off + (int64_t)ne * L.ES, 64);
+  L.len = L.f_off + (int64_t)nf * L.FS;
+  return L;
+}
+
+// One macro-face.  Vertices (v[0], v[1], v[2]) counter-clockwise; cot[m] =
+// cotangent of the interior angle at v[m].  Side r runs from v[r] to
+// v[(r+1)%3]; edge[r] is its macro-edge and aligned[r] = 1 when v[r] is that
+// edge's low-id vertex (edge index t then equals the side position p).
+struct FaceRec {
+  double cot[3];
+  int v[3];
+  int edge[3];
+  int aligned[3];
+};
+
+// A face seen from one of its edges: side `rot` of face `face`.
+struct EdgeSide {
+  int face, rot, aligned, pad;
+};
+
+struct EdgeRec {
+  int lo, hi, dirichlet, nfaces;
+  EdgeSide side[2];
+};
+
+// A face corner seen from its macro-vertex: the vertex is v[rot] of `face`.
+struct Corner {
+  int face, rot;
+};
+
+// A macro-edge seen from one of its end vertices.
+struct VertEdge {
+  int edge, is_low;
+};
+
+struct VertRec {
+  int dirichlet;
+  int c_begin, c_end;   // range in the corner table
+  int e_begin, e_end;   // range in the vertex-edge table
+};
+
+struct MeshTables {
+  const FaceRec* faces;
+  const EdgeRec* edges;
+  const VertRec* verts;
+  const Corner* corners;
+  const VertEdge* vedges;
+  int nv, ne, nf;
+};
+
+// ---------------------------------------------------------------- indexing
+// Rotated face frame: rotation r relabels the face as (v[r], v[r+1], v[r+2]);
+// its lattice point (ip, jp) is stored at slot base + ip * a + jp * b.
+// rot 0: (i, j) = (ip, jp)            -> slot ip + S jp
+// rot 1: (i, j) = (N - ip - jp, ip)   -> slot N + ip (S - 1) - jp
+// rot 2: (i, j) = (jp, N - ip - jp)   -> slot S N - S ip + (1 - S) jp
+__host__ __device__ inline int64_t rot_slot(const LevelView& L, int rot, int ip, int jp) {
+  const int64_t S = L.S, N = L.N;
+  if (rot == 0) return ip + S * jp;
+  if (rot == 1) return N + ip * (S - 1) - jp;
+  return S * N - S * ip + (1 - S) * jp;
+}
+// Upward micro-triangle (ip, jp) of the rotated frame in the "up" array.
+__host__ __device__ inline int64_t rot_up(const LevelView& L, int rot, int ip, int jp) {
+  const int64_t S = L.S, N = L.N;
+  if (rot == 0) return ip + S * jp;
+  if (rot == 1) return (N - 1) + ip * (S - 1) - jp;
+  return S * (N - 1) - S * ip + (1 - S) * jp;
+}
+// Downward micro-triangle (ip, jp) of the rotated frame in the "down" array.
+__host__ __device__ inline int64_t rot_dn(const LevelView& L, int rot, int ip, int jp) {
+  const int64_t S = L.S, N = L.N;
+  if (rot == 0) return ip + S * jp;
+  if (rot == 1) return (N - 2) + ip * (S - 1) - jp;
+  return S * (N - 2) - S * ip + (1 - S) * jp;
+}
+
+// ---------------------------------------------------------------- host mesh
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct LevelData {
+  LevelView lv;
+  int n_colours = 0;
+  std::vector<int> colour_ptr;      // host copy: colour c = [ptr[c], ptr[c+1])
+  int* colour_list = nullptr;       // device: packed e * (N + 1) + t
+  int64_t n_nodes = 0, n_free = 0;
+  // workspaces per precision [0] = double, [1] = float
+  void* x[2] = {nullptr, nullptr};  // coarse-level iterates (unused on the top level)
+  void* b[2] = {nullptr, nullptr};
+  void* r[2] = {nullptr, nullptr};
+  void* k[2] = {nullptr, nullptr};  // coefficient: up array then down array (2 * nf * FS)
+};
+
+struct Mesh {
+  int nv = 0, ne = 0, nf = 0, max_level = 0;
+  std::vector<FaceRec> h_faces;
+  std::vector<EdgeRec> h_edges;
+  std::vector<VertRec> h_verts;
+  std::vector<Corner> h_corners;
+  std::vector<VertEdge> h_vedges;
+  std::vector<double> h_xy;
+  MeshTables tab{};
+  std::vector<void*> allocations;
+  std::vector<LevelData> levels;
+  bool vark = false;
+  // level-0 coarse solve: dense matrix over free vertices (double), index map
+  int n0 = 0;
+  double* A0 = nullptr;             // n0 x n0, row-major
+  int* free0 = nullptr;             // n0 vertex ids
+  std::vector<double> h_cot_unit;   // cached for k = 1
+  // reduction scratch
+  double* partials = nullptr;       // kMaxPartials doubles
+  double* scalars = nullptr;        // 16 doubles of device scalars
+  int device = 0;
+};
+
+constexpr int kMaxPartials = 4096;
+
+// ---------------------------------------------------------------- launchers
+// All launchers are asynchronous on `st`; `prec` selects double (0) / float (1).
+void ghost_fill(const Mesh& m, int level, int prec, void* v, cudaStream_t st);
+void apply_op(const Mesh& m, int level, int prec, const void* x, void* y, cudaStream_t st);
+// r = b - A x; optional sum of squares over free DoFs into *norm2_dev (double)
+void residual_op(const Mesh& m, int level, int prec, const void* x, const void* b, void* r,
+                 double* norm2_dev, cudaStream_t st);
+void gs_sweep(const Mesh& m, int level, int prec, void* x, const void* b, bool forward,
+              cudaStream_t st);
+void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,
+                  void* work, cudaStream_t st);
+void restrict_op(const Mesh& m, int fine_level, int prec, const void* r_fine, void* b_coarse,
+                 cudaStream_t st);
+void prolongate_add(const Mesh& m, int fine_level, int prec, const void* x_coarse, void* x_fine,
+                    cudaStream_t st);
+void coarse_solve(const Mesh& m, int prec, const void* b0, void* x0, cudaStream_t st);
+void zero_vec(const Mesh& m, int level, int prec, void* v, cudaStream_t st);
+void assign_op(const Mesh& m, int level, int prec, double a, const void* x1, double b,
+               const void* x2, void* dst, cudaStream_t st);
+void dot_op(const Mesh& m, int level, int prec, const void* x1, const void* x2, double* out_dev,
+            cudaStream_t st);
+void canonical_op(const Mesh& m, int level, int prec, const void* src, void* dst, bool to_canon,
+                  cudaStream_t st);
+void coarsen_k(const Mesh& m, int coarse_level, int prec_src_dst, cudaStream_t st);
+void load_k_fine(const Mesh& m, const double* k_canon, cudaStream_t st);
+void convert_k_to_f32(const Mesh& m, int level, cudaStream_t st);
+void sqrt_scalar(double* v, cudaStream_t st);
+// mixed precision helpers for iterative refinement
+void residual_f64_to_f32(const Mesh& m, int level, const double* x, const double* b, float* r32,
+                         double* norm2_dev, cudaStream_t st);
+void update_f64_from_f32(const Mesh& m, int level, double* x, const float* d32, cudaStream_t st);
+
+void check_cuda(cudaError_t e, const char* what);
+
+// Counts one kernel launch of class `cls` (hhg_kernel_class); while profiling
+// is on for that class and level, brackets it with CUDA events on `st`.
+class LaunchScope {
+ public:
+  LaunchScope(int cls, int level, cudaStream_t st);
+  ~LaunchScope();
+  LaunchScope(const LaunchScope&) = delete;
+  LaunchScope& operator=(const LaunchScope&) = delete;
+
+ private:
+  int cls_;
+  cudaStream_t st_;
+  cudaEvent_t start_ = nullptr, stop_ = nullptr;
+};
+void profile_begin(uint32_t mask, int level);
+void profile_end(int64_t* launches, double* ms);
+
+}  // namespace hhg

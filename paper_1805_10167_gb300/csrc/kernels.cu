@@ -1,0 +1,835 @@
+// CUDA kernels of the HHG P1 multigrid path (sm_103a).
+//
+// Work decomposition: macro-vertices and edge-interior points are few
+// (0.3 % of the unknowns at level 10); they get one thread each.  Face
+// interiors hold the rest; there one warp walks one lattice row (coalesced
+// loads along i), eight rows per 256-thread block, grid-stride over all
+// (face, row) pairs.  Reductions are per-block partial sums summed in a fixed
+// order by a single block, so norms and dots are bitwise reproducible.
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+
+#include "stencil.cuh"
+
+namespace hhg {
+
+enum Mode { APPLY = 0, RESID = 1, GS = 2, JAC = 3 };
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxBlocksV = 256, kMaxBlocksE = 1024, kMaxBlocksF = 2432;
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw std::runtime_error(std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static inline void check_launch(const char* what) { check_cuda(cudaGetLastError(), what); }
+
+// Launch `...` counted (and, when profiled, timed) as class `cls` on `level`.
+#define HHG_LAUNCH(cls, level, st, what, ...)  \
+  do {                                         \
+    LaunchScope hhg_ls_((cls), (level), (st)); \
+    __VA_ARGS__;                               \
+    check_launch(what);                        \
+  } while (0)
+
+static inline int blocks_for(int64_t n, int per_block, int cap) {
+  int64_t b = (n + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[kWarps];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  }
+  __syncthreads();
+  return s;
+}
+
+// --------------------------------------------------------------- ghost fill
+// Alg. 3 (a)-(d): copy every owner value into the slots that hold copies of
+// it -- face boundary rows from edges and vertices, edge end points from
+// vertices.  The face reads its side in its own orientation (Sec. 3.3: the
+// higher-dimensional primitive handles the orientation).
+template <typename T>
+__global__ void k_ghost_fill(MeshTables M, LevelView L, T* __restrict__ v) {
+  const int64_t nface = (int64_t)M.nf * 3 * (L.N + 1);
+  const int64_t total = nface + M.ne;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    if (idx < nface) {
+      const int f = (int)(idx / (3 * (L.N + 1)));
+      const int rem = (int)(idx - (int64_t)f * 3 * (L.N + 1));
+      const int r = rem / (L.N + 1), p = rem % (L.N + 1);
+      const FaceRec& F = M.faces[f];
+      T val;
+      if (p == 0) {
+        val = v[L.v_off + F.v[r]];
+      } else if (p == L.N) {
+        val = v[L.v_off + F.v[(r + 1) % 3]];
+      } else {
+        const int t = F.aligned[r] ? p : L.N - p;
+        val = v[L.e_off + (int64_t)F.edge[r] * L.ES + t];
+      }
+      v[L.f_off + (int64_t)f * L.FS + rot_slot(L, r, p, 0)] = val;
+    } else {
+      const int e = (int)(idx - nface);
+      const EdgeRec& E = M.edges[e];
+      T* ve = v + L.e_off + (int64_t)e * L.ES;
+      ve[0] = v[L.v_off + E.lo];
+      ve[L.N] = v[L.v_off + E.hi];
+    }
+  }
+}
+
+// --------------------------------------------------------------- vertex rows
+template <typename T, typename TO, bool VARK, int MODE>
+__global__ void k_vertex(MeshTables M, LevelView L, const T* __restrict__ x, TO* out,
+                         const T* __restrict__ b, const T* __restrict__ k, double* partials,
+                         double omega) {
+  double acc = 0.0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < M.nv; v += gridDim.x * blockDim.x) {
+    const VertRec V = M.verts[v];
+    const int64_t s = L.v_off + v;
+    if (V.dirichlet) {
+      if (MODE == APPLY || MODE == RESID) out[s] = TO(0);
+      if (MODE == JAC) out[s] = (TO)x[s];
+      continue;
+    }
+    T off, diag;
+    vertex_row<T, VARK>(M, L, V, x, k, off, diag);
+    if (MODE == APPLY) {
+      out[s] = (TO)(diag * x[s] + off);
+    } else if (MODE == RESID) {
+      const T r = b[s] - (diag * x[s] + off);
+      out[s] = (TO)r;
+      acc += (double)r * (double)r;
+    } else if (MODE == JAC) {
+      out[s] = (TO)(x[s] + T(omega) * (b[s] - (diag * x[s] + off)) / diag);
+    } else {  // GS: update in place and push the new value to every copy
+      const T nv = (b[s] - off) / diag;
+      T* xo = (T*)out;
+      xo[s] = nv;
+      for (int c = V.c_begin; c < V.c_end; ++c) {
+        const Corner cn = M.corners[c];
+        xo[L.f_off + (int64_t)cn.face * L.FS + rot_slot(L, cn.rot, 0, 0)] = nv;
+      }
+      for (int c = V.e_begin; c < V.e_end; ++c) {
+        const VertEdge ve = M.vedges[c];
+        xo[L.e_off + (int64_t)ve.edge * L.ES + (ve.is_low ? 0 : L.N)] = nv;
+      }
+    }
+  }
+  if (MODE == RESID) {
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+// --------------------------------------------------------------- edge rows
+// list == nullptr: all edge-interior points; else packed e * (N + 1) + t.
+template <typename T, typename TO, bool VARK, int MODE>
+__global__ void k_edge(MeshTables M, LevelView L, const int* __restrict__ list, int64_t n,
+                       const T* __restrict__ x, TO* out, const T* __restrict__ b,
+                       const T* __restrict__ k, double* partials, double omega) {
+  double acc = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int e, t;
+    if (list) {
+      const int pk = list[idx];
+      e = pk / (L.N + 1);
+      t = pk - e * (L.N + 1);
+    } else {
+      e = (int)(idx / (L.N - 1));
+      t = (int)(idx - (int64_t)e * (L.N - 1)) + 1;
+    }
+    const EdgeRec E = M.edges[e];
+    const int64_t s = L.e_off + (int64_t)e * L.ES + t;
+    if (E.dirichlet) {
+      if (MODE == APPLY || MODE == RESID) out[s] = TO(0);
+      if (MODE == JAC) out[s] = (TO)x[s];
+      continue;
+    }
+    T off, diag;
+    edge_row<T, VARK>(M, L, E, t, x, k, off, diag);
+    if (MODE == APPLY) {
+      out[s] = (TO)(diag * x[s] + off);
+    } else if (MODE == RESID) {
+      const T r = b[s] - (diag * x[s] + off);
+      out[s] = (TO)r;
+      acc += (double)r * (double)r;
+    } else if (MODE == JAC) {
+      out[s] = (TO)(x[s] + T(omega) * (b[s] - (diag * x[s] + off)) / diag);
+    } else {
+      const T nv = (b[s] - off) / diag;
+      T* xo = (T*)out;
+      xo[s] = nv;
+      for (int q = 0; q < E.nfaces; ++q) {
+        const EdgeSide sd = E.side[q];
+        const int p = sd.aligned ? t : L.N - t;
+        xo[L.f_off + (int64_t)sd.face * L.FS + rot_slot(L, sd.rot, p, 0)] = nv;
+      }
+    }
+  }
+  if (MODE == RESID) {
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+// --------------------------------------------------------------- face rows
+// One warp per interior row j = 1..N-2 of a face; GS updates the points of
+// one colour (i + 2j) mod 3 == colour in place.
+template <typename T, typename TO, bool VARK, int MODE>
+__global__ void k_face(MeshTables M, LevelView L, const T* __restrict__ x, TO* out,
+                       const T* __restrict__ b, const T* __restrict__ k, int colour,
+                       double* partials, double omega) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int rows = L.N - 2;
+  const int64_t ntask = (int64_t)M.nf * rows;
+  double acc = 0.0;
+  for (int64_t task = warp; task < ntask; task += nwarps) {
+    const int f = (int)(task / rows);
+    const int j = (int)(task - (int64_t)f * rows) + 1;
+    const FaceRec& F = M.faces[f];
+    const T c0 = (T)F.cot[0], c1 = (T)F.cot[1], c2 = (T)F.cot[2];
+    const int64_t fb = L.f_off + (int64_t)f * L.FS;
+    const T* xf = x + fb;
+    const T* ku = VARK ? k + (int64_t)f * L.FS : nullptr;
+    const T* kd = VARK ? k + (int64_t)(M.nf + f) * L.FS : nullptr;
+    const int iend = L.N - j;  // exclusive
+    int i0 = 1 + lane, step = 32;
+    if (MODE == GS) {
+      int c = ((colour - 2 * j) % 3 + 3) % 3;
+      if (c == 0) c = 3;
+      i0 = c + 3 * lane;
+      step = 96;
+    }
+    for (int i = i0; i < iend; i += step) {
+      const int64_t p = (int64_t)j * L.S + i;
+      T off, diag;
+      face_row<T, VARK>(c0, c1, c2, L.S, xf, ku, kd, p, off, diag);
+      if (MODE == APPLY) {
+        out[fb + p] = (TO)(diag * xf[p] + off);
+      } else if (MODE == RESID) {
+        const T r = b[fb + p] - (diag * xf[p] + off);
+        out[fb + p] = (TO)r;
+        acc += (double)r * (double)r;
+      } else if (MODE == JAC) {
+        out[fb + p] = (TO)(xf[p] + T(omega) * (b[fb + p] - (diag * xf[p] + off)) / diag);
+      } else {
+        ((T*)out)[fb + p] = (b[fb + p] - off) / diag;
+      }
+    }
+  }
+  if (MODE == RESID) {
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+// --------------------------------------------------------------- reductions
+__global__ void k_sum_partials(const double* __restrict__ partials, int n, double* out,
+                               int take_sqrt) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) *out = take_sqrt ? sqrt(s) : s;
+}
+
+__global__ void k_sqrt(double* v) { *v = sqrt(*v); }
+
+template <typename T>
+__global__ void k_dot(MeshTables M, LevelView L, const T* __restrict__ x1,
+                      const T* __restrict__ x2, double* partials) {
+  // owned free DoFs: free vertices, free edge interiors, face interiors
+  const int64_t nE = (L.N >= 2) ? (int64_t)M.ne * (L.N - 1) : 0;
+  const int rows = L.N >= 3 ? L.N - 2 : 0;
+  const int64_t nrow = (int64_t)M.nf * rows;
+  double acc = 0.0;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = tid; v < M.nv; v += nth)
+    if (!M.verts[v].dirichlet) acc += (double)x1[L.v_off + v] * (double)x2[L.v_off + v];
+  for (int64_t idx = tid; idx < nE; idx += nth) {
+    const int e = (int)(idx / (L.N - 1));
+    const int t = (int)(idx - (int64_t)e * (L.N - 1)) + 1;
+    if (!M.edges[e].dirichlet) {
+      const int64_t s = L.e_off + (int64_t)e * L.ES + t;
+      acc += (double)x1[s] * (double)x2[s];
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  for (int64_t task = tid >> 5; task < nrow; task += nth >> 5) {
+    const int f = (int)(task / rows);
+    const int j = (int)(task - (int64_t)f * rows) + 1;
+    const int64_t base = L.f_off + (int64_t)f * L.FS + (int64_t)j * L.S;
+    for (int i = 1 + lane; i < L.N - j; i += 32) acc += (double)x1[base + i] * (double)x2[base + i];
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// --------------------------------------------------------------- transfers
+// Restriction R = P^T (full weighting) onto coarse owners; coarse Dirichlet
+// entries are 0.  Vertex and edge part: one thread per coarse unknown.
+template <typename T>
+__global__ void k_restrict_ve(MeshTables M, LevelView Lf, LevelView Lc, const T* __restrict__ rf,
+                              T* __restrict__ bc) {
+  const int Nc = Lc.N;
+  const int64_t nE = (Nc >= 2) ? (int64_t)M.ne * (Nc - 1) : 0;
+  const int64_t total = M.nv + nE;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    if (idx < M.nv) {
+      const int v = (int)idx;
+      const VertRec V = M.verts[v];
+      T val = T(0);
+      if (!V.dirichlet) {
+        val = rf[Lf.v_off + v];
+        T s = T(0);
+        for (int c = V.e_begin; c < V.e_end; ++c) {
+          const VertEdge ve = M.vedges[c];
+          s += rf[Lf.e_off + (int64_t)ve.edge * Lf.ES + (ve.is_low ? 1 : Lf.N - 1)];
+        }
+        val += T(0.5) * s;
+      }
+      bc[Lc.v_off + v] = val;
+    } else {
+      const int64_t q = idx - M.nv;
+      const int e = (int)(q / (Nc - 1));
+      const int tc = (int)(q - (int64_t)e * (Nc - 1)) + 1;
+      const EdgeRec E = M.edges[e];
+      T val = T(0);
+      if (!E.dirichlet) {
+        const T* re = rf + Lf.e_off + (int64_t)e * Lf.ES;
+        T s = re[2 * tc - 1] + re[2 * tc + 1];
+        for (int k = 0; k < E.nfaces; ++k) {
+          const EdgeSide sd = E.side[k];
+          const int p = 2 * (sd.aligned ? tc : Nc - tc);
+          const T* rff = rf + Lf.f_off + (int64_t)sd.face * Lf.FS;
+          s += rff[rot_slot(Lf, sd.rot, p, 1)] + rff[rot_slot(Lf, sd.rot, p - 1, 1)];
+        }
+        val = re[2 * tc] + T(0.5) * s;
+      }
+      bc[Lc.e_off + (int64_t)e * Lc.ES + tc] = val;
+    }
+  }
+}
+
+// Face part: one warp per coarse interior row J; coarse (I, J) gathers fine
+// (2I, 2J) and half of its six lattice neighbours.
+template <typename T>
+__global__ void k_restrict_face(MeshTables M, LevelView Lf, LevelView Lc,
+                                const T* __restrict__ rf, T* __restrict__ bc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int rows = Lc.N - 2;
+  const int64_t ntask = (int64_t)M.nf * rows;
+  const int64_t S = Lf.S;
+  for (int64_t task = warp; task < ntask; task += nwarps) {
+    const int f = (int)(task / rows);
+    const int J = (int)(task - (int64_t)f * rows) + 1;
+    const T* r = rf + Lf.f_off + (int64_t)f * Lf.FS;
+    T* o = bc + Lc.f_off + (int64_t)f * Lc.FS + (int64_t)J * Lc.S;
+    for (int I = 1 + lane; I < Lc.N - J; I += 32) {
+      const int64_t p = (int64_t)(2 * J) * S + 2 * I;
+      o[I] = r[p] + T(0.5) * ((r[p + 1] + r[p - 1]) + (r[p + S] + r[p - S]) +
+                              (r[p + 1 - S] + r[p - 1 + S]));
+    }
+  }
+}
+
+// Prolongation and correction x_f += P x_c (linear interpolation).  Vertex
+// and edge part covers the owners and the edge end-point copies.
+template <typename T>
+__global__ void k_prolong_ve(MeshTables M, LevelView Lf, LevelView Lc, const T* __restrict__ xc,
+                             T* __restrict__ xf) {
+  const int Nf = Lf.N;
+  const int64_t nE = (int64_t)M.ne * (Nf + 1);
+  const int64_t total = M.nv + nE;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    if (idx < M.nv) {
+      const int v = (int)idx;
+      if (!M.verts[v].dirichlet) xf[Lf.v_off + v] += xc[Lc.v_off + v];
+    } else {
+      const int64_t q = idx - M.nv;
+      const int e = (int)(q / (Nf + 1));
+      const int t = (int)(q - (int64_t)e * (Nf + 1));
+      const bool interior = (t > 0 && t < Nf);
+      if (interior && M.edges[e].dirichlet) continue;
+      const T* ce = xc + Lc.e_off + (int64_t)e * Lc.ES;
+      const int tc = t >> 1;
+      const T val = (t & 1) ? T(0.5) * (ce[tc] + ce[tc + 1]) : ce[tc];
+      xf[Lf.e_off + (int64_t)e * Lf.ES + t] += val;
+    }
+  }
+}
+
+// Face part: every closed-lattice point (boundary copies included, computed
+// from the coarse face's copies with the same arithmetic as the owners).
+template <typename T>
+__global__ void k_prolong_face(MeshTables M, LevelView Lf, LevelView Lc, const T* __restrict__ xc,
+                               T* __restrict__ xf) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int rows = Lf.N + 1;
+  const int64_t ntask = (int64_t)M.nf * rows;
+  const int64_t Sc = Lc.S;
+  for (int64_t task = warp; task < ntask; task += nwarps) {
+    const int f = (int)(task / rows);
+    const int j = (int)(task - (int64_t)f * rows);
+    const T* c = xc + Lc.f_off + (int64_t)f * Lc.FS;
+    T* o = xf + Lf.f_off + (int64_t)f * Lf.FS + (int64_t)j * Lf.S;
+    const int J = j >> 1;
+    for (int i = lane; i <= Lf.N - j; i += 32) {
+      const int I = i >> 1;
+      const int64_t q = (int64_t)J * Sc + I;
+      T val;
+      if (!(i & 1) && !(j & 1)) val = c[q];
+      else if ((i & 1) && !(j & 1)) val = T(0.5) * (c[q] + c[q + 1]);
+      else if (!(i & 1)) val = T(0.5) * (c[q] + c[q + Sc]);
+      else val = T(0.5) * (c[q + 1] + c[q + Sc]);
+      o[i] += val;
+    }
+  }
+}
+
+// --------------------------------------------------------------- coarse CG
+// Plain conjugate gradients on the dense level-0 matrix over the free
+// macro-vertices (one block; level 0 has only vertex unknowns), in double,
+// to ||r|| <= 1e-14 ||b|| or 2 n0 iterations.
+template <typename T>
+__global__ void k_coarse_cg(int n0, const double* __restrict__ A, const int* __restrict__ idx,
+                            const T* __restrict__ b, T* __restrict__ x, int64_t v_off) {
+  extern __shared__ double sh[];
+  double* xs = sh;
+  double* r = sh + n0;
+  double* p = sh + 2 * n0;
+  double* Ap = sh + 3 * n0;
+  double part = 0.0;
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+    const double bi = (double)b[v_off + idx[i]];
+    xs[i] = 0.0;
+    r[i] = bi;
+    p[i] = bi;
+    part += bi * bi;
+  }
+  double rr = block_sum(part);
+  __shared__ double bcast;
+  if (threadIdx.x == 0) bcast = rr;
+  __syncthreads();
+  rr = bcast;
+  const double stop = 1e-28 * rr;
+  for (int it = 0; it < 2 * n0 && rr > stop && rr > 0.0; ++it) {
+    double pap = 0.0;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+      double s = 0.0;
+      for (int j = 0; j < n0; ++j) s += A[(int64_t)i * n0 + j] * p[j];
+      Ap[i] = s;
+      pap += p[i] * s;
+    }
+    pap = block_sum(pap);
+    if (threadIdx.x == 0) bcast = pap;
+    __syncthreads();
+    const double alpha = rr / bcast;
+    double rn = 0.0;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+      xs[i] += alpha * p[i];
+      r[i] -= alpha * Ap[i];
+      rn += r[i] * r[i];
+    }
+    rn = block_sum(rn);
+    if (threadIdx.x == 0) bcast = rn;
+    __syncthreads();
+    const double beta = bcast / rr;
+    rr = bcast;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) p[i] = r[i] + beta * p[i];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) x[v_off + idx[i]] = (T)xs[i];
+}
+
+// --------------------------------------------------------------- BLAS-1
+template <typename T>
+__global__ void k_assign(int64_t n, T a, const T* __restrict__ x1, T b, const T* __restrict__ x2,
+                         T* dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = a * x1[i] + b * x2[i];
+}
+
+__global__ void k_update_f64(int64_t n, double* __restrict__ x, const float* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ o) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = (float)a[i];
+}
+
+// --------------------------------------------------------------- canonical order
+template <typename T>
+__global__ void k_canon_ve(MeshTables M, LevelView L, const T* __restrict__ src, T* __restrict__ dst,
+                           int to_canon) {
+  const int64_t nEi = (L.N >= 2) ? (int64_t)(L.N - 1) : 0;
+  const int64_t total = M.nv + (int64_t)M.ne * nEi;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s;
+    if (c < M.nv) {
+      s = L.v_off + c;
+    } else {
+      const int64_t q = c - M.nv;
+      const int64_t e = q / nEi;
+      s = L.e_off + e * L.ES + (q - e * nEi) + 1;
+    }
+    if (to_canon) dst[c] = src[s];
+    else dst[s] = src[c];
+  }
+}
+
+template <typename T>
+__global__ void k_canon_face(MeshTables M, LevelView L, const T* __restrict__ src, T* __restrict__ dst,
+                             int to_canon, int64_t face_canon_off) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int N = L.N, rows = N - 2;
+  const int64_t nfi = (int64_t)(N - 1) * (N - 2) / 2;
+  const int64_t ntask = (int64_t)M.nf * rows;
+  for (int64_t task = warp; task < ntask; task += nwarps) {
+    const int f = (int)(task / rows);
+    const int j = (int)(task - (int64_t)f * rows) + 1;
+    const int64_t cbase = face_canon_off + f * nfi + (int64_t)(j - 1) * (N - 1) - (int64_t)(j - 1) * j / 2 - 1;
+    const int64_t sbase = L.f_off + (int64_t)f * L.FS + (int64_t)j * L.S;
+    for (int i = 1 + lane; i < N - j; i += 32) {
+      if (to_canon) dst[cbase + i] = src[sbase + i];
+      else dst[sbase + i] = src[cbase + i];
+    }
+  }
+}
+
+// --------------------------------------------------------------- coefficient
+// Canonical element order -> up/down slot arrays of the finest level (double).
+__global__ void k_load_k(MeshTables M, LevelView L, const double* __restrict__ kc,
+                         double* __restrict__ k) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int N = L.N;
+  const int64_t per_face = (int64_t)N * N;
+  const int64_t ntask = (int64_t)M.nf * (2 * N - 1);   // N up rows + N-1 down rows
+  for (int64_t task = warp; task < ntask; task += nwarps) {
+    const int f = (int)(task / (2 * N - 1));
+    const int rr = (int)(task - (int64_t)f * (2 * N - 1));
+    const bool down = rr >= N;
+    const int j = down ? rr - N : rr;
+    const int len = down ? N - 1 - j : N - j;
+    const int64_t cb = f * per_face + (down ? (int64_t)N * (N + 1) / 2 + (int64_t)j * (N - 1) - (int64_t)j * (j - 1) / 2
+                                            : (int64_t)j * N - (int64_t)j * (j - 1) / 2);
+    double* o = k + (int64_t)((down ? M.nf : 0) + f) * L.FS + (int64_t)j * L.S;
+    for (int i = lane; i < len; i += 32) o[i] = kc[cb + i];
+  }
+}
+
+// Coarse element = mean of its four children.
+template <typename T>
+__global__ void k_coarsen_k(MeshTables M, LevelView Lf, LevelView Lc, const T* __restrict__ kf,
+                            T* __restrict__ kc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int Nc = Lc.N;
+  const int64_t ntask = (int64_t)M.nf * Nc;
+  const int64_t S = Lf.S;
+  for (int64_t task = warp; task < ntask; task += nwarps) {
+    const int f = (int)(task / Nc);
+    const int J = (int)(task - (int64_t)f * Nc);
+    const T* uf = kf + (int64_t)f * Lf.FS;
+    const T* df = kf + (int64_t)(M.nf + f) * Lf.FS;
+    T* uc = kc + (int64_t)f * Lc.FS + (int64_t)J * Lc.S;
+    T* dc = kc + (int64_t)(M.nf + f) * Lc.FS + (int64_t)J * Lc.S;
+    for (int I = lane; I < Nc - J; I += 32) {
+      const int64_t p = (int64_t)(2 * J) * S + 2 * I;   // fine (2I, 2J)
+      uc[I] = (uf[p] + uf[p + 1] + uf[p + S] + df[p]) * T(0.25);
+      if (I < Nc - 1 - J)
+        dc[I] = (df[p + 1] + df[p + S] + df[p + 1 + S] + uf[p + 1 + S]) * T(0.25);
+    }
+  }
+}
+
+// ================================================================ launchers
+template <typename T>
+static const T* kptr(const Mesh& m, int level) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  return m.vark ? (const T*)m.levels[level].k[prec] : nullptr;
+}
+
+template <typename T>
+static void ghost_fill_t(const Mesh& m, int level, T* v, cudaStream_t st) {
+  const LevelView& L = m.levels[level].lv;
+  const int64_t total = (int64_t)m.nf * 3 * (L.N + 1) + m.ne;
+  HHG_LAUNCH(HHG_K_GHOST, level, st, "ghost_fill", k_ghost_fill<T><<<blocks_for(total, kThreads, 4096), kThreads, 0, st>>>(m.tab, L, v));
+}
+
+void ghost_fill(const Mesh& m, int level, int prec, void* v, cudaStream_t st) {
+  if (prec == 0) ghost_fill_t(m, level, (double*)v, st);
+  else ghost_fill_t(m, level, (float*)v, st);
+}
+
+// Runs the vertex, edge and face kernels of one mode; returns the number of
+// partial sums written (RESID only).
+template <typename T, typename TO, bool VARK, int MODE>
+static int rows_all(const Mesh& m, int level, const T* x, TO* out, const T* b, double* partials,
+                    double omega, cudaStream_t st) {
+  const LevelView& L = m.levels[level].lv;
+  const T* k = kptr<T>(m, level);
+  const int bv = blocks_for(m.nv, kThreads, kMaxBlocksV);
+  HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "vertex rows", k_vertex<T, TO, VARK, MODE><<<bv, kThreads, 0, st>>>(m.tab, L, x, out, b, k, partials, omega));
+  int used = bv;
+  if (L.N >= 2) {
+    const int64_t nE = (int64_t)m.ne * (L.N - 1);
+    const int be = blocks_for(nE, kThreads, kMaxBlocksE);
+    HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "edge rows", k_edge<T, TO, VARK, MODE><<<be, kThreads, 0, st>>>(m.tab, L, nullptr, nE, x, out, b, k,
+                                                       partials ? partials + used : nullptr, omega));
+    used += be;
+  }
+  if (L.N >= 3) {
+    const int64_t ntask = (int64_t)m.nf * (L.N - 2);
+    const int bf = blocks_for(ntask, kWarps, kMaxBlocksF);
+    HHG_LAUNCH(HHG_K_FACE_ROWS, level, st, "face rows", k_face<T, TO, VARK, MODE><<<bf, kThreads, 0, st>>>(m.tab, L, x, out, b, k, 0,
+                                                       partials ? partials + used : nullptr, omega));
+    used += bf;
+  }
+  return used;
+}
+
+template <typename T, typename TO, int MODE>
+static int rows_dispatch(const Mesh& m, int level, const T* x, TO* out, const T* b,
+                         double* partials, double omega, cudaStream_t st) {
+  if (m.vark) return rows_all<T, TO, true, MODE>(m, level, x, out, b, partials, omega, st);
+  return rows_all<T, TO, false, MODE>(m, level, x, out, b, partials, omega, st);
+}
+
+void apply_op(const Mesh& m, int level, int prec, const void* x, void* y, cudaStream_t st) {
+  if (prec == 0) rows_dispatch<double, double, APPLY>(m, level, (const double*)x, (double*)y, nullptr, nullptr, 0.0, st);
+  else rows_dispatch<float, float, APPLY>(m, level, (const float*)x, (float*)y, nullptr, nullptr, 0.0, st);
+}
+
+void residual_op(const Mesh& m, int level, int prec, const void* x, const void* b, void* r,
+                 double* norm2_dev, cudaStream_t st) {
+  int used;
+  if (prec == 0)
+    used = rows_dispatch<double, double, RESID>(m, level, (const double*)x, (double*)r, (const double*)b, m.partials, 0.0, st);
+  else
+    used = rows_dispatch<float, float, RESID>(m, level, (const float*)x, (float*)r, (const float*)b, m.partials, 0.0, st);
+  if (norm2_dev) {
+    HHG_LAUNCH(HHG_K_OTHER, level, st, "sum partials", k_sum_partials<<<1, kThreads, 0, st>>>(m.partials, used, norm2_dev, 0));
+  }
+}
+
+void residual_f64_to_f32(const Mesh& m, int level, const double* x, const double* b, float* r32,
+                         double* norm2_dev, cudaStream_t st) {
+  const int used = rows_dispatch<double, float, RESID>(m, level, x, r32, b, m.partials, 0.0, st);
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "sum partials", k_sum_partials<<<1, kThreads, 0, st>>>(m.partials, used, norm2_dev, 0));
+}
+
+void update_f64_from_f32(const Mesh& m, int level, double* x, const float* d32, cudaStream_t st) {
+  const int64_t n = m.levels[level].lv.len;
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "update", k_update_f64<<<blocks_for(n, kThreads, 152 * 16), kThreads, 0, st>>>(n, x, d32));
+}
+
+template <typename T, bool VARK>
+static void gs_sweep_t(const Mesh& m, int level, T* x, const T* b, bool forward, cudaStream_t st) {
+  const LevelData& ld = m.levels[level];
+  const LevelView& L = ld.lv;
+  const T* k = kptr<T>(m, level);
+  auto vertex_phase = [&]() {
+    HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "gs vertex", k_vertex<T, T, VARK, GS><<<blocks_for(m.nv, kThreads, kMaxBlocksV), kThreads, 0, st>>>(
+        m.tab, L, x, x, b, k, nullptr, 0.0));
+  };
+  auto edge_phase = [&](int c) {
+    const int64_t n = ld.colour_ptr[c + 1] - ld.colour_ptr[c];
+    if (n == 0) return;
+    HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "gs edge", k_edge<T, T, VARK, GS><<<blocks_for(n, kThreads, kMaxBlocksE), kThreads, 0, st>>>(
+        m.tab, L, ld.colour_list + ld.colour_ptr[c], n, x, x, b, k, nullptr, 0.0));
+  };
+  auto face_phase = [&](int c) {
+    if (L.N < 3) return;
+    const int64_t ntask = (int64_t)m.nf * (L.N - 2);
+    HHG_LAUNCH(HHG_K_FACE_GS, level, st, "gs face", k_face<T, T, VARK, GS><<<blocks_for(ntask, kWarps, kMaxBlocksF), kThreads, 0, st>>>(
+        m.tab, L, x, x, b, k, c, nullptr, 0.0));
+  };
+  if (forward) {
+    vertex_phase();
+    for (int c = 0; c < ld.n_colours; ++c) edge_phase(c);
+    for (int c = 0; c < 3; ++c) face_phase(c);
+  } else {
+    for (int c = 2; c >= 0; --c) face_phase(c);
+    for (int c = ld.n_colours - 1; c >= 0; --c) edge_phase(c);
+    vertex_phase();
+  }
+}
+
+void gs_sweep(const Mesh& m, int level, int prec, void* x, const void* b, bool forward,
+              cudaStream_t st) {
+  if (prec == 0) {
+    if (m.vark) gs_sweep_t<double, true>(m, level, (double*)x, (const double*)b, forward, st);
+    else gs_sweep_t<double, false>(m, level, (double*)x, (const double*)b, forward, st);
+  } else {
+    if (m.vark) gs_sweep_t<float, true>(m, level, (float*)x, (const float*)b, forward, st);
+    else gs_sweep_t<float, false>(m, level, (float*)x, (const float*)b, forward, st);
+  }
+}
+
+void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,
+                  void* work, cudaStream_t st) {
+  const int64_t n = m.levels[level].lv.len;
+  if (prec == 0) {
+    rows_dispatch<double, double, JAC>(m, level, (const double*)x, (double*)work, (const double*)b, nullptr, omega, st);
+    check_cuda(cudaMemcpyAsync(x, work, n * sizeof(double), cudaMemcpyDeviceToDevice, st), "jacobi copy");
+  } else {
+    rows_dispatch<float, float, JAC>(m, level, (const float*)x, (float*)work, (const float*)b, nullptr, omega, st);
+    check_cuda(cudaMemcpyAsync(x, work, n * sizeof(float), cudaMemcpyDeviceToDevice, st), "jacobi copy");
+  }
+  ghost_fill(m, level, prec, x, st);
+}
+
+template <typename T>
+static void restrict_t(const Mesh& m, int lf, const T* rf, T* bc, cudaStream_t st) {
+  const LevelView& Lf = m.levels[lf].lv;
+  const LevelView& Lc = m.levels[lf - 1].lv;
+  const int64_t nve = m.nv + (Lc.N >= 2 ? (int64_t)m.ne * (Lc.N - 1) : 0);
+  HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "restrict ve", k_restrict_ve<T><<<blocks_for(nve, kThreads, 1024), kThreads, 0, st>>>(m.tab, Lf, Lc, rf, bc));
+  if (Lc.N >= 3) {
+    const int64_t ntask = (int64_t)m.nf * (Lc.N - 2);
+    HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "restrict face", k_restrict_face<T><<<blocks_for(ntask, kWarps, kMaxBlocksF), kThreads, 0, st>>>(m.tab, Lf, Lc, rf, bc));
+  }
+}
+
+void restrict_op(const Mesh& m, int fine_level, int prec, const void* r_fine, void* b_coarse,
+                 cudaStream_t st) {
+  if (prec == 0) restrict_t(m, fine_level, (const double*)r_fine, (double*)b_coarse, st);
+  else restrict_t(m, fine_level, (const float*)r_fine, (float*)b_coarse, st);
+}
+
+template <typename T>
+static void prolong_t(const Mesh& m, int lf, const T* xc, T* xf, cudaStream_t st) {
+  const LevelView& Lf = m.levels[lf].lv;
+  const LevelView& Lc = m.levels[lf - 1].lv;
+  const int64_t nve = m.nv + (int64_t)m.ne * (Lf.N + 1);
+  HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "prolong ve", k_prolong_ve<T><<<blocks_for(nve, kThreads, 1024), kThreads, 0, st>>>(m.tab, Lf, Lc, xc, xf));
+  const int64_t ntask = (int64_t)m.nf * (Lf.N + 1);
+  HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "prolong face", k_prolong_face<T><<<blocks_for(ntask, kWarps, kMaxBlocksF), kThreads, 0, st>>>(m.tab, Lf, Lc, xc, xf));
+}
+
+void prolongate_add(const Mesh& m, int fine_level, int prec, const void* x_coarse, void* x_fine,
+                    cudaStream_t st) {
+  if (prec == 0) prolong_t(m, fine_level, (const double*)x_coarse, (double*)x_fine, st);
+  else prolong_t(m, fine_level, (const float*)x_coarse, (float*)x_fine, st);
+}
+
+void coarse_solve(const Mesh& m, int prec, const void* b0, void* x0, cudaStream_t st) {
+  const int n0 = m.n0;
+  if (n0 > 0) {
+    const size_t smem = 4 * (size_t)n0 * sizeof(double);
+    if (prec == 0)
+      HHG_LAUNCH(HHG_K_OTHER, 0, st, "coarse cg", k_coarse_cg<double><<<1, kThreads, smem, st>>>(n0, m.A0, m.free0, (const double*)b0, (double*)x0, m.levels[0].lv.v_off));
+    else
+      HHG_LAUNCH(HHG_K_OTHER, 0, st, "coarse cg", k_coarse_cg<float><<<1, kThreads, smem, st>>>(n0, m.A0, m.free0, (const float*)b0, (float*)x0, m.levels[0].lv.v_off));
+  }
+  ghost_fill(m, 0, prec, x0, st);
+}
+
+void zero_vec(const Mesh& m, int level, int prec, void* v, cudaStream_t st) {
+  const int64_t n = m.levels[level].lv.len;
+  check_cuda(cudaMemsetAsync(v, 0, n * (prec == 0 ? 8 : 4), st), "memset");
+}
+
+void assign_op(const Mesh& m, int level, int prec, double a, const void* x1, double b,
+               const void* x2, void* dst, cudaStream_t st) {
+  const int64_t n = m.levels[level].lv.len;
+  const int g = blocks_for(n, kThreads, 152 * 16);
+  if (prec == 0)
+    HHG_LAUNCH(HHG_K_OTHER, level, st, "assign", k_assign<double><<<g, kThreads, 0, st>>>(n, a, (const double*)x1, b, (const double*)x2, (double*)dst));
+  else
+    HHG_LAUNCH(HHG_K_OTHER, level, st, "assign", k_assign<float><<<g, kThreads, 0, st>>>(n, (float)a, (const float*)x1, (float)b, (const float*)x2, (float*)dst));
+}
+
+void dot_op(const Mesh& m, int level, int prec, const void* x1, const void* x2, double* out_dev,
+            cudaStream_t st) {
+  const LevelView& L = m.levels[level].lv;
+  const int64_t work = m.nv + (int64_t)m.ne * L.N + (int64_t)m.nf * L.N * 4;
+  const int g = blocks_for(work, kThreads * 8, 2048);
+  if (prec == 0)
+    HHG_LAUNCH(HHG_K_OTHER, level, st, "dot", k_dot<double><<<g, kThreads, 0, st>>>(m.tab, L, (const double*)x1, (const double*)x2, m.partials));
+  else
+    HHG_LAUNCH(HHG_K_OTHER, level, st, "dot", k_dot<float><<<g, kThreads, 0, st>>>(m.tab, L, (const float*)x1, (const float*)x2, m.partials));
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "dot sum", k_sum_partials<<<1, kThreads, 0, st>>>(m.partials, g, out_dev, 0));
+}
+
+void sqrt_scalar(double* v, cudaStream_t st) {
+  HHG_LAUNCH(HHG_K_OTHER, -1, st, "sqrt", k_sqrt<<<1, 1, 0, st>>>(v));
+}
+
+template <typename T>
+static void canonical_t(const Mesh& m, int level, const T* src, T* dst, bool to_canon,
+                        cudaStream_t st) {
+  const LevelView& L = m.levels[level].lv;
+  const int64_t nve = m.nv + (L.N >= 2 ? (int64_t)m.ne * (L.N - 1) : 0);
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "canon ve", k_canon_ve<T><<<blocks_for(nve, kThreads, 4096), kThreads, 0, st>>>(m.tab, L, src, dst, to_canon));
+  if (L.N >= 3) {
+    const int64_t ntask = (int64_t)m.nf * (L.N - 2);
+    HHG_LAUNCH(HHG_K_OTHER, level, st, "canon face", k_canon_face<T><<<blocks_for(ntask, kWarps, kMaxBlocksF), kThreads, 0, st>>>(m.tab, L, src, dst, to_canon, nve));
+  }
+  if (!to_canon) ghost_fill_t(m, level, dst, st);
+}
+
+void canonical_op(const Mesh& m, int level, int prec, const void* src, void* dst, bool to_canon,
+                  cudaStream_t st) {
+  if (prec == 0) canonical_t(m, level, (const double*)src, (double*)dst, to_canon, st);
+  else canonical_t(m, level, (const float*)src, (float*)dst, to_canon, st);
+}
+
+void load_k_fine(const Mesh& m, const double* k_canon, cudaStream_t st) {
+  const int lv = m.max_level;
+  const LevelView& L = m.levels[lv].lv;
+  const int64_t ntask = (int64_t)m.nf * (2 * L.N - 1);
+  HHG_LAUNCH(HHG_K_OTHER, lv, st, "load k", k_load_k<<<blocks_for(ntask, kWarps, kMaxBlocksF), kThreads, 0, st>>>(m.tab, L, k_canon, (double*)m.levels[lv].k[0]));
+}
+
+void coarsen_k(const Mesh& m, int coarse_level, int prec, cudaStream_t st) {
+  const LevelView& Lf = m.levels[coarse_level + 1].lv;
+  const LevelView& Lc = m.levels[coarse_level].lv;
+  const int64_t ntask = (int64_t)m.nf * Lc.N;
+  const int g = blocks_for(ntask, kWarps, kMaxBlocksF);
+  if (prec == 0)
+    HHG_LAUNCH(HHG_K_OTHER, coarse_level, st, "coarsen k", k_coarsen_k<double><<<g, kThreads, 0, st>>>(m.tab, Lf, Lc, (const double*)m.levels[coarse_level + 1].k[0], (double*)m.levels[coarse_level].k[0]));
+  else
+    HHG_LAUNCH(HHG_K_OTHER, coarse_level, st, "coarsen k", k_coarsen_k<float><<<g, kThreads, 0, st>>>(m.tab, Lf, Lc, (const float*)m.levels[coarse_level + 1].k[1], (float*)m.levels[coarse_level].k[1]));
+}
+
+void convert_k_to_f32(const Mesh& m, int level, cudaStream_t st) {
+  const int64_t n = 2 * (int64_t)m.nf * m.levels[level].lv.FS;
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "k to f32", k_f64_to_f32<<<blocks_for(n, kThreads, 152 * 16), kThreads, 0, st>>>(n, (const double*)m.levels[level].k[0], (float*)m.levels[level].k[1]));
+}
+
+}  // namespace hhg

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of libhhg (include/hhg.h).
+
+Argument marshalling only: every step of the multigrid path runs in the
+library's CUDA kernels.  Vectors are passed as device pointers -- torch CUDA
+tensors (their ``data_ptr()``) or plain integers -- and streams as raw
+``cudaStream_t`` handles (``torch.cuda.current_stream().cuda_stream``).
+There is no CPU fallback: if ``libhhg.so`` has not been built, importing this
+module raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhhg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} not built: run `python -m paper_1805_10167_gb300.build` "
+                      "(or __graft_entry__.build())")
+lib = C.CDLL(LIB_PATH)
+
+OK, ERR_ARG, ERR_MESH, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_NAN, ERR_TIMEOUT, ERR_BREAKDOWN = range(9)
+F64, F32 = 0, 1
+GS_FWD, GS_BWD, JACOBI = 0, 1, 2
+SOLVE_MG, SOLVE_IR = 0, 1
+
+
+class Info(C.Structure):
+    _fields_ = [("N", C.c_int32), ("n_edge_colours", C.c_int32), ("n_nodes", C.c_int64),
+                ("n_free", C.c_int64), ("vec_len", C.c_int64), ("n_elems", C.c_int64),
+                ("row_stride", C.c_int64), ("v_off", C.c_int64), ("e_off", C.c_int64),
+                ("f_off", C.c_int64), ("edge_stride", C.c_int64), ("face_stride", C.c_int64),
+                ("n_vertices", C.c_int32), ("n_edges", C.c_int32), ("n_faces", C.c_int32),
+                ("max_level", C.c_int32)]
+
+
+class VcycleOpts(C.Structure):
+    _fields_ = [("nu1", C.c_int32), ("nu2", C.c_int32)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
+                ("max_iter", C.c_int32), ("tol", C.c_double)]
+
+
+class SolveReport(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("r0", C.c_double),
+                ("r_final", C.c_double), ("history", C.POINTER(C.c_double)),
+                ("history_cap", C.c_int32)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "hhg_mesh_create": [C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int32), C.c_int64,
+                        C.POINTER(C.c_uint8), C.c_int32, C.POINTER(_P)],
+    "hhg_mesh_destroy": [_P],
+    "hhg_mesh_info": [_P, C.c_int32, C.POINTER(Info)],
+    "hhg_set_coefficient": [_P, _P, _P],
+    "hhg_from_canonical": [_P, C.c_int32, C.c_int32, _P, _P, _P],
+    "hhg_to_canonical": [_P, C.c_int32, C.c_int32, _P, _P, _P],
+    "hhg_apply": [_P, C.c_int32, C.c_int32, _P, _P, _P],
+    "hhg_residual": [_P, C.c_int32, C.c_int32, _P, _P, _P, _P, _P],
+    "hhg_assign": [_P, C.c_int32, C.c_int32, C.c_double, _P, C.c_double, _P, _P, _P],
+    "hhg_dot": [_P, C.c_int32, C.c_int32, _P, _P, _P, _P],
+    "hhg_restrict": [_P, C.c_int32, C.c_int32, _P, _P, _P],
+    "hhg_prolongate_add": [_P, C.c_int32, C.c_int32, _P, _P, _P],
+    "hhg_smooth": [_P, C.c_int32, C.c_int32, _P, _P, C.c_int32, C.c_int32, C.c_double, _P],
+    "hhg_vcycle": [_P, C.c_int32, C.c_int32, _P, _P, C.POINTER(VcycleOpts), _P],
+    "hhg_solve": [_P, C.c_int32, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveReport), _P],
+    "hhg_profile_begin": [C.c_uint32, C.c_int32],
+    "hhg_profile_end": [C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+lib.hhg_last_error.argtypes = [C.c_char_p, C.c_size_t]
+lib.hhg_last_error.restype = C.c_size_t
+
+EXPORTED = sorted(list(_SIGS) + ["hhg_last_error"])
+
+
+K_FACE_GS, K_FACE_ROWS, K_EDGE_VERTEX, K_TRANSFER, K_GHOST, K_OTHER, K_COUNT = range(7)
+K_NAMES = ["face_gs", "face_rows", "edge_vertex", "transfer", "ghost", "other"]
+
+
+class HHGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"hhg status {status}: {msg}")
+        self.status = status
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(1024)
+    lib.hhg_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(status):
+    if status != OK:
+        raise HHGError(status, last_error())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def profile_begin(mask, level):
+    """Start counting launches (all classes) and timing classes in `mask` on `level`."""
+    _check(lib.hhg_profile_begin(int(mask), int(level)))
+
+
+def profile_end():
+    """Returns (launches per class, milliseconds per class) since profile_begin."""
+    n = (C.c_int64 * K_COUNT)()
+    ms = (C.c_double * K_COUNT)()
+    _check(lib.hhg_profile_end(n, ms))
+    return list(n), list(ms)
+
+
+class Mesh:
+    """A macro mesh with its level hierarchy and device workspaces."""
+
+    def __init__(self, xy, tri, max_level, dirichlet_vertex=None):
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        dv = None
+        if dirichlet_vertex is not None:
+            dv = np.ascontiguousarray(dirichlet_vertex, dtype=np.uint8)
+        h = _P()
+        st = lib.hhg_mesh_create(
+            xy.ctypes.data_as(C.POINTER(C.c_double)), xy.shape[0],
+            tri.ctypes.data_as(C.POINTER(C.c_int32)), tri.shape[0],
+            dv.ctypes.data_as(C.POINTER(C.c_uint8)) if dv is not None else None,
+            int(max_level), C.byref(h))
+        _check(st)
+        self.h = h
+        self.max_level = int(max_level)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.hhg_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, level) -> Info:
+        out = Info()
+        _check(lib.hhg_mesh_info(self.h, int(level), C.byref(out)))
+        return out
+
+    def set_coefficient(self, k_dev, stream=None):
+        _check(lib.hhg_set_coefficient(self.h, _ptr(k_dev), _stream(stream)))
+
+    def from_canonical(self, level, src, dst, prec=F64, stream=None):
+        _check(lib.hhg_from_canonical(self.h, level, prec, _ptr(src), _ptr(dst), _stream(stream)))
+
+    def to_canonical(self, level, src, dst, prec=F64, stream=None):
+        _check(lib.hhg_to_canonical(self.h, level, prec, _ptr(src), _ptr(dst), _stream(stream)))
+
+    def apply(self, level, x, y, prec=F64, stream=None):
+        _check(lib.hhg_apply(self.h, level, prec, _ptr(x), _ptr(y), _stream(stream)))
+
+    def residual(self, level, x, b, r, norm_dev=None, prec=F64, stream=None):
+        _check(lib.hhg_residual(self.h, level, prec, _ptr(x), _ptr(b), _ptr(r), _ptr(norm_dev),
+                                _stream(stream)))
+
+    def assign(self, level, alpha, x1, beta, x2, dst, prec=F64, stream=None):
+        _check(lib.hhg_assign(self.h, level, prec, float(alpha), _ptr(x1), float(beta), _ptr(x2),
+                              _ptr(dst), _stream(stream)))
+
+    def dot(self, level, x1, x2, out_dev, prec=F64, stream=None):
+        _check(lib.hhg_dot(self.h, level, prec, _ptr(x1), _ptr(x2), _ptr(out_dev), _stream(stream)))
+
+    def restrict(self, fine_level, r_fine, b_coarse, prec=F64, stream=None):
+        _check(lib.hhg_restrict(self.h, fine_level, prec, _ptr(r_fine), _ptr(b_coarse), _stream(stream)))
+
+    def prolongate_add(self, fine_level, x_coarse, x_fine, prec=F64, stream=None):
+        _check(lib.hhg_prolongate_add(self.h, fine_level, prec, _ptr(x_coarse), _ptr(x_fine),
+                                      _stream(stream)))
+
+    def smooth(self, level, x, b, smoother=GS_FWD, sweeps=1, omega=2.0 / 3.0, prec=F64, stream=None):
+        _check(lib.hhg_smooth(self.h, level, prec, _ptr(x), _ptr(b), smoother, sweeps, omega,
+                              _stream(stream)))
+
+    def vcycle(self, level, x, b, nu1=3, nu2=3, prec=F64, stream=None):
+        o = VcycleOpts(nu1, nu2)
+        _check(lib.hhg_vcycle(self.h, level, prec, _ptr(x), _ptr(b), C.byref(o), _stream(stream)))
+
+    def solve(self, level, x, b, mode=SOLVE_MG, nu1=3, nu2=3, tol=1e-10, max_iter=100,
+              stream=None, history=True, raise_on_error=True):
+        """Returns (status, report dict)."""
+        o = SolveOpts(mode, nu1, nu2, max_iter, tol)
+        hist = (C.c_double * (max_iter + 1))()
+        rep = SolveReport(0, 0, 0.0, 0.0, hist if history else None, max_iter + 1 if history else 0)
+        st = lib.hhg_solve(self.h, level, _ptr(x), _ptr(b), C.byref(o), C.byref(rep), _stream(stream))
+        out = {"iterations": rep.iterations, "status": rep.status, "r0": rep.r0,
+               "r_final": rep.r_final,
+               "history": [hist[i] for i in range(min(rep.iterations + 1, max_iter + 1))]}
+        if raise_on_error and st != OK:
+            raise HHGError(st, last_error())
+        return st, out

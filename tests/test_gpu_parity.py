@@ -1,0 +1,264 @@
+"""Parity of the CUDA path (called through the C-ABI) with the FP64 oracle on
+the same seeded inputs, element by element in canonical order.  Bound for
+every FP64 result: max-norm relative error <= 1e-12 (gpu_support.FP64_TOL)."""
+import numpy as np
+import pytest
+
+from gpu_support import FP64_TOL, Pair, rel_err
+from oracle import fem
+from oracle import multigrid as mg
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("square", 1), ("square", 3), ("annulus", 2), ("annulus", 4), ("random5", 3),
+         ("random11", 4), ("annulus16", 3)]
+
+
+@pytest.fixture(scope="module")
+def pairs():
+    cache = {}
+
+    def get(name, L, vark=False):
+        key = (name, L, vark)
+        if key not in cache:
+            cache[key] = Pair(name, L, vark=vark)
+        return cache[key]
+    yield get
+    for p in cache.values():
+        p.close()
+
+
+# ------------------------------------------------------------------ layout
+@pytest.mark.parametrize("name,L", CASES)
+def test_canonical_roundtrip_and_ghost_copies(pairs, name, L):
+    P = pairs(name, L)
+    for l in range(L + 1):
+        c = P.random(l)
+        v = P.to_dev(l, c)
+        assert np.array_equal(P.from_dev(l, v), c)
+        # every face boundary slot holds the owner's value
+        I = P.info(l)
+        h = v.cpu().numpy()
+        N, S = I.N, I.row_stride
+        G = P.H.levels[l].face_ids
+        for f in range(I.n_faces):
+            base = I.f_off + f * I.face_stride
+            for (i, j) in ((0, 0), (N, 0), (0, N), (N // 2, 0), (0, N // 2), (N // 2, N - N // 2)):
+                assert h[base + j * S + i] == c[G[f][j, i]]
+
+
+# ------------------------------------------------------------------ operator
+@pytest.mark.parametrize("name,L", CASES)
+@pytest.mark.parametrize("vark", [False, True])
+def test_apply_parity(pairs, name, L, vark):
+    P = pairs(name, L, vark)
+    for l in range(L + 1):
+        x = P.random(l)
+        y = P.new(l)
+        P.g.apply(l, P.to_dev(l, x), y)
+        want = fem.apply_element_loop(P.H.levels[l], x, P.H.k[l])
+        assert rel_err(P.from_dev(l, y), want) <= FP64_TOL
+
+
+@pytest.mark.parametrize("name,L", CASES[:4])
+@pytest.mark.parametrize("vark", [False, True])
+def test_residual_and_norm_parity(pairs, name, L, vark):
+    torch = pytest.importorskip("torch")
+    P = pairs(name, L, vark)
+    x, b = P.random(L), P.random(L)
+    r = P.new(L)
+    nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    P.g.residual(L, P.to_dev(L, x), P.to_dev(L, b), r, nrm)
+    want = P.H.residual(L, x, b)
+    assert rel_err(P.from_dev(L, r), want) <= FP64_TOL
+    assert abs(nrm.item() - mg.norm_free(P.H, L, want)) <= FP64_TOL * mg.norm_free(P.H, L, want)
+
+
+@pytest.mark.parametrize("name,L", CASES[:4])
+def test_dot_and_assign_parity(pairs, name, L):
+    torch = pytest.importorskip("torch")
+    P = pairs(name, L)
+    a, b = P.random(L), P.random(L)
+    da, db = P.to_dev(L, a), P.to_dev(L, b)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    P.g.dot(L, da, db, out)
+    fr = P.H.levels[L].free
+    want = float(a[fr] @ b[fr])
+    assert abs(out.item() - want) <= FP64_TOL * np.sqrt((a[fr] @ a[fr]) * (b[fr] @ b[fr]))
+    dst = P.new(L)
+    P.g.assign(L, 0.75, da, -2.5, db, dst)
+    assert rel_err(P.from_dev(L, dst), 0.75 * a - 2.5 * b) <= FP64_TOL
+
+
+# ------------------------------------------------------------------ smoothers
+@pytest.mark.parametrize("name,L", CASES)
+@pytest.mark.parametrize("vark", [False, True])
+def test_gauss_seidel_parity(pairs, name, L, vark):
+    P = pairs(name, L, vark)
+    hhg = P.hhg
+    for l in range(1, L + 1):
+        x0, b = P.random(l), P.random(l)
+        for fwd in (True, False):
+            x = P.to_dev(l, x0)
+            P.g.smooth(l, x, P.to_dev(l, b), hhg.GS_FWD if fwd else hhg.GS_BWD, sweeps=2)
+            want = x0.copy()
+            for _ in range(2):
+                mg.gs_sweep(P.H, l, want, b, forward=fwd)
+            assert rel_err(P.from_dev(l, x), want) <= FP64_TOL, (l, fwd)
+
+
+@pytest.mark.parametrize("name,L", CASES[:4])
+def test_jacobi_parity(pairs, name, L):
+    P = pairs(name, L)
+    x0, b = P.random(L), P.random(L)
+    x = P.to_dev(L, x0)
+    P.g.smooth(L, x, P.to_dev(L, b), P.hhg.JACOBI, sweeps=3, omega=0.6)
+    want = x0.copy()
+    for _ in range(3):
+        mg.jacobi_sweep(P.H, L, want, b, omega=0.6)
+    assert rel_err(P.from_dev(L, x), want) <= FP64_TOL
+
+
+# ------------------------------------------------------------------ transfers
+@pytest.mark.parametrize("name,L", CASES)
+def test_restriction_parity(pairs, name, L):
+    P = pairs(name, L)
+    for l in range(1, L + 1):
+        r = P.random(l, zero_dirichlet=True)
+        bc = P.new(l - 1)
+        P.g.restrict(l, P.to_dev(l, r), bc)
+        want = mg.restrict(P.H, l, r)
+        want[~P.H.levels[l - 1].free] = 0.0
+        assert rel_err(P.from_dev(l - 1, bc), want) <= FP64_TOL
+
+
+@pytest.mark.parametrize("name,L", CASES)
+def test_prolongation_parity(pairs, name, L):
+    P = pairs(name, L)
+    for l in range(1, L + 1):
+        xc = P.random(l - 1, zero_dirichlet=True)
+        xf = P.random(l)
+        d = P.to_dev(l, xf)
+        P.g.prolongate_add(l, P.to_dev(l - 1, xc), d)
+        want = mg.prolongate_add(P.H, l, xf.copy(), xc)
+        assert rel_err(P.from_dev(l, d), want) <= FP64_TOL
+
+
+# ------------------------------------------------------------------ cycle and solver
+@pytest.mark.parametrize("name", ["square", "annulus", "random5", "annulus16"])
+def test_coarse_solve_parity(pairs, name):
+    P = pairs(name, 1)
+    b = P.random(0)
+    x = P.new(0)
+    P.g.vcycle(0, x, P.to_dev(0, b))
+    want = mg.cg(P.H.A[0], P.H.levels[0].free, b)
+    got = P.from_dev(0, x)
+    fr = P.H.levels[0].free
+    if fr.any():
+        assert rel_err(got[fr], want[fr]) <= FP64_TOL
+
+
+@pytest.mark.parametrize("name,L", CASES)
+@pytest.mark.parametrize("vark", [False, True])
+def test_vcycle_parity(pairs, name, L, vark):
+    P = pairs(name, L, vark)
+    for nu in ((2, 2), (3, 3), (1, 0)):
+        x0, b = P.random(L), P.random(L)
+        x = P.to_dev(L, x0)
+        P.g.vcycle(L, x, P.to_dev(L, b), nu1=nu[0], nu2=nu[1])
+        want = mg.vcycle(P.H, L, x0.copy(), b, nu[0], nu[1])
+        assert rel_err(P.from_dev(L, x), want) <= FP64_TOL, nu
+
+
+def test_solve_parity_unit_square_manufactured():
+    """Unit square, 8 faces, level 5, b = M f_I for u = sin(pi x) sin(pi y),
+    V(2,2) to 1e-10: same cycle count, same residual history, same iterate."""
+    torch = pytest.importorskip("torch")
+    P = Pair("square", 5)
+    lv = P.H.levels[5]
+    f = lambda x, y: 2 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y)
+    b = fem.load_vector(lv, f)
+    x = P.to_dev(5, np.zeros(lv.n))
+    st, rep = P.g.solve(5, x, P.to_dev(5, b), nu1=2, nu2=2, tol=1e-10)
+    want, hist = mg.solve(P.H, np.zeros(lv.n), b, 2, 2, tol=1e-10)
+    assert rep["iterations"] == len(hist) - 1
+    np.testing.assert_allclose(rep["history"], hist, rtol=1e-9)
+    assert rel_err(P.from_dev(5, x), want) <= FP64_TOL
+    u = lambda X, Y: np.sin(np.pi * X) * np.sin(np.pi * Y)
+    assert fem.l2_error(lv, P.from_dev(5, x), u) < 6e-4
+    P.close()
+
+
+@pytest.mark.parametrize("vark", [False, True])
+def test_solve_parity_annulus(vark):
+    P = Pair("annulus", 5, vark=vark)
+    lv = P.H.levels[5]
+    from paper_1805_10167_gb300 import inputs
+    b = inputs.uniform_pm1(lv.n, 1234)
+    x = P.to_dev(5, np.zeros(lv.n))
+    st, rep = P.g.solve(5, x, P.to_dev(5, b), nu1=3, nu2=3, tol=1e-10)
+    want, hist = mg.solve(P.H, np.zeros(lv.n), b.copy(), 3, 3, tol=1e-10)
+    assert rep["iterations"] == len(hist) - 1
+    assert rel_err(P.from_dev(5, x), want) <= 1e-11
+    P.close()
+
+
+@pytest.mark.parametrize("vark", [False, True])
+def test_mixed_precision_refinement_reaches_fp64_tolerance(vark):
+    """FP32 V-cycles inside FP64 iterative refinement reach the same 1e-10
+    relative FP64 residual; the final iterate matches the oracle's FP64 solve
+    to the accuracy the stopping test allows."""
+    P = Pair("annulus", 5, vark=vark)
+    lv = P.H.levels[5]
+    from paper_1805_10167_gb300 import inputs
+    b = inputs.uniform_pm1(lv.n, 1234)
+    x = P.to_dev(5, np.zeros(lv.n))
+    st, rep = P.g.solve(5, x, P.to_dev(5, b), mode=P.hhg.SOLVE_IR, nu1=3, nu2=3, tol=1e-10)
+    assert rep["r_final"] <= 1e-10 * rep["r0"]
+    got = P.from_dev(5, x)
+    r = P.H.residual(5, got, b)
+    assert mg.norm_free(P.H, 5, r) <= 1.01e-10 * rep["r0"]
+    want, hist = mg.solve(P.H, np.zeros(lv.n), b.copy(), 3, 3, tol=1e-12)
+    assert rel_err(got, want) < 1e-8
+    assert rep["iterations"] <= len(hist) + 3
+    P.close()
+
+
+def test_fp32_vcycle_error_against_fp64_oracle():
+    """The FP32 path is not bitwise comparable; its error against the FP64
+    oracle is measured and bounded (FP32 unit roundoff 6e-8 times a modest
+    growth factor)."""
+    P = Pair("annulus", 5)
+    x0, b = P.random(5), P.random(5)
+    x = P.to_dev(5, x0, prec=1)
+    P.g.vcycle(5, x, P.to_dev(5, b, prec=1), prec=1)
+    want = mg.vcycle(P.H, 5, x0.copy(), b, 3, 3)
+    e = rel_err(P.from_dev(5, x, prec=1), want)
+    print(f"FP32 V(3,3) relative error vs FP64 oracle: {e:.3e}")
+    assert e < 1e-5
+    y = P.new(5, 1)
+    P.g.apply(5, P.to_dev(5, x0, prec=1), y, prec=1)
+    e2 = rel_err(P.from_dev(5, y, prec=1), fem.apply_element_loop(P.H.levels[5], x0))
+    print(f"FP32 apply relative error vs FP64 oracle: {e2:.3e}")
+    assert e2 < 1e-6
+    P.close()
+
+
+# ------------------------------------------------------------------ error paths
+def test_solver_reports_non_convergence_and_nan():
+    torch = pytest.importorskip("torch")
+    P = Pair("annulus", 3)
+    hhg = P.hhg
+    lv = P.H.levels[3]
+    b = P.random(3)
+    x = P.to_dev(3, np.zeros(lv.n))
+    st, rep = P.g.solve(3, x, P.to_dev(3, b), max_iter=2, raise_on_error=False)
+    assert st == hhg.ERR_NOT_CONVERGED and rep["iterations"] == 2
+    b[lv.free.nonzero()[0][7]] = np.nan
+    x = P.to_dev(3, np.zeros(lv.n))
+    st, rep = P.g.solve(3, x, P.to_dev(3, b), raise_on_error=False)
+    assert st == hhg.ERR_NAN
+    with pytest.raises(hhg.HHGError) as e:
+        P.g.apply(9, x, x)
+    assert e.value.status == hhg.ERR_ARG
+    P.close()
