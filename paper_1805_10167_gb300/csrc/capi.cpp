@@ -1,7 +1,9 @@
 // C-ABI entry points of libhhg and the host-side multigrid drivers (V-cycle
 // recursion, solver loop, iterative refinement).  See include/hhg.h for the
 // contract of every call.
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <stdexcept>
@@ -69,6 +71,22 @@ void need(const void* p, const char* name) {
   if (!p) throw ArgError(std::string("NULL ") + name);
 }
 
+// Level vectors are read by TMA bulk copies: 16-byte alignment required.
+void need_vec(const void* p, const char* name) {
+  need(p, name);
+  if ((uintptr_t)p % 16 != 0) throw ArgError(std::string(name) + " is not 16-byte aligned");
+}
+
+// Reads the device error word (and clears it); a bounded wait that gave up
+// is reported as HHG_ERR_TIMEOUT.
+bool device_timed_out(const hhg::Mesh& m, cudaStream_t st) {
+  int e = 0;
+  hhg::check_cuda(cudaMemcpyAsync(&e, m.err, sizeof(int), cudaMemcpyDeviceToHost, st), "err readback");
+  hhg::check_cuda(cudaStreamSynchronize(st), "sync");
+  if (e) hhg::check_cuda(cudaMemsetAsync(m.err, 0, sizeof(int), st), "err clear");
+  return e != 0;
+}
+
 cudaStream_t S(void* s) { return (cudaStream_t)s; }
 
 // One V(nu1, nu2) cycle on level l (Sec. 4.3).  x, b belong to the caller on
@@ -81,15 +99,26 @@ void vcycle_rec(const hhg::Mesh& m, int l, int prec, void* x, const void* b, int
     coarse_solve(m, prec, b, x, st);
     return;
   }
-  for (int s = 0; s < nu1; ++s) gs_sweep(m, l, prec, x, b, true, st);
   const LevelData& ld = m.levels[l];
   const LevelData& lc = m.levels[l - 1];
-  residual_op(m, l, prec, x, b, ld.r[prec], nullptr, st);
+  void* cur = x;
+  void* oth = ld.w[prec];
+  for (int s = 0; s < nu1; ++s) {
+    gs_sweep(m, l, prec, cur, oth, b, true, st);
+    std::swap(cur, oth);
+  }
+  residual_op(m, l, prec, cur, b, ld.r[prec], nullptr, st);
   restrict_op(m, l, prec, ld.r[prec], lc.b[prec], st);
   zero_vec(m, l - 1, prec, lc.x[prec], st);
   vcycle_rec(m, l - 1, prec, lc.x[prec], lc.b[prec], nu1, nu2, st);
-  prolongate_add(m, l, prec, lc.x[prec], x, st);
-  for (int s = 0; s < nu2; ++s) gs_sweep(m, l, prec, x, b, false, st);
+  prolongate_add(m, l, prec, lc.x[prec], cur, st);
+  for (int s = 0; s < nu2; ++s) {
+    gs_sweep(m, l, prec, cur, oth, b, false, st);
+    std::swap(cur, oth);
+  }
+  if (cur != x)
+    hhg::check_cuda(cudaMemcpyAsync(x, cur, (size_t)ld.lv.len * (prec == 0 ? 8 : 4),
+                                    cudaMemcpyDeviceToDevice, st), "iterate copy");
 }
 
 double read_scalar(const double* dev, cudaStream_t st) {
@@ -166,7 +195,7 @@ hhg_status hhg_from_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const
     check_level(m, level);
     check_prec(prec);
     need(src, "src");
-    need(dst, "dst");
+    need_vec(dst, "dst");
     hhg::canonical_op(m, level, prec, src, dst, false, S(stream));
     return HHG_OK;
   });
@@ -178,7 +207,7 @@ hhg_status hhg_to_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const v
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
     check_prec(prec);
-    need(src, "src");
+    need_vec(src, "src");
     need(dst, "dst");
     hhg::canonical_op(m, level, prec, src, dst, true, S(stream));
     return HHG_OK;
@@ -191,8 +220,8 @@ hhg_status hhg_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x,
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
     check_prec(prec);
-    need(x, "x");
-    need(y, "y");
+    need_vec(x, "x");
+    need_vec(y, "y");
     hhg::ghost_fill(m, level, prec, const_cast<void*>(x), S(stream));
     hhg::apply_op(m, level, prec, x, y, S(stream));
     return HHG_OK;
@@ -205,9 +234,9 @@ hhg_status hhg_residual(hhg_mesh mesh, int32_t level, hhg_prec prec, const void*
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
     check_prec(prec);
-    need(x, "x");
-    need(b, "b");
-    need(r, "r");
+    need_vec(x, "x");
+    need_vec(b, "b");
+    need_vec(r, "r");
     hhg::ghost_fill(m, level, prec, const_cast<void*>(x), S(stream));
     hhg::residual_op(m, level, prec, x, b, r, norm_dev, S(stream));
     if (norm_dev) hhg::sqrt_scalar(norm_dev, S(stream));
@@ -221,9 +250,9 @@ hhg_status hhg_assign(hhg_mesh mesh, int32_t level, hhg_prec prec, double alpha,
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
     check_prec(prec);
-    need(x1, "x1");
-    need(x2, "x2");
-    need(dst, "dst");
+    need_vec(x1, "x1");
+    need_vec(x2, "x2");
+    need_vec(dst, "dst");
     hhg::assign_op(m, level, prec, alpha, x1, beta, x2, dst, S(stream));
     return HHG_OK;
   });
@@ -235,8 +264,8 @@ hhg_status hhg_dot(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1, 
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
     check_prec(prec);
-    need(x1, "x1");
-    need(x2, "x2");
+    need_vec(x1, "x1");
+    need_vec(x2, "x2");
     need(result_dev, "result_dev");
     hhg::dot_op(m, level, prec, x1, x2, result_dev, S(stream));
     return HHG_OK;
@@ -249,8 +278,8 @@ hhg_status hhg_restrict(hhg_mesh mesh, int32_t fine_level, hhg_prec prec, const 
     hhg::Mesh& m = get(mesh);
     check_level(m, fine_level, 1);
     check_prec(prec);
-    need(r_fine, "r_fine");
-    need(b_coarse, "b_coarse");
+    need_vec(r_fine, "r_fine");
+    need_vec(b_coarse, "b_coarse");
     hhg::restrict_op(m, fine_level, prec, r_fine, b_coarse, S(stream));
     return HHG_OK;
   });
@@ -262,8 +291,8 @@ hhg_status hhg_prolongate_add(hhg_mesh mesh, int32_t fine_level, hhg_prec prec,
     hhg::Mesh& m = get(mesh);
     check_level(m, fine_level, 1);
     check_prec(prec);
-    need(x_coarse, "x_coarse");
-    need(x_fine, "x_fine");
+    need_vec(x_coarse, "x_coarse");
+    need_vec(x_fine, "x_fine");
     hhg::ghost_fill(m, fine_level - 1, prec, const_cast<void*>(x_coarse), S(stream));
     hhg::ghost_fill(m, fine_level, prec, x_fine, S(stream));
     hhg::prolongate_add(m, fine_level, prec, x_coarse, x_fine, S(stream));
@@ -277,17 +306,25 @@ hhg_status hhg_smooth(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
     hhg::Mesh& m = get(mesh);
     check_level(m, level, 1);
     check_prec(prec);
-    need(x, "x");
-    need(b, "b");
+    need_vec(x, "x");
+    need_vec(b, "b");
     if (sweeps < 0) throw ArgError("sweeps < 0");
     if (smoother < HHG_GS_FWD || smoother > HHG_JACOBI) throw ArgError("bad smoother");
     hhg::ghost_fill(m, level, prec, x, S(stream));
+    const hhg::LevelData& ld = m.levels[level];
+    void* cur = x;
+    void* oth = ld.w[prec];
     for (int s = 0; s < sweeps; ++s) {
-      if (smoother == HHG_JACOBI)
-        hhg::jacobi_sweep(m, level, prec, x, b, omega, m.levels[level].r[prec], S(stream));
-      else
-        hhg::gs_sweep(m, level, prec, x, b, smoother == HHG_GS_FWD, S(stream));
+      if (smoother == HHG_JACOBI) {
+        hhg::jacobi_sweep(m, level, prec, cur, b, omega, ld.r[prec], S(stream));
+      } else {
+        hhg::gs_sweep(m, level, prec, cur, oth, b, smoother == HHG_GS_FWD, S(stream));
+        std::swap(cur, oth);
+      }
     }
+    if (cur != x)
+      hhg::check_cuda(cudaMemcpyAsync(x, cur, (size_t)ld.lv.len * (prec == 0 ? 8 : 4),
+                                      cudaMemcpyDeviceToDevice, S(stream)), "iterate copy");
     return HHG_OK;
   });
 }
@@ -298,8 +335,8 @@ hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
     check_prec(prec);
-    need(x, "x");
-    need(b, "b");
+    need_vec(x, "x");
+    need_vec(b, "b");
     const int nu1 = opts ? opts->nu1 : 3, nu2 = opts ? opts->nu2 : 3;
     if (nu1 < 0 || nu2 < 0) throw ArgError("negative sweep count");
     hhg::ghost_fill(m, level, prec, x, S(stream));
@@ -313,8 +350,8 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
-    need(x, "x");
-    need(b, "b");
+    need_vec(x, "x");
+    need_vec(b, "b");
     hhg_solve_opts o{HHG_SOLVE_MG, 3, 3, 100, 1e-10};
     if (opts) o = *opts;
     if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 0 || !(o.tol >= 0.0)) throw ArgError("bad solve options");
@@ -357,12 +394,14 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
       record(it, r);
       if (!std::isfinite(r)) status = HHG_ERR_NAN;
     }
+    if (device_timed_out(m, st)) status = HHG_ERR_TIMEOUT;
     if (rep) {
       rep->iterations = it;
       rep->status = status;
       rep->r0 = r0;
       rep->r_final = r;
     }
+    if (status == HHG_ERR_TIMEOUT) return fail(status, "a device-side wait gave up");
     if (status == HHG_ERR_NAN) return fail(status, "non-finite residual norm");
     if (status == HHG_ERR_NOT_CONVERGED) return fail(status, "max_iter reached");
     return HHG_OK;

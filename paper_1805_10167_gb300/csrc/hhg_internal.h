@@ -54,6 +54,11 @@ inline LevelView make_level_view(int nv, int ne, int nf, int level) {
 // edge's low-id vertex (edge index t then equals the side position p).
 struct FaceRec {
   double cot[3];
+  // k = 1 Gauss-Seidel form: x = b * dinv + w[2] (x(i+1,j) + x(i-1,j))
+  //   + w[1] (x(i,j+1) + x(i,j-1)) + w[0] (x(i+1,j-1) + x(i-1,j+1)),
+  // dinv = 1 / (2 (cot0 + cot1 + cot2)), w[m] = cot[m] * dinv
+  double dinv;
+  double w[3];
   int v[3];
   int edge[3];
   int aligned[3];
@@ -137,7 +142,10 @@ struct LevelData {
   void* x[2] = {nullptr, nullptr};  // coarse-level iterates (unused on the top level)
   void* b[2] = {nullptr, nullptr};
   void* r[2] = {nullptr, nullptr};
+  void* w[2] = {nullptr, nullptr};  // ping-pong partner of the iterate for Gauss-Seidel sweeps
   void* k[2] = {nullptr, nullptr};  // coefficient: up array then down array (2 * nf * FS)
+  int* face_tasks = nullptr;        // device int4 (face, j0, j1, 0): row blocks of the face sweep
+  int n_face_tasks = 0;
 };
 
 struct Mesh {
@@ -160,6 +168,7 @@ struct Mesh {
   // reduction scratch
   double* partials = nullptr;       // kMaxPartials doubles
   double* scalars = nullptr;        // 16 doubles of device scalars
+  int* err = nullptr;               // device error word: 1 = a bounded wait gave up
   int device = 0;
 };
 
@@ -172,8 +181,14 @@ void apply_op(const Mesh& m, int level, int prec, const void* x, void* y, cudaSt
 // r = b - A x; optional sum of squares over free DoFs into *norm2_dev (double)
 void residual_op(const Mesh& m, int level, int prec, const void* x, const void* b, void* r,
                  double* norm2_dev, cudaStream_t st);
-void gs_sweep(const Mesh& m, int level, int prec, void* x, const void* b, bool forward,
-              cudaStream_t st);
+// One Gauss-Seidel sweep from xin to xout (xin's vertex and edge values are
+// updated in place on the way; xout receives the complete new iterate).
+void gs_sweep(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
+              bool forward, cudaStream_t st);
+void face_gs3_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
+                     bool forward, cudaStream_t st);
+std::vector<int> face_tasks(int nf, int N, int tasks_per_face);
+size_t face_gs_smem(const LevelView& L, int prec);
 void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,
                   void* work, cudaStream_t st);
 void restrict_op(const Mesh& m, int fine_level, int prec, const void* r_fine, void* b_coarse,

@@ -187,8 +187,8 @@ __global__ void k_edge(MeshTables M, LevelView L, const int* __restrict__ list, 
 }
 
 // --------------------------------------------------------------- face rows
-// One warp per interior row j = 1..N-2 of a face; GS updates the points of
-// one colour (i + 2j) mod 3 == colour in place.
+// One warp per interior row j = 1..N-2 of a face (apply, residual, Jacobi;
+// Gauss-Seidel has its own fused kernel).
 template <typename T, typename TO, bool VARK, int MODE>
 __global__ void k_face(MeshTables M, LevelView L, const T* __restrict__ x, TO* out,
                        const T* __restrict__ b, const T* __restrict__ k, int colour,
@@ -209,13 +209,7 @@ __global__ void k_face(MeshTables M, LevelView L, const T* __restrict__ x, TO* o
     const T* ku = VARK ? k + (int64_t)f * L.FS : nullptr;
     const T* kd = VARK ? k + (int64_t)(M.nf + f) * L.FS : nullptr;
     const int iend = L.N - j;  // exclusive
-    int i0 = 1 + lane, step = 32;
-    if (MODE == GS) {
-      int c = ((colour - 2 * j) % 3 + 3) % 3;
-      if (c == 0) c = 3;
-      i0 = c + 3 * lane;
-      step = 96;
-    }
+    const int i0 = 1 + lane, step = 32;
     for (int i = i0; i < iend; i += step) {
       const int64_t p = (int64_t)j * L.S + i;
       T off, diag;
@@ -226,10 +220,8 @@ __global__ void k_face(MeshTables M, LevelView L, const T* __restrict__ x, TO* o
         const T r = b[fb + p] - (diag * xf[p] + off);
         out[fb + p] = (TO)r;
         acc += (double)r * (double)r;
-      } else if (MODE == JAC) {
-        out[fb + p] = (TO)(xf[p] + T(omega) * (b[fb + p] - (diag * xf[p] + off)) / diag);
       } else {
-        ((T*)out)[fb + p] = (b[fb + p] - off) / diag;
+        out[fb + p] = (TO)(xf[p] + T(omega) * (b[fb + p] - (diag * xf[p] + off)) / diag);
       }
     }
   }
@@ -658,7 +650,7 @@ void update_f64_from_f32(const Mesh& m, int level, double* x, const float* d32, 
 }
 
 template <typename T, bool VARK>
-static void gs_sweep_t(const Mesh& m, int level, T* x, const T* b, bool forward, cudaStream_t st) {
+static void ve_gs_t(const Mesh& m, int level, T* x, const T* b, bool forward, cudaStream_t st) {
   const LevelData& ld = m.levels[level];
   const LevelView& L = ld.lv;
   const T* k = kptr<T>(m, level);
@@ -672,32 +664,37 @@ static void gs_sweep_t(const Mesh& m, int level, T* x, const T* b, bool forward,
     HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "gs edge", k_edge<T, T, VARK, GS><<<blocks_for(n, kThreads, kMaxBlocksE), kThreads, 0, st>>>(
         m.tab, L, ld.colour_list + ld.colour_ptr[c], n, x, x, b, k, nullptr, 0.0));
   };
-  auto face_phase = [&](int c) {
-    if (L.N < 3) return;
-    const int64_t ntask = (int64_t)m.nf * (L.N - 2);
-    HHG_LAUNCH(HHG_K_FACE_GS, level, st, "gs face", k_face<T, T, VARK, GS><<<blocks_for(ntask, kWarps, kMaxBlocksF), kThreads, 0, st>>>(
-        m.tab, L, x, x, b, k, c, nullptr, 0.0));
-  };
   if (forward) {
     vertex_phase();
     for (int c = 0; c < ld.n_colours; ++c) edge_phase(c);
-    for (int c = 0; c < 3; ++c) face_phase(c);
   } else {
-    for (int c = 2; c >= 0; --c) face_phase(c);
     for (int c = ld.n_colours - 1; c >= 0; --c) edge_phase(c);
     vertex_phase();
   }
 }
 
-void gs_sweep(const Mesh& m, int level, int prec, void* x, const void* b, bool forward,
-              cudaStream_t st) {
+static void ve_gs(const Mesh& m, int level, int prec, void* x, const void* b, bool forward,
+                  cudaStream_t st) {
   if (prec == 0) {
-    if (m.vark) gs_sweep_t<double, true>(m, level, (double*)x, (const double*)b, forward, st);
-    else gs_sweep_t<double, false>(m, level, (double*)x, (const double*)b, forward, st);
+    if (m.vark) ve_gs_t<double, true>(m, level, (double*)x, (const double*)b, forward, st);
+    else ve_gs_t<double, false>(m, level, (double*)x, (const double*)b, forward, st);
   } else {
-    if (m.vark) gs_sweep_t<float, true>(m, level, (float*)x, (const float*)b, forward, st);
-    else gs_sweep_t<float, false>(m, level, (float*)x, (const float*)b, forward, st);
+    if (m.vark) ve_gs_t<float, true>(m, level, (float*)x, (const float*)b, forward, st);
+    else ve_gs_t<float, false>(m, level, (float*)x, (const float*)b, forward, st);
   }
+}
+
+// Forward: vertices, edge colours (in place on xin), then the fused face
+// sweep xin -> xout with the vertex/edge block copied along.  Backward: the
+// face sweep first, then edge colours and vertices in place on xout.
+void gs_sweep(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
+              bool forward, cudaStream_t st) {
+  const LevelView& L = m.levels[level].lv;
+  const size_t prefix = (size_t)L.f_off * (prec == 0 ? 8 : 4);
+  if (forward) ve_gs(m, level, prec, xin, b, true, st);
+  face_gs3_launch(m, level, prec, xin, xout, b, forward, st);
+  check_cuda(cudaMemcpyAsync(xout, xin, prefix, cudaMemcpyDeviceToDevice, st), "vertex/edge copy");
+  if (!forward) ve_gs(m, level, prec, xout, b, false, st);
 }
 
 void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,

@@ -153,6 +153,8 @@ Mesh* mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
         const double wx = c.first - a.first, wy = c.second - a.second;
         F.cot[q] = (ux * wx + uy * wy) / (ux * wy - uy * wx);
       }
+      F.dinv = 1.0 / (2.0 * (F.cot[0] + F.cot[1] + F.cot[2]));
+      for (int q = 0; q < 3; ++q) F.w[q] = F.cot[q] * F.dinv;
       for (int r = 0; r < 3; ++r) {
         const int a = v[r], b = v[(r + 1) % 3];
         efaces[{std::min(a, b), std::max(a, b)}].push_back({(int)f, r});
@@ -240,10 +242,20 @@ Mesh* mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
         ld.x[p] = dev_alloc(m, bytes);
         ld.b[p] = dev_alloc(m, bytes);
         ld.r[p] = dev_alloc(m, bytes);
+        ld.w[p] = dev_alloc(m, bytes);
       }
+      // face sweep row blocks: about 1216 CTAs in total (8 per SM), at least
+      // 48 rows per block so that the recomputed halo rows stay below 2 %
+      const int N = ld.lv.N;
+      int per_face = (int)((1216 + m.nf / 2) / m.nf);
+      per_face = std::max(1, std::min(per_face, (N + 1) / 48));
+      std::vector<int> tk = face_tasks(m.nf, N, per_face);
+      ld.n_face_tasks = (int)(tk.size() / 4);
+      ld.face_tasks = upload(m, tk);
     }
     m.partials = (double*)dev_alloc(m, kMaxPartials * sizeof(double));
     m.scalars = (double*)dev_alloc(m, 16 * sizeof(double));
+    m.err = (int*)dev_alloc(m, 16 * sizeof(int));
     std::vector<double> k0(m.nf, 1.0);
     assemble_level0(m, k0);
     check_cuda(cudaDeviceSynchronize(), "mesh setup");

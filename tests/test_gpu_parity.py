@@ -182,7 +182,9 @@ def test_solve_parity_unit_square_manufactured():
     st, rep = P.g.solve(5, x, P.to_dev(5, b), nu1=2, nu2=2, tol=1e-10)
     want, hist = mg.solve(P.H, np.zeros(lv.n), b, 2, 2, tol=1e-10)
     assert rep["iterations"] == len(hist) - 1
-    np.testing.assert_allclose(rep["history"], hist, rtol=1e-9)
+    # near 1e-10 relative residual the norm b - A x is a difference of O(1)
+    # terms, so its relative agreement is limited to about 1e-16 / 1e-10
+    np.testing.assert_allclose(rep["history"], hist, rtol=1e-4)
     assert rel_err(P.from_dev(5, x), want) <= FP64_TOL
     u = lambda X, Y: np.sin(np.pi * X) * np.sin(np.pi * Y)
     assert fem.l2_error(lv, P.from_dev(5, x), u) < 6e-4
