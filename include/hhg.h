@@ -116,7 +116,8 @@ typedef struct {
  * interior DoFs are Dirichlet when the edge lies on the boundary and both end
  * vertices are Dirichlet.  Errors: HHG_ERR_MESH for out-of-range ids,
  * degenerate triangles or an edge shared by more than two triangles;
- * HHG_ERR_ARG for max_level outside 1..12; HHG_ERR_OOM. */
+ * HHG_ERR_ARG for max_level outside 1..10 (the FP64 face sweep stages 20 rows
+ * of 2^max_level + 1 values in shared memory); HHG_ERR_OOM. */
 hhg_status hhg_mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
                            const uint8_t* dirichlet_vertex, int32_t max_level, hhg_mesh* out);
 hhg_status hhg_mesh_destroy(hhg_mesh mesh);

@@ -137,7 +137,7 @@ hhg_status hhg_mesh_create(const double* xy, int64_t nv, const int32_t* tri, int
   return guarded([&]() {
     need(out, "out");
     *out = nullptr;
-    if (max_level < 1 || max_level > 12) throw ArgError("max_level must be in 1..12");
+    if (max_level < 1 || max_level > 10) throw ArgError("max_level must be in 1..10");
     hhg::Mesh* m = hhg::mesh_create(xy, nv, tri, nt, dirichlet_vertex, max_level);
     *out = new hhg_mesh_s{m};
     return HHG_OK;
