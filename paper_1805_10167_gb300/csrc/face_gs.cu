@@ -236,12 +236,19 @@ template <typename T, bool VARK, bool FWD>
 static void launch_t(const MeshTables& tab, const LevelView& L, const T* xin, T* xout, const T* b,
                      const T* k, const int4* tasks, int ntasks, int* err, cudaStream_t st) {
   const size_t smem = face_gs_smem(L, sizeof(T) == 8 ? 0 : 1);
-  static size_t configured = 0;   // per template instance
+  static size_t configured = 48 * 1024;   // per template instance: largest size enabled so far
   if (smem > configured) {
+    int dev = 0, optin = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    check_cuda(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem optin");
+    cudaFuncAttributes fa;
+    check_cuda(cudaFuncGetAttributes(&fa, k_face_gs3<T, VARK, FWD>), "func attributes");
+    if (smem + fa.sharedSizeBytes > (size_t)optin)
+      throw std::runtime_error("face sweep needs more shared memory than the device offers");
     check_cuda(cudaFuncSetAttribute(k_face_gs3<T, VARK, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(smem < 48 * 1024 ? 48 * 1024 : 227 * 1024)),
+                                    (int)smem),
                "face gs smem attribute");
-    configured = 227 * 1024;
+    configured = smem;
   }
   k_face_gs3<T, VARK, FWD><<<ntasks, kRC * 32, smem, st>>>(tab, L, xin, xout, b, k, tasks, err);
 }
