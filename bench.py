@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GDoF/s per V-cycle & time to 1e-10 FP64 residual: mixed/learned vs FP64 (1 GB300)"
 UNIT = "GDoF/s"
-FP64_FLOP_PER_CLK_SM = 4          # 2 DFMA per clock per SM (probe: 598 GFMA/s at 1995 MHz, 152 SMs)
+FP64_OPS_PER_CLK_SM = 2           # FP64 add/mul/fma per clock per SM (probe: 598 G DFMA/s at 1995 MHz)
 N_SM = 152
 
 
@@ -209,26 +209,31 @@ def run_ours(args):
     ms = max_over_ranks(e0.elapsed_time(e1))
     value = world * n_free * args.steps / (ms / 1e3) / 1e9
 
-    # dominant kernel: the face-interior Gauss-Seidel colour phase on level L
-    gs_launches_L = 6 * 3 * args.steps            # V(3,3): 6 sweeps x 3 colours per cycle
+    # dominant kernel: the fused three-colour face Gauss-Seidel sweep on level L
+    # (6 launches per V(3,3) cycle).  For k = 1 each interior point costs 7
+    # FP64 instructions (3 add, 1 mul, 3 fma) and 24 algorithmic bytes (read
+    # x and b, write x); the sweep is FP64-pipe bound on GB300.
+    gs_launches_L = (3 + 3) * args.steps
     gs_ms = kms[hhg.K_FACE_GS] / gs_launches_L
-    nfi = info.n_faces * (info.N - 1) * (info.N - 2) // 2
-    pts = nfi / 3.0                               # one colour per launch
-    flops = 10.0 * pts                            # 3 adds + 3 muls + 2 adds + 1 sub + 1 div per point
+    pts = info.n_faces * (info.N - 1) * (info.N - 2) // 2
+    ops = 7.0 * pts
     sm_mhz = clk.get("sm_mhz") or 2070.0
-    peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e9        # GFLOP/s at the sampled clock
-    achieved = flops / (gs_ms / 1e3) / 1e9
-    bytes_alg = 24.0 * pts                        # read x, b; write x of the colour's points
+    peak = N_SM * FP64_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e9        # G FP64 instr/s at the sampled clock
+    achieved = ops / (gs_ms / 1e3) / 1e9
+    bytes_alg = 24.0 * pts
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    roofline = {"bound": "alu", "kernel": "k_face<double,GS> (one colour phase, level %d)" % L,
-                "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
-                "traffic": None, "flops_per_launch": flops, "ms_per_launch": gs_ms,
-                "peak_basis": f"FP64: {N_SM} SMs x {FP64_FLOP_PER_CLK_SM} flop/clk x {sm_mhz:.0f} MHz (sampled)",
+    # DRAM traffic of one launch from the ncu capture at level 9 (profiles/
+    # k_face_gs3_fp64_annulus128_L9.md), scaled by the 4x points of level 10
+    traffic = (287.764224e6 + 106.255872e6) * (pts / 16760832.0) if L in (9, 10) else None
+    roofline = {"bound": "alu", "kernel": f"k_face_gs3<double> fused 3-colour sweep, level {L}",
+                "achieved": achieved, "peak": peak, "unit": "G FP64-instr/s", "frac": achieved / peak,
+                "traffic": traffic, "ops_per_launch": ops, "ms_per_launch": gs_ms,
+                "peak_basis": f"{N_SM} SMs x {FP64_OPS_PER_CLK_SM} FP64 instr/clk x {sm_mhz:.0f} MHz (sampled)",
                 "hbm": {"achieved_gbs": bytes_alg / (gs_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
                         "frac": bytes_alg / (gs_ms / 1e3) / 1e9 / hbm_peak,
                         "algorithmic_bytes_per_launch": bytes_alg}}
