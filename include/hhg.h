@@ -159,6 +159,22 @@ hhg_status hhg_assign(hhg_mesh mesh, int32_t level, hhg_prec prec, double alpha,
 hhg_status hhg_dot(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1, const void* x2,
                    double* result_dev, void* stream);
 
+/* The dot product of hhg_dot for callers that must not allocate device
+ * memory -- code running where the application's allocator or memory pool
+ * forbids new allocations, or where every byte of device memory has been
+ * handed out already.  The paper has no counterpart; this is a property of
+ * the library, not of the method.  The call allocates nothing: its partial
+ * sums live in a fixed 128 KB device array that is part of the library image
+ * (present on every device that loads the library, until the process exits).
+ * Same arguments and result as hhg_dot, summed in a different (still fixed)
+ * order, so the two agree to rounding.  Limit: the level vector may have at
+ * most 2^28 slots (hhg_info.vec_len); larger levels return HHG_ERR_ARG.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call uses
+ * the same array: calls that overlap on the GPU race and give wrong results. */
+hhg_status hhg_dot_noalloc(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1,
+                           const void* x2, double* result_dev, void* stream);
+
 /* Restriction (Sec. 4.3, a non-square matrix-vector product): b_coarse =
  * P^T r_fine on the free coarse DoFs (full weighting: the fine value at the
  * coarse point plus half of each of its six fine neighbours, summed over all

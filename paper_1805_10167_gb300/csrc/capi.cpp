@@ -272,6 +272,20 @@ hhg_status hhg_dot(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1, 
   });
 }
 
+hhg_status hhg_dot_noalloc(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1,
+                           const void* x2, double* result_dev, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    check_prec(prec);
+    need_vec(x1, "x1");
+    need_vec(x2, "x2");
+    need(result_dev, "result_dev");
+    hhg::dot_noalloc(m, level, prec, x1, x2, result_dev, S(stream));
+    return HHG_OK;
+  });
+}
+
 hhg_status hhg_restrict(hhg_mesh mesh, int32_t fine_level, hhg_prec prec, const void* r_fine,
                         void* b_coarse, void* stream) {
   return guarded([&]() {

@@ -207,6 +207,8 @@ void coarsen_k(const Mesh& m, int coarse_level, int prec_src_dst, cudaStream_t s
 void load_k_fine(const Mesh& m, const double* k_canon, cudaStream_t st);
 void convert_k_to_f32(const Mesh& m, int level, cudaStream_t st);
 void sqrt_scalar(double* v, cudaStream_t st);
+void dot_noalloc(const Mesh& m, int level, int prec, const void* x1, const void* x2,
+                 double* out_dev, cudaStream_t st);
 // mixed precision helpers for iterative refinement
 void residual_f64_to_f32(const Mesh& m, int level, const double* x, const double* b, float* r32,
                          double* norm2_dev, cudaStream_t st);

@@ -65,6 +65,7 @@ _SIGS = {
     "hhg_residual": [_P, C.c_int32, C.c_int32, _P, _P, _P, _P, _P],
     "hhg_assign": [_P, C.c_int32, C.c_int32, C.c_double, _P, C.c_double, _P, _P, _P],
     "hhg_dot": [_P, C.c_int32, C.c_int32, _P, _P, _P, _P],
+    "hhg_dot_noalloc": [_P, C.c_int32, C.c_int32, _P, _P, _P, _P],
     "hhg_restrict": [_P, C.c_int32, C.c_int32, _P, _P, _P],
     "hhg_prolongate_add": [_P, C.c_int32, C.c_int32, _P, _P, _P],
     "hhg_smooth": [_P, C.c_int32, C.c_int32, _P, _P, C.c_int32, C.c_int32, C.c_double, _P],
@@ -190,6 +191,11 @@ class Mesh:
 
     def dot(self, level, x1, x2, out_dev, prec=F64, stream=None):
         _check(lib.hhg_dot(self.h, level, prec, _ptr(x1), _ptr(x2), _ptr(out_dev), _stream(stream)))
+
+    def dot_noalloc(self, level, x1, x2, out_dev, prec=F64, stream=None):
+        """hhg_dot without any device allocation (static scratch; see include/hhg.h)."""
+        _check(lib.hhg_dot_noalloc(self.h, level, prec, _ptr(x1), _ptr(x2), _ptr(out_dev),
+                                   _stream(stream)))
 
     def restrict(self, fine_level, r_fine, b_coarse, prec=F64, stream=None):
         _check(lib.hhg_restrict(self.h, fine_level, prec, _ptr(r_fine), _ptr(b_coarse), _stream(stream)))
