@@ -210,6 +210,42 @@ hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
 hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
                      const hhg_solve_opts* opts, hhg_solve_report* rep, void* stream);
 
+/* Autotuner: for every level >= 2 times candidate row-block splits of the
+ * fused face Gauss-Seidel sweep in precision `prec` and keeps the fastest
+ * (results do not depend on the split).  If the environment variable
+ * HHG_TUNE_CACHE names a file, choices are read from and appended to it.
+ * Synchronous. */
+hhg_status hhg_tune(hhg_mesh mesh, hhg_prec prec, void* stream);
+
+/* Batches of independent problems (not in the paper: its multigrid solves
+ * one problem at a time).  Problem p is a macro mesh (xy[p]: nv[p] x 2 host
+ * doubles, tri[p]: nt[p] x 3 host ids, Dirichlet = its boundary vertices)
+ * refined to its own level levels[p] in 1..10.  Problems of equal level are
+ * merged into one mesh so that every kernel covers all of them; the level
+ * groups run concurrently on their own streams, one outer iteration of the
+ * whole batch is captured as a CUDA graph and replayed.  Errors as for
+ * hhg_mesh_create (HHG_ERR_MESH names the problem). */
+typedef struct hhg_batch_s* hhg_batch;
+hhg_status hhg_batch_create(int32_t n, const double* const* xy, const int64_t* nv,
+                            const int32_t* const* tri, const int64_t* nt, const int32_t* levels,
+                            hhg_batch* out);
+hhg_status hhg_batch_destroy(hhg_batch batch);
+/* Sizes of problem p: N, n_nodes (its canonical length), n_free, n_elems,
+ * n_vertices, n_edges, n_faces, max_level (= its level); vec_len = 0. */
+hhg_status hhg_batch_info(hhg_batch batch, int32_t problem, hhg_info* out);
+/* hhg_tune for every level group (FP32, the inner precision). */
+hhg_status hhg_batch_tune(hhg_batch batch, void* stream);
+/* Solve every problem: x[p], b[p] are DEVICE arrays of n_nodes(p) doubles in
+ * problem p's canonical order (x: initial guess with Dirichlet values in,
+ * solution out).  `x` and `b` themselves are HOST arrays of n pointers.
+ * opts->mode HHG_SOLVE_IR (default: FP32 V-cycles inside FP64 refinement) or
+ * HHG_SOLVE_MG (FP64 V-cycles); every problem iterates until its own
+ * ||b - A x|| <= tol ||b - A x0||.  reps: NULL or n reports (history unused;
+ * iterations = the outer iteration at which that problem met its tolerance).
+ * Synchronous. */
+hhg_status hhg_batch_solve(hhg_batch batch, double* const* x, const double* const* b,
+                           const hhg_solve_opts* opts, hhg_solve_report* reps, void* stream);
+
 /* Diagnostics.  The library counts every kernel it launches, by class; while
  * profiling is on it also brackets each launch of the classes in `mask`
  * (bit c = class c) on level `level` with CUDA events on the launching

@@ -15,12 +15,9 @@ struct hhg_mesh_s {
   hhg::Mesh* m;
 };
 
-namespace hhg {
-Mesh* mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
-                  const uint8_t* dirichlet_vertex, int max_level);
-void mesh_destroy(Mesh* m);
-void set_coefficient(Mesh& m, const double* k_dev, cudaStream_t st);
-}  // namespace hhg
+struct hhg_batch_s {
+  hhg::Batch* b;
+};
 
 namespace {
 
@@ -47,6 +44,8 @@ hhg_status guarded(F&& f) {
     return fail(HHG_ERR_ARG, e.what());
   } catch (const hhg::MeshError& e) {
     return fail(HHG_ERR_MESH, e.what());
+  } catch (const hhg::SolveStatus& e) {
+    return fail((hhg_status)e.status, e.what());
   } catch (const std::runtime_error& e) {
     return fail(HHG_ERR_CUDA, e.what());
   } catch (...) {
@@ -89,12 +88,22 @@ bool device_timed_out(const hhg::Mesh& m, cudaStream_t st) {
 
 cudaStream_t S(void* s) { return (cudaStream_t)s; }
 
+double read_scalar(const double* dev, cudaStream_t st) {
+  double h = 0.0;
+  hhg::check_cuda(cudaMemcpyAsync(&h, dev, sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
+  hhg::check_cuda(cudaStreamSynchronize(st), "sync");
+  return h;
+}
+
+}  // namespace
+
+namespace hhg {
 // One V(nu1, nu2) cycle on level l (Sec. 4.3).  x, b belong to the caller on
 // the top level and to the library below it.  Ghost copies of x are
-// consistent on entry and on exit.
-void vcycle_rec(const hhg::Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2,
+// consistent on entry and on exit.  Smoothing sweeps alternate between x and
+// the level's workspace w; an odd sweep count ends with a copy back to x.
+void vcycle_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2,
                 cudaStream_t st) {
-  using namespace hhg;
   if (l == 0) {
     coarse_solve(m, prec, b, x, st);
     return;
@@ -110,25 +119,17 @@ void vcycle_rec(const hhg::Mesh& m, int l, int prec, void* x, const void* b, int
   residual_op(m, l, prec, cur, b, ld.r[prec], nullptr, st);
   restrict_op(m, l, prec, ld.r[prec], lc.b[prec], st);
   zero_vec(m, l - 1, prec, lc.x[prec], st);
-  vcycle_rec(m, l - 1, prec, lc.x[prec], lc.b[prec], nu1, nu2, st);
+  vcycle_run(m, l - 1, prec, lc.x[prec], lc.b[prec], nu1, nu2, st);
   prolongate_add(m, l, prec, lc.x[prec], cur, st);
   for (int s = 0; s < nu2; ++s) {
     gs_sweep(m, l, prec, cur, oth, b, false, st);
     std::swap(cur, oth);
   }
   if (cur != x)
-    hhg::check_cuda(cudaMemcpyAsync(x, cur, (size_t)ld.lv.len * (prec == 0 ? 8 : 4),
-                                    cudaMemcpyDeviceToDevice, st), "iterate copy");
+    check_cuda(cudaMemcpyAsync(x, cur, (size_t)ld.lv.len * (prec == 0 ? 8 : 4),
+                               cudaMemcpyDeviceToDevice, st), "iterate copy");
 }
-
-double read_scalar(const double* dev, cudaStream_t st) {
-  double h = 0.0;
-  hhg::check_cuda(cudaMemcpyAsync(&h, dev, sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
-  hhg::check_cuda(cudaStreamSynchronize(st), "sync");
-  return h;
-}
-
-}  // namespace
+}  // namespace hhg
 
 extern "C" {
 
@@ -147,7 +148,7 @@ hhg_status hhg_mesh_create(const double* xy, int64_t nv, const int32_t* tri, int
 hhg_status hhg_mesh_destroy(hhg_mesh mesh) {
   return guarded([&]() {
     if (!mesh) return HHG_OK;
-    hhg::mesh_destroy(mesh->m);
+    hhg::mesh_destroy_internal(mesh->m);
     delete mesh;
     return HHG_OK;
   });
@@ -354,7 +355,7 @@ hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
     const int nu1 = opts ? opts->nu1 : 3, nu2 = opts ? opts->nu2 : 3;
     if (nu1 < 0 || nu2 < 0) throw ArgError("negative sweep count");
     hhg::ghost_fill(m, level, prec, x, S(stream));
-    vcycle_rec(m, level, prec, x, b, nu1, nu2, S(stream));
+    hhg::vcycle_run(m, level, prec, x, b, nu1, nu2, S(stream));
     return HHG_OK;
   });
 }
@@ -396,11 +397,11 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
       if (o.mode == HHG_SOLVE_IR) {
         // inner FP32 V-cycle on A d = r from d = 0, then x += d in FP64
         hhg::zero_vec(m, level, 1, ld.x[1], st);
-        vcycle_rec(m, level, 1, ld.x[1], ld.b[1], o.nu1, o.nu2, st);
+        hhg::vcycle_run(m, level, 1, ld.x[1], ld.b[1], o.nu1, o.nu2, st);
         hhg::update_f64_from_f32(m, level, x, (const float*)ld.x[1], st);
         hhg::residual_f64_to_f32(m, level, x, b, (float*)ld.b[1], nrm, st);
       } else {
-        vcycle_rec(m, level, 0, x, b, o.nu1, o.nu2, st);
+        hhg::vcycle_run(m, level, 0, x, b, o.nu1, o.nu2, st);
         hhg::residual_op(m, level, 0, x, b, ld.r[0], nrm, st);
       }
       ++it;
@@ -418,6 +419,68 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
     if (status == HHG_ERR_TIMEOUT) return fail(status, "a device-side wait gave up");
     if (status == HHG_ERR_NAN) return fail(status, "non-finite residual norm");
     if (status == HHG_ERR_NOT_CONVERGED) return fail(status, "max_iter reached");
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_tune(hhg_mesh mesh, hhg_prec prec, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_prec(prec);
+    for (int l = 2; l <= m.max_level; ++l) hhg::tune_face_sweep(m, l, prec, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_batch_create(int32_t n, const double* const* xy, const int64_t* nv,
+                            const int32_t* const* tri, const int64_t* nt, const int32_t* levels,
+                            hhg_batch* out) {
+  return guarded([&]() {
+    need(out, "out");
+    *out = nullptr;
+    hhg::Batch* b = hhg::batch_create(n, xy, nv, tri, nt, levels);
+    *out = new hhg_batch_s{b};
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_batch_destroy(hhg_batch batch) {
+  return guarded([&]() {
+    if (!batch) return HHG_OK;
+    hhg::batch_destroy(batch->b);
+    delete batch;
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_batch_info(hhg_batch batch, int32_t problem, hhg_info* out) {
+  return guarded([&]() {
+    if (!batch || !batch->b) throw ArgError("NULL batch");
+    need(out, "out");
+    hhg::batch_problem_info(*batch->b, problem, out);
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_batch_tune(hhg_batch batch, void* stream) {
+  return guarded([&]() {
+    if (!batch || !batch->b) throw ArgError("NULL batch");
+    hhg::batch_tune(*batch->b, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_batch_solve(hhg_batch batch, double* const* x, const double* const* b,
+                           const hhg_solve_opts* opts, hhg_solve_report* reps, void* stream) {
+  return guarded([&]() {
+    if (!batch || !batch->b) throw ArgError("NULL batch");
+    need(x, "x");
+    need(b, "b");
+    hhg_solve_opts o{HHG_SOLVE_IR, 3, 3, 100, 1e-10};
+    if (opts) o = *opts;
+    if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 0 || !(o.tol >= 0.0)) throw ArgError("bad solve options");
+    if (o.mode != HHG_SOLVE_MG && o.mode != HHG_SOLVE_IR) throw ArgError("bad solve mode");
+    hhg::batch_solve(*batch->b, x, b, o, reps, S(stream));
     return HHG_OK;
   });
 }

@@ -22,7 +22,9 @@ namespace hhg {
 
 namespace {
 
-constexpr int kRC = 8;                // rows per wavefront step = warps per CTA
+constexpr int kRC = 8;                // rows per wavefront step
+constexpr int kWPR = 2;               // warps per row
+constexpr int kThreadsGS = kRC * kWPR * 32;
 constexpr int kSlots = 2 * kRC + 4;   // ring: rows [q-3, q+RC] in use, [q+RC+1, q+2RC] in flight
 constexpr int kBarBytes = 256;
 constexpr long kMaxTries = 1L << 22;  // try_wait polls before a wait gives up
@@ -63,7 +65,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 }  // namespace
 
 template <typename T, bool VARK, bool FWD>
-__global__ void __launch_bounds__(kRC * 32)
+__global__ void __launch_bounds__(kThreadsGS)
     k_face_gs3(MeshTables M, LevelView L, const T* __restrict__ xin, T* __restrict__ xout,
                const T* __restrict__ b, const T* __restrict__ k, const int4* __restrict__ tasks,
                int* err) {
@@ -76,7 +78,10 @@ __global__ void __launch_bounds__(kRC * 32)
   const int f = tk.x, j0 = tk.y, j1 = tk.z;   // output rows [j0, j1)
   const int N = L.N;
   const int64_t S = L.S;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int rw = warp / kWPR;                                  // row within the step
+  const int lane = (warp % kWPR) * 32 + (threadIdx.x & 31);     // position within the row
+  constexpr int kStride = 3 * kWPR * 32;                        // same-colour points per pass
   const int64_t fb = L.f_off + (int64_t)f * L.FS;
   const T* xg = xin + fb;
   const T* bg = b + fb;
@@ -113,7 +118,30 @@ __global__ void __launch_bounds__(kRC * 32)
     }
   };
 
-  // one colour of one row; r interior, colour c
+  // one point of colour c in row r (k = 1 form or on-the-fly weights)
+  auto relax = [&](const T* rm, const T* r0, const T* rp, const T* br, int r, int i) -> T {
+    if (!VARK) {
+      T acc = br[i] * dinv;
+      acc = fma(w2, r0[i + 1] + r0[i - 1], acc);
+      acc = fma(w1, rp[i] + rm[i], acc);
+      acc = fma(w0, rm[i + 1] + rp[i - 1], acc);
+      return acc;
+    } else {
+      const int64_t p = (int64_t)r * S + i;
+      const T u = __ldg(ku + p), uw = __ldg(ku + p - 1), us = __ldg(ku + p - S);
+      const T ds = __ldg(kd + p - S), dw = __ldg(kd + p - 1), dsw = __ldg(kd + p - 1 - S);
+      const T h0 = T(0.5) * c0, h1 = T(0.5) * c1, h2 = T(0.5) * c2;
+      const T we = h2 * (u + ds), ww = h2 * (uw + dsw);
+      const T wn = h1 * (u + dw), ws = h1 * (us + dsw);
+      const T wse = h0 * (us + ds), wnw = h0 * (uw + dw);
+      const T off = -(we * r0[i + 1] + ww * r0[i - 1] + wn * rp[i] + ws * rm[i] + wse * rm[i + 1] +
+                      wnw * rp[i - 1]);
+      const T diag = we + ww + wn + ws + wse + wnw;
+      return (br[i] - off) / diag;
+    }
+  };
+  // one colour of one row (r interior): two points per thread and pass, both
+  // computed from values loaded before either is stored
   auto relax_row = [&](int r, int c) {
     T* r0 = row(r);
     const T* rm = row(r - 1);
@@ -122,26 +150,14 @@ __global__ void __launch_bounds__(kRC * 32)
     int i0 = ((c - 2 * r) % 3 + 3) % 3;
     if (i0 == 0) i0 = 3;
     const int iend = N - r;
-    for (int i = i0 + 3 * lane; i < iend; i += 96) {
-      if (!VARK) {
-        T acc = br[i] * dinv;
-        acc = fma(w2, r0[i + 1] + r0[i - 1], acc);
-        acc = fma(w1, rp[i] + rm[i], acc);
-        acc = fma(w0, rm[i + 1] + rp[i - 1], acc);
-        r0[i] = acc;
-      } else {
-        const int64_t p = (int64_t)r * S + i;
-        const T u = __ldg(ku + p), uw = __ldg(ku + p - 1), us = __ldg(ku + p - S);
-        const T ds = __ldg(kd + p - S), dw = __ldg(kd + p - 1), dsw = __ldg(kd + p - 1 - S);
-        const T h0 = T(0.5) * c0, h1 = T(0.5) * c1, h2 = T(0.5) * c2;
-        const T we = h2 * (u + ds), ww = h2 * (uw + dsw);
-        const T wn = h1 * (u + dw), ws = h1 * (us + dsw);
-        const T wse = h0 * (us + ds), wnw = h0 * (uw + dw);
-        const T off = -(we * r0[i + 1] + ww * r0[i - 1] + wn * rp[i] + ws * rm[i] + wse * rm[i + 1] +
-                        wnw * rp[i - 1]);
-        const T diag = we + ww + wn + ws + wse + wnw;
-        r0[i] = (br[i] - off) / diag;
+    for (int i = i0 + 3 * lane; i < iend; i += 2 * kStride) {
+      const int i2 = i + kStride;
+      const T v1 = relax(rm, r0, rp, br, r, i);
+      if (i2 < iend) {
+        const T v2 = relax(rm, r0, rp, br, r, i2);
+        r0[i2] = v2;
       }
+      r0[i] = v1;
     }
   };
 
@@ -164,26 +180,26 @@ __global__ void __launch_bounds__(kRC * 32)
     __syncthreads();
     if (s_fail) break;
     {  // colour A on rows q .. q+RC-1
-      const int r = q + warp;
+      const int r = q + rw;
       if (r >= max(lo_int, j0 - 2) && r <= min(hi_int, j1 + 1)) relax_row(r, cA);
     }
     __syncthreads();
     {  // colour B one row behind
-      const int r = q - 1 + warp;
+      const int r = q - 1 + rw;
       if (r >= max(lo_int, j0 - 1) && r <= min(hi_int, j1)) relax_row(r, cB);
     }
     __syncthreads();
     {  // colour C two rows behind
-      const int r = q - 2 + warp;
+      const int r = q - 2 + rw;
       if (r >= max(lo_int, j0) && r <= min(hi_int, j1 - 1)) relax_row(r, cC);
     }
     __syncthreads();
     {  // rows q-2 .. q+RC-3 are final: write them (boundary copies included)
-      const int r = q - 2 + warp;
+      const int r = q - 2 + rw;
       if (r >= j0 && r < j1) {
         const T* src = row(r);
         T* dst = xout + fb + (int64_t)r * S;
-        for (int i = lane; i <= N - r; i += 32) dst[i] = src[i];
+        for (int i = lane; i <= N - r; i += kWPR * 32) dst[i] = src[i];
       }
     }
     __syncthreads();
@@ -250,7 +266,7 @@ static void launch_t(const MeshTables& tab, const LevelView& L, const T* xin, T*
                "face gs smem attribute");
     configured = smem;
   }
-  k_face_gs3<T, VARK, FWD><<<ntasks, kRC * 32, smem, st>>>(tab, L, xin, xout, b, k, tasks, err);
+  k_face_gs3<T, VARK, FWD><<<ntasks, kThreadsGS, smem, st>>>(tab, L, xin, xout, b, k, tasks, err);
 }
 
 void face_gs3_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,

@@ -28,6 +28,12 @@ struct MeshError : std::runtime_error {
   using std::runtime_error::runtime_error;
 };
 
+// A solver outcome other than HHG_OK (not converged, NaN, timeout).
+struct SolveStatus : std::runtime_error {
+  int status;
+  explicit SolveStatus(int s) : std::runtime_error("solver status " + std::to_string(s)), status(s) {}
+};
+
 struct LevelView {
   int N;
   int64_t S, ES, FS;
@@ -90,6 +96,17 @@ struct VertRec {
   int e_begin, e_end;   // range in the vertex-edge table
 };
 
+// One independent problem inside a mesh (a plain mesh is one block; a batch
+// group merges several problems of the same level into one mesh).  Its
+// macro-vertices, macro-edges and macro-faces are contiguous ranges.
+struct Block {
+  int v0, v1, e0, e1, f0, f1;
+  int n0;          // free macro-vertices (level-0 unknowns)
+  int a0_off;      // offset of its dense level-0 matrix in Mesh::A0
+  int free0_off;   // offset of its level-0 vertex list in Mesh::free0
+  int pad;
+};
+
 struct MeshTables {
   const FaceRec* faces;
   const EdgeRec* edges;
@@ -146,6 +163,7 @@ struct LevelData {
   void* k[2] = {nullptr, nullptr};  // coefficient: up array then down array (2 * nf * FS)
   int* face_tasks = nullptr;        // device int4 (face, j0, j1, 0): row blocks of the face sweep
   int n_face_tasks = 0;
+  int face_tasks_per_face = 0;
 };
 
 struct Mesh {
@@ -160,10 +178,13 @@ struct Mesh {
   std::vector<void*> allocations;
   std::vector<LevelData> levels;
   bool vark = false;
-  // level-0 coarse solve: dense matrix over free vertices (double), index map
-  int n0 = 0;
-  double* A0 = nullptr;             // n0 x n0, row-major
-  int* free0 = nullptr;             // n0 vertex ids
+  // independent problems (blocks); level-0 coarse solve per block: dense
+  // n0 x n0 matrix over its free macro-vertices (row-major, in A0 at a0_off)
+  std::vector<Block> h_blocks;
+  Block* blocks = nullptr;          // device copy
+  int max_n0 = 0;
+  double* A0 = nullptr;
+  int* free0 = nullptr;             // level-0 vertex ids of all blocks
   std::vector<double> h_cot_unit;   // cached for k = 1
   // reduction scratch
   double* partials = nullptr;       // kMaxPartials doubles
@@ -215,6 +236,40 @@ void residual_f64_to_f32(const Mesh& m, int level, const double* x, const double
 void update_f64_from_f32(const Mesh& m, int level, double* x, const float* d32, cudaStream_t st);
 
 void check_cuda(cudaError_t e, const char* what);
+
+// Mesh of nblocks independent problems merged on the host: block b owns the
+// vertices [vstart[b], vstart[b+1]) and faces [fstart[b], fstart[b+1]); no face
+// may use a vertex of another block.  nblocks = 1, vstart = {0, nv},
+// fstart = {0, nt} is a plain mesh.
+Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                         const uint8_t* dirichlet_vertex, int max_level, int nblocks,
+                         const int64_t* vstart, const int64_t* fstart);
+Mesh* mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                  const uint8_t* dirichlet_vertex, int max_level);
+void mesh_destroy_internal(Mesh* m);
+void set_coefficient(Mesh& m, const double* k_dev, cudaStream_t st);
+// One V(nu1, nu2) cycle on level l (x, b in precision prec); ghost copies of
+// x consistent on entry and on exit.
+void vcycle_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2,
+                cudaStream_t st);
+
+struct Batch;
+Batch* batch_create(int n, const double* const* xy, const int64_t* nv, const int32_t* const* tri,
+                    const int64_t* nt, const int32_t* levels);
+void batch_destroy(Batch* B);
+void batch_problem_info(const Batch& B, int p, hhg_info* out);
+void batch_tune(Batch& B, cudaStream_t st);
+void batch_solve(Batch& B, double* const* x, const double* const* b, const hhg_solve_opts& o,
+                 hhg_solve_report* reps, cudaStream_t st);
+
+// Per-block sums of squares of the owned free entries of an FP64 level vector
+// (r64) into out[nblocks] (device); if r32 != nullptr also writes r32 = (float) r64.
+void block_norms2(const Mesh& m, int level, const double* r64, float* r32, double* out,
+                  cudaStream_t st);
+// Autotuner: picks the row-block split of the face sweep on `level` for
+// precision `prec` by timing candidates; returns the chosen tasks per face.
+int tune_face_sweep(Mesh& m, int level, int prec, cudaStream_t st);
+void set_face_tasks(Mesh& m, int level, int per_face);
 
 // Counts one kernel launch of class `cls` (hhg_kernel_class); while profiling
 // is on for that class and level, brackets it with CUDA events on `st`.

@@ -403,12 +403,18 @@ __global__ void k_prolong_face(MeshTables M, LevelView Lf, LevelView Lc, const T
 
 // --------------------------------------------------------------- coarse CG
 // Plain conjugate gradients on the dense level-0 matrix over the free
-// macro-vertices (one block; level 0 has only vertex unknowns), in double,
-// to ||r|| <= 1e-14 ||b|| or 2 n0 iterations.
+// macro-vertices of one problem (level 0 has only vertex unknowns), one CTA
+// per problem, in double, to ||r|| <= 1e-14 ||b|| or 2 n0 iterations.
 template <typename T>
-__global__ void k_coarse_cg(int n0, const double* __restrict__ A, const int* __restrict__ idx,
-                            const T* __restrict__ b, T* __restrict__ x, int64_t v_off) {
+__global__ void k_coarse_cg(const Block* __restrict__ blocks, const double* __restrict__ A0,
+                            const int* __restrict__ free0, const T* __restrict__ b, T* __restrict__ x,
+                            int64_t v_off) {
   extern __shared__ double sh[];
+  const Block B = blocks[blockIdx.x];
+  const int n0 = B.n0;
+  if (n0 == 0) return;
+  const double* A = A0 + B.a0_off;
+  const int* idx = free0 + B.free0_off;
   double* xs = sh;
   double* r = sh + n0;
   double* p = sh + 2 * n0;
@@ -745,15 +751,70 @@ void prolongate_add(const Mesh& m, int fine_level, int prec, const void* x_coars
 }
 
 void coarse_solve(const Mesh& m, int prec, const void* b0, void* x0, cudaStream_t st) {
-  const int n0 = m.n0;
-  if (n0 > 0) {
-    const size_t smem = 4 * (size_t)n0 * sizeof(double);
+  if (m.max_n0 > 0) {
+    const size_t smem = 4 * (size_t)m.max_n0 * sizeof(double);
+    const int nb = (int)m.h_blocks.size();
     if (prec == 0)
-      HHG_LAUNCH(HHG_K_OTHER, 0, st, "coarse cg", k_coarse_cg<double><<<1, kThreads, smem, st>>>(n0, m.A0, m.free0, (const double*)b0, (double*)x0, m.levels[0].lv.v_off));
+      HHG_LAUNCH(HHG_K_OTHER, 0, st, "coarse cg", k_coarse_cg<double><<<nb, kThreads, smem, st>>>(m.blocks, m.A0, m.free0, (const double*)b0, (double*)x0, m.levels[0].lv.v_off));
     else
-      HHG_LAUNCH(HHG_K_OTHER, 0, st, "coarse cg", k_coarse_cg<float><<<1, kThreads, smem, st>>>(n0, m.A0, m.free0, (const float*)b0, (float*)x0, m.levels[0].lv.v_off));
+      HHG_LAUNCH(HHG_K_OTHER, 0, st, "coarse cg", k_coarse_cg<float><<<nb, kThreads, smem, st>>>(m.blocks, m.A0, m.free0, (const float*)b0, (float*)x0, m.levels[0].lv.v_off));
   }
   ghost_fill(m, 0, prec, x0, st);
+}
+
+// --------------------------------------------------------------- per-block norms
+// Sum of squares of the owned free entries of each block (problem) of an FP64
+// level vector, optionally casting the vector to FP32 on the way.  A block's
+// slots are three contiguous ranges: its vertices, its edges, its faces.
+__device__ __forceinline__ bool owned_free_slot(const MeshTables& M, const LevelView& L, int64_t s) {
+  if (s < L.e_off) return s < M.nv && !M.verts[s].dirichlet;
+  if (s < L.f_off) {
+    const int64_t q = s - L.e_off;
+    const int64_t e = q / L.ES, t = q - e * L.ES;
+    return e < M.ne && t >= 1 && t <= L.N - 1 && !M.edges[e].dirichlet;
+  }
+  const int64_t q = (s - L.f_off) % L.FS;
+  const int64_t j = q / L.S, i = q - j * L.S;
+  return i >= 1 && j >= 1 && i + j <= L.N - 1;
+}
+
+__global__ void k_block_norms2(MeshTables M, LevelView L, const Block* __restrict__ blocks,
+                               const double* __restrict__ r64, float* r32, double* partials) {
+  const Block B = blocks[blockIdx.y];
+  const int64_t nvr = B.v1 - B.v0, ner = (int64_t)(B.e1 - B.e0) * L.ES;
+  const int64_t total = nvr + ner + (int64_t)(B.f1 - B.f0) * L.FS;
+  double acc = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s;
+    if (k < nvr) s = L.v_off + B.v0 + k;
+    else if (k < nvr + ner) s = L.e_off + (int64_t)B.e0 * L.ES + (k - nvr);
+    else s = L.f_off + (int64_t)B.f0 * L.FS + (k - nvr - ner);
+    const double v = r64[s];
+    if (r32) r32[s] = (float)v;
+    if (owned_free_slot(M, L, s)) acc += v * v;
+  }
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void k_block_sums(const double* __restrict__ partials, int per_block, double* out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < per_block; i += blockDim.x) acc += partials[(int64_t)blockIdx.x * per_block + i];
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+
+void block_norms2(const Mesh& m, int level, const double* r64, float* r32, double* out,
+                  cudaStream_t st) {
+  const LevelView& L = m.levels[level].lv;
+  const int nb = (int)m.h_blocks.size();
+  int per = kMaxPartials / nb;
+  if (per > 64) per = 64;
+  if (per < 1) throw std::runtime_error("too many blocks for the partial-sum buffer");
+  dim3 grid(per, nb);
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "block norms", k_block_norms2<<<grid, kThreads, 0, st>>>(m.tab, L, m.blocks, r64, r32, m.partials));
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "block sums", k_block_sums<<<nb, kThreads, 0, st>>>(m.partials, per, out));
 }
 
 void zero_vec(const Mesh& m, int level, int prec, void* v, cudaStream_t st) {

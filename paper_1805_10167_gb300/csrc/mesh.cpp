@@ -85,41 +85,59 @@ static void colour_edges(const Mesh& m, int N, std::vector<int>& ptr, std::vecto
   ptr[ncol] = (int)list.size();
 }
 
-// Dense level-0 matrix over the free macro-vertices (level 0 has no edge or
-// face interiors).  k0[f] = coefficient of face f's single micro-triangle.
+// Dense level-0 matrices, one per block, over its free macro-vertices (level
+// 0 has no edge or face interiors).  k0[f] = coefficient of face f's single
+// micro-triangle.
 static void assemble_level0(Mesh& m, const std::vector<double>& k0) {
   std::vector<int> map(m.nv, -1), free0;
-  for (int v = 0; v < m.nv; ++v)
-    if (!m.h_verts[v].dirichlet) {
-      map[v] = (int)free0.size();
-      free0.push_back(v);
-    }
-  const int n0 = (int)free0.size();
-  std::vector<double> A((size_t)n0 * n0, 0.0);
-  for (int f = 0; f < m.nf; ++f) {
-    const FaceRec& F = m.h_faces[f];
-    for (int r = 0; r < 3; ++r) {
-      const int a = F.v[r], b = F.v[(r + 1) % 3];
-      const double w = 0.5 * F.cot[(r + 2) % 3] * k0[f];
-      const int ia = map[a], ib = map[b];
-      if (ia >= 0) A[(size_t)ia * n0 + ia] += w;
-      if (ib >= 0) A[(size_t)ib * n0 + ib] += w;
-      if (ia >= 0 && ib >= 0) {
-        A[(size_t)ia * n0 + ib] -= w;
-        A[(size_t)ib * n0 + ia] -= w;
+  std::vector<double> A;
+  m.max_n0 = 0;
+  for (Block& B : m.h_blocks) {
+    B.free0_off = (int)free0.size();
+    for (int v = B.v0; v < B.v1; ++v)
+      if (!m.h_verts[v].dirichlet) {
+        map[v] = (int)free0.size() - B.free0_off;
+        free0.push_back(v);
+      }
+    B.n0 = (int)free0.size() - B.free0_off;
+    B.a0_off = (int)A.size();
+    A.resize(A.size() + (size_t)B.n0 * B.n0, 0.0);
+    double* Ab = A.data() + B.a0_off;
+    const int n0 = B.n0;
+    for (int f = B.f0; f < B.f1; ++f) {
+      const FaceRec& F = m.h_faces[f];
+      for (int r = 0; r < 3; ++r) {
+        const int a = F.v[r], b = F.v[(r + 1) % 3];
+        const double w = 0.5 * F.cot[(r + 2) % 3] * k0[f];
+        const int ia = map[a], ib = map[b];
+        if (ia >= 0) Ab[(size_t)ia * n0 + ia] += w;
+        if (ib >= 0) Ab[(size_t)ib * n0 + ib] += w;
+        if (ia >= 0 && ib >= 0) {
+          Ab[(size_t)ia * n0 + ib] -= w;
+          Ab[(size_t)ib * n0 + ia] -= w;
+        }
       }
     }
+    m.max_n0 = std::max(m.max_n0, n0);
   }
-  m.n0 = n0;
   if (!m.A0) {
     m.A0 = (double*)dev_alloc(m, std::max<size_t>(1, A.size()) * sizeof(double));
     m.free0 = upload(m, free0);
+    m.blocks = upload(m, m.h_blocks);
   }
-  if (n0) check_cuda(cudaMemcpy(m.A0, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice), "A0");
+  if (!A.empty()) check_cuda(cudaMemcpy(m.A0, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice), "A0");
+  check_cuda(cudaMemcpy(m.blocks, m.h_blocks.data(), m.h_blocks.size() * sizeof(Block), cudaMemcpyHostToDevice), "blocks");
 }
 
 Mesh* mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
                   const uint8_t* dirichlet_vertex, int max_level) {
+  const int64_t vs[2] = {0, nv}, fs[2] = {0, nt};
+  return mesh_create_blocks(xy, nv, tri, nt, dirichlet_vertex, max_level, 1, vs, fs);
+}
+
+Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                         const uint8_t* dirichlet_vertex, int max_level, int nblocks,
+                         const int64_t* vstart, const int64_t* fstart) {
   if (!xy || !tri || nv < 3 || nt < 1) throw MeshError("empty mesh");
   if (nv > (1 << 24) || nt > (1 << 24)) throw MeshError("mesh too large");
   Mesh* mp = new Mesh();
@@ -205,9 +223,31 @@ Mesh* mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
       m.h_vedges.insert(m.h_vedges.end(), vedge[v].begin(), vedge[v].end());
       V.e_end = (int)m.h_vedges.size();
     }
-    int nfree0 = 0;
-    for (auto& V : m.h_verts) nfree0 += V.dirichlet ? 0 : 1;
-    if (nfree0 > 1024) throw MeshError("more than 1024 free macro-vertices (dense level-0 solve)");
+    // blocks: contiguous vertex / face ranges, closed under incidence
+    if (nblocks < 1 || vstart[0] != 0 || fstart[0] != 0 || vstart[nblocks] != nv || fstart[nblocks] != nt)
+      throw MeshError("bad block ranges");
+    m.h_blocks.resize(nblocks);
+    {
+      int e = 0;
+      for (int bk = 0; bk < nblocks; ++bk) {
+        Block& B = m.h_blocks[bk];
+        B.v0 = (int)vstart[bk];
+        B.v1 = (int)vstart[bk + 1];
+        B.f0 = (int)fstart[bk];
+        B.f1 = (int)fstart[bk + 1];
+        if (B.v1 <= B.v0 || B.f1 <= B.f0) throw MeshError("empty block");
+        for (int f = B.f0; f < B.f1; ++f)
+          for (int q = 0; q < 3; ++q)
+            if (m.h_faces[f].v[q] < B.v0 || m.h_faces[f].v[q] >= B.v1)
+              throw MeshError("face " + std::to_string(f) + " uses a vertex of another block");
+        B.e0 = e;
+        while (e < m.ne && m.h_edges[e].lo < B.v1) ++e;
+        B.e1 = e;
+        int nfree0 = 0;
+        for (int v = B.v0; v < B.v1; ++v) nfree0 += m.h_verts[v].dirichlet ? 0 : 1;
+        if (nfree0 > 1024) throw MeshError("more than 1024 free macro-vertices in one problem (dense level-0 solve)");
+      }
+    }
     // levels: sizes and edge colourings (host)
     int free_v = 0, free_e = 0;
     for (auto& V : m.h_verts) free_v += V.dirichlet ? 0 : 1;
@@ -246,12 +286,11 @@ Mesh* mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
       }
       // face sweep row blocks: about 1216 CTAs in total (8 per SM), at least
       // 48 rows per block so that the recomputed halo rows stay below 2 %
+      // (the autotuner may change this later)
       const int N = ld.lv.N;
       int per_face = (int)((1216 + m.nf / 2) / m.nf);
       per_face = std::max(1, std::min(per_face, (N + 1) / 48));
-      std::vector<int> tk = face_tasks(m.nf, N, per_face);
-      ld.n_face_tasks = (int)(tk.size() / 4);
-      ld.face_tasks = upload(m, tk);
+      set_face_tasks(m, l, per_face);
     }
     m.partials = (double*)dev_alloc(m, kMaxPartials * sizeof(double));
     m.scalars = (double*)dev_alloc(m, 16 * sizeof(double));
@@ -267,11 +306,23 @@ Mesh* mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
   return mp;
 }
 
-void mesh_destroy(Mesh* m) {
+void mesh_destroy_internal(Mesh* m) {
   if (!m) return;
   cudaDeviceSynchronize();
   for (void* p : m->allocations) cudaFree(p);
   delete m;
+}
+
+// Row blocks of the face sweep on one level (the split never changes results:
+// every point is updated from the same operands whichever CTA owns it).
+void set_face_tasks(Mesh& m, int level, int per_face) {
+  LevelData& ld = m.levels[level];
+  std::vector<int> tk = face_tasks(m.nf, ld.lv.N, per_face);
+  const size_t need = tk.size() * sizeof(int);
+  if (!ld.face_tasks || (size_t)ld.n_face_tasks * 4 * sizeof(int) < need) ld.face_tasks = (int*)dev_alloc(m, need);
+  check_cuda(cudaMemcpy(ld.face_tasks, tk.data(), need, cudaMemcpyHostToDevice), "face tasks");
+  ld.n_face_tasks = (int)(tk.size() / 4);
+  ld.face_tasks_per_face = per_face;
 }
 
 // Coefficient pyramid: finest level from the canonical element order, coarse

@@ -71,6 +71,14 @@ _SIGS = {
     "hhg_smooth": [_P, C.c_int32, C.c_int32, _P, _P, C.c_int32, C.c_int32, C.c_double, _P],
     "hhg_vcycle": [_P, C.c_int32, C.c_int32, _P, _P, C.POINTER(VcycleOpts), _P],
     "hhg_solve": [_P, C.c_int32, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveReport), _P],
+    "hhg_tune": [_P, C.c_int32, _P],
+    "hhg_batch_create": [C.c_int32, C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.c_int64),
+                         C.POINTER(C.POINTER(C.c_int32)), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                         C.POINTER(_P)],
+    "hhg_batch_destroy": [_P],
+    "hhg_batch_info": [_P, C.c_int32, C.POINTER(Info)],
+    "hhg_batch_tune": [_P, _P],
+    "hhg_batch_solve": [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(SolveOpts), C.POINTER(SolveReport), _P],
     "hhg_profile_begin": [C.c_uint32, C.c_int32],
     "hhg_profile_end": [C.POINTER(C.c_int64), C.POINTER(C.c_double)],
 }
@@ -208,6 +216,9 @@ class Mesh:
         _check(lib.hhg_smooth(self.h, level, prec, _ptr(x), _ptr(b), smoother, sweeps, omega,
                               _stream(stream)))
 
+    def tune(self, prec=F64, stream=None):
+        _check(lib.hhg_tune(self.h, prec, _stream(stream)))
+
     def vcycle(self, level, x, b, nu1=3, nu2=3, prec=F64, stream=None):
         o = VcycleOpts(nu1, nu2)
         _check(lib.hhg_vcycle(self.h, level, prec, _ptr(x), _ptr(b), C.byref(o), _stream(stream)))
@@ -222,6 +233,57 @@ class Mesh:
         out = {"iterations": rep.iterations, "status": rep.status, "r0": rep.r0,
                "r_final": rep.r_final,
                "history": [hist[i] for i in range(min(rep.iterations + 1, max_iter + 1))]}
+        if raise_on_error and st != OK:
+            raise HHGError(st, last_error())
+        return st, out
+
+
+class Batch:
+    """Independent problems solved together (see hhg_batch_create)."""
+
+    def __init__(self, meshes, levels):
+        n = len(meshes)
+        self._xy = [np.ascontiguousarray(m[0], dtype=np.float64) for m in meshes]
+        self._tri = [np.ascontiguousarray(m[1], dtype=np.int32) for m in meshes]
+        xy_p = (C.POINTER(C.c_double) * n)(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in self._xy])
+        tri_p = (C.POINTER(C.c_int32) * n)(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in self._tri])
+        nv = (C.c_int64 * n)(*[a.shape[0] for a in self._xy])
+        nt = (C.c_int64 * n)(*[a.shape[0] for a in self._tri])
+        lv = (C.c_int32 * n)(*[int(v) for v in levels])
+        h = _P()
+        _check(lib.hhg_batch_create(n, xy_p, nv, tri_p, nt, lv, C.byref(h)))
+        self.h, self.n = h, n
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.hhg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, p) -> Info:
+        out = Info()
+        _check(lib.hhg_batch_info(self.h, int(p), C.byref(out)))
+        return out
+
+    def tune(self, stream=None):
+        _check(lib.hhg_batch_tune(self.h, _stream(stream)))
+
+    def solve(self, xs, bs, mode=SOLVE_IR, nu1=3, nu2=3, tol=1e-10, max_iter=100, stream=None,
+              raise_on_error=True):
+        """xs, bs: per-problem device vectors in canonical order.  Returns
+        (status, list of per-problem report dicts)."""
+        n = self.n
+        xp = (_P * n)(*[_ptr(v) for v in xs])
+        bp = (_P * n)(*[_ptr(v) for v in bs])
+        o = SolveOpts(mode, nu1, nu2, max_iter, tol)
+        reps = (SolveReport * n)()
+        st = lib.hhg_batch_solve(self.h, xp, bp, C.byref(o), reps, _stream(stream))
+        out = [{"iterations": r.iterations, "status": r.status, "r0": r.r0, "r_final": r.r_final} for r in reps]
         if raise_on_error and st != OK:
             raise HHGError(st, last_error())
         return st, out

@@ -60,3 +60,17 @@ def test_invalid_meshes_rejected_on_host():
         hhg.Mesh(xy, np.array([[0, 1, 2]]), 0)
     assert e.value.status == hhg.ERR_ARG
     assert "max_level" in hhg.last_error()
+
+
+def test_invalid_batch_rejected_on_host():
+    _lib_path()
+    from paper_1805_10167_gb300 import hhg, inputs
+    good = inputs.unit_square_mesh()
+    bad = (good[0], np.array([[0, 1, 42]]))
+    with pytest.raises(hhg.HHGError) as e:
+        hhg.Batch([good, bad], [2, 3])
+    assert e.value.status == hhg.ERR_MESH
+    assert "problem 1" in hhg.last_error()
+    with pytest.raises(hhg.HHGError) as e:
+        hhg.Batch([good], [11])
+    assert e.value.status == hhg.ERR_ARG
