@@ -109,6 +109,7 @@ struct Batch {
   std::vector<BatchProb> probs;
   std::vector<BatchGroup> groups;
   cudaEvent_t fork = nullptr;
+  cudaStream_t capture = nullptr;   // graphs are captured here (the legacy stream cannot capture)
   cudaGraphExec_t graph = nullptr;
   int graph_mode = -1, graph_nu1 = -1, graph_nu2 = -1;
   double* h_norms = nullptr;   // pinned: squared norms of all problems, group-major
@@ -190,6 +191,7 @@ Batch* batch_create(int n, const double* const* xy, const int64_t* nv, const int
       B->groups.push_back(g);
     }
     check_cuda(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming), "event");
+    check_cuda(cudaStreamCreateWithFlags(&B->capture, cudaStreamNonBlocking), "stream");
     int off = 0;
     for (auto& g : B->groups) {
       B->norm_off.push_back(off);
@@ -222,6 +224,7 @@ void batch_destroy(Batch* B) {
     cudaFree(g.norms);
   }
   if (B->fork) cudaEventDestroy(B->fork);
+  if (B->capture) cudaStreamDestroy(B->capture);
   if (B->h_norms) cudaFreeHost(B->h_norms);
   delete B;
 }
@@ -355,9 +358,9 @@ void batch_solve(Batch& B, double* const* x, const double* const* b, const hhg_s
     } else {
       if (!B.graph) {
         cudaGraph_t graph;
-        check_cuda(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
-        fork_join(B, st, o.mode, o.nu1, o.nu2, true);
-        check_cuda(cudaStreamEndCapture(st, &graph), "end capture");
+        check_cuda(cudaStreamBeginCapture(B.capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+        fork_join(B, B.capture, o.mode, o.nu1, o.nu2, true);
+        check_cuda(cudaStreamEndCapture(B.capture, &graph), "end capture");
         check_cuda(cudaGraphInstantiate(&B.graph, graph, 0), "instantiate");
         cudaGraphDestroy(graph);
         B.graph_mode = o.mode;

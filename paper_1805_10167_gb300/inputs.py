@@ -9,7 +9,7 @@ macro meshes, random right-hand sides and random coefficient fields.
   n_ang x n_rad quads, each split along its (i,j)-(i+1,j+1) diagonal.  Its
   shape follows the annulus of the paper's energy-transport example (Sec. 5.2).
 * ``random_square_mesh``: a seeded random valid triangulation of the unit
-  square (point insertion, boundary splits, Lawson flips with a min-angle test).
+  square (point insertion, boundary splits, Lawson flips to Delaunay).
 * ``splitmix64`` / ``uniform_pm1``: Vigna's SplitMix64 counter generator and
   its map to uniform doubles in [-1, 1); the value for canonical DoF p is drawn
   from ``splitmix64(seed ^ p)``.
@@ -84,10 +84,13 @@ def _min_angle(p, q, r):
 def random_square_mesh(seed: int, n_faces: int):
     """Seeded random valid triangulation of the unit square with n_faces >= 2
     triangles: start from the square cut by one diagonal; repeat interior point
-    insertion (+2 faces; barycentric weights drawn from [0.2, 0.6] and
-    normalised) or a boundary-edge split at t in [0.3, 0.7] (+1 face) until the
-    count is reached; then up to n_faces random Lawson flips, each kept only if
-    both new triangles have a minimum angle of at least 20 degrees."""
+    insertion into one of the three largest faces (+2 faces; barycentric
+    weights drawn from [0.2, 0.6] and normalised) or a split of one of the two
+    longest boundary edges at t in [0.3, 0.7] (+1 face) until the count is
+    reached; then Lawson flips until the triangulation is Delaunay (every
+    interior edge's two opposite angles sum to at most pi), and eight rounds
+    of Laplacian smoothing of the interior points (moves that would flip or
+    collapse a triangle are skipped), each followed by Delaunay flips."""
     if n_faces < 2:
         raise ValueError("n_faces must be >= 2")
     rng = np.random.default_rng(seed)
@@ -105,7 +108,13 @@ def random_square_mesh(seed: int, n_faces: int):
     while len(tris) < n_faces:
         need = n_faces - len(tris)
         if need >= 2 and rng.random() < 0.6:
-            f = int(rng.integers(len(tris)))
+            # one of the three largest faces, near its centroid
+            areas = []
+            for t in tris:
+                p0, p1, p2 = pts[t[0]], pts[t[1]], pts[t[2]]
+                areas.append(abs((p1[0] - p0[0]) * (p2[1] - p0[1]) - (p1[1] - p0[1]) * (p2[0] - p0[0])))
+            order = np.argsort(areas)[::-1]
+            f = int(order[int(rng.integers(min(3, len(order))))])
             w = rng.uniform(0.2, 0.6, size=3)
             w /= w.sum()
             a, b, c = tris[f]
@@ -118,7 +127,9 @@ def random_square_mesh(seed: int, n_faces: int):
         else:
             em = edge_faces()
             bnd = [e for e, fs in em.items() if len(fs) == 1]
-            e = bnd[int(rng.integers(len(bnd)))]
+            lens = [np.linalg.norm(pts[a] - pts[b]) for a, b in bnd]
+            order = np.argsort(lens)[::-1]
+            e = bnd[int(order[int(rng.integers(min(2, len(order))))])]   # one of the two longest
             f = em[e][0]
             t = rng.uniform(0.3, 0.7)
             a, b = e
@@ -133,30 +144,72 @@ def random_square_mesh(seed: int, n_faces: int):
                     break
             tris[f] = [u, n, w_]
             tris.append([n, v, w_])
-    for _ in range(n_faces):
+    # Lawson flips to the Delaunay triangulation of the points: an interior
+    # edge is flipped while the two angles opposite to it sum to more than pi
+    def opp_angle(t, e):
+        c = [v for v in t if v not in e][0]
+        u, w = pts[e[0]] - pts[c], pts[e[1]] - pts[c]
+        return np.arccos(np.clip(np.dot(u, w) / (np.linalg.norm(u) * np.linalg.norm(w)), -1.0, 1.0))
+    for _ in range(50 * n_faces):
         em = edge_faces()
-        inner = [e for e, fs in em.items() if len(fs) == 2]
-        if not inner:
+        flipped = False
+        for e, fs in em.items():
+            if len(fs) != 2:
+                continue
+            f1, f2 = fs
+            if opp_angle(tris[f1], e) + opp_angle(tris[f2], e) <= np.pi + 1e-12:
+                continue
+            a, b = e
+            c = [v for v in tris[f1] if v not in e][0]
+            d = [v for v in tris[f2] if v not in e][0]
+            tris[f1], tris[f2] = [c, d, a], [d, c, b]
+            flipped = True
             break
-        e = inner[int(rng.integers(len(inner)))]
-        f1, f2 = em[e]
-        a, b = e
-        c = [v for v in tris[f1] if v not in e][0]
-        d = [v for v in tris[f2] if v not in e][0]
-        t1, t2 = [c, d, a], [d, c, b]
-        P = lambda t: [pts[v] for v in t]
+        if not flipped:
+            break
+    def delaunay():
+        for _ in range(50 * n_faces):
+            em = edge_faces()
+            flipped = False
+            for e, fs in em.items():
+                if len(fs) != 2:
+                    continue
+                f1, f2 = fs
+                if opp_angle(tris[f1], e) + opp_angle(tris[f2], e) <= np.pi + 1e-12:
+                    continue
+                a, b = e
+                c = [v for v in tris[f1] if v not in e][0]
+                d = [v for v in tris[f2] if v not in e][0]
+                tris[f1], tris[f2] = [c, d, a], [d, c, b]
+                flipped = True
+                break
+            if not flipped:
+                return
 
-        def area2(t):
-            p, q, r = P(t)
-            return (q[0] - p[0]) * (r[1] - p[1]) - (q[1] - p[1]) * (r[0] - p[0])
-        if abs(area2(t1)) < 1e-12 or abs(area2(t2)) < 1e-12:
-            continue
-        # the flip is valid only if the quad a,c,b,d is convex: the new
-        # triangles then have opposite orientations relative to segment cd
-        if np.sign(area2([c, d, a])) == np.sign(area2([c, d, b])):
-            continue
-        if _min_angle(*P(t1)) >= 20.0 and _min_angle(*P(t2)) >= 20.0:
-            tris[f1], tris[f2] = t1, t2
+    def signed_area(t):
+        p0, p1, p2 = pts[t[0]], pts[t[1]], pts[t[2]]
+        return (p1[0] - p0[0]) * (p2[1] - p0[1]) - (p1[1] - p0[1]) * (p2[0] - p0[0])
+    # Laplacian smoothing of the interior points (a move is kept only if no
+    # incident triangle flips or collapses), then Delaunay flips again
+    for _ in range(8):
+        em = edge_faces()
+        on_bnd = set()
+        nbrs = {}
+        for (a, b), fs in em.items():
+            if len(fs) == 1:
+                on_bnd.update((a, b))
+            nbrs.setdefault(a, set()).add(b)
+            nbrs.setdefault(b, set()).add(a)
+        for v in range(4, len(pts)):
+            if v in on_bnd or v not in nbrs:
+                continue
+            inc = [t for t in tris if v in t]
+            sign = [np.sign(signed_area(t)) for t in inc]
+            old = pts[v].copy()
+            pts[v] = np.mean([pts[u] for u in nbrs[v]], axis=0)
+            if any(np.sign(signed_area(t)) != s0 or abs(signed_area(t)) < 1e-9 for t, s0 in zip(inc, sign)):
+                pts[v] = old
+        delaunay()
     xy = np.array(pts, dtype=np.float64)
     return xy, _ccw(xy, np.array(tris))
 
