@@ -266,3 +266,21 @@ def grf_coefficient(points: np.ndarray, seed: int = 42, length: float = 0.1,
         pr = points[s:s + step] @ w.T + phi[None, :]
         out[s:s + step] = sigma * np.sqrt(2.0 / n_features) * np.cos(pr).sum(axis=1)
     return np.exp(out)
+
+
+def batch_workload(n: int = 64, seed0: int = 1000, min_level: int = 6, max_level: int = 9):
+    """n independent problems: problem k uses seed s = seed0 + k, a random
+    triangulation of the unit square with 2 + (splitmix64(s) mod 63) faces
+    and level min_level + (splitmix64(s ^ 0x5bd1e995) mod (max_level -
+    min_level + 1)).  Returns [(xy, tri, level)]."""
+    out = []
+    span = max_level - min_level + 1
+    for k in range(n):
+        s = seed0 + k
+        h1 = int(splitmix64(np.array([s], dtype=np.uint64))[0])
+        h2 = int(splitmix64(np.array([s ^ 0x5BD1E995], dtype=np.uint64))[0])
+        nf = 2 + h1 % 63
+        L = min_level + h2 % span
+        xy, tri = random_square_mesh(s, nf)
+        out.append((xy, tri, L))
+    return out
