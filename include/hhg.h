@@ -90,14 +90,24 @@ typedef struct {
 
 typedef enum {
   HHG_SOLVE_MG = 0,       /* V-cycles in the precision of x (FP64)          */
-  HHG_SOLVE_IR = 1        /* FP32 V-cycle inside FP64 iterative refinement  */
+  HHG_SOLVE_IR = 1,       /* FP32 V-cycle inside FP64 iterative refinement  */
+  HHG_SOLVE_FGMRES = 2    /* FGMRES(restart), FP64, preconditioned by one   */
+                          /* FP32 V-cycle (Sec. 4.3: MG as preconditioner)  */
 } hhg_solve_mode;
+
+typedef enum {
+  HHG_SMOOTH_GS = 0,      /* three-colour Gauss-Seidel                       */
+  HHG_SMOOTH_LEARNED = 1  /* learned CNN step (hhg_learned_*), with GS on    */
+                          /* vertex/edge unknowns and on levels with N < 8   */
+} hhg_smoother_kind;
 
 typedef struct {
   int32_t mode;           /* hhg_solve_mode                                  */
   int32_t nu1, nu2;       /* V(nu1, nu2)                                     */
-  int32_t max_iter;       /* cycles / outer iterations, default 100          */
+  int32_t max_iter;       /* cycles / outer iterations / Krylov steps (100)  */
   double tol;             /* stop at ||r|| <= tol ||r0||, default 1e-10       */
+  int32_t smoother;       /* FGMRES preconditioner smoother (hhg_smoother_kind) */
+  int32_t restart;        /* FGMRES restart length, default 20               */
 } hhg_solve_opts;
 
 typedef struct {
@@ -107,6 +117,8 @@ typedef struct {
   double r_final;         /* final residual norm                             */
   double* history;        /* optional HOST array: residual norm per cycle    */
   int32_t history_cap;    /* its capacity (entries written: min(cap, it+1))   */
+  int32_t smoother_used;  /* FGMRES: smoother kept by the judge (learned ->  */
+                          /* GS when the CNN reduced the residual less)      */
 } hhg_solve_report;
 
 /* Build the macro-primitive graph (Sec. 2.1), the level hierarchy 0..max_level
@@ -264,6 +276,45 @@ typedef enum {
 } hhg_kernel_class;
 hhg_status hhg_profile_begin(uint32_t mask, int32_t level);
 hhg_status hhg_profile_end(int64_t* launches, double* ms);
+
+/* Learned smoother (not in the paper; an extension of its multigrid,
+ * Sec. 4.3): a CNN per macro-face lattice, conv3x3 3->16, ReLU, conv3x3
+ * 16->16, ReLU, conv3x3 16->1, inputs [(b - A x)/A_pp, log k_up, log k_down],
+ * zero padding outside the closed triangle, output added to the face-interior
+ * unknowns (x += d); BF16 weights and activations, FP32 accumulation.  The
+ * weights are HHG_LEARNED_NPARAMS FP32 values in the order W1 (16,3,3,3),
+ * b1, W2 (16,16,3,3), b2, W3 (1,16,3,3), b3, row-major; W[o][c][dj+1][di+1]
+ * multiplies input channel c at lattice offset (di, dj).  One network per
+ * mesh; its weights are copied to a process-wide constant bank before each
+ * use, so two meshes must not run the learned smoother concurrently. */
+#define HHG_LEARNED_NPARAMS 2913
+hhg_status hhg_learned_set_weights(hhg_mesh mesh, const float* w_host, int64_t n);
+hhg_status hhg_learned_get_weights(hhg_mesh mesh, float* w_host, int64_t n);
+/* d = CNN(s) on every face of `level`: s is an FP32 level vector holding the
+ * scaled residual with its ghost copies; d (FP32 level vector, may be NULL)
+ * receives the output at face-interior slots; x (prec, may be NULL) gets
+ * x += d there. */
+hhg_status hhg_learned_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const float* s,
+                             void* x, float* d, void* stream);
+/* Mean relative loss ||d - e||^2/||e||^2 and its gradient w.r.t. the weights
+ * over n_crops 64 x 64 crops: X (n_crops, 3, 64, 64) and E (n_crops, 64, 64)
+ * FP32 DEVICE arrays, crops_host: 4 ints per crop (face, i0, j0, N) placing
+ * crop pixel (ci, cj) at lattice point (i0 + ci, j0 + cj) of a face with N
+ * intervals; the loss counts face-interior pixels at least 3 away from the
+ * crop border.  grad_host: HHG_LEARNED_NPARAMS floats.  Synchronous. */
+hhg_status hhg_learned_grad(hhg_mesh mesh, int32_t n_crops, const float* X, const float* E,
+                            const int32_t* crops_host, float* grad_host, float* loss_host,
+                            void* stream);
+/* Generates n_pairs training crops on `level` (level >= 6) from FP64
+ * V(3,3) iterates x_k, k = 1..6, of random starts against x* (solved to
+ * 1e-12 for a random right-hand side) -- inputs from b - A x_k, target
+ * e = x* - x_k -- and trains the network for `epochs` passes with Adam
+ * (lr, beta 0.9 / 0.999, mini-batches of `batch` crops; weights initialised
+ * from `seed` unless already set).  loss_history_host (may be NULL) gets the
+ * mean loss of each epoch.  Synchronous. */
+hhg_status hhg_learned_train(hhg_mesh mesh, int32_t level, int32_t n_pairs, int32_t epochs,
+                             int32_t batch, float lr, uint64_t seed, float* loss_history_host,
+                             void* stream);
 
 /* Message of the last failed call on this thread ('\0'-terminated, truncated
  * to n bytes).  Returns the full message length. */

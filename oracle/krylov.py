@@ -1,0 +1,69 @@
+"""Flexible GMRES (oracle, FP64).  Paper Sec. 4.3: multigrid can be used as a
+preconditioner inside a Krylov solver.  FGMRES(m) after Saad (1993): right
+preconditioning with a preconditioner that may change from step to step,
+modified Gram-Schmidt, Givens rotations, restart after m steps.  Vectors are
+full-length; inner products run over the free DoFs only (Dirichlet entries
+of the Krylov vectors are zero).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def fgmres(apply_A, precond, b, x0, free, m=20, tol=1e-10, max_iter=200, history=None):
+    """Solve A x = b from x0.  apply_A(v) -> A v (zero Dirichlet rows);
+    precond(v, j) -> z_j (the j-th preconditioner application).  Stops when
+    ||b - A x|| <= tol ||b - A x0||.  Returns (x, residual history, steps)."""
+    x = x0.copy()
+    dot = lambda u, v: float(np.dot(u[free], v[free]))
+    r = b - apply_A(x)
+    r[~free] = 0.0
+    r0 = np.sqrt(dot(r, r))
+    hist = [r0] if history is None else history
+    if history is not None:
+        hist.append(r0)
+    steps = 0
+    beta = r0
+    while beta > tol * r0 and steps < max_iter:
+        V = [r / beta]
+        Z = []
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        k = 0
+        for j in range(m):
+            z = precond(V[j], steps)
+            z[~free] = 0.0
+            Z.append(z)
+            w = apply_A(z)
+            w[~free] = 0.0
+            for i in range(j + 1):
+                H[i, j] = dot(w, V[i])
+                w = w - H[i, j] * V[i]
+            h_next = np.sqrt(dot(w, w))
+            H[j + 1, j] = h_next
+            for i in range(j):                   # previous rotations
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            steps += 1
+            k = j + 1
+            hist.append(abs(g[j + 1]))
+            if abs(g[j + 1]) <= tol * r0 or steps >= max_iter or h_next == 0.0:
+                break
+            V.append(w / h_next)
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        for i in range(k):
+            x = x + y[i] * Z[i]
+        r = b - apply_A(x)
+        r[~free] = 0.0
+        beta = np.sqrt(dot(r, r))
+        hist[-1] = beta
+    return x, hist, steps

@@ -265,12 +265,12 @@ static void group_iteration(const BatchGroup& g, int mode, int nu1, int nu2) {
   double* b = (double*)ld.b[0];
   if (mode == HHG_SOLVE_IR) {
     zero_vec(m, L, 1, ld.x[1], g.st);
-    vcycle_run(m, L, 1, ld.x[1], ld.b[1], nu1, nu2, g.st);
+    vcycle_run(m, L, 1, ld.x[1], ld.b[1], nu1, nu2, 0, g.st);
     update_f64_from_f32(m, L, x, (const float*)ld.x[1], g.st);
     residual_op(m, L, 0, x, b, ld.r[0], nullptr, g.st);
     block_norms2(m, L, (const double*)ld.r[0], (float*)ld.b[1], g.norms, g.st);
   } else {
-    vcycle_run(m, L, 0, x, b, nu1, nu2, g.st);
+    vcycle_run(m, L, 0, x, b, nu1, nu2, 0, g.st);
     residual_op(m, L, 0, x, b, ld.r[0], nullptr, g.st);
     block_norms2(m, L, (const double*)ld.r[0], nullptr, g.norms, g.st);
   }

@@ -103,25 +103,34 @@ namespace hhg {
 // consistent on entry and on exit.  Smoothing sweeps alternate between x and
 // the level's workspace w; an odd sweep count ends with a copy back to x.
 void vcycle_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2,
-                cudaStream_t st) {
+                int smoother, cudaStream_t st) {
   if (l == 0) {
     coarse_solve(m, prec, b, x, st);
     return;
   }
   const LevelData& ld = m.levels[l];
   const LevelData& lc = m.levels[l - 1];
+  const bool learned = smoother == 1 && ld.lv.N >= 8;
   void* cur = x;
   void* oth = ld.w[prec];
   for (int s = 0; s < nu1; ++s) {
+    if (learned) {
+      learned_step(m, l, prec, cur, b, st);
+      continue;
+    }
     gs_sweep(m, l, prec, cur, oth, b, true, st);
     std::swap(cur, oth);
   }
   residual_op(m, l, prec, cur, b, ld.r[prec], nullptr, st);
   restrict_op(m, l, prec, ld.r[prec], lc.b[prec], st);
   zero_vec(m, l - 1, prec, lc.x[prec], st);
-  vcycle_run(m, l - 1, prec, lc.x[prec], lc.b[prec], nu1, nu2, st);
+  vcycle_run(m, l - 1, prec, lc.x[prec], lc.b[prec], nu1, nu2, smoother, st);
   prolongate_add(m, l, prec, lc.x[prec], cur, st);
   for (int s = 0; s < nu2; ++s) {
+    if (learned) {
+      learned_step(m, l, prec, cur, b, st);
+      continue;
+    }
     gs_sweep(m, l, prec, cur, oth, b, false, st);
     std::swap(cur, oth);
   }
@@ -355,7 +364,7 @@ hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
     const int nu1 = opts ? opts->nu1 : 3, nu2 = opts ? opts->nu2 : 3;
     if (nu1 < 0 || nu2 < 0) throw ArgError("negative sweep count");
     hhg::ghost_fill(m, level, prec, x, S(stream));
-    hhg::vcycle_run(m, level, prec, x, b, nu1, nu2, S(stream));
+    hhg::vcycle_run(m, level, prec, x, b, nu1, nu2, 0, S(stream));
     return HHG_OK;
   });
 }
@@ -367,10 +376,17 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
     check_level(m, level);
     need_vec(x, "x");
     need_vec(b, "b");
-    hhg_solve_opts o{HHG_SOLVE_MG, 3, 3, 100, 1e-10};
+    hhg_solve_opts o{HHG_SOLVE_MG, 3, 3, 100, 1e-10, HHG_SMOOTH_GS, 20};
     if (opts) o = *opts;
     if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 0 || !(o.tol >= 0.0)) throw ArgError("bad solve options");
-    if (o.mode != HHG_SOLVE_MG && o.mode != HHG_SOLVE_IR) throw ArgError("bad solve mode");
+    if (o.mode != HHG_SOLVE_MG && o.mode != HHG_SOLVE_IR && o.mode != HHG_SOLVE_FGMRES)
+      throw ArgError("bad solve mode");
+    if (o.mode == HHG_SOLVE_FGMRES) {
+      int used = 0;
+      hhg::fgmres_solve(m, level, x, b, o, o.smoother, o.restart > 0 ? o.restart : 20, rep, &used, S(stream));
+      if (rep) rep->smoother_used = used;
+      return HHG_OK;
+    }
     cudaStream_t st = S(stream);
     const hhg::LevelData& ld = m.levels[level];
     double* nrm = m.scalars;
@@ -397,11 +413,11 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
       if (o.mode == HHG_SOLVE_IR) {
         // inner FP32 V-cycle on A d = r from d = 0, then x += d in FP64
         hhg::zero_vec(m, level, 1, ld.x[1], st);
-        hhg::vcycle_run(m, level, 1, ld.x[1], ld.b[1], o.nu1, o.nu2, st);
+        hhg::vcycle_run(m, level, 1, ld.x[1], ld.b[1], o.nu1, o.nu2, 0, st);
         hhg::update_f64_from_f32(m, level, x, (const float*)ld.x[1], st);
         hhg::residual_f64_to_f32(m, level, x, b, (float*)ld.b[1], nrm, st);
       } else {
-        hhg::vcycle_run(m, level, 0, x, b, o.nu1, o.nu2, st);
+        hhg::vcycle_run(m, level, 0, x, b, o.nu1, o.nu2, 0, st);
         hhg::residual_op(m, level, 0, x, b, ld.r[0], nrm, st);
       }
       ++it;
@@ -411,6 +427,7 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
     }
     if (device_timed_out(m, st)) status = HHG_ERR_TIMEOUT;
     if (rep) {
+      rep->smoother_used = HHG_SMOOTH_GS;
       rep->iterations = it;
       rep->status = status;
       rep->r0 = r0;
@@ -476,11 +493,74 @@ hhg_status hhg_batch_solve(hhg_batch batch, double* const* x, const double* cons
     if (!batch || !batch->b) throw ArgError("NULL batch");
     need(x, "x");
     need(b, "b");
-    hhg_solve_opts o{HHG_SOLVE_IR, 3, 3, 100, 1e-10};
+    hhg_solve_opts o{HHG_SOLVE_IR, 3, 3, 100, 1e-10, HHG_SMOOTH_GS, 20};
     if (opts) o = *opts;
     if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 0 || !(o.tol >= 0.0)) throw ArgError("bad solve options");
     if (o.mode != HHG_SOLVE_MG && o.mode != HHG_SOLVE_IR) throw ArgError("bad solve mode");
     hhg::batch_solve(*batch->b, x, b, o, reps, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_learned_set_weights(hhg_mesh mesh, const float* w_host, int64_t n) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    need(w_host, "w_host");
+    if (n != HHG_LEARNED_NPARAMS) throw ArgError("expected HHG_LEARNED_NPARAMS weights");
+    hhg::learned_set_weights(m, w_host, nullptr);
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_learned_get_weights(hhg_mesh mesh, float* w_host, int64_t n) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    need(w_host, "w_host");
+    if (n != HHG_LEARNED_NPARAMS) throw ArgError("expected HHG_LEARNED_NPARAMS weights");
+    if (!hhg::learned_ready(m)) throw ArgError("no weights set or trained");
+    hhg::learned_get_weights(m, w_host);
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_learned_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const float* s,
+                             void* x, float* d, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level, 1);
+    check_prec(prec);
+    need_vec(s, "s");
+    if (!hhg::learned_ready(m)) throw ArgError("no weights set or trained");
+    hhg::learned_apply(m, level, prec, s, x, d, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_learned_grad(hhg_mesh mesh, int32_t n_crops, const float* X, const float* E,
+                            const int32_t* crops_host, float* grad_host, float* loss_host,
+                            void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    need(X, "X");
+    need(E, "E");
+    need(crops_host, "crops_host");
+    need(grad_host, "grad_host");
+    need(loss_host, "loss_host");
+    if (n_crops < 1) throw ArgError("n_crops < 1");
+    if (!hhg::learned_ready(m)) throw ArgError("no weights set or trained");
+    hhg::learned_grad(m, n_crops, X, E, crops_host, grad_host, loss_host, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_learned_train(hhg_mesh mesh, int32_t level, int32_t n_pairs, int32_t epochs,
+                             int32_t batch, float lr, uint64_t seed, float* loss_history_host,
+                             void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level, 6);
+    if (n_pairs < batch || batch < 1 || epochs < 0 || !(lr > 0.f)) throw ArgError("bad training arguments");
+    hhg::learned_train(m, level, n_pairs, epochs, batch, lr, seed, loss_history_host, S(stream));
     return HHG_OK;
   });
 }

@@ -166,8 +166,13 @@ struct LevelData {
   int face_tasks_per_face = 0;
 };
 
+struct Learned;
+struct KrylovSpace;
+
 struct Mesh {
   int nv = 0, ne = 0, nf = 0, max_level = 0;
+  Learned* learned = nullptr;       // learned-smoother weights and optimiser state
+  KrylovSpace* krylov = nullptr;    // FGMRES basis vectors
   std::vector<FaceRec> h_faces;
   std::vector<EdgeRec> h_edges;
   std::vector<VertRec> h_verts;
@@ -230,6 +235,9 @@ void convert_k_to_f32(const Mesh& m, int level, cudaStream_t st);
 void sqrt_scalar(double* v, cudaStream_t st);
 void dot_noalloc(const Mesh& m, int level, int prec, const void* x1, const void* x2,
                  double* out_dev, cudaStream_t st);
+void scaled_residual(const Mesh& m, int level, int prec, const void* x, const void* b, float* s,
+                     cudaStream_t st);
+void ve_gs(const Mesh& m, int level, int prec, void* x, const void* b, bool forward, cudaStream_t st);
 // mixed precision helpers for iterative refinement
 void residual_f64_to_f32(const Mesh& m, int level, const double* x, const double* b, float* r32,
                          double* norm2_dev, cudaStream_t st);
@@ -250,8 +258,25 @@ void mesh_destroy_internal(Mesh* m);
 void set_coefficient(Mesh& m, const double* k_dev, cudaStream_t st);
 // One V(nu1, nu2) cycle on level l (x, b in precision prec); ghost copies of
 // x consistent on entry and on exit.
+// smoother: 0 = three-colour Gauss-Seidel, 1 = learned CNN step (levels with
+// N >= 8; Gauss-Seidel below).
 void vcycle_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2,
-                cudaStream_t st);
+                int smoother, cudaStream_t st);
+// learned smoother and FGMRES
+bool learned_ready(const Mesh& m);
+void learned_free(Mesh& m);
+void learned_set_weights(Mesh& m, const float* w_host, cudaStream_t st);
+void learned_get_weights(Mesh& m, float* w_host);
+void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, float* delta, cudaStream_t st);
+void learned_step(const Mesh& m, int level, int prec, void* x, const void* b, cudaStream_t st);
+void learned_grad(Mesh& m, int B, const float* X_dev, const float* E_dev, const int* crops_host,
+                  float* grad_host, float* loss_host, cudaStream_t st);
+void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr, uint64_t seed,
+                   float* loss_hist, cudaStream_t st);
+void krylov_free(Mesh& m);
+void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts& o, int smoother,
+                  int restart, hhg_solve_report* rep, int* smoother_used, cudaStream_t st);
+void zero_dirichlet_and_ghosts(const Mesh& m, int level, double* x, cudaStream_t st);
 
 struct Batch;
 Batch* batch_create(int n, const double* const* xy, const int64_t* nv, const int32_t* const* tri,

@@ -14,7 +14,7 @@
 
 namespace hhg {
 
-enum Mode { APPLY = 0, RESID = 1, GS = 2, JAC = 3 };
+enum Mode { APPLY = 0, RESID = 1, GS = 2, JAC = 3, SRES = 4 };   // SRES: (b - A x) / A_pp
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -100,13 +100,15 @@ __global__ void k_vertex(MeshTables M, LevelView L, const T* __restrict__ x, TO*
     const VertRec V = M.verts[v];
     const int64_t s = L.v_off + v;
     if (V.dirichlet) {
-      if (MODE == APPLY || MODE == RESID) out[s] = TO(0);
+      if (MODE == APPLY || MODE == RESID || MODE == SRES) out[s] = TO(0);
       if (MODE == JAC) out[s] = (TO)x[s];
       continue;
     }
     T off, diag;
     vertex_row<T, VARK>(M, L, V, x, k, off, diag);
-    if (MODE == APPLY) {
+    if (MODE == SRES) {
+      out[s] = (TO)((b[s] - (diag * x[s] + off)) / diag);
+    } else if (MODE == APPLY) {
       out[s] = (TO)(diag * x[s] + off);
     } else if (MODE == RESID) {
       const T r = b[s] - (diag * x[s] + off);
@@ -155,13 +157,15 @@ __global__ void k_edge(MeshTables M, LevelView L, const int* __restrict__ list, 
     const EdgeRec E = M.edges[e];
     const int64_t s = L.e_off + (int64_t)e * L.ES + t;
     if (E.dirichlet) {
-      if (MODE == APPLY || MODE == RESID) out[s] = TO(0);
+      if (MODE == APPLY || MODE == RESID || MODE == SRES) out[s] = TO(0);
       if (MODE == JAC) out[s] = (TO)x[s];
       continue;
     }
     T off, diag;
     edge_row<T, VARK>(M, L, E, t, x, k, off, diag);
-    if (MODE == APPLY) {
+    if (MODE == SRES) {
+      out[s] = (TO)((b[s] - (diag * x[s] + off)) / diag);
+    } else if (MODE == APPLY) {
       out[s] = (TO)(diag * x[s] + off);
     } else if (MODE == RESID) {
       const T r = b[s] - (diag * x[s] + off);
@@ -214,7 +218,9 @@ __global__ void k_face(MeshTables M, LevelView L, const T* __restrict__ x, TO* o
       const int64_t p = (int64_t)j * L.S + i;
       T off, diag;
       face_row<T, VARK>(c0, c1, c2, L.S, xf, ku, kd, p, off, diag);
-      if (MODE == APPLY) {
+      if (MODE == SRES) {
+        out[fb + p] = (TO)((b[fb + p] - (diag * xf[p] + off)) / diag);
+      } else if (MODE == APPLY) {
         out[fb + p] = (TO)(diag * xf[p] + off);
       } else if (MODE == RESID) {
         const T r = b[fb + p] - (diag * xf[p] + off);
@@ -644,6 +650,14 @@ void residual_op(const Mesh& m, int level, int prec, const void* x, const void* 
   }
 }
 
+// s = (b - A x) / diag(A) at owned unknowns (0 at Dirichlet), ghost copies filled.
+void scaled_residual(const Mesh& m, int level, int prec, const void* x, const void* b, float* s,
+                     cudaStream_t st) {
+  if (prec == 0) rows_dispatch<double, float, SRES>(m, level, (const double*)x, s, (const double*)b, nullptr, 0.0, st);
+  else rows_dispatch<float, float, SRES>(m, level, (const float*)x, s, (const float*)b, nullptr, 0.0, st);
+  ghost_fill(m, level, 1, s, st);
+}
+
 void residual_f64_to_f32(const Mesh& m, int level, const double* x, const double* b, float* r32,
                          double* norm2_dev, cudaStream_t st) {
   const int used = rows_dispatch<double, float, RESID>(m, level, x, r32, b, m.partials, 0.0, st);
@@ -679,8 +693,8 @@ static void ve_gs_t(const Mesh& m, int level, T* x, const T* b, bool forward, cu
   }
 }
 
-static void ve_gs(const Mesh& m, int level, int prec, void* x, const void* b, bool forward,
-                  cudaStream_t st) {
+void ve_gs(const Mesh& m, int level, int prec, void* x, const void* b, bool forward,
+           cudaStream_t st) {
   if (prec == 0) {
     if (m.vark) ve_gs_t<double, true>(m, level, (double*)x, (const double*)b, forward, st);
     else ve_gs_t<double, false>(m, level, (double*)x, (const double*)b, forward, st);
@@ -815,6 +829,28 @@ void block_norms2(const Mesh& m, int level, const double* r64, float* r32, doubl
   dim3 grid(per, nb);
   HHG_LAUNCH(HHG_K_OTHER, level, st, "block norms", k_block_norms2<<<grid, kThreads, 0, st>>>(m.tab, L, m.blocks, r64, r32, m.partials));
   HHG_LAUNCH(HHG_K_OTHER, level, st, "block sums", k_block_sums<<<nb, kThreads, 0, st>>>(m.partials, per, out));
+}
+
+__global__ void k_zero_dirichlet(MeshTables M, LevelView L, double* x) {
+  const int64_t nE = (int64_t)M.ne * (L.N + 1);
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < M.nv + nE;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    if (idx < M.nv) {
+      if (M.verts[idx].dirichlet) x[L.v_off + idx] = 0.0;
+    } else {
+      const int64_t q = idx - M.nv;
+      const int64_t e = q / (L.N + 1);
+      if (M.edges[e].dirichlet) x[L.e_off + e * L.ES + (q - e * (L.N + 1))] = 0.0;
+    }
+  }
+}
+
+// Dirichlet entries of x set to 0, then ghost copies refreshed.
+void zero_dirichlet_and_ghosts(const Mesh& m, int level, double* x, cudaStream_t st) {
+  const LevelView& L = m.levels[level].lv;
+  const int64_t n = m.nv + (int64_t)m.ne * (L.N + 1);
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "zero dirichlet", k_zero_dirichlet<<<blocks_for(n, kThreads, 1024), kThreads, 0, st>>>(m.tab, L, x));
+  ghost_fill(m, level, 0, x, st);
 }
 
 void zero_vec(const Mesh& m, int level, int prec, void* v, cudaStream_t st) {

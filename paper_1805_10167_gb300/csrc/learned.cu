@@ -1,0 +1,626 @@
+// Learned smoother: a 3-layer CNN on each face's lattice (not in the paper;
+// an extension of its multigrid, Sec. 4.3).
+//
+//   h1 = M  relu(conv3x3(X,  W1) + b1)     3 -> 16 channels
+//   h2 = M  relu(conv3x3(h1, W2) + b2)     16 -> 16
+//   d  = Mi (conv3x3(h2, W3) + b3)         16 -> 1,   smoother step x += d
+//
+// X = [ (b - A x) / A_pp, log k_up(i,j), log k_down(i,j) ] on the closed
+// lattice (zero where a micro-triangle does not exist), M = closed triangle,
+// Mi = face interior; conv3x3 is a cross-correlation over (i +- 1, j +- 1)
+// with zeros outside the lattice.  Weights and activations are rounded to
+// BF16, products accumulate in FP32.  The weights live in __constant__
+// memory so that every FMA takes its weight as a broadcast operand; the
+// master copy (FP32) and Adam state live in device memory.
+//
+// Training (all on the GPU): pairs (X, e = x* - x_k) are cut as 64 x 64
+// crops of face lattices from FP64 V-cycle iterates; forward, backward-data
+// and backward-weight kernels per layer, a fixed-order reduction of the
+// per-CTA weight gradients, and Adam.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "hhg_internal.h"
+
+namespace hhg {
+
+namespace {
+
+constexpr int kNP = 2913;
+constexpr int oW1 = 0, ob1 = 432, oW2 = 448, ob2 = 2752, oW3 = 2768, ob3 = 2912;
+constexpr int kCS = 64;                       // crop size
+constexpr int kCore = 3;                      // loss ignores the outer 3 crop rows/cols
+constexpr int TJ = 8, TI = 32;                // output tile (256 threads)
+
+__constant__ float cW[kNP];
+
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+__device__ __forceinline__ bool closed_pt(int i, int j, int N) { return i >= 0 && j >= 0 && i + j <= N; }
+__device__ __forceinline__ bool interior_pt(int i, int j, int N) { return i >= 1 && j >= 1 && i + j <= N - 1; }
+
+// --------------------------------------------------------------- smoother
+// One CTA = an 8 x 32 output tile of one face.  Input region 14 x 38
+// (3 channels), h1 region 12 x 36, h2 region 10 x 34, all in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(TJ* TI)
+    k_cnn_smooth(MeshTables M, LevelView L, const float* __restrict__ s, const float* __restrict__ kf,
+                 T* x, float* delta) {
+  constexpr int J0 = TJ + 6, I0 = TI + 6, J1 = TJ + 4, I1 = TI + 4, J2 = TJ + 2, I2 = TI + 2;
+  __shared__ __nv_bfloat16 xin[3][J0][I0];   // activations are BF16 values: stored as such
+  __shared__ __nv_bfloat16 h1[16][J1][I1];
+  __shared__ __nv_bfloat16 h2[16][J2][I2];
+  const int f = blockIdx.z;
+  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
+  const int N = L.N;
+  if (i0 + j0 > N) return;   // tile entirely above the triangle (uniform per CTA)
+  const int64_t S = L.S;
+  const int64_t fb = L.f_off + (int64_t)f * L.FS;
+  const float* ku = kf ? kf + (int64_t)f * L.FS : nullptr;
+  const float* kd = kf ? kf + (int64_t)(M.nf + f) * L.FS : nullptr;
+  const int tid = threadIdx.x;
+  for (int q = tid; q < J0 * I0; q += TJ * TI) {
+    const int jj = q / I0, ii = q - jj * I0;
+    const int i = i0 - 3 + ii, j = j0 - 3 + jj;
+    float a = 0.f, bu = 0.f, bd = 0.f;
+    if (closed_pt(i, j, N)) {
+      const int64_t p = (int64_t)j * S + i;
+      a = s[fb + p];
+      if (ku && i + j <= N - 1) bu = __logf(ku[p]);
+      if (kd && i + j <= N - 2) bd = __logf(kd[p]);
+    }
+    xin[0][jj][ii] = __float2bfloat16_rn(a);
+    xin[1][jj][ii] = __float2bfloat16_rn(bu);
+    xin[2][jj][ii] = __float2bfloat16_rn(bd);
+  }
+  __syncthreads();
+  for (int q = tid; q < J1 * I1; q += TJ * TI) {
+    const int jj = q / I1, ii = q - jj * I1;
+    const int i = i0 - 2 + ii, j = j0 - 2 + jj;
+    float acc[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) acc[o] = cW[ob1 + o];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const float a = __bfloat162float(xin[c][jj + t / 3][ii + t % 3]);
+#pragma unroll
+        for (int o = 0; o < 16; ++o) acc[o] = fmaf(cW[oW1 + o * 27 + c * 9 + t], a, acc[o]);
+      }
+    const bool in = closed_pt(i, j, N);
+#pragma unroll
+    for (int o = 0; o < 16; ++o) h1[o][jj][ii] = __float2bfloat16_rn(in ? fmaxf(acc[o], 0.f) : 0.f);
+  }
+  __syncthreads();
+  for (int q = tid; q < J2 * I2; q += TJ * TI) {
+    const int jj = q / I2, ii = q - jj * I2;
+    const int i = i0 - 1 + ii, j = j0 - 1 + jj;
+    float acc[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) acc[o] = cW[ob2 + o];
+    for (int c = 0; c < 16; ++c)
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const float a = __bfloat162float(h1[c][jj + t / 3][ii + t % 3]);
+#pragma unroll
+        for (int o = 0; o < 16; ++o) acc[o] = fmaf(cW[oW2 + o * 144 + c * 9 + t], a, acc[o]);
+      }
+    const bool in = closed_pt(i, j, N);
+#pragma unroll
+    for (int o = 0; o < 16; ++o) h2[o][jj][ii] = __float2bfloat16_rn(in ? fmaxf(acc[o], 0.f) : 0.f);
+  }
+  __syncthreads();
+  const int ty = tid / TI, tx = tid % TI;
+  const int i = i0 + tx, j = j0 + ty;
+  if (!interior_pt(i, j, N)) return;
+  float acc = cW[ob3];
+  for (int c = 0; c < 16; ++c)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc = fmaf(cW[oW3 + c * 9 + t], __bfloat162float(h2[c][ty + t / 3][tx + t % 3]), acc);
+  const int64_t p = fb + (int64_t)j * S + i;
+  if (delta) delta[p] = acc;
+  if (x) x[p] = (T)((T)x[p] + (T)acc);
+}
+
+// --------------------------------------------------------------- training
+struct Crop {
+  int face, i0, j0, N;
+};
+
+// X (B, 3, 64, 64) and E (B, 64, 64) from the level vectors of one snapshot.
+__global__ void k_extract(MeshTables M, LevelView L, const float* __restrict__ s,
+                          const float* __restrict__ kf, const double* __restrict__ e,
+                          const Crop* __restrict__ crops, float* X, float* E) {
+  const Crop c = crops[blockIdx.y];
+  const int64_t fb = L.f_off + (int64_t)c.face * L.FS;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < kCS * kCS; q += gridDim.x * blockDim.x) {
+    const int cj = q / kCS, ci = q % kCS;
+    const int i = c.i0 + ci, j = c.j0 + cj;
+    float a = 0.f, bu = 0.f, bd = 0.f, ev = 0.f;
+    if (closed_pt(i, j, L.N)) {
+      const int64_t p = (int64_t)j * L.S + i;
+      a = s[fb + p];
+      if (kf && i + j <= L.N - 1) bu = __logf(kf[(int64_t)c.face * L.FS + p]);
+      if (kf && i + j <= L.N - 2) bd = __logf(kf[(int64_t)(M.nf + c.face) * L.FS + p]);
+      if (interior_pt(i, j, L.N)) ev = (float)e[fb + p];
+    }
+    float* Xc = X + (int64_t)blockIdx.y * 3 * kCS * kCS;
+    Xc[q] = bf16r(a);
+    Xc[kCS * kCS + q] = bf16r(bu);
+    Xc[2 * kCS * kCS + q] = bf16r(bd);
+    E[(int64_t)blockIdx.y * kCS * kCS + q] = ev;
+  }
+}
+
+// Forward conv on crops: thread = one point, all COUT outputs.  ACT 0: hidden
+// layer (relu, closed-triangle mask, BF16), ACT 1: output layer (interior mask).
+template <int CIN, int COUT, int ACT>
+__global__ void __launch_bounds__(TJ* TI)
+    k_tconv_fwd(const float* __restrict__ in, float* out, const Crop* __restrict__ crops, int woff, int boff) {
+  __shared__ float t[CIN][TJ + 2][TI + 2];
+  const Crop c = crops[blockIdx.y];
+  const int tj0 = (blockIdx.x / (kCS / TI)) * TJ, ti0 = (blockIdx.x % (kCS / TI)) * TI;
+  const float* inc = in + (int64_t)blockIdx.y * CIN * kCS * kCS;
+  for (int q = threadIdx.x; q < CIN * (TJ + 2) * (TI + 2); q += blockDim.x) {
+    const int ch = q / ((TJ + 2) * (TI + 2)), r = q % ((TJ + 2) * (TI + 2));
+    const int jj = r / (TI + 2), ii = r % (TI + 2);
+    const int cj = tj0 - 1 + jj, ci = ti0 - 1 + ii;
+    t[ch][jj][ii] = (cj >= 0 && cj < kCS && ci >= 0 && ci < kCS) ? inc[(int64_t)ch * kCS * kCS + cj * kCS + ci] : 0.f;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / TI, tx = threadIdx.x % TI;
+  float acc[COUT];
+#pragma unroll
+  for (int o = 0; o < COUT; ++o) acc[o] = cW[boff + o];
+  for (int ch = 0; ch < CIN; ++ch)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float a = t[ch][ty + k / 3][tx + k % 3];
+#pragma unroll
+      for (int o = 0; o < COUT; ++o) acc[o] = fmaf(cW[woff + o * CIN * 9 + ch * 9 + k], a, acc[o]);
+    }
+  const int cj = tj0 + ty, ci = ti0 + tx;
+  const int i = c.i0 + ci, j = c.j0 + cj;
+  float* oc = out + (int64_t)blockIdx.y * COUT * kCS * kCS + cj * kCS + ci;
+  if (ACT == 0) {
+    const bool in_t = closed_pt(i, j, c.N);
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) oc[(int64_t)o * kCS * kCS] = in_t ? bf16r(fmaxf(acc[o], 0.f)) : 0.f;
+  } else {
+    const bool in_i = interior_pt(i, j, c.N);
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) oc[(int64_t)o * kCS * kCS] = in_i ? acc[o] : 0.f;
+  }
+}
+
+// Loss per crop and its gradient w.r.t. d (mean over the B crops).
+__global__ void k_tloss(const float* __restrict__ d, const float* __restrict__ e,
+                        const Crop* __restrict__ crops, float* gd, float* loss, float inv_b) {
+  __shared__ float red[2][8];
+  const Crop c = crops[blockIdx.x];
+  const float* dc = d + (int64_t)blockIdx.x * kCS * kCS;
+  const float* ec = e + (int64_t)blockIdx.x * kCS * kCS;
+  float num = 0.f, den = 0.f;
+  for (int q = threadIdx.x; q < kCS * kCS; q += blockDim.x) {
+    const int cj = q / kCS, ci = q % kCS;
+    const bool ml = cj >= kCore && cj < kCS - kCore && ci >= kCore && ci < kCS - kCore &&
+                    interior_pt(c.i0 + ci, c.j0 + cj, c.N);
+    if (ml) {
+      const float r = dc[q] - ec[q];
+      num += r * r;
+      den += ec[q] * ec[q];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_down_sync(0xffffffffu, num, o);
+    den += __shfl_down_sync(0xffffffffu, den, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = num;
+    red[1][threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  num = den = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    num += red[0][w];
+    den += red[1][w];
+  }
+  const float scale = den > 0.f ? 2.f * inv_b / den : 0.f;
+  if (threadIdx.x == 0) loss[blockIdx.x] = den > 0.f ? num / den : 0.f;
+  float* g = gd + (int64_t)blockIdx.x * kCS * kCS;
+  for (int q = threadIdx.x; q < kCS * kCS; q += blockDim.x) {
+    const int cj = q / kCS, ci = q % kCS;
+    const bool ml = cj >= kCore && cj < kCS - kCore && ci >= kCore && ci < kCS - kCore &&
+                    interior_pt(c.i0 + ci, c.j0 + cj, c.N);
+    g[q] = ml ? scale * (dc[q] - ec[q]) : 0.f;
+  }
+}
+
+// Gradient w.r.t. the layer input, times the relu/mask derivative of that
+// input (hin > 0): gin[c][p] = (hin[c][p] > 0) sum_{o,t} W[o][c][t] gout[o][p - t].
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(TJ* TI)
+    k_tconv_bwd_data(const float* __restrict__ gout, const float* __restrict__ hin, float* gin, int woff) {
+  __shared__ float t[COUT][TJ + 2][TI + 2];
+  const int tj0 = (blockIdx.x / (kCS / TI)) * TJ, ti0 = (blockIdx.x % (kCS / TI)) * TI;
+  const float* gc = gout + (int64_t)blockIdx.y * COUT * kCS * kCS;
+  for (int q = threadIdx.x; q < COUT * (TJ + 2) * (TI + 2); q += blockDim.x) {
+    const int ch = q / ((TJ + 2) * (TI + 2)), r = q % ((TJ + 2) * (TI + 2));
+    const int jj = r / (TI + 2), ii = r % (TI + 2);
+    const int cj = tj0 - 1 + jj, ci = ti0 - 1 + ii;
+    t[ch][jj][ii] = (cj >= 0 && cj < kCS && ci >= 0 && ci < kCS) ? gc[(int64_t)ch * kCS * kCS + cj * kCS + ci] : 0.f;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / TI, tx = threadIdx.x % TI;
+  float acc[CIN];
+#pragma unroll
+  for (int c = 0; c < CIN; ++c) acc[c] = 0.f;
+  for (int o = 0; o < COUT; ++o)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      // out(p - tap) reads in(p): tap (dj, di) = (k / 3 - 1, k % 3 - 1)
+      const float g = t[o][ty + 2 - k / 3][tx + 2 - k % 3];
+#pragma unroll
+      for (int c = 0; c < CIN; ++c) acc[c] = fmaf(cW[woff + o * CIN * 9 + c * 9 + k], g, acc[c]);
+    }
+  const int cj = tj0 + ty, ci = ti0 + tx;
+  const float* hc = hin + (int64_t)blockIdx.y * CIN * kCS * kCS + cj * kCS + ci;
+  float* oc = gin + (int64_t)blockIdx.y * CIN * kCS * kCS + cj * kCS + ci;
+#pragma unroll
+  for (int c = 0; c < CIN; ++c) oc[(int64_t)c * kCS * kCS] = hc[(int64_t)c * kCS * kCS] > 0.f ? acc[c] : 0.f;
+}
+
+// Weight and bias gradients: per-CTA partial sums over its (crop, tile) pairs
+// (grid-stride), written to partial[blockIdx.x][COUT*CIN*9 + COUT].
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(TJ* TI)
+    k_tconv_bwd_w(const float* __restrict__ in, const float* __restrict__ gout, int B, float* partial) {
+  constexpr int NW = COUT * CIN * 9, NT = NW + COUT;
+  constexpr int PER = (NT + TJ * TI - 1) / (TJ * TI);
+  __shared__ float ti_[CIN][TJ + 2][TI + 2];
+  __shared__ float tg[COUT][TJ][TI];
+  float acc[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) acc[u] = 0.f;
+  const int ntile = (kCS / TJ) * (kCS / TI);
+  for (int w = blockIdx.x; w < B * ntile; w += gridDim.x) {
+    const int b = w / ntile, tile = w % ntile;
+    const int tj0 = (tile / (kCS / TI)) * TJ, ti0 = (tile % (kCS / TI)) * TI;
+    const float* inc = in + (int64_t)b * CIN * kCS * kCS;
+    const float* gc = gout + (int64_t)b * COUT * kCS * kCS;
+    __syncthreads();
+    for (int q = threadIdx.x; q < CIN * (TJ + 2) * (TI + 2); q += blockDim.x) {
+      const int ch = q / ((TJ + 2) * (TI + 2)), r = q % ((TJ + 2) * (TI + 2));
+      const int jj = r / (TI + 2), ii = r % (TI + 2);
+      const int cj = tj0 - 1 + jj, ci = ti0 - 1 + ii;
+      ti_[ch][jj][ii] = (cj >= 0 && cj < kCS && ci >= 0 && ci < kCS) ? inc[(int64_t)ch * kCS * kCS + cj * kCS + ci] : 0.f;
+    }
+    for (int q = threadIdx.x; q < COUT * TJ * TI; q += blockDim.x) {
+      const int ch = q / (TJ * TI), r = q % (TJ * TI);
+      tg[ch][r / TI][r % TI] = gc[(int64_t)ch * kCS * kCS + (tj0 + r / TI) * kCS + ti0 + r % TI];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int idx = threadIdx.x + u * TJ * TI;
+      if (idx < NW) {
+        const int o = idx / (CIN * 9), c = (idx / 9) % CIN, k = idx % 9;
+        float sacc = 0.f;
+        for (int py = 0; py < TJ; ++py)
+          for (int px = 0; px < TI; ++px) sacc = fmaf(tg[o][py][px], ti_[c][py + k / 3][px + k % 3], sacc);
+        acc[u] += sacc;
+      } else if (idx < NT) {
+        const int o = idx - NW;
+        float sacc = 0.f;
+        for (int py = 0; py < TJ; ++py)
+          for (int px = 0; px < TI; ++px) sacc += tg[o][py][px];
+        acc[u] += sacc;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int idx = threadIdx.x + u * TJ * TI;
+    if (idx < NT) partial[(int64_t)blockIdx.x * NT + idx] = acc[u];
+  }
+}
+
+// out[k] = sum_b partial[b][k] in fixed order; the layer's weights go to
+// grad[woff ...] and its biases to grad[boff ...].
+__global__ void k_reduce_grad(const float* __restrict__ partial, int nblk, int nw, int nb, float* grad,
+                              int woff, int boff) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nw + nb) return;
+  float s = 0.f;
+  for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * (nw + nb) + k];
+  if (k < nw) grad[woff + k] = s;
+  else grad[boff + k - nw] = s;
+}
+
+__global__ void k_adam(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
+                       float c1, float c2, float eps, float* wr) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float gk = g[k];
+  m[k] = b1 * m[k] + (1.f - b1) * gk;
+  v[k] = b2 * v[k] + (1.f - b2) * gk * gk;
+  w[k] -= lr * (m[k] / c1) / (sqrtf(v[k] / c2) + eps);
+  wr[k] = bf16r(w[k]);
+}
+
+__global__ void k_round_bf16(const float* w, float* wr, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) wr[k] = bf16r(w[k]);
+}
+
+// training-data helpers
+__global__ void k_fill_random(int64_t n, double* v, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed ^ (uint64_t)i;
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[i] = (double)(z >> 11) * 0x1.0p-52 - 1.0;
+  }
+}
+
+__global__ void k_sub(int64_t n, const double* a, const double* b, double* o) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = a[i] - b[i];
+}
+
+}  // namespace
+
+// ================================================================ host
+struct Learned {
+  float* w = nullptr;      // master FP32 weights (device)
+  float* wr = nullptr;     // BF16-rounded copy (device), source of the constant bank
+  float* g = nullptr;      // gradient
+  float* m = nullptr;      // Adam moments
+  float* v = nullptr;
+  int step = 0;
+  bool trained = false;
+};
+
+static Learned& learned_of(Mesh& m) {
+  if (!m.learned) {
+    Learned* L = new Learned();
+    for (float** p : {&L->w, &L->wr, &L->g, &L->m, &L->v}) {
+      check_cuda(cudaMalloc(p, kNP * sizeof(float)), "learned alloc");
+      check_cuda(cudaMemset(*p, 0, kNP * sizeof(float)), "learned memset");
+    }
+    m.learned = L;
+  }
+  return *m.learned;
+}
+
+void learned_free(Mesh& m) {
+  if (!m.learned) return;
+  Learned* L = m.learned;
+  for (float* p : {L->w, L->wr, L->g, L->m, L->v}) cudaFree(p);
+  delete L;
+  m.learned = nullptr;
+}
+
+static void load_constants(Learned& L, cudaStream_t st) {
+  check_cuda(cudaMemcpyToSymbolAsync(cW, L.wr, kNP * sizeof(float), 0, cudaMemcpyDeviceToDevice, st), "weights to constant bank");
+}
+
+void learned_set_weights(Mesh& m, const float* w_host, cudaStream_t st) {
+  Learned& L = learned_of(m);
+  check_cuda(cudaMemcpyAsync(L.w, w_host, kNP * sizeof(float), cudaMemcpyHostToDevice, st), "weights upload");
+  k_round_bf16<<<(kNP + 255) / 256, 256, 0, st>>>(L.w, L.wr, kNP);
+  check_cuda(cudaGetLastError(), "round");
+  check_cuda(cudaMemsetAsync(L.m, 0, kNP * sizeof(float), st), "adam m");
+  check_cuda(cudaMemsetAsync(L.v, 0, kNP * sizeof(float), st), "adam v");
+  L.step = 0;
+  L.trained = true;
+  check_cuda(cudaStreamSynchronize(st), "sync");
+}
+
+void learned_get_weights(Mesh& m, float* w_host) {
+  Learned& L = learned_of(m);
+  check_cuda(cudaMemcpy(w_host, L.w, kNP * sizeof(float), cudaMemcpyDeviceToHost), "weights download");
+}
+
+bool learned_ready(const Mesh& m) { return m.learned && m.learned->trained; }
+
+// x += CNN(s) on the face interiors of one level (s: FP32 scaled residual with
+// ghost copies); delta (optional) receives the correction.
+void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, float* delta, cudaStream_t st) {
+  if (!m.learned) throw std::invalid_argument("learned smoother has no weights");
+  Learned& L = *m.learned;
+  load_constants(L, st);
+  const LevelView& lv = m.levels[level].lv;
+  const float* kf = m.vark ? (const float*)m.levels[level].k[1] : nullptr;
+  dim3 grid((lv.N + 1 + TI - 1) / TI, (lv.N + 1 + TJ - 1) / TJ, m.nf);
+  LaunchScope ls(HHG_K_OTHER, level, st);
+  if (prec == 0) k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, (double*)x, delta);
+  else k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, (float*)x, delta);
+  check_cuda(cudaGetLastError(), "cnn smooth");
+}
+
+// One learned smoothing step: s = (b - A x)/diag, x += CNN(s) on faces,
+// then one Gauss-Seidel pass over the vertex and edge unknowns.
+void learned_step(const Mesh& m, int level, int prec, void* x, const void* b, cudaStream_t st) {
+  float* s = (float*)m.levels[level].r[1];
+  scaled_residual(m, level, prec, x, b, s, st);
+  learned_apply(m, level, prec, s, x, nullptr, st);
+  ve_gs(m, level, prec, x, b, true, st);
+}
+
+// Mean loss and gradient over crops (test hook and training step).
+static float grad_on_crops(Mesh& m, int B, const float* X, const float* E, const Crop* crops_dev, float* work,
+                           float* loss_dev, cudaStream_t st) {
+  Learned& L = learned_of(m);
+  load_constants(L, st);
+  const int64_t P = (int64_t)kCS * kCS;
+  float* h1 = work;
+  float* h2 = h1 + (int64_t)B * 16 * P;
+  float* d = h2 + (int64_t)B * 16 * P;
+  float* gd = d + (int64_t)B * P;
+  float* g2 = gd + (int64_t)B * P;
+  float* g1 = g2 + (int64_t)B * 16 * P;
+  float* part = g1 + (int64_t)B * 16 * P;
+  const dim3 grid((kCS / TJ) * (kCS / TI), B);
+  k_tconv_fwd<3, 16, 0><<<grid, TJ * TI, 0, st>>>(X, h1, crops_dev, oW1, ob1);
+  k_tconv_fwd<16, 16, 0><<<grid, TJ * TI, 0, st>>>(h1, h2, crops_dev, oW2, ob2);
+  k_tconv_fwd<16, 1, 1><<<grid, TJ * TI, 0, st>>>(h2, d, crops_dev, oW3, ob3);
+  k_tloss<<<B, 256, 0, st>>>(d, E, crops_dev, gd, loss_dev, 1.0f / B);
+  const int nblk = std::min(B * (kCS / TJ) * (kCS / TI), 304);
+  // layer 3
+  k_tconv_bwd_w<16, 1><<<nblk, TJ * TI, 0, st>>>(h2, gd, B, part);
+  k_reduce_grad<<<(145 + 255) / 256, 256, 0, st>>>(part, nblk, 144, 1, L.g, oW3, ob3);
+  k_tconv_bwd_data<16, 1><<<grid, TJ * TI, 0, st>>>(gd, h2, g2, oW3);
+  // layer 2
+  k_tconv_bwd_w<16, 16><<<nblk, TJ * TI, 0, st>>>(h1, g2, B, part);
+  k_reduce_grad<<<(2320 + 255) / 256, 256, 0, st>>>(part, nblk, 2304, 16, L.g, oW2, ob2);
+  k_tconv_bwd_data<16, 16><<<grid, TJ * TI, 0, st>>>(g2, h1, g1, oW2);
+  // layer 1
+  k_tconv_bwd_w<3, 16><<<nblk, TJ * TI, 0, st>>>(X, g1, B, part);
+  k_reduce_grad<<<(448 + 255) / 256, 256, 0, st>>>(part, nblk, 432, 16, L.g, oW1, ob1);
+  check_cuda(cudaGetLastError(), "train kernels");
+  return 0.f;
+}
+
+static size_t work_floats(int B) {
+  const int64_t P = (int64_t)kCS * kCS;
+  return (size_t)B * P * (16 + 16 + 1 + 1 + 16 + 16) + (size_t)304 * 2320;
+}
+
+void learned_grad(Mesh& m, int B, const float* X_dev, const float* E_dev, const int* crops_host,
+                  float* grad_host, float* loss_host, cudaStream_t st) {
+  Learned& L = learned_of(m);
+  std::vector<Crop> cr(B);
+  for (int b = 0; b < B; ++b) cr[b] = Crop{crops_host[4 * b], crops_host[4 * b + 1], crops_host[4 * b + 2], crops_host[4 * b + 3]};
+  Crop* cd = nullptr;
+  float* work = nullptr;
+  float* loss = nullptr;
+  check_cuda(cudaMalloc(&cd, B * sizeof(Crop)), "alloc");
+  check_cuda(cudaMalloc(&work, work_floats(B) * sizeof(float)), "alloc");
+  check_cuda(cudaMalloc(&loss, B * sizeof(float)), "alloc");
+  check_cuda(cudaMemcpyAsync(cd, cr.data(), B * sizeof(Crop), cudaMemcpyHostToDevice, st), "crops");
+  grad_on_crops(m, B, X_dev, E_dev, cd, work, loss, st);
+  std::vector<float> lh(B);
+  check_cuda(cudaMemcpyAsync(grad_host, L.g, kNP * sizeof(float), cudaMemcpyDeviceToHost, st), "grad");
+  check_cuda(cudaMemcpyAsync(lh.data(), loss, B * sizeof(float), cudaMemcpyDeviceToHost, st), "loss");
+  check_cuda(cudaStreamSynchronize(st), "sync");
+  double s = 0.0;
+  for (float v : lh) s += v;
+  *loss_host = (float)(s / B);
+  cudaFree(cd);
+  cudaFree(work);
+  cudaFree(loss);
+}
+
+// FP64 multigrid solve on level l (host loop, used for training data).
+static void solve_fp64(Mesh& m, int l, double* x, const double* b, double tol, cudaStream_t st) {
+  const LevelData& ld = m.levels[l];
+  residual_op(m, l, 0, x, b, ld.r[0], m.scalars, st);
+  double r0 = 0.0, r = 0.0;
+  check_cuda(cudaMemcpyAsync(&r0, m.scalars, 8, cudaMemcpyDeviceToHost, st), "norm");
+  check_cuda(cudaStreamSynchronize(st), "sync");
+  r = r0;
+  for (int it = 0; it < 60 && r > tol * tol * r0; ++it) {
+    vcycle_run(m, l, 0, x, b, 3, 3, 0, st);
+    residual_op(m, l, 0, x, b, ld.r[0], m.scalars, st);
+    check_cuda(cudaMemcpyAsync(&r, m.scalars, 8, cudaMemcpyDeviceToHost, st), "norm");
+    check_cuda(cudaStreamSynchronize(st), "sync");
+  }
+}
+
+// Generates n_pairs crops from FP64 V-cycle iterates on level l and trains
+// the network for `epochs` passes (Adam, lr, mini-batches of `batch` crops).
+void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr, uint64_t seed,
+                   float* loss_hist, cudaStream_t st) {
+  Learned& L = learned_of(m);
+  if (!L.trained) {   // He initialisation (seeded), last layer scaled by 0.1
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    std::vector<float> w(kNP, 0.f);
+    for (int k = oW1; k < ob1; ++k) w[k] = (float)(nd(rng) * std::sqrt(2.0 / 27.0));
+    for (int k = oW2; k < ob2; ++k) w[k] = (float)(nd(rng) * std::sqrt(2.0 / 144.0));
+    for (int k = oW3; k < ob3; ++k) w[k] = (float)(0.1 * nd(rng) * std::sqrt(2.0 / 144.0));
+    learned_set_weights(m, w.data(), st);
+  }
+  const LevelData& ld = m.levels[l];
+  const LevelView& lv = ld.lv;
+  const int N = lv.N;
+  if (N < kCS) throw std::invalid_argument("training level too coarse for 64 x 64 crops");
+  const int64_t len = lv.len;
+  double *b = nullptr, *xs = nullptr, *x = nullptr, *e = nullptr;
+  float *X = nullptr, *E = nullptr, *work = nullptr, *loss = nullptr;
+  Crop* crops = nullptr;
+  const int snapshots = 12;
+  const int per_snap = (n_pairs + snapshots - 1) / snapshots;
+  const int total = per_snap * snapshots;
+  for (double** p : {&b, &xs, &x, &e}) check_cuda(cudaMalloc(p, len * sizeof(double)), "alloc");
+  check_cuda(cudaMalloc(&X, (size_t)total * 3 * kCS * kCS * sizeof(float)), "alloc X");
+  check_cuda(cudaMalloc(&E, (size_t)total * kCS * kCS * sizeof(float)), "alloc E");
+  check_cuda(cudaMalloc(&crops, (size_t)total * sizeof(Crop)), "alloc crops");
+  check_cuda(cudaMalloc(&work, work_floats(batch) * sizeof(float)), "alloc work");
+  check_cuda(cudaMalloc(&loss, batch * sizeof(float)), "alloc loss");
+  // crop origins: centres uniformly inside the triangle
+  std::mt19937_64 rng(seed * 7919 + 17);
+  std::vector<Crop> hc(total);
+  for (int q = 0; q < total; ++q) {
+    int ci, cj;
+    do {
+      ci = (int)(rng() % (uint64_t)(N + 1));
+      cj = (int)(rng() % (uint64_t)(N + 1));
+    } while (ci + cj > N - 4 || ci < 2 || cj < 2);
+    hc[q] = Crop{(int)(rng() % (uint64_t)m.nf), ci - kCS / 2, cj - kCS / 2, N};
+  }
+  check_cuda(cudaMemcpyAsync(crops, hc.data(), total * sizeof(Crop), cudaMemcpyHostToDevice, st), "crops");
+  // x* for a random right-hand side
+  k_fill_random<<<1024, 256, 0, st>>>(len, b, seed);
+  check_cuda(cudaMemsetAsync(xs, 0, len * sizeof(double), st), "zero");
+  solve_fp64(m, l, xs, b, 1e-12, st);
+  const float* kf = m.vark ? (const float*)ld.k[1] : nullptr;
+  float* s = (float*)ld.r[1];
+  for (int snap = 0; snap < snapshots; ++snap) {
+    if (snap % 6 == 0) {   // fresh random start; snapshot k of a start has k cycles (1..6)
+      k_fill_random<<<1024, 256, 0, st>>>(len, x, seed + 1000 + snap);
+      zero_dirichlet_and_ghosts(m, l, x, st);
+    }
+    vcycle_run(m, l, 0, x, b, 3, 3, 0, st);
+    scaled_residual(m, l, 0, x, b, s, st);
+    k_sub<<<1024, 256, 0, st>>>(len, xs, x, e);
+    k_extract<<<dim3(4, per_snap), 256, 0, st>>>(m.tab, lv, s, kf, e, crops + (size_t)snap * per_snap,
+                                                  X + (size_t)snap * per_snap * 3 * kCS * kCS,
+                                                  E + (size_t)snap * per_snap * kCS * kCS);
+    check_cuda(cudaGetLastError(), "extract");
+  }
+  // training
+  const int nb = total / batch;
+  std::vector<int> order(nb);
+  for (int q = 0; q < nb; ++q) order[q] = q;
+  std::vector<float> lh(batch);
+  for (int ep = 0; ep < epochs; ++ep) {
+    std::shuffle(order.begin(), order.end(), rng);
+    double ep_loss = 0.0;
+    for (int q = 0; q < nb; ++q) {
+      const size_t off = (size_t)order[q] * batch;
+      grad_on_crops(m, batch, X + off * 3 * kCS * kCS, E + off * kCS * kCS, crops + off, work, loss, st);
+      L.step += 1;
+      const float c1 = 1.f - std::pow(0.9f, (float)L.step), c2 = 1.f - std::pow(0.999f, (float)L.step);
+      k_adam<<<(kNP + 255) / 256, 256, 0, st>>>(L.w, L.g, L.m, L.v, kNP, lr, 0.9f, 0.999f, c1, c2, 1e-8f, L.wr);
+      check_cuda(cudaGetLastError(), "adam");
+      check_cuda(cudaMemcpyAsync(lh.data(), loss, batch * sizeof(float), cudaMemcpyDeviceToHost, st), "loss");
+      check_cuda(cudaStreamSynchronize(st), "sync");
+      for (float v : lh) ep_loss += v;
+    }
+    if (loss_hist) loss_hist[ep] = (float)(ep_loss / ((double)nb * batch));
+  }
+  L.trained = true;
+  for (void* p : {(void*)b, (void*)xs, (void*)x, (void*)e, (void*)X, (void*)E, (void*)crops, (void*)work, (void*)loss}) cudaFree(p);
+}
+
+}  // namespace hhg

@@ -309,6 +309,8 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
 void mesh_destroy_internal(Mesh* m) {
   if (!m) return;
   cudaDeviceSynchronize();
+  learned_free(*m);
+  krylov_free(*m);
   for (void* p : m->allocations) cudaFree(p);
   delete m;
 }

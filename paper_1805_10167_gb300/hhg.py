@@ -25,7 +25,9 @@ lib = C.CDLL(LIB_PATH)
 OK, ERR_ARG, ERR_MESH, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_NAN, ERR_TIMEOUT, ERR_BREAKDOWN = range(9)
 F64, F32 = 0, 1
 GS_FWD, GS_BWD, JACOBI = 0, 1, 2
-SOLVE_MG, SOLVE_IR = 0, 1
+SOLVE_MG, SOLVE_IR, SOLVE_FGMRES = 0, 1, 2
+SMOOTH_GS, SMOOTH_LEARNED = 0, 1
+LEARNED_NPARAMS = 2913
 
 
 class Info(C.Structure):
@@ -43,13 +45,14 @@ class VcycleOpts(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
-                ("max_iter", C.c_int32), ("tol", C.c_double)]
+                ("max_iter", C.c_int32), ("tol", C.c_double), ("smoother", C.c_int32),
+                ("restart", C.c_int32)]
 
 
 class SolveReport(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("r0", C.c_double),
                 ("r_final", C.c_double), ("history", C.POINTER(C.c_double)),
-                ("history_cap", C.c_int32)]
+                ("history_cap", C.c_int32), ("smoother_used", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -79,6 +82,13 @@ _SIGS = {
     "hhg_batch_info": [_P, C.c_int32, C.POINTER(Info)],
     "hhg_batch_tune": [_P, _P],
     "hhg_batch_solve": [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(SolveOpts), C.POINTER(SolveReport), _P],
+    "hhg_learned_set_weights": [_P, C.POINTER(C.c_float), C.c_int64],
+    "hhg_learned_get_weights": [_P, C.POINTER(C.c_float), C.c_int64],
+    "hhg_learned_apply": [_P, C.c_int32, C.c_int32, _P, _P, _P, _P],
+    "hhg_learned_grad": [_P, C.c_int32, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float),
+                         C.POINTER(C.c_float), _P],
+    "hhg_learned_train": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_uint64,
+                          C.POINTER(C.c_float), _P],
     "hhg_profile_begin": [C.c_uint32, C.c_int32],
     "hhg_profile_end": [C.POINTER(C.c_int64), C.POINTER(C.c_double)],
 }
@@ -216,6 +226,35 @@ class Mesh:
         _check(lib.hhg_smooth(self.h, level, prec, _ptr(x), _ptr(b), smoother, sweeps, omega,
                               _stream(stream)))
 
+    # ---- learned smoother
+    def learned_set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(lib.hhg_learned_set_weights(self.h, w.ctypes.data_as(C.POINTER(C.c_float)), w.size))
+
+    def learned_get_weights(self):
+        w = np.zeros(LEARNED_NPARAMS, dtype=np.float32)
+        _check(lib.hhg_learned_get_weights(self.h, w.ctypes.data_as(C.POINTER(C.c_float)), w.size))
+        return w
+
+    def learned_apply(self, level, s, x=None, d=None, prec=F64, stream=None):
+        _check(lib.hhg_learned_apply(self.h, level, prec, _ptr(s), _ptr(x), _ptr(d), _stream(stream)))
+
+    def learned_grad(self, X, E, crops, stream=None):
+        crops = np.ascontiguousarray(crops, dtype=np.int32).reshape(-1, 4)
+        g = np.zeros(LEARNED_NPARAMS, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        _check(lib.hhg_learned_grad(self.h, crops.shape[0], _ptr(X), _ptr(E),
+                                    crops.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    g.ctypes.data_as(C.POINTER(C.c_float)),
+                                    loss.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)))
+        return float(loss[0]), g
+
+    def learned_train(self, level, n_pairs=10000, epochs=20, batch=128, lr=1e-3, seed=0, stream=None):
+        hist = np.zeros(max(epochs, 1), dtype=np.float32)
+        _check(lib.hhg_learned_train(self.h, level, n_pairs, epochs, batch, lr, seed,
+                                     hist.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)))
+        return hist[:epochs]
+
     def tune(self, prec=F64, stream=None):
         _check(lib.hhg_tune(self.h, prec, _stream(stream)))
 
@@ -224,14 +263,14 @@ class Mesh:
         _check(lib.hhg_vcycle(self.h, level, prec, _ptr(x), _ptr(b), C.byref(o), _stream(stream)))
 
     def solve(self, level, x, b, mode=SOLVE_MG, nu1=3, nu2=3, tol=1e-10, max_iter=100,
-              stream=None, history=True, raise_on_error=True):
+              stream=None, history=True, raise_on_error=True, smoother=SMOOTH_GS, restart=20):
         """Returns (status, report dict)."""
-        o = SolveOpts(mode, nu1, nu2, max_iter, tol)
+        o = SolveOpts(mode, nu1, nu2, max_iter, tol, smoother, restart)
         hist = (C.c_double * (max_iter + 1))()
-        rep = SolveReport(0, 0, 0.0, 0.0, hist if history else None, max_iter + 1 if history else 0)
+        rep = SolveReport(0, 0, 0.0, 0.0, hist if history else None, max_iter + 1 if history else 0, 0)
         st = lib.hhg_solve(self.h, level, _ptr(x), _ptr(b), C.byref(o), C.byref(rep), _stream(stream))
         out = {"iterations": rep.iterations, "status": rep.status, "r0": rep.r0,
-               "r_final": rep.r_final,
+               "r_final": rep.r_final, "smoother_used": rep.smoother_used,
                "history": [hist[i] for i in range(min(rep.iterations + 1, max_iter + 1))]}
         if raise_on_error and st != OK:
             raise HHGError(st, last_error())

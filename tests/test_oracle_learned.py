@@ -1,0 +1,142 @@
+"""Pins of the learned-smoother network and of FGMRES (CPU, FP64)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import krylov, learned
+from oracle import mesh as om
+from oracle import multigrid as mg
+from paper_1805_10167_gb300 import inputs
+
+
+def small_case(seed=0, N=8, H=None, W=None):
+    rng = np.random.default_rng(seed)
+    M, Mi = learned.masks(N, H=H, W=W)
+    X = rng.standard_normal((3,) + M.shape) * M
+    e = rng.standard_normal(M.shape) * Mi
+    return X, M, Mi, e
+
+
+def test_parameter_count():
+    assert learned.n_params() == 16 * (27 + 1) + 16 * (144 + 1) + (144 + 1)
+
+
+def test_conv_matches_direct_sum():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((3, 5, 6))
+    W = rng.standard_normal((2, 3, 3, 3))
+    b = rng.standard_normal(2)
+    out = learned.conv(x, W, b)
+    for o in range(2):
+        for j in range(5):
+            for i in range(6):
+                s = b[o]
+                for c in range(3):
+                    for dj in (-1, 0, 1):
+                        for di in (-1, 0, 1):
+                            if 0 <= j + dj < 5 and 0 <= i + di < 6:
+                                s += W[o, c, dj + 1, di + 1] * x[c, j + dj, i + di]
+                assert out[o, j, i] == pytest.approx(s, abs=1e-12)
+
+
+def test_backward_equals_central_differences():
+    X, M, Mi, e = small_case(2, N=7)
+    p = learned.init_params(3)
+    for k in learned.ORDER:
+        p[k] = p[k] + 0.05 * np.random.default_rng(4).standard_normal(p[k].shape)
+    L, g = learned.loss_and_grad(p, X, M, Mi, e, Mi)
+    v0 = learned.flatten(p)
+    gv = learned.flatten(g)
+    rng = np.random.default_rng(5)
+    idx = rng.choice(v0.size, 40, replace=False)
+    h = 1e-6
+    for t in idx:
+        vp, vm = v0.copy(), v0.copy()
+        vp[t] += h
+        vm[t] -= h
+        Lp = learned.loss_and_grad(learned.unflatten(vp), X, M, Mi, e, Mi)[0]
+        Lm = learned.loss_and_grad(learned.unflatten(vm), X, M, Mi, e, Mi)[0]
+        fd = (Lp - Lm) / (2 * h)
+        assert fd == pytest.approx(gv[t], rel=1e-5, abs=1e-8), (t, fd, gv[t])
+
+
+def test_output_vanishes_off_the_interior_and_is_local():
+    X, M, Mi, e = small_case(6, N=12)
+    p = learned.init_params(7)
+    d, _ = learned.forward(p, X, M, Mi)
+    assert np.all(d[Mi == 0] == 0)
+    # receptive field 7 x 7: a change at (6, 6) leaves points 4 away untouched
+    X2 = X.copy()
+    X2[:, 6, 3] += 1.0
+    d2, _ = learned.forward(p, X2, M, Mi)
+    changed = np.argwhere(np.abs(d2 - d) > 0)
+    assert np.all(np.abs(changed - np.array([6, 3])).max(axis=1) <= 3)
+
+
+def test_adam_matches_its_definition_on_a_quadratic():
+    v = np.array([1.0, -2.0])
+    m = s = np.zeros(2)
+    for t in range(1, 4):
+        g = 2 * v
+        v_new, m, s = learned.adam_step(v, g, m, s, t, lr=0.1)
+        # first step of Adam moves every coordinate by lr (bias-corrected)
+        if t == 1:
+            np.testing.assert_allclose(np.abs(v_new - v), 0.1, rtol=1e-6)
+        v = v_new
+
+
+# ------------------------------------------------------------------ FGMRES
+def _problem(L=2):
+    xy, tri = inputs.annulus_mesh(32, 2)
+    H = mg.Hierarchy(om.MacroMesh(xy, tri), L)
+    lv = H.levels[L]
+    b = inputs.uniform_pm1(lv.n, 3)
+    b[~lv.free] = 0
+    return H, lv, b
+
+
+def test_fgmres_identity_preconditioner_is_minimal_residual():
+    """With M = I, after k steps the iterate minimises ||b - A x|| over
+    x0 + K_k(A, r0) (least squares over an explicit Krylov basis)."""
+    H, lv, b = _problem(1)
+    fr = lv.free
+    A = lambda v: H.apply(1, v)
+    for k in (1, 3, 6):
+        x, hist, steps = krylov.fgmres(A, lambda v, j: v.copy(), b, np.zeros(lv.n), fr, m=20, tol=0.0, max_iter=k)
+        Af = H.A[1][fr][:, fr].toarray()
+        r0 = b[fr]
+        K = [r0]
+        for _ in range(k - 1):
+            K.append(Af @ K[-1])
+        K = np.array(K).T
+        y = np.linalg.lstsq(Af @ K, r0, rcond=None)[0]
+        np.testing.assert_allclose(x[fr], K @ y, rtol=1e-8, atol=1e-10)
+
+
+def test_fgmres_exact_preconditioner_one_step():
+    H, lv, b = _problem(2)
+    fr = lv.free
+    Af = H.A[2][fr][:, fr].toarray()
+    exact = lambda v, j: np.where(fr, 0.0, 0.0) + _embed(np.linalg.solve(Af, v[fr]), fr)
+    x, hist, steps = krylov.fgmres(lambda v: H.apply(2, v), exact, b, np.zeros(lv.n), fr, tol=1e-10)
+    assert steps == 1
+    assert hist[-1] <= 1e-10 * hist[0]
+
+
+def _embed(v, fr):
+    out = np.zeros(fr.size)
+    out[fr] = v
+    return out
+
+
+def test_fgmres_with_vcycle_preconditioner_converges_monotonically():
+    H, lv, b = _problem(4)
+    fr = lv.free
+
+    def pre(v, j):
+        z = np.zeros(lv.n)
+        return mg.vcycle(H, 4, z, v, 1, 1)
+    x, hist, steps = krylov.fgmres(lambda v: H.apply(4, v), pre, b, np.zeros(lv.n), fr, tol=1e-10)
+    assert hist[-1] <= 1e-10 * hist[0]
+    assert np.all(np.diff(hist) <= 1e-12 * hist[0])
+    assert steps < 20
