@@ -11,7 +11,10 @@ array: out[o, j, i] = sum_{c, dj, di} W[o, c, dj + 1, di + 1] x[c, j + dj, i + d
 M masks the closed triangle (i + j <= N), Mi the face interior (i, j >= 1,
 i + j <= N - 1).  Input channels: D^-1 r (residual over the operator
 diagonal), log k of the upward and of the downward micro-triangle (i, j)
-(0 where the downward one does not exist).  The smoother step is x += d.
+(0 where the downward one does not exist).  The residual channel enters
+divided by its RMS sigma over the face's closed lattice and d is multiplied
+by sigma (per crop in training), so the step is homogeneous of degree 1 in
+the residual.  The smoother step is x += d.
 
 Training pair: a crop of the lattice, target e = x* - x; loss per crop
 ||d - e||^2 / ||e||^2 over the crop's loss mask; Adam (Kingma & Ba 2015).
@@ -141,7 +144,8 @@ def face_images(level, s, k_elem=None):
     """Per macro-face input image X (3, N+1, N+1) and masks (M, Mi) from a
     canonical vector s (the scaled residual) and the per-element coefficient
     in canonical element order (None: k = 1).  Returns a list over faces of
-    (X, M, Mi, G) with G the lattice -> canonical id map."""
+    (X, M, Mi, G, sigma): X with its residual channel divided by sigma, the
+    face's residual RMS; G the lattice -> canonical id map."""
     N = level.N
     M, Mi = masks(N)
     out = []
@@ -149,6 +153,7 @@ def face_images(level, s, k_elem=None):
         X = np.zeros((3, N + 1, N + 1))
         ok = G >= 0
         X[0][ok] = s[G[ok]]
+        sig = np.sqrt(np.sum(X[0][ok] ** 2) / ((N + 1) * (N + 2) / 2))
         if k_elem is not None:
             kf = np.asarray(k_elem)[f * N * N:(f + 1) * N * N]
             r = 0
@@ -160,5 +165,7 @@ def face_images(level, s, k_elem=None):
                 for i in range(N - 1 - j):
                     X[2, j, i] = np.log(kf[r])
                     r += 1
-        out.append((X * M, M, Mi, G))
+        if sig > 0:
+            X[0] /= sig
+        out.append((X * M, M, Mi, G, sig))
     return out

@@ -13,6 +13,10 @@
 // memory so that every FMA takes its weight as a broadcast operand; the
 // master copy (FP32) and Adam state live in device memory.
 //
+// The residual channel is divided by its RMS over the face (per crop in
+// training) and the output multiplied back, so the step is homogeneous of
+// degree 1 in the residual, as an error estimate must be.
+//
 // Training (all on the GPU): pairs (X, e = x* - x_k) are cut as 64 x 64
 // crops of face lattices from FP64 V-cycle iterates; forward, backward-data
 // and backward-weight kernels per layer, a fixed-order reduction of the
@@ -42,6 +46,12 @@ __constant__ float cW[kNP];
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 __device__ __forceinline__ bool closed_pt(int i, int j, int N) { return i >= 0 && j >= 0 && i + j <= N; }
+
+// A 64 x 64 training crop: pixel (ci, cj) is lattice point (i0 + ci, j0 + cj)
+// of face `face` with N intervals.
+struct Crop {
+  int face, i0, j0, N;
+};
 __device__ __forceinline__ bool interior_pt(int i, int j, int N) { return i >= 1 && j >= 1 && i + j <= N - 1; }
 
 // --------------------------------------------------------------- smoother
@@ -50,7 +60,7 @@ __device__ __forceinline__ bool interior_pt(int i, int j, int N) { return i >= 1
 template <typename T>
 __global__ void __launch_bounds__(TJ* TI)
     k_cnn_smooth(MeshTables M, LevelView L, const float* __restrict__ s, const float* __restrict__ kf,
-                 T* x, float* delta) {
+                 const float* __restrict__ scale, T* x, float* delta) {
   constexpr int J0 = TJ + 6, I0 = TI + 6, J1 = TJ + 4, I1 = TI + 4, J2 = TJ + 2, I2 = TI + 2;
   __shared__ __nv_bfloat16 xin[3][J0][I0];   // activations are BF16 values: stored as such
   __shared__ __nv_bfloat16 h1[16][J1][I1];
@@ -58,7 +68,9 @@ __global__ void __launch_bounds__(TJ* TI)
   const int f = blockIdx.z;
   const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
   const int N = L.N;
-  if (i0 + j0 > N) return;   // tile entirely above the triangle (uniform per CTA)
+  const float sig = scale[f];
+  if (i0 + j0 > N || !(sig > 0.f)) return;   // tile above the triangle / zero residual (uniform per CTA)
+  const float isig = 1.f / sig;
   const int64_t S = L.S;
   const int64_t fb = L.f_off + (int64_t)f * L.FS;
   const float* ku = kf ? kf + (int64_t)f * L.FS : nullptr;
@@ -70,7 +82,7 @@ __global__ void __launch_bounds__(TJ* TI)
     float a = 0.f, bu = 0.f, bd = 0.f;
     if (closed_pt(i, j, N)) {
       const int64_t p = (int64_t)j * S + i;
-      a = s[fb + p];
+      a = s[fb + p] * isig;
       if (ku && i + j <= N - 1) bu = __logf(ku[p]);
       if (kd && i + j <= N - 2) bd = __logf(kd[p]);
     }
@@ -124,14 +136,71 @@ __global__ void __launch_bounds__(TJ* TI)
 #pragma unroll
     for (int t = 0; t < 9; ++t) acc = fmaf(cW[oW3 + c * 9 + t], __bfloat162float(h2[c][ty + t / 3][tx + t % 3]), acc);
   const int64_t p = fb + (int64_t)j * S + i;
+  acc *= sig;
   if (delta) delta[p] = acc;
   if (x) x[p] = (T)((T)x[p] + (T)acc);
 }
 
+// Per-face residual scale: sigma_f = sqrt(mean of s^2 over the closed lattice
+// (N+1)(N+2)/2 points of face f).  One CTA per face.
+__global__ void k_face_rms(MeshTables M, LevelView L, const float* __restrict__ s, float* scale) {
+  __shared__ float red[8];
+  const int f = blockIdx.x;
+  const int64_t fb = L.f_off + (int64_t)f * L.FS;
+  const int N = L.N;
+  float acc = 0.f;
+  for (int j = threadIdx.x >> 5; j <= N; j += blockDim.x >> 5)
+    for (int i = threadIdx.x & 31; i <= N - j; i += 32) {
+      const float v = s[fb + (int64_t)j * L.S + i];
+      acc = fmaf(v, v, acc);
+    }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    scale[f] = sqrtf(t / (0.5f * (float)(N + 1) * (float)(N + 2)));
+  }
+}
+
+// Training crops: input channel 0 and target divided by the crop's residual
+// scale (RMS of channel 0 over its closed-lattice pixels) -- the smoother is
+// homogeneous of degree 1 in the residual.
+__global__ void k_crop_normalise(const Crop* __restrict__ crops, float* X, float* E) {
+  __shared__ float red[2][8];
+  const Crop c = crops[blockIdx.x];
+  float* x0 = X + (int64_t)blockIdx.x * 3 * kCS * kCS;
+  float* e = E + (int64_t)blockIdx.x * kCS * kCS;
+  float acc = 0.f, cnt = 0.f;
+  for (int q = threadIdx.x; q < kCS * kCS; q += blockDim.x)
+    if (closed_pt(c.i0 + q % kCS, c.j0 + q / kCS, c.N)) {
+      acc = fmaf(x0[q], x0[q], acc);
+      cnt += 1.f;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_down_sync(0xffffffffu, acc, o);
+    cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = acc;
+    red[1][threadIdx.x >> 5] = cnt;
+  }
+  __syncthreads();
+  acc = cnt = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    acc += red[0][w];
+    cnt += red[1][w];
+  }
+  const float sig = cnt > 0.f ? sqrtf(acc / cnt) : 0.f;
+  const float inv = sig > 0.f ? 1.f / sig : 0.f;
+  for (int q = threadIdx.x; q < kCS * kCS; q += blockDim.x) {
+    x0[q] = bf16r(x0[q] * inv);
+    e[q] *= inv;
+  }
+}
+
 // --------------------------------------------------------------- training
-struct Crop {
-  int face, i0, j0, N;
-};
 
 // X (B, 3, 64, 64) and E (B, 64, 64) from the level vectors of one snapshot.
 __global__ void k_extract(MeshTables M, LevelView L, const float* __restrict__ s,
@@ -380,6 +449,8 @@ __global__ void k_sub(int64_t n, const double* a, const double* b, double* o) {
 
 // ================================================================ host
 struct Learned {
+  float* scale = nullptr;  // per-face residual scale of the last application
+  int scale_n = 0;
   float* w = nullptr;      // master FP32 weights (device)
   float* wr = nullptr;     // BF16-rounded copy (device), source of the constant bank
   float* g = nullptr;      // gradient
@@ -396,6 +467,8 @@ static Learned& learned_of(Mesh& m) {
       check_cuda(cudaMalloc(p, kNP * sizeof(float)), "learned alloc");
       check_cuda(cudaMemset(*p, 0, kNP * sizeof(float)), "learned memset");
     }
+    check_cuda(cudaMalloc(&L->scale, std::max(1, m.nf) * sizeof(float)), "learned alloc");
+    L->scale_n = m.nf;
     m.learned = L;
   }
   return *m.learned;
@@ -404,7 +477,7 @@ static Learned& learned_of(Mesh& m) {
 void learned_free(Mesh& m) {
   if (!m.learned) return;
   Learned* L = m.learned;
-  for (float* p : {L->w, L->wr, L->g, L->m, L->v}) cudaFree(p);
+  for (float* p : {L->w, L->wr, L->g, L->m, L->v, L->scale}) cudaFree(p);
   delete L;
   m.learned = nullptr;
 }
@@ -442,8 +515,10 @@ void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, 
   const float* kf = m.vark ? (const float*)m.levels[level].k[1] : nullptr;
   dim3 grid((lv.N + 1 + TI - 1) / TI, (lv.N + 1 + TJ - 1) / TJ, m.nf);
   LaunchScope ls(HHG_K_OTHER, level, st);
-  if (prec == 0) k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, (double*)x, delta);
-  else k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, (float*)x, delta);
+  k_face_rms<<<m.nf, 256, 0, st>>>(m.tab, lv, s, L.scale);
+  if (delta) check_cuda(cudaMemsetAsync(delta, 0, (size_t)lv.len * sizeof(float), st), "delta clear");
+  if (prec == 0) k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, L.scale, (double*)x, delta);
+  else k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, L.scale, (float*)x, delta);
   check_cuda(cudaGetLastError(), "cnn smooth");
 }
 
@@ -596,6 +671,9 @@ void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr,
     k_extract<<<dim3(4, per_snap), 256, 0, st>>>(m.tab, lv, s, kf, e, crops + (size_t)snap * per_snap,
                                                   X + (size_t)snap * per_snap * 3 * kCS * kCS,
                                                   E + (size_t)snap * per_snap * kCS * kCS);
+    k_crop_normalise<<<per_snap, 256, 0, st>>>(crops + (size_t)snap * per_snap,
+                                               X + (size_t)snap * per_snap * 3 * kCS * kCS,
+                                               E + (size_t)snap * per_snap * kCS * kCS);
     check_cuda(cudaGetLastError(), "extract");
   }
   // training

@@ -37,10 +37,10 @@ def test_cnn_forward_parity(vark):
     P.g.learned_apply(L, s32, d=d, prec=1)
     got = P.from_dev(L, d, prec=1)
     want = np.zeros(lv.n)
-    for X, M, Mi, G in learned.face_images(lv, s, P.H.k[L]):
+    for X, M, Mi, G, sig in learned.face_images(lv, s, P.H.k[L]):
         out, _ = learned.forward(p, X, M, Mi)
         ok = Mi > 0
-        want[G[ok]] = out[ok]
+        want[G[ok]] = sig * out[ok]
     e = rel_err(got, want)
     print(f"CNN forward BF16 vs FP64 oracle: max-norm relative error {e:.3e}")
     assert e < BF16_TOL
