@@ -56,15 +56,36 @@ __device__ __forceinline__ bool interior_pt(int i, int j, int N) { return i >= 1
 
 // --------------------------------------------------------------- smoother
 // One CTA = an 8 x 32 output tile of one face.  Input region 14 x 38
-// (3 channels), h1 region 12 x 36, h2 region 10 x 34, all in shared memory.
+// (3 channels), h1 region 12 x 36, h2 region 10 x 34, all BF16 in shared
+// memory, activations channel-last (16 channels = 32 bytes per point).
+// Layer 1 (3 -> 16) and layer 3 (16 -> 1) run on the CUDA cores; layer 2
+// (16 -> 16, 80 % of the work) on the tensor cores: for each tap a
+// 16-point x 16-channel block of h1 times the tap's 16 x 16 weight block,
+// mma.sync m16n8k16 BF16 -> FP32, two n-blocks of 8 output channels.
+
+// D += A * B for one m16n8k16 block (BF16 inputs, FP32 accumulators).
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const uint32_t l = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo));
+  const uint32_t h = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi));
+  return l | (h << 16);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TJ* TI)
     k_cnn_smooth(MeshTables M, LevelView L, const float* __restrict__ s, const float* __restrict__ kf,
                  const float* __restrict__ scale, T* x, float* delta) {
   constexpr int J0 = TJ + 6, I0 = TI + 6, J1 = TJ + 4, I1 = TI + 4, J2 = TJ + 2, I2 = TI + 2;
-  __shared__ __nv_bfloat16 xin[3][J0][I0];   // activations are BF16 values: stored as such
-  __shared__ __nv_bfloat16 h1[16][J1][I1];
-  __shared__ __nv_bfloat16 h2[16][J2][I2];
+  __shared__ __nv_bfloat16 xin[3][J0][I0];
+  __shared__ __align__(16) __nv_bfloat16 h1[J1][I1][16];
+  __shared__ __align__(16) __nv_bfloat16 h2[J2][I2][16];
   const int f = blockIdx.z;
   const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
   const int N = L.N;
@@ -91,6 +112,7 @@ __global__ void __launch_bounds__(TJ* TI)
     xin[2][jj][ii] = __float2bfloat16_rn(bd);
   }
   __syncthreads();
+  // layer 1 (CUDA cores)
   for (int q = tid; q < J1 * I1; q += TJ * TI) {
     const int jj = q / I1, ii = q - jj * I1;
     const int i = i0 - 2 + ii, j = j0 - 2 + jj;
@@ -106,35 +128,74 @@ __global__ void __launch_bounds__(TJ* TI)
         for (int o = 0; o < 16; ++o) acc[o] = fmaf(cW[oW1 + o * 27 + c * 9 + t], a, acc[o]);
       }
     const bool in = closed_pt(i, j, N);
+    uint32_t packed[8];
 #pragma unroll
-    for (int o = 0; o < 16; ++o) h1[o][jj][ii] = __float2bfloat16_rn(in ? fmaxf(acc[o], 0.f) : 0.f);
+    for (int o = 0; o < 8; ++o)
+      packed[o] = in ? pack_bf16(fmaxf(acc[2 * o], 0.f), fmaxf(acc[2 * o + 1], 0.f)) : 0u;
+    uint4* dst = reinterpret_cast<uint4*>(&h1[jj][ii][0]);
+    dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+  }
+  // weight fragments of layer 2 for this lane: B[k][n] = W2[n][k][tap]
+  const int lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  uint32_t bfr[9][2][2];
+#pragma unroll
+  for (int t = 0; t < 9; ++t)
+#pragma unroll
+    for (int nb = 0; nb < 2; ++nb) {
+      const int o = nb * 8 + g;
+      bfr[t][nb][0] = pack_bf16(cW[oW2 + o * 144 + (2 * tq) * 9 + t], cW[oW2 + o * 144 + (2 * tq + 1) * 9 + t]);
+      bfr[t][nb][1] = pack_bf16(cW[oW2 + o * 144 + (2 * tq + 8) * 9 + t], cW[oW2 + o * 144 + (2 * tq + 9) * 9 + t]);
+    }
+  __syncthreads();
+  // layer 2 (tensor cores): chunks of 16 points of the h2 region
+  constexpr int NP2 = J2 * I2;
+  for (int chunk = warp; chunk * 16 < NP2; chunk += TJ * TI / 32) {
+    const int qa = min(chunk * 16 + g, NP2 - 1), qb = min(chunk * 16 + g + 8, NP2 - 1);
+    const int ja = qa / I2, ia = qa % I2, jb = qb / I2, ib = qb % I2;
+    float d0[4], d1[4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      d0[u] = cW[ob2 + 2 * tq + u];
+      d0[u + 2] = d0[u];
+      d1[u] = cW[ob2 + 8 + 2 * tq + u];
+      d1[u + 2] = d1[u];
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int dy = t / 3, dx = t % 3;
+      const uint32_t* pa = reinterpret_cast<const uint32_t*>(&h1[ja + dy][ia + dx][0]);
+      const uint32_t* pb = reinterpret_cast<const uint32_t*>(&h1[jb + dy][ib + dx][0]);
+      const uint32_t afr[4] = {pa[tq], pb[tq], pa[tq + 4], pb[tq + 4]};
+      mma_bf16(d0, afr, bfr[t][0][0], bfr[t][0][1]);
+      mma_bf16(d1, afr, bfr[t][1][0], bfr[t][1][1]);
+    }
+    // rows g and g+8 of the block; columns 2tq, 2tq+1 of each n-block
+    const int pts[2] = {chunk * 16 + g, chunk * 16 + g + 8};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = pts[h];
+      if (q >= NP2) continue;
+      const int jj = q / I2, ii = q % I2;
+      const bool in = closed_pt(i0 - 1 + ii, j0 - 1 + jj, N);
+      uint32_t* row = reinterpret_cast<uint32_t*>(&h2[jj][ii][0]);
+      row[tq] = in ? pack_bf16(fmaxf(d0[2 * h], 0.f), fmaxf(d0[2 * h + 1], 0.f)) : 0u;
+      row[tq + 4] = in ? pack_bf16(fmaxf(d1[2 * h], 0.f), fmaxf(d1[2 * h + 1], 0.f)) : 0u;
+    }
   }
   __syncthreads();
-  for (int q = tid; q < J2 * I2; q += TJ * TI) {
-    const int jj = q / I2, ii = q - jj * I2;
-    const int i = i0 - 1 + ii, j = j0 - 1 + jj;
-    float acc[16];
-#pragma unroll
-    for (int o = 0; o < 16; ++o) acc[o] = cW[ob2 + o];
-    for (int c = 0; c < 16; ++c)
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const float a = __bfloat162float(h1[c][jj + t / 3][ii + t % 3]);
-#pragma unroll
-        for (int o = 0; o < 16; ++o) acc[o] = fmaf(cW[oW2 + o * 144 + c * 9 + t], a, acc[o]);
-      }
-    const bool in = closed_pt(i, j, N);
-#pragma unroll
-    for (int o = 0; o < 16; ++o) h2[o][jj][ii] = __float2bfloat16_rn(in ? fmaxf(acc[o], 0.f) : 0.f);
-  }
-  __syncthreads();
+  // layer 3 (CUDA cores)
   const int ty = tid / TI, tx = tid % TI;
   const int i = i0 + tx, j = j0 + ty;
   if (!interior_pt(i, j, N)) return;
   float acc = cW[ob3];
-  for (int c = 0; c < 16; ++c)
 #pragma unroll
-    for (int t = 0; t < 9; ++t) acc = fmaf(cW[oW3 + c * 9 + t], __bfloat162float(h2[c][ty + t / 3][tx + t % 3]), acc);
+  for (int t = 0; t < 9; ++t) {
+    const __nv_bfloat16* hv = &h2[ty + t / 3][tx + t % 3][0];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc = fmaf(cW[oW3 + c * 9 + t], __bfloat162float(hv[c]), acc);
+  }
   const int64_t p = fb + (int64_t)j * S + i;
   acc *= sig;
   if (delta) delta[p] = acc;
