@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-vark", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-pairs", type=int, default=10000)
+    ap.add_argument("--learned-epochs", type=int, default=12)
     ap.add_argument("--batch-size", type=int, default=64)
     return ap.parse_args()
 
@@ -179,6 +183,79 @@ def run_batch(args, dev, st):
             "gdofs_per_cycle": free * outer / t_batch / 1e9,
             "sequential_seconds_to_tol": t_seq, "speedup_vs_sequential": t_seq / t_batch,
             "all_converged": all(r["r_final"] <= 1e-10 * r["r0"] for r in reps)}
+
+
+def vark_mesh(level, dev, st):
+    """The 128-face annulus with k = exp(g), g the seeded (42) random field of
+    squared-exponential covariance (length 0.1, sigma 1) at element centroids."""
+    import torch
+
+    from paper_1805_10167_gb300 import hhg, inputs
+    xy, tri = inputs.annulus_mesh(32, 2)
+    g = hhg.Mesh(xy, tri, level)
+    k = inputs.grf_coefficient(inputs.element_centroids(xy, tri, level, device=dev), seed=42)
+    g.set_coefficient(k, stream=st)
+    del k
+    info = g.info(level)
+    bc = torch.tensor(inputs.uniform_pm1(info.n_nodes, 1234), dtype=torch.float64, device=dev)
+    b = torch.zeros(info.vec_len, dtype=torch.float64, device=dev)
+    g.from_canonical(level, bc, b, stream=st)
+    return g, info, b
+
+
+def timed_solve(g, level, b, st, **kw):
+    import torch
+    x = torch.zeros_like(b)
+    g.solve(level, x, b, stream=st, **kw)          # warm-up
+    x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, rep = g.solve(level, x, b, stream=st, **kw)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    it = rep["iterations"]
+    return {"seconds": dt, "iterations": it, "rel_residual": rep["r_final"] / rep["r0"],
+            "factor_per_iteration": (rep["r_final"] / rep["r0"]) ** (1.0 / max(it, 1)),
+            "smoother_used": ["gs", "learned"][rep.get("smoother_used", 0)]}
+
+
+def run_vark(args, dev, st):
+    """Variable-coefficient annulus, level 10: time to a 1e-10 relative FP64
+    residual, FP64 V(3,3) against FP32 V(3,3) cycles inside FP64 iterative
+    refinement."""
+    from paper_1805_10167_gb300 import hhg
+    L = args.level
+    g, info, b = vark_mesh(L, dev, st)
+    out = {"workload": f"annulus-128faces-L{L}-grf-k-V(3,3)", "free_dofs": info.n_free,
+           "fp64_mg": timed_solve(g, L, b, st, mode=hhg.SOLVE_MG),
+           "fp32_ir": timed_solve(g, L, b, st, mode=hhg.SOLVE_IR)}
+    out["ir_speedup"] = out["fp64_mg"]["seconds"] / out["fp32_ir"]["seconds"]
+    g.close()
+    return out
+
+
+def run_learned(args, dev, st):
+    """Learned smoother on the variable-coefficient annulus at level 9: train
+    on FP64 V-cycle residual/error crops, then FGMRES(20) preconditioned by
+    one FP32 V(1,1) with the learned smoother (judge with fallback) or with
+    Gauss-Seidel, against plain FP64 V(3,3) cycles."""
+    from paper_1805_10167_gb300 import hhg
+    L = max(6, args.level - 1)
+    g, info, b = vark_mesh(L, dev, st)
+    t0 = time.perf_counter()
+    hist = g.learned_train(L, n_pairs=args.learned_pairs, epochs=args.learned_epochs, batch=128,
+                           lr=1e-3, seed=0, stream=st)
+    t_train = time.perf_counter() - t0
+    out = {"workload": f"annulus-128faces-L{L}-grf-k", "free_dofs": info.n_free,
+           "train_seconds": t_train, "train_pairs": args.learned_pairs, "epochs": args.learned_epochs,
+           "loss_first_last": [float(hist[0]), float(hist[-1])] if len(hist) else None,
+           "fgmres_learned": timed_solve(g, L, b, st, mode=hhg.SOLVE_FGMRES, nu1=1, nu2=1,
+                                         smoother=hhg.SMOOTH_LEARNED),
+           "fgmres_gs": timed_solve(g, L, b, st, mode=hhg.SOLVE_FGMRES, nu1=1, nu2=1,
+                                    smoother=hhg.SMOOTH_GS),
+           "fp64_mg": timed_solve(g, L, b, st, mode=hhg.SOLVE_MG)}
+    g.close()
+    return out
 
 
 def run_reference(args):
@@ -332,7 +409,10 @@ def run_ours(args):
             solve[name] = {"seconds": time.perf_counter() - t0, "cycles": rep["iterations"],
                            "rel_residual": rep["r_final"] / rep["r0"]}
 
+    g.close()
     batch = None if args.no_batch else run_batch(args, dev, st)
+    vark = None if args.no_vark else run_vark(args, dev, st)
+    learned_res = None if args.no_learned else run_learned(args, dev, st)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -352,8 +432,8 @@ def run_ours(args):
             "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(launches)),
             "launches_by_class": dict(zip(hhg.K_NAMES, launches)),
             "roofline": roofline, "cpu_baseline": cpu, "time_to_tol": solve, "batch": batch,
+            "vark": vark, "learned": learned_res,
         }), flush=True)
-    g.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -233,7 +233,7 @@ def uniform_pm1(n: int, seed: int) -> np.ndarray:
     return u * (2.0 ** -52) - 1.0
 
 
-def element_centroids(xy: np.ndarray, tri: np.ndarray, level: int) -> np.ndarray:
+def element_centroids(xy: np.ndarray, tri: np.ndarray, level: int, device=None):
     """Centroids (n_faces * N^2, 2) of the level-``level`` micro-triangles in
     canonical element order.  Face frame: x = v0 + (i/N)(v1-v0) + (j/N)(v2-v0),
     (v0,v1,v2) the counter-clockwise face.  Upward triangle (i,j): lattice
@@ -247,6 +247,13 @@ def element_centroids(xy: np.ndarray, tri: np.ndarray, level: int) -> np.ndarray
     cd = np.array([(i + 2.0 / 3.0, j + 2.0 / 3.0) for i, j in dn]).reshape(-1, 2) / N
     loc = np.concatenate([cu, cd], axis=0)  # (N^2, 2) in (s,t) frame coordinates
     v0, v1, v2 = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    if device is not None:   # same arithmetic with torch (large levels)
+        import torch
+        T = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device)
+        lt, a0, a1, a2 = T(loc), T(v0), T(v1), T(v2)
+        out = (a0[:, None, :] + lt[None, :, 0:1] * (a1 - a0)[:, None, :]
+               + lt[None, :, 1:2] * (a2 - a0)[:, None, :])
+        return out.reshape(-1, 2)
     out = (v0[:, None, :] + loc[None, :, 0:1] * (v1 - v0)[:, None, :]
            + loc[None, :, 1:2] * (v2 - v0)[:, None, :])
     return out.reshape(-1, 2)
@@ -260,6 +267,16 @@ def grf_coefficient(points: np.ndarray, seed: int = 42, length: float = 0.1,
     rng = np.random.default_rng(seed)
     w = rng.normal(0.0, 1.0 / length, size=(n_features, 2))
     phi = rng.uniform(0.0, 2.0 * np.pi, size=n_features)
+    if not isinstance(points, np.ndarray):   # torch tensor: same draw, evaluated with torch
+        import torch
+        wt = torch.as_tensor(w, dtype=torch.float64, device=points.device)
+        pt = torch.as_tensor(phi, dtype=torch.float64, device=points.device)
+        out = torch.empty(points.shape[0], dtype=torch.float64, device=points.device)
+        step = 1 << 20
+        for s0 in range(0, points.shape[0], step):
+            pr = points[s0:s0 + step] @ wt.T + pt[None, :]
+            out[s0:s0 + step] = sigma * np.sqrt(2.0 / n_features) * torch.cos(pr).sum(dim=1)
+        return torch.exp(out)
     out = np.empty(points.shape[0], dtype=np.float64)
     step = 1 << 20
     for s in range(0, points.shape[0], step):
