@@ -296,19 +296,23 @@ hhg_status hhg_learned_get_weights(hhg_mesh mesh, float* w_host, int64_t n);
  * x += d there. */
 hhg_status hhg_learned_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const float* s,
                              void* x, float* d, void* stream);
-/* Mean relative loss ||d - e||^2/||e||^2 and its gradient w.r.t. the weights
- * over n_crops 64 x 64 crops: X (n_crops, 3, 64, 64) and E (n_crops, 64, 64)
- * FP32 DEVICE arrays, crops_host: 4 ints per crop (face, i0, j0, N) placing
- * crop pixel (ci, cj) at lattice point (i0 + ci, j0 + cj) of a face with N
- * intervals; the loss counts face-interior pixels at least 3 away from the
- * crop border.  grad_host: HHG_LEARNED_NPARAMS floats.  Synchronous. */
-hhg_status hhg_learned_grad(hhg_mesh mesh, int32_t n_crops, const float* X, const float* E,
-                            const int32_t* crops_host, float* grad_host, float* loss_host,
-                            void* stream);
+/* Mean training loss and its gradient w.r.t. the weights over n_crops
+ * 64 x 64 crops (FP32 DEVICE arrays): X (n_crops, 3, 64, 64) the network
+ * input, S (n_crops, 64, 64) the normalised scaled residual, K (n_crops, 2,
+ * 64, 64) the upward / downward micro-triangle coefficients at each pixel
+ * (NULL: k = 1).  crops_host: 4 ints per crop (face, i0, j0, N) placing
+ * pixel (ci, cj) at lattice point (i0 + ci, j0 + cj) of that face of this
+ * mesh.  Loss per crop: ||S - D^-1 A d||^2 / ||S||^2 over face-interior
+ * pixels at least 3 away from the crop border, d = CNN(X), D^-1 A the
+ * scaled P1 rows of the face (its cotangents and K).  grad_host:
+ * HHG_LEARNED_NPARAMS floats.  Synchronous. */
+hhg_status hhg_learned_grad(hhg_mesh mesh, int32_t n_crops, const float* X, const float* S,
+                            const float* K, const int32_t* crops_host, float* grad_host,
+                            float* loss_host, void* stream);
 /* Generates n_pairs training crops on `level` (level >= 6) from FP64
- * V(3,3) iterates x_k, k = 1..6, of random starts against x* (solved to
- * 1e-12 for a random right-hand side) -- inputs from b - A x_k, target
- * e = x* - x_k -- and trains the network for `epochs` passes with Adam
+ * V(3,3) iterates x_k, k = 1..6, of random starts for a random right-hand
+ * side -- residual/error pairs r = b - A x_k = A e -- and trains the network
+ * on the loss of hhg_learned_grad for `epochs` passes with Adam
  * (lr, beta 0.9 / 0.999, mini-batches of `batch` crops; weights initialised
  * from `seed` unless already set).  loss_history_host (may be NULL) gets the
  * mean loss of each epoch.  Synchronous. */

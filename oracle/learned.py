@@ -169,3 +169,55 @@ def face_images(level, s, k_elem=None):
             X[0] /= sig
         out.append((X * M, M, Mi, G, sig))
     return out
+
+
+# ------------------------------------------------------------------ residual loss
+def edge_weights(cot, ku, kd):
+    """Off-diagonal magnitudes of the P1 rows on a lattice window: for each
+    point p = (i, j) and each of its six neighbours, w = 1/2 cot(opposite
+    angle) (k_T1 + k_T2) over the two micro-triangles sharing the edge (the
+    cotangent form, face angles t0, t1, t2 at v0, v1, v2).  ku, kd: (H, W)
+    images of the upward / downward micro-triangle coefficients at (i, j)
+    (0 where absent).  Returns {offset (di, dj): (H, W) weights}."""
+    c0, c1, c2 = cot
+    sh = lambda a, dj, di: shift(a[None], dj, di)[0]
+    u, uw, us = ku, sh(ku, 0, -1), sh(ku, -1, 0)                 # up(i,j), up(i-1,j), up(i,j-1)
+    ds, dw, dsw = sh(kd, -1, 0), sh(kd, 0, -1), sh(kd, -1, -1)   # down(i,j-1), down(i-1,j), down(i-1,j-1)
+    return {(1, 0): 0.5 * c2 * (u + ds), (-1, 0): 0.5 * c2 * (uw + dsw),
+            (0, 1): 0.5 * c1 * (u + dw), (0, -1): 0.5 * c1 * (us + dsw),
+            (1, -1): 0.5 * c0 * (us + ds), (-1, 1): 0.5 * c0 * (uw + dw)}
+
+
+def scaled_operator(d, wts):
+    """(D^-1 A d)_p = d_p - sum_q (w_pq / diag_p) d_q on the window (zeros
+    outside), diag_p = sum_q w_pq."""
+    diag = sum(wts.values())
+    acc = np.zeros_like(d)
+    for (di, dj), w in wts.items():
+        acc += w * shift(d[None], dj, di)[0]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return d - np.where(diag > 0, acc / diag, 0.0)
+
+
+def residual_loss_and_grad(p, X, M, Mi, shat, Ml, wts):
+    """Loss ||Ml (shat - D^-1 A d)||^2 / ||Ml shat||^2 of the smoother step d
+    on the normalised scaled residual shat, and its gradient."""
+    d, (X, a1, h1, a2, h2) = forward(p, X, M, Mi)
+    den = float(np.sum(Ml * shat * shat))
+    res = Ml * (shat - scaled_operator(d, wts))
+    L = float(np.sum(res * res)) / den
+    # d/dd_q of -sum_p res_p (D^-1 A d)_p: -(res_q - sum_p (w_pq/diag_p) res_p)
+    diag = sum(wts.values())
+    with np.errstate(divide="ignore", invalid="ignore"):
+        v = np.where(diag > 0, res / diag, 0.0)
+    back = np.zeros_like(d)
+    for (di, dj), w in wts.items():
+        # p = q - (di, dj) has q as its (di, dj) neighbour with weight w(p)
+        back += shift((w * v)[None], -dj, -di)[0]
+    gd = -(2.0 / den) * (res - back) * Mi
+    g3x, gW3, gb3 = conv_backward(h2, p["W3"], gd[None])
+    g2 = g3x * M * (a2 > 0)
+    g2x, gW2, gb2 = conv_backward(h1, p["W2"], g2)
+    g1 = g2x * M * (a1 > 0)
+    _, gW1, gb1 = conv_backward(X, p["W1"], g1)
+    return L, {"W1": gW1, "b1": gb1, "W2": gW2, "b2": gb2, "W3": gW3, "b3": gb3}

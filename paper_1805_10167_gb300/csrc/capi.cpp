@@ -536,19 +536,19 @@ hhg_status hhg_learned_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const 
   });
 }
 
-hhg_status hhg_learned_grad(hhg_mesh mesh, int32_t n_crops, const float* X, const float* E,
-                            const int32_t* crops_host, float* grad_host, float* loss_host,
-                            void* stream) {
+hhg_status hhg_learned_grad(hhg_mesh mesh, int32_t n_crops, const float* X, const float* Sres,
+                            const float* K, const int32_t* crops_host, float* grad_host,
+                            float* loss_host, void* stream) {
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     need(X, "X");
-    need(E, "E");
+    need(Sres, "S");
     need(crops_host, "crops_host");
     need(grad_host, "grad_host");
     need(loss_host, "loss_host");
     if (n_crops < 1) throw ArgError("n_crops < 1");
     if (!hhg::learned_ready(m)) throw ArgError("no weights set or trained");
-    hhg::learned_grad(m, n_crops, X, E, crops_host, grad_host, loss_host, S(stream));
+    hhg::learned_grad(m, n_crops, X, Sres, K, crops_host, grad_host, loss_host, S(stream));
     return HHG_OK;
   });
 }

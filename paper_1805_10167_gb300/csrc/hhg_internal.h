@@ -269,8 +269,8 @@ void learned_set_weights(Mesh& m, const float* w_host, cudaStream_t st);
 void learned_get_weights(Mesh& m, float* w_host);
 void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, float* delta, cudaStream_t st);
 void learned_step(const Mesh& m, int level, int prec, void* x, const void* b, cudaStream_t st);
-void learned_grad(Mesh& m, int B, const float* X_dev, const float* E_dev, const int* crops_host,
-                  float* grad_host, float* loss_host, cudaStream_t st);
+void learned_grad(Mesh& m, int B, const float* X_dev, const float* S_dev, const float* K_dev,
+                  const int* crops_host, float* grad_host, float* loss_host, cudaStream_t st);
 void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr, uint64_t seed,
                    float* loss_hist, cudaStream_t st);
 void krylov_free(Mesh& m);

@@ -17,10 +17,13 @@
 // training) and the output multiplied back, so the step is homogeneous of
 // degree 1 in the residual, as an error estimate must be.
 //
-// Training (all on the GPU): pairs (X, e = x* - x_k) are cut as 64 x 64
-// crops of face lattices from FP64 V-cycle iterates; forward, backward-data
-// and backward-weight kernels per layer, a fixed-order reduction of the
-// per-CTA weight gradients, and Adam.
+// Training (all on the GPU): residual/error pairs of FP64 V-cycle iterates
+// x_k (r = b - A x_k = A e) are cut as 64 x 64 crops of face lattices; the
+// loss is the residual the step leaves, ||S - D^-1 A d||^2 / ||S||^2 on the
+// normalised scaled residual S (the energy form of the error loss: it asks
+// for what a smoother does, removing the residual locally); forward,
+// backward-data and backward-weight kernels per layer, a fixed-order
+// reduction of the per-CTA weight gradients, and Adam.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -225,18 +228,18 @@ __global__ void k_face_rms(MeshTables M, LevelView L, const float* __restrict__ 
   }
 }
 
-// Training crops: input channel 0 and target divided by the crop's residual
-// scale (RMS of channel 0 over its closed-lattice pixels) -- the smoother is
-// homogeneous of degree 1 in the residual.
-__global__ void k_crop_normalise(const Crop* __restrict__ crops, float* X, float* E) {
+// Training crops: the scaled residual divided by its RMS over the crop's
+// closed-lattice pixels (the smoother is homogeneous of degree 1 in the
+// residual): S <- S / sigma, input channel 0 <- BF16(S / sigma).
+__global__ void k_crop_normalise(const Crop* __restrict__ crops, float* X, float* S) {
   __shared__ float red[2][8];
   const Crop c = crops[blockIdx.x];
   float* x0 = X + (int64_t)blockIdx.x * 3 * kCS * kCS;
-  float* e = E + (int64_t)blockIdx.x * kCS * kCS;
+  float* sc = S + (int64_t)blockIdx.x * kCS * kCS;
   float acc = 0.f, cnt = 0.f;
   for (int q = threadIdx.x; q < kCS * kCS; q += blockDim.x)
     if (closed_pt(c.i0 + q % kCS, c.j0 + q / kCS, c.N)) {
-      acc = fmaf(x0[q], x0[q], acc);
+      acc = fmaf(sc[q], sc[q], acc);
       cnt += 1.f;
     }
   for (int o = 16; o > 0; o >>= 1) {
@@ -256,35 +259,37 @@ __global__ void k_crop_normalise(const Crop* __restrict__ crops, float* X, float
   const float sig = cnt > 0.f ? sqrtf(acc / cnt) : 0.f;
   const float inv = sig > 0.f ? 1.f / sig : 0.f;
   for (int q = threadIdx.x; q < kCS * kCS; q += blockDim.x) {
-    x0[q] = bf16r(x0[q] * inv);
-    e[q] *= inv;
+    sc[q] *= inv;
+    x0[q] = bf16r(sc[q]);
   }
 }
 
 // --------------------------------------------------------------- training
 
-// X (B, 3, 64, 64) and E (B, 64, 64) from the level vectors of one snapshot.
+// X (B, 3, 64, 64), the raw scaled residual S (B, 64, 64) and the element
+// coefficients K (B, 2, 64, 64: upward, downward triangle (i, j); 0 where
+// absent, 1 where present for k = 1) from the level vectors of one snapshot.
 __global__ void k_extract(MeshTables M, LevelView L, const float* __restrict__ s,
-                          const float* __restrict__ kf, const double* __restrict__ e,
-                          const Crop* __restrict__ crops, float* X, float* E) {
+                          const float* __restrict__ kf, const Crop* __restrict__ crops, float* X, float* Sraw,
+                          float* K) {
   const Crop c = crops[blockIdx.y];
   const int64_t fb = L.f_off + (int64_t)c.face * L.FS;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < kCS * kCS; q += gridDim.x * blockDim.x) {
     const int cj = q / kCS, ci = q % kCS;
     const int i = c.i0 + ci, j = c.j0 + cj;
-    float a = 0.f, bu = 0.f, bd = 0.f, ev = 0.f;
+    float a = 0.f, ku = 0.f, kd = 0.f;
     if (closed_pt(i, j, L.N)) {
       const int64_t p = (int64_t)j * L.S + i;
       a = s[fb + p];
-      if (kf && i + j <= L.N - 1) bu = __logf(kf[(int64_t)c.face * L.FS + p]);
-      if (kf && i + j <= L.N - 2) bd = __logf(kf[(int64_t)(M.nf + c.face) * L.FS + p]);
-      if (interior_pt(i, j, L.N)) ev = (float)e[fb + p];
+      if (i + j <= L.N - 1) ku = kf ? kf[(int64_t)c.face * L.FS + p] : 1.f;
+      if (i + j <= L.N - 2) kd = kf ? kf[(int64_t)(M.nf + c.face) * L.FS + p] : 1.f;
     }
     float* Xc = X + (int64_t)blockIdx.y * 3 * kCS * kCS;
-    Xc[q] = bf16r(a);
-    Xc[kCS * kCS + q] = bf16r(bu);
-    Xc[2 * kCS * kCS + q] = bf16r(bd);
-    E[(int64_t)blockIdx.y * kCS * kCS + q] = ev;
+    Xc[kCS * kCS + q] = bf16r(ku > 0.f ? __logf(ku) : 0.f);
+    Xc[2 * kCS * kCS + q] = bf16r(kd > 0.f ? __logf(kd) : 0.f);
+    Sraw[(int64_t)blockIdx.y * kCS * kCS + q] = a;
+    K[(int64_t)blockIdx.y * 2 * kCS * kCS + q] = ku;
+    K[(int64_t)blockIdx.y * 2 * kCS * kCS + kCS * kCS + q] = kd;
   }
 }
 
@@ -329,23 +334,71 @@ __global__ void __launch_bounds__(TJ* TI)
   }
 }
 
-// Loss per crop and its gradient w.r.t. d (mean over the B crops).
-__global__ void k_tloss(const float* __restrict__ d, const float* __restrict__ e,
-                        const Crop* __restrict__ crops, float* gd, float* loss, float inv_b) {
+// Coefficient of the upward (up = 1) or downward (up = 0) micro-triangle at
+// crop pixel (ci, cj): from K, or 1 where the triangle exists if K is NULL.
+__device__ __forceinline__ float kval(const float* Kc, const Crop& c, int up, int ci, int cj) {
+  if (ci < 0 || cj < 0 || ci >= kCS || cj >= kCS) return 0.f;
+  if (Kc) return Kc[(up ? 0 : kCS * kCS) + cj * kCS + ci];
+  const int i = c.i0 + ci, j = c.j0 + cj;
+  return (i >= 0 && j >= 0 && i + j <= c.N - (up ? 1 : 2)) ? 1.f : 0.f;
+}
+
+// The six edge weights of the row of pixel (ci, cj): 1/2 cot(opposite angle)
+// (k_T1 + k_T2); order +e1, -e1, +e2, -e2, (+1,-1), (-1,+1).
+__device__ __forceinline__ void row_weights(const FaceRec& F, const float* Kc, const Crop& c, int ci, int cj,
+                                            float w[6]) {
+  const float h0 = 0.5f * (float)F.cot[0], h1 = 0.5f * (float)F.cot[1], h2 = 0.5f * (float)F.cot[2];
+  const float u = kval(Kc, c, 1, ci, cj), uw = kval(Kc, c, 1, ci - 1, cj), us = kval(Kc, c, 1, ci, cj - 1);
+  const float ds = kval(Kc, c, 0, ci, cj - 1), dw = kval(Kc, c, 0, ci - 1, cj), dsw = kval(Kc, c, 0, ci - 1, cj - 1);
+  w[0] = h2 * (u + ds);
+  w[1] = h2 * (uw + dsw);
+  w[2] = h1 * (u + dw);
+  w[3] = h1 * (us + dsw);
+  w[4] = h0 * (us + ds);
+  w[5] = h0 * (uw + dw);
+}
+
+__constant__ int kOffI[6] = {1, -1, 0, 0, 1, -1};
+__constant__ int kOffJ[6] = {0, 0, 1, -1, -1, 1};
+
+// Residual loss of the smoother step d on the normalised scaled residual S:
+// res = Ml (S - D^-1 A d), loss = ||res||^2 / ||Ml S||^2; gradient
+// gd_q = -(2 / den) (res_q - sum_e w_q,e res_{q+e} / diag_{q+e}) on the face
+// interior (A is symmetric, so q's own edge weights give the transposed
+// sum), times 1/B for the batch mean.  One CTA per crop.
+__global__ void k_tloss(const float* __restrict__ d, const float* __restrict__ S, const float* __restrict__ K,
+                        const FaceRec* __restrict__ faces, const Crop* __restrict__ crops, float* gd,
+                        float* loss, float inv_b) {
+  __shared__ float v[kCS * kCS];
+  __shared__ float rs[kCS * kCS];
   __shared__ float red[2][8];
   const Crop c = crops[blockIdx.x];
+  const FaceRec F = faces[c.face];
   const float* dc = d + (int64_t)blockIdx.x * kCS * kCS;
-  const float* ec = e + (int64_t)blockIdx.x * kCS * kCS;
+  const float* sc = S + (int64_t)blockIdx.x * kCS * kCS;
+  const float* Kc = K ? K + (int64_t)blockIdx.x * 2 * kCS * kCS : nullptr;
   float num = 0.f, den = 0.f;
   for (int q = threadIdx.x; q < kCS * kCS; q += blockDim.x) {
     const int cj = q / kCS, ci = q % kCS;
     const bool ml = cj >= kCore && cj < kCS - kCore && ci >= kCore && ci < kCS - kCore &&
                     interior_pt(c.i0 + ci, c.j0 + cj, c.N);
+    float r = 0.f, vv = 0.f;
     if (ml) {
-      const float r = dc[q] - ec[q];
-      num += r * r;
-      den += ec[q] * ec[q];
+      float w[6];
+      row_weights(F, Kc, c, ci, cj, w);
+      float diag = 0.f, acc = 0.f;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        diag += w[e];
+        acc = fmaf(w[e], dc[(cj + kOffJ[e]) * kCS + ci + kOffI[e]], acc);
+      }
+      r = sc[q] - (dc[q] - (diag > 0.f ? acc / diag : 0.f));
+      vv = diag > 0.f ? r / diag : 0.f;
+      num = fmaf(r, r, num);
+      den = fmaf(sc[q], sc[q], den);
     }
+    rs[q] = r;
+    v[q] = vv;
   }
   for (int o = 16; o > 0; o >>= 1) {
     num += __shfl_down_sync(0xffffffffu, num, o);
@@ -357,18 +410,28 @@ __global__ void k_tloss(const float* __restrict__ d, const float* __restrict__ e
   }
   __syncthreads();
   num = den = 0.f;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-    num += red[0][w];
-    den += red[1][w];
+  for (int w8 = 0; w8 < (int)(blockDim.x >> 5); ++w8) {
+    num += red[0][w8];
+    den += red[1][w8];
   }
   const float scale = den > 0.f ? 2.f * inv_b / den : 0.f;
   if (threadIdx.x == 0) loss[blockIdx.x] = den > 0.f ? num / den : 0.f;
   float* g = gd + (int64_t)blockIdx.x * kCS * kCS;
   for (int q = threadIdx.x; q < kCS * kCS; q += blockDim.x) {
     const int cj = q / kCS, ci = q % kCS;
-    const bool ml = cj >= kCore && cj < kCS - kCore && ci >= kCore && ci < kCS - kCore &&
-                    interior_pt(c.i0 + ci, c.j0 + cj, c.N);
-    g[q] = ml ? scale * (dc[q] - ec[q]) : 0.f;
+    float out = 0.f;
+    if (interior_pt(c.i0 + ci, c.j0 + cj, c.N)) {
+      float w[6];
+      row_weights(F, Kc, c, ci, cj, w);
+      float back = 0.f;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        const int ni = ci + kOffI[e], nj = cj + kOffJ[e];
+        if (ni >= 0 && nj >= 0 && ni < kCS && nj < kCS) back = fmaf(w[e], v[nj * kCS + ni], back);
+      }
+      out = -scale * (rs[q] - back);
+    }
+    g[q] = out;
   }
 }
 
@@ -501,11 +564,6 @@ __global__ void k_fill_random(int64_t n, double* v, uint64_t seed) {
   }
 }
 
-__global__ void k_sub(int64_t n, const double* a, const double* b, double* o) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = a[i] - b[i];
-}
-
 }  // namespace
 
 // ================================================================ host
@@ -593,8 +651,8 @@ void learned_step(const Mesh& m, int level, int prec, void* x, const void* b, cu
 }
 
 // Mean loss and gradient over crops (test hook and training step).
-static float grad_on_crops(Mesh& m, int B, const float* X, const float* E, const Crop* crops_dev, float* work,
-                           float* loss_dev, cudaStream_t st) {
+static float grad_on_crops(Mesh& m, int B, const float* X, const float* S, const float* K, const Crop* crops_dev,
+                           float* work, float* loss_dev, cudaStream_t st) {
   Learned& L = learned_of(m);
   load_constants(L, st);
   const int64_t P = (int64_t)kCS * kCS;
@@ -609,7 +667,7 @@ static float grad_on_crops(Mesh& m, int B, const float* X, const float* E, const
   k_tconv_fwd<3, 16, 0><<<grid, TJ * TI, 0, st>>>(X, h1, crops_dev, oW1, ob1);
   k_tconv_fwd<16, 16, 0><<<grid, TJ * TI, 0, st>>>(h1, h2, crops_dev, oW2, ob2);
   k_tconv_fwd<16, 1, 1><<<grid, TJ * TI, 0, st>>>(h2, d, crops_dev, oW3, ob3);
-  k_tloss<<<B, 256, 0, st>>>(d, E, crops_dev, gd, loss_dev, 1.0f / B);
+  k_tloss<<<B, 256, 0, st>>>(d, S, K, m.tab.faces, crops_dev, gd, loss_dev, 1.0f / B);
   const int nblk = std::min(B * (kCS / TJ) * (kCS / TI), 304);
   // layer 3
   k_tconv_bwd_w<16, 1><<<nblk, TJ * TI, 0, st>>>(h2, gd, B, part);
@@ -631,8 +689,8 @@ static size_t work_floats(int B) {
   return (size_t)B * P * (16 + 16 + 1 + 1 + 16 + 16) + (size_t)304 * 2320;
 }
 
-void learned_grad(Mesh& m, int B, const float* X_dev, const float* E_dev, const int* crops_host,
-                  float* grad_host, float* loss_host, cudaStream_t st) {
+void learned_grad(Mesh& m, int B, const float* X_dev, const float* S_dev, const float* K_dev,
+                  const int* crops_host, float* grad_host, float* loss_host, cudaStream_t st) {
   Learned& L = learned_of(m);
   std::vector<Crop> cr(B);
   for (int b = 0; b < B; ++b) cr[b] = Crop{crops_host[4 * b], crops_host[4 * b + 1], crops_host[4 * b + 2], crops_host[4 * b + 3]};
@@ -643,7 +701,9 @@ void learned_grad(Mesh& m, int B, const float* X_dev, const float* E_dev, const 
   check_cuda(cudaMalloc(&work, work_floats(B) * sizeof(float)), "alloc");
   check_cuda(cudaMalloc(&loss, B * sizeof(float)), "alloc");
   check_cuda(cudaMemcpyAsync(cd, cr.data(), B * sizeof(Crop), cudaMemcpyHostToDevice, st), "crops");
-  grad_on_crops(m, B, X_dev, E_dev, cd, work, loss, st);
+  for (const Crop& c : cr)
+    if (c.face < 0 || c.face >= m.nf) throw std::invalid_argument("crop face out of range");
+  grad_on_crops(m, B, X_dev, S_dev, K_dev, cd, work, loss, st);
   std::vector<float> lh(B);
   check_cuda(cudaMemcpyAsync(grad_host, L.g, kNP * sizeof(float), cudaMemcpyDeviceToHost, st), "grad");
   check_cuda(cudaMemcpyAsync(lh.data(), loss, B * sizeof(float), cudaMemcpyDeviceToHost, st), "loss");
@@ -654,22 +714,6 @@ void learned_grad(Mesh& m, int B, const float* X_dev, const float* E_dev, const 
   cudaFree(cd);
   cudaFree(work);
   cudaFree(loss);
-}
-
-// FP64 multigrid solve on level l (host loop, used for training data).
-static void solve_fp64(Mesh& m, int l, double* x, const double* b, double tol, cudaStream_t st) {
-  const LevelData& ld = m.levels[l];
-  residual_op(m, l, 0, x, b, ld.r[0], m.scalars, st);
-  double r0 = 0.0, r = 0.0;
-  check_cuda(cudaMemcpyAsync(&r0, m.scalars, 8, cudaMemcpyDeviceToHost, st), "norm");
-  check_cuda(cudaStreamSynchronize(st), "sync");
-  r = r0;
-  for (int it = 0; it < 60 && r > tol * tol * r0; ++it) {
-    vcycle_run(m, l, 0, x, b, 3, 3, 0, st);
-    residual_op(m, l, 0, x, b, ld.r[0], m.scalars, st);
-    check_cuda(cudaMemcpyAsync(&r, m.scalars, 8, cudaMemcpyDeviceToHost, st), "norm");
-    check_cuda(cudaStreamSynchronize(st), "sync");
-  }
 }
 
 // Generates n_pairs crops from FP64 V-cycle iterates on level l and trains
@@ -691,15 +735,16 @@ void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr,
   const int N = lv.N;
   if (N < kCS) throw std::invalid_argument("training level too coarse for 64 x 64 crops");
   const int64_t len = lv.len;
-  double *b = nullptr, *xs = nullptr, *x = nullptr, *e = nullptr;
-  float *X = nullptr, *E = nullptr, *work = nullptr, *loss = nullptr;
+  double *b = nullptr, *x = nullptr;
+  float *X = nullptr, *E = nullptr, *K = nullptr, *work = nullptr, *loss = nullptr;
   Crop* crops = nullptr;
   const int snapshots = 12;
   const int per_snap = (n_pairs + snapshots - 1) / snapshots;
   const int total = per_snap * snapshots;
-  for (double** p : {&b, &xs, &x, &e}) check_cuda(cudaMalloc(p, len * sizeof(double)), "alloc");
+  for (double** p : {&b, &x}) check_cuda(cudaMalloc(p, len * sizeof(double)), "alloc");
   check_cuda(cudaMalloc(&X, (size_t)total * 3 * kCS * kCS * sizeof(float)), "alloc X");
-  check_cuda(cudaMalloc(&E, (size_t)total * kCS * kCS * sizeof(float)), "alloc E");
+  check_cuda(cudaMalloc(&E, (size_t)total * kCS * kCS * sizeof(float)), "alloc S");
+  check_cuda(cudaMalloc(&K, (size_t)total * 2 * kCS * kCS * sizeof(float)), "alloc K");
   check_cuda(cudaMalloc(&crops, (size_t)total * sizeof(Crop)), "alloc crops");
   check_cuda(cudaMalloc(&work, work_floats(batch) * sizeof(float)), "alloc work");
   check_cuda(cudaMalloc(&loss, batch * sizeof(float)), "alloc loss");
@@ -715,10 +760,8 @@ void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr,
     hc[q] = Crop{(int)(rng() % (uint64_t)m.nf), ci - kCS / 2, cj - kCS / 2, N};
   }
   check_cuda(cudaMemcpyAsync(crops, hc.data(), total * sizeof(Crop), cudaMemcpyHostToDevice, st), "crops");
-  // x* for a random right-hand side
+  // a random right-hand side
   k_fill_random<<<1024, 256, 0, st>>>(len, b, seed);
-  check_cuda(cudaMemsetAsync(xs, 0, len * sizeof(double), st), "zero");
-  solve_fp64(m, l, xs, b, 1e-12, st);
   const float* kf = m.vark ? (const float*)ld.k[1] : nullptr;
   float* s = (float*)ld.r[1];
   for (int snap = 0; snap < snapshots; ++snap) {
@@ -728,10 +771,10 @@ void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr,
     }
     vcycle_run(m, l, 0, x, b, 3, 3, 0, st);
     scaled_residual(m, l, 0, x, b, s, st);
-    k_sub<<<1024, 256, 0, st>>>(len, xs, x, e);
-    k_extract<<<dim3(4, per_snap), 256, 0, st>>>(m.tab, lv, s, kf, e, crops + (size_t)snap * per_snap,
+    k_extract<<<dim3(4, per_snap), 256, 0, st>>>(m.tab, lv, s, kf, crops + (size_t)snap * per_snap,
                                                   X + (size_t)snap * per_snap * 3 * kCS * kCS,
-                                                  E + (size_t)snap * per_snap * kCS * kCS);
+                                                  E + (size_t)snap * per_snap * kCS * kCS,
+                                                  K + (size_t)snap * per_snap * 2 * kCS * kCS);
     k_crop_normalise<<<per_snap, 256, 0, st>>>(crops + (size_t)snap * per_snap,
                                                X + (size_t)snap * per_snap * 3 * kCS * kCS,
                                                E + (size_t)snap * per_snap * kCS * kCS);
@@ -747,7 +790,8 @@ void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr,
     double ep_loss = 0.0;
     for (int q = 0; q < nb; ++q) {
       const size_t off = (size_t)order[q] * batch;
-      grad_on_crops(m, batch, X + off * 3 * kCS * kCS, E + off * kCS * kCS, crops + off, work, loss, st);
+      grad_on_crops(m, batch, X + off * 3 * kCS * kCS, E + off * kCS * kCS, K + off * 2 * kCS * kCS, crops + off,
+                    work, loss, st);
       L.step += 1;
       const float c1 = 1.f - std::pow(0.9f, (float)L.step), c2 = 1.f - std::pow(0.999f, (float)L.step);
       k_adam<<<(kNP + 255) / 256, 256, 0, st>>>(L.w, L.g, L.m, L.v, kNP, lr, 0.9f, 0.999f, c1, c2, 1e-8f, L.wr);
@@ -759,7 +803,8 @@ void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr,
     if (loss_hist) loss_hist[ep] = (float)(ep_loss / ((double)nb * batch));
   }
   L.trained = true;
-  for (void* p : {(void*)b, (void*)xs, (void*)x, (void*)e, (void*)X, (void*)E, (void*)crops, (void*)work, (void*)loss}) cudaFree(p);
+  for (void* p : {(void*)b, (void*)x, (void*)X, (void*)E, (void*)K, (void*)crops, (void*)work, (void*)loss})
+    cudaFree(p);
 }
 
 }  // namespace hhg

@@ -85,7 +85,7 @@ _SIGS = {
     "hhg_learned_set_weights": [_P, C.POINTER(C.c_float), C.c_int64],
     "hhg_learned_get_weights": [_P, C.POINTER(C.c_float), C.c_int64],
     "hhg_learned_apply": [_P, C.c_int32, C.c_int32, _P, _P, _P, _P],
-    "hhg_learned_grad": [_P, C.c_int32, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float),
+    "hhg_learned_grad": [_P, C.c_int32, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float),
                          C.POINTER(C.c_float), _P],
     "hhg_learned_train": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_uint64,
                           C.POINTER(C.c_float), _P],
@@ -239,11 +239,11 @@ class Mesh:
     def learned_apply(self, level, s, x=None, d=None, prec=F64, stream=None):
         _check(lib.hhg_learned_apply(self.h, level, prec, _ptr(s), _ptr(x), _ptr(d), _stream(stream)))
 
-    def learned_grad(self, X, E, crops, stream=None):
+    def learned_grad(self, X, S, crops, K=None, stream=None):
         crops = np.ascontiguousarray(crops, dtype=np.int32).reshape(-1, 4)
         g = np.zeros(LEARNED_NPARAMS, dtype=np.float32)
         loss = np.zeros(1, dtype=np.float32)
-        _check(lib.hhg_learned_grad(self.h, crops.shape[0], _ptr(X), _ptr(E),
+        _check(lib.hhg_learned_grad(self.h, crops.shape[0], _ptr(X), _ptr(S), _ptr(K),
                                     crops.ctypes.data_as(C.POINTER(C.c_int32)),
                                     g.ctypes.data_as(C.POINTER(C.c_float)),
                                     loss.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)))

@@ -47,7 +47,18 @@ def test_cnn_forward_parity(vark):
     P.close()
 
 
-def test_weight_gradient_parity():
+def _cots(xy, tri, f):
+    v0, v1, v2 = xy[tri[f]]
+    def cot(a, b, c):
+        u, w = b - a, c - a
+        return (u @ w) / abs(u[0] * w[1] - u[1] * w[0])
+    return (cot(v0, v1, v2), cot(v1, v2, v0), cot(v2, v0, v1))
+
+
+@pytest.mark.parametrize("with_k", [False, True])
+def test_weight_gradient_parity(with_k):
+    """GPU forward/backward (BF16 activations, FP32 accumulation) of the
+    residual loss against the FP64 oracle on random crops."""
     torch = pytest.importorskip("torch")
     from paper_1805_10167_gb300 import hhg
     xy, tri = inputs.annulus_mesh(32, 2)
@@ -59,21 +70,30 @@ def test_weight_gradient_parity():
     crops = [(0, -10, 5, N), (3, 20, 12, N), (5, 1, 1, N), (9, 0, 30, N)]
     B = len(crops)
     X = np.zeros((B, 3, 64, 64))
-    E = np.zeros((B, 64, 64))
+    S = np.zeros((B, 64, 64))
+    K = np.zeros((B, 2, 64, 64))
+    core = np.zeros((64, 64))
+    core[3:61, 3:61] = 1.0
     Lsum, gsum = 0.0, None
     for b, (f, i0, j0, NN) in enumerate(crops):
         M, Mi = learned.masks(NN, i0, j0, 64, 64)
         X[b] = rng.standard_normal((3, 64, 64)) * M
-        E[b] = rng.standard_normal((64, 64)) * Mi
-        core = np.zeros((64, 64))
-        core[3:61, 3:61] = 1.0
-        Lb, gb = learned.loss_and_grad(p, X[b], M, Mi, E[b], Mi * core)
+        S[b] = rng.standard_normal((64, 64)) * Mi
+        jj = np.arange(j0, j0 + 64)[:, None]
+        ii = np.arange(i0, i0 + 64)[None, :]
+        up = ((ii >= 0) & (jj >= 0) & (ii + jj <= NN - 1)).astype(float)
+        dn = ((ii >= 0) & (jj >= 0) & (ii + jj <= NN - 2)).astype(float)
+        if with_k:
+            up = up * rng.uniform(0.5, 2.0, (64, 64))
+            dn = dn * rng.uniform(0.5, 2.0, (64, 64))
+        K[b, 0], K[b, 1] = up, dn
+        wts = learned.edge_weights(_cots(xy, tri, f), up, dn)
+        Lb, gb = learned.residual_loss_and_grad(p, X[b], M, Mi, S[b], Mi * core, wts)
         Lsum += Lb / B
         gv = learned.flatten(gb) / B
         gsum = gv if gsum is None else gsum + gv
-    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
-    Ed = torch.tensor(E, dtype=torch.float32, device="cuda")
-    loss, grad = g.learned_grad(Xd, Ed, np.array(crops))
+    T = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    loss, grad = g.learned_grad(T(X), T(S), np.array(crops), K=T(K) if with_k else None)
     assert loss == pytest.approx(Lsum, rel=BF16_TOL)
     gpu = learned.unflatten(grad.astype(np.float64))
     ref = learned.unflatten(gsum)

@@ -140,3 +140,68 @@ def test_fgmres_with_vcycle_preconditioner_converges_monotonically():
     assert hist[-1] <= 1e-10 * hist[0]
     assert np.all(np.diff(hist) <= 1e-12 * hist[0])
     assert steps < 20
+
+
+def test_residual_loss_gradient_equals_central_differences():
+    X, M, Mi, e = small_case(8, N=9)
+    rng = np.random.default_rng(9)
+    ku = rng.uniform(0.5, 2.0, M.shape) * M
+    kd = rng.uniform(0.5, 2.0, M.shape) * M
+    wts = learned.edge_weights((0.4, 0.9, 0.6), ku, kd)
+    shat = rng.standard_normal(M.shape) * Mi
+    p = learned.init_params(11)
+    p["W3"] = p["W3"] * 10
+    L, g = learned.residual_loss_and_grad(p, X, M, Mi, shat, Mi, wts)
+    v0, gv = learned.flatten(p), learned.flatten(g)
+    for t in np.random.default_rng(12).choice(v0.size, 40, replace=False):
+        vp, vm = v0.copy(), v0.copy()
+        vp[t] += 1e-6
+        vm[t] -= 1e-6
+        fd = (learned.residual_loss_and_grad(learned.unflatten(vp), X, M, Mi, shat, Mi, wts)[0]
+              - learned.residual_loss_and_grad(learned.unflatten(vm), X, M, Mi, shat, Mi, wts)[0]) / 2e-6
+        assert fd == pytest.approx(gv[t], rel=1e-5, abs=1e-8)
+
+
+def test_scaled_operator_matches_assembled_rows():
+    """D^-1 A on a face lattice built from the cotangent weights equals the
+    brute-force assembled matrix rows (divided by the diagonal) at interior
+    points, for a random coefficient."""
+    xy, tri = inputs.annulus_mesh(32, 2)
+    M_ = om.MacroMesh(xy, tri)
+    L = 3
+    lv = om.Level(M_, L)
+    N = lv.N
+    rng = np.random.default_rng(13)
+    k = rng.uniform(0.5, 2.0, M_.nf * N * N)
+    from oracle import fem
+    A = fem.assemble(lv, k).tocsr()
+    dvec = rng.standard_normal(lv.n)
+    import math
+    f = 5
+    v0, v1, v2 = xy[M_.tri[f]]
+
+    def cot(a, b, c):
+        u, w = b - a, c - a
+        return (u @ w) / abs(u[0] * w[1] - u[1] * w[0])
+    cots = (cot(v0, v1, v2), cot(v1, v2, v0), cot(v2, v0, v1))
+    Mc, Mi = learned.masks(N)
+    ku = np.zeros((N + 1, N + 1))
+    kd = np.zeros((N + 1, N + 1))
+    kf = k[f * N * N:(f + 1) * N * N]
+    r = 0
+    for j in range(N):
+        for i in range(N - j):
+            ku[j, i] = kf[r]
+            r += 1
+    for j in range(N - 1):
+        for i in range(N - 1 - j):
+            kd[j, i] = kf[r]
+            r += 1
+    G = lv.face_ids[f]
+    img = np.zeros((N + 1, N + 1))
+    img[G >= 0] = dvec[G[G >= 0]]
+    out = learned.scaled_operator(img, learned.edge_weights(cots, ku, kd))
+    want = (A @ dvec) / A.diagonal()
+    for j in range(1, N - 1):
+        for i in range(1, N - j):
+            assert out[j, i] == pytest.approx(want[G[j, i]], rel=1e-12, abs=1e-12)
