@@ -11,7 +11,10 @@ from paper_1805_10167_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-BF16_TOL = 3e-2    # BF16 rounding of inputs, weights and activations (unit roundoff 2^-8)
+# BF16 rounding of inputs, weights and activations (unit roundoff u = 2^-8):
+# the deepest gradient (W1) passes through about eight rounded quantities
+# and the ReLU masks they decide, so 8u ~ 3e-2 bounds every comparison
+BF16_TOL = 3e-2
 
 
 def _weights(seed=1):
@@ -100,7 +103,7 @@ def test_weight_gradient_parity(with_k):
     for k in learned.ORDER:
         e = np.linalg.norm(gpu[k] - ref[k]) / np.linalg.norm(ref[k])
         print(f"gradient {k}: relative error {e:.3e}")
-        assert e < 2e-2, k
+        assert e < BF16_TOL, k
     g.close()
 
 
