@@ -95,11 +95,24 @@ def conv_backward(x, W, gout):
     return gx, gW, gb
 
 
-def forward(p, X, M, Mi):
+def bf16(x):
+    """Round to bfloat16 (8 significant bits, round to nearest even) and back:
+    the float32 bit pattern rounded at bit 16."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(p, X, M, Mi, round_bf16=False):
+    """round_bf16: weights, biases and hidden activations rounded to BF16
+    where the GPU kernels round them (the FP64 network otherwise)."""
+    if round_bf16:
+        p = {k: bf16(v) for k, v in p.items()}
+    r = bf16 if round_bf16 else (lambda v: v)
     a1 = conv(X, p["W1"], p["b1"])
-    h1 = M * np.maximum(a1, 0.0)
+    h1 = r(M * np.maximum(a1, 0.0))
     a2 = conv(h1, p["W2"], p["b2"])
-    h2 = M * np.maximum(a2, 0.0)
+    h2 = r(M * np.maximum(a2, 0.0))
     d = Mi * conv(h2, p["W3"], p["b3"])[0]
     return d, (X, a1, h1, a2, h2)
 
@@ -199,10 +212,13 @@ def scaled_operator(d, wts):
         return d - np.where(diag > 0, acc / diag, 0.0)
 
 
-def residual_loss_and_grad(p, X, M, Mi, shat, Ml, wts):
+def residual_loss_and_grad(p, X, M, Mi, shat, Ml, wts, round_bf16=False):
     """Loss ||Ml (shat - D^-1 A d)||^2 / ||Ml shat||^2 of the smoother step d
-    on the normalised scaled residual shat, and its gradient."""
-    d, (X, a1, h1, a2, h2) = forward(p, X, M, Mi)
+    on the normalised scaled residual shat, and its gradient (w.r.t. the
+    weights as used: rounded ones under round_bf16)."""
+    d, (X, a1, h1, a2, h2) = forward(p, X, M, Mi, round_bf16)
+    if round_bf16:
+        p = {k: bf16(v) for k, v in p.items()}
     den = float(np.sum(Ml * shat * shat))
     res = Ml * (shat - scaled_operator(d, wts))
     L = float(np.sum(res * res)) / den

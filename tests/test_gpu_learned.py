@@ -77,10 +77,10 @@ def test_weight_gradient_parity(with_k):
     K = np.zeros((B, 2, 64, 64))
     core = np.zeros((64, 64))
     core[3:61, 3:61] = 1.0
-    Lsum, gsum = 0.0, None
+    Lsum, gsum, g16 = 0.0, None, None
     for b, (f, i0, j0, NN) in enumerate(crops):
         M, Mi = learned.masks(NN, i0, j0, 64, 64)
-        X[b] = rng.standard_normal((3, 64, 64)) * M
+        X[b] = learned.bf16(rng.standard_normal((3, 64, 64)) * M)
         S[b] = rng.standard_normal((64, 64)) * Mi
         jj = np.arange(j0, j0 + 64)[:, None]
         ii = np.arange(i0, i0 + 64)[None, :]
@@ -95,15 +95,23 @@ def test_weight_gradient_parity(with_k):
         Lsum += Lb / B
         gv = learned.flatten(gb) / B
         gsum = gv if gsum is None else gsum + gv
+        _, gq = learned.residual_loss_and_grad(p, X[b], M, Mi, S[b], Mi * core, wts, round_bf16=True)
+        gq = learned.flatten(gq) / B
+        g16 = gq if g16 is None else g16 + gq
     T = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
     loss, grad = g.learned_grad(T(X), T(S), np.array(crops), K=T(K) if with_k else None)
     assert loss == pytest.approx(Lsum, rel=BF16_TOL)
     gpu = learned.unflatten(grad.astype(np.float64))
     ref = learned.unflatten(gsum)
+    ref16 = learned.unflatten(g16)
     for k in learned.ORDER:
-        e = np.linalg.norm(gpu[k] - ref[k]) / np.linalg.norm(ref[k])
-        print(f"gradient {k}: relative error {e:.3e}")
-        assert e < BF16_TOL, k
+        e64 = np.linalg.norm(gpu[k] - ref[k]) / np.linalg.norm(ref[k])
+        e16 = np.linalg.norm(gpu[k] - ref16[k]) / np.linalg.norm(ref16[k])
+        print(f"gradient {k}: vs BF16-emulating oracle {e16:.2e}, vs FP64 oracle {e64:.2e}")
+        # same roundings as the oracle's BF16 emulation: only FP32 accumulation
+        # order (and an occasional ReLU flip of a value at zero) differ
+        assert e16 < 2e-3, k
+        assert e64 < 2 * BF16_TOL, k      # BF16 error of the network itself
     g.close()
 
 
