@@ -216,7 +216,8 @@ def timed_solve(g, level, b, st, **kw):
     it = rep["iterations"]
     return {"seconds": dt, "iterations": it, "rel_residual": rep["r_final"] / rep["r0"],
             "factor_per_iteration": (rep["r_final"] / rep["r0"]) ** (1.0 / max(it, 1)),
-            "smoother_used": ["gs", "learned"][rep.get("smoother_used", 0)]}
+            "smoother_used": ["gs", "learned"][rep.get("smoother_used", 0)],
+            "judge": [rep.get("judge_learned", 0.0), rep.get("judge_gs", 0.0)]}
 
 
 def run_vark(args, dev, st):

@@ -119,6 +119,9 @@ typedef struct {
   int32_t history_cap;    /* its capacity (entries written: min(cap, it+1))   */
   int32_t smoother_used;  /* FGMRES: smoother kept by the judge (learned ->  */
                           /* GS when the CNN reduced the residual less)      */
+  double judge_learned;   /* FGMRES judge: ||v1 - A M(v1)|| with the learned */
+  double judge_gs;        /* and with the Gauss-Seidel preconditioner (0 if  */
+                          /* no judgement was made)                          */
 } hhg_solve_report;
 
 /* Build the macro-primitive graph (Sec. 2.1), the level hierarchy 0..max_level
@@ -310,7 +313,7 @@ hhg_status hhg_learned_grad(hhg_mesh mesh, int32_t n_crops, const float* X, cons
                             const float* K, const int32_t* crops_host, float* grad_host,
                             float* loss_host, void* stream);
 /* Generates n_pairs training crops on `level` (level >= 6) from FP64
- * V(3,3) iterates x_k, k = 1..6, of random starts for a random right-hand
+ * V(3,3) iterates x_k, k = 0..5, of random starts for a random right-hand
  * side -- residual/error pairs r = b - A x_k = A e -- and trains the network
  * on the loss of hhg_learned_grad for `epochs` passes with Adam
  * (lr, beta 0.9 / 0.999, mini-batches of `batch` crops; weights initialised

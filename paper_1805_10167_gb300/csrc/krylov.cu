@@ -134,6 +134,7 @@ void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_op
   int use = smoother;
   bool judged = false;
   std::vector<double> Hh((size_t)(restart + 1) * restart), cs(restart), sn(restart), gv(restart + 1), y(restart);
+  if (rep) rep->judge_learned = rep->judge_gs = 0.0;
   while (beta > o.tol * r0 && r0 > 0.0) {
     if (steps >= o.max_iter) {
       status = HHG_ERR_NOT_CONVERGED;
@@ -149,6 +150,10 @@ void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_op
       const double q_gs = precond_quality(m, L, K.V[0], K.w, tmp, st);
       if (!(q_learned <= q_gs)) use = 0;
       judged = true;
+      if (rep) {
+        rep->judge_learned = q_learned;
+        rep->judge_gs = q_gs;
+      }
     }
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;

@@ -13,8 +13,8 @@
 // memory so that every FMA takes its weight as a broadcast operand; the
 // master copy (FP32) and Adam state live in device memory.
 //
-// The residual channel is divided by its RMS over the face (per crop in
-// training) and the output multiplied back, so the step is homogeneous of
+// The residual channel is divided by its RMS over the face (in training
+// and in use) and the output multiplied back, so the step is homogeneous of
 // degree 1 in the residual, as an error estimate must be.
 //
 // Training (all on the GPU): residual/error pairs of FP64 V-cycle iterates
@@ -228,36 +228,16 @@ __global__ void k_face_rms(MeshTables M, LevelView L, const float* __restrict__ 
   }
 }
 
-// Training crops: the scaled residual divided by its RMS over the crop's
-// closed-lattice pixels (the smoother is homogeneous of degree 1 in the
-// residual): S <- S / sigma, input channel 0 <- BF16(S / sigma).
-__global__ void k_crop_normalise(const Crop* __restrict__ crops, float* X, float* S) {
-  __shared__ float red[2][8];
+// Training crops: the scaled residual divided by the residual scale of its
+// face (the same per-face RMS the smoother uses): S <- S / sigma_face,
+// input channel 0 <- BF16(S / sigma_face).
+__global__ void k_crop_normalise(const Crop* __restrict__ crops, const float* __restrict__ face_scale, float* X,
+                                 float* S) {
   const Crop c = crops[blockIdx.x];
+  const float sig = face_scale[c.face];
+  const float inv = sig > 0.f ? 1.f / sig : 0.f;
   float* x0 = X + (int64_t)blockIdx.x * 3 * kCS * kCS;
   float* sc = S + (int64_t)blockIdx.x * kCS * kCS;
-  float acc = 0.f, cnt = 0.f;
-  for (int q = threadIdx.x; q < kCS * kCS; q += blockDim.x)
-    if (closed_pt(c.i0 + q % kCS, c.j0 + q / kCS, c.N)) {
-      acc = fmaf(sc[q], sc[q], acc);
-      cnt += 1.f;
-    }
-  for (int o = 16; o > 0; o >>= 1) {
-    acc += __shfl_down_sync(0xffffffffu, acc, o);
-    cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = acc;
-    red[1][threadIdx.x >> 5] = cnt;
-  }
-  __syncthreads();
-  acc = cnt = 0.f;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-    acc += red[0][w];
-    cnt += red[1][w];
-  }
-  const float sig = cnt > 0.f ? sqrtf(acc / cnt) : 0.f;
-  const float inv = sig > 0.f ? 1.f / sig : 0.f;
   for (int q = threadIdx.x; q < kCS * kCS; q += blockDim.x) {
     sc[q] *= inv;
     x0[q] = bf16r(sc[q]);
@@ -765,17 +745,19 @@ void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr,
   const float* kf = m.vark ? (const float*)ld.k[1] : nullptr;
   float* s = (float*)ld.r[1];
   for (int snap = 0; snap < snapshots; ++snap) {
-    if (snap % 6 == 0) {   // fresh random start; snapshot k of a start has k cycles (1..6)
+    if (snap % 6 == 0) {   // fresh random start; snapshot k of a start follows k cycles (0..5)
       k_fill_random<<<1024, 256, 0, st>>>(len, x, seed + 1000 + snap);
       zero_dirichlet_and_ghosts(m, l, x, st);
+    } else {
+      vcycle_run(m, l, 0, x, b, 3, 3, 0, st);
     }
-    vcycle_run(m, l, 0, x, b, 3, 3, 0, st);
     scaled_residual(m, l, 0, x, b, s, st);
+    k_face_rms<<<m.nf, 256, 0, st>>>(m.tab, lv, s, L.scale);
     k_extract<<<dim3(4, per_snap), 256, 0, st>>>(m.tab, lv, s, kf, crops + (size_t)snap * per_snap,
                                                   X + (size_t)snap * per_snap * 3 * kCS * kCS,
                                                   E + (size_t)snap * per_snap * kCS * kCS,
                                                   K + (size_t)snap * per_snap * 2 * kCS * kCS);
-    k_crop_normalise<<<per_snap, 256, 0, st>>>(crops + (size_t)snap * per_snap,
+    k_crop_normalise<<<per_snap, 256, 0, st>>>(crops + (size_t)snap * per_snap, L.scale,
                                                X + (size_t)snap * per_snap * 3 * kCS * kCS,
                                                E + (size_t)snap * per_snap * kCS * kCS);
     check_cuda(cudaGetLastError(), "extract");

@@ -52,7 +52,8 @@ class SolveOpts(C.Structure):
 class SolveReport(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("r0", C.c_double),
                 ("r_final", C.c_double), ("history", C.POINTER(C.c_double)),
-                ("history_cap", C.c_int32), ("smoother_used", C.c_int32)]
+                ("history_cap", C.c_int32), ("smoother_used", C.c_int32),
+                ("judge_learned", C.c_double), ("judge_gs", C.c_double)]
 
 
 _P = C.c_void_p
@@ -267,10 +268,11 @@ class Mesh:
         """Returns (status, report dict)."""
         o = SolveOpts(mode, nu1, nu2, max_iter, tol, smoother, restart)
         hist = (C.c_double * (max_iter + 1))()
-        rep = SolveReport(0, 0, 0.0, 0.0, hist if history else None, max_iter + 1 if history else 0, 0)
+        rep = SolveReport(0, 0, 0.0, 0.0, hist if history else None, max_iter + 1 if history else 0, 0, 0.0, 0.0)
         st = lib.hhg_solve(self.h, level, _ptr(x), _ptr(b), C.byref(o), C.byref(rep), _stream(stream))
         out = {"iterations": rep.iterations, "status": rep.status, "r0": rep.r0,
                "r_final": rep.r_final, "smoother_used": rep.smoother_used,
+               "judge_learned": rep.judge_learned, "judge_gs": rep.judge_gs,
                "history": [hist[i] for i in range(min(rep.iterations + 1, max_iter + 1))]}
         if raise_on_error and st != OK:
             raise HHGError(st, last_error())

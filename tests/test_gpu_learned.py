@@ -158,5 +158,6 @@ def test_training_lowers_loss_and_learned_fgmres_converges():
         rates[name] = (rep["r_final"] / rep["r0"]) ** (1.0 / max(rep["iterations"], 1))
         rates[name + "_used"] = rep["smoother_used"]
         rates[name + "_steps"] = rep["iterations"]
+        rates[name + "_judge"] = (rep["judge_learned"], rep["judge_gs"])
     print("FGMRES per-step factors:", rates)
     g.close()
