@@ -38,6 +38,10 @@ METRIC = "GDoF/s per V-cycle & time to 1e-10 FP64 residual: mixed/learned vs FP6
 UNIT = "GDoF/s"
 FP64_OPS_PER_CLK_SM = 2           # FP64 add/mul/fma per clock per SM (probe: 598 G DFMA/s at 1995 MHz)
 N_SM = 152
+# dram__bytes_read.sum + dram__bytes_write.sum of one level-9 launch of the
+# FP64 face sweep (annulus, 128 faces), per (kernel variant, split), from the
+# ncu captures summarised under profiles/; None until captured
+TRAFFIC_L9 = {}
 
 
 def parse():
@@ -340,7 +344,7 @@ def run_ours(args):
     ms = max_over_ranks(e0.elapsed_time(e1))
     value = world * n_free * args.steps / (ms / 1e3) / 1e9
 
-    # dominant kernel: the fused three-colour face Gauss-Seidel sweep on level L
+    # dominant kernel: the three-colour face Gauss-Seidel sweep on level L
     # (6 launches per V(3,3) cycle).  For k = 1 each interior point costs 7
     # FP64 instructions (3 add, 1 mul, 3 fma) and 24 algorithmic bytes (read
     # x and b, write x); the sweep is FP64-pipe bound on GB300.
@@ -358,10 +362,15 @@ def run_ours(args):
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    # DRAM traffic of one launch from the ncu capture at level 9 (profiles/
-    # k_face_gs3_fp64_annulus128_L9.md), scaled by the 4x points of level 10
-    traffic = (287.764224e6 + 106.255872e6) * (pts / 16760832.0) if L in (9, 10) else None
-    roofline = {"bound": "alu", "kernel": f"k_face_gs3<double> fused 3-colour sweep, level {L}",
+    variant, split = g.sweep_config(L, hhg.F64)
+    kname = ("k_face_gs_strip<double> register-strip sweep, %d-row tasks" % split if variant == hhg.SWEEP_STRIP
+             else "k_face_gs3<double> shared-memory ring sweep, %d row blocks per face" % split)
+    # DRAM traffic of one launch from the ncu capture of this kernel at level 9
+    # (profiles/), scaled by the points of level L
+    traffic = TRAFFIC_L9.get((variant, split))
+    if traffic is not None:
+        traffic *= pts / 16760832.0
+    roofline = {"bound": "alu", "kernel": f"{kname}, level {L}",
                 "achieved": achieved, "peak": peak, "unit": "G FP64-instr/s", "frac": achieved / peak,
                 "traffic": traffic, "ops_per_launch": ops, "ms_per_launch": gs_ms,
                 "peak_basis": f"{N_SM} SMs x {FP64_OPS_PER_CLK_SM} FP64 instr/clk x {sm_mhz:.0f} MHz (sampled)",

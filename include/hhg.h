@@ -225,12 +225,25 @@ hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
 hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
                      const hhg_solve_opts* opts, hhg_solve_report* rep, void* stream);
 
-/* Autotuner: for every level >= 2 times candidate row-block splits of the
- * fused face Gauss-Seidel sweep in precision `prec` and keeps the fastest
- * (results do not depend on the split).  If the environment variable
- * HHG_TUNE_CACHE names a file, choices are read from and appended to it.
- * Synchronous. */
+/* Face Gauss-Seidel kernels (the face phase of the multi-colour sweep,
+ * Sec. 3.2): HHG_SWEEP_RING = one CTA per block of face rows, rows staged in
+ * a shared-memory ring by bulk copies, param = row blocks per face;
+ * HHG_SWEEP_STRIP = one warp per 90-column strip of a face with its rows in
+ * registers, param = rows per strip task.  Results are the same for every
+ * kernel and split. */
+typedef enum { HHG_SWEEP_RING = 0, HHG_SWEEP_STRIP = 1 } hhg_sweep_variant;
+
+/* Autotuner: for every level >= 4 times the candidate kernels and splits of
+ * the face sweep in precision `prec` and keeps the fastest.  If the
+ * environment variable HHG_TUNE_CACHE names a file, choices are read from
+ * and appended to it.  Synchronous. */
 hhg_status hhg_tune(hhg_mesh mesh, hhg_prec prec, void* stream);
+
+/* Sets (set != 0: *variant, *param are inputs, param >= 1) or reads
+ * (set == 0: written) the face-sweep kernel of one level and precision.
+ * Synchronous with respect to the host (the task list is uploaded). */
+hhg_status hhg_sweep_config(hhg_mesh mesh, int32_t level, hhg_prec prec, int32_t set,
+                            int32_t* variant, int32_t* param);
 
 /* Batches of independent problems (not in the paper: its multigrid solves
  * one problem at a time).  Problem p is a macro mesh (xy[p]: nv[p] x 2 host

@@ -30,40 +30,51 @@ static std::string tune_key(const Mesh& m, int level, int prec) {
   return k.str();
 }
 
-static std::map<std::string, int> read_cache(const char* path) {
-  std::map<std::string, int> c;
+// cache lines "key|variant param"
+static std::map<std::string, std::pair<int, int>> read_cache(const char* path) {
+  std::map<std::string, std::pair<int, int>> c;
   if (!path) return c;
   std::ifstream in(path);
   std::string line;
   while (std::getline(in, line)) {
     const size_t bar = line.rfind('|');
     if (bar == std::string::npos) continue;
-    c[line.substr(0, bar)] = std::atoi(line.c_str() + bar + 1);
+    int v = 0, p = 0;
+    if (std::sscanf(line.c_str() + bar + 1, "%d %d", &v, &p) != 2) continue;
+    if ((v != SWEEP_RING && v != SWEEP_STRIP) || p < 1) continue;
+    c[line.substr(0, bar)] = {v, p};
   }
   return c;
 }
 
+// Picks the face-sweep kernel and its work split for one level and precision
+// by timing every candidate (three sweeps each, after one warm-up) on the
+// level's own workspaces; the choice never changes results.  Returns the
+// encoded choice variant * 10000 + param.
 int tune_face_sweep(Mesh& m, int level, int prec, cudaStream_t st) {
   LevelData& ld = m.levels[level];
   const int N = ld.lv.N;
-  if (N < 16) return ld.face_tasks_per_face;
+  SweepCfg& cur = ld.sweep[prec];
+  if (N < 16) return cur.variant * 10000 + cur.param;
   const char* cache_path = std::getenv("HHG_TUNE_CACHE");
   const std::string key = tune_key(m, level, prec);
   auto cache = read_cache(cache_path);
   if (cache.count(key)) {
-    set_face_tasks(m, level, cache[key]);
-    return cache[key];
+    set_sweep(m, level, prec, cache[key].first, cache[key].second);
+    return cache[key].first * 10000 + cache[key].second;
   }
-  const int cand_all[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
-  const int max_per_face = std::max(1, (N + 1) / 16);
+  std::vector<std::pair<int, int>> cands;
+  for (int c : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
+    if (c <= std::max(1, (N + 1) / 16)) cands.push_back({SWEEP_RING, c});
+  for (int h : {16, 32, 64, 128, 256, 512, 1024})
+    if (h <= 2 * (N + 1)) cands.push_back({SWEEP_STRIP, h});
   cudaEvent_t e0, e1;
   check_cuda(cudaEventCreate(&e0), "event");
   check_cuda(cudaEventCreate(&e1), "event");
-  int best = ld.face_tasks_per_face;
+  std::pair<int, int> best{cur.variant, cur.param};
   float best_ms = 1e30f;
-  for (int c : cand_all) {
-    if (c > max_per_face) break;
-    set_face_tasks(m, level, c);
+  for (auto c : cands) {
+    set_sweep(m, level, prec, c.first, c.second);
     face_gs3_launch(m, level, prec, ld.x[prec], ld.w[prec], ld.b[prec], true, st);  // warm-up
     check_cuda(cudaEventRecord(e0, st), "record");
     for (int rep = 0; rep < 3; ++rep)
@@ -79,12 +90,12 @@ int tune_face_sweep(Mesh& m, int level, int prec, cudaStream_t st) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  set_face_tasks(m, level, best);
+  set_sweep(m, level, prec, best.first, best.second);
   if (cache_path) {
     std::ofstream out(cache_path, std::ios::app);
-    out << key << "|" << best << "\n";
+    out << key << "|" << best.first << " " << best.second << "\n";
   }
-  return best;
+  return best.first * 10000 + best.second;
 }
 
 // ------------------------------------------------------------------ batches

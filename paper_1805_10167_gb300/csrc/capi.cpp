@@ -444,7 +444,27 @@ hhg_status hhg_tune(hhg_mesh mesh, hhg_prec prec, void* stream) {
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_prec(prec);
-    for (int l = 2; l <= m.max_level; ++l) hhg::tune_face_sweep(m, l, prec, S(stream));
+    for (int l = 4; l <= m.max_level; ++l) hhg::tune_face_sweep(m, l, prec, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_sweep_config(hhg_mesh mesh, int32_t level, hhg_prec prec, int32_t set,
+                            int32_t* variant, int32_t* param) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    check_prec(prec);
+    need(variant, "variant");
+    need(param, "param");
+    if (set) {
+      if (*variant != HHG_SWEEP_RING && *variant != HHG_SWEEP_STRIP) throw ArgError("bad sweep variant");
+      if (*param < 1 || *param > (1 << 20)) throw ArgError("sweep param must be in [1, 2^20]");
+      hhg::set_sweep(m, level, prec, *variant, *param);
+    } else {
+      *variant = m.levels[level].sweep[prec].variant;
+      *param = m.levels[level].sweep[prec].param;
+    }
     return HHG_OK;
   });
 }

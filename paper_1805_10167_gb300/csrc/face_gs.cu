@@ -269,13 +269,10 @@ static void launch_t(const MeshTables& tab, const LevelView& L, const T* xin, T*
   k_face_gs3<T, VARK, FWD><<<ntasks, kThreadsGS, smem, st>>>(tab, L, xin, xout, b, k, tasks, err);
 }
 
-void face_gs3_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
-                     bool forward, cudaStream_t st) {
+void face_ring_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
+                      bool forward, const int4* tasks, int nt, cudaStream_t st) {
   const LevelData& ld = m.levels[level];
   const LevelView& L = ld.lv;
-  LaunchScope ls(HHG_K_FACE_GS, level, st);
-  const int4* tasks = (const int4*)ld.face_tasks;
-  const int nt = ld.n_face_tasks;
   if (prec == 0) {
     const double* k = m.vark ? (const double*)ld.k[0] : nullptr;
     auto* xi = (const double*)xin;
@@ -302,6 +299,17 @@ void face_gs3_launch(const Mesh& m, int level, int prec, const void* xin, void* 
     }
   }
   check_cuda(cudaGetLastError(), "face gs3");
+}
+
+// The face phase of one sweep with the level's configured kernel.
+void face_gs3_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
+                     bool forward, cudaStream_t st) {
+  const SweepCfg& c = m.levels[level].sweep[prec];
+  LaunchScope ls(HHG_K_FACE_GS, level, st);
+  if (c.variant == SWEEP_STRIP)
+    face_strip_launch(m, level, prec, xin, xout, b, forward, (const int4*)c.tasks, c.ntasks, st);
+  else
+    face_ring_launch(m, level, prec, xin, xout, b, forward, (const int4*)c.tasks, c.ntasks, st);
 }
 
 }  // namespace hhg

@@ -1,0 +1,301 @@
+// Register-blocked three-colour Gauss-Seidel over the face interiors
+// (sm_103a), the barrier-free alternative to the shared-memory ring sweep.
+//
+// One warp sweeps one vertical strip of one face.  Lane l keeps the columns
+// ws + 3l, ws + 3l + 1, ws + 3l + 2 of a window of rows in registers, where
+// ws = 90 s is a multiple of 3: the colour (i + 2j) mod 3 of column
+// ws + 3l + m in row j is then (m + 2j) mod 3 for every lane, so a colour of
+// one row is exactly one point per lane and the warp never diverges on it.
+// The sweep is a wavefront over the rows: at step t colour A is applied to
+// row t, colour B to row t - 1 and colour C to row t - 2 (A, B, C = 0, 1, 2
+// forward and 2, 1, 0 backward, the order of the multi-colour Gauss-Seidel
+// of Sec. 3.2), after which row t - 2 is final and stored.  Horizontal
+// neighbours held by the lanes on either side arrive by warp shuffles; there
+// is no shared memory and no block-wide barrier.
+//
+// Strips overlap.  A window is 96 columns wide and stores its middle 90 (the
+// first strip stores columns 0..92: column 0 is the face boundary, whose
+// values are exact copies).  A value written by the colour applied first is
+// exact at distance >= 1 from a window edge whose outside is not held, by
+// the second colour at distance >= 2 and by the third at >= 3, so the three
+// halo columns on each side absorb everything that saw an edge.  Row blocks
+// [j0, j1) of a strip overlap in the same way: colour A is also applied to
+// the two rows below and the row above... up to j1 + 1, colour B to j0 - 1
+// and j1, as the dependency cone of the three colour phases requires.
+//
+// The sweep reads x_in and writes x_out (ping-pong); each point is stored by
+// exactly one (strip, row block).
+#include "stencil.cuh"
+
+namespace hhg {
+
+namespace {
+
+constexpr int kStripUseful = 90;   // stored columns per strip (a multiple of 3)
+constexpr int kStripWarps = 4;     // independent strip tasks per CTA
+constexpr int kPrefetchRows = 8;   // L2 prefetch distance in rows
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+struct StripArgs {
+  const T* xg;        // x_in of the face
+  T* xo;              // x_out of the face
+  const T* bg;        // b of the face
+  const T* ku;        // coefficients of the upward / downward micro-triangles
+  const T* kd;
+  int64_t S;
+  int N, ic, ws, us, ue, j0, j1;
+  T dinv, w0, w1, w2, c0, c1, c2;
+};
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// row r, column i inside the closed triangle (every such slot is allocated)
+__device__ __forceinline__ bool in_tri(int N, int r, int i) { return r >= 0 && r <= N && i <= N - r; }
+
+// Colour phase on row t + DR at the lane's column M; U = t mod 6 places the
+// rows in the six-slot register ring (row r lives in slot r mod 6).
+template <typename T, bool VARK, int DR, int M, int U>
+__device__ __forceinline__ void strip_phase(T (&X)[6][3], T bv, int t, int rlo, int rhi,
+                                            const StripArgs<T>& a) {
+  constexpr int sc = (U + 6 + DR) % 6, sn = (U + 7 + DR) % 6, ss = (U + 5 + DR) % 6;
+  const int r = t + DR;
+  // warp-uniform: the row is in this phase's range, is a face-interior row,
+  // and holds at least one interior column of the window
+  if (r < rlo || r > rhi || r < 1 || r > a.N - 2 || a.ws + 1 > a.N - 1 - r) return;
+  T xe, xse, xw, xnw;
+  if (M < 2) {
+    xe = X[sc][(M + 1) % 3];
+    xse = X[ss][(M + 1) % 3];
+  } else {
+    xe = __shfl_down_sync(kFull, X[sc][0], 1);
+    xse = __shfl_down_sync(kFull, X[ss][0], 1);
+  }
+  if (M > 0) {
+    xw = X[sc][(M + 2) % 3];
+    xnw = X[sn][(M + 2) % 3];
+  } else {
+    xw = __shfl_up_sync(kFull, X[sc][2], 1);
+    xnw = __shfl_up_sync(kFull, X[sn][2], 1);
+  }
+  const T xn = X[sn][M], xs = X[ss][M];
+  const int i = a.ic + M;
+  const bool act = i >= 1 && i + r <= a.N - 1;
+  if (!VARK) {
+    T acc = bv * a.dinv;
+    acc = fma(a.w2, xe + xw, acc);
+    acc = fma(a.w1, xn + xs, acc);
+    acc = fma(a.w0, xse + xnw, acc);
+    if (act) X[sc][M] = acc;
+  } else if (act) {
+    const int64_t p = (int64_t)r * a.S + i;
+    const T u = __ldg(a.ku + p), uw = __ldg(a.ku + p - 1), us = __ldg(a.ku + p - a.S);
+    const T ds = __ldg(a.kd + p - a.S), dw = __ldg(a.kd + p - 1), dsw = __ldg(a.kd + p - 1 - a.S);
+    const T h0 = T(0.5) * a.c0, h1 = T(0.5) * a.c1, h2 = T(0.5) * a.c2;
+    const T we = h2 * (u + ds), ww = h2 * (uw + dsw);
+    const T wn = h1 * (u + dw), wsn = h1 * (us + dsw);
+    const T wse = h0 * (us + ds), wnw = h0 * (uw + dw);
+    const T off = we * xe + ww * xw + wn * xn + wsn * xs + wse * xse + wnw * xnw;
+    const T diag = we + ww + wn + wsn + wse + wnw;
+    X[sc][M] = (bv + off) / diag;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_row(T (&dst)[3], int r, int rmax, const StripArgs<T>& a) {
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int i = a.ic + m;
+    dst[m] = (r <= rmax && in_tri(a.N, r, i)) ? a.xg[(int64_t)r * a.S + i] : T(0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T load_b(int r, int m, const StripArgs<T>& a) {
+  const int i = a.ic + m;
+  return (r >= 1 && r <= a.j1 + 1 && in_tri(a.N, r, i)) ? a.bg[(int64_t)r * a.S + i] : T(0);
+}
+
+// Column of the phase with colour c on row r: (c + r) mod 3, since the
+// colour of column ws + 3l + m in row r is (m + 2r) mod 3.
+template <bool FWD, int U>
+struct StripCols {
+  static constexpr int cA = FWD ? 0 : 2, cB = 1, cC = FWD ? 2 : 0;
+  static constexpr int mA = (cA + U) % 3;            // row t
+  static constexpr int mB = (cB + U + 2) % 3;        // row t - 1
+  static constexpr int mC = (cC + U + 1) % 3;        // row t - 2
+};
+
+// b ring: step t uses the three values loaded two steps earlier
+template <typename T, bool FWD, int U>
+__device__ __forceinline__ void load_b_step(T (&Bv)[3], int t, const StripArgs<T>& a) {
+  using C = StripCols<FWD, U % 3>;
+  Bv[0] = load_b(t, C::mA, a);
+  Bv[1] = load_b(t - 1, C::mB, a);
+  Bv[2] = load_b(t - 2, C::mC, a);
+}
+
+template <typename T, bool VARK, bool FWD, int U>
+__device__ __forceinline__ void strip_step(T (&X)[6][3], T (&Bq)[2][3], int t, int rmax,
+                                           const StripArgs<T>& a) {
+  using C = StripCols<FWD, U % 3>;
+  // next row of x into the slot of row t - 4 (dead), b for step t + 2, and
+  // an L2 prefetch further ahead
+  load_row(X[(U + 2) % 6], t + 2, rmax, a);
+  T Bv[3] = {Bq[U % 2][0], Bq[U % 2][1], Bq[U % 2][2]};
+  load_b_step<T, FWD, (U + 2) % 6>(Bq[U % 2], t + 2, a);
+  {
+    const int rp = t + 2 + kPrefetchRows, ip = a.ic;
+    if (rp <= rmax && in_tri(a.N, rp, ip)) {
+      prefetch_l2(a.xg + (int64_t)rp * a.S + ip);
+      prefetch_l2(a.bg + (int64_t)rp * a.S + ip);
+    }
+  }
+  strip_phase<T, VARK, 0, C::mA, U>(X, Bv[0], t, a.j0 - 2, a.j1 + 1, a);
+  strip_phase<T, VARK, -1, C::mB, U>(X, Bv[1], t, a.j0 - 1, a.j1, a);
+  strip_phase<T, VARK, -2, C::mC, U>(X, Bv[2], t, a.j0, a.j1 - 1, a);
+  // row t - 2 is final
+  const int r = t - 2;
+  if (r >= a.j0 && r < a.j1) {
+    constexpr int sl = (U + 4) % 6;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const int i = a.ic + m;
+      if (i >= a.us && i < a.ue && i <= a.N - r) a.xo[(int64_t)r * a.S + i] = X[sl][m];
+    }
+  }
+}
+
+template <typename T, bool VARK, bool FWD>
+__global__ void __launch_bounds__(kStripWarps * 32)
+    k_face_gs_strip(MeshTables M, LevelView L, const T* __restrict__ xin, T* __restrict__ xout,
+                    const T* __restrict__ b, const T* __restrict__ k, const int4* __restrict__ tasks,
+                    int ntasks) {
+  const int wt = blockIdx.x * kStripWarps + (int)(threadIdx.x >> 5);
+  if (wt >= ntasks) return;   // whole warp
+  const int lane = threadIdx.x & 31;
+  const int4 tk = tasks[wt];
+  const int f = tk.x, s = tk.y;
+  StripArgs<T> a;
+  a.N = L.N;
+  a.S = L.S;
+  a.ws = kStripUseful * s;
+  a.ic = a.ws + 3 * lane;
+  a.us = s == 0 ? 0 : a.ws + 3;
+  a.ue = a.ws + kStripUseful + 3;
+  a.j0 = tk.z;
+  a.j1 = tk.w;
+  const int64_t fb = L.f_off + (int64_t)f * L.FS;
+  a.xg = xin + fb;
+  a.xo = xout + fb;
+  a.bg = b + fb;
+  a.ku = VARK ? k + (int64_t)f * L.FS : nullptr;
+  a.kd = VARK ? k + (int64_t)(M.nf + f) * L.FS : nullptr;
+  const FaceRec& F = M.faces[f];
+  a.c0 = (T)F.cot[0];
+  a.c1 = (T)F.cot[1];
+  a.c2 = (T)F.cot[2];
+  a.dinv = (T)F.dinv;
+  a.w0 = (T)F.w[0];
+  a.w1 = (T)F.w[1];
+  a.w2 = (T)F.w[2];
+  const int rmax = min(a.N, a.j1 + 2);   // last row read
+
+  // first step: a multiple of 6 at or below j0 - 2 (the steps before j0 - 2
+  // do no work; they only keep the register ring indices static)
+  const int first = a.j0 - 2;
+  const int t0 = first >= 0 ? first - first % 6 : -(((-first) + 5) / 6) * 6;
+  const int tend = a.j1 + 1;
+  T X[6][3];
+  T Bq[2][3];
+  // rows t0 - 3 .. t0 + 1 into slots (r mod 6); b for steps t0, t0 + 1
+  load_row(X[3], t0 - 3, rmax, a);
+  load_row(X[4], t0 - 2, rmax, a);
+  load_row(X[5], t0 - 1, rmax, a);
+  load_row(X[0], t0, rmax, a);
+  load_row(X[1], t0 + 1, rmax, a);
+  load_b_step<T, FWD, 0>(Bq[0], t0, a);
+  load_b_step<T, FWD, 1>(Bq[1], t0 + 1, a);
+  for (int t = t0; t <= tend; t += 6) {
+    strip_step<T, VARK, FWD, 0>(X, Bq, t, rmax, a);
+    if (t + 1 > tend) break;
+    strip_step<T, VARK, FWD, 1>(X, Bq, t + 1, rmax, a);
+    if (t + 2 > tend) break;
+    strip_step<T, VARK, FWD, 2>(X, Bq, t + 2, rmax, a);
+    if (t + 3 > tend) break;
+    strip_step<T, VARK, FWD, 3>(X, Bq, t + 3, rmax, a);
+    if (t + 4 > tend) break;
+    strip_step<T, VARK, FWD, 4>(X, Bq, t + 4, rmax, a);
+    if (t + 5 > tend) break;
+    strip_step<T, VARK, FWD, 5>(X, Bq, t + 5, rmax, a);
+  }
+}
+
+}  // namespace
+
+// Strip tasks (face, strip, j0, j1): strip s stores columns [us, us + 90)
+// (us = 0 for s = 0, else 90 s + 3) on rows [0, N - us]; each strip's rows
+// are cut into blocks of about `rows_per_task` rows.
+std::vector<int> strip_tasks(int nf, int N, int rows_per_task) {
+  std::vector<int> out;
+  const int H = std::max(1, rows_per_task);
+  for (int f = 0; f < nf; ++f) {
+    for (int s = 0;; ++s) {
+      const int us = s == 0 ? 0 : kStripUseful * s + 3;
+      if (us > N) break;
+      const int rows = N - us + 1;
+      const int nb = (rows + H - 1) / H;
+      for (int q = 0; q < nb; ++q) {
+        const int j0 = (int)((int64_t)rows * q / nb), j1 = (int)((int64_t)rows * (q + 1) / nb);
+        if (j1 <= j0) continue;
+        out.push_back(f);
+        out.push_back(s);
+        out.push_back(j0);
+        out.push_back(j1);
+      }
+    }
+  }
+  return out;
+}
+
+template <typename T, bool VARK, bool FWD>
+static void launch_strip_t(const MeshTables& tab, const LevelView& L, const T* xin, T* xout,
+                           const T* b, const T* k, const int4* tasks, int ntasks, cudaStream_t st) {
+  const int grid = (ntasks + kStripWarps - 1) / kStripWarps;
+  k_face_gs_strip<T, VARK, FWD><<<grid, kStripWarps * 32, 0, st>>>(tab, L, xin, xout, b, k, tasks, ntasks);
+}
+
+void face_strip_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
+                       bool forward, const int4* tasks, int ntasks, cudaStream_t st) {
+  const LevelView& L = m.levels[level].lv;
+  if (prec == 0) {
+    const double* k = m.vark ? (const double*)m.levels[level].k[0] : nullptr;
+    auto* xi = (const double*)xin;
+    auto* xo = (double*)xout;
+    auto* bb = (const double*)b;
+    if (m.vark) {
+      if (forward) launch_strip_t<double, true, true>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
+      else launch_strip_t<double, true, false>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
+    } else {
+      if (forward) launch_strip_t<double, false, true>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
+      else launch_strip_t<double, false, false>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
+    }
+  } else {
+    const float* k = m.vark ? (const float*)m.levels[level].k[1] : nullptr;
+    auto* xi = (const float*)xin;
+    auto* xo = (float*)xout;
+    auto* bb = (const float*)b;
+    if (m.vark) {
+      if (forward) launch_strip_t<float, true, true>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
+      else launch_strip_t<float, true, false>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
+    } else {
+      if (forward) launch_strip_t<float, false, true>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
+      else launch_strip_t<float, false, false>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
+    }
+  }
+  check_cuda(cudaGetLastError(), "face strip sweep");
+}
+
+}  // namespace hhg

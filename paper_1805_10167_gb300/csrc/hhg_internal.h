@@ -149,6 +149,17 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Face Gauss-Seidel configuration of one level and precision: the kernel
+// variant and its work split, with the device task list it implies.
+enum SweepVariant { SWEEP_RING = 0, SWEEP_STRIP = 1 };
+struct SweepCfg {
+  int variant = SWEEP_STRIP;
+  int param = 0;            // RING: row blocks per face; STRIP: rows per strip task
+  int* tasks = nullptr;     // device int4: RING (face, j0, j1, 0), STRIP (face, strip, j0, j1)
+  int ntasks = 0;
+  size_t cap = 0;           // bytes allocated at tasks
+};
+
 struct LevelData {
   LevelView lv;
   int n_colours = 0;
@@ -161,9 +172,7 @@ struct LevelData {
   void* r[2] = {nullptr, nullptr};
   void* w[2] = {nullptr, nullptr};  // ping-pong partner of the iterate for Gauss-Seidel sweeps
   void* k[2] = {nullptr, nullptr};  // coefficient: up array then down array (2 * nf * FS)
-  int* face_tasks = nullptr;        // device int4 (face, j0, j1, 0): row blocks of the face sweep
-  int n_face_tasks = 0;
-  int face_tasks_per_face = 0;
+  SweepCfg sweep[2];                // face sweep configuration per precision
 };
 
 struct Learned;
@@ -214,6 +223,11 @@ void gs_sweep(const Mesh& m, int level, int prec, void* xin, void* xout, const v
 void face_gs3_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
                      bool forward, cudaStream_t st);
 std::vector<int> face_tasks(int nf, int N, int tasks_per_face);
+std::vector<int> strip_tasks(int nf, int N, int rows_per_task);
+void face_ring_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
+                      bool forward, const int4* tasks, int ntasks, cudaStream_t st);
+void face_strip_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
+                       bool forward, const int4* tasks, int ntasks, cudaStream_t st);
 size_t face_gs_smem(const LevelView& L, int prec);
 void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,
                   void* work, cudaStream_t st);
@@ -294,7 +308,8 @@ void block_norms2(const Mesh& m, int level, const double* r64, float* r32, doubl
 // Autotuner: picks the row-block split of the face sweep on `level` for
 // precision `prec` by timing candidates; returns the chosen tasks per face.
 int tune_face_sweep(Mesh& m, int level, int prec, cudaStream_t st);
-void set_face_tasks(Mesh& m, int level, int per_face);
+void set_sweep(Mesh& m, int level, int prec, int variant, int param);
+void default_sweep(Mesh& m, int level);
 
 // Counts one kernel launch of class `cls` (hhg_kernel_class); while profiling
 // is on for that class and level, brackets it with CUDA events on `st`.

@@ -284,13 +284,7 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
         ld.r[p] = dev_alloc(m, bytes);
         ld.w[p] = dev_alloc(m, bytes);
       }
-      // face sweep row blocks: about 1216 CTAs in total (8 per SM), at least
-      // 48 rows per block so that the recomputed halo rows stay below 2 %
-      // (the autotuner may change this later)
-      const int N = ld.lv.N;
-      int per_face = (int)((1216 + m.nf / 2) / m.nf);
-      per_face = std::max(1, std::min(per_face, (N + 1) / 48));
-      set_face_tasks(m, l, per_face);
+      default_sweep(m, l);
     }
     m.partials = (double*)dev_alloc(m, kMaxPartials * sizeof(double));
     m.scalars = (double*)dev_alloc(m, 16 * sizeof(double));
@@ -315,16 +309,29 @@ void mesh_destroy_internal(Mesh* m) {
   delete m;
 }
 
-// Row blocks of the face sweep on one level (the split never changes results:
-// every point is updated from the same operands whichever CTA owns it).
-void set_face_tasks(Mesh& m, int level, int per_face) {
+// Work split of the face sweep of one level and precision (a split never
+// changes results: every point is updated from the same operands whichever
+// CTA or warp owns it).
+void set_sweep(Mesh& m, int level, int prec, int variant, int param) {
   LevelData& ld = m.levels[level];
-  std::vector<int> tk = face_tasks(m.nf, ld.lv.N, per_face);
+  SweepCfg& c = ld.sweep[prec];
+  std::vector<int> tk = variant == SWEEP_STRIP ? strip_tasks(m.nf, ld.lv.N, param)
+                                               : face_tasks(m.nf, ld.lv.N, param);
   const size_t need = tk.size() * sizeof(int);
-  if (!ld.face_tasks || (size_t)ld.n_face_tasks * 4 * sizeof(int) < need) ld.face_tasks = (int*)dev_alloc(m, need);
-  check_cuda(cudaMemcpy(ld.face_tasks, tk.data(), need, cudaMemcpyHostToDevice), "face tasks");
-  ld.n_face_tasks = (int)(tk.size() / 4);
-  ld.face_tasks_per_face = per_face;
+  if (!c.tasks || c.cap < need) {
+    c.tasks = (int*)dev_alloc(m, need);
+    c.cap = need;
+  }
+  check_cuda(cudaMemcpy(c.tasks, tk.data(), need, cudaMemcpyHostToDevice), "face tasks");
+  c.ntasks = (int)(tk.size() / 4);
+  c.variant = variant;
+  c.param = param;
+}
+
+// Untuned default: register strips with row blocks of about 32 rows (the
+// fastest split at levels 7-10 in both precisions on the 128-face annulus).
+void default_sweep(Mesh& m, int level) {
+  for (int p = 0; p < 2; ++p) set_sweep(m, level, p, SWEEP_STRIP, 32);
 }
 
 // Coefficient pyramid: finest level from the canonical element order, coarse

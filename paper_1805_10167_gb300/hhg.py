@@ -24,6 +24,7 @@ lib = C.CDLL(LIB_PATH)
 
 OK, ERR_ARG, ERR_MESH, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_NAN, ERR_TIMEOUT, ERR_BREAKDOWN = range(9)
 F64, F32 = 0, 1
+SWEEP_RING, SWEEP_STRIP = 0, 1
 GS_FWD, GS_BWD, JACOBI = 0, 1, 2
 SOLVE_MG, SOLVE_IR, SOLVE_FGMRES = 0, 1, 2
 SMOOTH_GS, SMOOTH_LEARNED = 0, 1
@@ -76,6 +77,7 @@ _SIGS = {
     "hhg_vcycle": [_P, C.c_int32, C.c_int32, _P, _P, C.POINTER(VcycleOpts), _P],
     "hhg_solve": [_P, C.c_int32, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveReport), _P],
     "hhg_tune": [_P, C.c_int32, _P],
+    "hhg_sweep_config": [_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "hhg_batch_create": [C.c_int32, C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.c_int64),
                          C.POINTER(C.POINTER(C.c_int32)), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                          C.POINTER(_P)],
@@ -258,6 +260,14 @@ class Mesh:
 
     def tune(self, prec=F64, stream=None):
         _check(lib.hhg_tune(self.h, prec, _stream(stream)))
+
+    def sweep_config(self, level, prec=F64, variant=None, param=None):
+        """Reads the face-sweep kernel (SWEEP_RING / SWEEP_STRIP) and its split
+        of one level, or sets them when variant and param are given."""
+        v, p = C.c_int32(variant or 0), C.c_int32(param or 0)
+        set_ = variant is not None
+        _check(lib.hhg_sweep_config(self.h, level, prec, 1 if set_ else 0, C.byref(v), C.byref(p)))
+        return v.value, p.value
 
     def vcycle(self, level, x, b, nu1=3, nu2=3, prec=F64, stream=None):
         o = VcycleOpts(nu1, nu2)
