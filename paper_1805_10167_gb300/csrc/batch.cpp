@@ -48,8 +48,9 @@ static std::map<std::string, std::pair<int, int>> read_cache(const char* path) {
 }
 
 // Picks the face-sweep kernel and its work split for one level and precision
-// by timing every candidate (three sweeps each, after one warm-up) on the
-// level's own workspaces; the choice never changes results.  Returns the
+// by timing whole Gauss-Seidel sweeps with every candidate (four each, after
+// one warm-up) on the level's own workspaces; the choice never changes
+// results.  Returns the
 // encoded choice variant * 10000 + param.
 int tune_face_sweep(Mesh& m, int level, int prec, cudaStream_t st) {
   LevelData& ld = m.levels[level];
@@ -66,7 +67,7 @@ int tune_face_sweep(Mesh& m, int level, int prec, cudaStream_t st) {
   std::vector<std::pair<int, int>> cands;
   for (int c : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
     if (c <= std::max(1, (N + 1) / 16)) cands.push_back({SWEEP_RING, c});
-  for (int h : {16, 32, 64, 128, 256, 512, 1024})
+  for (int h : {8, 16, 32, 64, 128, 256, 512})
     if (h <= 2 * (N + 1)) cands.push_back({SWEEP_STRIP, h});
   cudaEvent_t e0, e1;
   check_cuda(cudaEventCreate(&e0), "event");
@@ -75,10 +76,11 @@ int tune_face_sweep(Mesh& m, int level, int prec, cudaStream_t st) {
   float best_ms = 1e30f;
   for (auto c : cands) {
     set_sweep(m, level, prec, c.first, c.second);
-    face_gs3_launch(m, level, prec, ld.x[prec], ld.w[prec], ld.b[prec], true, st);  // warm-up
+    gs_sweep(m, level, prec, ld.x[prec], ld.w[prec], ld.b[prec], true, st);  // warm-up
     check_cuda(cudaEventRecord(e0, st), "record");
-    for (int rep = 0; rep < 3; ++rep)
-      face_gs3_launch(m, level, prec, ld.x[prec], ld.w[prec], ld.b[prec], rep % 2 == 0, st);
+    for (int rep = 0; rep < 4; ++rep)   // whole sweeps, ping-pong
+      gs_sweep(m, level, prec, rep % 2 ? ld.w[prec] : ld.x[prec], rep % 2 ? ld.x[prec] : ld.w[prec], ld.b[prec],
+               rep < 2, st);
     check_cuda(cudaEventRecord(e1, st), "record");
     check_cuda(cudaEventSynchronize(e1), "sync");
     float ms = 0.f;

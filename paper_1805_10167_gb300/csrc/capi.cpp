@@ -82,7 +82,10 @@ bool device_timed_out(const hhg::Mesh& m, cudaStream_t st) {
   int e = 0;
   hhg::check_cuda(cudaMemcpyAsync(&e, m.err, sizeof(int), cudaMemcpyDeviceToHost, st), "err readback");
   hhg::check_cuda(cudaStreamSynchronize(st), "sync");
-  if (e) hhg::check_cuda(cudaMemsetAsync(m.err, 0, sizeof(int), st), "err clear");
+  if (e) {
+    hhg::check_cuda(cudaMemsetAsync(m.err, 0, sizeof(int), st), "err clear");
+    hhg::check_cuda(cudaMemsetAsync(m.gbar, 0, 4 * sizeof(unsigned), st), "grid barrier reset");
+  }
   return e != 0;
 }
 
@@ -399,6 +402,7 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
     double r0 = std::sqrt(read_scalar(nrm, st));
     double r = r0;
     int it = 0;
+    double* cur = x;   // IR: the iterate alternates between x and ld.w[0]
     hhg_status status = HHG_OK;
     auto record = [&](int k, double v) {
       if (rep && rep->history && k < rep->history_cap) rep->history[k] = v;
@@ -411,11 +415,14 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
         break;
       }
       if (o.mode == HHG_SOLVE_IR) {
-        // inner FP32 V-cycle on A d = r from d = 0, then x += d in FP64
+        // inner FP32 V-cycle on A d = r from d = 0, then x += d and the new
+        // residual in FP64 in one pass, ping-ponging between x and the
+        // level's FP64 workspace
         hhg::zero_vec(m, level, 1, ld.x[1], st);
         hhg::vcycle_run(m, level, 1, ld.x[1], ld.b[1], o.nu1, o.nu2, 0, st);
-        hhg::update_f64_from_f32(m, level, x, (const float*)ld.x[1], st);
-        hhg::residual_f64_to_f32(m, level, x, b, (float*)ld.b[1], nrm, st);
+        double* nxt = cur == x ? (double*)ld.w[0] : x;
+        hhg::update_residual_f64(m, level, cur, (const float*)ld.x[1], nxt, b, (float*)ld.b[1], nrm, st);
+        cur = nxt;
       } else {
         hhg::vcycle_run(m, level, 0, x, b, o.nu1, o.nu2, 0, st);
         hhg::residual_op(m, level, 0, x, b, ld.r[0], nrm, st);
@@ -425,6 +432,9 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
       record(it, r);
       if (!std::isfinite(r)) status = HHG_ERR_NAN;
     }
+    if (cur != x)
+      hhg::check_cuda(cudaMemcpyAsync(x, cur, (size_t)ld.lv.len * sizeof(double), cudaMemcpyDeviceToDevice, st),
+                 "iterate copy");
     if (device_timed_out(m, st)) status = HHG_ERR_TIMEOUT;
     if (rep) {
       rep->smoother_used = HHG_SMOOTH_GS;

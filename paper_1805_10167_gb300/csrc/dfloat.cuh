@@ -11,7 +11,8 @@
 //
 // Conversions to and from double use integer bit operations only, so that
 // they do not occupy the (narrow) FP64 pipe, except one FP64 addition in
-// to_double.  Magnitudes below 2^-126 are flushed to zero; the low word is
+// to_double; d2f_rn and f2d_bits are the plain binary64 <-> binary32
+// conversions done the same way.  Magnitudes below 2^-126 are flushed to zero; the low word is
 // dropped below 2^-74 (relative error 2^-24 of such tiny values).
 #pragma once
 
@@ -129,5 +130,24 @@ HHG_HD double f2d_bits(float f) {
 }
 
 HHG_HD double to_double(dfl x) { return f2d_bits(x.hi) + f2d_bits(x.lo); }
+
+// double -> float rounded to nearest, ties to even (IEEE 754 binary64 to
+// binary32), by integer operations only: the 52-bit significand keeps its
+// top 23 bits and the 29 dropped bits decide the rounding; a carry out of
+// the significand moves into the exponent (and to infinity past the largest
+// float).  Magnitudes below 2^-126 are flushed to zero; NaN stays NaN.
+HHG_HD float d2f_rn(double d) {
+  const uint64_t u = dbits(d);
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7FF) - 1023;
+  const uint64_t m = u & 0x000FFFFFFFFFFFFFull;
+  if (e == 1024) return bitsf(sign | (m ? 0x7FC00000u : 0x7F800000u));
+  if (e > 127) return bitsf(sign | 0x7F800000u);
+  if (e < -126) return bitsf(sign);
+  uint32_t bits = ((uint32_t)(e + 127) << 23) | (uint32_t)(m >> 29);
+  const uint32_t rest = (uint32_t)(m & 0x1FFFFFFFull);
+  if (rest > 0x10000000u || (rest == 0x10000000u && (bits & 1u))) bits += 1u;
+  return bitsf(sign | bits);
+}
 
 }  // namespace hhg

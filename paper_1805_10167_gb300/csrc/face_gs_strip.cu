@@ -168,15 +168,39 @@ __device__ __forceinline__ void strip_step(T (&X)[6][3], T (&Bq)[2][3], int t, i
   }
 }
 
+// The wavefront of one strip task from step t0 (a multiple of 6) to tend.
 template <typename T, bool VARK, bool FWD>
-__global__ void __launch_bounds__(kStripWarps * 32)
-    k_face_gs_strip(MeshTables M, LevelView L, const T* __restrict__ xin, T* __restrict__ xout,
-                    const T* __restrict__ b, const T* __restrict__ k, const int4* __restrict__ tasks,
-                    int ntasks) {
-  const int wt = blockIdx.x * kStripWarps + (int)(threadIdx.x >> 5);
-  if (wt >= ntasks) return;   // whole warp
-  const int lane = threadIdx.x & 31;
-  const int4 tk = tasks[wt];
+__device__ __forceinline__ void strip_run(int t0, int tend, int rmax, const StripArgs<T>& a) {
+  T X[6][3];
+  T Bq[2][3];
+  // rows t0 - 3 .. t0 + 1 into slots (r mod 6); b for steps t0, t0 + 1
+  load_row(X[3], t0 - 3, rmax, a);
+  load_row(X[4], t0 - 2, rmax, a);
+  load_row(X[5], t0 - 1, rmax, a);
+  load_row(X[0], t0, rmax, a);
+  load_row(X[1], t0 + 1, rmax, a);
+  load_b_step<T, FWD, 0>(Bq[0], t0, a);
+  load_b_step<T, FWD, 1>(Bq[1], t0 + 1, a);
+  for (int t = t0; t <= tend; t += 6) {
+    strip_step<T, VARK, FWD, 0>(X, Bq, t, rmax, a);
+    if (t + 1 > tend) break;
+    strip_step<T, VARK, FWD, 1>(X, Bq, t + 1, rmax, a);
+    if (t + 2 > tend) break;
+    strip_step<T, VARK, FWD, 2>(X, Bq, t + 2, rmax, a);
+    if (t + 3 > tend) break;
+    strip_step<T, VARK, FWD, 3>(X, Bq, t + 3, rmax, a);
+    if (t + 4 > tend) break;
+    strip_step<T, VARK, FWD, 4>(X, Bq, t + 4, rmax, a);
+    if (t + 5 > tend) break;
+    strip_step<T, VARK, FWD, 5>(X, Bq, t + 5, rmax, a);
+  }
+}
+
+// One strip task (face, strip, j0, j1) by one warp.
+template <typename T, bool VARK, bool FWD>
+__device__ __forceinline__ void strip_task(const MeshTables& M, const LevelView& L, const T* xin, T* xout,
+                                           const T* __restrict__ b, const T* __restrict__ k, int4 tk,
+                                           int lane) {
   const int f = tk.x, s = tk.y;
   StripArgs<T> a;
   a.N = L.N;
@@ -203,33 +227,193 @@ __global__ void __launch_bounds__(kStripWarps * 32)
   a.w2 = (T)F.w[2];
   const int rmax = min(a.N, a.j1 + 2);   // last row read
 
-  // first step: a multiple of 6 at or below j0 - 2 (the steps before j0 - 2
-  // do no work; they only keep the register ring indices static)
+  // the wavefront runs from t = j0 - 2 to j1 + 1; it starts at the multiple
+  // of 6 at or below j0 - 2 so that the register ring slot of row r is the
+  // static r mod 6 (the steps before j0 - 2 only load)
   const int first = a.j0 - 2;
   const int t0 = first >= 0 ? first - first % 6 : -(((-first) + 5) / 6) * 6;
-  const int tend = a.j1 + 1;
-  T X[6][3];
-  T Bq[2][3];
-  // rows t0 - 3 .. t0 + 1 into slots (r mod 6); b for steps t0, t0 + 1
-  load_row(X[3], t0 - 3, rmax, a);
-  load_row(X[4], t0 - 2, rmax, a);
-  load_row(X[5], t0 - 1, rmax, a);
-  load_row(X[0], t0, rmax, a);
-  load_row(X[1], t0 + 1, rmax, a);
-  load_b_step<T, FWD, 0>(Bq[0], t0, a);
-  load_b_step<T, FWD, 1>(Bq[1], t0 + 1, a);
-  for (int t = t0; t <= tend; t += 6) {
-    strip_step<T, VARK, FWD, 0>(X, Bq, t, rmax, a);
-    if (t + 1 > tend) break;
-    strip_step<T, VARK, FWD, 1>(X, Bq, t + 1, rmax, a);
-    if (t + 2 > tend) break;
-    strip_step<T, VARK, FWD, 2>(X, Bq, t + 2, rmax, a);
-    if (t + 3 > tend) break;
-    strip_step<T, VARK, FWD, 3>(X, Bq, t + 3, rmax, a);
-    if (t + 4 > tend) break;
-    strip_step<T, VARK, FWD, 4>(X, Bq, t + 4, rmax, a);
-    if (t + 5 > tend) break;
-    strip_step<T, VARK, FWD, 5>(X, Bq, t + 5, rmax, a);
+  strip_run<T, VARK, FWD>(t0, a.j1 + 1, rmax, a);
+}
+
+template <typename T, bool VARK, bool FWD>
+__global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
+    k_face_gs_strip(MeshTables M, LevelView L, const T* __restrict__ xin, T* __restrict__ xout,
+                    const T* __restrict__ b, const T* __restrict__ k, const int4* __restrict__ tasks,
+                    int ntasks) {
+  const int wt = blockIdx.x * kStripWarps + (int)(threadIdx.x >> 5);
+  if (wt >= ntasks) return;   // whole warp
+  strip_task<T, VARK, FWD>(M, L, xin, xout, b, k, tasks[wt], threadIdx.x & 31);
+}
+
+// A whole face of a small level (N <= kSmallN) by one CTA in shared memory:
+// the closed triangle is staged, the three colours are applied one after the
+// other, every point of a colour at once, and the triangle is written out.
+constexpr int kSmallN = 64;
+
+template <typename T, bool VARK, bool FWD>
+__device__ __forceinline__ void face_small(const MeshTables& M, const LevelView& L, int f, const T* xin,
+                                           T* xout, const T* __restrict__ b, const T* __restrict__ k,
+                                           T* sx) {
+  const int N = L.N;
+  const int S = (int)L.S;
+  const int64_t fb = L.f_off + (int64_t)f * L.FS;
+  const int n = (N + 1) * S;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int j = q / S, i = q - j * S;
+    if (i <= N - j) sx[q] = xin[fb + q];
+  }
+  __syncthreads();
+  const FaceRec& F = M.faces[f];
+  const T dinv = (T)F.dinv, w0 = (T)F.w[0], w1 = (T)F.w[1], w2 = (T)F.w[2];
+  const T* ku = VARK ? k + (int64_t)f * L.FS : nullptr;
+  const T* kd = VARK ? k + (int64_t)(M.nf + f) * L.FS : nullptr;
+  const int W3 = N / 3 + 1;   // points of one colour in one row, at most
+  for (int ph = 0; ph < 3; ++ph) {
+    const int c = FWD ? ph : 2 - ph;
+    for (int q = threadIdx.x; q < (N - 2) * W3; q += blockDim.x) {
+      const int j = 1 + q / W3;
+      int i = ((c - 2 * j) % 3 + 3) % 3;   // first column of colour c in row j, >= 1
+      if (i == 0) i = 3;
+      i += 3 * (q - (j - 1) * W3);
+      if (i + j > N - 1) continue;
+      const int p = j * S + i;
+      const T xe = sx[p + 1], xw = sx[p - 1], xn = sx[p + S], xs = sx[p - S];
+      const T xse = sx[p + 1 - S], xnw = sx[p - 1 + S];
+      const T bv = b[fb + p];
+      if (!VARK) {
+        T acc = bv * dinv;
+        acc = fma(w2, xe + xw, acc);
+        acc = fma(w1, xn + xs, acc);
+        acc = fma(w0, xse + xnw, acc);
+        sx[p] = acc;
+      } else {
+        const T c0 = (T)F.cot[0], c1 = (T)F.cot[1], c2 = (T)F.cot[2];
+        const T u = __ldg(ku + p), uw = __ldg(ku + p - 1), us = __ldg(ku + p - S);
+        const T ds = __ldg(kd + p - S), dw = __ldg(kd + p - 1), dsw = __ldg(kd + p - 1 - S);
+        const T h0 = T(0.5) * c0, h1 = T(0.5) * c1, h2 = T(0.5) * c2;
+        const T we = h2 * (u + ds), ww = h2 * (uw + dsw);
+        const T wn = h1 * (u + dw), wsn = h1 * (us + dsw);
+        const T wse = h0 * (us + ds), wnw = h0 * (uw + dw);
+        const T off = we * xe + ww * xw + wn * xn + wsn * xs + wse * xse + wnw * xnw;
+        const T diag = we + ww + wn + wsn + wse + wnw;
+        sx[p] = (bv + off) / diag;
+      }
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int j = q / S, i = q - j * S;
+    if (i <= N - j) xout[fb + q] = sx[q];
+  }
+  __syncthreads();   // sx is reused by the CTA's next face
+}
+
+// ----------------------------------------------------------- whole sweep
+// Grid-wide barrier for a cooperative launch (every CTA resident; bar[0..1]
+// = count, generation, bar[2..3] = the face phase's task tickets): CTA
+// leaders count in, the last one resets the count and advances the
+// generation, the others wait for it -- for at most about a second, after
+// which they set *err and go on (the sweep's result is then wrong and the
+// host reports a timeout).  The fences order every write before the barrier
+// before every read after it, across the grid.
+constexpr long kBarrierPolls = 1L << 25;   // x ~32 ns sleep
+
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long polls = 0;
+      while (*gen == g) {
+        if (++polls > kBarrierPolls) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// One whole multi-colour Gauss-Seidel sweep of a level in one cooperative
+// launch: forward = vertices, edge colours 0, 1, ..., then the face strips;
+// backward = face strips, edge colours in reverse, vertices (the order of
+// the colour sets, reversed for the backward sweep).  Vertices and edges are
+// updated in place, on x_in going forward and on x_out going backward; the
+// faces go from x_in to x_out, and the vertex/edge block of x_in is copied
+// to x_out along with them.  Grid barriers separate the phases.
+template <typename T, bool VARK, bool FWD>
+__global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
+    k_gs_sweep(MeshTables M, LevelView L, T* xin, T* xout, const T* __restrict__ b,
+               const T* __restrict__ k, const int4* __restrict__ tasks, int ntasks,
+               const int* __restrict__ clist, EdgeColours cs, int small, unsigned* bar, int* err) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kStripWarps + (int)(threadIdx.x >> 5);
+  const int nw = gridDim.x * kStripWarps;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nt = gridDim.x * blockDim.x;
+  auto vertices = [&](T* x) {
+    for (int v = gw; v < M.nv; v += nw) vertex_gs<T, VARK>(M, L, v, lane, x, b, k);
+  };
+  auto edges = [&](T* x, int c) {
+    for (int q = cs.ptr[c] + gt; q < cs.ptr[c + 1]; q += nt) {
+      const int pk = clist[q];
+      const int e = pk / (L.N + 1);
+      edge_gs<T, VARK>(M, L, e, pk - e * (L.N + 1), x, b, k);
+    }
+  };
+  auto faces = [&]() {
+    for (int64_t q = gt; q < L.f_off; q += nt) xout[q] = xin[q];
+    if (small) {
+      for (int f = blockIdx.x; f < M.nf; f += gridDim.x)
+        face_small<T, VARK, FWD>(M, L, f, xin, xout, b, k, reinterpret_cast<T*>(dyn_smem));
+    } else {
+      // tasks handed out one at a time from a ticket counter (the strips of
+      // a face differ in height, the rows of a task in length); the last
+      // warp to finish resets the counters for the next launch
+      unsigned* ticket = bar + 2;
+      for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(ticket, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= (unsigned)ntasks) break;
+        strip_task<T, VARK, FWD>(M, L, xin, xout, b, k, tasks[w], lane);
+      }
+      if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(bar + 3, 1u) == (unsigned)nw - 1) {
+          bar[2] = 0;
+          bar[3] = 0;
+          __threadfence();
+        }
+      }
+    }
+  };
+  if (FWD) {
+    vertices(xin);
+    grid_barrier(bar, err);
+    for (int c = 0; c < cs.n; ++c) {
+      edges(xin, c);
+      grid_barrier(bar, err);
+    }
+    faces();
+  } else {
+    faces();
+    grid_barrier(bar, err);
+    for (int c = cs.n - 1; c >= 0; --c) {
+      edges(xout, c);
+      grid_barrier(bar, err);
+    }
+    vertices(xout);
   }
 }
 
@@ -265,6 +449,83 @@ static void launch_strip_t(const MeshTables& tab, const LevelView& L, const T* x
                            const T* b, const T* k, const int4* tasks, int ntasks, cudaStream_t st) {
   const int grid = (ntasks + kStripWarps - 1) / kStripWarps;
   k_face_gs_strip<T, VARK, FWD><<<grid, kStripWarps * 32, 0, st>>>(tab, L, xin, xout, b, k, tasks, ntasks);
+}
+
+template <typename T, bool VARK, bool FWD>
+static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b, const T* k,
+                           cudaStream_t st) {
+  const LevelData& ld = m.levels[level];
+  const SweepCfg& c = ld.sweep[sizeof(T) == 8 ? 0 : 1];
+  const int small = ld.lv.N <= kSmallN ? 1 : 0;
+  const size_t smem = small ? (size_t)(ld.lv.N + 1) * ld.lv.S * sizeof(T) : 0;
+  // CTAs per SM of this instance for each level (the shared memory of the
+  // small-level face phase depends on N only; the same on every device of a run)
+  static int resident_at[32] = {0};
+  const int lvl = std::min(level, 31);
+  if (resident_at[lvl] == 0) {
+    int r = 0;
+    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_gs_sweep<T, VARK, FWD>, kStripWarps * 32, smem),
+               "sweep occupancy");
+    if (r < 1) throw std::runtime_error("whole-sweep kernel cannot be resident");
+    resident_at[lvl] = r;
+  }
+  const int resident = resident_at[lvl];
+  int dev = 0, sms = 0;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  // enough CTAs for the widest phase, never more than are resident at once
+  int64_t want = std::max<int64_t>(small ? m.nf : (c.ntasks + kStripWarps - 1) / kStripWarps,
+                                   (m.nv + kStripWarps - 1) / kStripWarps);
+  want = std::max<int64_t>(want, (ld.lv.f_off + kStripWarps * 32 - 1) / (kStripWarps * 32));
+  want = std::max<int64_t>(want, 1);
+  const int grid = (int)std::min<int64_t>(want, (int64_t)resident * sms);
+  EdgeColours cs{};
+  cs.n = ld.n_colours;
+  if (cs.n > kMaxEdgeColours) throw std::runtime_error("too many edge colours for the whole-sweep kernel");
+  for (int q = 0; q <= cs.n; ++q) cs.ptr[q] = ld.colour_ptr.empty() ? 0 : ld.colour_ptr[q];
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kStripWarps * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  check_cuda(cudaLaunchKernelEx(&cfg, k_gs_sweep<T, VARK, FWD>, m.tab, ld.lv, xin, xout, b, k,
+                                (const int4*)c.tasks, c.ntasks, (const int*)ld.colour_list, cs, small, m.gbar, m.err),
+             "whole sweep launch");
+}
+
+void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
+                    bool forward, cudaStream_t st) {
+  const LevelData& ld = m.levels[level];
+  if (prec == 0) {
+    const double* k = m.vark ? (const double*)ld.k[0] : nullptr;
+    auto* xi = (double*)xin;
+    auto* xo = (double*)xout;
+    auto* bb = (const double*)b;
+    if (m.vark) {
+      if (forward) launch_sweep_t<double, true, true>(m, level, xi, xo, bb, k, st);
+      else launch_sweep_t<double, true, false>(m, level, xi, xo, bb, k, st);
+    } else {
+      if (forward) launch_sweep_t<double, false, true>(m, level, xi, xo, bb, k, st);
+      else launch_sweep_t<double, false, false>(m, level, xi, xo, bb, k, st);
+    }
+  } else {
+    const float* k = m.vark ? (const float*)ld.k[1] : nullptr;
+    auto* xi = (float*)xin;
+    auto* xo = (float*)xout;
+    auto* bb = (const float*)b;
+    if (m.vark) {
+      if (forward) launch_sweep_t<float, true, true>(m, level, xi, xo, bb, k, st);
+      else launch_sweep_t<float, true, false>(m, level, xi, xo, bb, k, st);
+    } else {
+      if (forward) launch_sweep_t<float, false, true>(m, level, xi, xo, bb, k, st);
+      else launch_sweep_t<float, false, false>(m, level, xi, xo, bb, k, st);
+    }
+  }
 }
 
 void face_strip_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,

@@ -160,6 +160,13 @@ struct SweepCfg {
   size_t cap = 0;           // bytes allocated at tasks
 };
 
+// Edge colour classes of one level passed by value to the whole-sweep kernel.
+constexpr int kMaxEdgeColours = 15;
+struct EdgeColours {
+  int n;
+  int ptr[kMaxEdgeColours + 1];
+};
+
 struct LevelData {
   LevelView lv;
   int n_colours = 0;
@@ -173,6 +180,8 @@ struct LevelData {
   void* w[2] = {nullptr, nullptr};  // ping-pong partner of the iterate for Gauss-Seidel sweeps
   void* k[2] = {nullptr, nullptr};  // coefficient: up array then down array (2 * nf * FS)
   SweepCfg sweep[2];                // face sweep configuration per precision
+  int* row_tasks = nullptr;         // device int4 (face, strip, j0, j1) of the row kernels
+  int n_row_tasks = 0;
 };
 
 struct Learned;
@@ -204,6 +213,7 @@ struct Mesh {
   double* partials = nullptr;       // kMaxPartials doubles
   double* scalars = nullptr;        // 16 doubles of device scalars
   int* err = nullptr;               // device error word: 1 = a bounded wait gave up
+  unsigned* gbar = nullptr;         // device state of the whole-sweep kernel: barrier count, generation, task tickets
   int device = 0;
 };
 
@@ -226,6 +236,10 @@ std::vector<int> face_tasks(int nf, int N, int tasks_per_face);
 std::vector<int> strip_tasks(int nf, int N, int rows_per_task);
 void face_ring_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
                       bool forward, const int4* tasks, int ntasks, cudaStream_t st);
+// One whole Gauss-Seidel sweep (vertices, edge colours, faces) in one
+// cooperative launch (the STRIP variant).
+void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
+                    bool forward, cudaStream_t st);
 void face_strip_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
                        bool forward, const int4* tasks, int ntasks, cudaStream_t st);
 size_t face_gs_smem(const LevelView& L, int prec);
@@ -256,6 +270,13 @@ void ve_gs(const Mesh& m, int level, int prec, void* x, const void* b, bool forw
 void residual_f64_to_f32(const Mesh& m, int level, const double* x, const double* b, float* r32,
                          double* norm2_dev, cudaStream_t st);
 void update_f64_from_f32(const Mesh& m, int level, double* x, const float* d32, cudaStream_t st);
+void update_residual_f64(const Mesh& m, int level, const double* x, const float* d32, double* x_new,
+                         const double* b, float* r32, double* norm2_dev, cudaStream_t st);
+// Face part of the row kernels (register strips); returns the partial sums written.
+int face_rows(const Mesh& m, int level, int prec_in, int prec_out, int mode, const void* x, void* x_upd,
+              const float* d, void* out, const void* b, double* partials, double omega, cudaStream_t st);
+std::vector<int> row_strip_tasks(int nf, int N, int rows_per_task);
+constexpr int kMaxRowCtas = 2432;
 
 void check_cuda(cudaError_t e, const char* what);
 

@@ -1,11 +1,12 @@
 // CUDA kernels of the HHG P1 multigrid path (sm_103a).
 //
 // Work decomposition: macro-vertices and edge-interior points are few
-// (0.3 % of the unknowns at level 10); they get one thread each.  Face
-// interiors hold the rest; there one warp walks one lattice row (coalesced
-// loads along i), eight rows per 256-thread block, grid-stride over all
-// (face, row) pairs.  Reductions are per-block partial sums summed in a fixed
-// order by a single block, so norms and dots are bitwise reproducible.
+// (0.3 % of the unknowns at level 10); a vertex gets one warp (its lanes
+// take its face corners), an edge point one thread.  Face interiors hold
+// the rest; their row kernels (face_rows.cu) and Gauss-Seidel sweeps
+// (face_gs_strip.cu, face_gs.cu) walk register strips or row blocks.
+// Reductions are per-block partial sums summed in a fixed order by a single
+// block, so norms and dots are bitwise reproducible.
 #include <cstdio>
 #include <stdexcept>
 #include <string>
@@ -91,57 +92,72 @@ __global__ void k_ghost_fill(MeshTables M, LevelView L, T* __restrict__ v) {
 }
 
 // --------------------------------------------------------------- vertex rows
+// One warp per macro-vertex (vertex_row_warp; in Gauss-Seidel mode
+// vertex_gs, which also pushes the new value to the copies).
+// d != nullptr (residual only): the refinement update x_new = x_old + d of the
+// vertex slot comes first (x is x_new: its face copies are already updated).
 template <typename T, typename TO, bool VARK, int MODE>
-__global__ void k_vertex(MeshTables M, LevelView L, const T* __restrict__ x, TO* out,
-                         const T* __restrict__ b, const T* __restrict__ k, double* partials,
-                         double omega) {
+__global__ void k_vertex(MeshTables M, LevelView L, const T* x, TO* out, const T* __restrict__ b,
+                         const T* __restrict__ k, double* partials, double omega,
+                         const T* __restrict__ xold, const float* __restrict__ d, T* xnew) {
   double acc = 0.0;
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < M.nv; v += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < M.nv; v += nwarps) {
     const VertRec V = M.verts[v];
     const int64_t s = L.v_off + v;
+    T xv = T(0);
+    if (lane == 0) {
+      if (d) {
+        xv = xold[s] + (T)d[s];
+        xnew[s] = xv;
+      } else if (MODE != GS) {
+        xv = x[s];
+      }
+    }
     if (V.dirichlet) {
-      if (MODE == APPLY || MODE == RESID || MODE == SRES) out[s] = TO(0);
-      if (MODE == JAC) out[s] = (TO)x[s];
+      if (lane == 0) {
+        if (MODE == APPLY || MODE == RESID || MODE == SRES) out[s] = TO(0);
+        if (MODE == JAC) out[s] = (TO)x[s];
+      }
+      continue;
+    }
+    if (MODE == GS) {
+      vertex_gs<T, VARK>(M, L, v, lane, (T*)out, b, k);
       continue;
     }
     T off, diag;
-    vertex_row<T, VARK>(M, L, V, x, k, off, diag);
-    if (MODE == SRES) {
-      out[s] = (TO)((b[s] - (diag * x[s] + off)) / diag);
-    } else if (MODE == APPLY) {
-      out[s] = (TO)(diag * x[s] + off);
-    } else if (MODE == RESID) {
-      const T r = b[s] - (diag * x[s] + off);
-      out[s] = (TO)r;
-      acc += (double)r * (double)r;
-    } else if (MODE == JAC) {
-      out[s] = (TO)(x[s] + T(omega) * (b[s] - (diag * x[s] + off)) / diag);
-    } else {  // GS: update in place and push the new value to every copy
-      const T nv = (b[s] - off) / diag;
-      T* xo = (T*)out;
-      xo[s] = nv;
-      for (int c = V.c_begin; c < V.c_end; ++c) {
-        const Corner cn = M.corners[c];
-        xo[L.f_off + (int64_t)cn.face * L.FS + rot_slot(L, cn.rot, 0, 0)] = nv;
-      }
-      for (int c = V.e_begin; c < V.e_end; ++c) {
-        const VertEdge ve = M.vedges[c];
-        xo[L.e_off + (int64_t)ve.edge * L.ES + (ve.is_low ? 0 : L.N)] = nv;
+    vertex_row_warp<T, VARK>(M, L, V, lane, x, k, off, diag);
+    if (lane == 0) {
+      if (MODE == SRES) {
+        out[s] = (TO)((b[s] - (diag * xv + off)) / diag);
+      } else if (MODE == APPLY) {
+        out[s] = (TO)(diag * xv + off);
+      } else if (MODE == RESID) {
+        const T r = b[s] - (diag * xv + off);
+        out[s] = (TO)r;
+        acc += (double)r * (double)r;
+      } else if (MODE == JAC) {
+        out[s] = (TO)(xv + T(omega) * (b[s] - (diag * xv + off)) / diag);
       }
     }
   }
   if (MODE == RESID) {
-    const double s = block_sum(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    const double sum = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
   }
 }
 
 // --------------------------------------------------------------- edge rows
 // list == nullptr: all edge-interior points; else packed e * (N + 1) + t.
+// d != nullptr (residual only, list == nullptr): the refinement update
+// x_new = x_old + d of the edge's slots, end copies included, comes first (x
+// is x_new: its face copies are already updated).
 template <typename T, typename TO, bool VARK, int MODE>
 __global__ void k_edge(MeshTables M, LevelView L, const int* __restrict__ list, int64_t n,
-                       const T* __restrict__ x, TO* out, const T* __restrict__ b,
-                       const T* __restrict__ k, double* partials, double omega) {
+                       const T* x, TO* out, const T* __restrict__ b, const T* __restrict__ k,
+                       double* partials, double omega, const T* __restrict__ xold,
+                       const float* __restrict__ d, T* xnew) {
   double acc = 0.0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -156,79 +172,36 @@ __global__ void k_edge(MeshTables M, LevelView L, const int* __restrict__ list, 
     }
     const EdgeRec E = M.edges[e];
     const int64_t s = L.e_off + (int64_t)e * L.ES + t;
+    T xs;
+    if (d) {
+      xs = xold[s] + (T)d[s];
+      xnew[s] = xs;
+      if (t == 1) xnew[s - 1] = xold[s - 1] + (T)d[s - 1];
+      if (t == L.N - 1) xnew[s + 1] = xold[s + 1] + (T)d[s + 1];
+    } else {
+      xs = MODE == GS ? T(0) : x[s];
+    }
     if (E.dirichlet) {
       if (MODE == APPLY || MODE == RESID || MODE == SRES) out[s] = TO(0);
-      if (MODE == JAC) out[s] = (TO)x[s];
+      if (MODE == JAC) out[s] = (TO)xs;
+      continue;
+    }
+    if (MODE == GS) {
+      edge_gs<T, VARK>(M, L, e, t, (T*)out, b, k);
       continue;
     }
     T off, diag;
     edge_row<T, VARK>(M, L, E, t, x, k, off, diag);
     if (MODE == SRES) {
-      out[s] = (TO)((b[s] - (diag * x[s] + off)) / diag);
+      out[s] = (TO)((b[s] - (diag * xs + off)) / diag);
     } else if (MODE == APPLY) {
-      out[s] = (TO)(diag * x[s] + off);
+      out[s] = (TO)(diag * xs + off);
     } else if (MODE == RESID) {
-      const T r = b[s] - (diag * x[s] + off);
+      const T r = b[s] - (diag * xs + off);
       out[s] = (TO)r;
       acc += (double)r * (double)r;
     } else if (MODE == JAC) {
-      out[s] = (TO)(x[s] + T(omega) * (b[s] - (diag * x[s] + off)) / diag);
-    } else {
-      const T nv = (b[s] - off) / diag;
-      T* xo = (T*)out;
-      xo[s] = nv;
-      for (int q = 0; q < E.nfaces; ++q) {
-        const EdgeSide sd = E.side[q];
-        const int p = sd.aligned ? t : L.N - t;
-        xo[L.f_off + (int64_t)sd.face * L.FS + rot_slot(L, sd.rot, p, 0)] = nv;
-      }
-    }
-  }
-  if (MODE == RESID) {
-    const double s = block_sum(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
-  }
-}
-
-// --------------------------------------------------------------- face rows
-// One warp per interior row j = 1..N-2 of a face (apply, residual, Jacobi;
-// Gauss-Seidel has its own fused kernel).
-template <typename T, typename TO, bool VARK, int MODE>
-__global__ void k_face(MeshTables M, LevelView L, const T* __restrict__ x, TO* out,
-                       const T* __restrict__ b, const T* __restrict__ k, int colour,
-                       double* partials, double omega) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int rows = L.N - 2;
-  const int64_t ntask = (int64_t)M.nf * rows;
-  double acc = 0.0;
-  for (int64_t task = warp; task < ntask; task += nwarps) {
-    const int f = (int)(task / rows);
-    const int j = (int)(task - (int64_t)f * rows) + 1;
-    const FaceRec& F = M.faces[f];
-    const T c0 = (T)F.cot[0], c1 = (T)F.cot[1], c2 = (T)F.cot[2];
-    const int64_t fb = L.f_off + (int64_t)f * L.FS;
-    const T* xf = x + fb;
-    const T* ku = VARK ? k + (int64_t)f * L.FS : nullptr;
-    const T* kd = VARK ? k + (int64_t)(M.nf + f) * L.FS : nullptr;
-    const int iend = L.N - j;  // exclusive
-    const int i0 = 1 + lane, step = 32;
-    for (int i = i0; i < iend; i += step) {
-      const int64_t p = (int64_t)j * L.S + i;
-      T off, diag;
-      face_row<T, VARK>(c0, c1, c2, L.S, xf, ku, kd, p, off, diag);
-      if (MODE == SRES) {
-        out[fb + p] = (TO)((b[fb + p] - (diag * xf[p] + off)) / diag);
-      } else if (MODE == APPLY) {
-        out[fb + p] = (TO)(diag * xf[p] + off);
-      } else if (MODE == RESID) {
-        const T r = b[fb + p] - (diag * xf[p] + off);
-        out[fb + p] = (TO)r;
-        acc += (double)r * (double)r;
-      } else {
-        out[fb + p] = (TO)(xf[p] + T(omega) * (b[fb + p] - (diag * xf[p] + off)) / diag);
-      }
+      out[s] = (TO)(xs + T(omega) * (b[s] - (diag * xs + off)) / diag);
     }
   }
   if (MODE == RESID) {
@@ -599,31 +572,33 @@ void ghost_fill(const Mesh& m, int level, int prec, void* v, cudaStream_t st) {
   else ghost_fill_t(m, level, (float*)v, st);
 }
 
-// Runs the vertex, edge and face kernels of one mode; returns the number of
-// partial sums written (RESID only).
+// Runs the face, edge and vertex kernels of one mode (in that order); returns
+// the number of partial sums written (RESID only; vertex blocks first, then
+// edge blocks, then face blocks, whatever the launch order).  With d (FP64
+// RESID only) the refinement update x_new = x + d is fused in: the face
+// kernel writes every face slot of x_new, the edge and vertex kernels their
+// own slots, and every row is evaluated on x_new.
 template <typename T, typename TO, bool VARK, int MODE>
 static int rows_all(const Mesh& m, int level, const T* x, TO* out, const T* b, double* partials,
-                    double omega, cudaStream_t st) {
+                    double omega, cudaStream_t st, const float* d = nullptr, T* x_new = nullptr) {
   const LevelView& L = m.levels[level].lv;
   const T* k = kptr<T>(m, level);
-  const int bv = blocks_for(m.nv, kThreads, kMaxBlocksV);
-  HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "vertex rows", k_vertex<T, TO, VARK, MODE><<<bv, kThreads, 0, st>>>(m.tab, L, x, out, b, k, partials, omega));
-  int used = bv;
-  if (L.N >= 2) {
-    const int64_t nE = (int64_t)m.ne * (L.N - 1);
-    const int be = blocks_for(nE, kThreads, kMaxBlocksE);
-    HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "edge rows", k_edge<T, TO, VARK, MODE><<<be, kThreads, 0, st>>>(m.tab, L, nullptr, nE, x, out, b, k,
-                                                       partials ? partials + used : nullptr, omega));
-    used += be;
+  const int bv = blocks_for(m.nv, kWarps, kMaxBlocksV);   // one warp per vertex
+  const int64_t nE = L.N >= 2 ? (int64_t)m.ne * (L.N - 1) : 0;
+  const int be = nE > 0 ? blocks_for(nE, kThreads, kMaxBlocksE) : 0;
+  int bf = 0;
+  {
+    LaunchScope ls(HHG_K_FACE_ROWS, level, st);
+    bf = face_rows(m, level, sizeof(T) == 8 ? 0 : 1, sizeof(TO) == 8 ? 0 : 1, MODE, x, d ? x_new : nullptr, d,
+                   out, b, partials ? partials + bv + be : nullptr, omega, st);
   }
-  if (L.N >= 3) {
-    const int64_t ntask = (int64_t)m.nf * (L.N - 2);
-    const int bf = blocks_for(ntask, kWarps, kMaxBlocksF);
-    HHG_LAUNCH(HHG_K_FACE_ROWS, level, st, "face rows", k_face<T, TO, VARK, MODE><<<bf, kThreads, 0, st>>>(m.tab, L, x, out, b, k, 0,
-                                                       partials ? partials + used : nullptr, omega));
-    used += bf;
+  const T* xr = d ? x_new : x;   // the edge and vertex rows read the updated face copies
+  if (nE > 0) {
+    HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "edge rows", k_edge<T, TO, VARK, MODE><<<be, kThreads, 0, st>>>(m.tab, L, nullptr, nE, xr, out, b, k,
+                                                       partials ? partials + bv : nullptr, omega, x, d, x_new));
   }
-  return used;
+  HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "vertex rows", k_vertex<T, TO, VARK, MODE><<<bv, kThreads, 0, st>>>(m.tab, L, xr, out, b, k, partials, omega, x, d, x_new));
+  return bv + be + bf;
 }
 
 template <typename T, typename TO, int MODE>
@@ -664,6 +639,22 @@ void residual_f64_to_f32(const Mesh& m, int level, const double* x, const double
   HHG_LAUNCH(HHG_K_OTHER, level, st, "sum partials", k_sum_partials<<<1, kThreads, 0, st>>>(m.partials, used, norm2_dev, 0));
 }
 
+// x_new = x + d (every slot that holds a value), then r32 = b - A x_new with
+// its sum of squares in *norm2_dev; x_new must not alias x.
+void update_residual_f64(const Mesh& m, int level, const double* x, const float* d32, double* x_new,
+                         const double* b, float* r32, double* norm2_dev, cudaStream_t st) {
+  if (m.levels[level].lv.N < 2) {   // no edge-interior points to carry the edge end copies
+    check_cuda(cudaMemcpyAsync(x_new, x, (size_t)m.levels[level].lv.len * 8, cudaMemcpyDeviceToDevice, st), "copy");
+    update_f64_from_f32(m, level, x_new, d32, st);
+    residual_f64_to_f32(m, level, x_new, b, r32, norm2_dev, st);
+    return;
+  }
+  int used;
+  if (m.vark) used = rows_all<double, float, true, RESID>(m, level, x, r32, b, m.partials, 0.0, st, d32, x_new);
+  else used = rows_all<double, float, false, RESID>(m, level, x, r32, b, m.partials, 0.0, st, d32, x_new);
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "sum partials", k_sum_partials<<<1, kThreads, 0, st>>>(m.partials, used, norm2_dev, 0));
+}
+
 void update_f64_from_f32(const Mesh& m, int level, double* x, const float* d32, cudaStream_t st) {
   const int64_t n = m.levels[level].lv.len;
   HHG_LAUNCH(HHG_K_OTHER, level, st, "update", k_update_f64<<<blocks_for(n, kThreads, 152 * 16), kThreads, 0, st>>>(n, x, d32));
@@ -675,14 +666,14 @@ static void ve_gs_t(const Mesh& m, int level, T* x, const T* b, bool forward, cu
   const LevelView& L = ld.lv;
   const T* k = kptr<T>(m, level);
   auto vertex_phase = [&]() {
-    HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "gs vertex", k_vertex<T, T, VARK, GS><<<blocks_for(m.nv, kThreads, kMaxBlocksV), kThreads, 0, st>>>(
-        m.tab, L, x, x, b, k, nullptr, 0.0));
+    HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "gs vertex", k_vertex<T, T, VARK, GS><<<blocks_for(m.nv, kWarps, kMaxBlocksV), kThreads, 0, st>>>(
+        m.tab, L, x, x, b, k, nullptr, 0.0, nullptr, nullptr, nullptr));
   };
   auto edge_phase = [&](int c) {
     const int64_t n = ld.colour_ptr[c + 1] - ld.colour_ptr[c];
     if (n == 0) return;
     HHG_LAUNCH(HHG_K_EDGE_VERTEX, level, st, "gs edge", k_edge<T, T, VARK, GS><<<blocks_for(n, kThreads, kMaxBlocksE), kThreads, 0, st>>>(
-        m.tab, L, ld.colour_list + ld.colour_ptr[c], n, x, x, b, k, nullptr, 0.0));
+        m.tab, L, ld.colour_list + ld.colour_ptr[c], n, x, x, b, k, nullptr, 0.0, nullptr, nullptr, nullptr));
   };
   if (forward) {
     vertex_phase();
@@ -706,10 +697,16 @@ void ve_gs(const Mesh& m, int level, int prec, void* x, const void* b, bool forw
 
 // Forward: vertices, edge colours (in place on xin), then the fused face
 // sweep xin -> xout with the vertex/edge block copied along.  Backward: the
-// face sweep first, then edge colours and vertices in place on xout.
+// face sweep first, then edge colours and vertices in place on xout.  With
+// the STRIP face kernel all of it is one cooperative launch.
 void gs_sweep(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
               bool forward, cudaStream_t st) {
   const LevelView& L = m.levels[level].lv;
+  if (m.levels[level].sweep[prec].variant == SWEEP_STRIP) {   // the whole sweep in one launch
+    LaunchScope ls(HHG_K_FACE_GS, level, st);
+    gs_sweep_fused(m, level, prec, xin, xout, b, forward, st);
+    return;
+  }
   const size_t prefix = (size_t)L.f_off * (prec == 0 ? 8 : 4);
   if (forward) ve_gs(m, level, prec, xin, b, true, st);
   face_gs3_launch(m, level, prec, xin, xout, b, forward, st);

@@ -285,10 +285,16 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
         ld.w[p] = dev_alloc(m, bytes);
       }
       default_sweep(m, l);
+      {   // row kernels: 96-column strips in blocks of about 64 rows
+        const std::vector<int> rt = row_strip_tasks(m.nf, ld.lv.N, 64);
+        ld.row_tasks = upload(m, rt);
+        ld.n_row_tasks = (int)(rt.size() / 4);
+      }
     }
     m.partials = (double*)dev_alloc(m, kMaxPartials * sizeof(double));
     m.scalars = (double*)dev_alloc(m, 16 * sizeof(double));
     m.err = (int*)dev_alloc(m, 16 * sizeof(int));
+    m.gbar = (unsigned*)dev_alloc(m, 4 * sizeof(unsigned));   // zeroed
     std::vector<double> k0(m.nf, 1.0);
     assemble_level0(m, k0);
     check_cuda(cudaDeviceSynchronize(), "mesh setup");

@@ -83,15 +83,17 @@ __device__ __forceinline__ void edge_row(const MeshTables& M, const LevelView& L
   }
 }
 
-// Macro-vertex v: sum over its face corners; at corner (0,0) of the rotated
-// frame the neighbours are (1,0) and (0,1), both in micro-triangle up(0,0).
+// Macro-vertex row by one warp: the lanes take its face corners (at corner
+// (0,0) of the rotated frame the neighbours are (1,0) and (0,1), both in
+// micro-triangle up(0,0)); a butterfly leaves the same, order-fixed sums in
+// every lane.
 template <typename T, bool VARK>
-__device__ __forceinline__ void vertex_row(const MeshTables& M, const LevelView& L,
-                                           const VertRec& V, const T* __restrict__ x,
-                                           const T* __restrict__ k, T& off, T& diag) {
+__device__ __forceinline__ void vertex_row_warp(const MeshTables& M, const LevelView& L,
+                                                const VertRec& V, int lane, const T* x,
+                                                const T* __restrict__ k, T& off, T& diag) {
   off = T(0);
   diag = T(0);
-  for (int c = V.c_begin; c < V.c_end; ++c) {
+  for (int c = V.c_begin + lane; c < V.c_end; c += 32) {
     const Corner cn = M.corners[c];
     const FaceRec& F = M.faces[cn.face];
     const int r = cn.rot;
@@ -103,6 +105,51 @@ __device__ __forceinline__ void vertex_row(const MeshTables& M, const LevelView&
     const T wa = T(0.5) * c2 * kk, wb = T(0.5) * c1 * kk;
     off -= wa * xa + wb * xb;
     diag += wa + wb;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    off += __shfl_xor_sync(0xffffffffu, off, o);
+    diag += __shfl_xor_sync(0xffffffffu, diag, o);
+  }
+}
+
+// Gauss-Seidel update of free macro-vertex v by one warp, in place, with
+// the new value pushed to every copy (face corners, edge end slots).
+template <typename T, bool VARK>
+__device__ __forceinline__ void vertex_gs(const MeshTables& M, const LevelView& L, int v, int lane,
+                                          T* x, const T* __restrict__ b, const T* __restrict__ k) {
+  const VertRec V = M.verts[v];
+  if (V.dirichlet) return;
+  T off, diag;
+  vertex_row_warp<T, VARK>(M, L, V, lane, x, k, off, diag);
+  const int64_t s = L.v_off + v;
+  const T nv = (b[s] - off) / diag;
+  if (lane == 0) x[s] = nv;
+  for (int c = V.c_begin + lane; c < V.c_end; c += 32) {
+    const Corner cn = M.corners[c];
+    x[L.f_off + (int64_t)cn.face * L.FS + rot_slot(L, cn.rot, 0, 0)] = nv;
+  }
+  for (int c = V.e_begin + lane; c < V.e_end; c += 32) {
+    const VertEdge ve = M.vedges[c];
+    x[L.e_off + (int64_t)ve.edge * L.ES + (ve.is_low ? 0 : L.N)] = nv;
+  }
+}
+
+// Gauss-Seidel update of edge-interior point t of free edge e, in place,
+// with the new value pushed to the edge's slot in each of its faces.
+template <typename T, bool VARK>
+__device__ __forceinline__ void edge_gs(const MeshTables& M, const LevelView& L, int e, int t, T* x,
+                                        const T* __restrict__ b, const T* __restrict__ k) {
+  const EdgeRec E = M.edges[e];
+  if (E.dirichlet) return;
+  T off, diag;
+  edge_row<T, VARK>(M, L, E, t, x, k, off, diag);
+  const int64_t s = L.e_off + (int64_t)e * L.ES + t;
+  const T nv = (b[s] - off) / diag;
+  x[s] = nv;
+  for (int q = 0; q < E.nfaces; ++q) {
+    const EdgeSide sd = E.side[q];
+    const int p = sd.aligned ? t : L.N - t;
+    x[L.f_off + (int64_t)sd.face * L.FS + rot_slot(L, sd.rot, p, 0)] = nv;
   }
 }
 

@@ -1,5 +1,6 @@
 """Host build of the double-float header (csrc/dfloat.cuh) checked against
-its error bounds on random values (CPU; g++)."""
+its error bounds on random values, and its bit-level binary64 <-> binary32
+conversions against the compiler's (CPU; g++)."""
 import os
 import shutil
 import subprocess
@@ -31,7 +32,27 @@ int main() {
   // exact cases
   const double z = to_double(from_double(0.0)), one = to_double(from_double(1.0));
   const double m = to_double(from_double(-0.375)), big = to_double(from_double(3.0e20));
-  printf("%.3e %.3e %.3e %g %g %g %g\n", worst_rt, worst_add, worst_mul, z, one, m, big);
+  // binary64 -> binary32 (round to nearest even) and back, against the
+  // compiler's conversions: random magnitudes, exact ties, overflow, flush
+  long bad = 0;
+  std::uniform_int_distribution<int> E2(-125, 127);
+  std::uniform_int_distribution<uint64_t> M(0, (1ull << 52) - 1);
+  for (int k = 0; k < 2000000; ++k) {
+    double v = std::ldexp(U(rng), E2(rng));
+    if (k % 4 == 1) {   // an exact tie: 24 significant bits followed by a single 1
+      uint64_t u = dbits(v) & ~0x1FFFFFFFull;
+      u |= 0x10000000ull;
+      v = bitsd(u);
+    }
+    if (k % 4 == 2) v = bitsd((dbits(v) & 0xFFF0000000000000ull) | M(rng));
+    if (std::fabs(v) < std::ldexp(1.0, -126)) continue;
+    const float want = (float)v;
+    if (fbits(d2f_rn(v)) != fbits(want)) ++bad;
+    if (f2d_bits(want) != (double)want) ++bad;
+  }
+  const float mx = d2f_rn(3.4028234663852886e38), ov = d2f_rn(3.5e38), tiny = d2f_rn(1e-40);
+  printf("%.3e %.3e %.3e %g %g %g %g %ld %d %g %g\n", worst_rt, worst_add, worst_mul, z, one, m, big, bad,
+         (int)(fbits(mx) == 0x7F7FFFFFu), (double)ov, (double)tiny);
   return 0;
 }
 """
@@ -53,4 +74,9 @@ def test_double_float_error_bounds(tmp_path):
     assert rt <= 1.01 * 2.0 ** -48
     assert add <= 2.0 ** -45         # sloppy addition, absolute in |x| + |y|
     assert mul <= 2.0 ** -44
-    assert [float(v) for v in out[3:]] == [0.0, 1.0, -0.375, 3.0e20]
+    assert [float(v) for v in out[3:7]] == [0.0, 1.0, -0.375, 3.0e20]
+    # binary64 -> binary32 conversion: bit-identical to the compiler's cast
+    # on 2e6 values (a quarter of them exact ties), the largest float kept,
+    # overflow to infinity, magnitudes below 2^-126 flushed to zero
+    assert int(out[7]) == 0
+    assert out[8] == "1" and out[9] == "inf" and float(out[10]) == 0.0
