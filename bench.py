@@ -41,7 +41,7 @@ N_SM = 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one level-9 launch of the
 # FP64 face sweep (annulus, 128 faces), per (kernel variant, split), from the
 # ncu captures summarised under profiles/; None until captured
-TRAFFIC_L9 = {}
+TRAFFIC_L9 = {(1, 32): 390.061568e6 + 120.651776e6}   # k_gs_sweep<double>, default split
 
 
 def parse():
@@ -60,6 +60,12 @@ def parse():
     ap.add_argument("--learned-pairs", type=int, default=10000)
     ap.add_argument("--learned-epochs", type=int, default=12)
     ap.add_argument("--batch-size", type=int, default=64)
+    ap.add_argument("--case", default="bench", choices=["bench", "sweep"],
+                    help="sweep: only four forward Gauss-Seidel sweeps on --level in --prec "
+                         "(the small case of the ncu captures under profiles/), no JSON line")
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--arith", default="ieee", choices=["ieee", "dfloat"],
+                    help="arithmetic of the FP64 face kernels in the sweep case")
     return ap.parse_args()
 
 
@@ -363,7 +369,8 @@ def run_ours(args):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     variant, split = g.sweep_config(L, hhg.F64)
-    kname = ("k_face_gs_strip<double> register-strip sweep, %d-row tasks" % split if variant == hhg.SWEEP_STRIP
+    kname = ("k_gs_sweep<double> whole sweep (vertices, edge colours, register-strip faces, %d-row tasks)" % split
+             if variant == hhg.SWEEP_STRIP
              else "k_face_gs3<double> shared-memory ring sweep, %d row blocks per face" % split)
     # DRAM traffic of one launch from the ncu capture of this kernel at level 9
     # (profiles/), scaled by the points of level L
@@ -448,9 +455,32 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_sweep_case(args):
+    """Four forward Gauss-Seidel sweeps of level --level of the 128-face
+    annulus in --prec with the default kernel configuration (inputs, output
+    and workspace above the 129 MB L2 from level 9 on)."""
+    import torch
+    from paper_1805_10167_gb300 import hhg, inputs
+    xy, tri = inputs.annulus_mesh(32, 2)
+    g = hhg.Mesh(xy, tri, args.level)
+    g.fp64_arith(hhg.ARITH_DFLOAT if args.arith == "dfloat" else hhg.ARITH_IEEE)
+    prec = hhg.F64 if args.prec == "f64" else hhg.F32
+    info = g.info(args.level)
+    dt = torch.float64 if prec == hhg.F64 else torch.float32
+    gen = torch.Generator(device="cuda").manual_seed(1234)
+    x = torch.rand(info.vec_len, dtype=dt, device="cuda", generator=gen)
+    b = torch.rand(info.vec_len, dtype=dt, device="cuda", generator=gen)
+    g.smooth(args.level, x, b, hhg.GS_FWD, sweeps=4, prec=prec)
+    torch.cuda.synchronize()
+    g.close()
+    print("sweep case done")
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.case == "sweep":
+        run_sweep_case(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

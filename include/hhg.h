@@ -239,6 +239,20 @@ typedef enum { HHG_SWEEP_RING = 0, HHG_SWEEP_STRIP = 1 } hhg_sweep_variant;
  * and appended to it.  Synchronous. */
 hhg_status hhg_tune(hhg_mesh mesh, hhg_prec prec, void* stream);
 
+/* Arithmetic of the FP64 face kernels (Gauss-Seidel sweeps on levels with
+ * N > 64, apply and residual rows on levels with N > 64): HHG_ARITH_IEEE
+ * (default) = IEEE binary64; HHG_ARITH_DFLOAT = double-float, the FP64 data
+ * read into pairs of floats (Dekker 1971 / Knuth error-free sums and
+ * FMA-based products, about 47 significant bits) so that the stencil
+ * arithmetic runs on the FP32 pipes.  Storage, vertex and edge rows,
+ * transfers, norms, the coarse solve and the refinement update stay IEEE
+ * binary64; boundary copies are stored bit for bit.  Full precision needs
+ * the data in [2^-74, 2^127] in magnitude (smaller magnitudes keep 24 bits,
+ * below 2^-126 they are flushed to zero).  set != 0: *mode is an input;
+ * set == 0: *mode is written.  Synchronous with respect to the host. */
+typedef enum { HHG_ARITH_IEEE = 0, HHG_ARITH_DFLOAT = 1 } hhg_fp64_arith_mode;
+hhg_status hhg_fp64_arith(hhg_mesh mesh, int32_t set, int32_t* mode);
+
 /* Sets (set != 0: *variant, *param are inputs, param >= 1) or reads
  * (set == 0: written) the face-sweep kernel of one level and precision.
  * Synchronous with respect to the host (the task list is uploaded). */

@@ -459,6 +459,21 @@ hhg_status hhg_tune(hhg_mesh mesh, hhg_prec prec, void* stream) {
   });
 }
 
+hhg_status hhg_fp64_arith(hhg_mesh mesh, int32_t set, int32_t* mode) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    need(mode, "mode");
+    if (set) {
+      if (*mode != HHG_ARITH_IEEE && *mode != HHG_ARITH_DFLOAT) throw ArgError("bad FP64 arithmetic mode");
+      hhg::check_cuda(cudaDeviceSynchronize(), "sync");   // kernels in flight keep their arithmetic
+      m.fp64_df = *mode == HHG_ARITH_DFLOAT;
+    } else {
+      *mode = m.fp64_df ? HHG_ARITH_DFLOAT : HHG_ARITH_IEEE;
+    }
+    return HHG_OK;
+  });
+}
+
 hhg_status hhg_sweep_config(hhg_mesh mesh, int32_t level, hhg_prec prec, int32_t set,
                             int32_t* variant, int32_t* param) {
   return guarded([&]() {

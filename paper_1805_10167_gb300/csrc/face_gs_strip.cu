@@ -25,6 +25,7 @@
 //
 // The sweep reads x_in and writes x_out (ping-pong); each point is stored by
 // exactly one (strip, row block).
+#include "arith.cuh"
 #include "stencil.cuh"
 
 namespace hhg {
@@ -36,86 +37,96 @@ constexpr int kStripWarps = 4;     // independent strip tasks per CTA
 constexpr int kPrefetchRows = 8;   // L2 prefetch distance in rows
 constexpr unsigned kFull = 0xffffffffu;
 
-template <typename T>
+template <typename T, bool DF>
 struct StripArgs {
+  using V = typename Arith<T, DF>::V;
   const T* xg;        // x_in of the face
   T* xo;              // x_out of the face
   const T* bg;        // b of the face
   const T* ku;        // coefficients of the upward / downward micro-triangles
   const T* kd;
-  int64_t S;
-  int N, ic, ws, us, ue, j0, j1;
-  T dinv, w0, w1, w2, c0, c1, c2;
+  int S, N, ic, ws, us, ue, j0, j1;   // offsets inside a face fit in 32 bits
+  V dinv, w0, w1, w2;                 // k = 1 update: b / A_pp and the scaled weights
+  T c0, c1, c2;                       // cotangents (variable k)
 };
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// row r, column i inside the closed triangle (every such slot is allocated)
-__device__ __forceinline__ bool in_tri(int N, int r, int i) { return r >= 0 && r <= N && i <= N - r; }
-
 // Colour phase on row t + DR at the lane's column M; U = t mod 6 places the
 // rows in the six-slot register ring (row r lives in slot r mod 6).
-template <typename T, bool VARK, int DR, int M, int U>
-__device__ __forceinline__ void strip_phase(T (&X)[6][3], T bv, int t, int rlo, int rhi,
-                                            const StripArgs<T>& a) {
+template <typename T, bool DF, bool VARK, int DR, int M, int U>
+__device__ __forceinline__ void strip_phase(typename Arith<T, DF>::V (&X)[6][3], typename Arith<T, DF>::V bv,
+                                            int t, int rlo, int rhi, const StripArgs<T, DF>& a) {
+  using A = Arith<T, DF>;
+  using V = typename A::V;
   constexpr int sc = (U + 6 + DR) % 6, sn = (U + 7 + DR) % 6, ss = (U + 5 + DR) % 6;
   const int r = t + DR;
   // warp-uniform: the row is in this phase's range, is a face-interior row,
   // and holds at least one interior column of the window
   if (r < rlo || r > rhi || r < 1 || r > a.N - 2 || a.ws + 1 > a.N - 1 - r) return;
-  T xe, xse, xw, xnw;
+  V xe, xse, xw, xnw;
   if (M < 2) {
     xe = X[sc][(M + 1) % 3];
     xse = X[ss][(M + 1) % 3];
   } else {
-    xe = __shfl_down_sync(kFull, X[sc][0], 1);
-    xse = __shfl_down_sync(kFull, X[ss][0], 1);
+    xe = A::shfl_down(X[sc][0]);
+    xse = A::shfl_down(X[ss][0]);
   }
   if (M > 0) {
     xw = X[sc][(M + 2) % 3];
     xnw = X[sn][(M + 2) % 3];
   } else {
-    xw = __shfl_up_sync(kFull, X[sc][2], 1);
-    xnw = __shfl_up_sync(kFull, X[sn][2], 1);
+    xw = A::shfl_up(X[sc][2]);
+    xnw = A::shfl_up(X[sn][2]);
   }
-  const T xn = X[sn][M], xs = X[ss][M];
+  const V xn = X[sn][M], xs = X[ss][M];
   const int i = a.ic + M;
   const bool act = i >= 1 && i + r <= a.N - 1;
   if (!VARK) {
-    T acc = bv * a.dinv;
-    acc = fma(a.w2, xe + xw, acc);
-    acc = fma(a.w1, xn + xs, acc);
-    acc = fma(a.w0, xse + xnw, acc);
+    V acc = A::mul(bv, a.dinv);
+    acc = A::fma(a.w2, A::add(xe, xw), acc);
+    acc = A::fma(a.w1, A::add(xn, xs), acc);
+    acc = A::fma(a.w0, A::add(xse, xnw), acc);
     if (act) X[sc][M] = acc;
   } else if (act) {
-    const int64_t p = (int64_t)r * a.S + i;
-    const T u = __ldg(a.ku + p), uw = __ldg(a.ku + p - 1), us = __ldg(a.ku + p - a.S);
-    const T ds = __ldg(a.kd + p - a.S), dw = __ldg(a.kd + p - 1), dsw = __ldg(a.kd + p - 1 - a.S);
-    const T h0 = T(0.5) * a.c0, h1 = T(0.5) * a.c1, h2 = T(0.5) * a.c2;
-    const T we = h2 * (u + ds), ww = h2 * (uw + dsw);
-    const T wn = h1 * (u + dw), wsn = h1 * (us + dsw);
-    const T wse = h0 * (us + ds), wnw = h0 * (uw + dw);
-    const T off = we * xe + ww * xw + wn * xn + wsn * xs + wse * xse + wnw * xnw;
-    const T diag = we + ww + wn + wsn + wse + wnw;
-    X[sc][M] = (bv + off) / diag;
+    const int p = r * a.S + i;
+    const V u = A::in(__ldg(a.ku + p)), uw = A::in(__ldg(a.ku + p - 1)), us = A::in(__ldg(a.ku + p - a.S));
+    const V ds = A::in(__ldg(a.kd + p - a.S)), dw = A::in(__ldg(a.kd + p - 1));
+    const V dsw = A::in(__ldg(a.kd + p - 1 - a.S));
+    const V h0 = A::in(T(0.5) * a.c0), h1 = A::in(T(0.5) * a.c1), h2 = A::in(T(0.5) * a.c2);
+    const V we = A::mul(h2, A::add(u, ds)), ww = A::mul(h2, A::add(uw, dsw));
+    const V wn = A::mul(h1, A::add(u, dw)), wsn = A::mul(h1, A::add(us, dsw));
+    const V wse = A::mul(h0, A::add(us, ds)), wnw = A::mul(h0, A::add(uw, dw));
+    V off = A::mul(we, xe);
+    off = A::fma(ww, xw, off);
+    off = A::fma(wn, xn, off);
+    off = A::fma(wsn, xs, off);
+    off = A::fma(wse, xse, off);
+    off = A::fma(wnw, xnw, off);
+    const V diag = A::add(A::add(A::add(we, ww), A::add(wn, wsn)), A::add(wse, wnw));
+    X[sc][M] = A::div(A::add(bv, off), diag);
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void load_row(T (&dst)[3], int r, int rmax, const StripArgs<T>& a) {
+// Row r of x into the lane's three registers (zero outside the closed
+// triangle and beyond the last row the task reads).
+template <typename T, bool DF>
+__device__ __forceinline__ void load_row(typename Arith<T, DF>::V (&dst)[3], int r, int rmax,
+                                         const StripArgs<T, DF>& a) {
+  using A = Arith<T, DF>;
+  const int lim = (r >= 0 && r <= rmax) ? a.N - r - a.ic : -1;   // element m exists iff m <= lim
+  const T* p = a.xg + (r * a.S + a.ic);
 #pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    const int i = a.ic + m;
-    dst[m] = (r <= rmax && in_tri(a.N, r, i)) ? a.xg[(int64_t)r * a.S + i] : T(0);
-  }
+  for (int m = 0; m < 3; ++m) dst[m] = m <= lim ? A::in(p[m]) : typename A::V{};
 }
 
-template <typename T>
-__device__ __forceinline__ T load_b(int r, int m, const StripArgs<T>& a) {
+template <typename T, bool DF>
+__device__ __forceinline__ typename Arith<T, DF>::V load_b(int r, int m, const StripArgs<T, DF>& a) {
+  using A = Arith<T, DF>;
   const int i = a.ic + m;
-  return (r >= 1 && r <= a.j1 + 1 && in_tri(a.N, r, i)) ? a.bg[(int64_t)r * a.S + i] : T(0);
+  return (r >= 1 && r <= a.j1 + 1 && i <= a.N - r) ? A::in(a.bg[r * a.S + i]) : typename A::V{};
 }
 
 // Column of the phase with colour c on row r: (c + r) mod 3, since the
@@ -129,82 +140,94 @@ struct StripCols {
 };
 
 // b ring: step t uses the three values loaded two steps earlier
-template <typename T, bool FWD, int U>
-__device__ __forceinline__ void load_b_step(T (&Bv)[3], int t, const StripArgs<T>& a) {
+template <typename T, bool DF, bool FWD, int U>
+__device__ __forceinline__ void load_b_step(typename Arith<T, DF>::V (&Bv)[3], int t, const StripArgs<T, DF>& a) {
   using C = StripCols<FWD, U % 3>;
   Bv[0] = load_b(t, C::mA, a);
   Bv[1] = load_b(t - 1, C::mB, a);
   Bv[2] = load_b(t - 2, C::mC, a);
 }
 
-template <typename T, bool VARK, bool FWD, int U>
-__device__ __forceinline__ void strip_step(T (&X)[6][3], T (&Bq)[2][3], int t, int rmax,
-                                           const StripArgs<T>& a) {
+template <typename T, bool DF, bool VARK, bool FWD, int U>
+__device__ __forceinline__ void strip_step(typename Arith<T, DF>::V (&X)[6][3], typename Arith<T, DF>::V (&Bq)[2][3],
+                                           int t, int rmax, const StripArgs<T, DF>& a) {
+  using A = Arith<T, DF>;
+  using V = typename A::V;
   using C = StripCols<FWD, U % 3>;
   // next row of x into the slot of row t - 4 (dead), b for step t + 2, and
   // an L2 prefetch further ahead
-  load_row(X[(U + 2) % 6], t + 2, rmax, a);
-  T Bv[3] = {Bq[U % 2][0], Bq[U % 2][1], Bq[U % 2][2]};
-  load_b_step<T, FWD, (U + 2) % 6>(Bq[U % 2], t + 2, a);
+  load_row<T, DF>(X[(U + 2) % 6], t + 2, rmax, a);
+  const V Bv[3] = {Bq[U % 2][0], Bq[U % 2][1], Bq[U % 2][2]};
+  load_b_step<T, DF, FWD, (U + 2) % 6>(Bq[U % 2], t + 2, a);
   {
-    const int rp = t + 2 + kPrefetchRows, ip = a.ic;
-    if (rp <= rmax && in_tri(a.N, rp, ip)) {
-      prefetch_l2(a.xg + (int64_t)rp * a.S + ip);
-      prefetch_l2(a.bg + (int64_t)rp * a.S + ip);
+    const int rp = t + 2 + kPrefetchRows;
+    if (rp <= rmax && a.ic <= a.N - rp) {
+      prefetch_l2(a.xg + (rp * a.S + a.ic));
+      prefetch_l2(a.bg + (rp * a.S + a.ic));
     }
   }
-  strip_phase<T, VARK, 0, C::mA, U>(X, Bv[0], t, a.j0 - 2, a.j1 + 1, a);
-  strip_phase<T, VARK, -1, C::mB, U>(X, Bv[1], t, a.j0 - 1, a.j1, a);
-  strip_phase<T, VARK, -2, C::mC, U>(X, Bv[2], t, a.j0, a.j1 - 1, a);
+  strip_phase<T, DF, VARK, 0, C::mA, U>(X, Bv[0], t, a.j0 - 2, a.j1 + 1, a);
+  strip_phase<T, DF, VARK, -1, C::mB, U>(X, Bv[1], t, a.j0 - 1, a.j1, a);
+  strip_phase<T, DF, VARK, -2, C::mC, U>(X, Bv[2], t, a.j0, a.j1 - 1, a);
   // row t - 2 is final
   const int r = t - 2;
   if (r >= a.j0 && r < a.j1) {
     constexpr int sl = (U + 4) % 6;
+    const int hi = min(a.ue - 1, a.N - r);   // last stored column of the row
+    const int off = r * a.S;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const int i = a.ic + m;
-      if (i >= a.us && i < a.ue && i <= a.N - r) a.xo[(int64_t)r * a.S + i] = X[sl][m];
+      if (i < a.us || i > hi) continue;
+      if (!DF) {
+        a.xo[off + i] = A::out(X[sl][m]);
+      } else {   // boundary copies are stored bit for bit, only updated points rounded
+        const bool interior = r >= 1 && i >= 1 && i + r <= a.N - 1;
+        a.xo[off + i] = interior ? A::out(X[sl][m]) : a.xg[off + i];
+      }
     }
   }
 }
 
 // The wavefront of one strip task from step t0 (a multiple of 6) to tend.
-template <typename T, bool VARK, bool FWD>
-__device__ __forceinline__ void strip_run(int t0, int tend, int rmax, const StripArgs<T>& a) {
-  T X[6][3];
-  T Bq[2][3];
+template <typename T, bool DF, bool VARK, bool FWD>
+__device__ __forceinline__ void strip_run(int t0, int tend, int rmax, const StripArgs<T, DF>& a) {
+  using V = typename Arith<T, DF>::V;
+  V X[6][3];
+  V Bq[2][3];
   // rows t0 - 3 .. t0 + 1 into slots (r mod 6); b for steps t0, t0 + 1
-  load_row(X[3], t0 - 3, rmax, a);
-  load_row(X[4], t0 - 2, rmax, a);
-  load_row(X[5], t0 - 1, rmax, a);
-  load_row(X[0], t0, rmax, a);
-  load_row(X[1], t0 + 1, rmax, a);
-  load_b_step<T, FWD, 0>(Bq[0], t0, a);
-  load_b_step<T, FWD, 1>(Bq[1], t0 + 1, a);
+  load_row<T, DF>(X[3], t0 - 3, rmax, a);
+  load_row<T, DF>(X[4], t0 - 2, rmax, a);
+  load_row<T, DF>(X[5], t0 - 1, rmax, a);
+  load_row<T, DF>(X[0], t0, rmax, a);
+  load_row<T, DF>(X[1], t0 + 1, rmax, a);
+  load_b_step<T, DF, FWD, 0>(Bq[0], t0, a);
+  load_b_step<T, DF, FWD, 1>(Bq[1], t0 + 1, a);
   for (int t = t0; t <= tend; t += 6) {
-    strip_step<T, VARK, FWD, 0>(X, Bq, t, rmax, a);
+    strip_step<T, DF, VARK, FWD, 0>(X, Bq, t, rmax, a);
     if (t + 1 > tend) break;
-    strip_step<T, VARK, FWD, 1>(X, Bq, t + 1, rmax, a);
+    strip_step<T, DF, VARK, FWD, 1>(X, Bq, t + 1, rmax, a);
     if (t + 2 > tend) break;
-    strip_step<T, VARK, FWD, 2>(X, Bq, t + 2, rmax, a);
+    strip_step<T, DF, VARK, FWD, 2>(X, Bq, t + 2, rmax, a);
     if (t + 3 > tend) break;
-    strip_step<T, VARK, FWD, 3>(X, Bq, t + 3, rmax, a);
+    strip_step<T, DF, VARK, FWD, 3>(X, Bq, t + 3, rmax, a);
     if (t + 4 > tend) break;
-    strip_step<T, VARK, FWD, 4>(X, Bq, t + 4, rmax, a);
+    strip_step<T, DF, VARK, FWD, 4>(X, Bq, t + 4, rmax, a);
     if (t + 5 > tend) break;
-    strip_step<T, VARK, FWD, 5>(X, Bq, t + 5, rmax, a);
+    strip_step<T, DF, VARK, FWD, 5>(X, Bq, t + 5, rmax, a);
   }
 }
 
 // One strip task (face, strip, j0, j1) by one warp.
-template <typename T, bool VARK, bool FWD>
+template <typename T, bool DF, bool VARK, bool FWD>
 __device__ __forceinline__ void strip_task(const MeshTables& M, const LevelView& L, const T* xin, T* xout,
                                            const T* __restrict__ b, const T* __restrict__ k, int4 tk,
                                            int lane) {
+  using A = Arith<T, DF>;
   const int f = tk.x, s = tk.y;
-  StripArgs<T> a;
+  StripArgs<T, DF> a;
   a.N = L.N;
-  a.S = L.S;
+  a.S = (int)L.S;
   a.ws = kStripUseful * s;
   a.ic = a.ws + 3 * lane;
   a.us = s == 0 ? 0 : a.ws + 3;
@@ -221,18 +244,17 @@ __device__ __forceinline__ void strip_task(const MeshTables& M, const LevelView&
   a.c0 = (T)F.cot[0];
   a.c1 = (T)F.cot[1];
   a.c2 = (T)F.cot[2];
-  a.dinv = (T)F.dinv;
-  a.w0 = (T)F.w[0];
-  a.w1 = (T)F.w[1];
-  a.w2 = (T)F.w[2];
+  a.dinv = A::in((T)F.dinv);
+  a.w0 = A::in((T)F.w[0]);
+  a.w1 = A::in((T)F.w[1]);
+  a.w2 = A::in((T)F.w[2]);
   const int rmax = min(a.N, a.j1 + 2);   // last row read
-
   // the wavefront runs from t = j0 - 2 to j1 + 1; it starts at the multiple
   // of 6 at or below j0 - 2 so that the register ring slot of row r is the
   // static r mod 6 (the steps before j0 - 2 only load)
   const int first = a.j0 - 2;
   const int t0 = first >= 0 ? first - first % 6 : -(((-first) + 5) / 6) * 6;
-  strip_run<T, VARK, FWD>(t0, a.j1 + 1, rmax, a);
+  strip_run<T, DF, VARK, FWD>(t0, a.j1 + 1, rmax, a);
 }
 
 template <typename T, bool VARK, bool FWD>
@@ -242,7 +264,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
                     int ntasks) {
   const int wt = blockIdx.x * kStripWarps + (int)(threadIdx.x >> 5);
   if (wt >= ntasks) return;   // whole warp
-  strip_task<T, VARK, FWD>(M, L, xin, xout, b, k, tasks[wt], threadIdx.x & 31);
+  strip_task<T, false, VARK, FWD>(M, L, xin, xout, b, k, tasks[wt], threadIdx.x & 31);
 }
 
 // A whole face of a small level (N <= kSmallN) by one CTA in shared memory:
@@ -350,7 +372,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
 // updated in place, on x_in going forward and on x_out going backward; the
 // faces go from x_in to x_out, and the vertex/edge block of x_in is copied
 // to x_out along with them.  Grid barriers separate the phases.
-template <typename T, bool VARK, bool FWD>
+template <typename T, bool DF, bool VARK, bool FWD>
 __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
     k_gs_sweep(MeshTables M, LevelView L, T* xin, T* xout, const T* __restrict__ b,
                const T* __restrict__ k, const int4* __restrict__ tasks, int ntasks,
@@ -386,7 +408,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
         if (lane == 0) w = atomicAdd(ticket, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= (unsigned)ntasks) break;
-        strip_task<T, VARK, FWD>(M, L, xin, xout, b, k, tasks[w], lane);
+        strip_task<T, DF, VARK, FWD>(M, L, xin, xout, b, k, tasks[w], lane);
       }
       if (lane == 0) {
         __threadfence();
@@ -451,7 +473,7 @@ static void launch_strip_t(const MeshTables& tab, const LevelView& L, const T* x
   k_face_gs_strip<T, VARK, FWD><<<grid, kStripWarps * 32, 0, st>>>(tab, L, xin, xout, b, k, tasks, ntasks);
 }
 
-template <typename T, bool VARK, bool FWD>
+template <typename T, bool DF, bool VARK, bool FWD>
 static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b, const T* k,
                            cudaStream_t st) {
   const LevelData& ld = m.levels[level];
@@ -464,7 +486,7 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
   const int lvl = std::min(level, 31);
   if (resident_at[lvl] == 0) {
     int r = 0;
-    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_gs_sweep<T, VARK, FWD>, kStripWarps * 32, smem),
+    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_gs_sweep<T, DF, VARK, FWD>, kStripWarps * 32, smem),
                "sweep occupancy");
     if (r < 1) throw std::runtime_error("whole-sweep kernel cannot be resident");
     resident_at[lvl] = r;
@@ -493,7 +515,7 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  check_cuda(cudaLaunchKernelEx(&cfg, k_gs_sweep<T, VARK, FWD>, m.tab, ld.lv, xin, xout, b, k,
+  check_cuda(cudaLaunchKernelEx(&cfg, k_gs_sweep<T, DF, VARK, FWD>, m.tab, ld.lv, xin, xout, b, k,
                                 (const int4*)c.tasks, c.ntasks, (const int*)ld.colour_list, cs, small, m.gbar, m.err),
              "whole sweep launch");
 }
@@ -506,12 +528,20 @@ void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, c
     auto* xi = (double*)xin;
     auto* xo = (double*)xout;
     auto* bb = (const double*)b;
-    if (m.vark) {
-      if (forward) launch_sweep_t<double, true, true>(m, level, xi, xo, bb, k, st);
-      else launch_sweep_t<double, true, false>(m, level, xi, xo, bb, k, st);
+    if (m.fp64_df) {
+      if (m.vark) {
+        if (forward) launch_sweep_t<double, true, true, true>(m, level, xi, xo, bb, k, st);
+        else launch_sweep_t<double, true, true, false>(m, level, xi, xo, bb, k, st);
+      } else {
+        if (forward) launch_sweep_t<double, true, false, true>(m, level, xi, xo, bb, k, st);
+        else launch_sweep_t<double, true, false, false>(m, level, xi, xo, bb, k, st);
+      }
+    } else if (m.vark) {
+      if (forward) launch_sweep_t<double, false, true, true>(m, level, xi, xo, bb, k, st);
+      else launch_sweep_t<double, false, true, false>(m, level, xi, xo, bb, k, st);
     } else {
-      if (forward) launch_sweep_t<double, false, true>(m, level, xi, xo, bb, k, st);
-      else launch_sweep_t<double, false, false>(m, level, xi, xo, bb, k, st);
+      if (forward) launch_sweep_t<double, false, false, true>(m, level, xi, xo, bb, k, st);
+      else launch_sweep_t<double, false, false, false>(m, level, xi, xo, bb, k, st);
     }
   } else {
     const float* k = m.vark ? (const float*)ld.k[1] : nullptr;
@@ -519,11 +549,11 @@ void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, c
     auto* xo = (float*)xout;
     auto* bb = (const float*)b;
     if (m.vark) {
-      if (forward) launch_sweep_t<float, true, true>(m, level, xi, xo, bb, k, st);
-      else launch_sweep_t<float, true, false>(m, level, xi, xo, bb, k, st);
+      if (forward) launch_sweep_t<float, false, true, true>(m, level, xi, xo, bb, k, st);
+      else launch_sweep_t<float, false, true, false>(m, level, xi, xo, bb, k, st);
     } else {
-      if (forward) launch_sweep_t<float, false, true>(m, level, xi, xo, bb, k, st);
-      else launch_sweep_t<float, false, false>(m, level, xi, xo, bb, k, st);
+      if (forward) launch_sweep_t<float, false, false, true>(m, level, xi, xo, bb, k, st);
+      else launch_sweep_t<float, false, false, false>(m, level, xi, xo, bb, k, st);
     }
   }
 }

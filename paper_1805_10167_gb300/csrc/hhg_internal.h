@@ -201,6 +201,7 @@ struct Mesh {
   std::vector<void*> allocations;
   std::vector<LevelData> levels;
   bool vark = false;
+  bool fp64_df = false;             // FP64 face kernels in double-float arithmetic (hhg_set_fp64_arith)
   // independent problems (blocks); level-0 coarse solve per block: dense
   // n0 x n0 matrix over its free macro-vertices (row-major, in A0 at a0_off)
   std::vector<Block> h_blocks;

@@ -25,6 +25,7 @@ lib = C.CDLL(LIB_PATH)
 OK, ERR_ARG, ERR_MESH, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_NAN, ERR_TIMEOUT, ERR_BREAKDOWN = range(9)
 F64, F32 = 0, 1
 SWEEP_RING, SWEEP_STRIP = 0, 1
+ARITH_IEEE, ARITH_DFLOAT = 0, 1
 GS_FWD, GS_BWD, JACOBI = 0, 1, 2
 SOLVE_MG, SOLVE_IR, SOLVE_FGMRES = 0, 1, 2
 SMOOTH_GS, SMOOTH_LEARNED = 0, 1
@@ -77,6 +78,7 @@ _SIGS = {
     "hhg_vcycle": [_P, C.c_int32, C.c_int32, _P, _P, C.POINTER(VcycleOpts), _P],
     "hhg_solve": [_P, C.c_int32, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveReport), _P],
     "hhg_tune": [_P, C.c_int32, _P],
+    "hhg_fp64_arith": [_P, C.c_int32, C.POINTER(C.c_int32)],
     "hhg_sweep_config": [_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "hhg_batch_create": [C.c_int32, C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.c_int64),
                          C.POINTER(C.POINTER(C.c_int32)), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -260,6 +262,13 @@ class Mesh:
 
     def tune(self, prec=F64, stream=None):
         _check(lib.hhg_tune(self.h, prec, _stream(stream)))
+
+    def fp64_arith(self, mode=None):
+        """Reads, or sets when mode is given, the arithmetic of the FP64 face
+        kernels (ARITH_IEEE / ARITH_DFLOAT)."""
+        v = C.c_int32(mode or 0)
+        _check(lib.hhg_fp64_arith(self.h, 0 if mode is None else 1, C.byref(v)))
+        return v.value
 
     def sweep_config(self, level, prec=F64, variant=None, param=None):
         """Reads the face-sweep kernel (SWEEP_RING / SWEEP_STRIP) and its split
