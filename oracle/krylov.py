@@ -1,9 +1,18 @@
-"""Flexible GMRES (oracle, FP64).  Paper Sec. 4.3: multigrid can be used as a
-preconditioner inside a Krylov solver.  FGMRES(m) after Saad (1993): right
-preconditioning with a preconditioner that may change from step to step,
-modified Gram-Schmidt, Givens rotations, restart after m steps.  Vectors are
-full-length; inner products run over the free DoFs only (Dirichlet entries
-of the Krylov vectors are zero).
+"""Krylov solvers with a multigrid preconditioner (oracle, FP64; test
+infrastructure only).  Paper Sec. 4.3: multigrid can be used as a
+preconditioner inside a Krylov solver.
+
+* fgmres: FGMRES(m) after Saad (1993): right preconditioning with a
+  preconditioner that may change from step to step, modified Gram-Schmidt,
+  Givens rotations, restart after m steps.
+* pcg: preconditioned conjugate gradients (Hestenes & Stiefel 1952, in the
+  preconditioned form of e.g. Saad, Iterative Methods for Sparse Linear
+  Systems, Alg. 9.1) for a symmetric positive definite operator and a
+  symmetric positive definite preconditioner (one symmetric V-cycle: forward
+  Gauss-Seidel before, backward after, exact coarse solve).
+
+Vectors are full-length; inner products run over the free DoFs only
+(Dirichlet entries of the Krylov vectors are zero).
 """
 from __future__ import annotations
 
@@ -66,4 +75,52 @@ def fgmres(apply_A, precond, b, x0, free, m=20, tol=1e-10, max_iter=200, history
         r[~free] = 0.0
         beta = np.sqrt(dot(r, r))
         hist[-1] = beta
+    return x, hist, steps
+
+
+def pcg(apply_A, precond, b, x0, free, tol=1e-10, max_iter=200):
+    """Solve A x = b from x0 with preconditioner z = precond(r).  Stops when
+    the updated residual satisfies ||r|| <= tol ||b - A x0||; the true
+    residual is then recomputed and, should it miss the tolerance, the
+    iteration restarts from it.  Returns (x, residual-norm history, steps)."""
+    x = x0.copy()
+    dot = lambda u, v: float(np.dot(u[free], v[free]))
+    r = b - apply_A(x)
+    r[~free] = 0.0
+    r0 = np.sqrt(dot(r, r))
+    hist = [r0]
+    steps = 0
+    if r0 == 0.0:
+        return x, hist, steps
+    z = precond(r)
+    z[~free] = 0.0
+    p = z.copy()
+    rz = dot(r, z)
+    while steps < max_iter:
+        q = apply_A(p)
+        q[~free] = 0.0
+        alpha = rz / dot(p, q)
+        x = x + alpha * p
+        r = r - alpha * q
+        steps += 1
+        rn = np.sqrt(dot(r, r))
+        if rn <= tol * r0:
+            rt = b - apply_A(x)
+            rt[~free] = 0.0
+            rn = np.sqrt(dot(rt, rt))
+            hist.append(rn)
+            if rn <= tol * r0:
+                break
+            r = rt                       # restart from the true residual
+            z = precond(r)
+            z[~free] = 0.0
+            p = z.copy()
+            rz = dot(r, z)
+            continue
+        hist.append(rn)
+        z = precond(r)
+        z[~free] = 0.0
+        rz_new = dot(r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
     return x, hist, steps
