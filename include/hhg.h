@@ -91,8 +91,10 @@ typedef struct {
 typedef enum {
   HHG_SOLVE_MG = 0,       /* V-cycles in the precision of x (FP64)          */
   HHG_SOLVE_IR = 1,       /* FP32 V-cycle inside FP64 iterative refinement  */
-  HHG_SOLVE_FGMRES = 2    /* FGMRES(restart), FP64, preconditioned by one   */
+  HHG_SOLVE_FGMRES = 2,   /* FGMRES(restart), FP64, preconditioned by one   */
                           /* FP32 V-cycle (Sec. 4.3: MG as preconditioner)  */
+  HHG_SOLVE_PCG = 3       /* conjugate gradients, FP64, preconditioned by    */
+                          /* one FP64 V(nu1, nu2) cycle (Sec. 4.3)           */
 } hhg_solve_mode;
 
 typedef enum {
@@ -219,7 +221,9 @@ hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
 
 /* Solve A x = b (FP64 vectors) from the initial guess in x until
  * ||b - A x||_2 <= tol * ||b - A x0||_2 (free DoFs).  Synchronous: reads one
- * residual norm back per cycle.  Returns HHG_ERR_NOT_CONVERGED after max_iter
+ * residual norm back per cycle (MG, IR) or Krylov step (FGMRES, PCG; for PCG
+ * the norm of the updated residual, confirmed by the true residual before
+ * the solve returns).  Returns HHG_ERR_NOT_CONVERGED after max_iter
  * (x holds the last iterate) and HHG_ERR_NAN on a non-finite norm.  opts may
  * be NULL (MG, V(3,3), 1e-10, 100); rep may be NULL. */
 hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,

@@ -43,6 +43,23 @@ __global__ void k_normalize(int64_t n, const double* __restrict__ nrm2, const do
     y[i] = x[i] * inv;
 }
 
+// x += alpha p, r -= alpha q with alpha = rz / pq from device memory
+__global__ void k_cg_step(int64_t n, const double* __restrict__ rz, const double* __restrict__ pq,
+                          const double* __restrict__ p, const double* __restrict__ q, double* x, double* r) {
+  const double alpha = *rz / *pq;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+// p = z + (rz_new / rz_old) p
+__global__ void k_cg_dir(int64_t n, const double* __restrict__ rz_new, const double* __restrict__ rz_old,
+                         const double* __restrict__ z, double* p) {
+  const double beta = *rz_new / *rz_old;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
 }  // namespace
 
 struct KrylovSpace {
@@ -50,6 +67,11 @@ struct KrylovSpace {
   std::vector<double*> V, Z;
   double* w = nullptr;
   double* H = nullptr;   // (m + 1) x m device scalars, column-major
+  // conjugate gradients: search direction p, q = A p, device scalars
+  int cg_level = -1;
+  double* p = nullptr;
+  double* q = nullptr;
+  double* cs = nullptr;  // [0] p.q, [1] ||r||^2, [2], [3] r.z (alternating)
 };
 
 static KrylovSpace& space(Mesh& m, int level, int restart) {
@@ -80,6 +102,9 @@ void krylov_free(Mesh& m) {
   for (double* p : K.Z) cudaFree(p);
   if (K.w) cudaFree(K.w);
   if (K.H) cudaFree(K.H);
+  if (K.p) cudaFree(K.p);
+  if (K.q) cudaFree(K.q);
+  if (K.cs) cudaFree(K.cs);
   delete m.krylov;
   m.krylov = nullptr;
 }
@@ -215,6 +240,94 @@ void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_op
     rep->r_final = beta;
   }
   if (smoother_used) *smoother_used = use;
+  if (status != HHG_OK) throw SolveStatus(status);
+}
+
+// Preconditioned conjugate gradients (Sec. 4.3: multigrid as a Krylov
+// preconditioner), preconditioned form of Hestenes & Stiefel: the
+// preconditioner is one FP64 V(nu1, nu2) cycle from zero (forward Gauss-Seidel
+// before, backward after, exact coarse solve: a symmetric positive definite
+// map).  alpha and beta stay on the device; the host reads ||r|| once per
+// step for the stopping test.  When the updated residual meets the tolerance
+// the true residual is recomputed and, should it miss, the iteration restarts
+// from it.  r lives in the level's b workspace, z in its x workspace.
+void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts& o, hhg_solve_report* rep,
+               cudaStream_t st) {
+  if (!m.krylov) m.krylov = new KrylovSpace();
+  KrylovSpace& K = *m.krylov;
+  const LevelData& ld = m.levels[L];
+  const int64_t n = ld.lv.len;
+  if (K.cg_level != L) {
+    if (K.p) cudaFree(K.p);
+    if (K.q) cudaFree(K.q);
+    K.p = K.q = nullptr;
+    check_cuda(cudaMalloc(&K.p, n * sizeof(double)), "cg alloc");
+    check_cuda(cudaMalloc(&K.q, n * sizeof(double)), "cg alloc");
+    if (!K.cs) check_cuda(cudaMalloc(&K.cs, 8 * sizeof(double)), "cg alloc");
+    K.cg_level = L;
+  }
+  double* r = (double*)ld.b[0];
+  double* z = (double*)ld.x[0];
+  const int g = 152 * 8;
+  auto precond = [&]() {
+    zero_vec(m, L, 0, z, st);
+    vcycle_run(m, L, 0, z, r, o.nu1, o.nu2, 0, st);
+  };
+  auto record = [&](int k, double v) {
+    if (rep && rep->history && k < rep->history_cap) rep->history[k] = v;
+  };
+  ghost_fill(m, L, 0, x, st);
+  residual_op(m, L, 0, x, b, r, K.cs + 1, st);
+  const double r0 = std::sqrt(host_scalar(K.cs + 1, st));
+  double rn = r0;
+  record(0, r0);
+  int it = 0, cur = 2;   // r.z of the current step in K.cs[cur]
+  hhg_status status = std::isfinite(r0) ? HHG_OK : HHG_ERR_NAN;
+  auto restart_from_r = [&]() {
+    precond();
+    dot_op(m, L, 0, r, z, K.cs + cur, st);
+    check_cuda(cudaMemcpyAsync(K.p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st), "p = z");
+  };
+  if (status == HHG_OK && r0 > 0.0) restart_from_r();
+  while (status == HHG_OK && rn > o.tol * r0) {
+    if (it >= o.max_iter) {
+      status = HHG_ERR_NOT_CONVERGED;
+      break;
+    }
+    apply_op(m, L, 0, K.p, K.q, st);
+    dot_op(m, L, 0, K.p, K.q, K.cs, st);
+    k_cg_step<<<g, 256, 0, st>>>(n, K.cs + cur, K.cs, K.p, K.q, x, r);
+    check_cuda(cudaGetLastError(), "cg step");
+    dot_op(m, L, 0, r, r, K.cs + 1, st);
+    ++it;
+    rn = std::sqrt(host_scalar(K.cs + 1, st));
+    if (!std::isfinite(rn)) {
+      status = HHG_ERR_NAN;
+      break;
+    }
+    if (rn <= o.tol * r0) {   // confirm with the true residual
+      residual_op(m, L, 0, x, b, r, K.cs + 1, st);
+      rn = std::sqrt(host_scalar(K.cs + 1, st));
+      record(it, rn);
+      if (rn <= o.tol * r0) break;
+      restart_from_r();
+      continue;
+    }
+    record(it, rn);
+    precond();
+    const int nxt = cur == 2 ? 3 : 2;
+    dot_op(m, L, 0, r, z, K.cs + nxt, st);
+    k_cg_dir<<<g, 256, 0, st>>>(n, K.cs + nxt, K.cs + cur, z, K.p);
+    check_cuda(cudaGetLastError(), "cg direction");
+    cur = nxt;
+  }
+  if (rep) {
+    rep->iterations = it;
+    rep->status = status;
+    rep->r0 = r0;
+    rep->r_final = rn;
+    rep->smoother_used = HHG_SMOOTH_GS;
+  }
   if (status != HHG_OK) throw SolveStatus(status);
 }
 
