@@ -306,10 +306,8 @@ void face_gs3_launch(const Mesh& m, int level, int prec, const void* xin, void* 
                      bool forward, cudaStream_t st) {
   const SweepCfg& c = m.levels[level].sweep[prec];
   LaunchScope ls(HHG_K_FACE_GS, level, st);
-  if (c.variant == SWEEP_STRIP)
-    face_strip_launch(m, level, prec, xin, xout, b, forward, (const int4*)c.tasks, c.ntasks, st);
-  else
-    face_ring_launch(m, level, prec, xin, xout, b, forward, (const int4*)c.tasks, c.ntasks, st);
+  if (c.variant != SWEEP_RING) throw std::logic_error("face_gs3_launch: the strip variant runs as a whole sweep");
+  face_ring_launch(m, level, prec, xin, xout, b, forward, (const int4*)c.tasks, c.ntasks, st);
 }
 
 }  // namespace hhg

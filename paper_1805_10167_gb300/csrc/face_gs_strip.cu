@@ -257,16 +257,6 @@ __device__ __forceinline__ void strip_task(const MeshTables& M, const LevelView&
   strip_run<T, DF, VARK, FWD>(t0, a.j1 + 1, rmax, a);
 }
 
-template <typename T, bool VARK, bool FWD>
-__global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
-    k_face_gs_strip(MeshTables M, LevelView L, const T* __restrict__ xin, T* __restrict__ xout,
-                    const T* __restrict__ b, const T* __restrict__ k, const int4* __restrict__ tasks,
-                    int ntasks) {
-  const int wt = blockIdx.x * kStripWarps + (int)(threadIdx.x >> 5);
-  if (wt >= ntasks) return;   // whole warp
-  strip_task<T, false, VARK, FWD>(M, L, xin, xout, b, k, tasks[wt], threadIdx.x & 31);
-}
-
 // A whole face of a small level (N <= kSmallN) by one CTA in shared memory:
 // the closed triangle is staged, the three colours are applied one after the
 // other, every point of a colour at once, and the triangle is written out.
@@ -466,13 +456,6 @@ std::vector<int> strip_tasks(int nf, int N, int rows_per_task) {
   return out;
 }
 
-template <typename T, bool VARK, bool FWD>
-static void launch_strip_t(const MeshTables& tab, const LevelView& L, const T* xin, T* xout,
-                           const T* b, const T* k, const int4* tasks, int ntasks, cudaStream_t st) {
-  const int grid = (ntasks + kStripWarps - 1) / kStripWarps;
-  k_face_gs_strip<T, VARK, FWD><<<grid, kStripWarps * 32, 0, st>>>(tab, L, xin, xout, b, k, tasks, ntasks);
-}
-
 template <typename T, bool DF, bool VARK, bool FWD>
 static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b, const T* k,
                            cudaStream_t st) {
@@ -556,37 +539,6 @@ void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, c
       else launch_sweep_t<float, false, false, false>(m, level, xi, xo, bb, k, st);
     }
   }
-}
-
-void face_strip_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
-                       bool forward, const int4* tasks, int ntasks, cudaStream_t st) {
-  const LevelView& L = m.levels[level].lv;
-  if (prec == 0) {
-    const double* k = m.vark ? (const double*)m.levels[level].k[0] : nullptr;
-    auto* xi = (const double*)xin;
-    auto* xo = (double*)xout;
-    auto* bb = (const double*)b;
-    if (m.vark) {
-      if (forward) launch_strip_t<double, true, true>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
-      else launch_strip_t<double, true, false>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
-    } else {
-      if (forward) launch_strip_t<double, false, true>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
-      else launch_strip_t<double, false, false>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
-    }
-  } else {
-    const float* k = m.vark ? (const float*)m.levels[level].k[1] : nullptr;
-    auto* xi = (const float*)xin;
-    auto* xo = (float*)xout;
-    auto* bb = (const float*)b;
-    if (m.vark) {
-      if (forward) launch_strip_t<float, true, true>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
-      else launch_strip_t<float, true, false>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
-    } else {
-      if (forward) launch_strip_t<float, false, true>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
-      else launch_strip_t<float, false, false>(m.tab, L, xi, xo, bb, k, tasks, ntasks, st);
-    }
-  }
-  check_cuda(cudaGetLastError(), "face strip sweep");
 }
 
 }  // namespace hhg

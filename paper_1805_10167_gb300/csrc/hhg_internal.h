@@ -241,8 +241,6 @@ void face_ring_launch(const Mesh& m, int level, int prec, const void* xin, void*
 // cooperative launch (the STRIP variant).
 void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
                     bool forward, cudaStream_t st);
-void face_strip_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
-                       bool forward, const int4* tasks, int ntasks, cudaStream_t st);
 size_t face_gs_smem(const LevelView& L, int prec);
 void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,
                   void* work, cudaStream_t st);

@@ -367,15 +367,19 @@ __global__ void k_prolong_face(MeshTables M, LevelView Lf, LevelView Lc, const T
     const T* c = xc + Lc.f_off + (int64_t)f * Lc.FS;
     T* o = xf + Lf.f_off + (int64_t)f * Lf.FS + (int64_t)j * Lf.S;
     const int J = j >> 1;
+    // branch-free (neighbouring lanes alternate between coincident and
+    // interpolated points; a divergent branch would cost the FP64 pipe both
+    // paths): x_f += w1 c[q1] + w2 c[q2] with (w1, w2) = (1, 0) at coincident
+    // points and (1/2, 1/2) between two coarse points
     for (int i = lane; i <= Lf.N - j; i += 32) {
       const int I = i >> 1;
       const int64_t q = (int64_t)J * Sc + I;
-      T val;
-      if (!(i & 1) && !(j & 1)) val = c[q];
-      else if ((i & 1) && !(j & 1)) val = T(0.5) * (c[q] + c[q + 1]);
-      else if (!(i & 1)) val = T(0.5) * (c[q] + c[q + Sc]);
-      else val = T(0.5) * (c[q + 1] + c[q + Sc]);
-      o[i] += val;
+      const bool io = i & 1, jo = j & 1;
+      // (even, even): q; (odd, even): q, q+1; (even, odd): q, q+Sc; (odd, odd): q+1, q+Sc
+      const int64_t qa = (io && jo) ? q + 1 : q;
+      const int64_t qb = jo ? q + Sc : (io ? q + 1 : q);
+      const T wa = (io || jo) ? T(0.5) : T(1), wb = (io || jo) ? T(0.5) : T(0);
+      o[i] = fma(wa, c[qa], fma(wb, c[qb], o[i]));
     }
   }
 }
