@@ -9,7 +9,11 @@ preconditioner inside a Krylov solver.
   preconditioned form of e.g. Saad, Iterative Methods for Sparse Linear
   Systems, Alg. 9.1) for a symmetric positive definite operator and a
   symmetric positive definite preconditioner (one symmetric V-cycle: forward
-  Gauss-Seidel before, backward after, exact coarse solve).
+  Gauss-Seidel before, backward after, exact coarse solve).  flexible=True
+  takes the Polak-Ribiere form of beta, z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k)
+  (Notay 2000, "Flexible conjugate gradients"), which stays robust when the
+  preconditioner varies slightly from step to step (a V-cycle in FP32); with
+  r_{k+1} = r_k - alpha q_k it reads -alpha (q_k.z_{k+1}) / (z_k.r_k).
 
 Vectors are full-length; inner products run over the free DoFs only
 (Dirichlet entries of the Krylov vectors are zero).
@@ -78,7 +82,7 @@ def fgmres(apply_A, precond, b, x0, free, m=20, tol=1e-10, max_iter=200, history
     return x, hist, steps
 
 
-def pcg(apply_A, precond, b, x0, free, tol=1e-10, max_iter=200):
+def pcg(apply_A, precond, b, x0, free, tol=1e-10, max_iter=200, flexible=False):
     """Solve A x = b from x0 with preconditioner z = precond(r).  Stops when
     the updated residual satisfies ||r|| <= tol ||b - A x0||; the true
     residual is then recomputed and, should it miss the tolerance, the
@@ -121,6 +125,7 @@ def pcg(apply_A, precond, b, x0, free, tol=1e-10, max_iter=200):
         z = precond(r)
         z[~free] = 0.0
         rz_new = dot(r, z)
-        p = z + (rz_new / rz) * p
+        beta = -alpha * dot(q, z) / rz if flexible else rz_new / rz
+        p = z + beta * p
         rz = rz_new
     return x, hist, steps

@@ -93,3 +93,39 @@ def test_pcg_beats_plain_multigrid_in_cycles():
     assert hist[-1] <= 1e-10 * hist[0]
     _, mg_hist = mg.solve(H, np.zeros(lv.n), b.copy(), 3, 3, tol=1e-10)
     assert steps <= len(mg_hist) - 1
+
+
+def test_flexible_beta_equals_standard_beta_for_a_fixed_preconditioner():
+    """For a fixed symmetric preconditioner z_{k+1}.r_k = 0 in exact
+    arithmetic, so the flexible (Polak-Ribiere) and the standard
+    (Fletcher-Reeves) beta give the same iterates up to rounding."""
+    H, lv, b = _problem(4)
+    fr = lv.free
+    pre = lambda v: mg.vcycle(H, 4, np.zeros(lv.n), v, 2, 2)
+    for k in (2, 5):
+        xs, _, _ = krylov.pcg(lambda v: H.apply(4, v), pre, b, np.zeros(lv.n), fr, tol=0.0, max_iter=k)
+        xf, _, _ = krylov.pcg(lambda v: H.apply(4, v), pre, b, np.zeros(lv.n), fr, tol=0.0, max_iter=k,
+                              flexible=True)
+        np.testing.assert_allclose(xf[fr], xs[fr], rtol=1e-9, atol=1e-12)
+
+
+def test_flexible_cg_with_a_single_precision_preconditioner_reaches_fp64_tolerance():
+    """A V-cycle whose result is rounded to FP32 (a preconditioner that
+    varies with its input's rounding, as the FP32 V-cycle does) inside
+    flexible CG still reaches 1e-10 in FP64, within a step or two of the
+    exact-arithmetic step count."""
+    H, lv, b = _problem(5)
+    fr = lv.free
+
+    def pre32(v):
+        s = np.abs(v).max()
+        z = mg.vcycle(H, 5, np.zeros(lv.n), (v / s).astype(np.float32).astype(np.float64), 3, 3)
+        return z.astype(np.float32).astype(np.float64) * s
+    x, hist, steps = krylov.pcg(lambda v: H.apply(5, v), pre32, b, np.zeros(lv.n), fr, tol=1e-10,
+                                flexible=True)
+    assert hist[-1] <= 1e-10 * hist[0]
+    r = b - H.apply(5, x)
+    assert np.linalg.norm(r[fr]) <= 1.01e-10 * hist[0]
+    pre = lambda v: mg.vcycle(H, 5, np.zeros(lv.n), v, 3, 3)
+    _, _, steps64 = krylov.pcg(lambda v: H.apply(5, v), pre, b, np.zeros(lv.n), fr, tol=1e-10)
+    assert steps <= steps64 + 2
