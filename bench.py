@@ -17,8 +17,9 @@ seconds / 1e9 over all ranks (independent replicas, weak scaling), with
                inside the timed region, against the FP64 ALU peak;
   cpu_baseline the FP64 oracle timed on the host cores on a bounded sample;
   time_to_tol  wall time to a 1e-10 relative FP64 residual: FP64 V-cycles,
-               FP32 V-cycles inside FP64 iterative refinement, and
-               V-cycle-preconditioned conjugate gradients (FP64).
+               FP32 V-cycles inside FP64 iterative refinement,
+               V-cycle-preconditioned conjugate gradients (FP64), and
+               flexible CG preconditioned by an FP32 V-cycle.
 ``--impl reference`` times the oracle instead (rank 0 only).
 """
 from __future__ import annotations
@@ -241,7 +242,8 @@ def run_vark(args, dev, st):
     out = {"workload": f"annulus-128faces-L{L}-grf-k-V(3,3)", "free_dofs": info.n_free,
            "fp64_mg": timed_solve(g, L, b, st, mode=hhg.SOLVE_MG),
            "fp32_ir": timed_solve(g, L, b, st, mode=hhg.SOLVE_IR),
-           "fp64_pcg": timed_solve(g, L, b, st, mode=hhg.SOLVE_PCG)}
+           "fp64_pcg": timed_solve(g, L, b, st, mode=hhg.SOLVE_PCG),
+           "fp32_fpcg": timed_solve(g, L, b, st, mode=hhg.SOLVE_FPCG)}
     out["ir_speedup"] = out["fp64_mg"]["seconds"] / out["fp32_ir"]["seconds"]
     g.close()
     return out
@@ -417,7 +419,8 @@ def run_ours(args):
     solve = None
     if not args.no_solve:
         solve = {}
-        for name, mode in (("fp64_mg", hhg.SOLVE_MG), ("fp32_ir", hhg.SOLVE_IR), ("fp64_pcg", hhg.SOLVE_PCG)):
+        for name, mode in (("fp64_mg", hhg.SOLVE_MG), ("fp32_ir", hhg.SOLVE_IR), ("fp64_pcg", hhg.SOLVE_PCG),
+                           ("fp32_fpcg", hhg.SOLVE_FPCG)):
             x.zero_()
             g.solve(L, x, b, mode=mode, stream=st)          # warm-up
             x.zero_()

@@ -93,8 +93,10 @@ typedef enum {
   HHG_SOLVE_IR = 1,       /* FP32 V-cycle inside FP64 iterative refinement  */
   HHG_SOLVE_FGMRES = 2,   /* FGMRES(restart), FP64, preconditioned by one   */
                           /* FP32 V-cycle (Sec. 4.3: MG as preconditioner)  */
-  HHG_SOLVE_PCG = 3       /* conjugate gradients, FP64, preconditioned by    */
+  HHG_SOLVE_PCG = 3,      /* conjugate gradients, FP64, preconditioned by    */
                           /* one FP64 V(nu1, nu2) cycle (Sec. 4.3)           */
+  HHG_SOLVE_FPCG = 4      /* flexible conjugate gradients, FP64 vectors and  */
+                          /* operator, preconditioned by one FP32 V-cycle    */
 } hhg_solve_mode;
 
 typedef enum {

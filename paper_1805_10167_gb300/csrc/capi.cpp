@@ -382,10 +382,11 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
     hhg_solve_opts o{HHG_SOLVE_MG, 3, 3, 100, 1e-10, HHG_SMOOTH_GS, 20};
     if (opts) o = *opts;
     if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 0 || !(o.tol >= 0.0)) throw ArgError("bad solve options");
-    if (o.mode != HHG_SOLVE_MG && o.mode != HHG_SOLVE_IR && o.mode != HHG_SOLVE_FGMRES && o.mode != HHG_SOLVE_PCG)
+    if (o.mode != HHG_SOLVE_MG && o.mode != HHG_SOLVE_IR && o.mode != HHG_SOLVE_FGMRES && o.mode != HHG_SOLVE_PCG &&
+        o.mode != HHG_SOLVE_FPCG)
       throw ArgError("bad solve mode");
-    if (o.mode == HHG_SOLVE_PCG) {
-      hhg::pcg_solve(m, level, x, b, o, rep, S(stream));
+    if (o.mode == HHG_SOLVE_PCG || o.mode == HHG_SOLVE_FPCG) {
+      hhg::pcg_solve(m, level, x, b, o, rep, o.mode == HHG_SOLVE_FPCG, S(stream));
       if (device_timed_out(m, S(stream))) return fail(HHG_ERR_TIMEOUT, "a device-side wait gave up");
       return HHG_OK;
     }

@@ -309,7 +309,7 @@ void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr,
                    float* loss_hist, cudaStream_t st);
 void krylov_free(Mesh& m);
 void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts& o, hhg_solve_report* rep,
-               cudaStream_t st);
+               bool mixed, cudaStream_t st);
 void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts& o, int smoother,
                   int restart, hhg_solve_report* rep, int* smoother_used, cudaStream_t st);
 void zero_dirichlet_and_ghosts(const Mesh& m, int level, double* x, cudaStream_t st);

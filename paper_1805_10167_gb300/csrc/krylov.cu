@@ -13,19 +13,22 @@
 #include <cmath>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "hhg_internal.h"
 
 namespace hhg {
 
 namespace {
 
+// FP64 <-> FP32 casts by integer bit operations (round to nearest even;
+// magnitudes below 2^-126 flushed), off the FP64 pipe
 __global__ void k_cast_f64_f32(int64_t n, const double* __restrict__ a, float* __restrict__ o) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = (float)a[i];
+    o[i] = d2f_rn(a[i]);
 }
 __global__ void k_cast_f32_f64(int64_t n, const float* __restrict__ a, double* __restrict__ o) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = (double)a[i];
+    o[i] = f2d_bits(a[i]);
 }
 // y -= h * x with h read from device memory
 __global__ void k_axpy_dev(int64_t n, const double* __restrict__ h, const double* __restrict__ x, double* y) {
@@ -43,21 +46,119 @@ __global__ void k_normalize(int64_t n, const double* __restrict__ nrm2, const do
     y[i] = x[i] * inv;
 }
 
-// x += alpha p, r -= alpha q with alpha = rz / pq from device memory
-__global__ void k_cg_step(int64_t n, const double* __restrict__ rz, const double* __restrict__ pq,
-                          const double* __restrict__ p, const double* __restrict__ q, double* x, double* r) {
-  const double alpha = *rz / *pq;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    r[i] -= alpha * q[i];
+
+// ------------------------------------------------------------- fused vector passes
+// Whole-vector steps of the flexible CG that touch only the slots that hold
+// values (vertices, edge slots t = 0..N, face slots i + j <= N; the padding
+// of the face squares is skipped), with their inner products over the owned
+// free unknowns accumulated on the way: per-thread sums, a fixed-order
+// reduction per block, partials summed in order by one block.
+constexpr int kVecThreads = 256;
+constexpr int kVecBlocks = 1216;   // 8 per SM; kVecBlocks <= kMaxPartials / 2
+
+template <typename F>
+__device__ __forceinline__ void for_valid_slots(const MeshTables& M, const LevelView& L, F f) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = tid; v < M.nv; v += nth) f(L.v_off + v, !M.verts[v].dirichlet);
+  const int64_t ne = (int64_t)M.ne * (L.N + 1);
+  for (int64_t q = tid; q < ne; q += nth) {
+    const int64_t e = q / (L.N + 1), t = q - e * (L.N + 1);
+    f(L.e_off + e * L.ES + t, t >= 1 && t <= L.N - 1 && !M.edges[e].dirichlet);
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t nrow = (int64_t)M.nf * (L.N + 1);
+  for (int64_t w = tid >> 5; w < nrow; w += nth >> 5) {
+    const int64_t fc = w / (L.N + 1);
+    const int j = (int)(w - fc * (L.N + 1));
+    const int64_t base = L.f_off + fc * L.FS + (int64_t)j * L.S;
+    for (int i = lane; i <= L.N - j; i += 32) f(base + i, i >= 1 && j >= 1 && i + j <= L.N - 1);
   }
 }
-// p = z + (rz_new / rz_old) p
-__global__ void k_cg_dir(int64_t n, const double* __restrict__ rz_new, const double* __restrict__ rz_old,
-                         const double* __restrict__ z, double* p) {
-  const double beta = *rz_new / *rz_old;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+
+__device__ __forceinline__ void block_sums(double a, double b, double* out, int stride) {
+  __shared__ double ra[kVecThreads / 32], rb[kVecThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ra[threadIdx.x >> 5] = a;
+    rb[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < kVecThreads / 32; ++w) {
+      sa += ra[w];
+      sb += rb[w];
+    }
+    out[blockIdx.x] = sa;
+    out[stride + blockIdx.x] = sb;
+  }
+}
+
+// x += alpha p (every slot), r -= alpha q and r32 = r rounded to FP32 (owned
+// slots), with alpha = rz / pq; partial sums of r.r
+__global__ void __launch_bounds__(kVecThreads) k_fcg_step(MeshTables M, LevelView L, const double* __restrict__ rz,
+                                                         const double* __restrict__ pq, const double* __restrict__ p,
+                                                         const double* __restrict__ q, double* x, double* r,
+                                                         float* r32, double* partials) {
+  const double alpha = *rz / *pq;
+  double rr = 0.0;
+  for_valid_slots(M, L, [&](int64_t s, bool own) {
+    x[s] += alpha * p[s];
+    if (own) {
+      const double v = r[s] - alpha * q[s];
+      r[s] = v;
+      if (r32) r32[s] = d2f_rn(v);
+      rr = fma(v, v, rr);
+    }
+  });
+  block_sums(rr, 0.0, partials, gridDim.x);
+}
+
+// z = z32 widened (every slot; z32 == nullptr: z as it is); partial sums of
+// r.z and q.z
+__global__ void __launch_bounds__(kVecThreads) k_fcg_widen(MeshTables M, LevelView L, const float* __restrict__ z32,
+                                                          double* z, const double* __restrict__ r,
+                                                          const double* __restrict__ q, double* partials) {
+  double rz = 0.0, qz = 0.0;
+  for_valid_slots(M, L, [&](int64_t s, bool own) {
+    double v;
+    if (z32) {
+      v = f2d_bits(z32[s]);
+      z[s] = v;
+    } else {
+      v = z[s];
+    }
+    if (own) {
+      rz = fma(r[s], v, rz);
+      qz = fma(q[s], v, qz);
+    }
+  });
+  block_sums(rz, qz, partials, gridDim.x);
+}
+
+// p = z + beta p (every slot), beta = sign * num / den
+__global__ void __launch_bounds__(kVecThreads) k_fcg_dir(MeshTables M, LevelView L, const double* __restrict__ num,
+                                                        const double* __restrict__ den, double sign,
+                                                        const double* __restrict__ z, double* p) {
+  const double beta = sign * *num / *den;
+  for_valid_slots(M, L, [&](int64_t s, bool) { p[s] = z[s] + beta * p[s]; });
+}
+
+__global__ void k_sum_ordered(const double* __restrict__ partials, int n, double* out) {
+  __shared__ double red[kVecThreads / 32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+    *out = sum;
+  }
 }
 
 }  // namespace
@@ -247,12 +348,15 @@ void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_op
 // preconditioner), preconditioned form of Hestenes & Stiefel: the
 // preconditioner is one FP64 V(nu1, nu2) cycle from zero (forward Gauss-Seidel
 // before, backward after, exact coarse solve: a symmetric positive definite
-// map).  alpha and beta stay on the device; the host reads ||r|| once per
+// map).  mixed: the V-cycle runs in FP32 (r rounded to FP32, z widened back)
+// and beta takes the flexible Polak-Ribiere form -(q.z_new) / (p.q) (Notay
+// 2000), robust to a preconditioner that varies with rounding; vectors,
+// operator, dots and the stopping test stay FP64.  alpha and beta stay on the device; the host reads ||r|| once per
 // step for the stopping test.  When the updated residual meets the tolerance
 // the true residual is recomputed and, should it miss, the iteration restarts
 // from it.  r lives in the level's b workspace, z in its x workspace.
 void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts& o, hhg_solve_report* rep,
-               cudaStream_t st) {
+               bool mixed, cudaStream_t st) {
   if (!m.krylov) m.krylov = new KrylovSpace();
   KrylovSpace& K = *m.krylov;
   const LevelData& ld = m.levels[L];
@@ -268,13 +372,26 @@ void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts&
   }
   double* r = (double*)ld.b[0];
   double* z = (double*)ld.x[0];
-  const int g = 152 * 8;
-  auto precond = [&]() {
-    zero_vec(m, L, 0, z, st);
-    vcycle_run(m, L, 0, z, r, o.nu1, o.nu2, 0, st);
-  };
+  float* r32 = (float*)ld.b[1];
+  float* z32 = (float*)ld.x[1];
+  double* part = m.partials;
+  const int nb = kVecBlocks;
   auto record = [&](int k, double v) {
     if (rep && rep->history && k < rep->history_cap) rep->history[k] = v;
+  };
+  // z = M(r) (r32 already holds r in the mixed form); r.z into cs[slot], q.z into cs[4]
+  auto precond = [&](int slot) {
+    if (mixed) {
+      zero_vec(m, L, 1, z32, st);
+      vcycle_run(m, L, 1, z32, r32, o.nu1, o.nu2, 0, st);
+    } else {
+      zero_vec(m, L, 0, z, st);
+      vcycle_run(m, L, 0, z, r, o.nu1, o.nu2, 0, st);
+    }
+    k_fcg_widen<<<nb, kVecThreads, 0, st>>>(m.tab, ld.lv, mixed ? z32 : nullptr, z, r, K.q, part);
+    check_cuda(cudaGetLastError(), "cg widen");
+    k_sum_ordered<<<1, kVecThreads, 0, st>>>(part, nb, K.cs + slot);
+    k_sum_ordered<<<1, kVecThreads, 0, st>>>(part + nb, nb, K.cs + 4);
   };
   ghost_fill(m, L, 0, x, st);
   residual_op(m, L, 0, x, b, r, K.cs + 1, st);
@@ -284,8 +401,12 @@ void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts&
   int it = 0, cur = 2;   // r.z of the current step in K.cs[cur]
   hhg_status status = std::isfinite(r0) ? HHG_OK : HHG_ERR_NAN;
   auto restart_from_r = [&]() {
-    precond();
-    dot_op(m, L, 0, r, z, K.cs + cur, st);
+    if (mixed) {
+      k_cast_f64_f32<<<152 * 8, 256, 0, st>>>(n, r, r32);
+      check_cuda(cudaGetLastError(), "cast");
+    }
+    check_cuda(cudaMemsetAsync(K.q, 0, n * sizeof(double), st), "q = 0");
+    precond(cur);
     check_cuda(cudaMemcpyAsync(K.p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st), "p = z");
   };
   if (status == HHG_OK && r0 > 0.0) restart_from_r();
@@ -296,9 +417,10 @@ void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts&
     }
     apply_op(m, L, 0, K.p, K.q, st);
     dot_op(m, L, 0, K.p, K.q, K.cs, st);
-    k_cg_step<<<g, 256, 0, st>>>(n, K.cs + cur, K.cs, K.p, K.q, x, r);
+    // x += alpha p, r -= alpha q (and its FP32 copy), ||r||^2
+    k_fcg_step<<<nb, kVecThreads, 0, st>>>(m.tab, ld.lv, K.cs + cur, K.cs, K.p, K.q, x, r, mixed ? r32 : nullptr, part);
     check_cuda(cudaGetLastError(), "cg step");
-    dot_op(m, L, 0, r, r, K.cs + 1, st);
+    k_sum_ordered<<<1, kVecThreads, 0, st>>>(part, nb, K.cs + 1);
     ++it;
     rn = std::sqrt(host_scalar(K.cs + 1, st));
     if (!std::isfinite(rn)) {
@@ -314,10 +436,12 @@ void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts&
       continue;
     }
     record(it, rn);
-    precond();
     const int nxt = cur == 2 ? 3 : 2;
-    dot_op(m, L, 0, r, z, K.cs + nxt, st);
-    k_cg_dir<<<g, 256, 0, st>>>(n, K.cs + nxt, K.cs + cur, z, K.p);
+    precond(nxt);
+    if (mixed)   // flexible: beta = -(q.z) / (p.q)
+      k_fcg_dir<<<nb, kVecThreads, 0, st>>>(m.tab, ld.lv, K.cs + 4, K.cs, -1.0, z, K.p);
+    else         // beta = (r.z)_new / (r.z)_old
+      k_fcg_dir<<<nb, kVecThreads, 0, st>>>(m.tab, ld.lv, K.cs + nxt, K.cs + cur, 1.0, z, K.p);
     check_cuda(cudaGetLastError(), "cg direction");
     cur = nxt;
   }

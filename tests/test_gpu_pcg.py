@@ -64,3 +64,26 @@ def test_pcg_reaches_tolerance_on_multi_strip_faces_in_fewer_cycles_than_mg():
     assert rep["iterations"] <= rep_mg["iterations"]
     assert rel_err(got, P.from_dev(L, xm)) < 1e-8
     P.close()
+
+
+@pytest.mark.parametrize("name,L,vark", [("square", 7, False), ("annulus", 6, True)])
+def test_flexible_cg_with_fp32_vcycle_reaches_fp64_tolerance(name, L, vark):
+    """Flexible CG (FP64 vectors, operator and dots) preconditioned by one
+    FP32 V(3,3) cycle reaches the 1e-10 FP64 residual, checked by the
+    oracle, in at most two steps more than FP64-preconditioned CG."""
+    P = Pair(name, L, vark=vark)
+    hhg = P.hhg
+    lv = P.H.levels[L]
+    from paper_1805_10167_gb300 import inputs
+    b = inputs.uniform_pm1(lv.n, 4321)
+    b[~lv.free] = 0.0
+    x = P.to_dev(L, np.zeros(lv.n))
+    st, rep = P.g.solve(L, x, P.to_dev(L, b), mode=hhg.SOLVE_FPCG, nu1=3, nu2=3, tol=1e-10)
+    got = P.from_dev(L, x)
+    assert mg.norm_free(P.H, L, P.H.residual(L, got, b)) <= 1.01e-10 * rep["r0"]
+    want, hist, steps = _oracle_pcg(P, L, b, (3, 3), 100, 1e-12)
+    assert rel_err(got, want) < 1e-8
+    x64 = P.to_dev(L, np.zeros(lv.n))
+    st, rep64 = P.g.solve(L, x64, P.to_dev(L, b), mode=hhg.SOLVE_PCG, nu1=3, nu2=3, tol=1e-10)
+    assert rep["iterations"] <= rep64["iterations"] + 2
+    P.close()
