@@ -116,6 +116,11 @@ struct BatchGroup {
   double* canon = nullptr;     // group canonical vector (n_nodes of the merged mesh)
   double* norms = nullptr;     // per-problem squared norms (device)
   int64_t n_nodes = 0;
+  // flexible CG (allocated on first use): search direction, its image, and
+  // per-problem scalars (6 x problems)
+  double* p = nullptr;
+  double* q = nullptr;
+  double* sc = nullptr;
 };
 
 struct Batch {
@@ -235,6 +240,9 @@ void batch_destroy(Batch* B) {
     cudaEventDestroy(g.join);
     cudaFree(g.canon);
     cudaFree(g.norms);
+    if (g.p) cudaFree(g.p);
+    if (g.q) cudaFree(g.q);
+    if (g.sc) cudaFree(g.sc);
   }
   if (B->fork) cudaEventDestroy(B->fork);
   if (B->capture) cudaStreamDestroy(B->capture);
@@ -270,13 +278,61 @@ void batch_tune(Batch& B, cudaStream_t st) {
 
 // One outer iteration of group g on its stream: inner V-cycle on A d = r,
 // x += d, r = b - A x (FP64), per-problem norms (and the FP32 copy of r).
+// Flexible CG (HHG_SOLVE_FPCG): q = A p, per-problem p.q, x and r updated
+// (alpha per problem, frozen problems untouched), FP32 V-cycle on r, z
+// widened with per-problem r.z and q.z, p = z + beta p; the per-problem
+// ||r||^2 go to the host.  r lives in the level's r workspace, z in w.
+static void group_cg_iteration(const BatchGroup& g, int nu1, int nu2) {
+  const Mesh& m = *g.m;
+  const int L = g.level;
+  const LevelData& ld = m.levels[L];
+  const int nb = (int)g.probs.size();
+  double* x = (double*)ld.x[0];
+  double* r = (double*)ld.r[0];
+  double* z = (double*)ld.w[0];
+  float* r32 = (float*)ld.b[1];
+  float* z32 = (float*)ld.x[1];
+  apply_op(m, L, 0, g.p, g.q, g.st);
+  batch_cg_dot(m, L, g.p, g.q, g.sc, g.st);
+  batch_cg_step(m, L, g.sc, g.p, g.q, x, r, r32, g.sc + 2 * nb, g.st);
+  zero_vec(m, L, 1, z32, g.st);
+  vcycle_run(m, L, 1, z32, r32, nu1, nu2, 0, g.st);
+  batch_cg_widen(m, L, z32, z, r, g.q, g.sc + nb, g.sc + 3 * nb, g.st);
+  batch_cg_dir(m, L, g.sc, false, z, g.p, g.st);
+  check_cuda(cudaMemcpyAsync(g.norms, g.sc + 2 * nb, nb * sizeof(double), cudaMemcpyDeviceToDevice, g.st), "norms");
+}
+
+// Start (or restart) of the flexible CG from the true residual r = b - A x.
+static void group_cg_start(const BatchGroup& g, int nu1, int nu2, double tol, bool first) {
+  const Mesh& m = *g.m;
+  const int L = g.level;
+  const LevelData& ld = m.levels[L];
+  double* x = (double*)ld.x[0];
+  double* r = (double*)ld.r[0];
+  double* z = (double*)ld.w[0];
+  float* r32 = (float*)ld.b[1];
+  float* z32 = (float*)ld.x[1];
+  const int nb = (int)g.probs.size();
+  ghost_fill(m, L, 0, x, g.st);
+  residual_op(m, L, 0, x, ld.b[0], r, nullptr, g.st);
+  block_norms2(m, L, r, r32, g.norms, g.st);
+  batch_cg_init(m, g.norms, tol, first, g.sc, g.st);
+  check_cuda(cudaMemsetAsync(g.q, 0, ld.lv.len * sizeof(double), g.st), "q = 0");
+  zero_vec(m, L, 1, z32, g.st);
+  vcycle_run(m, L, 1, z32, r32, nu1, nu2, 0, g.st);
+  batch_cg_widen(m, L, z32, z, r, g.q, g.sc + nb, g.sc + 3 * nb, g.st);
+  batch_cg_dir(m, L, g.sc, true, z, g.p, g.st);
+}
+
 static void group_iteration(const BatchGroup& g, int mode, int nu1, int nu2) {
   const Mesh& m = *g.m;
   const int L = g.level;
   const LevelData& ld = m.levels[L];
   double* x = (double*)ld.x[0];
   double* b = (double*)ld.b[0];
-  if (mode == HHG_SOLVE_IR) {
+  if (mode == HHG_SOLVE_FPCG) {
+    group_cg_iteration(g, nu1, nu2);
+  } else if (mode == HHG_SOLVE_IR) {
     zero_vec(m, L, 1, ld.x[1], g.st);
     vcycle_run(m, L, 1, ld.x[1], ld.b[1], nu1, nu2, 0, g.st);
     update_f64_from_f32(m, L, x, (const float*)ld.x[1], g.st);
@@ -289,13 +345,18 @@ static void group_iteration(const BatchGroup& g, int mode, int nu1, int nu2) {
   }
 }
 
-static void fork_join(Batch& B, cudaStream_t st, int mode, int nu1, int nu2, bool iteration) {
+// iteration: one outer iteration of every group; else the initial (or, for
+// the flexible CG, a restarting) true residual and its norms.
+static void fork_join(Batch& B, cudaStream_t st, int mode, int nu1, int nu2, bool iteration, double tol = 0.0,
+                      bool first = true) {
   check_cuda(cudaEventRecord(B.fork, st), "fork");
   for (size_t gi = 0; gi < B.groups.size(); ++gi) {
     BatchGroup& g = B.groups[gi];
     check_cuda(cudaStreamWaitEvent(g.st, B.fork, 0), "wait fork");
     if (iteration) {
       group_iteration(g, mode, nu1, nu2);
+    } else if (mode == HHG_SOLVE_FPCG) {
+      group_cg_start(g, nu1, nu2, tol, first);
     } else {   // initial residual and norms
       const LevelData& ld = g.m->levels[g.level];
       ghost_fill(*g.m, g.level, 0, ld.x[0], g.st);
@@ -330,7 +391,15 @@ void batch_solve(Batch& B, double* const* x, const double* const* b, const hhg_s
       canonical_op(*g.m, g.level, 0, g.canon, which == 0 ? ld.x[0] : ld.b[0], false, st);
     }
   }
-  fork_join(B, st, o.mode, o.nu1, o.nu2, false);
+  if (o.mode == HHG_SOLVE_FPCG)
+    for (auto& g : B.groups)
+      if (!g.p) {
+        const size_t bytes = (size_t)g.m->levels[g.level].lv.len * sizeof(double);
+        check_cuda(cudaMalloc(&g.p, bytes), "cg alloc");
+        check_cuda(cudaMalloc(&g.q, bytes), "cg alloc");
+        check_cuda(cudaMalloc(&g.sc, 6 * g.probs.size() * sizeof(double)), "cg alloc");
+      }
+  fork_join(B, st, o.mode, o.nu1, o.nu2, false, o.tol, true);
   check_cuda(cudaStreamSynchronize(st), "sync");
   std::vector<double> r0(n), r(n);
   std::vector<int> done_at(n, -1);
@@ -360,7 +429,18 @@ void batch_solve(Batch& B, double* const* x, const double* const* b, const hhg_s
     cudaGraphExecDestroy(B.graph);
     B.graph = nullptr;
   }
-  while (!all_done() && status == HHG_OK) {
+  for (;;) {
+    if (all_done() || status != HHG_OK) {
+      if (o.mode != HHG_SOLVE_FPCG || status != HHG_OK) break;
+      // the flexible CG's updated residuals met the tolerance: confirm with
+      // the true residuals (which also restart the iteration should one miss)
+      fork_join(B, st, o.mode, o.nu1, o.nu2, false, o.tol, false);
+      check_cuda(cudaStreamSynchronize(st), "sync");
+      collect(r);
+      if (all_done()) break;
+      std::fill(done_at.begin(), done_at.end(), -1);
+      if (all_done()) break;
+    }
     if (it >= o.max_iter) {
       status = HHG_ERR_NOT_CONVERGED;
       break;

@@ -547,7 +547,7 @@ hhg_status hhg_batch_solve(hhg_batch batch, double* const* x, const double* cons
     hhg_solve_opts o{HHG_SOLVE_IR, 3, 3, 100, 1e-10, HHG_SMOOTH_GS, 20};
     if (opts) o = *opts;
     if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 0 || !(o.tol >= 0.0)) throw ArgError("bad solve options");
-    if (o.mode != HHG_SOLVE_MG && o.mode != HHG_SOLVE_IR) throw ArgError("bad solve mode");
+    if (o.mode != HHG_SOLVE_MG && o.mode != HHG_SOLVE_IR && o.mode != HHG_SOLVE_FPCG) throw ArgError("bad solve mode");
     hhg::batch_solve(*batch->b, x, b, o, reps, S(stream));
     return HHG_OK;
   });

@@ -308,6 +308,15 @@ void learned_grad(Mesh& m, int B, const float* X_dev, const float* S_dev, const 
 void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr, uint64_t seed,
                    float* loss_hist, cudaStream_t st);
 void krylov_free(Mesh& m);
+// batched flexible CG passes over the problems (Blocks) of a merged mesh;
+// sc = 6 arrays of nb per-problem scalars (p.q, r.z, ||r||^2, q.z, ||r0||^2, threshold)
+void batch_cg_init(const Mesh& m, const double* norms, double tol, bool first, double* sc, cudaStream_t st);
+void batch_cg_dot(const Mesh& m, int L, const double* u, const double* v, double* out_nb, cudaStream_t st);
+void batch_cg_step(const Mesh& m, int L, const double* sc, const double* p, const double* q, double* x, double* r,
+                   float* r32, double* rr_out, cudaStream_t st);
+void batch_cg_widen(const Mesh& m, int L, const float* z32, double* z, const double* r, const double* q,
+                    double* rz_out, double* qz_out, cudaStream_t st);
+void batch_cg_dir(const Mesh& m, int L, const double* sc, bool restart, const double* z, double* p, cudaStream_t st);
 void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts& o, hhg_solve_report* rep,
                bool mixed, cudaStream_t st);
 void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts& o, int smoother,

@@ -161,6 +161,152 @@ __global__ void k_sum_ordered(const double* __restrict__ partials, int n, double
   }
 }
 
+// ------------------------------------------------------------- batched CG
+// The same passes per problem of a merged batch mesh: problem (Block) b owns
+// the vertex range [v0, v1), the edges [e0, e1) and the faces [f0, f1); grid
+// (chunks, blocks), per-problem scalars in device arrays indexed by the
+// block.  A problem whose last ||r||^2 is at or below its threshold is
+// frozen (alpha = beta = 0), so one captured iteration serves every problem
+// until the last one converges.
+template <typename F>
+__device__ __forceinline__ void for_block_slots(const MeshTables& M, const LevelView& L, const Block& B, F f) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = B.v0 + tid; v < B.v1; v += nth) f(L.v_off + v, !M.verts[v].dirichlet);
+  const int64_t ne = (int64_t)(B.e1 - B.e0) * (L.N + 1);
+  for (int64_t q = tid; q < ne; q += nth) {
+    const int64_t e = B.e0 + q / (L.N + 1), t = q % (L.N + 1);
+    f(L.e_off + e * L.ES + t, t >= 1 && t <= L.N - 1 && !M.edges[e].dirichlet);
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t nrow = (int64_t)(B.f1 - B.f0) * (L.N + 1);
+  for (int64_t w = tid >> 5; w < nrow; w += nth >> 5) {
+    const int64_t fc = B.f0 + w / (L.N + 1);
+    const int j = (int)(w % (L.N + 1));
+    const int64_t base = L.f_off + fc * L.FS + (int64_t)j * L.S;
+    for (int i = lane; i <= L.N - j; i += 32) f(base + i, i >= 1 && j >= 1 && i + j <= L.N - 1);
+  }
+}
+
+// partial sums of one chunk of one problem: out[b * nchunks + chunk] (and
+// out2 likewise)
+__device__ __forceinline__ void chunk_sums(double a, double c, double* out, double* out2) {
+  __shared__ double ra[kVecThreads / 32], rc[kVecThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ra[threadIdx.x >> 5] = a;
+    rc[threadIdx.x >> 5] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sc = 0.0;
+    for (int w = 0; w < kVecThreads / 32; ++w) {
+      sa += ra[w];
+      sc += rc[w];
+    }
+    const int64_t k = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    out[k] = sa;
+    if (out2) out2[k] = sc;
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_bcg_dot(MeshTables M, LevelView L, const Block* __restrict__ blocks,
+                                                        const double* __restrict__ u, const double* __restrict__ v,
+                                                        double* partials) {
+  const Block B = blocks[blockIdx.y];
+  double acc = 0.0;
+  for_block_slots(M, L, B, [&](int64_t s, bool own) {
+    if (own) acc = fma(u[s], v[s], acc);
+  });
+  chunk_sums(acc, 0.0, partials, nullptr);
+}
+
+// alpha_b = rz_b / pq_b unless frozen; x += alpha p, r -= alpha q, r32 = r;
+// partial sums of ||r||^2
+__global__ void __launch_bounds__(kVecThreads) k_bcg_step(MeshTables M, LevelView L, const Block* __restrict__ blocks,
+                                                         const double* __restrict__ sc, int nb,
+                                                         const double* __restrict__ p, const double* __restrict__ q,
+                                                         double* x, double* r, float* r32, double* partials) {
+  const int b = blockIdx.y;
+  const Block B = blocks[b];
+  const double rr = sc[2 * nb + b], thr = sc[5 * nb + b], pq = sc[0 * nb + b], rz = sc[1 * nb + b];
+  const bool frozen = rr <= thr || !(pq > 0.0);
+  const double alpha = frozen ? 0.0 : rz / pq;
+  double acc = 0.0;
+  for_block_slots(M, L, B, [&](int64_t s, bool own) {
+    if (!frozen) x[s] += alpha * p[s];
+    if (own) {
+      double v = r[s];
+      if (!frozen) {
+        v -= alpha * q[s];
+        r[s] = v;
+      }
+      r32[s] = d2f_rn(v);
+      acc = fma(v, v, acc);
+    }
+  });
+  chunk_sums(acc, 0.0, partials, nullptr);
+}
+
+// z = z32 widened; partial sums of r.z and q.z
+__global__ void __launch_bounds__(kVecThreads) k_bcg_widen(MeshTables M, LevelView L, const Block* __restrict__ blocks,
+                                                          const float* __restrict__ z32, double* z,
+                                                          const double* __restrict__ r, const double* __restrict__ q,
+                                                          double* partials, double* partials2) {
+  const Block B = blocks[blockIdx.y];
+  double rz = 0.0, qz = 0.0;
+  for_block_slots(M, L, B, [&](int64_t s, bool own) {
+    const double v = f2d_bits(z32[s]);
+    z[s] = v;
+    if (own) {
+      rz = fma(r[s], v, rz);
+      qz = fma(q[s], v, qz);
+    }
+  });
+  chunk_sums(rz, qz, partials, partials2);
+}
+
+// p = z + beta_b p, beta_b = -(q.z)_b / (p.q)_b (0 when frozen or restart)
+__global__ void __launch_bounds__(kVecThreads) k_bcg_dir(MeshTables M, LevelView L, const Block* __restrict__ blocks,
+                                                        const double* __restrict__ sc, int nb, int restart,
+                                                        const double* __restrict__ z, double* p) {
+  const int b = blockIdx.y;
+  const Block B = blocks[b];
+  const double rr = sc[2 * nb + b], thr = sc[5 * nb + b], pq = sc[0 * nb + b], qz = sc[3 * nb + b];
+  const bool frozen = rr <= thr || !(pq > 0.0);
+  const double beta = (restart || frozen) ? 0.0 : -qz / pq;
+  for_block_slots(M, L, B, [&](int64_t s, bool) { p[s] = restart ? z[s] : z[s] + beta * p[s]; });
+}
+
+// after a true residual: ||r||^2 = norms; on the first one also ||r0||^2 and
+// the freezing threshold tol^2 ||r0||^2
+__global__ void k_bcg_init(int nb, const double* __restrict__ norms, double tol2, int first, double* sc) {
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    sc[2 * nb + b] = norms[b];
+    if (first) {
+      sc[4 * nb + b] = norms[b];
+      sc[5 * nb + b] = tol2 * norms[b];
+    }
+  }
+}
+
+// out[b] = sum of partials[b * per .. b * per + per)
+__global__ void k_bcg_sums(const double* __restrict__ partials, int per, double* out) {
+  __shared__ double red[kVecThreads / 32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < per; i += blockDim.x) acc += partials[(int64_t)blockIdx.x * per + i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+    out[blockIdx.x] = sum;
+  }
+}
+
 }  // namespace
 
 struct KrylovSpace {
@@ -453,6 +599,56 @@ void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts&
     rep->smoother_used = HHG_SMOOTH_GS;
   }
   if (status != HHG_OK) throw SolveStatus(status);
+}
+
+// ------------------------------------------------------------- batched CG, host side
+// Scalars per problem in sc: [0] p.q, [1] r.z, [2] ||r||^2, [3] q.z, [4] ||r0||^2,
+// [5] freezing threshold tol^2 ||r0||^2 (each nb doubles).  Partial sums use
+// the mesh's partial buffer (2 * chunks * nb <= kMaxPartials).
+static int bcg_chunks(int nb) {
+  int per = kMaxPartials / (2 * nb);
+  if (per > 64) per = 64;
+  if (per < 1) throw std::runtime_error("too many problems for the partial-sum buffer");
+  return per;
+}
+
+void batch_cg_init(const Mesh& m, const double* norms, double tol, bool first, double* sc, cudaStream_t st) {
+  const int nb = (int)m.h_blocks.size();
+  k_bcg_init<<<1, kVecThreads, 0, st>>>(nb, norms, tol * tol, first ? 1 : 0, sc);
+  check_cuda(cudaGetLastError(), "batched cg init");
+}
+
+void batch_cg_dot(const Mesh& m, int L, const double* u, const double* v, double* out_nb, cudaStream_t st) {
+  const int nb = (int)m.h_blocks.size(), per = bcg_chunks(nb);
+  k_bcg_dot<<<dim3(per, nb), kVecThreads, 0, st>>>(m.tab, m.levels[L].lv, m.blocks, u, v, m.partials);
+  k_bcg_sums<<<nb, kVecThreads, 0, st>>>(m.partials, per, out_nb);
+  check_cuda(cudaGetLastError(), "batched dot");
+}
+
+void batch_cg_step(const Mesh& m, int L, const double* sc, const double* p, const double* q, double* x, double* r,
+                   float* r32, double* rr_out, cudaStream_t st) {
+  const int nb = (int)m.h_blocks.size(), per = bcg_chunks(nb);
+  k_bcg_step<<<dim3(per, nb), kVecThreads, 0, st>>>(m.tab, m.levels[L].lv, m.blocks, sc, nb, p, q, x, r, r32,
+                                                    m.partials);
+  k_bcg_sums<<<nb, kVecThreads, 0, st>>>(m.partials, per, rr_out);
+  check_cuda(cudaGetLastError(), "batched cg step");
+}
+
+void batch_cg_widen(const Mesh& m, int L, const float* z32, double* z, const double* r, const double* q,
+                    double* rz_out, double* qz_out, cudaStream_t st) {
+  const int nb = (int)m.h_blocks.size(), per = bcg_chunks(nb);
+  k_bcg_widen<<<dim3(per, nb), kVecThreads, 0, st>>>(m.tab, m.levels[L].lv, m.blocks, z32, z, r, q, m.partials,
+                                                     m.partials + (int64_t)per * nb);
+  k_bcg_sums<<<nb, kVecThreads, 0, st>>>(m.partials, per, rz_out);
+  k_bcg_sums<<<nb, kVecThreads, 0, st>>>(m.partials + (int64_t)per * nb, per, qz_out);
+  check_cuda(cudaGetLastError(), "batched widen");
+}
+
+void batch_cg_dir(const Mesh& m, int L, const double* sc, bool restart, const double* z, double* p,
+                  cudaStream_t st) {
+  const int nb = (int)m.h_blocks.size(), per = bcg_chunks(nb);
+  k_bcg_dir<<<dim3(per, nb), kVecThreads, 0, st>>>(m.tab, m.levels[L].lv, m.blocks, sc, nb, restart ? 1 : 0, z, p);
+  check_cuda(cudaGetLastError(), "batched direction");
 }
 
 }  // namespace hhg

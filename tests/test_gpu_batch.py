@@ -29,7 +29,7 @@ def oracle_solution(xy, tri, L, b, tol=1e-12):
     return H, x
 
 
-@pytest.mark.parametrize("mode", ["ir", "mg"])
+@pytest.mark.parametrize("mode", ["ir", "mg", "fpcg"])
 def test_batch_solve_matches_oracle(mode):
     torch = pytest.importorskip("torch")
     from paper_1805_10167_gb300 import hhg
@@ -42,7 +42,7 @@ def test_batch_solve_matches_oracle(mode):
         bh.append(b)
         bs.append(torch.tensor(b, dtype=torch.float64, device="cuda"))
         xs.append(torch.zeros(n, dtype=torch.float64, device="cuda"))
-    st, reps = B.solve(xs, bs, mode=hhg.SOLVE_IR if mode == "ir" else hhg.SOLVE_MG)
+    st, reps = B.solve(xs, bs, mode={"ir": hhg.SOLVE_IR, "mg": hhg.SOLVE_MG, "fpcg": hhg.SOLVE_FPCG}[mode])
     for p, (xy, tri, L) in enumerate(probs):
         H, want = oracle_solution(xy, tri, L, bh[p])
         got = xs[p].cpu().numpy()
@@ -108,3 +108,40 @@ def test_autotuned_split_gives_identical_results():
     want = mg.vcycle(P.H, 5, x0.copy(), b, 3, 3)
     assert rel_err(P.from_dev(5, xb), want) <= FP64_TOL
     P.close()
+
+
+def test_batch_flexible_cg_matches_single_problem_solves_and_needs_fewer_steps():
+    """Batched flexible CG: every problem reaches the FP64 tolerance in the
+    step count of the single-mesh flexible CG (within one step: FP32 rounding
+    differs between the merged and the single mesh), and never more steps
+    than FP32-in-FP64 refinement needs on the same problem."""
+    torch = pytest.importorskip("torch")
+    from paper_1805_10167_gb300 import hhg
+    probs = problems(5, 2000)
+    B = hhg.Batch([(xy, tri) for xy, tri, L in probs], [L for xy, tri, L in probs])
+    bs, xs = [], []
+    for p in range(len(probs)):
+        n = B.info(p).n_nodes
+        bs.append(torch.tensor(inputs.uniform_pm1(n, 2000 + p), dtype=torch.float64, device="cuda"))
+        xs.append(torch.zeros(n, dtype=torch.float64, device="cuda"))
+    st, reps = B.solve(xs, bs, mode=hhg.SOLVE_FPCG)
+    for _ in range(2):   # replays of the captured iteration give the same answer
+        xs2 = [torch.zeros_like(x) for x in xs]
+        st, reps2 = B.solve(xs2, bs, mode=hhg.SOLVE_FPCG)
+        for a, c in zip(xs, xs2):
+            assert torch.equal(a, c)
+    for p, (xy, tri, L) in enumerate(probs):
+        g = hhg.Mesh(xy, tri, L)
+        I = g.info(L)
+        bi = torch.zeros(I.vec_len, dtype=torch.float64, device="cuda")
+        g.from_canonical(L, bs[p], bi)
+        its = {}
+        for mode in (hhg.SOLVE_FPCG, hhg.SOLVE_IR):
+            xi = torch.zeros_like(bi)
+            _, rep = g.solve(L, xi, bi, mode=mode)
+            its[mode] = rep["iterations"]
+        assert abs(reps[p]["iterations"] - its[hhg.SOLVE_FPCG]) <= 1, (p, reps[p]["iterations"], its)
+        assert reps[p]["iterations"] <= its[hhg.SOLVE_IR], (p, reps[p]["iterations"], its)
+        assert reps[p]["r_final"] <= 1e-10 * reps[p]["r0"]
+        g.close()
+    B.close()
