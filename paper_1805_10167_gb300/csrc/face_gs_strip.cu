@@ -46,6 +46,7 @@ struct StripArgs {
   const T* ku;        // coefficients of the upward / downward micro-triangles
   const T* kd;
   int S, N, ic, ws, us, ue, j0, j1;   // offsets inside a face fit in 32 bits
+  int own;                            // bit m: column ic + m is one this strip stores
   V dinv, w0, w1, w2;                 // k = 1 update: b / A_pp and the scaled weights
   T c0, c1, c2;                       // cotangents (variable k)
 };
@@ -56,7 +57,9 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 
 // Colour phase on row t + DR at the lane's column M; U = t mod 6 places the
 // rows in the six-slot register ring (row r lives in slot r mod 6).
-template <typename T, bool DF, bool VARK, int DR, int M, int U>
+// FAST: the caller knows that the row is in range and every column of the
+// window interior (no checks).
+template <typename T, bool DF, bool VARK, int DR, int M, int U, bool FAST = false>
 __device__ __forceinline__ void strip_phase(typename Arith<T, DF>::V (&X)[6][3], typename Arith<T, DF>::V bv,
                                             int t, int rlo, int rhi, const StripArgs<T, DF>& a) {
   using A = Arith<T, DF>;
@@ -65,7 +68,7 @@ __device__ __forceinline__ void strip_phase(typename Arith<T, DF>::V (&X)[6][3],
   const int r = t + DR;
   // warp-uniform: the row is in this phase's range, is a face-interior row,
   // and holds at least one interior column of the window
-  if (r < rlo || r > rhi || r < 1 || r > a.N - 2 || a.ws + 1 > a.N - 1 - r) return;
+  if (!FAST && (r < rlo || r > rhi || r < 1 || r > a.N - 2 || a.ws + 1 > a.N - 1 - r)) return;
   V xe, xse, xw, xnw;
   if (M < 2) {
     xe = X[sc][(M + 1) % 3];
@@ -83,7 +86,7 @@ __device__ __forceinline__ void strip_phase(typename Arith<T, DF>::V (&X)[6][3],
   }
   const V xn = X[sn][M], xs = X[ss][M];
   const int i = a.ic + M;
-  const bool act = i >= 1 && i + r <= a.N - 1;
+  const bool act = FAST || (i >= 1 && i + r <= a.N - 1);
   if (!VARK) {
     V acc = A::mul(bv, a.dinv);
     acc = A::fma(a.w2, A::add(xe, xw), acc);
@@ -148,7 +151,7 @@ __device__ __forceinline__ void load_b_step(typename Arith<T, DF>::V (&Bv)[3], i
   Bv[2] = load_b(t - 2, C::mC, a);
 }
 
-template <typename T, bool DF, bool VARK, bool FWD, int U>
+template <typename T, bool DF, bool VARK, bool FWD, int U, bool FAST = false>
 __device__ __forceinline__ void strip_step(typename Arith<T, DF>::V (&X)[6][3], typename Arith<T, DF>::V (&Bq)[2][3],
                                            int t, int rmax, const StripArgs<T, DF>& a) {
   using A = Arith<T, DF>;
@@ -166,12 +169,18 @@ __device__ __forceinline__ void strip_step(typename Arith<T, DF>::V (&X)[6][3], 
       prefetch_l2(a.bg + (rp * a.S + a.ic));
     }
   }
-  strip_phase<T, DF, VARK, 0, C::mA, U>(X, Bv[0], t, a.j0 - 2, a.j1 + 1, a);
-  strip_phase<T, DF, VARK, -1, C::mB, U>(X, Bv[1], t, a.j0 - 1, a.j1, a);
-  strip_phase<T, DF, VARK, -2, C::mC, U>(X, Bv[2], t, a.j0, a.j1 - 1, a);
+  strip_phase<T, DF, VARK, 0, C::mA, U, FAST>(X, Bv[0], t, a.j0 - 2, a.j1 + 1, a);
+  strip_phase<T, DF, VARK, -1, C::mB, U, FAST>(X, Bv[1], t, a.j0 - 1, a.j1, a);
+  strip_phase<T, DF, VARK, -2, C::mC, U, FAST>(X, Bv[2], t, a.j0, a.j1 - 1, a);
   // row t - 2 is final
   const int r = t - 2;
-  if (r >= a.j0 && r < a.j1) {
+  if (FAST) {   // interior window: the stored columns are the strip's own, every one interior
+    constexpr int sl = (U + 4) % 6;
+    const int off = r * a.S;
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+      if (a.own & (1 << m)) a.xo[off + a.ic + m] = A::out(X[sl][m]);
+  } else if (r >= a.j0 && r < a.j1) {
     constexpr int sl = (U + 4) % 6;
     const int hi = min(a.ue - 1, a.N - r);   // last stored column of the row
     const int off = r * a.S;
@@ -203,7 +212,32 @@ __device__ __forceinline__ void strip_run(int t0, int tend, int rmax, const Stri
   load_row<T, DF>(X[1], t0 + 1, rmax, a);
   load_b_step<T, DF, FWD, 0>(Bq[0], t0, a);
   load_b_step<T, DF, FWD, 1>(Bq[1], t0 + 1, a);
-  for (int t = t0; t <= tend; t += 6) {
+  int t = t0;
+  if constexpr (sizeof(T) == 4 && !DF) {
+    // Steps t in [max(j0 + 2, 3), j1 + 1] with the whole window interior on
+    // rows t - 2 .. t (strips s >= 1, ws + 95 <= N - 1 - t) need no checks:
+    // run them as whole groups of six in the unchecked form.
+    const int flo = max(a.j0 + 2, 3), fhi = min(a.j1 + 1, a.N - 1 - (a.ws + 95));
+    if (a.ws >= 1 && flo <= fhi) {
+      for (; t < flo; t += 6) {   // checked groups up to the first group that starts at or after flo
+        strip_step<T, DF, VARK, FWD, 0>(X, Bq, t, rmax, a);
+        strip_step<T, DF, VARK, FWD, 1>(X, Bq, t + 1, rmax, a);
+        strip_step<T, DF, VARK, FWD, 2>(X, Bq, t + 2, rmax, a);
+        strip_step<T, DF, VARK, FWD, 3>(X, Bq, t + 3, rmax, a);
+        strip_step<T, DF, VARK, FWD, 4>(X, Bq, t + 4, rmax, a);
+        strip_step<T, DF, VARK, FWD, 5>(X, Bq, t + 5, rmax, a);
+      }
+      for (; t + 5 <= fhi; t += 6) {
+        strip_step<T, DF, VARK, FWD, 0, true>(X, Bq, t, rmax, a);
+        strip_step<T, DF, VARK, FWD, 1, true>(X, Bq, t + 1, rmax, a);
+        strip_step<T, DF, VARK, FWD, 2, true>(X, Bq, t + 2, rmax, a);
+        strip_step<T, DF, VARK, FWD, 3, true>(X, Bq, t + 3, rmax, a);
+        strip_step<T, DF, VARK, FWD, 4, true>(X, Bq, t + 4, rmax, a);
+        strip_step<T, DF, VARK, FWD, 5, true>(X, Bq, t + 5, rmax, a);
+      }
+    }
+  }
+  for (; t <= tend; t += 6) {
     strip_step<T, DF, VARK, FWD, 0>(X, Bq, t, rmax, a);
     if (t + 1 > tend) break;
     strip_step<T, DF, VARK, FWD, 1>(X, Bq, t + 1, rmax, a);
@@ -234,6 +268,8 @@ __device__ __forceinline__ void strip_task(const MeshTables& M, const LevelView&
   a.ue = a.ws + kStripUseful + 3;
   a.j0 = tk.z;
   a.j1 = tk.w;
+  a.own = 0;
+  for (int m = 0; m < 3; ++m) a.own |= (a.ic + m >= a.us && a.ic + m < a.ue) ? 1 << m : 0;
   const int64_t fb = L.f_off + (int64_t)f * L.FS;
   a.xg = xin + fb;
   a.xo = xout + fb;
