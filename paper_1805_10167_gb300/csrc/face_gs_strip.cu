@@ -213,7 +213,7 @@ __device__ __forceinline__ void strip_run(int t0, int tend, int rmax, const Stri
   load_b_step<T, DF, FWD, 0>(Bq[0], t0, a);
   load_b_step<T, DF, FWD, 1>(Bq[1], t0 + 1, a);
   int t = t0;
-  if constexpr (sizeof(T) == 4 && !DF) {
+  if constexpr (sizeof(T) == 4 && !DF && !VARK) {   // (with variable k the doubled code overflows the instruction cache)
     // Steps t in [max(j0 + 2, 3), j1 + 1] with the whole window interior on
     // rows t - 2 .. t (strips s >= 1, ws + 95 <= N - 1 - t) need no checks:
     // run them as whole groups of six in the unchecked form.

@@ -39,7 +39,7 @@ constexpr int kSmallRowsN = 64;    // double-float rows from this level size up 
 constexpr int kStripCols = 96;
 constexpr unsigned kAll = 0xffffffffu;
 
-enum RowMode { R_APPLY = 0, R_RESID = 1, R_JAC = 3, R_SRES = 4 };   // same codes as the row kernels
+enum RowMode { R_APPLY = 0, R_RESID = 1, R_JAC = 3, R_SRES = 4, R_ADOT = 5 };   // same codes as the row kernels
 
 template <typename T>
 struct RowArgs {
@@ -57,12 +57,14 @@ template <typename T, bool DF>
 struct SqAcc {
   double s = 0.0;
   __device__ __forceinline__ void add(T v) { s = fma((double)v, (double)v, s); }
+  __device__ __forceinline__ void add_prod(T u, T v) { s = fma((double)u, (double)v, s); }
   __device__ __forceinline__ double value() const { return s; }
 };
 template <>
 struct SqAcc<double, true> {
   dfl s{0.f, 0.f};
   __device__ __forceinline__ void add(dfl v) { s = df_add(s, df_mul(v, v)); }
+  __device__ __forceinline__ void add_prod(dfl u, dfl v) { s = df_add(s, df_mul(u, v)); }
   __device__ __forceinline__ double value() const { return to_double(s); }
 };
 
@@ -147,12 +149,16 @@ __device__ __forceinline__ void rows_step(typename Arith<T, DF>::V (&R)[4][3], t
     if (!VARK) {
       // constant stencil: r = b - dg x_c + c2 (x_e + x_w) + c1 (x_n + x_s)
       // + c0 (x_se + x_nw), seven operations (Ax likewise)
-      V v = MODE == R_APPLY ? A::mul(kc.dg, xc) : A::fma(kc.ndg, xc, A::in(bg[p]));
-      v = A::fma(MODE == R_APPLY ? kc.nc2 : kc.c2, A::add(xe, xw), v);
-      v = A::fma(MODE == R_APPLY ? kc.nc1 : kc.c1, A::add(xn, xs), v);
-      v = A::fma(MODE == R_APPLY ? kc.nc0 : kc.c0, A::add(xse, xnw), v);
+      constexpr bool ax = MODE == R_APPLY || MODE == R_ADOT;
+      V v = ax ? A::mul(kc.dg, xc) : A::fma(kc.ndg, xc, A::in(bg[p]));
+      v = A::fma(ax ? kc.nc2 : kc.c2, A::add(xe, xw), v);
+      v = A::fma(ax ? kc.nc1 : kc.c1, A::add(xn, xs), v);
+      v = A::fma(ax ? kc.nc0 : kc.c0, A::add(xse, xnw), v);
       if (MODE == R_APPLY) {
         out[fb + p] = out_cast<T, DF, TO>(v);
+      } else if (MODE == R_ADOT) {
+        out[fb + p] = out_cast<T, DF, TO>(v);
+        acc.add_prod(xc, v);
       } else if (MODE == R_RESID) {
         out[fb + p] = out_cast<T, DF, TO>(v);
         acc.add(v);
@@ -181,6 +187,9 @@ __device__ __forceinline__ void rows_step(typename Arith<T, DF>::V (&R)[4][3], t
       const V ax = A::sub(A::mul(diag, xc), off);
       if (MODE == R_APPLY) {
         out[fb + p] = out_cast<T, DF, TO>(ax);
+      } else if (MODE == R_ADOT) {
+        out[fb + p] = out_cast<T, DF, TO>(ax);
+        acc.add_prod(xc, ax);
       } else if (MODE == R_RESID) {
         const V r = A::sub(A::in(bg[p]), ax);
         out[fb + p] = out_cast<T, DF, TO>(r);
@@ -221,7 +230,7 @@ __global__ void __launch_bounds__(kRowWarps * 32)
     a.dg = UPD ? d + fb : nullptr;
     a.ku = VARK ? k + (int64_t)f * L.FS : nullptr;
     a.kd = VARK ? k + (int64_t)(M.nf + f) * L.FS : nullptr;
-    const T* bg = (MODE == R_APPLY) ? nullptr : b + fb;
+    const T* bg = (MODE == R_APPLY || MODE == R_ADOT) ? nullptr : b + fb;
     const FaceRec& F = M.faces[f];
     const T c0 = (T)F.cot[0], c1 = (T)F.cot[1], c2 = (T)F.cot[2];
     const T dg = T(2) * (c0 + c1 + c2), dgi = T(1) / dg;
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(kRowWarps * 32)
       rows_step<T, DF, TO, VARK, MODE, UPD, 3>(R, E, t + 3, a, out, fb, bg, kc, c0, c1, c2, dgi, omega, acc);
     }
   }
-  if (MODE == R_RESID) {
+  if (MODE == R_RESID || MODE == R_ADOT) {
     // fixed-order block sum (warp butterflies, then warp 0 over the warps)
     __shared__ double red[kRowWarps];
     double v = acc.value();
@@ -347,6 +356,7 @@ int face_rows(const Mesh& m, int level, int prec_in, int prec_out, int mode, con
   auto* o = (double*)out;
   switch (mode) {
     case R_APPLY: launch_rows_f64<double, R_APPLY, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st); return 0;
+    case R_ADOT: return launch_rows_f64<double, R_ADOT, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st);
     case R_RESID:
       if (x_upd) return launch_rows_f64<double, R_RESID, true>(m, level, xx, (double*)x_upd, d, o, bb, partials, omega, st);
       return launch_rows_f64<double, R_RESID, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st);

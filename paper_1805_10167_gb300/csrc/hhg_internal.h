@@ -224,6 +224,8 @@ constexpr int kMaxPartials = 4096;
 // All launchers are asynchronous on `st`; `prec` selects double (0) / float (1).
 void ghost_fill(const Mesh& m, int level, int prec, void* v, cudaStream_t st);
 void apply_op(const Mesh& m, int level, int prec, const void* x, void* y, cudaStream_t st);
+// y = A x (FP64) and x . y over the free unknowns into *dot_dev
+void apply_dot_op(const Mesh& m, int level, const double* x, double* y, double* dot_dev, cudaStream_t st);
 // r = b - A x; optional sum of squares over free DoFs into *norm2_dev (double)
 void residual_op(const Mesh& m, int level, int prec, const void* x, const void* b, void* r,
                  double* norm2_dev, cudaStream_t st);

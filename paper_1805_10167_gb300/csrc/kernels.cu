@@ -15,7 +15,8 @@
 
 namespace hhg {
 
-enum Mode { APPLY = 0, RESID = 1, GS = 2, JAC = 3, SRES = 4 };   // SRES: (b - A x) / A_pp
+// SRES: (b - A x) / A_pp; ADOT: A x and the partial sums of x . (A x)
+enum Mode { APPLY = 0, RESID = 1, GS = 2, JAC = 3, SRES = 4, ADOT = 5 };
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -117,7 +118,7 @@ __global__ void k_vertex(MeshTables M, LevelView L, const T* x, TO* out, const T
     }
     if (V.dirichlet) {
       if (lane == 0) {
-        if (MODE == APPLY || MODE == RESID || MODE == SRES) out[s] = TO(0);
+        if (MODE == APPLY || MODE == RESID || MODE == SRES || MODE == ADOT) out[s] = TO(0);
         if (MODE == JAC) out[s] = (TO)x[s];
       }
       continue;
@@ -133,6 +134,10 @@ __global__ void k_vertex(MeshTables M, LevelView L, const T* x, TO* out, const T
         out[s] = (TO)((b[s] - (diag * xv + off)) / diag);
       } else if (MODE == APPLY) {
         out[s] = (TO)(diag * xv + off);
+      } else if (MODE == ADOT) {
+        const T y = diag * xv + off;
+        out[s] = (TO)y;
+        acc += (double)xv * (double)y;
       } else if (MODE == RESID) {
         const T r = b[s] - (diag * xv + off);
         out[s] = (TO)r;
@@ -142,7 +147,7 @@ __global__ void k_vertex(MeshTables M, LevelView L, const T* x, TO* out, const T
       }
     }
   }
-  if (MODE == RESID) {
+  if (MODE == RESID || MODE == ADOT) {
     const double sum = block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = sum;
   }
@@ -182,7 +187,7 @@ __global__ void k_edge(MeshTables M, LevelView L, const int* __restrict__ list, 
       xs = MODE == GS ? T(0) : x[s];
     }
     if (E.dirichlet) {
-      if (MODE == APPLY || MODE == RESID || MODE == SRES) out[s] = TO(0);
+      if (MODE == APPLY || MODE == RESID || MODE == SRES || MODE == ADOT) out[s] = TO(0);
       if (MODE == JAC) out[s] = (TO)xs;
       continue;
     }
@@ -196,6 +201,10 @@ __global__ void k_edge(MeshTables M, LevelView L, const int* __restrict__ list, 
       out[s] = (TO)((b[s] - (diag * xs + off)) / diag);
     } else if (MODE == APPLY) {
       out[s] = (TO)(diag * xs + off);
+    } else if (MODE == ADOT) {
+      const T y = diag * xs + off;
+      out[s] = (TO)y;
+      acc += (double)xs * (double)y;
     } else if (MODE == RESID) {
       const T r = b[s] - (diag * xs + off);
       out[s] = (TO)r;
@@ -204,7 +213,7 @@ __global__ void k_edge(MeshTables M, LevelView L, const int* __restrict__ list, 
       out[s] = (TO)(xs + T(omega) * (b[s] - (diag * xs + off)) / diag);
     }
   }
-  if (MODE == RESID) {
+  if (MODE == RESID || MODE == ADOT) {
     const double s = block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
   }
@@ -617,6 +626,12 @@ void apply_op(const Mesh& m, int level, int prec, const void* x, void* y, cudaSt
   else rows_dispatch<float, float, APPLY>(m, level, (const float*)x, (float*)y, nullptr, nullptr, 0.0, st);
 }
 
+// y = A x (FP64) and x . y over the free unknowns into *dot_dev.
+void apply_dot_op(const Mesh& m, int level, const double* x, double* y, double* dot_dev, cudaStream_t st) {
+  const int used = rows_dispatch<double, double, ADOT>(m, level, x, y, nullptr, m.partials, 0.0, st);
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "sum partials", k_sum_partials<<<1, kThreads, 0, st>>>(m.partials, used, dot_dev, 0));
+}
+
 void residual_op(const Mesh& m, int level, int prec, const void* x, const void* b, void* r,
                  double* norm2_dev, cudaStream_t st) {
   int used;
@@ -872,8 +887,9 @@ void assign_op(const Mesh& m, int level, int prec, double a, const void* x1, dou
 void dot_op(const Mesh& m, int level, int prec, const void* x1, const void* x2, double* out_dev,
             cudaStream_t st) {
   const LevelView& L = m.levels[level].lv;
-  const int64_t work = m.nv + (int64_t)m.ne * L.N + (int64_t)m.nf * L.N * 4;
-  const int g = blocks_for(work, kThreads * 8, 2048);
+  // face-interior points dominate: nf (N - 1)(N - 2) / 2; up to 8 CTAs per SM
+  const int64_t work = m.nv + (int64_t)m.ne * L.N + (int64_t)m.nf * L.N * L.N / 2;
+  const int g = blocks_for(work, kThreads * 4, 1216);
   if (prec == 0)
     HHG_LAUNCH(HHG_K_OTHER, level, st, "dot", k_dot<double><<<g, kThreads, 0, st>>>(m.tab, L, (const double*)x1, (const double*)x2, m.partials));
   else

@@ -561,8 +561,7 @@ void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts&
       status = HHG_ERR_NOT_CONVERGED;
       break;
     }
-    apply_op(m, L, 0, K.p, K.q, st);
-    dot_op(m, L, 0, K.p, K.q, K.cs, st);
+    apply_dot_op(m, L, K.p, K.q, K.cs, st);   // q = A p and p.q
     // x += alpha p, r -= alpha q (and its FP32 copy), ||r||^2
     k_fcg_step<<<nb, kVecThreads, 0, st>>>(m.tab, ld.lv, K.cs + cur, K.cs, K.p, K.q, x, r, mixed ? r32 : nullptr, part);
     check_cuda(cudaGetLastError(), "cg step");
