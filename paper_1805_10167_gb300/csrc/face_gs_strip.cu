@@ -294,8 +294,9 @@ __device__ __forceinline__ void strip_task(const MeshTables& M, const LevelView&
 }
 
 // A whole face of a small level (N <= kSmallN) by one CTA in shared memory:
-// the closed triangle is staged, the three colours are applied one after the
-// other, every point of a colour at once, and the triangle is written out.
+// the closed triangle of x and of b is staged, the three colours are applied
+// one after the other, every point of a colour at once, and the triangle of
+// x is written out.
 constexpr int kSmallN = 64;
 
 template <typename T, bool VARK, bool FWD>
@@ -306,9 +307,29 @@ __device__ __forceinline__ void face_small(const MeshTables& M, const LevelView&
   const int S = (int)L.S;
   const int64_t fb = L.f_off + (int64_t)f * L.FS;
   const int n = (N + 1) * S;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    const int j = q / S, i = q - j * S;
-    if (i <= N - j) sx[q] = xin[fb + q];
+  T* sb = sx + n;   // b staged beside x: every read of the colour phases is a shared-memory read
+  // staging in batches of 8 slots per thread, all loads issued before any
+  // store (one memory latency per batch, not per slot); slots outside the
+  // closed triangle are not read (their shared copies are never used)
+  constexpr int kB = 8;
+  for (int q0 = threadIdx.x; q0 < n; q0 += kB * blockDim.x) {
+    T vx[kB], vb[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int q = q0 + u * blockDim.x;
+      const int j = q / S, i = q - j * S;
+      const bool ok = q < n && i <= N - j;
+      vx[u] = ok ? xin[fb + q] : T(0);
+      vb[u] = ok ? b[fb + q] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int q = q0 + u * blockDim.x;
+      if (q < n) {
+        sx[q] = vx[u];
+        sb[q] = vb[u];
+      }
+    }
   }
   __syncthreads();
   const FaceRec& F = M.faces[f];
@@ -327,7 +348,7 @@ __device__ __forceinline__ void face_small(const MeshTables& M, const LevelView&
       const int p = j * S + i;
       const T xe = sx[p + 1], xw = sx[p - 1], xn = sx[p + S], xs = sx[p - S];
       const T xse = sx[p + 1 - S], xnw = sx[p - 1 + S];
-      const T bv = b[fb + p];
+      const T bv = sb[p];
       if (!VARK) {
         T acc = bv * dinv;
         acc = fma(w2, xe + xw, acc);
@@ -362,31 +383,45 @@ __device__ __forceinline__ void face_small(const MeshTables& M, const LevelView&
 // leaders count in, the last one resets the count and advances the
 // generation, the others wait for it -- for at most about a second, after
 // which they set *err and go on (the sweep's result is then wrong and the
-// host reports a timeout).  The fences order every write before the barrier
-// before every read after it, across the grid.
-constexpr long kBarrierPolls = 1L << 25;   // x ~32 ns sleep
+// host reports a timeout).  Release/acquire order every write before the
+// barrier before every read after it, across the grid.
+constexpr long kBarrierPolls = 1L << 21;   // L2 round trips: a second or two
 
-__device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// The generation a CTA leader expects to see advanced by its next barrier:
+// read once at kernel start (no barrier of this launch can have completed
+// before this CTA arrives at it).
+__device__ __forceinline__ unsigned barrier_start(unsigned* bar) {
+  return threadIdx.x == 0 ? ld_acquire(bar + 1) : 0u;
+}
+
+// Arrival is one acquire-release atomic (releasing this CTA's writes,
+// ordered before it by the CTA barrier); the last arrival resets the count
+// and releases the next generation; the others poll it with acquire loads.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned& gen, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      bar[0] = 0;
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+    if (old == gridDim.x - 1) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
     } else {
       long polls = 0;
-      while (*gen == g) {
+      while (ld_acquire(bar + 1) == gen) {
         if (++polls > kBarrierPolls) {
           atomicExch(err, 1);
           break;
         }
-        __nanosleep(32);
       }
     }
-    __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    ++gen;
   }
   __syncthreads();
 }
@@ -404,6 +439,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
                const T* __restrict__ k, const int4* __restrict__ tasks, int ntasks,
                const int* __restrict__ clist, EdgeColours cs, int small, unsigned* bar, int* err) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
+  unsigned gen = barrier_start(bar);
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kStripWarps + (int)(threadIdx.x >> 5);
   const int nw = gridDim.x * kStripWarps;
@@ -448,18 +484,18 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
   };
   if (FWD) {
     vertices(xin);
-    grid_barrier(bar, err);
+    grid_barrier(bar, gen, err);
     for (int c = 0; c < cs.n; ++c) {
       edges(xin, c);
-      grid_barrier(bar, err);
+      grid_barrier(bar, gen, err);
     }
     faces();
   } else {
     faces();
-    grid_barrier(bar, err);
+    grid_barrier(bar, gen, err);
     for (int c = cs.n - 1; c >= 0; --c) {
       edges(xout, c);
-      grid_barrier(bar, err);
+      grid_barrier(bar, gen, err);
     }
     vertices(xout);
   }
@@ -498,11 +534,18 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
   const LevelData& ld = m.levels[level];
   const SweepCfg& c = ld.sweep[sizeof(T) == 8 ? 0 : 1];
   const int small = ld.lv.N <= kSmallN ? 1 : 0;
-  const size_t smem = small ? (size_t)(ld.lv.N + 1) * ld.lv.S * sizeof(T) : 0;
+  const size_t smem = small ? 2 * (size_t)(ld.lv.N + 1) * ld.lv.S * sizeof(T) : 0;
   // CTAs per SM of this instance for each level (the shared memory of the
   // small-level face phase depends on N only; the same on every device of a run)
   static int resident_at[32] = {0};
   const int lvl = std::min(level, 31);
+  static size_t configured = 48 * 1024;   // largest dynamic shared memory enabled for this instance
+  if (smem > configured) {
+    check_cuda(cudaFuncSetAttribute(k_gs_sweep<T, DF, VARK, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem),
+               "whole sweep shared memory");
+    configured = smem;
+  }
   if (resident_at[lvl] == 0) {
     int r = 0;
     check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_gs_sweep<T, DF, VARK, FWD>, kStripWarps * 32, smem),
