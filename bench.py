@@ -43,7 +43,7 @@ N_SM = 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one level-9 launch of the
 # FP64 face sweep (annulus, 128 faces), per (kernel variant, split), from the
 # ncu captures summarised under profiles/; None until captured
-TRAFFIC_L9 = {(1, 32): 390.061568e6 + 120.651776e6}   # k_gs_sweep<double>, default split
+TRAFFIC_L9 = {(1, 32): 390.379008e6 + 120.408576e6}   # k_gs_sweep<double>, default split
 
 
 def parse():
@@ -287,13 +287,15 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    steps = max(1, min(args.steps, 4))
-    rate, spc, n_free = oracle_rate(args.cpu_level, steps, warmup=min(args.warmup, 1))
+    # each step is one oracle V(3,3) + residual norm on the level --cpu-level
+    # sample of the same annulus (about 0.6 s at level 8), K steps after W
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    rate, spc, n_free = oracle_rate(args.cpu_level, steps, warmup=warm)
     sample = (f"annulus 32x2 (128 faces) at level {args.cpu_level} ({n_free} free DoFs), FP64 V(3,3) + "
-              f"residual norm, {steps} cycles after {min(args.warmup, 1)} warm-up; numpy/scipy oracle")
+              f"residual norm, {steps} cycles after {warm} warm-up; numpy/scipy oracle")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": spc * 1e3, "higher_is_better": True,
+        "steps": steps, "warmup": warm, "ms_per_step": spc * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload(args.level)[2], "level": args.level},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
