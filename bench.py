@@ -46,6 +46,31 @@ N_SM = 152
 TRAFFIC_L9 = {(1, 32): 390.379008e6 + 120.408576e6}   # k_gs_sweep<double>, default split
 
 
+# ------------------------------------------------------------------ ranks
+def rank_barrier(world):
+    """Barrier over the ranks of the job (one process per GPU)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def rank_max(v, world, device):
+    """The maximum of a per-rank value over all ranks (the slowest rank's time)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, steps, ms):
+    """Whole-job throughput (weak scaling: every rank processes its own
+    replica): all ranks' units per second, in units of 1e9."""
+    return world * units_per_rank * steps / (ms / 1e3) / 1e9
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,15 +360,10 @@ def run_ours(args):
         g.residual(L, x, b, r, nrm, stream=st)
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        rank_barrier(world)
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(v, world, dev)
 
     for _ in range(args.warmup):
         step()
@@ -364,7 +384,7 @@ def run_ours(args):
     clk = clocks.stop()
     barrier()
     ms = max_over_ranks(e0.elapsed_time(e1))
-    value = world * n_free * args.steps / (ms / 1e3) / 1e9
+    value = job_rate(world, n_free, args.steps, ms)
 
     # dominant kernel: the three-colour face Gauss-Seidel sweep on level L
     # (6 launches per V(3,3) cycle).  For k = 1 each interior point costs 7
@@ -423,7 +443,7 @@ def run_ours(args):
     e1.record(st)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1))
-    e2e = {"value": world * n_free * args.steps / (ms_e2e / 1e3) / 1e9, "unit": UNIT,
+    e2e = {"value": job_rate(world, n_free, args.steps, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": int(b_host.numel() * 8), "d2h_bytes_per_step": 8,
            "ms_per_step": ms_e2e / args.steps}
 
