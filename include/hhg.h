@@ -216,8 +216,16 @@ hhg_status hhg_smooth(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
 
 /* One V(nu1, nu2) cycle on A x = b at `level` (Sec. 4.3): forward GS
  * pre-smoothing, residual, full-weighting restriction, recursion with zero
- * initial guess, CG on level 0, linear prolongation and correction, backward
- * GS post-smoothing.  opts may be NULL (V(3,3)). */
+ * initial guess, level-0 solve (a stored inverse of the level-0 matrix when
+ * every problem has at most 512 free macro-vertices and a positive definite
+ * matrix, else conjugate gradients to 1e-14), linear prolongation and
+ * correction, backward GS post-smoothing.  opts may be NULL (V(3,3)).
+ * Asynchronous.  Calls repeated with the same level, precision, cycle shape
+ * and x, b pointers replay a CUDA graph of the cycle's launches (captured on
+ * the second such call on a stream of the library's own, launched on
+ * `stream`); a change of sweep split, arithmetic mode or coefficient drops
+ * the captured graphs.  While launch profiling is on, or while `stream` is
+ * itself being captured, the launches are issued one by one. */
 hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, const void* b,
                       const hhg_vcycle_opts* opts, void* stream);
 
@@ -225,7 +233,9 @@ hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
  * ||b - A x||_2 <= tol * ||b - A x0||_2 (free DoFs).  Synchronous: reads one
  * residual norm back per cycle (MG, IR) or Krylov step (FGMRES, PCG; for PCG
  * the norm of the updated residual, confirmed by the true residual before
- * the solve returns).  Returns HHG_ERR_NOT_CONVERGED after max_iter
+ * the solve returns).  The launches of one cycle (MG, IR) or of one
+ * preconditioner application and direction update (PCG) are replayed as a
+ * CUDA graph from their third use on, as for hhg_vcycle.  Returns HHG_ERR_NOT_CONVERGED after max_iter
  * (x holds the last iterate) and HHG_ERR_NAN on a non-finite norm.  opts may
  * be NULL (MG, V(3,3), 1e-10, 100); rep may be NULL. */
 hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,

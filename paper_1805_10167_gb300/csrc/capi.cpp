@@ -84,7 +84,7 @@ bool device_timed_out(const hhg::Mesh& m, cudaStream_t st) {
   hhg::check_cuda(cudaStreamSynchronize(st), "sync");
   if (e) {
     hhg::check_cuda(cudaMemsetAsync(m.err, 0, sizeof(int), st), "err clear");
-    hhg::check_cuda(cudaMemsetAsync(m.gbar, 0, 4 * sizeof(unsigned), st), "grid barrier reset");
+    hhg::check_cuda(cudaMemsetAsync(m.gbar, 0, hhg::kGridBarWords * sizeof(unsigned), st), "grid barrier reset");
   }
   return e != 0;
 }
@@ -366,8 +366,12 @@ hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
     need_vec(b, "b");
     const int nu1 = opts ? opts->nu1 : 3, nu2 = opts ? opts->nu2 : 3;
     if (nu1 < 0 || nu2 < 0) throw ArgError("negative sweep count");
-    hhg::ghost_fill(m, level, prec, x, S(stream));
-    hhg::vcycle_run(m, level, prec, x, b, nu1, nu2, 0, S(stream));
+    const hhg::GraphKey key{1, (uint64_t)level, (uint64_t)prec, (uint64_t)nu1, (uint64_t)nu2, 0,
+                            hhg::key_ptr(x), hhg::key_ptr(b)};
+    hhg::graphed(m, key, S(stream), [&](cudaStream_t s) {
+      hhg::ghost_fill(m, level, prec, x, s);
+      hhg::vcycle_run(m, level, prec, x, b, nu1, nu2, 0, s);
+    });
     return HHG_OK;
   });
 }
@@ -424,14 +428,22 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
         // inner FP32 V-cycle on A d = r from d = 0, then x += d and the new
         // residual in FP64 in one pass, ping-ponging between x and the
         // level's FP64 workspace
-        hhg::zero_vec(m, level, 1, ld.x[1], st);
-        hhg::vcycle_run(m, level, 1, ld.x[1], ld.b[1], o.nu1, o.nu2, 0, st);
         double* nxt = cur == x ? (double*)ld.w[0] : x;
-        hhg::update_residual_f64(m, level, cur, (const float*)ld.x[1], nxt, b, (float*)ld.b[1], nrm, st);
+        const hhg::GraphKey key{2, (uint64_t)level, 1, (uint64_t)o.nu1, (uint64_t)o.nu2, hhg::key_ptr(cur),
+                                hhg::key_ptr(nxt), hhg::key_ptr(b)};
+        hhg::graphed(m, key, st, [&](cudaStream_t s) {
+          hhg::zero_vec(m, level, 1, ld.x[1], s);
+          hhg::vcycle_run(m, level, 1, ld.x[1], ld.b[1], o.nu1, o.nu2, 0, s);
+          hhg::update_residual_f64(m, level, cur, (const float*)ld.x[1], nxt, b, (float*)ld.b[1], nrm, s);
+        });
         cur = nxt;
       } else {
-        hhg::vcycle_run(m, level, 0, x, b, o.nu1, o.nu2, 0, st);
-        hhg::residual_op(m, level, 0, x, b, ld.r[0], nrm, st);
+        const hhg::GraphKey key{3, (uint64_t)level, 0, (uint64_t)o.nu1, (uint64_t)o.nu2, 0, hhg::key_ptr(x),
+                                hhg::key_ptr(b)};
+        hhg::graphed(m, key, st, [&](cudaStream_t s) {
+          hhg::vcycle_run(m, level, 0, x, b, o.nu1, o.nu2, 0, s);
+          hhg::residual_op(m, level, 0, x, b, ld.r[0], nrm, s);
+        });
       }
       ++it;
       r = std::sqrt(read_scalar(nrm, st));
@@ -473,6 +485,7 @@ hhg_status hhg_fp64_arith(hhg_mesh mesh, int32_t set, int32_t* mode) {
       if (*mode != HHG_ARITH_IEEE && *mode != HHG_ARITH_DFLOAT) throw ArgError("bad FP64 arithmetic mode");
       hhg::check_cuda(cudaDeviceSynchronize(), "sync");   // kernels in flight keep their arithmetic
       m.fp64_df = *mode == HHG_ARITH_DFLOAT;
+      hhg::graphs_clear(m);
     } else {
       *mode = m.fp64_df ? HHG_ARITH_DFLOAT : HHG_ARITH_IEEE;
     }

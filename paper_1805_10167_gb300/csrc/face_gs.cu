@@ -17,6 +17,7 @@
 // Every wait on an mbarrier is bounded; a CTA that gives up sets *err, drains
 // (bounded) the copies it issued and returns.
 #include "stencil.cuh"
+#include "tma.cuh"
 
 namespace hhg {
 
@@ -28,39 +29,6 @@ constexpr int kThreadsGS = kRC * kWPR * 32;
 constexpr int kSlots = 2 * kRC + 4;   // ring: rows [q-3, q+RC] in use, [q+RC+1, q+2RC] in flight
 constexpr int kBarBytes = 256;
 constexpr long kMaxTries = 1L << 22;  // try_wait polls before a wait gives up
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
 
 }  // namespace
 
@@ -95,7 +63,7 @@ __global__ void __launch_bounds__(kThreadsGS)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kSlots; ++s) mbar_init(&bars[s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
     s_fail = 0;
   }
   __syncthreads();
@@ -166,7 +134,7 @@ __global__ void __launch_bounds__(kThreadsGS)
     // prefetch: rows up to q + 2 RC whose ring slot is free (slot of row
     // r - kSlots < q - 3 has been read for the last time in the previous step)
     if (threadIdx.x == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      fence_proxy_async_smem();
       const int last = min(rhi, q + 2 * kRC);
       for (; next_issue <= last; ++next_issue) {
         const int r = next_issue;

@@ -27,6 +27,7 @@
 // exactly one (strip, row block).
 #include "arith.cuh"
 #include "stencil.cuh"
+#include "tma.cuh"
 
 namespace hhg {
 
@@ -294,58 +295,56 @@ __device__ __forceinline__ void strip_task(const MeshTables& M, const LevelView&
 }
 
 // A whole face of a small level (N <= kSmallN) by one CTA in shared memory:
-// the closed triangle of x and of b is staged, the three colours are applied
-// one after the other, every point of a colour at once, and the triangle of
-// x is written out.
-constexpr int kSmallN = 64;
+// the face blocks of x and b (contiguous, (N + 1) S slots each) arrive by two
+// bulk copies on one mbarrier, the three colours are applied one after the
+// other -- each colour's points taken from the level's list of interior
+// points by colour, so no thread idles outside the triangle -- and the
+// closed triangle of x is written out.  `phase` is the mbarrier parity of
+// the CTA's next face.  A copy that never lands (the wait is bounded) sets
+// *err; the face is then left as it was.
+constexpr long kSmallWaitPolls = 1L << 22;   // mbarrier polls before giving up
+constexpr int kSmallHeader = 128;            // dynamic shared memory before sx: the mbarrier
 
 template <typename T, bool VARK, bool FWD>
 __device__ __forceinline__ void face_small(const MeshTables& M, const LevelView& L, int f, const T* xin,
                                            T* xout, const T* __restrict__ b, const T* __restrict__ k,
-                                           T* sx) {
+                                           T* sx, uint64_t* mb, uint32_t& phase,
+                                           const unsigned short* __restrict__ pts, int4 cptr, int* err) {
   const int N = L.N;
   const int S = (int)L.S;
   const int64_t fb = L.f_off + (int64_t)f * L.FS;
   const int n = (N + 1) * S;
-  T* sb = sx + n;   // b staged beside x: every read of the colour phases is a shared-memory read
-  // staging in batches of 8 slots per thread, all loads issued before any
-  // store (one memory latency per batch, not per slot); slots outside the
-  // closed triangle are not read (their shared copies are never used)
-  constexpr int kB = 8;
-  for (int q0 = threadIdx.x; q0 < n; q0 += kB * blockDim.x) {
-    T vx[kB], vb[kB];
-#pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      const int q = q0 + u * blockDim.x;
-      const int j = q / S, i = q - j * S;
-      const bool ok = q < n && i <= N - j;
-      vx[u] = ok ? xin[fb + q] : T(0);
-      vb[u] = ok ? b[fb + q] : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      const int q = q0 + u * blockDim.x;
-      if (q < n) {
-        sx[q] = vx[u];
-        sb[q] = vb[u];
-      }
+  T* sb = sx + n;
+  if (threadIdx.x == 0) {
+    const uint32_t bytes = (uint32_t)(n * sizeof(T));   // S is a multiple of 8: 16-byte multiples
+    fence_proxy_async_smem();   // earlier generic accesses of sx, sb before the copies overwrite them
+    mbar_arrive_expect_tx(mb, 2 * bytes);
+    bulk_load(sx, xin + fb, bytes, mb);
+    bulk_load(sb, b + fb, bytes, mb);
+  }
+  bool landed = true;
+  for (long t = 0; !mbar_try_wait(mb, phase);) {
+    if (++t > kSmallWaitPolls) {
+      landed = false;
+      break;
     }
   }
-  __syncthreads();
+  phase ^= 1u;
+  if (!__syncthreads_and(landed)) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
   const FaceRec& F = M.faces[f];
   const T dinv = (T)F.dinv, w0 = (T)F.w[0], w1 = (T)F.w[1], w2 = (T)F.w[2];
   const T* ku = VARK ? k + (int64_t)f * L.FS : nullptr;
   const T* kd = VARK ? k + (int64_t)(M.nf + f) * L.FS : nullptr;
-  const int W3 = N / 3 + 1;   // points of one colour in one row, at most
+#pragma unroll
   for (int ph = 0; ph < 3; ++ph) {
     const int c = FWD ? ph : 2 - ph;
-    for (int q = threadIdx.x; q < (N - 2) * W3; q += blockDim.x) {
-      const int j = 1 + q / W3;
-      int i = ((c - 2 * j) % 3 + 3) % 3;   // first column of colour c in row j, >= 1
-      if (i == 0) i = 3;
-      i += 3 * (q - (j - 1) * W3);
-      if (i + j > N - 1) continue;
-      const int p = j * S + i;
+    const int q0 = c == 0 ? cptr.x : c == 1 ? cptr.y : cptr.z;
+    const int q1 = c == 0 ? cptr.y : c == 1 ? cptr.z : cptr.w;
+    for (int q = q0 + (int)threadIdx.x; q < q1; q += blockDim.x) {
+      const int p = __ldg(pts + q);
       const T xe = sx[p + 1], xw = sx[p - 1], xn = sx[p + S], xs = sx[p - S];
       const T xse = sx[p + 1 - S], xnw = sx[p - 1 + S];
       const T bv = sb[p];
@@ -378,13 +377,16 @@ __device__ __forceinline__ void face_small(const MeshTables& M, const LevelView&
 }
 
 // ----------------------------------------------------------- whole sweep
-// Grid-wide barrier for a cooperative launch (every CTA resident; bar[0..1]
-// = count, generation, bar[2..3] = the face phase's task tickets): CTA
-// leaders count in, the last one resets the count and advances the
-// generation, the others wait for it -- for at most about a second, after
-// which they set *err and go on (the sweep's result is then wrong and the
-// host reports a timeout).  Release/acquire order every write before the
-// barrier before every read after it, across the grid.
+// Grid-wide barriers of a cooperative launch (every CTA resident).  Barrier
+// k of a launch has its own arrival counter: CTA leaders add 1 with release
+// semantics and poll it with acquire loads until it reaches gridDim.x.  Two
+// sets of counters alternate between launches: at the start of a launch
+// every leader reads which set is in use (bar[0]), CTA 0 zeroes the other
+// set (the previous launch, which used it, has finished), and after the
+// first barrier -- when every leader has read bar[0] -- CTA 0 flips bar[0]
+// for the next launch.  A wait gives up after about a second: it sets *err
+// and goes on (the sweep's result is then wrong, the host reports a timeout
+// and zeroes the words).
 constexpr long kBarrierPolls = 1L << 21;   // L2 round trips: a second or two
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -393,35 +395,42 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-// The generation a CTA leader expects to see advanced by its next barrier:
-// read once at kernel start (no barrier of this launch can have completed
-// before this CTA arrives at it).
-__device__ __forceinline__ unsigned barrier_start(unsigned* bar) {
-  return threadIdx.x == 0 ? ld_acquire(bar + 1) : 0u;
+__device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Arrival is one acquire-release atomic (releasing this CTA's writes,
-// ordered before it by the CTA barrier); the last arrival resets the count
-// and releases the next generation; the others poll it with acquire loads.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned& gen, int* err) {
+struct GridBar {
+  unsigned* cnt;   // this launch's counter set (thread 0 of each CTA)
+  unsigned set;    // its index, 0 or 1
+  int k;           // barriers passed
+};
+
+__device__ __forceinline__ GridBar barrier_start(unsigned* bar) {
+  GridBar g{nullptr, 0u, 0};
+  if (threadIdx.x == 0) {
+    g.set = ld_acquire(bar) & 1u;
+    g.cnt = bar + 4 + g.set * kGridBarSlots;
+    if (blockIdx.x == 0) {
+      unsigned* other = bar + 4 + (g.set ^ 1u) * kGridBarSlots;
+      for (int q = 0; q < kGridBarSlots; ++q) st_relaxed(other + q, 0u);
+    }
+  }
+  return g;
+}
+
+__device__ __forceinline__ void grid_barrier(unsigned* bar, GridBar& g, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
-    if (old == gridDim.x - 1) {
-      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
-    } else {
-      long polls = 0;
-      while (ld_acquire(bar + 1) == gen) {
-        if (++polls > kBarrierPolls) {
-          atomicExch(err, 1);
-          break;
-        }
+    unsigned* c = g.cnt + g.k;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c) : "memory");
+    for (long polls = 0; ld_acquire(c) < gridDim.x;) {
+      if (++polls > kBarrierPolls) {
+        atomicExch(err, 1);
+        break;
       }
     }
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    ++gen;
+    if (g.k == 0 && blockIdx.x == 0) st_relaxed(bar, g.set ^ 1u);
+    ++g.k;
   }
   __syncthreads();
 }
@@ -437,34 +446,64 @@ template <typename T, bool DF, bool VARK, bool FWD>
 __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
     k_gs_sweep(MeshTables M, LevelView L, T* xin, T* xout, const T* __restrict__ b,
                const T* __restrict__ k, const int4* __restrict__ tasks, int ntasks,
-               const int* __restrict__ clist, EdgeColours cs, int small, unsigned* bar, int* err) {
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
-  unsigned gen = barrier_start(bar);
+               const int* __restrict__ clist, const __grid_constant__ EdgeColours cs, int small,
+               const unsigned short* __restrict__ spts, int4 sptr, unsigned* bar, int* err) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  GridBar gb = barrier_start(bar);
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kStripWarps + (int)(threadIdx.x >> 5);
   const int nw = gridDim.x * kStripWarps;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int nt = gridDim.x * blockDim.x;
-  auto vertices = [&](T* x) {
-    for (int v = gw; v < M.nv; v += nw) vertex_gs<T, VARK>(M, L, v, lane, x, b, k);
+  // The table records of a thread's first edge point of a colour (and of a
+  // warp's first vertex) are loaded before the grid barrier that precedes
+  // their phase, so that after it only x and b are waited for; the packed
+  // point of the colour after is loaded one phase earlier still.
+  struct EdgePre {
+    EdgeRec E;
+    int e, t;
   };
-  auto edges = [&](T* x, int c) {
-    for (int q = cs.ptr[c] + gt; q < cs.ptr[c + 1]; q += nt) {
-      const int pk = clist[q];
-      const int e = pk / (L.N + 1);
-      edge_gs<T, VARK>(M, L, e, pk - e * (L.N + 1), x, b, k);
+  auto edge_pk = [&](int c) -> int {
+    if (c < 0 || c >= cs.n) return -1;
+    const int q = cs.ptr[c] + gt;
+    return q < cs.ptr[c + 1] ? __ldg(clist + q) : -1;
+  };
+  auto edge_pre = [&](int pk, EdgePre& p) {
+    if (pk < 0) return;
+    p.e = pk / (L.N + 1);
+    p.t = pk - p.e * (L.N + 1);
+    p.E = M.edges[p.e];
+  };
+  auto vertices = [&](T* x, const VertRec& V0) {
+    if (gw < M.nv) vertex_gs_rec<T, VARK>(M, L, V0, gw, lane, x, b, k);
+    for (int v = gw + nw; v < M.nv; v += nw) vertex_gs<T, VARK>(M, L, v, lane, x, b, k);
+  };
+  auto edges = [&](T* x, int c, int pk, const EdgePre& p) {
+    if (pk >= 0) edge_gs_rec<T, VARK>(M, L, p.E, p.e, p.t, x, b, k);
+    for (int q = cs.ptr[c] + gt + nt; q < cs.ptr[c + 1]; q += nt) {
+      const int pq = clist[q];
+      const int e = pq / (L.N + 1);
+      edge_gs<T, VARK>(M, L, e, pq - e * (L.N + 1), x, b, k);
     }
   };
   auto faces = [&]() {
     for (int64_t q = gt; q < L.f_off; q += nt) xout[q] = xin[q];
     if (small) {
+      uint64_t* mb = reinterpret_cast<uint64_t*>(dyn_smem);
+      T* sx = reinterpret_cast<T*>(dyn_smem + kSmallHeader);
+      uint32_t phase = 0;
+      if (threadIdx.x == 0) {
+        mbar_init(mb, 1);
+        mbar_init_fence();
+      }
+      __syncthreads();
       for (int f = blockIdx.x; f < M.nf; f += gridDim.x)
-        face_small<T, VARK, FWD>(M, L, f, xin, xout, b, k, reinterpret_cast<T*>(dyn_smem));
+        face_small<T, VARK, FWD>(M, L, f, xin, xout, b, k, sx, mb, phase, spts, sptr, err);
     } else {
       // tasks handed out one at a time from a ticket counter (the strips of
       // a face differ in height, the rows of a task in length); the last
       // warp to finish resets the counters for the next launch
-      unsigned* ticket = bar + 2;
+      unsigned* ticket = bar + 1;
       for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(ticket, 1u);
@@ -474,30 +513,46 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
       }
       if (lane == 0) {
         __threadfence();
-        if (atomicAdd(bar + 3, 1u) == (unsigned)nw - 1) {
+        if (atomicAdd(bar + 2, 1u) == (unsigned)nw - 1) {
+          bar[1] = 0;
           bar[2] = 0;
-          bar[3] = 0;
           __threadfence();
         }
       }
     }
   };
+  VertRec V0{};
+  EdgePre ep{};
   if (FWD) {
-    vertices(xin);
-    grid_barrier(bar, gen, err);
+    int pk = edge_pk(0), pk_next = edge_pk(1);
+    if (gw < M.nv) V0 = M.verts[gw];
+    vertices(xin, V0);
+    edge_pre(pk, ep);
+    grid_barrier(bar, gb, err);
     for (int c = 0; c < cs.n; ++c) {
-      edges(xin, c);
-      grid_barrier(bar, gen, err);
+      edges(xin, c, pk, ep);
+      pk = pk_next;
+      pk_next = edge_pk(c + 2);
+      edge_pre(pk, ep);
+      grid_barrier(bar, gb, err);
     }
     faces();
   } else {
+    int pk = edge_pk(cs.n - 1);
     faces();
-    grid_barrier(bar, gen, err);
+    int pk_next = edge_pk(cs.n - 2);
+    edge_pre(pk, ep);
+    grid_barrier(bar, gb, err);
     for (int c = cs.n - 1; c >= 0; --c) {
-      edges(xout, c);
-      grid_barrier(bar, gen, err);
+      edges(xout, c, pk, ep);
+      pk = pk_next;
+      pk_next = edge_pk(c - 2);
+      edge_pre(pk, ep);
+      if (c == 0 && gw < M.nv) V0 = M.verts[gw];
+      grid_barrier(bar, gb, err);
     }
-    vertices(xout);
+    if (cs.n == 0 && gw < M.nv) V0 = M.verts[gw];
+    vertices(xout, V0);
   }
 }
 
@@ -534,7 +589,7 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
   const LevelData& ld = m.levels[level];
   const SweepCfg& c = ld.sweep[sizeof(T) == 8 ? 0 : 1];
   const int small = ld.lv.N <= kSmallN ? 1 : 0;
-  const size_t smem = small ? 2 * (size_t)(ld.lv.N + 1) * ld.lv.S * sizeof(T) : 0;
+  const size_t smem = small ? kSmallHeader + 2 * (size_t)(ld.lv.N + 1) * ld.lv.S * sizeof(T) : 0;
   // CTAs per SM of this instance for each level (the shared memory of the
   // small-level face phase depends on N only; the same on every device of a run)
   static int resident_at[32] = {0};
@@ -578,7 +633,10 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   check_cuda(cudaLaunchKernelEx(&cfg, k_gs_sweep<T, DF, VARK, FWD>, m.tab, ld.lv, xin, xout, b, k,
-                                (const int4*)c.tasks, c.ntasks, (const int*)ld.colour_list, cs, small, m.gbar, m.err),
+                                (const int4*)c.tasks, c.ntasks, (const int*)ld.colour_list, cs, small,
+                                (const unsigned short*)ld.small_pts,
+                                make_int4(ld.small_ptr[0], ld.small_ptr[1], ld.small_ptr[2], ld.small_ptr[3]),
+                                m.gbar, m.err),
              "whole sweep launch");
 }
 

@@ -12,7 +12,9 @@
 // in the "up" array, downward (i,j) in the "down" array.
 #pragma once
 
+#include <array>
 #include <cstdint>
+#include <functional>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -167,6 +169,19 @@ struct EdgeColours {
   int ptr[kMaxEdgeColours + 1];
 };
 
+// Device state of the whole-sweep kernel (32-bit words): [0] which of the
+// two barrier-counter sets the next launch uses, [1] face-task ticket,
+// [2] finished-warp count, [3] unused, then two sets of kGridBarSlots
+// arrival counters (one per grid barrier of a launch).
+constexpr int kGridBarSlots = kMaxEdgeColours + 1;
+constexpr int kGridBarWords = 4 + 2 * kGridBarSlots;
+
+// Level-0 blocks of at most kDirectMaxN0 unknowns are solved by a stored inverse.
+constexpr int kDirectMaxN0 = 512;
+
+// Faces of levels with N <= kSmallN are swept one CTA per face in shared memory.
+constexpr int kSmallN = 64;
+
 struct LevelData {
   LevelView lv;
   int n_colours = 0;
@@ -182,15 +197,21 @@ struct LevelData {
   SweepCfg sweep[2];                // face sweep configuration per precision
   int* row_tasks = nullptr;         // device int4 (face, strip, j0, j1) of the row kernels
   int n_row_tasks = 0;
+  // N <= kSmallN: the interior points of a face ordered by colour (i + 2j) mod 3,
+  // as slots j * S + i; colour c is [small_ptr[c], small_ptr[c + 1])
+  unsigned short* small_pts = nullptr;
+  int small_ptr[4] = {0, 0, 0, 0};
 };
 
 struct Learned;
 struct KrylovSpace;
+struct GraphCache;
 
 struct Mesh {
   int nv = 0, ne = 0, nf = 0, max_level = 0;
   Learned* learned = nullptr;       // learned-smoother weights and optimiser state
   KrylovSpace* krylov = nullptr;    // FGMRES basis vectors
+  GraphCache* graphs = nullptr;     // captured launch sequences (graph.cpp)
   std::vector<FaceRec> h_faces;
   std::vector<EdgeRec> h_edges;
   std::vector<VertRec> h_verts;
@@ -208,13 +229,18 @@ struct Mesh {
   Block* blocks = nullptr;          // device copy
   int max_n0 = 0;
   double* A0 = nullptr;
+  // the inverse of every block's matrix (same offsets) when every block has
+  // n0 <= kDirectMaxN0 and is positive definite; the coarse solve is then one
+  // dense product instead of conjugate gradients
+  double* A0inv = nullptr;
+  bool coarse_direct = false;
   int* free0 = nullptr;             // level-0 vertex ids of all blocks
   std::vector<double> h_cot_unit;   // cached for k = 1
   // reduction scratch
   double* partials = nullptr;       // kMaxPartials doubles
   double* scalars = nullptr;        // 16 doubles of device scalars
   int* err = nullptr;               // device error word: 1 = a bounded wait gave up
-  unsigned* gbar = nullptr;         // device state of the whole-sweep kernel: barrier count, generation, task tickets
+  unsigned* gbar = nullptr;         // device state of the whole-sweep kernel (kGridBarWords words)
   int device = 0;
 };
 
@@ -360,5 +386,16 @@ class LaunchScope {
 };
 void profile_begin(uint32_t mask, int level);
 void profile_end(int64_t* launches, double* ms);
+bool profiling_on();
+
+// CUDA-graph replay of a fixed launch sequence (graph.cpp): `body` issues
+// kernel launches and asynchronous copies on the stream it is given and
+// nothing else (no host synchronisation); `key` must determine every launch.
+using GraphKey = std::array<uint64_t, 8>;
+void graphs_create(Mesh& m);
+void graphs_destroy(Mesh& m);
+void graphs_clear(const Mesh& m);
+void graphed(const Mesh& m, const GraphKey& key, cudaStream_t st, const std::function<void(cudaStream_t)>& body);
+inline uint64_t key_ptr(const void* p) { return (uint64_t)(uintptr_t)p; }
 
 }  // namespace hhg

@@ -295,7 +295,9 @@ __global__ void k_restrict_ve(MeshTables M, LevelView Lf, LevelView Lc, const T*
       if (!E.dirichlet) {
         const T* re = rf + Lf.e_off + (int64_t)e * Lf.ES;
         T s = re[2 * tc - 1] + re[2 * tc + 1];
-        for (int k = 0; k < E.nfaces; ++k) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {   // unrolled: the record stays in registers
+          if (k >= E.nfaces) break;
           const EdgeSide sd = E.side[k];
           const int p = 2 * (sd.aligned ? tc : Nc - tc);
           const T* rff = rf + Lf.f_off + (int64_t)sd.face * Lf.FS;
@@ -452,6 +454,35 @@ __global__ void k_coarse_cg(const Block* __restrict__ blocks, const double* __re
     __syncthreads();
   }
   for (int i = threadIdx.x; i < n0; i += blockDim.x) x[v_off + idx[i]] = (T)xs[i];
+}
+
+// Direct level-0 solve x = A0^{-1} b with the stored inverse: CTA (cx, blk)
+// takes rows [32 cx, 32 cx + 32) of block blk, one warp per row at a time,
+// lanes over the columns (b staged in shared memory), in double.
+constexpr int kDirectRows = 32;
+
+template <typename T>
+__global__ void k_coarse_direct(const Block* __restrict__ blocks, const double* __restrict__ Ainv,
+                                const int* __restrict__ free0, const T* __restrict__ b, T* __restrict__ x,
+                                int64_t v_off) {
+  extern __shared__ double bs[];
+  const Block B = blocks[blockIdx.y];
+  const int n0 = B.n0;
+  const int r0 = blockIdx.x * kDirectRows;
+  if (r0 >= n0) return;
+  const double* A = Ainv + B.a0_off;
+  const int* idx = free0 + B.free0_off;
+  for (int j = threadIdx.x; j < n0; j += blockDim.x) bs[j] = (double)b[v_off + idx[j]];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int r1 = min(n0, r0 + kDirectRows);
+  for (int r = r0 + warp; r < r1; r += nwarp) {
+    const double* row = A + (int64_t)r * n0;
+    double s = 0.0;
+    for (int j = lane; j < n0; j += 32) s = fma(row[j], bs[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[v_off + idx[r]] = (T)s;
+  }
 }
 
 // --------------------------------------------------------------- BLAS-1
@@ -781,7 +812,14 @@ void prolongate_add(const Mesh& m, int fine_level, int prec, const void* x_coars
 }
 
 void coarse_solve(const Mesh& m, int prec, const void* b0, void* x0, cudaStream_t st) {
-  if (m.max_n0 > 0) {
+  if (m.max_n0 > 0 && m.coarse_direct) {
+    const dim3 grid((m.max_n0 + kDirectRows - 1) / kDirectRows, (unsigned)m.h_blocks.size());
+    const size_t smem = (size_t)m.max_n0 * sizeof(double);
+    if (prec == 0)
+      HHG_LAUNCH(HHG_K_OTHER, 0, st, "coarse direct", k_coarse_direct<double><<<grid, kThreads, smem, st>>>(m.blocks, m.A0inv, m.free0, (const double*)b0, (double*)x0, m.levels[0].lv.v_off));
+    else
+      HHG_LAUNCH(HHG_K_OTHER, 0, st, "coarse direct", k_coarse_direct<float><<<grid, kThreads, smem, st>>>(m.blocks, m.A0inv, m.free0, (const float*)b0, (float*)x0, m.levels[0].lv.v_off));
+  } else if (m.max_n0 > 0) {
     const size_t smem = 4 * (size_t)m.max_n0 * sizeof(double);
     const int nb = (int)m.h_blocks.size();
     if (prec == 0)

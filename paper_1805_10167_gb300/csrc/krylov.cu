@@ -526,19 +526,20 @@ void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts&
     if (rep && rep->history && k < rep->history_cap) rep->history[k] = v;
   };
   // z = M(r) (r32 already holds r in the mixed form); r.z into cs[slot], q.z into cs[4]
-  auto precond = [&](int slot) {
+  auto precond_on = [&](int slot, cudaStream_t s) {
     if (mixed) {
-      zero_vec(m, L, 1, z32, st);
-      vcycle_run(m, L, 1, z32, r32, o.nu1, o.nu2, 0, st);
+      zero_vec(m, L, 1, z32, s);
+      vcycle_run(m, L, 1, z32, r32, o.nu1, o.nu2, 0, s);
     } else {
-      zero_vec(m, L, 0, z, st);
-      vcycle_run(m, L, 0, z, r, o.nu1, o.nu2, 0, st);
+      zero_vec(m, L, 0, z, s);
+      vcycle_run(m, L, 0, z, r, o.nu1, o.nu2, 0, s);
     }
-    k_fcg_widen<<<nb, kVecThreads, 0, st>>>(m.tab, ld.lv, mixed ? z32 : nullptr, z, r, K.q, part);
+    k_fcg_widen<<<nb, kVecThreads, 0, s>>>(m.tab, ld.lv, mixed ? z32 : nullptr, z, r, K.q, part);
     check_cuda(cudaGetLastError(), "cg widen");
-    k_sum_ordered<<<1, kVecThreads, 0, st>>>(part, nb, K.cs + slot);
-    k_sum_ordered<<<1, kVecThreads, 0, st>>>(part + nb, nb, K.cs + 4);
+    k_sum_ordered<<<1, kVecThreads, 0, s>>>(part, nb, K.cs + slot);
+    k_sum_ordered<<<1, kVecThreads, 0, s>>>(part + nb, nb, K.cs + 4);
   };
+  auto precond = [&](int slot) { precond_on(slot, st); };
   ghost_fill(m, L, 0, x, st);
   residual_op(m, L, 0, x, b, r, K.cs + 1, st);
   const double r0 = std::sqrt(host_scalar(K.cs + 1, st));
@@ -582,12 +583,17 @@ void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts&
     }
     record(it, rn);
     const int nxt = cur == 2 ? 3 : 2;
-    precond(nxt);
-    if (mixed)   // flexible: beta = -(q.z) / (p.q)
-      k_fcg_dir<<<nb, kVecThreads, 0, st>>>(m.tab, ld.lv, K.cs + 4, K.cs, -1.0, z, K.p);
-    else         // beta = (r.z)_new / (r.z)_old
-      k_fcg_dir<<<nb, kVecThreads, 0, st>>>(m.tab, ld.lv, K.cs + nxt, K.cs + cur, 1.0, z, K.p);
-    check_cuda(cudaGetLastError(), "cg direction");
+    // the preconditioner and the new direction: one captured sequence per slot
+    const GraphKey key{4, (uint64_t)L, (uint64_t)mixed, (uint64_t)o.nu1, (uint64_t)o.nu2, (uint64_t)nxt,
+                       key_ptr(K.p), key_ptr(K.cs)};
+    graphed(m, key, st, [&](cudaStream_t s) {
+      precond_on(nxt, s);
+      if (mixed)   // flexible: beta = -(q.z) / (p.q)
+        k_fcg_dir<<<nb, kVecThreads, 0, s>>>(m.tab, ld.lv, K.cs + 4, K.cs, -1.0, z, K.p);
+      else         // beta = (r.z)_new / (r.z)_old
+        k_fcg_dir<<<nb, kVecThreads, 0, s>>>(m.tab, ld.lv, K.cs + nxt, K.cs + cur, 1.0, z, K.p);
+      check_cuda(cudaGetLastError(), "cg direction");
+    });
     cur = nxt;
   }
   if (rep) {

@@ -88,6 +88,40 @@ static void colour_edges(const Mesh& m, int N, std::vector<int>& ptr, std::vecto
 // Dense level-0 matrices, one per block, over its free macro-vertices (level
 // 0 has no edge or face interiors).  k0[f] = coefficient of face f's single
 // micro-triangle.
+// Inverse of the symmetric positive definite n x n matrix A (row-major) by
+// its Cholesky factor A = L L^T: column c of the inverse solves L L^T y = e_c.
+// Returns false when a pivot is not positive (A not positive definite).
+static bool spd_inverse(const double* A, int n, double* inv) {
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = A[(size_t)j * n + j];
+    for (int q = 0; q < j; ++q) d -= L[(size_t)j * n + q] * L[(size_t)j * n + q];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double v = A[(size_t)i * n + j];
+      for (int q = 0; q < j; ++q) v -= L[(size_t)i * n + q] * L[(size_t)j * n + q];
+      L[(size_t)i * n + j] = v / ljj;
+    }
+  }
+  std::vector<double> y(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {   // L y = e_c
+      double v = i == c ? 1.0 : 0.0;
+      for (int q = 0; q < i; ++q) v -= L[(size_t)i * n + q] * y[q];
+      y[i] = v / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {   // L^T z = y
+      double v = y[i];
+      for (int q = i + 1; q < n; ++q) v -= L[(size_t)q * n + i] * y[q];
+      y[i] = v / L[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = y[i];
+  }
+  return true;
+}
+
 static void assemble_level0(Mesh& m, const std::vector<double>& k0) {
   std::vector<int> map(m.nv, -1), free0;
   std::vector<double> A;
@@ -120,12 +154,22 @@ static void assemble_level0(Mesh& m, const std::vector<double>& k0) {
     }
     m.max_n0 = std::max(m.max_n0, n0);
   }
+  std::vector<double> Ainv;
+  m.coarse_direct = m.max_n0 <= kDirectMaxN0;
+  if (m.coarse_direct) {
+    Ainv.assign(A.size(), 0.0);
+    for (const Block& B : m.h_blocks)
+      if (B.n0 > 0 && !spd_inverse(A.data() + B.a0_off, B.n0, Ainv.data() + B.a0_off)) m.coarse_direct = false;
+  }
   if (!m.A0) {
     m.A0 = (double*)dev_alloc(m, std::max<size_t>(1, A.size()) * sizeof(double));
+    m.A0inv = (double*)dev_alloc(m, std::max<size_t>(1, A.size()) * sizeof(double));
     m.free0 = upload(m, free0);
     m.blocks = upload(m, m.h_blocks);
   }
   if (!A.empty()) check_cuda(cudaMemcpy(m.A0, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice), "A0");
+  if (m.coarse_direct && !A.empty())
+    check_cuda(cudaMemcpy(m.A0inv, Ainv.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice), "A0 inverse");
   check_cuda(cudaMemcpy(m.blocks, m.h_blocks.data(), m.h_blocks.size() * sizeof(Block), cudaMemcpyHostToDevice), "blocks");
 }
 
@@ -285,6 +329,18 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
         ld.w[p] = dev_alloc(m, bytes);
       }
       default_sweep(m, l);
+      if (ld.lv.N <= kSmallN) {
+        const int N = ld.lv.N, S = (int)ld.lv.S;
+        std::vector<unsigned short> pts;
+        for (int c = 0; c < 3; ++c) {
+          ld.small_ptr[c] = (int)pts.size();
+          for (int j = 1; j + 2 <= N; ++j)
+            for (int i = 1; i + j <= N - 1; ++i)
+              if ((i + 2 * j) % 3 == c) pts.push_back((unsigned short)(j * S + i));
+        }
+        ld.small_ptr[3] = (int)pts.size();
+        if (!pts.empty()) ld.small_pts = upload(m, pts);
+      }
       {   // row kernels: 96-column strips in blocks of about 64 rows
         const std::vector<int> rt = row_strip_tasks(m.nf, ld.lv.N, 64);
         ld.row_tasks = upload(m, rt);
@@ -294,11 +350,13 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
     m.partials = (double*)dev_alloc(m, kMaxPartials * sizeof(double));
     m.scalars = (double*)dev_alloc(m, 16 * sizeof(double));
     m.err = (int*)dev_alloc(m, 16 * sizeof(int));
-    m.gbar = (unsigned*)dev_alloc(m, 4 * sizeof(unsigned));   // zeroed
+    m.gbar = (unsigned*)dev_alloc(m, kGridBarWords * sizeof(unsigned));   // zeroed
     std::vector<double> k0(m.nf, 1.0);
     assemble_level0(m, k0);
+    graphs_create(m);
     check_cuda(cudaDeviceSynchronize(), "mesh setup");
   } catch (...) {
+    graphs_destroy(m);
     for (void* p : m.allocations) cudaFree(p);
     delete mp;
     throw;
@@ -309,6 +367,7 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
 void mesh_destroy_internal(Mesh* m) {
   if (!m) return;
   cudaDeviceSynchronize();
+  graphs_destroy(*m);
   learned_free(*m);
   krylov_free(*m);
   for (void* p : m->allocations) cudaFree(p);
@@ -319,6 +378,7 @@ void mesh_destroy_internal(Mesh* m) {
 // changes results: every point is updated from the same operands whichever
 // CTA or warp owns it).
 void set_sweep(Mesh& m, int level, int prec, int variant, int param) {
+  graphs_clear(m);
   LevelData& ld = m.levels[level];
   SweepCfg& c = ld.sweep[prec];
   std::vector<int> tk = variant == SWEEP_STRIP ? strip_tasks(m.nf, ld.lv.N, param)
@@ -343,6 +403,7 @@ void default_sweep(Mesh& m, int level) {
 // Coefficient pyramid: finest level from the canonical element order, coarse
 // levels as means of four children, FP32 copies, then the level-0 matrix.
 void set_coefficient(Mesh& m, const double* k_dev, cudaStream_t st) {
+  graphs_clear(m);
   if (!k_dev) {
     m.vark = false;
     std::vector<double> k0(m.nf, 1.0);

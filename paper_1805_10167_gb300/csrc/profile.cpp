@@ -59,6 +59,8 @@ void profile_begin(uint32_t mask, int level) {
   p.used = 0;
 }
 
+bool profiling_on() { return P().on; }
+
 void profile_end(int64_t* launches, double* ms) {
   Prof& p = P();
   for (int c = 0; c < HHG_K_COUNT; ++c) {

@@ -54,7 +54,9 @@ __device__ __forceinline__ void edge_row(const MeshTables& M, const LevelView& L
                                          const T* __restrict__ k, T& off, T& diag) {
   off = T(0);
   diag = T(0);
-  for (int s = 0; s < E.nfaces; ++s) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {   // unrolled: the record stays in registers
+    if (s >= E.nfaces) break;
     const EdgeSide sd = E.side[s];
     const FaceRec& F = M.faces[sd.face];
     const int r = sd.rot;
@@ -115,9 +117,9 @@ __device__ __forceinline__ void vertex_row_warp(const MeshTables& M, const Level
 // Gauss-Seidel update of free macro-vertex v by one warp, in place, with
 // the new value pushed to every copy (face corners, edge end slots).
 template <typename T, bool VARK>
-__device__ __forceinline__ void vertex_gs(const MeshTables& M, const LevelView& L, int v, int lane,
-                                          T* x, const T* __restrict__ b, const T* __restrict__ k) {
-  const VertRec V = M.verts[v];
+__device__ __forceinline__ void vertex_gs_rec(const MeshTables& M, const LevelView& L, const VertRec& V,
+                                              int v, int lane, T* x, const T* __restrict__ b,
+                                              const T* __restrict__ k) {
   if (V.dirichlet) return;
   T off, diag;
   vertex_row_warp<T, VARK>(M, L, V, lane, x, k, off, diag);
@@ -134,23 +136,39 @@ __device__ __forceinline__ void vertex_gs(const MeshTables& M, const LevelView& 
   }
 }
 
-// Gauss-Seidel update of edge-interior point t of free edge e, in place,
-// with the new value pushed to the edge's slot in each of its faces.
 template <typename T, bool VARK>
-__device__ __forceinline__ void edge_gs(const MeshTables& M, const LevelView& L, int e, int t, T* x,
-                                        const T* __restrict__ b, const T* __restrict__ k) {
-  const EdgeRec E = M.edges[e];
+__device__ __forceinline__ void vertex_gs(const MeshTables& M, const LevelView& L, int v, int lane,
+                                          T* x, const T* __restrict__ b, const T* __restrict__ k) {
+  const VertRec V = M.verts[v];
+  vertex_gs_rec<T, VARK>(M, L, V, v, lane, x, b, k);
+}
+
+// Gauss-Seidel update of edge-interior point t of free edge e (record E),
+// in place, with the new value pushed to the edge's slot in each of its faces.
+template <typename T, bool VARK>
+__device__ __forceinline__ void edge_gs_rec(const MeshTables& M, const LevelView& L, const EdgeRec& E,
+                                            int e, int t, T* x, const T* __restrict__ b,
+                                            const T* __restrict__ k) {
   if (E.dirichlet) return;
   T off, diag;
   edge_row<T, VARK>(M, L, E, t, x, k, off, diag);
   const int64_t s = L.e_off + (int64_t)e * L.ES + t;
   const T nv = (b[s] - off) / diag;
   x[s] = nv;
-  for (int q = 0; q < E.nfaces; ++q) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (q >= E.nfaces) break;
     const EdgeSide sd = E.side[q];
     const int p = sd.aligned ? t : L.N - t;
     x[L.f_off + (int64_t)sd.face * L.FS + rot_slot(L, sd.rot, p, 0)] = nv;
   }
+}
+
+template <typename T, bool VARK>
+__device__ __forceinline__ void edge_gs(const MeshTables& M, const LevelView& L, int e, int t, T* x,
+                                        const T* __restrict__ b, const T* __restrict__ k) {
+  const EdgeRec E = M.edges[e];
+  edge_gs_rec<T, VARK>(M, L, E, e, t, x, b, k);
 }
 
 }  // namespace hhg
