@@ -400,13 +400,17 @@ def run_ours(args):
     ms_profiled = max_over_ranks(e2.elapsed_time(e3))
 
     # dominant kernel: the three-colour face Gauss-Seidel sweep on level L
-    # (6 launches per V(3,3) cycle).  For k = 1 each interior point costs 7
-    # FP64 instructions (3 add, 1 mul, 3 fma) and 24 algorithmic bytes (read
-    # x and b, write x); the sweep is FP64-pipe bound on GB300.
+    # (6 launches per V(3,3) cycle).  For k = 1 each interior point costs 6
+    # FP64 instructions (3 add, 3 fma) when the strip kernel reads the scaled
+    # right-hand side b / A_pp (made once per cycle on this level), else 7
+    # (one more mul), and 24 algorithmic bytes (read x and b, write x); the
+    # sweep is FP64-pipe bound on GB300.
     gs_launches_L = (3 + 3) * args.steps
     gs_ms = kms[hhg.K_FACE_GS] / gs_launches_L
     pts = info.n_faces * (info.N - 1) * (info.N - 2) // 2
-    ops = 7.0 * pts
+    variant, split = g.sweep_config(L, hhg.F64)
+    ops_per_point = 6.0 if variant == hhg.SWEEP_STRIP and info.N > 64 else 7.0
+    ops = ops_per_point * pts
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peak = N_SM * FP64_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e9        # G FP64 instr/s at the sampled clock
     achieved = ops / (gs_ms / 1e3) / 1e9
@@ -417,7 +421,6 @@ def run_ours(args):
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    variant, split = g.sweep_config(L, hhg.F64)
     kname = ("k_gs_sweep<double> whole sweep (vertices, edge colours, register-strip faces, %d-row tasks)" % split
              if variant == hhg.SWEEP_STRIP
              else "k_face_gs3<double> shared-memory ring sweep, %d row blocks per face" % split)
@@ -428,7 +431,7 @@ def run_ours(args):
         traffic *= pts / 16760832.0
     roofline = {"bound": "alu", "kernel": f"{kname}, level {L}",
                 "achieved": achieved, "peak": peak, "unit": "G FP64-instr/s", "frac": achieved / peak,
-                "traffic": traffic, "ops_per_launch": ops, "ms_per_launch": gs_ms,
+                "traffic": traffic, "ops_per_launch": ops, "ops_per_point": ops_per_point, "ms_per_launch": gs_ms,
                 "peak_basis": f"{N_SM} SMs x {FP64_OPS_PER_CLK_SM} FP64 instr/clk x {sm_mhz:.0f} MHz (sampled)",
                 "hbm": {"achieved_gbs": bytes_alg / (gs_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
                         "frac": bytes_alg / (gs_ms / 1e3) / 1e9 / hbm_peak,

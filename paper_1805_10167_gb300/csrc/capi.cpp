@@ -105,8 +105,12 @@ namespace hhg {
 // the top level and to the library below it.  Ghost copies of x are
 // consistent on entry and on exit.  Smoothing sweeps alternate between x and
 // the level's workspace w; an odd sweep count ends with a copy back to x.
-void vcycle_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2,
-                int smoother, cudaStream_t st) {
+// bs_ready: the level's scaled right-hand side (b / A_pp on the face
+// interiors, read by the FP64 constant-stencil sweeps) was written along
+// with b by the restriction; on the level a cycle starts from it is
+// computed here from the caller's b.
+static void vcycle_level(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2,
+                         int smoother, bool bs_ready, cudaStream_t st) {
   if (l == 0) {
     coarse_solve(m, prec, b, x, st);
     return;
@@ -114,6 +118,11 @@ void vcycle_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1,
   const LevelData& ld = m.levels[l];
   const LevelData& lc = m.levels[l - 1];
   const bool learned = smoother == 1 && ld.lv.N >= 8;
+  const double* bs = nullptr;
+  if (!learned && nu1 + nu2 > 0 && uses_scaled_rhs(m, l, prec)) {
+    if (!bs_ready) scale_rhs(m, l, (const double*)b, ld.bs, st);
+    bs = ld.bs;
+  }
   void* cur = x;
   void* oth = ld.w[prec];
   for (int s = 0; s < nu1; ++s) {
@@ -121,25 +130,31 @@ void vcycle_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1,
       learned_step(m, l, prec, cur, b, st);
       continue;
     }
-    gs_sweep(m, l, prec, cur, oth, b, true, st);
+    gs_sweep(m, l, prec, cur, oth, b, true, st, bs);
     std::swap(cur, oth);
   }
   residual_op(m, l, prec, cur, b, ld.r[prec], nullptr, st);
-  restrict_op(m, l, prec, ld.r[prec], lc.b[prec], st);
+  const bool coarse_bs = smoother != 1 && uses_scaled_rhs(m, l - 1, prec);
+  restrict_op(m, l, prec, ld.r[prec], lc.b[prec], st, coarse_bs ? lc.bs : nullptr);
   zero_vec(m, l - 1, prec, lc.x[prec], st);
-  vcycle_run(m, l - 1, prec, lc.x[prec], lc.b[prec], nu1, nu2, smoother, st);
+  vcycle_level(m, l - 1, prec, lc.x[prec], lc.b[prec], nu1, nu2, smoother, coarse_bs, st);
   prolongate_add(m, l, prec, lc.x[prec], cur, st);
   for (int s = 0; s < nu2; ++s) {
     if (learned) {
       learned_step(m, l, prec, cur, b, st);
       continue;
     }
-    gs_sweep(m, l, prec, cur, oth, b, false, st);
+    gs_sweep(m, l, prec, cur, oth, b, false, st, bs);
     std::swap(cur, oth);
   }
   if (cur != x)
     check_cuda(cudaMemcpyAsync(x, cur, (size_t)ld.lv.len * (prec == 0 ? 8 : 4),
                                cudaMemcpyDeviceToDevice, st), "iterate copy");
+}
+
+void vcycle_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2,
+                int smoother, cudaStream_t st) {
+  vcycle_level(m, l, prec, x, b, nu1, nu2, smoother, false, st);
 }
 }  // namespace hhg
 

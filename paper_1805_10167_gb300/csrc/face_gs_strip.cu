@@ -57,10 +57,13 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 }
 
 // Colour phase on row t + DR at the lane's column M; U = t mod 6 places the
-// rows in the six-slot register ring (row r lives in slot r mod 6).
+// rows in the six-slot register ring (row r lives in slot r mod 6).  KM:
+// 0 = constant stencil, bv = b; 1 = variable coefficient; 2 = constant
+// stencil with bv = b / A_pp already (the product the KM = 0 form takes
+// first, computed once per right-hand side instead of once per sweep).
 // FAST: the caller knows that the row is in range and every column of the
 // window interior (no checks).
-template <typename T, bool DF, bool VARK, int DR, int M, int U, bool FAST = false>
+template <typename T, bool DF, int KM, int DR, int M, int U, bool FAST = false>
 __device__ __forceinline__ void strip_phase(typename Arith<T, DF>::V (&X)[6][3], typename Arith<T, DF>::V bv,
                                             int t, int rlo, int rhi, const StripArgs<T, DF>& a) {
   using A = Arith<T, DF>;
@@ -88,13 +91,13 @@ __device__ __forceinline__ void strip_phase(typename Arith<T, DF>::V (&X)[6][3],
   const V xn = X[sn][M], xs = X[ss][M];
   const int i = a.ic + M;
   const bool act = FAST || (i >= 1 && i + r <= a.N - 1);
-  if (!VARK) {
-    V acc = A::mul(bv, a.dinv);
+  if (KM != 1) {
+    V acc = KM == 2 ? bv : A::mul(bv, a.dinv);
     acc = A::fma(a.w2, A::add(xe, xw), acc);
     acc = A::fma(a.w1, A::add(xn, xs), acc);
     acc = A::fma(a.w0, A::add(xse, xnw), acc);
     if (act) X[sc][M] = acc;
-  } else if (act) {
+  } else if (act) {   // KM == 1
     const int p = r * a.S + i;
     const V u = A::in(__ldg(a.ku + p)), uw = A::in(__ldg(a.ku + p - 1)), us = A::in(__ldg(a.ku + p - a.S));
     const V ds = A::in(__ldg(a.kd + p - a.S)), dw = A::in(__ldg(a.kd + p - 1));
@@ -152,7 +155,7 @@ __device__ __forceinline__ void load_b_step(typename Arith<T, DF>::V (&Bv)[3], i
   Bv[2] = load_b(t - 2, C::mC, a);
 }
 
-template <typename T, bool DF, bool VARK, bool FWD, int U, bool FAST = false>
+template <typename T, bool DF, int KM, bool FWD, int U, bool FAST = false>
 __device__ __forceinline__ void strip_step(typename Arith<T, DF>::V (&X)[6][3], typename Arith<T, DF>::V (&Bq)[2][3],
                                            int t, int rmax, const StripArgs<T, DF>& a) {
   using A = Arith<T, DF>;
@@ -170,9 +173,9 @@ __device__ __forceinline__ void strip_step(typename Arith<T, DF>::V (&X)[6][3], 
       prefetch_l2(a.bg + (rp * a.S + a.ic));
     }
   }
-  strip_phase<T, DF, VARK, 0, C::mA, U, FAST>(X, Bv[0], t, a.j0 - 2, a.j1 + 1, a);
-  strip_phase<T, DF, VARK, -1, C::mB, U, FAST>(X, Bv[1], t, a.j0 - 1, a.j1, a);
-  strip_phase<T, DF, VARK, -2, C::mC, U, FAST>(X, Bv[2], t, a.j0, a.j1 - 1, a);
+  strip_phase<T, DF, KM, 0, C::mA, U, FAST>(X, Bv[0], t, a.j0 - 2, a.j1 + 1, a);
+  strip_phase<T, DF, KM, -1, C::mB, U, FAST>(X, Bv[1], t, a.j0 - 1, a.j1, a);
+  strip_phase<T, DF, KM, -2, C::mC, U, FAST>(X, Bv[2], t, a.j0, a.j1 - 1, a);
   // row t - 2 is final
   const int r = t - 2;
   if (FAST) {   // interior window: the stored columns are the strip's own, every one interior
@@ -200,7 +203,7 @@ __device__ __forceinline__ void strip_step(typename Arith<T, DF>::V (&X)[6][3], 
 }
 
 // The wavefront of one strip task from step t0 (a multiple of 6) to tend.
-template <typename T, bool DF, bool VARK, bool FWD>
+template <typename T, bool DF, int KM, bool FWD>
 __device__ __forceinline__ void strip_run(int t0, int tend, int rmax, const StripArgs<T, DF>& a) {
   using V = typename Arith<T, DF>::V;
   V X[6][3];
@@ -214,47 +217,47 @@ __device__ __forceinline__ void strip_run(int t0, int tend, int rmax, const Stri
   load_b_step<T, DF, FWD, 0>(Bq[0], t0, a);
   load_b_step<T, DF, FWD, 1>(Bq[1], t0 + 1, a);
   int t = t0;
-  if constexpr (sizeof(T) == 4 && !DF && !VARK) {   // (with variable k the doubled code overflows the instruction cache)
+  if constexpr (sizeof(T) == 4 && !DF && KM != 1) {   // (with variable k the doubled code overflows the instruction cache)
     // Steps t in [max(j0 + 2, 3), j1 + 1] with the whole window interior on
     // rows t - 2 .. t (strips s >= 1, ws + 95 <= N - 1 - t) need no checks:
     // run them as whole groups of six in the unchecked form.
     const int flo = max(a.j0 + 2, 3), fhi = min(a.j1 + 1, a.N - 1 - (a.ws + 95));
     if (a.ws >= 1 && flo <= fhi) {
       for (; t < flo; t += 6) {   // checked groups up to the first group that starts at or after flo
-        strip_step<T, DF, VARK, FWD, 0>(X, Bq, t, rmax, a);
-        strip_step<T, DF, VARK, FWD, 1>(X, Bq, t + 1, rmax, a);
-        strip_step<T, DF, VARK, FWD, 2>(X, Bq, t + 2, rmax, a);
-        strip_step<T, DF, VARK, FWD, 3>(X, Bq, t + 3, rmax, a);
-        strip_step<T, DF, VARK, FWD, 4>(X, Bq, t + 4, rmax, a);
-        strip_step<T, DF, VARK, FWD, 5>(X, Bq, t + 5, rmax, a);
+        strip_step<T, DF, KM, FWD, 0>(X, Bq, t, rmax, a);
+        strip_step<T, DF, KM, FWD, 1>(X, Bq, t + 1, rmax, a);
+        strip_step<T, DF, KM, FWD, 2>(X, Bq, t + 2, rmax, a);
+        strip_step<T, DF, KM, FWD, 3>(X, Bq, t + 3, rmax, a);
+        strip_step<T, DF, KM, FWD, 4>(X, Bq, t + 4, rmax, a);
+        strip_step<T, DF, KM, FWD, 5>(X, Bq, t + 5, rmax, a);
       }
       for (; t + 5 <= fhi; t += 6) {
-        strip_step<T, DF, VARK, FWD, 0, true>(X, Bq, t, rmax, a);
-        strip_step<T, DF, VARK, FWD, 1, true>(X, Bq, t + 1, rmax, a);
-        strip_step<T, DF, VARK, FWD, 2, true>(X, Bq, t + 2, rmax, a);
-        strip_step<T, DF, VARK, FWD, 3, true>(X, Bq, t + 3, rmax, a);
-        strip_step<T, DF, VARK, FWD, 4, true>(X, Bq, t + 4, rmax, a);
-        strip_step<T, DF, VARK, FWD, 5, true>(X, Bq, t + 5, rmax, a);
+        strip_step<T, DF, KM, FWD, 0, true>(X, Bq, t, rmax, a);
+        strip_step<T, DF, KM, FWD, 1, true>(X, Bq, t + 1, rmax, a);
+        strip_step<T, DF, KM, FWD, 2, true>(X, Bq, t + 2, rmax, a);
+        strip_step<T, DF, KM, FWD, 3, true>(X, Bq, t + 3, rmax, a);
+        strip_step<T, DF, KM, FWD, 4, true>(X, Bq, t + 4, rmax, a);
+        strip_step<T, DF, KM, FWD, 5, true>(X, Bq, t + 5, rmax, a);
       }
     }
   }
   for (; t <= tend; t += 6) {
-    strip_step<T, DF, VARK, FWD, 0>(X, Bq, t, rmax, a);
+    strip_step<T, DF, KM, FWD, 0>(X, Bq, t, rmax, a);
     if (t + 1 > tend) break;
-    strip_step<T, DF, VARK, FWD, 1>(X, Bq, t + 1, rmax, a);
+    strip_step<T, DF, KM, FWD, 1>(X, Bq, t + 1, rmax, a);
     if (t + 2 > tend) break;
-    strip_step<T, DF, VARK, FWD, 2>(X, Bq, t + 2, rmax, a);
+    strip_step<T, DF, KM, FWD, 2>(X, Bq, t + 2, rmax, a);
     if (t + 3 > tend) break;
-    strip_step<T, DF, VARK, FWD, 3>(X, Bq, t + 3, rmax, a);
+    strip_step<T, DF, KM, FWD, 3>(X, Bq, t + 3, rmax, a);
     if (t + 4 > tend) break;
-    strip_step<T, DF, VARK, FWD, 4>(X, Bq, t + 4, rmax, a);
+    strip_step<T, DF, KM, FWD, 4>(X, Bq, t + 4, rmax, a);
     if (t + 5 > tend) break;
-    strip_step<T, DF, VARK, FWD, 5>(X, Bq, t + 5, rmax, a);
+    strip_step<T, DF, KM, FWD, 5>(X, Bq, t + 5, rmax, a);
   }
 }
 
 // One strip task (face, strip, j0, j1) by one warp.
-template <typename T, bool DF, bool VARK, bool FWD>
+template <typename T, bool DF, int KM, bool FWD>
 __device__ __forceinline__ void strip_task(const MeshTables& M, const LevelView& L, const T* xin, T* xout,
                                            const T* __restrict__ b, const T* __restrict__ k, int4 tk,
                                            int lane) {
@@ -275,8 +278,8 @@ __device__ __forceinline__ void strip_task(const MeshTables& M, const LevelView&
   a.xg = xin + fb;
   a.xo = xout + fb;
   a.bg = b + fb;
-  a.ku = VARK ? k + (int64_t)f * L.FS : nullptr;
-  a.kd = VARK ? k + (int64_t)(M.nf + f) * L.FS : nullptr;
+  a.ku = KM == 1 ? k + (int64_t)f * L.FS : nullptr;
+  a.kd = KM == 1 ? k + (int64_t)(M.nf + f) * L.FS : nullptr;
   const FaceRec& F = M.faces[f];
   a.c0 = (T)F.cot[0];
   a.c1 = (T)F.cot[1];
@@ -291,7 +294,7 @@ __device__ __forceinline__ void strip_task(const MeshTables& M, const LevelView&
   // static r mod 6 (the steps before j0 - 2 only load)
   const int first = a.j0 - 2;
   const int t0 = first >= 0 ? first - first % 6 : -(((-first) + 5) / 6) * 6;
-  strip_run<T, DF, VARK, FWD>(t0, a.j1 + 1, rmax, a);
+  strip_run<T, DF, KM, FWD>(t0, a.j1 + 1, rmax, a);
 }
 
 // A whole face of a small level (N <= kSmallN) by one CTA in shared memory:
@@ -442,10 +445,10 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, GridBar& g, int* err
 // updated in place, on x_in going forward and on x_out going backward; the
 // faces go from x_in to x_out, and the vertex/edge block of x_in is copied
 // to x_out along with them.  Grid barriers separate the phases.
-template <typename T, bool DF, bool VARK, bool FWD>
+template <typename T, bool DF, bool VARK, bool FWD, bool BS>
 __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
     k_gs_sweep(MeshTables M, LevelView L, T* xin, T* xout, const T* __restrict__ b,
-               const T* __restrict__ k, const int4* __restrict__ tasks, int ntasks,
+               const T* __restrict__ bsf, const T* __restrict__ k, const int4* __restrict__ tasks, int ntasks,
                const int* __restrict__ clist, const __grid_constant__ EdgeColours cs, int small,
                const unsigned short* __restrict__ spts, int4 sptr, unsigned* bar, int* err) {
   extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -509,7 +512,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
         if (lane == 0) w = atomicAdd(ticket, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= (unsigned)ntasks) break;
-        strip_task<T, DF, VARK, FWD>(M, L, xin, xout, b, k, tasks[w], lane);
+        strip_task<T, DF, VARK ? 1 : (BS ? 2 : 0), FWD>(M, L, xin, xout, BS ? bsf : b, k, tasks[w], lane);
       }
       if (lane == 0) {
         __threadfence();
@@ -583,8 +586,8 @@ std::vector<int> strip_tasks(int nf, int N, int rows_per_task) {
   return out;
 }
 
-template <typename T, bool DF, bool VARK, bool FWD>
-static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b, const T* k,
+template <typename T, bool DF, bool VARK, bool FWD, bool BS>
+static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b, const T* bs, const T* k,
                            cudaStream_t st) {
   const LevelData& ld = m.levels[level];
   const SweepCfg& c = ld.sweep[sizeof(T) == 8 ? 0 : 1];
@@ -596,14 +599,14 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
   const int lvl = std::min(level, 31);
   static size_t configured = 48 * 1024;   // largest dynamic shared memory enabled for this instance
   if (smem > configured) {
-    check_cuda(cudaFuncSetAttribute(k_gs_sweep<T, DF, VARK, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    check_cuda(cudaFuncSetAttribute(k_gs_sweep<T, DF, VARK, FWD, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem),
                "whole sweep shared memory");
     configured = smem;
   }
   if (resident_at[lvl] == 0) {
     int r = 0;
-    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_gs_sweep<T, DF, VARK, FWD>, kStripWarps * 32, smem),
+    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_gs_sweep<T, DF, VARK, FWD, BS>, kStripWarps * 32, smem),
                "sweep occupancy");
     if (r < 1) throw std::runtime_error("whole-sweep kernel cannot be resident");
     resident_at[lvl] = r;
@@ -632,7 +635,7 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  check_cuda(cudaLaunchKernelEx(&cfg, k_gs_sweep<T, DF, VARK, FWD>, m.tab, ld.lv, xin, xout, b, k,
+  check_cuda(cudaLaunchKernelEx(&cfg, k_gs_sweep<T, DF, VARK, FWD, BS>, m.tab, ld.lv, xin, xout, b, bs, k,
                                 (const int4*)c.tasks, c.ntasks, (const int*)ld.colour_list, cs, small,
                                 (const unsigned short*)ld.small_pts,
                                 make_int4(ld.small_ptr[0], ld.small_ptr[1], ld.small_ptr[2], ld.small_ptr[3]),
@@ -640,41 +643,38 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
              "whole sweep launch");
 }
 
+template <typename T, bool DF>
+static void sweep_dispatch(const Mesh& m, int level, T* xi, T* xo, const T* b, const T* bs, const T* k,
+                           bool forward, cudaStream_t st) {
+  if (m.vark) {
+    if (forward) launch_sweep_t<T, DF, true, true, false>(m, level, xi, xo, b, nullptr, k, st);
+    else launch_sweep_t<T, DF, true, false, false>(m, level, xi, xo, b, nullptr, k, st);
+  } else if (bs) {
+    if constexpr (sizeof(T) == 8) {   // FP64 only
+      if (forward) launch_sweep_t<T, DF, false, true, true>(m, level, xi, xo, b, bs, nullptr, st);
+      else launch_sweep_t<T, DF, false, false, true>(m, level, xi, xo, b, bs, nullptr, st);
+    }
+  } else {
+    if (forward) launch_sweep_t<T, DF, false, true, false>(m, level, xi, xo, b, nullptr, nullptr, st);
+    else launch_sweep_t<T, DF, false, false, false>(m, level, xi, xo, b, nullptr, nullptr, st);
+  }
+}
+
+// bs: the face part of b / A_pp (scale_rhs) for the strip kernel of an FP64
+// level with k = 1 and N > kSmallN, or nullptr
 void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
-                    bool forward, cudaStream_t st) {
+                    const void* bs, bool forward, cudaStream_t st) {
   const LevelData& ld = m.levels[level];
   if (prec == 0) {
     const double* k = m.vark ? (const double*)ld.k[0] : nullptr;
-    auto* xi = (double*)xin;
-    auto* xo = (double*)xout;
-    auto* bb = (const double*)b;
-    if (m.fp64_df) {
-      if (m.vark) {
-        if (forward) launch_sweep_t<double, true, true, true>(m, level, xi, xo, bb, k, st);
-        else launch_sweep_t<double, true, true, false>(m, level, xi, xo, bb, k, st);
-      } else {
-        if (forward) launch_sweep_t<double, true, false, true>(m, level, xi, xo, bb, k, st);
-        else launch_sweep_t<double, true, false, false>(m, level, xi, xo, bb, k, st);
-      }
-    } else if (m.vark) {
-      if (forward) launch_sweep_t<double, false, true, true>(m, level, xi, xo, bb, k, st);
-      else launch_sweep_t<double, false, true, false>(m, level, xi, xo, bb, k, st);
-    } else {
-      if (forward) launch_sweep_t<double, false, false, true>(m, level, xi, xo, bb, k, st);
-      else launch_sweep_t<double, false, false, false>(m, level, xi, xo, bb, k, st);
-    }
+    const double* bsd = (!m.vark && ld.lv.N > kSmallN) ? (const double*)bs : nullptr;
+    if (m.fp64_df)
+      sweep_dispatch<double, true>(m, level, (double*)xin, (double*)xout, (const double*)b, bsd, k, forward, st);
+    else
+      sweep_dispatch<double, false>(m, level, (double*)xin, (double*)xout, (const double*)b, bsd, k, forward, st);
   } else {
     const float* k = m.vark ? (const float*)ld.k[1] : nullptr;
-    auto* xi = (float*)xin;
-    auto* xo = (float*)xout;
-    auto* bb = (const float*)b;
-    if (m.vark) {
-      if (forward) launch_sweep_t<float, false, true, true>(m, level, xi, xo, bb, k, st);
-      else launch_sweep_t<float, false, true, false>(m, level, xi, xo, bb, k, st);
-    } else {
-      if (forward) launch_sweep_t<float, false, false, true>(m, level, xi, xo, bb, k, st);
-      else launch_sweep_t<float, false, false, false>(m, level, xi, xo, bb, k, st);
-    }
+    sweep_dispatch<float, false>(m, level, (float*)xin, (float*)xout, (const float*)b, nullptr, k, forward, st);
   }
 }
 

@@ -199,6 +199,7 @@ struct LevelData {
   int n_row_tasks = 0;
   // N <= kSmallN: the interior points of a face ordered by colour (i + 2j) mod 3,
   // as slots j * S + i; colour c is [small_ptr[c], small_ptr[c + 1])
+  double* bs = nullptr;             // FP64 b / A_pp on the face interiors (levels with N > kSmallN)
   unsigned short* small_pts = nullptr;
   int small_ptr[4] = {0, 0, 0, 0};
 };
@@ -257,8 +258,10 @@ void residual_op(const Mesh& m, int level, int prec, const void* x, const void* 
                  double* norm2_dev, cudaStream_t st);
 // One Gauss-Seidel sweep from xin to xout (xin's vertex and edge values are
 // updated in place on the way; xout receives the complete new iterate).
+// bs (optional, FP64 levels with k = 1): the face part of b / A_pp
+// (scale_rhs), read by the register-strip face kernel instead of b.
 void gs_sweep(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
-              bool forward, cudaStream_t st);
+              bool forward, cudaStream_t st, const void* bs = nullptr);
 void face_gs3_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
                      bool forward, cudaStream_t st);
 std::vector<int> face_tasks(int nf, int N, int tasks_per_face);
@@ -268,12 +271,17 @@ void face_ring_launch(const Mesh& m, int level, int prec, const void* xin, void*
 // One whole Gauss-Seidel sweep (vertices, edge colours, faces) in one
 // cooperative launch (the STRIP variant).
 void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
-                    bool forward, cudaStream_t st);
+                    const void* bs, bool forward, cudaStream_t st);
 size_t face_gs_smem(const LevelView& L, int prec);
 void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,
                   void* work, cudaStream_t st);
+// bs_coarse (optional, FP64): also writes b_coarse / A_pp on the coarse face interiors
 void restrict_op(const Mesh& m, int fine_level, int prec, const void* r_fine, void* b_coarse,
-                 cudaStream_t st);
+                 cudaStream_t st, double* bs_coarse = nullptr);
+// bs = b / A_pp on the face interiors of an FP64 level with k = 1
+void scale_rhs(const Mesh& m, int level, const double* b, double* bs, cudaStream_t st);
+// whether the sweeps of `level` in precision `prec` read a scaled right-hand side
+bool uses_scaled_rhs(const Mesh& m, int level, int prec);
 void prolongate_add(const Mesh& m, int fine_level, int prec, const void* x_coarse, void* x_fine,
                     cudaStream_t st);
 void coarse_solve(const Mesh& m, int prec, const void* b0, void* x0, cudaStream_t st);

@@ -314,7 +314,7 @@ __global__ void k_restrict_ve(MeshTables M, LevelView Lf, LevelView Lc, const T*
 // (2I, 2J) and half of its six lattice neighbours.
 template <typename T>
 __global__ void k_restrict_face(MeshTables M, LevelView Lf, LevelView Lc,
-                                const T* __restrict__ rf, T* __restrict__ bc) {
+                                const T* __restrict__ rf, T* __restrict__ bc, T* __restrict__ bsc) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -325,11 +325,15 @@ __global__ void k_restrict_face(MeshTables M, LevelView Lf, LevelView Lc,
     const int f = (int)(task / rows);
     const int J = (int)(task - (int64_t)f * rows) + 1;
     const T* r = rf + Lf.f_off + (int64_t)f * Lf.FS;
-    T* o = bc + Lc.f_off + (int64_t)f * Lc.FS + (int64_t)J * Lc.S;
+    const int64_t ob = Lc.f_off + (int64_t)f * Lc.FS + (int64_t)J * Lc.S;
+    T* o = bc + ob;
+    const T dinv = bsc ? (T)M.faces[f].dinv : T(0);
     for (int I = 1 + lane; I < Lc.N - J; I += 32) {
       const int64_t p = (int64_t)(2 * J) * S + 2 * I;
-      o[I] = r[p] + T(0.5) * ((r[p + 1] + r[p - 1]) + (r[p + S] + r[p - S]) +
-                              (r[p + 1 - S] + r[p - 1 + S]));
+      const T v = r[p] + T(0.5) * ((r[p + 1] + r[p - 1]) + (r[p + S] + r[p - S]) +
+                                   (r[p + 1 - S] + r[p - 1 + S]));
+      o[I] = v;
+      if (bsc) bsc[ob + I] = v * dinv;
     }
   }
 }
@@ -750,11 +754,11 @@ void ve_gs(const Mesh& m, int level, int prec, void* x, const void* b, bool forw
 // face sweep first, then edge colours and vertices in place on xout.  With
 // the STRIP face kernel all of it is one cooperative launch.
 void gs_sweep(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
-              bool forward, cudaStream_t st) {
+              bool forward, cudaStream_t st, const void* bs) {
   const LevelView& L = m.levels[level].lv;
   if (m.levels[level].sweep[prec].variant == SWEEP_STRIP) {   // the whole sweep in one launch
     LaunchScope ls(HHG_K_FACE_GS, level, st);
-    gs_sweep_fused(m, level, prec, xin, xout, b, forward, st);
+    gs_sweep_fused(m, level, prec, xin, xout, b, bs, forward, st);
     return;
   }
   const size_t prefix = (size_t)L.f_off * (prec == 0 ? 8 : 4);
@@ -778,21 +782,50 @@ void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, do
 }
 
 template <typename T>
-static void restrict_t(const Mesh& m, int lf, const T* rf, T* bc, cudaStream_t st) {
+static void restrict_t(const Mesh& m, int lf, const T* rf, T* bc, cudaStream_t st, T* bsc) {
   const LevelView& Lf = m.levels[lf].lv;
   const LevelView& Lc = m.levels[lf - 1].lv;
   const int64_t nve = m.nv + (Lc.N >= 2 ? (int64_t)m.ne * (Lc.N - 1) : 0);
   HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "restrict ve", k_restrict_ve<T><<<blocks_for(nve, kThreads, 1024), kThreads, 0, st>>>(m.tab, Lf, Lc, rf, bc));
   if (Lc.N >= 3) {
     const int64_t ntask = (int64_t)m.nf * (Lc.N - 2);
-    HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "restrict face", k_restrict_face<T><<<blocks_for(ntask, kWarps, kMaxBlocksF), kThreads, 0, st>>>(m.tab, Lf, Lc, rf, bc));
+    HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "restrict face", k_restrict_face<T><<<blocks_for(ntask, kWarps, kMaxBlocksF), kThreads, 0, st>>>(m.tab, Lf, Lc, rf, bc, bsc));
   }
 }
 
 void restrict_op(const Mesh& m, int fine_level, int prec, const void* r_fine, void* b_coarse,
-                 cudaStream_t st) {
-  if (prec == 0) restrict_t(m, fine_level, (const double*)r_fine, (double*)b_coarse, st);
-  else restrict_t(m, fine_level, (const float*)r_fine, (float*)b_coarse, st);
+                 cudaStream_t st, double* bs_coarse) {
+  if (prec == 0) restrict_t(m, fine_level, (const double*)r_fine, (double*)b_coarse, st, bs_coarse);
+  else restrict_t<float>(m, fine_level, (const float*)r_fine, (float*)b_coarse, st, nullptr);
+}
+
+// b / A_pp on the face interiors (one warp per face row), the first product
+// of the constant-stencil Gauss-Seidel update, once per right-hand side
+__global__ void k_scale_rhs(MeshTables M, LevelView L, const double* __restrict__ b, double* __restrict__ bs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int rows = L.N - 2;
+  const int64_t ntask = (int64_t)M.nf * rows;
+  for (int64_t task = warp; task < ntask; task += nwarps) {
+    const int f = (int)(task / rows);
+    const int j = (int)(task - (int64_t)f * rows) + 1;
+    const double dinv = M.faces[f].dinv;
+    const int64_t o = L.f_off + (int64_t)f * L.FS + (int64_t)j * L.S;
+    for (int i = 1 + lane; i < L.N - j; i += 32) bs[o + i] = b[o + i] * dinv;
+  }
+}
+
+bool uses_scaled_rhs(const Mesh& m, int level, int prec) {
+  const LevelData& ld = m.levels[level];
+  return prec == 0 && !m.vark && ld.bs != nullptr && ld.sweep[0].variant == SWEEP_STRIP;
+}
+
+void scale_rhs(const Mesh& m, int level, const double* b, double* bs, cudaStream_t st) {
+  const LevelView& L = m.levels[level].lv;
+  const int64_t ntask = (int64_t)m.nf * (L.N - 2);
+  if (ntask <= 0) return;
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "scale rhs", k_scale_rhs<<<blocks_for(ntask, kWarps, kMaxBlocksF), kThreads, 0, st>>>(m.tab, L, b, bs));
 }
 
 template <typename T>

@@ -328,6 +328,7 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
         ld.r[p] = dev_alloc(m, bytes);
         ld.w[p] = dev_alloc(m, bytes);
       }
+      if (ld.lv.N > kSmallN) ld.bs = (double*)dev_alloc(m, (size_t)ld.lv.len * sizeof(double));
       default_sweep(m, l);
       if (ld.lv.N <= kSmallN) {
         const int N = ld.lv.N, S = (int)ld.lv.S;

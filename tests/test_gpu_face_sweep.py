@@ -77,3 +77,31 @@ def test_tuner_choice_is_a_valid_config(pairs):
     for l in range(4, 9):
         v, p = P.g.sweep_config(l, hhg.F32)
         assert v in (hhg.SWEEP_RING, hhg.SWEEP_STRIP) and p >= 1
+
+
+@pytest.mark.parametrize("name,L", [("square", 8), ("random5", 7)])
+@pytest.mark.parametrize("vark", [False, True])
+@pytest.mark.parametrize("split", [(1, 16), (1, 64), (0, 3)])
+def test_vcycle_with_scaled_right_hand_sides_matches_oracle(pairs, name, L, vark, split):
+    """Inside a V-cycle the FP64 strip sweeps of levels with N > 64 and k = 1
+    read b / A_pp computed once per right-hand side (from the caller's b on
+    the top level, by the restriction below it); the cycle must still give
+    the oracle's to 1e-12, with every split on levels L - 1 and L."""
+    P = pairs(name, L, vark)
+    hhg = P.hhg
+    old = [P.g.sweep_config(l) for l in (L - 1, L)]
+    try:
+        for l in (L - 1, L):
+            P.g.sweep_config(l, hhg.F64, *split)
+        rng = np.random.default_rng(11)
+        x0, b = rng.standard_normal(P.H.levels[L].n), rng.standard_normal(P.H.levels[L].n)
+        x = P.to_dev(L, x0)
+        bd = P.to_dev(L, b)
+        want = x0.copy()
+        for call in range(3):   # the third call replays a captured graph
+            P.g.vcycle(L, x, bd, nu1=2, nu2=1)
+            want = mg.vcycle(P.H, L, want, b, 2, 1)
+            assert rel_err(P.from_dev(L, x), want) <= FP64_TOL, call
+    finally:
+        for l, c in zip((L - 1, L), old):
+            P.g.sweep_config(l, hhg.F64, *c)
