@@ -43,7 +43,7 @@ N_SM = 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one level-9 launch of the
 # FP64 face sweep (annulus, 128 faces), per (kernel variant, split), from the
 # ncu captures summarised under profiles/; None until captured
-TRAFFIC_L9 = {(1, 32): 390.379008e6 + 120.408576e6}   # k_gs_sweep<double>, default split
+TRAFFIC_L9 = {(1, 32): 391.005440e6 + 113.611264e6}   # k_gs_sweep<double, 0, 0, 1, 1>, default split
 
 
 # ------------------------------------------------------------------ ranks
@@ -515,7 +515,8 @@ def run_ours(args):
 def run_sweep_case(args):
     """Four forward Gauss-Seidel sweeps of level --level of the 128-face
     annulus in --prec with the default kernel configuration (inputs, output
-    and workspace above the 129 MB L2 from level 9 on)."""
+    and workspace above the 129 MB L2 from level 9 on); in FP64 they read
+    b / A_pp made by one scaling pass first, as inside a V-cycle."""
     import torch
     from paper_1805_10167_gb300 import hhg, inputs
     xy, tri = inputs.annulus_mesh(32, 2)

@@ -210,7 +210,10 @@ hhg_status hhg_prolongate_add(hhg_mesh mesh, int32_t fine_level, hhg_prec prec,
 
 /* `sweeps` smoothing sweeps in place on x (Sec. 4.3; multi-colour order: free
  * macro-vertices, edge-interior colours, face colours (i + 2j) mod 3 = 0,1,2;
- * HHG_GS_BWD runs the exact reverse).  omega is used by HHG_JACOBI only. */
+ * HHG_GS_BWD runs the exact reverse).  omega is used by HHG_JACOBI only.
+ * With two or more FP64 Gauss-Seidel sweeps on a level with N > 64 and
+ * k = 1, b / A_pp is formed once on the face interiors and read by every
+ * sweep (the same products, so the same results).  Asynchronous. */
 hhg_status hhg_smooth(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, const void* b,
                       int32_t smoother, int32_t sweeps, double omega, void* stream);
 

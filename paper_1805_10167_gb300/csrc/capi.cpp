@@ -354,13 +354,19 @@ hhg_status hhg_smooth(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
     if (smoother < HHG_GS_FWD || smoother > HHG_JACOBI) throw ArgError("bad smoother");
     hhg::ghost_fill(m, level, prec, x, S(stream));
     const hhg::LevelData& ld = m.levels[level];
+    // two or more Gauss-Seidel sweeps: b / A_pp once, read by every sweep
+    const double* bs = nullptr;
+    if (smoother != HHG_JACOBI && sweeps >= 2 && hhg::uses_scaled_rhs(m, level, prec)) {
+      hhg::scale_rhs(m, level, (const double*)b, ld.bs, S(stream));
+      bs = ld.bs;
+    }
     void* cur = x;
     void* oth = ld.w[prec];
     for (int s = 0; s < sweeps; ++s) {
       if (smoother == HHG_JACOBI) {
         hhg::jacobi_sweep(m, level, prec, cur, b, omega, ld.r[prec], S(stream));
       } else {
-        hhg::gs_sweep(m, level, prec, cur, oth, b, smoother == HHG_GS_FWD, S(stream));
+        hhg::gs_sweep(m, level, prec, cur, oth, b, smoother == HHG_GS_FWD, S(stream), bs);
         std::swap(cur, oth);
       }
     }

@@ -812,7 +812,15 @@ __global__ void k_scale_rhs(MeshTables M, LevelView L, const double* __restrict_
     const int j = (int)(task - (int64_t)f * rows) + 1;
     const double dinv = M.faces[f].dinv;
     const int64_t o = L.f_off + (int64_t)f * L.FS + (int64_t)j * L.S;
-    for (int i = 1 + lane; i < L.N - j; i += 32) bs[o + i] = b[o + i] * dinv;
+    const int end = L.N - j;
+    for (int i0 = 1 + lane; i0 < end; i0 += 128) {   // four loads in flight per lane
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = i0 + 32 * u < end ? b[o + i0 + 32 * u] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + 32 * u < end) bs[o + i0 + 32 * u] = v[u] * dinv;
+    }
   }
 }
 

@@ -47,10 +47,13 @@ def test_face_sweep_kernels_match_oracle(pairs, name, L, vark, split):
         x0 = rng.standard_normal(P.H.levels[l].n)
         b = rng.standard_normal(P.H.levels[l].n)
         for fwd in (True, False):
-            want = x0.copy()
-            for _ in range(2):
-                mg.gs_sweep(P.H, l, want, b, forward=fwd)
+            # one FP64 sweep reads b, two or more read b / A_pp (one scaling pass)
+            want1 = mg.gs_sweep(P.H, l, x0.copy(), b, forward=fwd)
+            want = mg.gs_sweep(P.H, l, want1.copy(), b, forward=fwd)
             mode = hhg.GS_FWD if fwd else hhg.GS_BWD
+            x = P.to_dev(l, x0)
+            P.g.smooth(l, x, P.to_dev(l, b), mode, sweeps=1)
+            assert rel_err(P.from_dev(l, x), want1) <= FP64_TOL, (l, fwd, "f64, 1 sweep")
             x = P.to_dev(l, x0)
             P.g.smooth(l, x, P.to_dev(l, b), mode, sweeps=2)
             assert rel_err(P.from_dev(l, x), want) <= FP64_TOL, (l, fwd, "f64")
