@@ -85,9 +85,6 @@ static void colour_edges(const Mesh& m, int N, std::vector<int>& ptr, std::vecto
   ptr[ncol] = (int)list.size();
 }
 
-// Dense level-0 matrices, one per block, over its free macro-vertices (level
-// 0 has no edge or face interiors).  k0[f] = coefficient of face f's single
-// micro-triangle.
 // Inverse of the symmetric positive definite n x n matrix A (row-major) by
 // its Cholesky factor A = L L^T: column c of the inverse solves L L^T y = e_c.
 // Returns false when a pivot is not positive (A not positive definite).
@@ -122,6 +119,9 @@ static bool spd_inverse(const double* A, int n, double* inv) {
   return true;
 }
 
+// Dense level-0 matrices, one per block, over its free macro-vertices (level
+// 0 has no edge or face interiors), and their inverses when every block is
+// small enough.  k0[f] = coefficient of face f's single micro-triangle.
 static void assemble_level0(Mesh& m, const std::vector<double>& k0) {
   std::vector<int> map(m.nv, -1), free0;
   std::vector<double> A;
@@ -395,10 +395,13 @@ void set_sweep(Mesh& m, int level, int prec, int variant, int param) {
   c.param = param;
 }
 
-// Untuned default: register strips with row blocks of about 32 rows (the
-// fastest split at levels 7-10 in both precisions on the 128-face annulus).
+// Untuned default: register strips with row blocks of about 32 rows, 12 at
+// N = 128 (the fastest or within 1 % of it at levels 7-10 in both precisions
+// on the 128-face annulus; fewer rows at N = 128 give enough tasks to fill
+// the GPU).
 void default_sweep(Mesh& m, int level) {
-  for (int p = 0; p < 2; ++p) set_sweep(m, level, p, SWEEP_STRIP, 32);
+  const int rows = m.levels[level].lv.N <= 128 ? 12 : 32;
+  for (int p = 0; p < 2; ++p) set_sweep(m, level, p, SWEEP_STRIP, rows);
 }
 
 // Coefficient pyramid: finest level from the canonical element order, coarse
