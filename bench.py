@@ -263,7 +263,7 @@ def timed_solve(g, level, b, st, **kw):
     it = rep["iterations"]
     return {"seconds": dt, "iterations": it, "rel_residual": rep["r_final"] / rep["r0"],
             "factor_per_iteration": (rep["r_final"] / rep["r0"]) ** (1.0 / max(it, 1)),
-            "smoother_used": ["gs", "learned"][rep.get("smoother_used", 0)],
+            "smoother_used": ["gs", "learned", "learned_gs"][rep.get("smoother_used", 0)],
             "judge": [rep.get("judge_learned", 0.0), rep.get("judge_gs", 0.0)]}
 
 
@@ -287,7 +287,8 @@ def run_vark(args, dev, st):
 def run_learned(args, dev, st):
     """Learned smoother on the variable-coefficient annulus at level 9: train
     on FP64 V-cycle residual/error crops, then FGMRES(20) preconditioned by
-    one FP32 V(1,1) with the learned smoother (judge with fallback) or with
+    one FP32 V(1,1) with the learned smoother alone, with a Gauss-Seidel sweep
+    followed by the learned step (each judged, with fallback) or with
     Gauss-Seidel, against plain FP64 V(3,3) cycles."""
     from paper_1805_10167_gb300 import hhg
     L = max(6, args.level - 1)
@@ -301,6 +302,8 @@ def run_learned(args, dev, st):
            "loss_first_last": [float(hist[0]), float(hist[-1])] if len(hist) else None,
            "fgmres_learned": timed_solve(g, L, b, st, mode=hhg.SOLVE_FGMRES, nu1=1, nu2=1,
                                          smoother=hhg.SMOOTH_LEARNED),
+           "fgmres_learned_gs": timed_solve(g, L, b, st, mode=hhg.SOLVE_FGMRES, nu1=1, nu2=1,
+                                            smoother=hhg.SMOOTH_LEARNED_GS),
            "fgmres_gs": timed_solve(g, L, b, st, mode=hhg.SOLVE_FGMRES, nu1=1, nu2=1,
                                     smoother=hhg.SMOOTH_GS),
            "fp64_mg": timed_solve(g, L, b, st, mode=hhg.SOLVE_MG)}

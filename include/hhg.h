@@ -100,9 +100,12 @@ typedef enum {
 } hhg_solve_mode;
 
 typedef enum {
-  HHG_SMOOTH_GS = 0,      /* three-colour Gauss-Seidel                       */
-  HHG_SMOOTH_LEARNED = 1  /* learned CNN step (hhg_learned_*), with GS on    */
-                          /* vertex/edge unknowns and on levels with N < 8   */
+  HHG_SMOOTH_GS = 0,         /* three-colour Gauss-Seidel                    */
+  HHG_SMOOTH_LEARNED = 1,    /* learned CNN step (hhg_learned_*), with GS on */
+                             /* vertex/edge unknowns and on levels with N < 8 */
+  HHG_SMOOTH_LEARNED_GS = 2  /* one Gauss-Seidel sweep (forward before, back- */
+                             /* ward after the coarse correction), then the  */
+                             /* learned step on the residual the sweep left  */
 } hhg_smoother_kind;
 
 typedef struct {

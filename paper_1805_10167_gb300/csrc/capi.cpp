@@ -117,7 +117,10 @@ static void vcycle_level(const Mesh& m, int l, int prec, void* x, const void* b,
   }
   const LevelData& ld = m.levels[l];
   const LevelData& lc = m.levels[l - 1];
-  const bool learned = smoother == 1 && ld.lv.N >= 8;
+  // smoother 1: the CNN step alone; 2: a Gauss-Seidel sweep, then the CNN
+  // step on the residual it leaves (levels with N < 8: Gauss-Seidel only)
+  const bool learned = smoother >= 1 && ld.lv.N >= 8;
+  const bool gs_first = smoother == 2;
   const double* bs = nullptr;
   if (!learned && nu1 + nu2 > 0 && uses_scaled_rhs(m, l, prec)) {
     if (!bs_ready) scale_rhs(m, l, (const double*)b, ld.bs, st);
@@ -127,6 +130,10 @@ static void vcycle_level(const Mesh& m, int l, int prec, void* x, const void* b,
   void* oth = ld.w[prec];
   for (int s = 0; s < nu1; ++s) {
     if (learned) {
+      if (gs_first) {
+        gs_sweep(m, l, prec, cur, oth, b, true, st, nullptr);
+        std::swap(cur, oth);
+      }
       learned_step(m, l, prec, cur, b, st);
       continue;
     }
@@ -134,13 +141,17 @@ static void vcycle_level(const Mesh& m, int l, int prec, void* x, const void* b,
     std::swap(cur, oth);
   }
   residual_op(m, l, prec, cur, b, ld.r[prec], nullptr, st);
-  const bool coarse_bs = smoother != 1 && uses_scaled_rhs(m, l - 1, prec);
+  const bool coarse_bs = smoother == 0 && uses_scaled_rhs(m, l - 1, prec);
   restrict_op(m, l, prec, ld.r[prec], lc.b[prec], st, coarse_bs ? lc.bs : nullptr);
   zero_vec(m, l - 1, prec, lc.x[prec], st);
   vcycle_level(m, l - 1, prec, lc.x[prec], lc.b[prec], nu1, nu2, smoother, coarse_bs, st);
   prolongate_add(m, l, prec, lc.x[prec], cur, st);
   for (int s = 0; s < nu2; ++s) {
     if (learned) {
+      if (gs_first) {
+        gs_sweep(m, l, prec, cur, oth, b, false, st, nullptr);
+        std::swap(cur, oth);
+      }
       learned_step(m, l, prec, cur, b, st);
       continue;
     }
@@ -407,6 +418,7 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
     hhg_solve_opts o{HHG_SOLVE_MG, 3, 3, 100, 1e-10, HHG_SMOOTH_GS, 20};
     if (opts) o = *opts;
     if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 0 || !(o.tol >= 0.0)) throw ArgError("bad solve options");
+    if (o.smoother < HHG_SMOOTH_GS || o.smoother > HHG_SMOOTH_LEARNED_GS) throw ArgError("bad smoother kind");
     if (o.mode != HHG_SOLVE_MG && o.mode != HHG_SOLVE_IR && o.mode != HHG_SOLVE_FGMRES && o.mode != HHG_SOLVE_PCG &&
         o.mode != HHG_SOLVE_FPCG)
       throw ArgError("bad solve mode");

@@ -5,8 +5,9 @@
 // projection coefficients kept on the device; Givens rotations on the host.
 //
 // Outer vectors and inner products are FP64.  M_j = one FP32 V(nu1, nu2)
-// cycle on A z = v from z = 0 whose smoother is 3-colour Gauss-Seidel or the
-// learned CNN step.  Judge: before the first restart both preconditioners
+// cycle on A z = v from z = 0 whose smoother is 3-colour Gauss-Seidel, the
+// learned CNN step, or a Gauss-Seidel sweep followed by the learned step.
+// Judge: before the first restart both preconditioners
 // are applied to v_1 and the learned one is kept only if its residual
 // ||v_1 - A z|| is not larger than Gauss-Seidel's; otherwise the whole solve
 // falls back to Gauss-Seidel.
@@ -388,7 +389,7 @@ static double precond_quality(Mesh& m, int L, const double* v, const double* z, 
 void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts& o, int smoother,
                   int restart, hhg_solve_report* rep, int* smoother_used, cudaStream_t st) {
   if (restart < 1 || restart > 200) throw std::invalid_argument("restart must be in 1..200");
-  if (smoother == 1 && !learned_ready(m)) throw std::invalid_argument("learned smoother requested but not trained/loaded");
+  if (smoother >= 1 && !learned_ready(m)) throw std::invalid_argument("learned smoother requested but not trained/loaded");
   KrylovSpace& K = space(m, L, restart);
   const LevelData& ld = m.levels[L];
   const int64_t n = ld.lv.len;
@@ -414,9 +415,9 @@ void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_op
     }
     k_normalize<<<g, 256, 0, st>>>(n, m.scalars, r, K.V[0], nullptr);
     check_cuda(cudaGetLastError(), "normalize");
-    if (use == 1 && !judged) {
+    if (use >= 1 && !judged) {
       double* tmp = K.V[restart];   // not used before the last step of a restart
-      precondition(m, L, K.V[0], K.Z[0], o.nu1, o.nu2, 1, st);
+      precondition(m, L, K.V[0], K.Z[0], o.nu1, o.nu2, use, st);
       const double q_learned = precond_quality(m, L, K.V[0], K.Z[0], tmp, st);
       precondition(m, L, K.V[0], K.w, o.nu1, o.nu2, 0, st);
       const double q_gs = precond_quality(m, L, K.V[0], K.w, tmp, st);

@@ -18,7 +18,8 @@
 // degree 1 in the residual, as an error estimate must be.
 //
 // Training (all on the GPU): residual/error pairs of FP64 V-cycle iterates
-// x_k (r = b - A x_k = A e) are cut as 64 x 64 crops of face lattices; the
+// x_k (r = b - A x_k = A e; random starts after one Gauss-Seidel sweep, the
+// others after k cycles) are cut as 64 x 64 crops of face lattices; the
 // loss is the residual the step leaves, ||S - D^-1 A d||^2 / ||S||^2 on the
 // normalised scaled residual S (the energy form of the error loss: it asks
 // for what a smoother does, removing the residual locally); forward,
@@ -43,6 +44,7 @@ constexpr int oW1 = 0, ob1 = 432, oW2 = 448, ob2 = 2752, oW3 = 2768, ob3 = 2912;
 constexpr int kCS = 64;                       // crop size
 constexpr int kCore = 3;                      // loss ignores the outer 3 crop rows/cols
 constexpr int TJ = 8, TI = 32;                // output tile (256 threads)
+constexpr int kW2Frag = 9 * 2 * 2 * 32;       // layer-2 B fragments (uint32)
 
 __constant__ float cW[kNP];
 
@@ -84,7 +86,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 template <typename T>
 __global__ void __launch_bounds__(TJ* TI)
     k_cnn_smooth(MeshTables M, LevelView L, const float* __restrict__ s, const float* __restrict__ kf,
-                 const float* __restrict__ scale, T* x, float* delta) {
+                 const float* __restrict__ scale, const uint32_t* __restrict__ w2frag,
+                 const float* __restrict__ wr, T* x, float* delta) {
   constexpr int J0 = TJ + 6, I0 = TI + 6, J1 = TJ + 4, I1 = TI + 4, J2 = TJ + 2, I2 = TI + 2;
   __shared__ __nv_bfloat16 xin[3][J0][I0];
   __shared__ __align__(16) __nv_bfloat16 h1[J1][I1][16];
@@ -139,18 +142,24 @@ __global__ void __launch_bounds__(TJ* TI)
     dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
     dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
   }
-  // weight fragments of layer 2 for this lane: B[k][n] = W2[n][k][tap]
+  // weight fragments of layer 2 for this lane (packed by k_pack_w2 in lane
+  // order, so that the loads are coalesced; a per-lane index into the
+  // constant bank would serialise the warp)
   const int lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tq = lane & 3;
   uint32_t bfr[9][2][2];
 #pragma unroll
   for (int t = 0; t < 9; ++t)
 #pragma unroll
-    for (int nb = 0; nb < 2; ++nb) {
-      const int o = nb * 8 + g;
-      bfr[t][nb][0] = pack_bf16(cW[oW2 + o * 144 + (2 * tq) * 9 + t], cW[oW2 + o * 144 + (2 * tq + 1) * 9 + t]);
-      bfr[t][nb][1] = pack_bf16(cW[oW2 + o * 144 + (2 * tq + 8) * 9 + t], cW[oW2 + o * 144 + (2 * tq + 9) * 9 + t]);
-    }
+    for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) bfr[t][nb][h] = w2frag[((t * 2 + nb) * 2 + h) * 32 + lane];
+  float bias0[2], bias1[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    bias0[u] = wr[ob2 + 2 * tq + u];
+    bias1[u] = wr[ob2 + 8 + 2 * tq + u];
+  }
   __syncthreads();
   // layer 2 (tensor cores): chunks of 16 points of the h2 region
   constexpr int NP2 = J2 * I2;
@@ -160,10 +169,8 @@ __global__ void __launch_bounds__(TJ* TI)
     float d0[4], d1[4];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      d0[u] = cW[ob2 + 2 * tq + u];
-      d0[u + 2] = d0[u];
-      d1[u] = cW[ob2 + 8 + 2 * tq + u];
-      d1[u + 2] = d1[u];
+      d0[u] = d0[u + 2] = bias0[u];
+      d1[u] = d1[u + 2] = bias1[u];
     }
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
@@ -203,6 +210,18 @@ __global__ void __launch_bounds__(TJ* TI)
   acc *= sig;
   if (delta) delta[p] = acc;
   if (x) x[p] = (T)((T)x[p] + (T)acc);
+}
+
+// Layer-2 weights as mma.sync B fragments in lane order: entry
+// ((t * 2 + nb) * 2 + h) * 32 + lane holds, for output channel
+// o = nb * 8 + lane / 4 and c = 2 (lane % 4) + 8 h, the BF16 pair
+// (W2[o][c][t], W2[o][c + 1][t]).  One thread per entry.
+__global__ void k_pack_w2(const float* __restrict__ wr, uint32_t* w2frag) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kW2Frag) return;
+  const int lane = e & 31, h = (e >> 5) & 1, nb = (e >> 6) & 1, t = e >> 7;
+  const int o = nb * 8 + (lane >> 2), c = 2 * (lane & 3) + 8 * h;
+  w2frag[e] = pack_bf16(wr[oW2 + o * 144 + c * 9 + t], wr[oW2 + o * 144 + (c + 1) * 9 + t]);
 }
 
 // Per-face residual scale: sigma_f = sqrt(mean of s^2 over the closed lattice
@@ -555,6 +574,7 @@ struct Learned {
   float* g = nullptr;      // gradient
   float* m = nullptr;      // Adam moments
   float* v = nullptr;
+  uint32_t* w2frag = nullptr;   // layer-2 B fragments of the smoother kernel
   int step = 0;
   bool trained = false;
 };
@@ -567,6 +587,7 @@ static Learned& learned_of(Mesh& m) {
       check_cuda(cudaMemset(*p, 0, kNP * sizeof(float)), "learned memset");
     }
     check_cuda(cudaMalloc(&L->scale, std::max(1, m.nf) * sizeof(float)), "learned alloc");
+    check_cuda(cudaMalloc(&L->w2frag, kW2Frag * sizeof(uint32_t)), "learned alloc");
     L->scale_n = m.nf;
     m.learned = L;
   }
@@ -577,12 +598,15 @@ void learned_free(Mesh& m) {
   if (!m.learned) return;
   Learned* L = m.learned;
   for (float* p : {L->w, L->wr, L->g, L->m, L->v, L->scale}) cudaFree(p);
+  cudaFree(L->w2frag);
   delete L;
   m.learned = nullptr;
 }
 
 static void load_constants(Learned& L, cudaStream_t st) {
   check_cuda(cudaMemcpyToSymbolAsync(cW, L.wr, kNP * sizeof(float), 0, cudaMemcpyDeviceToDevice, st), "weights to constant bank");
+  k_pack_w2<<<(kW2Frag + 127) / 128, 128, 0, st>>>(L.wr, L.w2frag);
+  check_cuda(cudaGetLastError(), "pack layer-2 fragments");
 }
 
 void learned_set_weights(Mesh& m, const float* w_host, cudaStream_t st) {
@@ -616,8 +640,10 @@ void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, 
   LaunchScope ls(HHG_K_OTHER, level, st);
   k_face_rms<<<m.nf, 256, 0, st>>>(m.tab, lv, s, L.scale);
   if (delta) check_cuda(cudaMemsetAsync(delta, 0, (size_t)lv.len * sizeof(float), st), "delta clear");
-  if (prec == 0) k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, L.scale, (double*)x, delta);
-  else k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, L.scale, (float*)x, delta);
+  if (prec == 0)
+    k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, L.scale, L.w2frag, L.wr, (double*)x, delta);
+  else
+    k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, L.scale, L.w2frag, L.wr, (float*)x, delta);
   check_cuda(cudaGetLastError(), "cnn smooth");
 }
 
@@ -748,6 +774,11 @@ void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr,
     if (snap % 6 == 0) {   // fresh random start; snapshot k of a start follows k cycles (0..5)
       k_fill_random<<<1024, 256, 0, st>>>(len, x, seed + 1000 + snap);
       zero_dirichlet_and_ghosts(m, l, x, st);
+      // one forward sweep: every snapshot then holds a residual that a
+      // Gauss-Seidel sweep left behind, the state the learned step meets
+      gs_sweep(m, l, 0, x, ld.w[0], b, true, st);
+      check_cuda(cudaMemcpyAsync(x, ld.w[0], (size_t)len * sizeof(double), cudaMemcpyDeviceToDevice, st),
+                 "snapshot copy");
     } else {
       vcycle_run(m, l, 0, x, b, 3, 3, 0, st);
     }

@@ -28,7 +28,7 @@ SWEEP_RING, SWEEP_STRIP = 0, 1
 ARITH_IEEE, ARITH_DFLOAT = 0, 1
 GS_FWD, GS_BWD, JACOBI = 0, 1, 2
 SOLVE_MG, SOLVE_IR, SOLVE_FGMRES, SOLVE_PCG, SOLVE_FPCG = 0, 1, 2, 3, 4
-SMOOTH_GS, SMOOTH_LEARNED = 0, 1
+SMOOTH_GS, SMOOTH_LEARNED, SMOOTH_LEARNED_GS = 0, 1, 2
 LEARNED_NPARAMS = 2913
 
 

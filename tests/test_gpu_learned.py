@@ -133,8 +133,12 @@ def test_fgmres_gs_preconditioner_reaches_fp64_tolerance():
 
 def test_training_lowers_loss_and_learned_fgmres_converges():
     """Small training run (level 6): the loss falls; FGMRES with the learned
-    V-cycle reaches the FP64 tolerance; the judge's choice and both
-    convergence factors are reported."""
+    V-cycle reaches the FP64 tolerance; the judge's choice and the
+    convergence factors are reported.  What the trained network gains over
+    the method without it: a Gauss-Seidel sweep followed by the learned step
+    leaves less residual in one V(1,1) than the Gauss-Seidel V(1,1) (the
+    judge's measurement), so the judge keeps it and FGMRES needs no more
+    steps than with Gauss-Seidel."""
     torch = pytest.importorskip("torch")
     from paper_1805_10167_gb300 import hhg
     xy, tri = inputs.annulus_mesh(32, 2)
@@ -151,7 +155,8 @@ def test_training_lowers_loss_and_learned_fgmres_converges():
     b = torch.zeros(I.vec_len, dtype=torch.float64, device="cuda")
     g.from_canonical(L, bc, b)
     rates = {}
-    for name, sm in (("gs", hhg.SMOOTH_GS), ("learned", hhg.SMOOTH_LEARNED)):
+    for name, sm in (("gs", hhg.SMOOTH_GS), ("learned", hhg.SMOOTH_LEARNED),
+                     ("learned_gs", hhg.SMOOTH_LEARNED_GS)):
         x = torch.zeros_like(b)
         st, rep = g.solve(L, x, b, mode=hhg.SOLVE_FGMRES, nu1=1, nu2=1, tol=1e-10, smoother=sm)
         assert rep["r_final"] <= 1e-10 * rep["r0"]
@@ -160,4 +165,8 @@ def test_training_lowers_loss_and_learned_fgmres_converges():
         rates[name + "_steps"] = rep["iterations"]
         rates[name + "_judge"] = (rep["judge_learned"], rep["judge_gs"])
     print("FGMRES per-step factors:", rates)
+    q_learned, q_gs = rates["learned_gs_judge"]
+    assert 0.0 < q_learned < q_gs
+    assert rates["learned_gs_used"] == hhg.SMOOTH_LEARNED_GS
+    assert rates["learned_gs_steps"] <= rates["gs_steps"]
     g.close()
