@@ -223,6 +223,7 @@ struct Mesh {
   std::vector<void*> allocations;
   std::vector<LevelData> levels;
   bool vark = false;
+  int k_version = 0;                // incremented by every set_coefficient
   bool fp64_df = false;             // FP64 face kernels in double-float arithmetic (hhg_set_fp64_arith)
   // independent problems (blocks); level-0 coarse solve per block: dense
   // n0 x n0 matrix over its free macro-vertices (row-major, in A0 at a0_off)

@@ -44,7 +44,6 @@ constexpr int oW1 = 0, ob1 = 432, oW2 = 448, ob2 = 2752, oW3 = 2768, ob3 = 2912;
 constexpr int kCS = 64;                       // crop size
 constexpr int kCore = 3;                      // loss ignores the outer 3 crop rows/cols
 constexpr int TJ = 8, TI = 32;                // output tile (256 threads)
-constexpr int kW2Frag = 9 * 2 * 2 * 32;       // layer-2 B fragments (uint32)
 
 __constant__ float cW[kNP];
 
@@ -60,13 +59,25 @@ struct Crop {
 __device__ __forceinline__ bool interior_pt(int i, int j, int N) { return i >= 1 && j >= 1 && i + j <= N - 1; }
 
 // --------------------------------------------------------------- smoother
-// One CTA = an 8 x 32 output tile of one face.  Input region 14 x 38
-// (3 channels), h1 region 12 x 36, h2 region 10 x 34, all BF16 in shared
-// memory, activations channel-last (16 channels = 32 bytes per point).
-// Layer 1 (3 -> 16) and layer 3 (16 -> 1) run on the CUDA cores; layer 2
-// (16 -> 16, 80 % of the work) on the tensor cores: for each tap a
-// 16-point x 16-channel block of h1 times the tap's 16 x 16 weight block,
-// mma.sync m16n8k16 BF16 -> FP32, two n-blocks of 8 output channels.
+// One CTA = an 8 x 32 output tile of one face.  Input region 14 x 38, h1
+// region 12 x 36, h2 region 10 x 34, all BF16 in shared memory, channel-last.
+// All three layers run on the tensor cores (mma.sync m16n8k16, BF16 inputs,
+// FP32 accumulators) as implicit GEMMs over chunks of 16 points of the
+// layer's output region:
+//   layer 1: A[p][k] = X[p + tap(k / 4)][k % 4], k over 9 taps x 4 channels
+//            (the 3 inputs and a zero channel), padded to 48 (3 k-steps);
+//   layer 2: per tap, A[p][c] = h1[p + tap][c] (16 channels), 9 k-steps,
+//            two n-blocks of 8 output channels;
+//   layer 3: per tap, A[p][c] = h2[p + tap][c], one n-block whose column 0
+//            is the single output channel (columns 1-7 have zero weights).
+// B fragments are packed in lane order once per weight load (k_pack_frags),
+// so each lane reads its own with coalesced loads.  h1 and h2 keep 48 bytes
+// per point (16 channels and padding): the eight 16-byte rows that one
+// ldmatrix phase reads from consecutive points then fall in distinct banks.
+
+constexpr int kPS = 24;                               // BF16 slots per point in h1, h2
+constexpr int kF1 = 0, kF2 = 3 * 2 * 2 * 32, kF3 = kF2 + 9 * 2 * 2 * 32;
+constexpr int kFrag = kF3 + 9 * 2 * 32;               // packed B fragments (uint32)
 
 // D += A * B for one m16n8k16 block (BF16 inputs, FP32 accumulators).
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -77,21 +88,181 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Four 8 x 8 BF16 matrices from shared memory: lane l gives the address of
+// row l % 8 of matrix l / 8; register i receives matrix i's pair at (row
+// lane / 4, columns 2 (lane % 4), +1) -- the A fragment of m16n8k16 when
+// matrices 0-3 are (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k
+// 8-15), (rows 8-15, k 8-15).
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a)
+               : "memory");
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const uint32_t l = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo));
   const uint32_t h = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi));
   return l | (h << 16);
 }
 
+__device__ __forceinline__ uint32_t relu_pack(float lo, float hi, bool in) {
+  return in ? pack_bf16(fmaxf(lo, 0.f), fmaxf(hi, 0.f)) : 0u;
+}
+
+constexpr int J0 = TJ + 6, I0 = TI + 6, J1 = TJ + 4, I1 = TI + 4, J2 = TJ + 2, I2 = TI + 2;
+constexpr int NP0 = J0 * I0, NP1 = J1 * I1, NP2 = J2 * I2, NP3 = TJ * TI;
+static_assert(NP1 % 16 == 0, "layer-1 region is a whole number of 16-point chunks");
+static_assert(TI % 16 == 0, "output rows are whole chunks");
+
+// Layer 1 (3 -> 16) on NC chunks of 16 points of the h1 region at once (NC
+// independent accumulator chains hide the mma latency).
+template <int NC>
+__device__ __forceinline__ void cnn_layer1(const int (&chunk)[NC], const uint32_t* X, __nv_bfloat16 (*h1)[kPS],
+                                           const uint32_t (&bf)[3][2][2], const float (&bias)[2][2], int i0,
+                                           int j0, int N, int g, int tq) {
+  int pa[NC], pb[NC];
+  float d[NC][2][4];
+#pragma unroll
+  for (int u = 0; u < NC; ++u) {
+    const int qa = chunk[u] * 16 + g, qb = qa + 8;
+    const int ja = qa / I1, jb = qb / I1;
+    pa[u] = ja * I0 + (qa - ja * I1);   // window origins in the input region
+    pb[u] = jb * I0 + (qb - jb * I1);
+#pragma unroll
+    for (int nb = 0; nb < 2; ++nb) {
+      d[u][nb][0] = d[u][nb][2] = bias[nb][0];
+      d[u][nb][1] = d[u][nb][3] = bias[nb][1];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    // this lane's k pairs: taps ta (k pair 2tq) and ta + 2 (2tq + 8), word tq & 1 of the point
+    const int ta = k * 4 + (tq >> 1), tb = ta + 2;
+    const int oa = (ta / 3) * I0 + ta % 3, ob = (tb / 3) * I0 + tb % 3;
+    const int w = tq & 1;
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      uint32_t afr[4];
+      afr[0] = ta < 9 ? X[(pa[u] + oa) * 2 + w] : 0u;
+      afr[1] = ta < 9 ? X[(pb[u] + oa) * 2 + w] : 0u;
+      afr[2] = tb < 9 ? X[(pa[u] + ob) * 2 + w] : 0u;
+      afr[3] = tb < 9 ? X[(pb[u] + ob) * 2 + w] : 0u;
+      mma_bf16(d[u][0], afr, bf[k][0][0], bf[k][0][1]);
+      mma_bf16(d[u][1], afr, bf[k][1][0], bf[k][1][1]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NC; ++u)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = chunk[u] * 16 + g + 8 * h;
+      const int jj = q / I1, ii = q - jj * I1;
+      const bool in = closed_pt(i0 - 2 + ii, j0 - 2 + jj, N);
+      uint32_t* row = reinterpret_cast<uint32_t*>(&h1[q][0]);
+      row[tq] = relu_pack(d[u][0][2 * h], d[u][0][2 * h + 1], in);
+      row[tq + 4] = relu_pack(d[u][1][2 * h], d[u][1][2 * h + 1], in);
+    }
+}
+
+// Layer 2 (16 -> 16) on NC chunks of the h2 region (the last chunk may be
+// ragged: its rows past the region repeat the last point and are not stored).
+template <int NC>
+__device__ __forceinline__ void cnn_layer2(const int (&chunk)[NC], __nv_bfloat16 (*h1)[kPS],
+                                           __nv_bfloat16 (*h2)[kPS], const uint32_t (&bf)[9][2][2],
+                                           const float (&bias)[2][2], int i0, int j0, int N, int g, int tq,
+                                           int lrow, int lhalf) {
+  int pr[NC];
+  float d[NC][2][4];
+#pragma unroll
+  for (int u = 0; u < NC; ++u) {
+    const int qr = min(chunk[u] * 16 + lrow, NP2 - 1);
+    const int jr = qr / I2;
+    pr[u] = jr * I1 + (qr - jr * I2);                    // window origin in h1
+#pragma unroll
+    for (int nb = 0; nb < 2; ++nb) {
+      d[u][nb][0] = d[u][nb][2] = bias[nb][0];
+      d[u][nb][1] = d[u][nb][3] = bias[nb][1];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 9; ++t)
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      uint32_t afr[4];
+      ldsm_x4(afr, &h1[pr[u] + (t / 3) * I1 + t % 3][lhalf]);
+      mma_bf16(d[u][0], afr, bf[t][0][0], bf[t][0][1]);
+      mma_bf16(d[u][1], afr, bf[t][1][0], bf[t][1][1]);
+    }
+#pragma unroll
+  for (int u = 0; u < NC; ++u)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = chunk[u] * 16 + g + 8 * h;
+      if (q < NP2) {
+        const int jj = q / I2, ii = q - jj * I2;
+        const bool in = closed_pt(i0 - 1 + ii, j0 - 1 + jj, N);
+        uint32_t* row = reinterpret_cast<uint32_t*>(&h2[q][0]);
+        row[tq] = relu_pack(d[u][0][2 * h], d[u][0][2 * h + 1], in);
+        row[tq + 4] = relu_pack(d[u][1][2 * h], d[u][1][2 * h + 1], in);
+      }
+    }
+}
+
+// Layer 3 (16 -> 1) on NC chunks of the output tile (half a row each);
+// column 0 of the n-block is the output channel, held by the lanes with
+// tq = 0 for rows g (d[0]) and g + 8 (d[2]).
+template <int NC, typename T>
+__device__ __forceinline__ void cnn_layer3(const int (&chunk)[NC], __nv_bfloat16 (*h2)[kPS],
+                                           const uint32_t (&bf)[9][2], float bias, float sig, int64_t fb,
+                                           int64_t S, int i0, int j0, int N, int g, int tq, int lrow, int lhalf,
+                                           T* x, float* delta) {
+  int pr[NC];
+  float d[NC][4];
+#pragma unroll
+  for (int u = 0; u < NC; ++u) {
+    const int ty = chunk[u] / (TI / 16), tx0 = (chunk[u] % (TI / 16)) * 16;
+    pr[u] = ty * I2 + tx0 + lrow;                         // window origin in h2
+    d[u][0] = d[u][1] = d[u][2] = d[u][3] = 0.f;
+  }
+#pragma unroll
+  for (int t = 0; t < 9; ++t)
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      uint32_t afr[4];
+      ldsm_x4(afr, &h2[pr[u] + (t / 3) * I2 + t % 3][lhalf]);
+      mma_bf16(d[u], afr, bf[t][0], bf[t][1]);
+    }
+  if (tq == 0) {
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      const int ty = chunk[u] / (TI / 16), tx0 = (chunk[u] % (TI / 16)) * 16;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + tx0 + g + 8 * h, j = j0 + ty;
+        if (interior_pt(i, j, N)) {
+          const int64_t p = fb + (int64_t)j * S + i;
+          const float acc = (d[u][2 * h] + bias) * sig;
+          if (delta) delta[p] = acc;
+          if (x) x[p] = (T)((T)x[p] + (T)acc);
+        }
+      }
+    }
+  }
+}
+
+// logk: per face slot the BF16 pair (log k of the upward, of the downward
+// micro-triangle at (i, j)), zero where a triangle does not exist; NULL for
+// k = 1.
 template <typename T>
 __global__ void __launch_bounds__(TJ* TI)
-    k_cnn_smooth(MeshTables M, LevelView L, const float* __restrict__ s, const float* __restrict__ kf,
-                 const float* __restrict__ scale, const uint32_t* __restrict__ w2frag,
+    k_cnn_smooth(LevelView L, const float* __restrict__ s, const uint32_t* __restrict__ logk,
+                 const float* __restrict__ scale, const uint32_t* __restrict__ frag,
                  const float* __restrict__ wr, T* x, float* delta) {
-  constexpr int J0 = TJ + 6, I0 = TI + 6, J1 = TJ + 4, I1 = TI + 4, J2 = TJ + 2, I2 = TI + 2;
-  __shared__ __nv_bfloat16 xin[3][J0][I0];
-  __shared__ __align__(16) __nv_bfloat16 h1[J1][I1][16];
-  __shared__ __align__(16) __nv_bfloat16 h2[J2][I2][16];
+  __shared__ __align__(16) uint2 xin[NP0];                 // 4 BF16 channels per point
+  __shared__ __align__(16) __nv_bfloat16 h1[NP1][kPS];
+  __shared__ __align__(16) __nv_bfloat16 h2[NP2][kPS];
   const int f = blockIdx.z;
   const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
   const int N = L.N;
@@ -100,128 +271,123 @@ __global__ void __launch_bounds__(TJ* TI)
   const float isig = 1.f / sig;
   const int64_t S = L.S;
   const int64_t fb = L.f_off + (int64_t)f * L.FS;
-  const float* ku = kf ? kf + (int64_t)f * L.FS : nullptr;
-  const float* kd = kf ? kf + (int64_t)(M.nf + f) * L.FS : nullptr;
+  const uint32_t* lk = logk ? logk + (int64_t)f * L.FS : nullptr;
   const int tid = threadIdx.x;
-  for (int q = tid; q < J0 * I0; q += TJ * TI) {
+  for (int q = tid; q < NP0; q += TJ * TI) {
     const int jj = q / I0, ii = q - jj * I0;
     const int i = i0 - 3 + ii, j = j0 - 3 + jj;
-    float a = 0.f, bu = 0.f, bd = 0.f;
+    float a = 0.f;
+    uint32_t kk = 0u;
     if (closed_pt(i, j, N)) {
       const int64_t p = (int64_t)j * S + i;
       a = s[fb + p] * isig;
-      if (ku && i + j <= N - 1) bu = __logf(ku[p]);
-      if (kd && i + j <= N - 2) bd = __logf(kd[p]);
+      if (lk) kk = lk[p];
     }
-    xin[0][jj][ii] = __float2bfloat16_rn(a);
-    xin[1][jj][ii] = __float2bfloat16_rn(bu);
-    xin[2][jj][ii] = __float2bfloat16_rn(bd);
+    // channels (residual, log k up | log k down, 0)
+    xin[q] = make_uint2((pack_bf16(a, 0.f) & 0xffffu) | (kk << 16), kk >> 16);
   }
-  __syncthreads();
-  // layer 1 (CUDA cores)
-  for (int q = tid; q < J1 * I1; q += TJ * TI) {
-    const int jj = q / I1, ii = q - jj * I1;
-    const int i = i0 - 2 + ii, j = j0 - 2 + jj;
-    float acc[16];
-#pragma unroll
-    for (int o = 0; o < 16; ++o) acc[o] = cW[ob1 + o];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const float a = __bfloat162float(xin[c][jj + t / 3][ii + t % 3]);
-#pragma unroll
-        for (int o = 0; o < 16; ++o) acc[o] = fmaf(cW[oW1 + o * 27 + c * 9 + t], a, acc[o]);
-      }
-    const bool in = closed_pt(i, j, N);
-    uint32_t packed[8];
-#pragma unroll
-    for (int o = 0; o < 8; ++o)
-      packed[o] = in ? pack_bf16(fmaxf(acc[2 * o], 0.f), fmaxf(acc[2 * o + 1], 0.f)) : 0u;
-    uint4* dst = reinterpret_cast<uint4*>(&h1[jj][ii][0]);
-    dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-    dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-  }
-  // weight fragments of layer 2 for this lane (packed by k_pack_w2 in lane
-  // order, so that the loads are coalesced; a per-lane index into the
-  // constant bank would serialise the warp)
   const int lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = TJ * TI / 32;
   const int g = lane >> 2, tq = lane & 3;
-  uint32_t bfr[9][2][2];
+  // ldmatrix row of this lane: point offset in a chunk and channel half
+  const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lhalf = (lane >> 4) * 8;
+  {
+    uint32_t bf[3][2][2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) bf[k][nb][h] = frag[kF1 + ((k * 2 + nb) * 2 + h) * 32 + lane];
+    const float bias[2][2] = {{wr[ob1 + 2 * tq], wr[ob1 + 2 * tq + 1]}, {wr[ob1 + 8 + 2 * tq], wr[ob1 + 9 + 2 * tq]}};
+    const uint32_t* X = reinterpret_cast<const uint32_t*>(xin);
+    __syncthreads();
+    int c = warp;
+    for (; c + NW < NP1 / 16; c += 2 * NW) cnn_layer1<2>({c, c + NW}, X, h1, bf, bias, i0, j0, N, g, tq);
+    if (c < NP1 / 16) cnn_layer1<1>({c}, X, h1, bf, bias, i0, j0, N, g, tq);
+  }
+  {
+    uint32_t bf[9][2][2];
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+      for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) bf[t][nb][h] = frag[kF2 + ((t * 2 + nb) * 2 + h) * 32 + lane];
+    const float bias[2][2] = {{wr[ob2 + 2 * tq], wr[ob2 + 2 * tq + 1]}, {wr[ob2 + 8 + 2 * tq], wr[ob2 + 9 + 2 * tq]}};
+    __syncthreads();
+    constexpr int NC2 = (NP2 + 15) / 16;
+    int c = warp;
+    for (; c + NW < NC2; c += 2 * NW) cnn_layer2<2>({c, c + NW}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
+    if (c < NC2) cnn_layer2<1>({c}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
+  }
+  uint32_t bf[9][2];
 #pragma unroll
   for (int t = 0; t < 9; ++t)
 #pragma unroll
-    for (int nb = 0; nb < 2; ++nb)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) bfr[t][nb][h] = w2frag[((t * 2 + nb) * 2 + h) * 32 + lane];
-  float bias0[2], bias1[2];
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    bias0[u] = wr[ob2 + 2 * tq + u];
-    bias1[u] = wr[ob2 + 8 + 2 * tq + u];
-  }
+    for (int h = 0; h < 2; ++h) bf[t][h] = frag[kF3 + (t * 2 + h) * 32 + lane];
+  const float b3 = wr[ob3];
   __syncthreads();
-  // layer 2 (tensor cores): chunks of 16 points of the h2 region
-  constexpr int NP2 = J2 * I2;
-  for (int chunk = warp; chunk * 16 < NP2; chunk += TJ * TI / 32) {
-    const int qa = min(chunk * 16 + g, NP2 - 1), qb = min(chunk * 16 + g + 8, NP2 - 1);
-    const int ja = qa / I2, ia = qa % I2, jb = qb / I2, ib = qb % I2;
-    float d0[4], d1[4];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      d0[u] = d0[u + 2] = bias0[u];
-      d1[u] = d1[u + 2] = bias1[u];
-    }
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      const int dy = t / 3, dx = t % 3;
-      const uint32_t* pa = reinterpret_cast<const uint32_t*>(&h1[ja + dy][ia + dx][0]);
-      const uint32_t* pb = reinterpret_cast<const uint32_t*>(&h1[jb + dy][ib + dx][0]);
-      const uint32_t afr[4] = {pa[tq], pb[tq], pa[tq + 4], pb[tq + 4]};
-      mma_bf16(d0, afr, bfr[t][0][0], bfr[t][0][1]);
-      mma_bf16(d1, afr, bfr[t][1][0], bfr[t][1][1]);
-    }
-    // rows g and g+8 of the block; columns 2tq, 2tq+1 of each n-block
-    const int pts[2] = {chunk * 16 + g, chunk * 16 + g + 8};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int q = pts[h];
-      if (q >= NP2) continue;
-      const int jj = q / I2, ii = q % I2;
-      const bool in = closed_pt(i0 - 1 + ii, j0 - 1 + jj, N);
-      uint32_t* row = reinterpret_cast<uint32_t*>(&h2[jj][ii][0]);
-      row[tq] = in ? pack_bf16(fmaxf(d0[2 * h], 0.f), fmaxf(d0[2 * h + 1], 0.f)) : 0u;
-      row[tq + 4] = in ? pack_bf16(fmaxf(d1[2 * h], 0.f), fmaxf(d1[2 * h + 1], 0.f)) : 0u;
-    }
-  }
-  __syncthreads();
-  // layer 3 (CUDA cores)
-  const int ty = tid / TI, tx = tid % TI;
-  const int i = i0 + tx, j = j0 + ty;
-  if (!interior_pt(i, j, N)) return;
-  float acc = cW[ob3];
-#pragma unroll
-  for (int t = 0; t < 9; ++t) {
-    const __nv_bfloat16* hv = &h2[ty + t / 3][tx + t % 3][0];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) acc = fmaf(cW[oW3 + c * 9 + t], __bfloat162float(hv[c]), acc);
-  }
-  const int64_t p = fb + (int64_t)j * S + i;
-  acc *= sig;
-  if (delta) delta[p] = acc;
-  if (x) x[p] = (T)((T)x[p] + (T)acc);
+  int c = warp;
+  for (; c + NW < NP3 / 16; c += 2 * NW)
+    cnn_layer3<2, T>({c, c + NW}, h2, bf, b3, sig, fb, S, i0, j0, N, g, tq, lrow, lhalf, x, delta);
+  if (c < NP3 / 16) cnn_layer3<1, T>({c}, h2, bf, b3, sig, fb, S, i0, j0, N, g, tq, lrow, lhalf, x, delta);
 }
 
-// Layer-2 weights as mma.sync B fragments in lane order: entry
-// ((t * 2 + nb) * 2 + h) * 32 + lane holds, for output channel
-// o = nb * 8 + lane / 4 and c = 2 (lane % 4) + 8 h, the BF16 pair
-// (W2[o][c][t], W2[o][c + 1][t]).  One thread per entry.
-__global__ void k_pack_w2(const float* __restrict__ wr, uint32_t* w2frag) {
+// Log-coefficient pairs of one level for the smoother's input channels:
+// out[f * FS + j * S + i] = BF16 (log k_up(i, j), log k_down(i, j)), zero
+// where the micro-triangle does not exist.
+__global__ void k_logk_pack(LevelView L, int nf, const float* __restrict__ k, uint32_t* out) {
+  const int64_t n = (int64_t)nf * L.FS;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e % L.FS;
+    const int j = (int)(p / L.S), i = (int)(p - (int64_t)j * L.S);
+    float up = 0.f, dn = 0.f;
+    if (i + j <= L.N - 1) up = logf(k[e]);
+    if (i + j <= L.N - 2) dn = logf(k[n + e]);
+    out[e] = pack_bf16(up, dn);
+  }
+}
+
+// Weights of one layer as mma.sync B fragments in lane order (one thread per
+// entry; lane = e % 32, g = lane / 4, tq = lane % 4, column n = g of the
+// n-block, k pair 2 tq + 8 h, + 1):
+//   layer 1, entry ((k * 2 + nb) * 2 + h) * 32 + lane: output channel
+//            nb * 8 + g, k = 16 k-step + 2 tq + 8 h = 4 tap + channel
+//            (zero for channel 3 and taps 9-11);
+//   layer 2, entry ((t * 2 + nb) * 2 + h) * 32 + lane: output channel
+//            nb * 8 + g, input channels 2 tq + 8 h, + 1 at tap t;
+//   layer 3, entry (t * 2 + h) * 32 + lane: input channels 2 tq + 8 h, + 1 at
+//            tap t for column 0 (g = 0), zero for the other columns.
+__device__ __forceinline__ float w1_at(const float* wr, int o, int k) {
+  const int t = k >> 2, c = k & 3;
+  return (t < 9 && c < 3) ? wr[oW1 + o * 27 + c * 9 + t] : 0.f;
+}
+
+__global__ void k_pack_frags(const float* __restrict__ wr, uint32_t* frag) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= kW2Frag) return;
-  const int lane = e & 31, h = (e >> 5) & 1, nb = (e >> 6) & 1, t = e >> 7;
-  const int o = nb * 8 + (lane >> 2), c = 2 * (lane & 3) + 8 * h;
-  w2frag[e] = pack_bf16(wr[oW2 + o * 144 + c * 9 + t], wr[oW2 + o * 144 + (c + 1) * 9 + t]);
+  if (e >= kFrag) return;
+  const int lane = e & 31, g = lane >> 2, tq = lane & 3;
+  float lo = 0.f, hi = 0.f;
+  if (e < kF2) {
+    const int r = (e - kF1) >> 5, h = r & 1, nb = (r >> 1) & 1, k = r >> 2;
+    const int o = nb * 8 + g, kk = k * 16 + 2 * tq + 8 * h;
+    lo = w1_at(wr, o, kk);
+    hi = w1_at(wr, o, kk + 1);
+  } else if (e < kF3) {
+    const int r = (e - kF2) >> 5, h = r & 1, nb = (r >> 1) & 1, t = r >> 2;
+    const int o = nb * 8 + g, c = 2 * tq + 8 * h;
+    lo = wr[oW2 + o * 144 + c * 9 + t];
+    hi = wr[oW2 + o * 144 + (c + 1) * 9 + t];
+  } else {
+    const int r = (e - kF3) >> 5, h = r & 1, t = r >> 1;
+    const int c = 2 * tq + 8 * h;
+    if (g == 0) {
+      lo = wr[oW3 + c * 9 + t];
+      hi = wr[oW3 + (c + 1) * 9 + t];
+    }
+  }
+  frag[e] = pack_bf16(lo, hi);
 }
 
 // Per-face residual scale: sigma_f = sqrt(mean of s^2 over the closed lattice
@@ -574,7 +740,9 @@ struct Learned {
   float* g = nullptr;      // gradient
   float* m = nullptr;      // Adam moments
   float* v = nullptr;
-  uint32_t* w2frag = nullptr;   // layer-2 B fragments of the smoother kernel
+  uint32_t* frag = nullptr;     // B fragments of the smoother kernel (k_pack_frags)
+  std::vector<uint32_t*> logk;  // per level: log-coefficient pairs (k_logk_pack)
+  std::vector<int> logk_ver;    // Mesh::k_version they were made from
   int step = 0;
   bool trained = false;
 };
@@ -587,7 +755,7 @@ static Learned& learned_of(Mesh& m) {
       check_cuda(cudaMemset(*p, 0, kNP * sizeof(float)), "learned memset");
     }
     check_cuda(cudaMalloc(&L->scale, std::max(1, m.nf) * sizeof(float)), "learned alloc");
-    check_cuda(cudaMalloc(&L->w2frag, kW2Frag * sizeof(uint32_t)), "learned alloc");
+    check_cuda(cudaMalloc(&L->frag, kFrag * sizeof(uint32_t)), "learned alloc");
     L->scale_n = m.nf;
     m.learned = L;
   }
@@ -598,15 +766,16 @@ void learned_free(Mesh& m) {
   if (!m.learned) return;
   Learned* L = m.learned;
   for (float* p : {L->w, L->wr, L->g, L->m, L->v, L->scale}) cudaFree(p);
-  cudaFree(L->w2frag);
+  cudaFree(L->frag);
+  for (uint32_t* p : L->logk) cudaFree(p);
   delete L;
   m.learned = nullptr;
 }
 
 static void load_constants(Learned& L, cudaStream_t st) {
   check_cuda(cudaMemcpyToSymbolAsync(cW, L.wr, kNP * sizeof(float), 0, cudaMemcpyDeviceToDevice, st), "weights to constant bank");
-  k_pack_w2<<<(kW2Frag + 127) / 128, 128, 0, st>>>(L.wr, L.w2frag);
-  check_cuda(cudaGetLastError(), "pack layer-2 fragments");
+  k_pack_frags<<<(kFrag + 127) / 128, 128, 0, st>>>(L.wr, L.frag);
+  check_cuda(cudaGetLastError(), "pack weight fragments");
 }
 
 void learned_set_weights(Mesh& m, const float* w_host, cudaStream_t st) {
@@ -635,15 +804,29 @@ void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, 
   Learned& L = *m.learned;
   load_constants(L, st);
   const LevelView& lv = m.levels[level].lv;
-  const float* kf = m.vark ? (const float*)m.levels[level].k[1] : nullptr;
+  const uint32_t* lk = nullptr;
+  if (m.vark) {   // log k pairs of the level, made once per coefficient
+    if ((int)L.logk.size() < (int)m.levels.size()) {
+      L.logk.resize(m.levels.size(), nullptr);
+      L.logk_ver.resize(m.levels.size(), -1);
+    }
+    if (!L.logk[level])
+      check_cuda(cudaMalloc(&L.logk[level], (size_t)m.nf * lv.FS * sizeof(uint32_t)), "log k alloc");
+    if (L.logk_ver[level] != m.k_version) {
+      k_logk_pack<<<152 * 8, 256, 0, st>>>(lv, m.nf, (const float*)m.levels[level].k[1], L.logk[level]);
+      check_cuda(cudaGetLastError(), "log k pack");
+      L.logk_ver[level] = m.k_version;
+    }
+    lk = L.logk[level];
+  }
   dim3 grid((lv.N + 1 + TI - 1) / TI, (lv.N + 1 + TJ - 1) / TJ, m.nf);
   LaunchScope ls(HHG_K_OTHER, level, st);
   k_face_rms<<<m.nf, 256, 0, st>>>(m.tab, lv, s, L.scale);
   if (delta) check_cuda(cudaMemsetAsync(delta, 0, (size_t)lv.len * sizeof(float), st), "delta clear");
   if (prec == 0)
-    k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, L.scale, L.w2frag, L.wr, (double*)x, delta);
+    k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (double*)x, delta);
   else
-    k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(m.tab, lv, s, kf, L.scale, L.w2frag, L.wr, (float*)x, delta);
+    k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (float*)x, delta);
   check_cuda(cudaGetLastError(), "cnn smooth");
 }
 

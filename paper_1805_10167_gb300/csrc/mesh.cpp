@@ -408,6 +408,7 @@ void default_sweep(Mesh& m, int level) {
 // levels as means of four children, FP32 copies, then the level-0 matrix.
 void set_coefficient(Mesh& m, const double* k_dev, cudaStream_t st) {
   graphs_clear(m);
+  ++m.k_version;
   if (!k_dev) {
     m.vark = false;
     std::vector<double> k0(m.nf, 1.0);
