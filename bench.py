@@ -87,9 +87,11 @@ def parse():
     ap.add_argument("--learned-pairs", type=int, default=10000)
     ap.add_argument("--learned-epochs", type=int, default=12)
     ap.add_argument("--batch-size", type=int, default=64)
-    ap.add_argument("--case", default="bench", choices=["bench", "sweep"],
-                    help="sweep: only four forward Gauss-Seidel sweeps on --level in --prec "
-                         "(the small case of the ncu captures under profiles/), no JSON line")
+    ap.add_argument("--case", default="bench", choices=["bench", "sweep", "cnn"],
+                    help="sweep: only four forward Gauss-Seidel sweeps on --level in --prec; "
+                         "cnn: only --steps applications of the learned smoother's network on "
+                         "--level of the variable-coefficient annulus, timed (the small cases of "
+                         "the ncu captures under profiles/), no JSON line")
     ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
     ap.add_argument("--arith", default="ieee", choices=["ieee", "dfloat"],
                     help="arithmetic of the FP64 face kernels in the sweep case")
@@ -306,9 +308,51 @@ def run_learned(args, dev, st):
                                             smoother=hhg.SMOOTH_LEARNED_GS),
            "fgmres_gs": timed_solve(g, L, b, st, mode=hhg.SOLVE_FGMRES, nu1=1, nu2=1,
                                     smoother=hhg.SMOOTH_GS),
-           "fp64_mg": timed_solve(g, L, b, st, mode=hhg.SOLVE_MG)}
+           "fp64_mg": timed_solve(g, L, b, st, mode=hhg.SOLVE_MG),
+           "cnn_roofline": cnn_roofline(g, L, info, dev)}
     g.close()
     return out
+
+
+def cnn_roofline(g, L, info, dev, reps=20):
+    """The trained network applied on level L (face scale, clear and the
+    tensor-core kernel), timed by CUDA events on the launching stream,
+    against the measured dense BF16 peak; flops = the network's own
+    2 (27 + 144) 16 + 2 * 144 multiply-adds per face-interior point (no halo
+    recomputation or padding counted)."""
+    import torch
+    from paper_1805_10167_gb300 import hhg
+    gen = torch.Generator(device=dev).manual_seed(99)
+    s = torch.randn(info.vec_len, dtype=torch.float32, device=dev, generator=gen)
+    d = torch.zeros_like(s)
+    for _ in range(3):
+        g.learned_apply(L, s, d=d, prec=hhg.F32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.learned_apply(L, s, d=d, prec=hhg.F32)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    pts = info.n_faces * (info.N - 1) * (info.N - 2) // 2
+    tflops = 2 * (3 * 9 * 16 + 16 * 9 * 16 + 16 * 9) * pts / (ms / 1e3) / 1e12
+    peak = _peaks().get("bf16_tflops")
+    basis = "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst), of measured"
+    if not peak:
+        peak, basis = 1900.0, "1.9 PFLOP/s bf16 burst, of fallback"
+    return {"bound": "tensor", "kernel": "k_cnn_smooth (3 layers, mma.sync BF16, FP32 accumulate)",
+            "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+            "ms_per_application": ms, "peak_basis": basis}
+
+
+def _peaks():
+    """The measured peaks of the GB300s, {} when absent."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
 
 
 def run_reference(args):
@@ -537,10 +581,44 @@ def run_sweep_case(args):
     print("sweep case done")
 
 
+def run_cnn_case(args):
+    """The learned smoother's network (k_cnn_smooth) on every face of level
+    --level of the variable-coefficient 128-face annulus: --warmup untimed
+    and --steps timed applications to a random FP32 scaled residual, with
+    seeded random weights (the cost does not depend on their values)."""
+    import torch
+    from paper_1805_10167_gb300 import hhg
+    dev = torch.device("cuda:0")
+    L = args.level
+    g, info, _ = vark_mesh(L, dev, None)
+    rng = np.random.default_rng(0)
+    g.learned_set_weights((0.1 * rng.standard_normal(hhg.LEARNED_NPARAMS)).astype(np.float32))
+    gen = torch.Generator(device="cuda").manual_seed(1234)
+    s = torch.randn(info.vec_len, dtype=torch.float32, device=dev, generator=gen)
+    d = torch.zeros_like(s)
+    for _ in range(args.warmup):
+        g.learned_apply(L, s, d=d, prec=hhg.F32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        g.learned_apply(L, s, d=d, prec=hhg.F32)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    pts = info.n_faces * (info.N - 1) * (info.N - 2) // 2
+    flop = 2 * (3 * 9 * 16 + 16 * 9 * 16 + 16 * 9 * 1) * pts
+    print(f"cnn case: level {L}, {pts} face-interior points, {ms:.3f} ms per application "
+          f"(face scale, clear, network), {flop / ms / 1e9:.1f} TFLOP/s of the network's own flops")
+    g.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.case == "sweep":
         run_sweep_case(a)
+    elif a.case == "cnn":
+        run_cnn_case(a)
     elif a.impl == "reference":
         run_reference(a)
     else:
