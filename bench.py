@@ -487,28 +487,50 @@ def run_ours(args):
     # end to end through the public API from pinned host memory
     b_host = b_canon.cpu().pin_memory()
     nrm_host = torch.zeros(1, dtype=torch.float64).pin_memory()
-    b_stage = torch.empty_like(b_canon)
     x.zero_()
+    # Two staging vectors and a copy stream: the host->device copy of step
+    # k + 1's right-hand side runs while step k computes.  Step k waits for
+    # its own copy; a staging vector is refilled only after the canonical
+    # conversion that read it.
+    copy_st = torch.cuda.Stream(device=dev)
+    stages = [torch.empty_like(b_canon), torch.empty_like(b_canon)]
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    consumed = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def e2e_step():
-        b_stage.copy_(b_host, non_blocking=True)
-        g.from_canonical(L, b_stage, b, stream=st)
-        step()
-        nrm_host.copy_(nrm, non_blocking=True)
+    def upload(k):
+        s = k % 2
+        copy_st.wait_event(consumed[s])
+        with torch.cuda.stream(copy_st):
+            stages[s].copy_(b_host, non_blocking=True)
+        copied[s].record(copy_st)
 
-    for _ in range(args.warmup):
-        e2e_step()
+    def e2e_steps(n):
+        for ev in consumed:
+            ev.record(st)
+        upload(0)
+        for k in range(n):
+            if k + 1 < n:
+                upload(k + 1)
+            s = k % 2
+            st.wait_event(copied[s])
+            g.from_canonical(L, stages[s], b, stream=st)
+            consumed[s].record(st)
+            step()
+            nrm_host.copy_(nrm, non_blocking=True)
+
+    e2e_steps(args.warmup)
     torch.cuda.synchronize()
     barrier()
     e0.record(st)
-    for _ in range(args.steps):
-        e2e_step()
+    e2e_steps(args.steps)
     e1.record(st)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1))
     e2e = {"value": job_rate(world, n_free, args.steps, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": int(b_host.numel() * 8), "d2h_bytes_per_step": 8,
-           "ms_per_step": ms_e2e / args.steps}
+           "ms_per_step": ms_e2e / args.steps,
+           "pipeline": "each step: pinned host b -> device (second stream, overlapping the previous "
+                       "step), canonical -> internal layout, V(3,3), residual norm -> pinned host"}
 
     # time to a 1e-10 relative FP64 residual: FP64 MG vs FP32-in-FP64 IR
     solve = None
