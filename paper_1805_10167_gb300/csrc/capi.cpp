@@ -431,6 +431,7 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
       int used = 0;
       hhg::fgmres_solve(m, level, x, b, o, o.smoother, o.restart > 0 ? o.restart : 20, rep, &used, S(stream));
       if (rep) rep->smoother_used = used;
+      if (device_timed_out(m, S(stream))) return fail(HHG_ERR_TIMEOUT, "a device-side wait gave up");
       return HHG_OK;
     }
     cudaStream_t st = S(stream);

@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 
 #include "hhg_internal.h"
+#include "umma.cuh"
 
 namespace hhg {
 
@@ -60,24 +61,34 @@ __device__ __forceinline__ bool interior_pt(int i, int j, int N) { return i >= 1
 
 // --------------------------------------------------------------- smoother
 // One CTA = an 8 x 32 output tile of one face.  Input region 14 x 38, h1
-// region 12 x 36, h2 region 10 x 34, all BF16 in shared memory, channel-last.
-// All three layers run on the tensor cores (mma.sync m16n8k16, BF16 inputs,
-// FP32 accumulators) as implicit GEMMs over chunks of 16 points of the
-// layer's output region:
-//   layer 1: A[p][k] = X[p + tap(k / 4)][k % 4], k over 9 taps x 4 channels
-//            (the 3 inputs and a zero channel), padded to 48 (3 k-steps);
-//   layer 2: per tap, A[p][c] = h1[p + tap][c] (16 channels), 9 k-steps,
-//            two n-blocks of 8 output channels;
-//   layer 3: per tap, A[p][c] = h2[p + tap][c], one n-block whose column 0
-//            is the single output channel (columns 1-7 have zero weights).
-// B fragments are packed in lane order once per weight load (k_pack_frags),
-// so each lane reads its own with coalesced loads.  h1 and h2 keep 48 bytes
-// per point (16 channels and padding): the eight 16-byte rows that one
-// ldmatrix phase reads from consecutive points then fall in distinct banks.
+// region 12 x 36, h2 region 10 x 34, all BF16 in shared memory.  All three
+// layers run on the tensor cores as implicit GEMMs (BF16 inputs, FP32
+// accumulators):
+//   layer 1 (mma.sync m16n8k16, chunks of 16 points): A[p][k] =
+//            X[p + tap(k / 4)][k % 4], k over 9 taps x 4 channels (the 3
+//            inputs and a zero channel), padded to 48 (3 k-steps);
+//   layer 2 (tcgen05.mma, M = 128, N = 16, K = 16, accumulator in tensor
+//            memory): for the rows m = 0..383 of the h1-linear index
+//            (row jj * 36 + ii is h2 point (jj, ii); rows with ii >= 34 are
+//            computed and dropped) and each tap t, A_t = the 128 rows of h1
+//            starting at m0 + jj(t) * 36 + ii(t): a shifted window of h1,
+//            which is stored as two planes (channels 0-7 and 8-15, 16 bytes
+//            per point) so that every window is a K-major operand without
+//            swizzling; 3 row blocks x 9 taps, issued by one thread;
+//   layer 3 (mma.sync, chunks of 16 output points): per tap, A[p][c] =
+//            h2[p + tap][c], one n-block whose column 0 is the single output
+//            channel (columns 1-7 have zero weights).
+// B operands are packed once per weight load (k_pack_frags): the mma.sync
+// fragments in lane order (coalesced per-lane loads), the tcgen05 operand in
+// its core-matrix layout.  h2 keeps 48 bytes per point (16 channels and
+// padding): the eight 16-byte rows that one ldmatrix phase reads from
+// consecutive points then fall in distinct banks.
 
-constexpr int kPS = 24;                               // BF16 slots per point in h1, h2
-constexpr int kF1 = 0, kF2 = 3 * 2 * 2 * 32, kF3 = kF2 + 9 * 2 * 2 * 32;
-constexpr int kFrag = kF3 + 9 * 2 * 32;               // packed B fragments (uint32)
+constexpr int kPS = 24;                               // BF16 slots per point in h2
+constexpr int kF1 = 0, kF3 = 3 * 2 * 2 * 32, kFU = kF3 + 9 * 2 * 32;
+constexpr int kFrag = kFU + 9 * 128;                  // packed weights (uint32)
+static_assert(kFU % 4 == 0, "the tcgen05 operand is copied as 16-byte words");
+constexpr long kUmmaPolls = 1L << 22;                 // mbarrier polls before a product is given up
 
 // D += A * B for one m16n8k16 block (BF16 inputs, FP32 accumulators).
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -113,13 +124,17 @@ __device__ __forceinline__ uint32_t relu_pack(float lo, float hi, bool in) {
 
 constexpr int J0 = TJ + 6, I0 = TI + 6, J1 = TJ + 4, I1 = TI + 4, J2 = TJ + 2, I2 = TI + 2;
 constexpr int NP0 = J0 * I0, NP1 = J1 * I1, NP2 = J2 * I2, NP3 = TJ * TI;
+constexpr int kMB = 3;                                // 128-row blocks of layer 2
+constexpr int NP1P = 464;                             // h1 plane length: the windows' reach, padded
+static_assert(kMB * 128 >= (J2 - 1) * I1 + I2, "layer-2 rows cover the h2 region");
+static_assert(NP1P >= kMB * 128 + 2 * I1 + 2 && NP1P >= NP1, "layer-2 windows stay inside the h1 planes");
 static_assert(NP1 % 16 == 0, "layer-1 region is a whole number of 16-point chunks");
 static_assert(TI % 16 == 0, "output rows are whole chunks");
 
 // Layer 1 (3 -> 16) on NC chunks of 16 points of the h1 region at once (NC
 // independent accumulator chains hide the mma latency).
 template <int NC>
-__device__ __forceinline__ void cnn_layer1(const int (&chunk)[NC], const uint32_t* X, __nv_bfloat16 (*h1)[kPS],
+__device__ __forceinline__ void cnn_layer1(const int (&chunk)[NC], const uint32_t* X, uint32_t* h1w,
                                            const uint32_t (&bf)[3][2][2], const float (&bias)[2][2], int i0,
                                            int j0, int N, int g, int tq) {
   int pa[NC], pb[NC];
@@ -160,53 +175,9 @@ __device__ __forceinline__ void cnn_layer1(const int (&chunk)[NC], const uint32_
       const int q = chunk[u] * 16 + g + 8 * h;
       const int jj = q / I1, ii = q - jj * I1;
       const bool in = closed_pt(i0 - 2 + ii, j0 - 2 + jj, N);
-      uint32_t* row = reinterpret_cast<uint32_t*>(&h1[q][0]);
-      row[tq] = relu_pack(d[u][0][2 * h], d[u][0][2 * h + 1], in);
-      row[tq + 4] = relu_pack(d[u][1][2 * h], d[u][1][2 * h + 1], in);
-    }
-}
-
-// Layer 2 (16 -> 16) on NC chunks of the h2 region (the last chunk may be
-// ragged: its rows past the region repeat the last point and are not stored).
-template <int NC>
-__device__ __forceinline__ void cnn_layer2(const int (&chunk)[NC], __nv_bfloat16 (*h1)[kPS],
-                                           __nv_bfloat16 (*h2)[kPS], const uint32_t (&bf)[9][2][2],
-                                           const float (&bias)[2][2], int i0, int j0, int N, int g, int tq,
-                                           int lrow, int lhalf) {
-  int pr[NC];
-  float d[NC][2][4];
-#pragma unroll
-  for (int u = 0; u < NC; ++u) {
-    const int qr = min(chunk[u] * 16 + lrow, NP2 - 1);
-    const int jr = qr / I2;
-    pr[u] = jr * I1 + (qr - jr * I2);                    // window origin in h1
-#pragma unroll
-    for (int nb = 0; nb < 2; ++nb) {
-      d[u][nb][0] = d[u][nb][2] = bias[nb][0];
-      d[u][nb][1] = d[u][nb][3] = bias[nb][1];
-    }
-  }
-#pragma unroll
-  for (int t = 0; t < 9; ++t)
-#pragma unroll
-    for (int u = 0; u < NC; ++u) {
-      uint32_t afr[4];
-      ldsm_x4(afr, &h1[pr[u] + (t / 3) * I1 + t % 3][lhalf]);
-      mma_bf16(d[u][0], afr, bf[t][0][0], bf[t][0][1]);
-      mma_bf16(d[u][1], afr, bf[t][1][0], bf[t][1][1]);
-    }
-#pragma unroll
-  for (int u = 0; u < NC; ++u)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int q = chunk[u] * 16 + g + 8 * h;
-      if (q < NP2) {
-        const int jj = q / I2, ii = q - jj * I2;
-        const bool in = closed_pt(i0 - 1 + ii, j0 - 1 + jj, N);
-        uint32_t* row = reinterpret_cast<uint32_t*>(&h2[q][0]);
-        row[tq] = relu_pack(d[u][0][2 * h], d[u][0][2 * h + 1], in);
-        row[tq + 4] = relu_pack(d[u][1][2 * h], d[u][1][2 * h + 1], in);
-      }
+      // plane 0: channels 0-7, plane 1: channels 8-15 (4 words per point)
+      h1w[q * 4 + tq] = relu_pack(d[u][0][2 * h], d[u][0][2 * h + 1], in);
+      h1w[NP1P * 4 + q * 4 + tq] = relu_pack(d[u][1][2 * h], d[u][1][2 * h + 1], in);
     }
 }
 
@@ -256,13 +227,16 @@ __device__ __forceinline__ void cnn_layer3(const int (&chunk)[NC], __nv_bfloat16
 // micro-triangle at (i, j)), zero where a triangle does not exist; NULL for
 // k = 1.
 template <typename T>
-__global__ void __launch_bounds__(TJ* TI)
+__global__ void __launch_bounds__(TJ* TI, 4)
     k_cnn_smooth(LevelView L, const float* __restrict__ s, const uint32_t* __restrict__ logk,
                  const float* __restrict__ scale, const uint32_t* __restrict__ frag,
-                 const float* __restrict__ wr, T* x, float* delta) {
+                 const float* __restrict__ wr, T* x, float* delta, int* err) {
   __shared__ __align__(16) uint2 xin[NP0];                 // 4 BF16 channels per point
-  __shared__ __align__(16) __nv_bfloat16 h1[NP1][kPS];
+  __shared__ __align__(128) uint4 h1p[2][NP1P];            // h1: channels 0-7 | 8-15, 16 B per point
+  __shared__ __align__(128) uint4 w2s[9 * 32];             // layer-2 weights, tcgen05 operand layout
   __shared__ __align__(16) __nv_bfloat16 h2[NP2][kPS];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
   const int f = blockIdx.z;
   const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
   const int N = L.N;
@@ -273,6 +247,16 @@ __global__ void __launch_bounds__(TJ* TI)
   const int64_t fb = L.f_off + (int64_t)f * L.FS;
   const uint32_t* lk = logk ? logk + (int64_t)f * L.FS : nullptr;
   const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = TJ * TI / 32;
+  if (warp == 0) {   // 64 tensor-memory columns: layer 2's three 128 x 16 accumulators
+    tmem_alloc(&tslot, 64);
+    tmem_relinquish();
+  }
+  if (tid == 32) {
+    mbar_init(&mbar, 1);
+    mbar_init_fence();
+  }
   for (int q = tid; q < NP0; q += TJ * TI) {
     const int jj = q / I0, ii = q - jj * I0;
     const int i = i0 - 3 + ii, j = j0 - 3 + jj;
@@ -286,12 +270,16 @@ __global__ void __launch_bounds__(TJ* TI)
     // channels (residual, log k up | log k down, 0)
     xin[q] = make_uint2((pack_bf16(a, 0.f) & 0xffffu) | (kk << 16), kk >> 16);
   }
-  const int lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = TJ * TI / 32;
+  {
+    const uint4* wsrc = reinterpret_cast<const uint4*>(frag + kFU);
+    for (int q = tid; q < 9 * 32; q += TJ * TI) w2s[q] = wsrc[q];
+    for (int q = tid; q < 2 * (NP1P - NP1); q += TJ * TI)   // finite values under the windows' reach
+      h1p[q / (NP1P - NP1)][NP1 + q % (NP1P - NP1)] = make_uint4(0u, 0u, 0u, 0u);
+  }
   const int g = lane >> 2, tq = lane & 3;
   // ldmatrix row of this lane: point offset in a chunk and channel half
   const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lhalf = (lane >> 4) * 8;
-  {
+  {  // layer 1: 3 -> 16 (mma.sync)
     uint32_t bf[3][2][2];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -301,33 +289,92 @@ __global__ void __launch_bounds__(TJ* TI)
         for (int h = 0; h < 2; ++h) bf[k][nb][h] = frag[kF1 + ((k * 2 + nb) * 2 + h) * 32 + lane];
     const float bias[2][2] = {{wr[ob1 + 2 * tq], wr[ob1 + 2 * tq + 1]}, {wr[ob1 + 8 + 2 * tq], wr[ob1 + 9 + 2 * tq]}};
     const uint32_t* X = reinterpret_cast<const uint32_t*>(xin);
+    uint32_t* h1w = reinterpret_cast<uint32_t*>(&h1p[0][0]);
     __syncthreads();
     int c = warp;
-    for (; c + NW < NP1 / 16; c += 2 * NW) cnn_layer1<2>({c, c + NW}, X, h1, bf, bias, i0, j0, N, g, tq);
-    if (c < NP1 / 16) cnn_layer1<1>({c}, X, h1, bf, bias, i0, j0, N, g, tq);
+    for (; c + NW < NP1 / 16; c += 2 * NW) cnn_layer1<2>({c, c + NW}, X, h1w, bf, bias, i0, j0, N, g, tq);
+    if (c < NP1 / 16) cnn_layer1<1>({c}, X, h1w, bf, bias, i0, j0, N, g, tq);
   }
-  {
-    uint32_t bf[9][2][2];
+  // layer 2: 16 -> 16 (tcgen05).  The generic-proxy writes of h1 and of the
+  // weights are made visible to the tensor cores' reads, then one thread
+  // issues the 27 products and commits them to the mbarrier.
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = tslot;
+  if (tid == 0) {
+    constexpr uint32_t idesc = idesc_bf16_f32(128, 16);
+#pragma unroll 1
+    for (int mb = 0; mb < kMB; ++mb)
 #pragma unroll
-    for (int t = 0; t < 9; ++t)
-#pragma unroll
-      for (int nb = 0; nb < 2; ++nb)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) bf[t][nb][h] = frag[kF2 + ((t * 2 + nb) * 2 + h) * 32 + lane];
-    const float bias[2][2] = {{wr[ob2 + 2 * tq], wr[ob2 + 2 * tq + 1]}, {wr[ob2 + 8 + 2 * tq], wr[ob2 + 9 + 2 * tq]}};
-    __syncthreads();
-    constexpr int NC2 = (NP2 + 15) / 16;
-    int c = warp;
-    for (; c + NW < NC2; c += 2 * NW) cnn_layer2<2>({c, c + NW}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
-    if (c < NC2) cnn_layer2<1>({c}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
+      for (int t = 0; t < 9; ++t)
+        umma_bf16(taddr + 16 * mb, smem_desc_kmajor(&h1p[0][mb * 128 + (t / 3) * I1 + t % 3], NP1P * 16, 128),
+                  smem_desc_kmajor(&w2s[t * 32], 128, 256), idesc, t > 0);
+    umma_commit(&mbar);
   }
-  uint32_t bf[9][2];
+  uint32_t bf[9][2];   // layer-3 fragments, loaded while the products run
 #pragma unroll
   for (int t = 0; t < 9; ++t)
 #pragma unroll
     for (int h = 0; h < 2; ++h) bf[t][h] = frag[kF3 + (t * 2 + h) * 32 + lane];
   const float b3 = wr[ob3];
+  // the issuing thread waits for the products (bounded); the others wait at
+  // the CTA barrier, taking no issue slots from the SM's other CTAs
+  bool done = true;
+  if (tid == 0) {
+    done = false;
+    for (long it = 0; it < kUmmaPolls; ++it)
+      if (mbar_try_wait(&mbar, 0)) {
+        done = true;
+        break;
+      }
+  }
+  if (!__syncthreads_and(done)) {
+    // the products did not complete in time: report it, wait once more
+    // (bounded) so that none is in flight, free the columns, leave the tile
+    if (tid == 0) {
+      atomicExch(err, 1);
+      for (long it = 0; it < kUmmaPolls; ++it)
+        if (mbar_try_wait(&mbar, 0)) break;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tc_fence_after();
+      tmem_dealloc(taddr, 64);
+    }
+    return;
+  }
+  tc_fence_after();
+  {  // accumulator rows -> bias, relu, closed-triangle mask, BF16 -> h2
+    float b2[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) b2[o] = wr[ob2 + o];
+    for (int u = warp; u < 4 * kMB; u += NW) {   // (row block, lane quarter); quarter = warp % 4
+      const int mb = u >> 2, qq = u & 3;
+      float v[16];
+      tmem_ld16(taddr + ((uint32_t)(qq * 32) << 16) + 16 * mb, v);
+      const int m = mb * 128 + qq * 32 + lane;
+      const int jj = m / I1, ii = m - jj * I1;
+      if (jj < J2 && ii < I2) {
+        const bool in = closed_pt(i0 - 1 + ii, j0 - 1 + jj, N);
+        uint32_t w[8];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) w[o] = relu_pack(v[2 * o] + b2[2 * o], v[2 * o + 1] + b2[2 * o + 1], in);
+        uint4* dst = reinterpret_cast<uint4*>(&h2[jj * I2 + ii][0]);
+        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      }
+    }
+  }
+  tc_fence_before();
   __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(taddr, 64);
+  }
+  // layer 3: 16 -> 1 (mma.sync)
   int c = warp;
   for (; c + NW < NP3 / 16; c += 2 * NW)
     cnn_layer3<2, T>({c, c + NW}, h2, bf, b3, sig, fb, S, i0, j0, N, g, tq, lrow, lhalf, x, delta);
@@ -349,19 +396,26 @@ __global__ void k_logk_pack(LevelView L, int nf, const float* __restrict__ k, ui
   }
 }
 
-// Weights of one layer as mma.sync B fragments in lane order (one thread per
-// entry; lane = e % 32, g = lane / 4, tq = lane % 4, column n = g of the
-// n-block, k pair 2 tq + 8 h, + 1):
-//   layer 1, entry ((k * 2 + nb) * 2 + h) * 32 + lane: output channel
-//            nb * 8 + g, k = 16 k-step + 2 tq + 8 h = 4 tap + channel
-//            (zero for channel 3 and taps 9-11);
-//   layer 2, entry ((t * 2 + nb) * 2 + h) * 32 + lane: output channel
-//            nb * 8 + g, input channels 2 tq + 8 h, + 1 at tap t;
-//   layer 3, entry (t * 2 + h) * 32 + lane: input channels 2 tq + 8 h, + 1 at
-//            tap t for column 0 (g = 0), zero for the other columns.
+// Weights packed once per load (one thread per uint32 entry; lane = e % 32,
+// g = lane / 4, tq = lane % 4):
+//   layer 1 (mma.sync B fragments), entry ((k * 2 + nb) * 2 + h) * 32 + lane:
+//            output channel nb * 8 + g, k pair 16 k + 2 tq + 8 h, + 1 where
+//            k = 4 tap + channel (zero for channel 3 and taps 9-11);
+//   layer 3 (mma.sync B fragments), entry (t * 2 + h) * 32 + lane: input
+//            channels 2 tq + 8 h, + 1 at tap t for column 0 (g = 0), zero for
+//            the other columns;
+//   layer 2 (tcgen05 B operand, K-major, no swizzle), per tap t 256 BF16 at
+//            element (n / 8) * 128 + (k / 8) * 64 + (n % 8) * 8 + k % 8 for
+//            output channel n and input channel k: 8 x 8 core matrices, 128
+//            bytes apart along K and 256 bytes apart along N.
 __device__ __forceinline__ float w1_at(const float* wr, int o, int k) {
   const int t = k >> 2, c = k & 3;
   return (t < 9 && c < 3) ? wr[oW1 + o * 27 + c * 9 + t] : 0.f;
+}
+
+__device__ __forceinline__ float w2_core(const float* wr, int t, int el) {
+  const int n = (el >> 7) * 8 + ((el >> 3) & 7), k = ((el >> 6) & 1) * 8 + (el & 7);
+  return wr[oW2 + n * 144 + k * 9 + t];
 }
 
 __global__ void k_pack_frags(const float* __restrict__ wr, uint32_t* frag) {
@@ -369,23 +423,22 @@ __global__ void k_pack_frags(const float* __restrict__ wr, uint32_t* frag) {
   if (e >= kFrag) return;
   const int lane = e & 31, g = lane >> 2, tq = lane & 3;
   float lo = 0.f, hi = 0.f;
-  if (e < kF2) {
+  if (e < kF3) {
     const int r = (e - kF1) >> 5, h = r & 1, nb = (r >> 1) & 1, k = r >> 2;
     const int o = nb * 8 + g, kk = k * 16 + 2 * tq + 8 * h;
     lo = w1_at(wr, o, kk);
     hi = w1_at(wr, o, kk + 1);
-  } else if (e < kF3) {
-    const int r = (e - kF2) >> 5, h = r & 1, nb = (r >> 1) & 1, t = r >> 2;
-    const int o = nb * 8 + g, c = 2 * tq + 8 * h;
-    lo = wr[oW2 + o * 144 + c * 9 + t];
-    hi = wr[oW2 + o * 144 + (c + 1) * 9 + t];
-  } else {
+  } else if (e < kFU) {
     const int r = (e - kF3) >> 5, h = r & 1, t = r >> 1;
     const int c = 2 * tq + 8 * h;
     if (g == 0) {
       lo = wr[oW3 + c * 9 + t];
       hi = wr[oW3 + (c + 1) * 9 + t];
     }
+  } else {
+    const int w = e - kFU, t = w >> 7, el = 2 * (w & 127);
+    lo = w2_core(wr, t, el);
+    hi = w2_core(wr, t, el + 1);
   }
   frag[e] = pack_bf16(lo, hi);
 }
@@ -824,9 +877,9 @@ void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, 
   k_face_rms<<<m.nf, 256, 0, st>>>(m.tab, lv, s, L.scale);
   if (delta) check_cuda(cudaMemsetAsync(delta, 0, (size_t)lv.len * sizeof(float), st), "delta clear");
   if (prec == 0)
-    k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (double*)x, delta);
+    k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (double*)x, delta, m.err);
   else
-    k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (float*)x, delta);
+    k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (float*)x, delta, m.err);
   check_cuda(cudaGetLastError(), "cnn smooth");
 }
 
