@@ -604,10 +604,11 @@ def run_sweep_case(args):
 
 
 def run_cnn_case(args):
-    """The learned smoother's network (k_cnn_smooth) on every face of level
-    --level of the variable-coefficient 128-face annulus: --warmup untimed
-    and --steps timed applications to a random FP32 scaled residual, with
-    seeded random weights (the cost does not depend on their values)."""
+    """The learned smoother's network on every face of level --level of the
+    variable-coefficient 128-face annulus, on each tensor-core path
+    (k_cnn_smooth, then k_cnn_smooth_tc): --warmup untimed and --steps timed
+    applications to a random FP32 scaled residual, with seeded random weights
+    (the cost does not depend on their values)."""
     import torch
     from paper_1805_10167_gb300 import hhg
     dev = torch.device("cuda:0")
@@ -618,20 +619,23 @@ def run_cnn_case(args):
     gen = torch.Generator(device="cuda").manual_seed(1234)
     s = torch.randn(info.vec_len, dtype=torch.float32, device=dev, generator=gen)
     d = torch.zeros_like(s)
-    for _ in range(args.warmup):
-        g.learned_apply(L, s, d=d, prec=hhg.F32)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        g.learned_apply(L, s, d=d, prec=hhg.F32)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / max(args.steps, 1)
     pts = info.n_faces * (info.N - 1) * (info.N - 2) // 2
     flop = 2 * (3 * 9 * 16 + 16 * 9 * 16 + 16 * 9 * 1) * pts
-    print(f"cnn case: level {L}, {pts} face-interior points, {ms:.3f} ms per application "
-          f"(face scale, clear, network), {flop / ms / 1e9:.1f} TFLOP/s of the network's own flops")
+    for name, path in (("mma.sync", hhg.TC_MMA_SYNC), ("tcgen05 layer 2", hhg.TC_TCGEN05)):
+        g.learned_tensor_path(path)
+        for _ in range(args.warmup):
+            g.learned_apply(L, s, d=d, prec=hhg.F32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            g.learned_apply(L, s, d=d, prec=hhg.F32)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(args.steps, 1)
+        print(f"cnn case ({name}): level {L}, {pts} face-interior points, {ms:.3f} ms per application "
+              f"(face scale, clear, network), {flop / ms / 1e9:.1f} TFLOP/s of the network's own flops")
+    g.learned_tensor_path(hhg.TC_MMA_SYNC)
     g.close()
 
 

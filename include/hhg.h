@@ -348,6 +348,18 @@ hhg_status hhg_learned_get_weights(hhg_mesh mesh, float* w_host, int64_t n);
  * x += d there. */
 hhg_status hhg_learned_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const float* s,
                              void* x, float* d, void* stream);
+/* Tensor-core path of the network kernel (not in the paper): reads it
+ * (set == 0: *path is written) or sets it (set != 0: *path is an input).
+ * HHG_TC_MMA_SYNC (default): all three layers on mma.sync.m16n8k16;
+ * HHG_TC_TCGEN05: layer 2 (16 -> 16, 80 % of the flops) on tcgen05.mma with
+ * its accumulator in tensor memory (64 columns per CTA), layers 1 and 3 on
+ * mma.sync.  Both give the network's result within BF16 rounding; the
+ * first is faster on GB300.  A tcgen05 product that does not complete
+ * within its bounded wait sets the mesh's device error word, which the next
+ * hhg_solve reports as HHG_ERR_TIMEOUT.  HHG_ERR_ARG for another value.
+ * Synchronous with respect to the host. */
+typedef enum { HHG_TC_MMA_SYNC = 0, HHG_TC_TCGEN05 = 1 } hhg_tensor_path;
+hhg_status hhg_learned_tensor_path(hhg_mesh mesh, int32_t set, int32_t* path);
 /* Mean training loss and its gradient w.r.t. the weights over n_crops
  * 64 x 64 crops (FP32 DEVICE arrays): X (n_crops, 3, 64, 64) the network
  * input, S (n_crops, 64, 64) the normalised scaled residual, K (n_crops, 2,

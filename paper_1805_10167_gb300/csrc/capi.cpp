@@ -634,6 +634,16 @@ hhg_status hhg_learned_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const 
   });
 }
 
+hhg_status hhg_learned_tensor_path(hhg_mesh mesh, int32_t set, int32_t* path) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    need(path, "path");
+    if (set && *path != HHG_TC_MMA_SYNC && *path != HHG_TC_TCGEN05) throw ArgError("bad tensor path");
+    *path = hhg::learned_tensor_path(m, set, *path);
+    return HHG_OK;
+  });
+}
+
 hhg_status hhg_learned_grad(hhg_mesh mesh, int32_t n_crops, const float* X, const float* Sres,
                             const float* K, const int32_t* crops_host, float* grad_host,
                             float* loss_host, void* stream) {

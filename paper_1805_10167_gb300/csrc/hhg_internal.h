@@ -335,6 +335,8 @@ void vcycle_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1,
                 int smoother, cudaStream_t st);
 // learned smoother and FGMRES
 bool learned_ready(const Mesh& m);
+// reads, or sets when set != 0, the network kernel's tensor-core path
+int learned_tensor_path(Mesh& m, int set, int path);
 void learned_free(Mesh& m);
 void learned_set_weights(Mesh& m, const float* w_host, cudaStream_t st);
 void learned_get_weights(Mesh& m, float* w_host);

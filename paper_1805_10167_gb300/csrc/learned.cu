@@ -29,6 +29,7 @@
 #include <cmath>
 #include <cstring>
 #include <random>
+#include <stdexcept>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -61,31 +62,39 @@ __device__ __forceinline__ bool interior_pt(int i, int j, int N) { return i >= 1
 
 // --------------------------------------------------------------- smoother
 // One CTA = an 8 x 32 output tile of one face.  Input region 14 x 38, h1
-// region 12 x 36, h2 region 10 x 34, all BF16 in shared memory.  All three
-// layers run on the tensor cores as implicit GEMMs (BF16 inputs, FP32
-// accumulators):
-//   layer 1 (mma.sync m16n8k16, chunks of 16 points): A[p][k] =
-//            X[p + tap(k / 4)][k % 4], k over 9 taps x 4 channels (the 3
-//            inputs and a zero channel), padded to 48 (3 k-steps);
-//   layer 2 (tcgen05.mma, M = 128, N = 16, K = 16, accumulator in tensor
-//            memory): for the rows m = 0..383 of the h1-linear index
-//            (row jj * 36 + ii is h2 point (jj, ii); rows with ii >= 34 are
-//            computed and dropped) and each tap t, A_t = the 128 rows of h1
-//            starting at m0 + jj(t) * 36 + ii(t): a shifted window of h1,
-//            which is stored as two planes (channels 0-7 and 8-15, 16 bytes
-//            per point) so that every window is a K-major operand without
-//            swizzling; 3 row blocks x 9 taps, issued by one thread;
-//   layer 3 (mma.sync, chunks of 16 output points): per tap, A[p][c] =
-//            h2[p + tap][c], one n-block whose column 0 is the single output
-//            channel (columns 1-7 have zero weights).
-// B operands are packed once per weight load (k_pack_frags): the mma.sync
-// fragments in lane order (coalesced per-lane loads), the tcgen05 operand in
-// its core-matrix layout.  h2 keeps 48 bytes per point (16 channels and
-// padding): the eight 16-byte rows that one ldmatrix phase reads from
-// consecutive points then fall in distinct banks.
+// region 12 x 36, h2 region 10 x 34, all BF16 in shared memory, channel-last.
+// All three layers run on the tensor cores (mma.sync m16n8k16, BF16 inputs,
+// FP32 accumulators) as implicit GEMMs over chunks of 16 points of the
+// layer's output region:
+//   layer 1: A[p][k] = X[p + tap(k / 4)][k % 4], k over 9 taps x 4 channels
+//            (the 3 inputs and a zero channel), padded to 48 (3 k-steps);
+//   layer 2: per tap, A[p][c] = h1[p + tap][c] (16 channels), 9 k-steps,
+//            two n-blocks of 8 output channels;
+//   layer 3: per tap, A[p][c] = h2[p + tap][c], one n-block whose column 0
+//            is the single output channel (columns 1-7 have zero weights).
+// B fragments are packed in lane order once per weight load (k_pack_frags),
+// so each lane reads its own with coalesced loads.  h1 and h2 keep 48 bytes
+// per point (16 channels and padding): the eight 16-byte rows that one
+// ldmatrix phase reads from consecutive points then fall in distinct banks.
+//
+// Opt-in variant (k_cnn_smooth_tc, hhg_learned_tensor_path): layer 2 on the
+// fifth-generation tensor cores, tcgen05.mma with M = 128, N = 16, K = 16 and
+// the accumulator in tensor memory.  For the rows m = 0..383 of the
+// h1-linear index (row jj * 36 + ii is h2 point (jj, ii); rows with ii >= 34
+// are computed and dropped) and each tap t, A_t is the 128 rows of h1
+// starting at m0 + jj(t) * 36 + ii(t): a shifted window of h1, which that
+// kernel stores as two planes (channels 0-7 and 8-15, 16 bytes per point)
+// so that every window is a K-major operand without swizzling; 3 row blocks
+// x 9 taps issued by one thread and committed to an mbarrier, the
+// accumulator read back by tcgen05.ld.  Its weights are packed in the
+// operand's core-matrix layout.  It gives the same results within BF16
+// rounding and is slower on GB300 (the network's time is in staging,
+// layers 1 and 3 and the epilogues; the per-tile allocation, fences and
+// commit round trip cost more than layer 2's share of the mma.sync issue).
 
-constexpr int kPS = 24;                               // BF16 slots per point in h2
-constexpr int kF1 = 0, kF3 = 3 * 2 * 2 * 32, kFU = kF3 + 9 * 2 * 32;
+constexpr int kPS = 24;                               // BF16 slots per point in h1, h2 records
+constexpr int kF1 = 0, kF2 = 3 * 2 * 2 * 32, kF3 = kF2 + 9 * 2 * 2 * 32;
+constexpr int kFU = kF3 + 9 * 2 * 32;                 // tcgen05 layer-2 operand, 9 x 128 words
 constexpr int kFrag = kFU + 9 * 128;                  // packed weights (uint32)
 static_assert(kFU % 4 == 0, "the tcgen05 operand is copied as 16-byte words");
 constexpr long kUmmaPolls = 1L << 22;                 // mbarrier polls before a product is given up
@@ -124,16 +133,19 @@ __device__ __forceinline__ uint32_t relu_pack(float lo, float hi, bool in) {
 
 constexpr int J0 = TJ + 6, I0 = TI + 6, J1 = TJ + 4, I1 = TI + 4, J2 = TJ + 2, I2 = TI + 2;
 constexpr int NP0 = J0 * I0, NP1 = J1 * I1, NP2 = J2 * I2, NP3 = TJ * TI;
-constexpr int kMB = 3;                                // 128-row blocks of layer 2
-constexpr int NP1P = 464;                             // h1 plane length: the windows' reach, padded
+constexpr int kMB = 3;                                // 128-row blocks of the tcgen05 layer 2
+constexpr int NP1P = 464;                             // its h1 plane length: the windows' reach, padded
 static_assert(kMB * 128 >= (J2 - 1) * I1 + I2, "layer-2 rows cover the h2 region");
 static_assert(NP1P >= kMB * 128 + 2 * I1 + 2 && NP1P >= NP1, "layer-2 windows stay inside the h1 planes");
 static_assert(NP1 % 16 == 0, "layer-1 region is a whole number of 16-point chunks");
 static_assert(TI % 16 == 0, "output rows are whole chunks");
 
 // Layer 1 (3 -> 16) on NC chunks of 16 points of the h1 region at once (NC
-// independent accumulator chains hide the mma latency).
-template <int NC>
+// independent accumulator chains hide the mma latency).  h1w: h1 as words;
+// the channel pair (2 w, 2 w + 1) of point q is word q * QS + w, the pair
+// (8 + 2 w, 9 + 2 w) word P1 + q * QS + w (48-byte records: QS = 12, P1 = 4;
+// two planes: QS = 4, P1 = the plane length in words).
+template <int NC, int QS, int P1>
 __device__ __forceinline__ void cnn_layer1(const int (&chunk)[NC], const uint32_t* X, uint32_t* h1w,
                                            const uint32_t (&bf)[3][2][2], const float (&bias)[2][2], int i0,
                                            int j0, int N, int g, int tq) {
@@ -175,9 +187,52 @@ __device__ __forceinline__ void cnn_layer1(const int (&chunk)[NC], const uint32_
       const int q = chunk[u] * 16 + g + 8 * h;
       const int jj = q / I1, ii = q - jj * I1;
       const bool in = closed_pt(i0 - 2 + ii, j0 - 2 + jj, N);
-      // plane 0: channels 0-7, plane 1: channels 8-15 (4 words per point)
-      h1w[q * 4 + tq] = relu_pack(d[u][0][2 * h], d[u][0][2 * h + 1], in);
-      h1w[NP1P * 4 + q * 4 + tq] = relu_pack(d[u][1][2 * h], d[u][1][2 * h + 1], in);
+      h1w[q * QS + tq] = relu_pack(d[u][0][2 * h], d[u][0][2 * h + 1], in);
+      h1w[P1 + q * QS + tq] = relu_pack(d[u][1][2 * h], d[u][1][2 * h + 1], in);
+    }
+}
+
+// Layer 2 (16 -> 16) on NC chunks of the h2 region (the last chunk may be
+// ragged: its rows past the region repeat the last point and are not stored).
+template <int NC>
+__device__ __forceinline__ void cnn_layer2(const int (&chunk)[NC], __nv_bfloat16 (*h1)[kPS],
+                                           __nv_bfloat16 (*h2)[kPS], const uint32_t (&bf)[9][2][2],
+                                           const float (&bias)[2][2], int i0, int j0, int N, int g, int tq,
+                                           int lrow, int lhalf) {
+  int pr[NC];
+  float d[NC][2][4];
+#pragma unroll
+  for (int u = 0; u < NC; ++u) {
+    const int qr = min(chunk[u] * 16 + lrow, NP2 - 1);
+    const int jr = qr / I2;
+    pr[u] = jr * I1 + (qr - jr * I2);                    // window origin in h1
+#pragma unroll
+    for (int nb = 0; nb < 2; ++nb) {
+      d[u][nb][0] = d[u][nb][2] = bias[nb][0];
+      d[u][nb][1] = d[u][nb][3] = bias[nb][1];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 9; ++t)
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      uint32_t afr[4];
+      ldsm_x4(afr, &h1[pr[u] + (t / 3) * I1 + t % 3][lhalf]);
+      mma_bf16(d[u][0], afr, bf[t][0][0], bf[t][0][1]);
+      mma_bf16(d[u][1], afr, bf[t][1][0], bf[t][1][1]);
+    }
+#pragma unroll
+  for (int u = 0; u < NC; ++u)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = chunk[u] * 16 + g + 8 * h;
+      if (q < NP2) {
+        const int jj = q / I2, ii = q - jj * I2;
+        const bool in = closed_pt(i0 - 1 + ii, j0 - 1 + jj, N);
+        uint32_t* row = reinterpret_cast<uint32_t*>(&h2[q][0]);
+        row[tq] = relu_pack(d[u][0][2 * h], d[u][0][2 * h + 1], in);
+        row[tq + 4] = relu_pack(d[u][1][2 * h], d[u][1][2 * h + 1], in);
+      }
     }
 }
 
@@ -227,8 +282,92 @@ __device__ __forceinline__ void cnn_layer3(const int (&chunk)[NC], __nv_bfloat16
 // micro-triangle at (i, j)), zero where a triangle does not exist; NULL for
 // k = 1.
 template <typename T>
-__global__ void __launch_bounds__(TJ* TI, 4)
+__global__ void __launch_bounds__(TJ* TI)
     k_cnn_smooth(LevelView L, const float* __restrict__ s, const uint32_t* __restrict__ logk,
+                 const float* __restrict__ scale, const uint32_t* __restrict__ frag,
+                 const float* __restrict__ wr, T* x, float* delta) {
+  __shared__ __align__(16) uint2 xin[NP0];                 // 4 BF16 channels per point
+  __shared__ __align__(16) __nv_bfloat16 h1[NP1][kPS];
+  __shared__ __align__(16) __nv_bfloat16 h2[NP2][kPS];
+  const int f = blockIdx.z;
+  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
+  const int N = L.N;
+  const float sig = scale[f];
+  if (i0 + j0 > N || !(sig > 0.f)) return;   // tile above the triangle / zero residual (uniform per CTA)
+  const float isig = 1.f / sig;
+  const int64_t S = L.S;
+  const int64_t fb = L.f_off + (int64_t)f * L.FS;
+  const uint32_t* lk = logk ? logk + (int64_t)f * L.FS : nullptr;
+  const int tid = threadIdx.x;
+  for (int q = tid; q < NP0; q += TJ * TI) {
+    const int jj = q / I0, ii = q - jj * I0;
+    const int i = i0 - 3 + ii, j = j0 - 3 + jj;
+    float a = 0.f;
+    uint32_t kk = 0u;
+    if (closed_pt(i, j, N)) {
+      const int64_t p = (int64_t)j * S + i;
+      a = s[fb + p] * isig;
+      if (lk) kk = lk[p];
+    }
+    // channels (residual, log k up | log k down, 0)
+    xin[q] = make_uint2((pack_bf16(a, 0.f) & 0xffffu) | (kk << 16), kk >> 16);
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = TJ * TI / 32;
+  const int g = lane >> 2, tq = lane & 3;
+  // ldmatrix row of this lane: point offset in a chunk and channel half
+  const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lhalf = (lane >> 4) * 8;
+  {
+    uint32_t bf[3][2][2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) bf[k][nb][h] = frag[kF1 + ((k * 2 + nb) * 2 + h) * 32 + lane];
+    const float bias[2][2] = {{wr[ob1 + 2 * tq], wr[ob1 + 2 * tq + 1]}, {wr[ob1 + 8 + 2 * tq], wr[ob1 + 9 + 2 * tq]}};
+    const uint32_t* X = reinterpret_cast<const uint32_t*>(xin);
+    uint32_t* h1w = reinterpret_cast<uint32_t*>(&h1[0][0]);
+    __syncthreads();
+    int c = warp;
+    for (; c + NW < NP1 / 16; c += 2 * NW)
+      cnn_layer1<2, kPS / 2, 4>({c, c + NW}, X, h1w, bf, bias, i0, j0, N, g, tq);
+    if (c < NP1 / 16) cnn_layer1<1, kPS / 2, 4>({c}, X, h1w, bf, bias, i0, j0, N, g, tq);
+  }
+  {
+    uint32_t bf[9][2][2];
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+      for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) bf[t][nb][h] = frag[kF2 + ((t * 2 + nb) * 2 + h) * 32 + lane];
+    const float bias[2][2] = {{wr[ob2 + 2 * tq], wr[ob2 + 2 * tq + 1]}, {wr[ob2 + 8 + 2 * tq], wr[ob2 + 9 + 2 * tq]}};
+    __syncthreads();
+    constexpr int NC2 = (NP2 + 15) / 16;
+    int c = warp;
+    for (; c + NW < NC2; c += 2 * NW) cnn_layer2<2>({c, c + NW}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
+    if (c < NC2) cnn_layer2<1>({c}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
+  }
+  uint32_t bf[9][2];
+#pragma unroll
+  for (int t = 0; t < 9; ++t)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) bf[t][h] = frag[kF3 + (t * 2 + h) * 32 + lane];
+  const float b3 = wr[ob3];
+  __syncthreads();
+  int c = warp;
+  for (; c + NW < NP3 / 16; c += 2 * NW)
+    cnn_layer3<2, T>({c, c + NW}, h2, bf, b3, sig, fb, S, i0, j0, N, g, tq, lrow, lhalf, x, delta);
+  if (c < NP3 / 16) cnn_layer3<1, T>({c}, h2, bf, b3, sig, fb, S, i0, j0, N, g, tq, lrow, lhalf, x, delta);
+}
+
+// The network with layer 2 on tcgen05 (the opt-in variant described above):
+// one CTA per 8 x 32 tile, 64 tensor-memory columns per CTA, at least four
+// CTAs per SM (64 registers a thread).
+template <typename T>
+__global__ void __launch_bounds__(TJ* TI, 4)
+    k_cnn_smooth_tc(LevelView L, const float* __restrict__ s, const uint32_t* __restrict__ logk,
                  const float* __restrict__ scale, const uint32_t* __restrict__ frag,
                  const float* __restrict__ wr, T* x, float* delta, int* err) {
   __shared__ __align__(16) uint2 xin[NP0];                 // 4 BF16 channels per point
@@ -292,8 +431,9 @@ __global__ void __launch_bounds__(TJ* TI, 4)
     uint32_t* h1w = reinterpret_cast<uint32_t*>(&h1p[0][0]);
     __syncthreads();
     int c = warp;
-    for (; c + NW < NP1 / 16; c += 2 * NW) cnn_layer1<2>({c, c + NW}, X, h1w, bf, bias, i0, j0, N, g, tq);
-    if (c < NP1 / 16) cnn_layer1<1>({c}, X, h1w, bf, bias, i0, j0, N, g, tq);
+    for (; c + NW < NP1 / 16; c += 2 * NW)
+      cnn_layer1<2, 4, NP1P * 4>({c, c + NW}, X, h1w, bf, bias, i0, j0, N, g, tq);
+    if (c < NP1 / 16) cnn_layer1<1, 4, NP1P * 4>({c}, X, h1w, bf, bias, i0, j0, N, g, tq);
   }
   // layer 2: 16 -> 16 (tcgen05).  The generic-proxy writes of h1 and of the
   // weights are made visible to the tensor cores' reads, then one thread
@@ -396,23 +536,25 @@ __global__ void k_logk_pack(LevelView L, int nf, const float* __restrict__ k, ui
   }
 }
 
-// Weights packed once per load (one thread per uint32 entry; lane = e % 32,
-// g = lane / 4, tq = lane % 4):
-//   layer 1 (mma.sync B fragments), entry ((k * 2 + nb) * 2 + h) * 32 + lane:
-//            output channel nb * 8 + g, k pair 16 k + 2 tq + 8 h, + 1 where
-//            k = 4 tap + channel (zero for channel 3 and taps 9-11);
-//   layer 3 (mma.sync B fragments), entry (t * 2 + h) * 32 + lane: input
-//            channels 2 tq + 8 h, + 1 at tap t for column 0 (g = 0), zero for
-//            the other columns;
-//   layer 2 (tcgen05 B operand, K-major, no swizzle), per tap t 256 BF16 at
-//            element (n / 8) * 128 + (k / 8) * 64 + (n % 8) * 8 + k % 8 for
-//            output channel n and input channel k: 8 x 8 core matrices, 128
-//            bytes apart along K and 256 bytes apart along N.
+// Weights of one layer as mma.sync B fragments in lane order (one thread per
+// entry; lane = e % 32, g = lane / 4, tq = lane % 4, column n = g of the
+// n-block, k pair 2 tq + 8 h, + 1):
+//   layer 1, entry ((k * 2 + nb) * 2 + h) * 32 + lane: output channel
+//            nb * 8 + g, k = 16 k-step + 2 tq + 8 h = 4 tap + channel
+//            (zero for channel 3 and taps 9-11);
+//   layer 2, entry ((t * 2 + nb) * 2 + h) * 32 + lane: output channel
+//            nb * 8 + g, input channels 2 tq + 8 h, + 1 at tap t;
+//   layer 3, entry (t * 2 + h) * 32 + lane: input channels 2 tq + 8 h, + 1 at
+//            tap t for column 0 (g = 0), zero for the other columns.
 __device__ __forceinline__ float w1_at(const float* wr, int o, int k) {
   const int t = k >> 2, c = k & 3;
   return (t < 9 && c < 3) ? wr[oW1 + o * 27 + c * 9 + t] : 0.f;
 }
 
+// tcgen05 layer-2 operand (K-major, no swizzle), per tap t 256 BF16 at
+// element (n / 8) * 128 + (k / 8) * 64 + (n % 8) * 8 + k % 8 for output
+// channel n and input channel k: 8 x 8 core matrices, 128 bytes apart along
+// K and 256 bytes apart along N; entry kFU + t * 128 + w holds elements 2w, 2w + 1.
 __device__ __forceinline__ float w2_core(const float* wr, int t, int el) {
   const int n = (el >> 7) * 8 + ((el >> 3) & 7), k = ((el >> 6) & 1) * 8 + (el & 7);
   return wr[oW2 + n * 144 + k * 9 + t];
@@ -423,11 +565,16 @@ __global__ void k_pack_frags(const float* __restrict__ wr, uint32_t* frag) {
   if (e >= kFrag) return;
   const int lane = e & 31, g = lane >> 2, tq = lane & 3;
   float lo = 0.f, hi = 0.f;
-  if (e < kF3) {
+  if (e < kF2) {
     const int r = (e - kF1) >> 5, h = r & 1, nb = (r >> 1) & 1, k = r >> 2;
     const int o = nb * 8 + g, kk = k * 16 + 2 * tq + 8 * h;
     lo = w1_at(wr, o, kk);
     hi = w1_at(wr, o, kk + 1);
+  } else if (e < kF3) {
+    const int r = (e - kF2) >> 5, h = r & 1, nb = (r >> 1) & 1, t = r >> 2;
+    const int o = nb * 8 + g, c = 2 * tq + 8 * h;
+    lo = wr[oW2 + o * 144 + c * 9 + t];
+    hi = wr[oW2 + o * 144 + (c + 1) * 9 + t];
   } else if (e < kFU) {
     const int r = (e - kF3) >> 5, h = r & 1, t = r >> 1;
     const int c = 2 * tq + 8 * h;
@@ -794,6 +941,7 @@ struct Learned {
   float* m = nullptr;      // Adam moments
   float* v = nullptr;
   uint32_t* frag = nullptr;     // B fragments of the smoother kernel (k_pack_frags)
+  int tensor_path = 0;          // 0: mma.sync network, 1: layer 2 on tcgen05
   std::vector<uint32_t*> logk;  // per level: log-coefficient pairs (k_logk_pack)
   std::vector<int> logk_ver;    // Mesh::k_version they were made from
   int step = 0;
@@ -850,6 +998,15 @@ void learned_get_weights(Mesh& m, float* w_host) {
 
 bool learned_ready(const Mesh& m) { return m.learned && m.learned->trained; }
 
+int learned_tensor_path(Mesh& m, int set, int path) {
+  Learned& L = learned_of(m);
+  if (set) {
+    if (path != 0 && path != 1) throw std::invalid_argument("tensor path must be 0 (mma.sync) or 1 (tcgen05)");
+    L.tensor_path = path;
+  }
+  return L.tensor_path;
+}
+
 // x += CNN(s) on the face interiors of one level (s: FP32 scaled residual with
 // ghost copies); delta (optional) receives the correction.
 void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, float* delta, cudaStream_t st) {
@@ -876,10 +1033,16 @@ void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, 
   LaunchScope ls(HHG_K_OTHER, level, st);
   k_face_rms<<<m.nf, 256, 0, st>>>(m.tab, lv, s, L.scale);
   if (delta) check_cuda(cudaMemsetAsync(delta, 0, (size_t)lv.len * sizeof(float), st), "delta clear");
-  if (prec == 0)
-    k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (double*)x, delta, m.err);
-  else
-    k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (float*)x, delta, m.err);
+  if (L.tensor_path == 1) {
+    if (prec == 0)
+      k_cnn_smooth_tc<double><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (double*)x, delta, m.err);
+    else
+      k_cnn_smooth_tc<float><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (float*)x, delta, m.err);
+  } else if (prec == 0) {
+    k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (double*)x, delta);
+  } else {
+    k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (float*)x, delta);
+  }
   check_cuda(cudaGetLastError(), "cnn smooth");
 }
 

@@ -29,6 +29,7 @@ ARITH_IEEE, ARITH_DFLOAT = 0, 1
 GS_FWD, GS_BWD, JACOBI = 0, 1, 2
 SOLVE_MG, SOLVE_IR, SOLVE_FGMRES, SOLVE_PCG, SOLVE_FPCG = 0, 1, 2, 3, 4
 SMOOTH_GS, SMOOTH_LEARNED, SMOOTH_LEARNED_GS = 0, 1, 2
+TC_MMA_SYNC, TC_TCGEN05 = 0, 1
 LEARNED_NPARAMS = 2913
 
 
@@ -90,6 +91,7 @@ _SIGS = {
     "hhg_learned_set_weights": [_P, C.POINTER(C.c_float), C.c_int64],
     "hhg_learned_get_weights": [_P, C.POINTER(C.c_float), C.c_int64],
     "hhg_learned_apply": [_P, C.c_int32, C.c_int32, _P, _P, _P, _P],
+    "hhg_learned_tensor_path": [_P, C.c_int32, C.POINTER(C.c_int32)],
     "hhg_learned_grad": [_P, C.c_int32, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float),
                          C.POINTER(C.c_float), _P],
     "hhg_learned_train": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_uint64,
@@ -243,6 +245,13 @@ class Mesh:
 
     def learned_apply(self, level, s, x=None, d=None, prec=F64, stream=None):
         _check(lib.hhg_learned_apply(self.h, level, prec, _ptr(s), _ptr(x), _ptr(d), _stream(stream)))
+
+    def learned_tensor_path(self, path=None):
+        """Reads, or sets when path is given, the network kernel's tensor-core
+        path (TC_MMA_SYNC / TC_TCGEN05)."""
+        v = C.c_int32(path or 0)
+        _check(lib.hhg_learned_tensor_path(self.h, 0 if path is None else 1, C.byref(v)))
+        return v.value
 
     def learned_grad(self, X, S, crops, K=None, stream=None):
         crops = np.ascontiguousarray(crops, dtype=np.int32).reshape(-1, 4)

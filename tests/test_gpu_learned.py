@@ -26,14 +26,18 @@ def _weights(seed=1):
     return p
 
 
+@pytest.mark.parametrize("path", ["mma_sync", "tcgen05"])
 @pytest.mark.parametrize("vark", [False, True])
-def test_cnn_forward_parity(vark):
+def test_cnn_forward_parity(vark, path):
+    """Both tensor-core paths of the network kernel against the FP64 oracle."""
     torch = pytest.importorskip("torch")
     P = Pair("annulus", 5, vark=vark)
     L = 5
     lv = P.H.levels[L]
     p = _weights(3)
     P.g.learned_set_weights(learned.flatten(p).astype(np.float32))
+    code = {"mma_sync": P.hhg.TC_MMA_SYNC, "tcgen05": P.hhg.TC_TCGEN05}[path]
+    assert P.g.learned_tensor_path(code) == code
     s = P.random(L)
     s32 = P.to_dev(L, s, prec=1)
     d = P.new(L, 1)
@@ -45,7 +49,7 @@ def test_cnn_forward_parity(vark):
         ok = Mi > 0
         want[G[ok]] = sig * out[ok]
     e = rel_err(got, want)
-    print(f"CNN forward BF16 vs FP64 oracle: max-norm relative error {e:.3e}")
+    print(f"CNN forward ({path}) BF16 vs FP64 oracle: max-norm relative error {e:.3e}")
     assert e < BF16_TOL
     P.close()
 
