@@ -21,31 +21,6 @@ namespace hhg {
 
 namespace {
 
-// FP64 <-> FP32 casts by integer bit operations (round to nearest even;
-// magnitudes below 2^-126 flushed), off the FP64 pipe
-__global__ void k_cast_f64_f32(int64_t n, const double* __restrict__ a, float* __restrict__ o) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = d2f_rn(a[i]);
-}
-__global__ void k_cast_f32_f64(int64_t n, const float* __restrict__ a, double* __restrict__ o) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = f2d_bits(a[i]);
-}
-// y -= h * x with h read from device memory
-__global__ void k_axpy_dev(int64_t n, const double* __restrict__ h, const double* __restrict__ x, double* y) {
-  const double a = *h;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] -= a * x[i];
-}
-// y = x / sqrt(*nrm2)  (nrm2 holds a squared norm); *h = sqrt(*nrm2)
-__global__ void k_normalize(int64_t n, const double* __restrict__ nrm2, const double* __restrict__ x, double* y,
-                            double* h) {
-  const double nv = sqrt(*nrm2);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && h) *h = nv;
-  const double inv = nv > 0.0 ? 1.0 / nv : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = x[i] * inv;
-}
 
 
 // ------------------------------------------------------------- fused vector passes
@@ -74,6 +49,34 @@ __device__ __forceinline__ void for_valid_slots(const MeshTables& M, const Level
     const int64_t base = L.f_off + fc * L.FS + (int64_t)j * L.S;
     for (int i = lane; i <= L.N - j; i += 32) f(base + i, i >= 1 && j >= 1 && i + j <= L.N - 1);
   }
+}
+
+// Vector steps of FGMRES and the FP64 <-> FP32 casts of the mixed solvers,
+// over the slots that hold values (ghost copies included, padding skipped).
+// Casts by integer bit operations (round to nearest even; magnitudes below
+// 2^-126 flushed), off the FP64 pipe.
+__global__ void __launch_bounds__(kVecThreads) k_cast_f64_f32(MeshTables M, LevelView L,
+                                                             const double* __restrict__ a, float* __restrict__ o) {
+  for_valid_slots(M, L, [&](int64_t s, bool) { o[s] = d2f_rn(a[s]); });
+}
+__global__ void __launch_bounds__(kVecThreads) k_cast_f32_f64(MeshTables M, LevelView L,
+                                                             const float* __restrict__ a, double* __restrict__ o) {
+  for_valid_slots(M, L, [&](int64_t s, bool) { o[s] = f2d_bits(a[s]); });
+}
+// y -= h * x with h read from device memory
+__global__ void __launch_bounds__(kVecThreads) k_axpy_dev(MeshTables M, LevelView L, const double* __restrict__ h,
+                                                         const double* __restrict__ x, double* y) {
+  const double a = *h;
+  for_valid_slots(M, L, [&](int64_t s, bool) { y[s] -= a * x[s]; });
+}
+// y = x / sqrt(*nrm2)  (nrm2 holds a squared norm); *h = sqrt(*nrm2)
+__global__ void __launch_bounds__(kVecThreads) k_normalize(MeshTables M, LevelView L,
+                                                          const double* __restrict__ nrm2,
+                                                          const double* __restrict__ x, double* y, double* h) {
+  const double nv = sqrt(*nrm2);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && h) *h = nv;
+  const double inv = nv > 0.0 ? 1.0 / nv : 0.0;
+  for_valid_slots(M, L, [&](int64_t s, bool) { y[s] = x[s] * inv; });
 }
 
 __device__ __forceinline__ void block_sums(double a, double b, double* out, int stride) {
@@ -361,13 +364,18 @@ void krylov_free(Mesh& m) {
 static void precondition(Mesh& m, int L, const double* v, double* z, int nu1, int nu2, int smoother,
                          cudaStream_t st) {
   const LevelData& ld = m.levels[L];
-  const int64_t n = ld.lv.len;
-  const int g = 152 * 8;
-  k_cast_f64_f32<<<g, 256, 0, st>>>(n, v, (float*)ld.b[1]);
+  k_cast_f64_f32<<<kVecBlocks, kVecThreads, 0, st>>>(m.tab, ld.lv, v, (float*)ld.b[1]);
   check_cuda(cudaGetLastError(), "cast");
-  zero_vec(m, L, 1, ld.x[1], st);
-  vcycle_run(m, L, 1, ld.x[1], ld.b[1], nu1, nu2, smoother, st);
-  k_cast_f32_f64<<<g, 256, 0, st>>>(n, (const float*)ld.x[1], z);
+  // the cycle itself works on the level's own FP32 vectors: one captured
+  // sequence per level, smoother, cycle shape and network kernel path
+  const int path = smoother >= 1 ? learned_tensor_path(m, 0, 0) : 0;
+  const GraphKey key{5, (uint64_t)L, (uint64_t)smoother, (uint64_t)nu1, (uint64_t)nu2, (uint64_t)path,
+                     key_ptr(ld.x[1]), key_ptr(ld.b[1])};
+  graphed(m, key, st, [&](cudaStream_t s) {
+    zero_vec(m, L, 1, ld.x[1], s);
+    vcycle_run(m, L, 1, ld.x[1], ld.b[1], nu1, nu2, smoother, s);
+  });
+  k_cast_f32_f64<<<kVecBlocks, kVecThreads, 0, st>>>(m.tab, ld.lv, (const float*)ld.x[1], z);
   check_cuda(cudaGetLastError(), "cast");
 }
 
@@ -392,8 +400,6 @@ void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_op
   if (smoother >= 1 && !learned_ready(m)) throw std::invalid_argument("learned smoother requested but not trained/loaded");
   KrylovSpace& K = space(m, L, restart);
   const LevelData& ld = m.levels[L];
-  const int64_t n = ld.lv.len;
-  const int g = 152 * 8;
   double* r = (double*)ld.r[0];
   ghost_fill(m, L, 0, x, st);
   residual_op(m, L, 0, x, b, r, m.scalars, st);
@@ -413,7 +419,7 @@ void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_op
       status = HHG_ERR_NOT_CONVERGED;
       break;
     }
-    k_normalize<<<g, 256, 0, st>>>(n, m.scalars, r, K.V[0], nullptr);
+    k_normalize<<<kVecBlocks, kVecThreads, 0, st>>>(m.tab, ld.lv, m.scalars, r, K.V[0], nullptr);
     check_cuda(cudaGetLastError(), "normalize");
     if (use >= 1 && !judged) {
       double* tmp = K.V[restart];   // not used before the last step of a restart
@@ -437,12 +443,12 @@ void fgmres_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_op
       for (int i = 0; i <= j; ++i) {
         double* h = K.H + (size_t)j * (restart + 1) + i;
         dot_op(m, L, 0, K.w, K.V[i], h, st);
-        k_axpy_dev<<<g, 256, 0, st>>>(n, h, K.V[i], K.w);
+        k_axpy_dev<<<kVecBlocks, kVecThreads, 0, st>>>(m.tab, ld.lv, h, K.V[i], K.w);
         check_cuda(cudaGetLastError(), "axpy");
       }
       double* hn = K.H + (size_t)j * (restart + 1) + j + 1;
       dot_op(m, L, 0, K.w, K.w, m.scalars + 1, st);
-      k_normalize<<<g, 256, 0, st>>>(n, m.scalars + 1, K.w, K.V[j + 1], hn);
+      k_normalize<<<kVecBlocks, kVecThreads, 0, st>>>(m.tab, ld.lv, m.scalars + 1, K.w, K.V[j + 1], hn);
       check_cuda(cudaGetLastError(), "normalize");
       std::vector<double> col(j + 2);
       check_cuda(cudaMemcpyAsync(col.data(), K.H + (size_t)j * (restart + 1), (j + 2) * sizeof(double),
@@ -550,7 +556,7 @@ void pcg_solve(Mesh& m, int L, double* x, const double* b, const hhg_solve_opts&
   hhg_status status = std::isfinite(r0) ? HHG_OK : HHG_ERR_NAN;
   auto restart_from_r = [&]() {
     if (mixed) {
-      k_cast_f64_f32<<<152 * 8, 256, 0, st>>>(n, r, r32);
+      k_cast_f64_f32<<<kVecBlocks, kVecThreads, 0, st>>>(m.tab, ld.lv, r, r32);
       check_cuda(cudaGetLastError(), "cast");
     }
     check_cuda(cudaMemsetAsync(K.q, 0, n * sizeof(double), st), "q = 0");
