@@ -347,7 +347,7 @@ def cnn_roofline(g, L, info, dev, reps=20):
 
 
 def _peaks():
-    """The measured peaks of the GB300s, {} when absent."""
+    """The measured peak rates of the GB300 (MEASURED_PEAKS.json), {} when absent."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             return json.load(fh)

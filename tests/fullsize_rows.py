@@ -1,0 +1,65 @@
+"""Single rows of the P1 operator, for checking GPU results on sampled
+points of levels too large for the oracle's whole-level arrays.
+
+The row of a face-interior lattice point p = (i, j) of face f is built from
+the oracle's own element matrices (Sec. 4.2: A_pq = sum over the
+micro-triangles T of k_T * integral_T grad(phi_p).grad(phi_q)) on the six
+micro-triangles around p, all inside face f, translated so that p is at the
+origin (the matrices do not change under translation).  Lattice point (a, b) of face f
+sits at v0 + (a/N)(v1 - v0) + (b/N)(v2 - v0), (v0, v1, v2) the face's
+counter-clockwise vertices; upward triangle (a, b) has the vertices
+(a, b), (a+1, b), (a, b+1), downward triangle (a, b) the vertices
+(a+1, b), (a, b+1), (a+1, b+1), each numbered row by row within its face
+(the canonical element order).
+"""
+from types import SimpleNamespace
+
+import numpy as np
+
+from oracle import fem
+
+# the seven stencil points as offsets from p; local id = position here
+NEIGH = [(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1), (1, -1), (-1, 1)]
+# the six micro-triangles containing p: (kind, origin offset)
+PATCH = [("up", 0, 0), ("up", -1, 0), ("up", 0, -1), ("dn", -1, 0), ("dn", 0, -1), ("dn", -1, -1)]
+
+
+def tri_vertices(kind, a, b):
+    if kind == "up":
+        return [(a, b), (a + 1, b), (a, b + 1)]
+    return [(a + 1, b), (a, b + 1), (a + 1, b + 1)]
+
+
+def element_index(N, kind, a, b):
+    """Position of a micro-triangle within its face in the canonical element
+    order (all upward triangles row by row, then all downward ones)."""
+    if kind == "up":
+        return b * N - b * (b - 1) // 2 + a
+    return N * (N + 1) // 2 + b * (N - 1) - b * (b - 1) // 2 + a
+
+
+def row_weights(xy, tri, N, f, i, j, k_patch=None):
+    """w (7,) with (A x)_p = sum_m w[m] x[p + NEIGH[m]]; k_patch: the six
+    coefficients in PATCH order (None: k = 1)."""
+    v0, v1, v2 = (np.asarray(xy[v], dtype=np.float64) for v in tri[f])
+    pts = [(i + di, j + dj) for di, dj in NEIGH]
+    local = {pt: m for m, pt in enumerate(pts)}
+    # the element matrices depend on coordinate differences only: the patch
+    # is placed relative to p, so that its edge vectors are (v1 - v0) / N and
+    # (v2 - v0) / N to rounding (absolute coordinates would lose about
+    # log2(N) bits of them to cancellation)
+    coords = np.array([((a - i) / N) * (v1 - v0) + ((b - j) / N) * (v2 - v0) for a, b in pts])
+    elems = np.array([[local[v] for v in tri_vertices(kind, i + da, j + db)] for kind, da, db in PATCH])
+    k = np.ones(6) if k_patch is None else np.asarray(k_patch, dtype=np.float64)
+    K = fem.element_stiffness(SimpleNamespace(coords=coords, elements=elems), k)
+    w = np.zeros(7)
+    for e in range(6):
+        a_loc = int(np.where(elems[e] == 0)[0][0])
+        for bpos in range(3):
+            w[elems[e, bpos]] += K[e, a_loc, bpos]
+    return w
+
+
+def patch_element_ids(N, f, i, j):
+    """Canonical element ids (6,) of the PATCH triangles of point (i, j) of face f."""
+    return np.array([f * N * N + element_index(N, kind, i + da, j + db) for kind, da, db in PATCH])

@@ -1,0 +1,54 @@
+"""The sampled-row helper of the full-size GPU tests, pinned on the CPU: its
+rows equal the oracle's element-loop operator at every face-interior point of
+a small level (constant and random coefficient), and its element numbering is
+the canonical one of the oracle's level."""
+import numpy as np
+import pytest
+
+from oracle import fem
+from oracle import mesh as om
+from paper_1805_10167_gb300 import inputs
+
+import fullsize_rows as fr
+
+
+@pytest.mark.parametrize("name", ["annulus", "random"])
+@pytest.mark.parametrize("vark", [False, True])
+def test_rows_equal_element_loop(name, vark):
+    xy, tri = inputs.annulus_mesh(32, 2) if name == "annulus" else inputs.random_square_mesh(5, 12)
+    M = om.MacroMesh(xy, tri)
+    L = 4
+    lv = om.Level(M, L)
+    N = lv.N
+    rng = np.random.default_rng(3)
+    k = rng.uniform(0.3, 3.0, size=lv.elements.shape[0]) if vark else None
+    x = rng.standard_normal(lv.n)
+    want = fem.apply_element_loop(lv, x, k)
+    worst = 0.0
+    for f in range(0, M.nf, max(1, M.nf // 6)):
+        G = lv.face_ids[f]
+        for j in range(1, N - 1):
+            for i in range(1, N - j):
+                kp = None if k is None else k[fr.patch_element_ids(N, f, i, j)]
+                w = fr.row_weights(M.xy, M.tri, N, f, i, j, kp)
+                ids = [G[j + dj, i + di] for di, dj in fr.NEIGH]
+                got = w @ x[ids]
+                worst = max(worst, abs(got - want[G[j, i]]))
+    assert worst <= 1e-13 * np.abs(want).max()
+
+
+def test_element_numbering_matches_oracle_level():
+    xy, tri = inputs.annulus_mesh(32, 2)
+    M = om.MacroMesh(xy, tri)
+    lv = om.Level(M, 3)
+    N = lv.N
+    for f in (0, 7, M.nf - 1):
+        G = lv.face_ids[f]
+        for b in range(N):
+            for a in range(N - b):
+                e = f * N * N + fr.element_index(N, "up", a, b)
+                assert list(lv.elements[e]) == [G[v[1], v[0]] for v in fr.tri_vertices("up", a, b)]
+        for b in range(N - 1):
+            for a in range(N - 1 - b):
+                e = f * N * N + fr.element_index(N, "dn", a, b)
+                assert list(lv.elements[e]) == [G[v[1], v[0]] for v in fr.tri_vertices("dn", a, b)]
