@@ -9,9 +9,10 @@
 // lattice (zero where a micro-triangle does not exist), M = closed triangle,
 // Mi = face interior; conv3x3 is a cross-correlation over (i +- 1, j +- 1)
 // with zeros outside the lattice.  Weights and activations are rounded to
-// BF16, products accumulate in FP32.  The weights live in __constant__
-// memory so that every FMA takes its weight as a broadcast operand; the
-// master copy (FP32) and Adam state live in device memory.
+// BF16, products accumulate in FP32.  The training kernels read the weights
+// from __constant__ memory (warp-uniform indices: broadcast operands); the
+// smoother kernels read tensor-core operands packed from them once per
+// weight load.  The master copy (FP32) and Adam state live in device memory.
 //
 // The residual channel is divided by its RMS over the face (in training
 // and in use) and the output multiplied back, so the step is homogeneous of
