@@ -15,9 +15,16 @@ Modules
   fem        P1 element stiffness / mass, brute-force CSR assembly, element-loop
              apply (Sec. 4.2), quadrature-based L2 error
   multigrid  colour-ordered Gauss-Seidel, damped Jacobi, prolongation and
-             restriction, coarse CG, V-cycle, solver, iterative refinement (Sec. 4.3)
-  pointwise  single-row evaluation of the operator, for sampled checks at sizes
-             where assembling the whole matrix is too slow
+             restriction, coarse CG, V-cycle and the V-cycle solver (Sec. 4.3)
+  krylov     flexible GMRES (Saad 1993) and preconditioned / flexible conjugate
+             gradients, each taking the operator and preconditioner as callables
+  learned    the learned smoother's network (convolutions, forward, hand-derived
+             backward passes, BF16 rounding, Adam step, face images and crops)
+
+Iterative refinement has no oracle function of its own: its FP64 outer loop is
+checked against the tolerance and against the oracle's V-cycle solve.  Single
+rows of the operator at sizes the oracle cannot assemble are built in
+``tests/fullsize_rows.py`` from this package's element matrices.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against
 closed forms, invariants or brute force; the multigrid cycle as a whole is an

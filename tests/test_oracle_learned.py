@@ -205,3 +205,32 @@ def test_scaled_operator_matches_assembled_rows():
     for j in range(1, N - 1):
         for i in range(1, N - j):
             assert out[j, i] == pytest.approx(want[G[j, i]], rel=1e-12, abs=1e-12)
+
+
+def test_bf16_rounding_matches_torch_bfloat16():
+    """The oracle's BF16 rounding (round to nearest, ties to even, at bit 16 of
+    the binary32 pattern) against torch's own float32 -> bfloat16 conversion,
+    element by element over about 10^6 values: random finite bit patterns
+    (normal and subnormal), exact ties with even and odd kept parts, the
+    neighbours of each tie, +-0, the largest finite values (which round to
+    infinity) and plain normal samples."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(2024)
+    bits = rng.integers(0, 2 ** 32, 600_000, dtype=np.uint64).astype(np.uint32)
+    bits = bits[(bits & 0x7F800000) != 0x7F800000]          # finite patterns only
+    hi = rng.integers(0, 2 ** 16, 100_000, dtype=np.uint64).astype(np.uint32) << 16
+    hi = hi[(hi & 0x7F800000) != 0x7F800000]
+    ties = hi | 0x8000                                         # exactly half-way
+    below, above = hi | 0x7FFF, hi | 0x8001
+    special = np.array([0x00000000, 0x80000000, 0x7F7FFFFF, 0xFF7FFFFF, 0x7F7F8000,
+                        0x00000001, 0x00008000, 0x00018000, 0x3F808000, 0x3F818000],
+                       dtype=np.uint32)
+    x = np.concatenate([bits, ties, below, above, special]).view(np.float32)
+    x = np.concatenate([x, rng.standard_normal(200_000).astype(np.float32)])
+    assert x.size > 900_000
+    got = learned.bf16(x)
+    want = torch.from_numpy(x.copy()).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(got, want)
+    # +-0 keep their sign
+    z = learned.bf16(np.array([0.0, -0.0], dtype=np.float32))
+    assert np.signbit(z).tolist() == [False, True]

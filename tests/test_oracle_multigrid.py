@@ -217,15 +217,37 @@ def test_manufactured_solution_second_order():
     assert np.all((orders > 1.9) & (orders < 2.1)), orders
 
 
-def test_jacobi_sweep_definition():
+@pytest.mark.parametrize("omega", [2.0 / 3.0, 0.5, 1.0])
+@pytest.mark.parametrize("L", [2, 3])
+def test_jacobi_sweep_scales_eigenvector(omega, L):
+    """Damped Jacobi on the unit square: the matrix is the 5-point Laplacian
+    with diagonal 4 at every free node, and v = sin(k pi x) sin(l pi y) is an
+    eigenvector with eigenvalue lam = 4 sin^2(k pi h/2) + 4 sin^2(l pi h/2),
+    h = 1/(2N).  With b = 0 one sweep therefore multiplies v by exactly
+    1 - omega lam / 4; from x = 0 with b = lam v it gives omega lam v / 4.
+    A wrong damping convention or a wrong diagonal changes both."""
+    M = mesh_of("square")
+    H = mg.Hierarchy(M, L)
+    lv = H.levels[L]
+    h = 1.0 / (2 * lv.N)
+    X, Y = lv.coords[:, 0], lv.coords[:, 1]
+    for (k, l) in ((1, 1), (2, 3), (3, 1)):
+        v = np.sin(k * np.pi * X) * np.sin(l * np.pi * Y)
+        v[~lv.free] = 0.0
+        lam = 4 * np.sin(k * np.pi * h / 2) ** 2 + 4 * np.sin(l * np.pi * h / 2) ** 2
+        got = mg.jacobi_sweep(H, L, v.copy(), np.zeros(lv.n), omega)
+        np.testing.assert_allclose(got, (1 - omega * lam / 4) * v, atol=1e-13)
+        got = mg.jacobi_sweep(H, L, np.zeros(lv.n), lam * v, omega)
+        np.testing.assert_allclose(got, (omega * lam / 4) * v, atol=1e-13)
+
+
+def test_jacobi_sweep_keeps_dirichlet_values():
+    """Dirichlet unknowns are not smoothed: their values in x pass through."""
     M = mesh_of("random")
     H = mg.Hierarchy(M, 2)
     lv = H.levels[2]
     rng = np.random.default_rng(10)
     x = rng.standard_normal(lv.n)
-    b = rng.standard_normal(lv.n)
-    A = H.A[2].toarray()
-    want = x.copy()
-    fr = lv.free
-    want[fr] = x[fr] + (2 / 3) * (b - A @ x)[fr] / np.diag(A)[fr]
-    np.testing.assert_allclose(mg.jacobi_sweep(H, 2, x.copy(), b), want, atol=1e-14)
+    got = mg.jacobi_sweep(H, 2, x.copy(), rng.standard_normal(lv.n))
+    np.testing.assert_array_equal(got[~lv.free], x[~lv.free])
+    assert np.abs(got[lv.free] - x[lv.free]).min() > 0
