@@ -163,6 +163,19 @@ hhg_status hhg_from_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const
 hhg_status hhg_to_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* src,
                             void* dst, void* stream);
 
+/* Coordinates of the lattice points of one level (Sec. 3.1: point (i, j) of a
+ * macro-face lies at v0 + (i/N)(v1 - v0) + (j/N)(v2 - v0) in the face's
+ * counter-clockwise frame; a macro-edge's point t at lo + (t/N)(hi - lo) from
+ * its low-id vertex).  xy_dev: DEVICE array of 2 * vec_len doubles, caller-
+ * owned, planar: x of slot s at xy_dev[s], y at xy_dev[vec_len + s], so each
+ * half is a level vector in the internal layout (hhg_to_canonical turns it
+ * into canonical order).  Every slot that holds an unknown or a ghost copy
+ * is written -- copies with their owner's coordinates, bit for bit; padding
+ * slots are left untouched.  Evaluated in IEEE binary64 in the order written
+ * above.  Asynchronous.  HHG_ERR_ARG for a bad level or a NULL or
+ * unaligned (16-byte) pointer. */
+hhg_status hhg_dof_coords(hhg_mesh mesh, int32_t level, double* xy_dev, void* stream);
+
 /* y = A x on free DoFs, 0 on Dirichlet DoFs (Alg. 3). */
 hhg_status hhg_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x, void* y,
                      void* stream);
@@ -191,9 +204,11 @@ hhg_status hhg_dot(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1, 
  * Same arguments and result as hhg_dot, summed in a different (still fixed)
  * order, so the two agree to rounding.  Limit: the level vector may have at
  * most 2^28 slots (hhg_info.vec_len); larger levels return HHG_ERR_ARG.
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call uses
- * the same array: calls that overlap on the GPU race and give wrong results. */
+ * hhg_mesh_create, with the mesh's device current, looks up the array's
+ * device address and loads the kernels of this call, so no call -- the first
+ * included -- does either.  Every call uses the same array: calls that
+ * overlap on the GPU (any meshes, streams or threads) race and give wrong
+ * results. */
 hhg_status hhg_dot_noalloc(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1,
                            const void* x2, double* result_dev, void* stream);
 
@@ -312,11 +327,11 @@ hhg_status hhg_batch_solve(hhg_batch batch, double* const* x, const double* cons
 
 /* Diagnostics.  The library counts every kernel it launches, by class; while
  * profiling is on it also brackets each launch of the classes in `mask`
- * (bit c = class c) on level `level` with CUDA events on the launching
- * stream.  hhg_profile_end synchronises those events and returns, per class,
- * the launches counted since hhg_profile_begin (all levels) and the summed
- * event time in milliseconds (timed level only).  Arrays have
- * HHG_K_COUNT entries.  Process-wide; not for concurrent use. */
+ * (bit c = class c) on level `level` (-1: on every level) with CUDA events
+ * on the launching stream.  hhg_profile_end synchronises those events and
+ * returns, per class, the launches counted since hhg_profile_begin (all
+ * levels) and the summed event time in milliseconds (timed levels only).
+ * Arrays have HHG_K_COUNT entries.  Process-wide; not for concurrent use. */
 typedef enum {
   HHG_K_FACE_GS = 0,      /* face-interior Gauss-Seidel                      */
   HHG_K_FACE_ROWS = 1,    /* face-interior apply / residual / Jacobi          */
@@ -383,6 +398,24 @@ hhg_status hhg_learned_grad(hhg_mesh mesh, int32_t n_crops, const float* X, cons
 hhg_status hhg_learned_train(hhg_mesh mesh, int32_t level, int32_t n_pairs, int32_t epochs,
                              int32_t batch, float lr, uint64_t seed, float* loss_history_host,
                              void* stream);
+
+/* Waits for `stream` and reports whether a bounded device-side wait of this
+ * mesh's kernels gave up since the last report (HHG_ERR_TIMEOUT; the device
+ * error word is then cleared and the next call runs normally).  hhg_solve
+ * and hhg_batch_solve report this themselves; the asynchronous calls
+ * (hhg_smooth, hhg_vcycle, ...) leave it to this call.  Synchronous. */
+hhg_status hhg_sync(hhg_mesh mesh, void* stream);
+
+/* Test hook of the bounded device-side waits (not in the paper): while
+ * extra_arrivals > 0, every grid barrier of the whole-sweep Gauss-Seidel
+ * kernel awaits extra_arrivals more CTAs than its launch has -- arrivals
+ * that never come -- and gives up after max_polls polls (<= 0: the default
+ * limit of about a second).  The launch then sets the device error word and
+ * runs to its end without waiting again (every access stays in bounds; the
+ * sweep's result is wrong); hhg_sync or hhg_solve reports HHG_ERR_TIMEOUT.
+ * extra_arrivals = 0 restores normal operation.  Waits for the device and
+ * drops captured graphs.  HHG_ERR_ARG for extra_arrivals < 0. */
+hhg_status hhg_debug_wait_limit(hhg_mesh mesh, int32_t extra_arrivals, int64_t max_polls);
 
 /* Message of the last failed call on this thread ('\0'-terminated, truncated
  * to n bytes).  Returns the full message length. */

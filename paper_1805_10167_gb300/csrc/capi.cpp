@@ -253,6 +253,16 @@ hhg_status hhg_to_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const v
   });
 }
 
+hhg_status hhg_dof_coords(hhg_mesh mesh, int32_t level, double* xy_dev, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    check_level(m, level);
+    need_vec(xy_dev, "xy_dev");
+    hhg::dof_coords(m, level, xy_dev, S(stream));
+    return HHG_OK;
+  });
+}
+
 hhg_status hhg_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x, void* y,
                      void* stream) {
   return guarded([&]() {
@@ -498,6 +508,26 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
     if (status == HHG_ERR_TIMEOUT) return fail(status, "a device-side wait gave up");
     if (status == HHG_ERR_NAN) return fail(status, "non-finite residual norm");
     if (status == HHG_ERR_NOT_CONVERGED) return fail(status, "max_iter reached");
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_sync(hhg_mesh mesh, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    if (device_timed_out(m, S(stream))) return fail(HHG_ERR_TIMEOUT, "a device-side wait gave up");
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_debug_wait_limit(hhg_mesh mesh, int32_t extra_arrivals, int64_t max_polls) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    if (extra_arrivals < 0) throw ArgError("extra_arrivals < 0");
+    hhg::check_cuda(cudaDeviceSynchronize(), "sync");
+    m.dbg_bar_extra = (unsigned)extra_arrivals;
+    m.dbg_bar_polls = extra_arrivals > 0 && max_polls > 0 ? (long long)max_polls : 0;
+    hhg::graphs_clear(m);
     return HHG_OK;
   });
 }

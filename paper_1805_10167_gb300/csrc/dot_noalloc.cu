@@ -7,46 +7,33 @@
 // allowed, or a pool that rejects new allocations.  hhg_dot itself already
 // performs no allocation per call (its scratch is allocated once with the
 // mesh); this variant goes further: its reduction scratch is part of the
-// library image (128 KB loaded with the module on every device that uses the
-// library, kept until the process exits) and is never allocated at all.
+// library image (128 KB on every device that uses the library, kept until
+// the process exits) and is never allocated at all.
 //
-// Scratch: kNoallocPartials doubles, one partial sum per CTA.  CTA c reduces
-// the slots [c * kSlotsPerCta, (c + 1) * kSlotsPerCta) of the level vector,
-// keeping the owned free unknowns.  A level whose vector needs more partial
-// sums than the array holds (vec_len > kNoallocPartials * kSlotsPerCta) is
-// rejected with HHG_ERR_ARG.  Every CTA writes its partial before the final
-// sum reads it, so nothing has to be cleared between calls; calls that
-// overlap on the GPU (two streams, or two threads) share the array and race.
-#include <mutex>
-
+// Set-up: hhg_mesh_create (where allocating is allowed) calls
+// noalloc_setup(), which, with the mesh's device current, looks up the
+// array's device address and touches the kernels of this file, so that the
+// code module holding them is loaded then (under lazy module loading a
+// module's first use loads it, which can allocate).  The address is kept in
+// the mesh; a call reads it from there and allocates nothing, on its first
+// use as on every later one.
+//
+// Scratch: kNoallocPartials doubles, one partial sum per CTA (noalloc.h).
+// CTA c reduces the slots [c * kNoallocSlotsPerCta, (c + 1) *
+// kNoallocSlotsPerCta) of the level vector, keeping the owned free unknowns.
+// Every CTA writes its partial before the final sum reads it, so nothing has
+// to be cleared between calls; calls that overlap on the GPU (two streams, or
+// two threads) share the array and race.
 #include "hhg_internal.h"
+#include "noalloc.h"
 
 namespace hhg {
 
-constexpr int kNoallocPartials = 16384;
-constexpr int64_t kSlotsPerCta = 16384;
 constexpr int kNoallocThreads = 256;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_partials[kNoallocPartials];
 
 namespace {
-
-// Per-device address of g_noalloc_partials.  Host code may not pass the
-// symbol itself to a kernel (on the host it names a host-side stand-in), so
-// the device address is looked up once per device, with that device current.
-double* partials_address(int dev) {
-  static std::mutex mu;
-  static double* addr[kMaxDevices] = {};
-  if (dev < 0 || dev >= kMaxDevices) throw std::runtime_error("device ordinal out of range");
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    check_cuda(cudaGetSymbolAddress(&p, g_noalloc_partials), "cudaGetSymbolAddress");
-    addr[dev] = (double*)p;
-  }
-  return addr[dev];
-}
 
 __device__ __forceinline__ double block_sum_noalloc(double v) {
   __shared__ double red[kNoallocThreads / 32];
@@ -76,8 +63,8 @@ template <typename T>
 __global__ void __launch_bounds__(kNoallocThreads)
     k_dot_chunks(MeshTables M, LevelView L, const T* __restrict__ x1, const T* __restrict__ x2,
                  double* partials) {
-  const int64_t lo = blockIdx.x * kSlotsPerCta;
-  const int64_t hi = min(lo + kSlotsPerCta, L.len);
+  const int64_t lo = blockIdx.x * kNoallocSlotsPerCta;
+  const int64_t hi = min(lo + kNoallocSlotsPerCta, L.len);
   double acc = 0.0;
   for (int64_t s = lo + threadIdx.x; s < hi; s += kNoallocThreads)
     if (owned_free(M, L, s)) acc += (double)x1[s] * (double)x2[s];
@@ -95,30 +82,36 @@ __global__ void __launch_bounds__(kNoallocThreads)
 
 }  // namespace
 
+// With the mesh's device current: the device address of the static array
+// (host code may not pass the symbol itself to a kernel: on the host it names
+// a host-side stand-in), and a query of each kernel so that their module is
+// loaded now rather than inside the first hhg_dot_noalloc call.
+void noalloc_setup(Mesh& m) {
+  void* p = nullptr;
+  check_cuda(cudaGetSymbolAddress(&p, g_noalloc_partials), "cudaGetSymbolAddress(noalloc scratch)");
+  cudaFuncAttributes fa;
+  check_cuda(cudaFuncGetAttributes(&fa, k_dot_chunks<double>), "noalloc kernel load");
+  check_cuda(cudaFuncGetAttributes(&fa, k_dot_chunks<float>), "noalloc kernel load");
+  check_cuda(cudaFuncGetAttributes(&fa, k_sum_noalloc), "noalloc kernel load");
+  m.noalloc_partials = (double*)p;
+}
+
 void dot_noalloc(const Mesh& m, int level, int prec, const void* x1, const void* x2,
                  double* out_dev, cudaStream_t st) {
   const LevelView& L = m.levels[level].lv;
-  const int64_t ncta = (L.len + kSlotsPerCta - 1) / kSlotsPerCta;
-  if (ncta > kNoallocPartials)
-    throw std::invalid_argument("hhg_dot_noalloc: level vector of " + std::to_string(L.len) +
-                                " slots exceeds the static scratch limit of " +
-                                std::to_string((int64_t)kNoallocPartials * kSlotsPerCta) + " slots");
-  int dev = 0;
-  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
-  double* partials = partials_address(dev);
-  {
-    if (prec == 0)
-      k_dot_chunks<double><<<(int)ncta, kNoallocThreads, 0, st>>>(m.tab, L, (const double*)x1,
-                                                                  (const double*)x2, partials);
-    else
-      k_dot_chunks<float><<<(int)ncta, kNoallocThreads, 0, st>>>(m.tab, L, (const float*)x1,
-                                                                 (const float*)x2, partials);
-    check_cuda(cudaGetLastError(), "dot_noalloc chunks");
-  }
-  {
-    k_sum_noalloc<<<1, kNoallocThreads, 0, st>>>(partials, (int)ncta, out_dev);
-    check_cuda(cudaGetLastError(), "dot_noalloc sum");
-  }
+  const int ncta = noalloc_ctas(L.len);
+  if (!m.noalloc_partials) throw std::runtime_error("hhg_dot_noalloc: scratch address not set up");
+  double* partials = m.noalloc_partials;
+  if (prec == 0)
+    HHG_LAUNCH(HHG_K_OTHER, level, st, "dot_noalloc chunks",
+               k_dot_chunks<double><<<ncta, kNoallocThreads, 0, st>>>(m.tab, L, (const double*)x1,
+                                                                     (const double*)x2, partials));
+  else
+    HHG_LAUNCH(HHG_K_OTHER, level, st, "dot_noalloc chunks",
+               k_dot_chunks<float><<<ncta, kNoallocThreads, 0, st>>>(m.tab, L, (const float*)x1,
+                                                                    (const float*)x2, partials));
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "dot_noalloc sum",
+             k_sum_noalloc<<<1, kNoallocThreads, 0, st>>>(partials, ncta, out_dev));
 }
 
 }  // namespace hhg

@@ -388,9 +388,11 @@ __device__ __forceinline__ void face_small(const MeshTables& M, const LevelView&
 // set (the previous launch, which used it, has finished), and after the
 // first barrier -- when every leader has read bar[0] -- CTA 0 flips bar[0]
 // for the next launch.  A wait gives up after about a second: it sets *err
-// and goes on (the sweep's result is then wrong, the host reports a timeout
-// and zeroes the words).
-constexpr long kBarrierPolls = 1L << 21;   // L2 round trips: a second or two
+// and goes on without waiting at the launch's later barriers (the sweep's
+// result is then wrong, the host reports a timeout and zeroes the words).
+// A test hook (hhg_debug_wait_limit) can raise the awaited count above the
+// grid size -- arrivals that never come -- and shorten the limit.
+constexpr long long kBarrierPolls = 1LL << 21;   // L2 round trips: a second or two
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -403,13 +405,16 @@ __device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
 }
 
 struct GridBar {
-  unsigned* cnt;   // this launch's counter set (thread 0 of each CTA)
-  unsigned set;    // its index, 0 or 1
-  int k;           // barriers passed
+  unsigned* cnt;      // this launch's counter set (thread 0 of each CTA)
+  unsigned set;       // its index, 0 or 1
+  int k;              // barriers passed
+  unsigned target;    // arrivals awaited: the grid size (+ a test hook's extra)
+  long long polls;    // polls before a wait gives up
+  bool failed;        // a wait of this CTA gave up: later barriers do not wait
 };
 
-__device__ __forceinline__ GridBar barrier_start(unsigned* bar) {
-  GridBar g{nullptr, 0u, 0};
+__device__ __forceinline__ GridBar barrier_start(unsigned* bar, unsigned extra, long long polls) {
+  GridBar g{nullptr, 0u, 0, gridDim.x + extra, polls > 0 ? polls : kBarrierPolls, false};
   if (threadIdx.x == 0) {
     g.set = ld_acquire(bar) & 1u;
     g.cnt = bar + 4 + g.set * kGridBarSlots;
@@ -426,10 +431,10 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, GridBar& g, int* err
   if (threadIdx.x == 0) {
     unsigned* c = g.cnt + g.k;
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c) : "memory");
-    for (long polls = 0; ld_acquire(c) < gridDim.x;) {
-      if (++polls > kBarrierPolls) {
+    for (long long polls = 0; !g.failed && ld_acquire(c) < g.target;) {
+      if (++polls > g.polls) {
         atomicExch(err, 1);
-        break;
+        g.failed = true;
       }
     }
     if (g.k == 0 && blockIdx.x == 0) st_relaxed(bar, g.set ^ 1u);
@@ -450,9 +455,10 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
     k_gs_sweep(MeshTables M, LevelView L, T* xin, T* xout, const T* __restrict__ b,
                const T* __restrict__ bsf, const T* __restrict__ k, const int4* __restrict__ tasks, int ntasks,
                const int* __restrict__ clist, const __grid_constant__ EdgeColours cs, int small,
-               const unsigned short* __restrict__ spts, int4 sptr, unsigned* bar, int* err) {
+               const unsigned short* __restrict__ spts, int4 sptr, unsigned* bar, int* err,
+               unsigned bar_extra, long long bar_polls) {
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  GridBar gb = barrier_start(bar);
+  GridBar gb = barrier_start(bar, bar_extra, bar_polls);
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kStripWarps + (int)(threadIdx.x >> 5);
   const int nw = gridDim.x * kStripWarps;
@@ -639,7 +645,7 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
                                 (const int4*)c.tasks, c.ntasks, (const int*)ld.colour_list, cs, small,
                                 (const unsigned short*)ld.small_pts,
                                 make_int4(ld.small_ptr[0], ld.small_ptr[1], ld.small_ptr[2], ld.small_ptr[3]),
-                                m.gbar, m.err),
+                                m.gbar, m.err, m.dbg_bar_extra, m.dbg_bar_polls),
              "whole sweep launch");
 }
 

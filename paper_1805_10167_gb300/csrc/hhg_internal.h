@@ -243,6 +243,12 @@ struct Mesh {
   double* scalars = nullptr;        // 16 doubles of device scalars
   int* err = nullptr;               // device error word: 1 = a bounded wait gave up
   unsigned* gbar = nullptr;         // device state of the whole-sweep kernel (kGridBarWords words)
+  // test hook of the bounded waits (hhg_debug_wait_limit): extra arrivals the
+  // whole-sweep kernel's grid barriers await, and their poll limit (0 = default)
+  unsigned dbg_bar_extra = 0;
+  long long dbg_bar_polls = 0;
+  double* xy_dev = nullptr;         // macro-vertex coordinates (2 * nv doubles)
+  double* noalloc_partials = nullptr;  // device address of hhg_dot_noalloc's static array (noalloc_setup)
   int device = 0;
 };
 
@@ -297,6 +303,10 @@ void coarsen_k(const Mesh& m, int coarse_level, int prec_src_dst, cudaStream_t s
 void load_k_fine(const Mesh& m, const double* k_canon, cudaStream_t st);
 void convert_k_to_f32(const Mesh& m, int level, cudaStream_t st);
 void sqrt_scalar(double* v, cudaStream_t st);
+// coordinates of every slot of a level vector: x at xy_out[s], y at xy_out[len + s]
+void dof_coords(const Mesh& m, int level, double* xy_out, cudaStream_t st);
+// looks up hhg_dot_noalloc's static scratch and loads its kernels (mesh set-up)
+void noalloc_setup(Mesh& m);
 void dot_noalloc(const Mesh& m, int level, int prec, const void* x1, const void* x2,
                  double* out_dev, cudaStream_t st);
 void scaled_residual(const Mesh& m, int level, int prec, const void* x, const void* b, float* s,
@@ -396,6 +406,16 @@ class LaunchScope {
   cudaEvent_t start_ = nullptr, stop_ = nullptr;
 };
 void profile_begin(uint32_t mask, int level);
+inline void check_launch(const char* what) { check_cuda(cudaGetLastError(), what); }
+
+// Launch `...` counted (and, when profiled, timed) as class `cls` on `level`.
+#define HHG_LAUNCH(cls, level, st, what, ...)  \
+  do {                                         \
+    LaunchScope hhg_ls_((cls), (level), (st)); \
+    __VA_ARGS__;                               \
+    check_launch(what);                        \
+  } while (0)
+
 void profile_end(int64_t* launches, double* ms);
 bool profiling_on();
 

@@ -26,15 +26,6 @@ void check_cuda(cudaError_t e, const char* what) {
   if (e != cudaSuccess) throw std::runtime_error(std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-static inline void check_launch(const char* what) { check_cuda(cudaGetLastError(), what); }
-
-// Launch `...` counted (and, when profiled, timed) as class `cls` on `level`.
-#define HHG_LAUNCH(cls, level, st, what, ...)  \
-  do {                                         \
-    LaunchScope hhg_ls_((cls), (level), (st)); \
-    __VA_ARGS__;                               \
-    check_launch(what);                        \
-  } while (0)
 
 static inline int blocks_for(int64_t n, int per_block, int cap) {
   int64_t b = (n + per_block - 1) / per_block;
@@ -552,6 +543,69 @@ __global__ void k_canon_face(MeshTables M, LevelView L, const T* __restrict__ sr
   }
 }
 
+// --------------------------------------------------------------- coordinates
+// Point t (0..N) of the macro-edge from vertex lo to vertex hi: the vertices
+// themselves at t = 0, N; lo + (t / N)(hi - lo) in between, evaluated as
+// written (no contraction into an FMA).
+__device__ __forceinline__ void edge_point_xy(const double* __restrict__ xy, int lo, int hi, int t,
+                                              int N, double& x, double& y) {
+  if (t == 0) { x = xy[2 * lo]; y = xy[2 * lo + 1]; return; }
+  if (t == N) { x = xy[2 * hi]; y = xy[2 * hi + 1]; return; }
+  const double s = (double)t / (double)N;
+  x = __dadd_rn(xy[2 * lo], __dmul_rn(s, __dsub_rn(xy[2 * hi], xy[2 * lo])));
+  y = __dadd_rn(xy[2 * lo + 1], __dmul_rn(s, __dsub_rn(xy[2 * hi + 1], xy[2 * lo + 1])));
+}
+
+// Coordinates of every slot of a level vector (Sec. 3.1: lattice point (i, j)
+// of a face sits at v0 + (i / N)(v1 - v0) + (j / N)(v2 - v0) in the face's
+// counter-clockwise frame).  Face boundary slots hold their owner's
+// coordinates (computed along the owning edge, as the ghost copies of a level
+// vector hold the owner's values).  x goes to out[s], y to out[len + s];
+// padding slots are not written.
+__global__ void k_dof_coords(MeshTables M, LevelView L, const double* __restrict__ xy,
+                             double* __restrict__ out) {
+  const int N = L.N;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < L.len;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    double x, y;
+    if (s < L.e_off) {
+      if (s >= M.nv) continue;
+      x = xy[2 * s];
+      y = xy[2 * s + 1];
+    } else if (s < L.f_off) {
+      const int64_t q = s - L.e_off;
+      const int64_t e = q / L.ES;
+      const int t = (int)(q - e * L.ES);
+      if (e >= M.ne || t > N) continue;
+      edge_point_xy(xy, M.edges[e].lo, M.edges[e].hi, t, N, x, y);
+    } else {
+      const int64_t q = s - L.f_off;
+      const int64_t f = q / L.FS;
+      const int64_t r = q - f * L.FS;
+      const int j = (int)(r / L.S), i = (int)(r - (int64_t)j * L.S);
+      if (f >= M.nf || i + j > N) continue;
+      const FaceRec& F = M.faces[f];
+      // boundary: side 0 (j = 0) runs v0 -> v1 at p = i, side 1 (i + j = N)
+      // v1 -> v2 at p = j, side 2 (i = 0) v2 -> v0 at p = N - j
+      const int side = j == 0 ? 0 : (i + j == N ? 1 : (i == 0 ? 2 : -1));
+      if (side >= 0) {
+        const int p = side == 0 ? i : (side == 1 ? j : N - j);
+        const EdgeRec& E = M.edges[F.edge[side]];
+        edge_point_xy(xy, E.lo, E.hi, F.aligned[side] ? p : N - p, N, x, y);
+      } else {
+        const double si = (double)i / (double)N, sj = (double)j / (double)N;
+        const int a = F.v[0], b = F.v[1], c = F.v[2];
+        x = __dadd_rn(__dadd_rn(xy[2 * a], __dmul_rn(si, __dsub_rn(xy[2 * b], xy[2 * a]))),
+                      __dmul_rn(sj, __dsub_rn(xy[2 * c], xy[2 * a])));
+        y = __dadd_rn(__dadd_rn(xy[2 * a + 1], __dmul_rn(si, __dsub_rn(xy[2 * b + 1], xy[2 * a + 1]))),
+                      __dmul_rn(sj, __dsub_rn(xy[2 * c + 1], xy[2 * a + 1])));
+      }
+    }
+    out[s] = x;
+    out[L.len + s] = y;
+  }
+}
+
 // --------------------------------------------------------------- coefficient
 // Canonical element order -> up/down slot arrays of the finest level (double).
 __global__ void k_load_k(MeshTables M, LevelView L, const double* __restrict__ kc,
@@ -997,6 +1051,12 @@ void canonical_op(const Mesh& m, int level, int prec, const void* src, void* dst
                   cudaStream_t st) {
   if (prec == 0) canonical_t(m, level, (const double*)src, (double*)dst, to_canon, st);
   else canonical_t(m, level, (const float*)src, (float*)dst, to_canon, st);
+}
+
+void dof_coords(const Mesh& m, int level, double* xy_out, cudaStream_t st) {
+  const LevelView& L = m.levels[level].lv;
+  HHG_LAUNCH(HHG_K_OTHER, level, st, "dof coords",
+             k_dof_coords<<<blocks_for(L.len, kThreads, 152 * 16), kThreads, 0, st>>>(m.tab, L, m.xy_dev, xy_out));
 }
 
 void load_k_fine(const Mesh& m, const double* k_canon, cudaStream_t st) {

@@ -310,6 +310,7 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
     }
     // ---- device part: everything above is validated on the host first
     check_cuda(cudaGetDevice(&m.device), "cudaGetDevice");
+    m.xy_dev = upload(m, m.h_xy);
     m.tab.faces = upload(m, m.h_faces);
     m.tab.edges = upload(m, m.h_edges);
     m.tab.verts = upload(m, m.h_verts);
@@ -352,6 +353,7 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
     m.scalars = (double*)dev_alloc(m, 16 * sizeof(double));
     m.err = (int*)dev_alloc(m, 16 * sizeof(int));
     m.gbar = (unsigned*)dev_alloc(m, kGridBarWords * sizeof(unsigned));   // zeroed
+    noalloc_setup(m);
     std::vector<double> k0(m.nf, 1.0);
     assemble_level0(m, k0);
     graphs_create(m);

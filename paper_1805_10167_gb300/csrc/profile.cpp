@@ -35,7 +35,7 @@ cudaEvent_t take() {
 LaunchScope::LaunchScope(int cls, int level, cudaStream_t st) : cls_(cls), st_(st) {
   Prof& p = P();
   p.launches[cls] += 1;
-  if (p.on && (p.mask >> cls & 1u) && level == p.level) {
+  if (p.on && (p.mask >> cls & 1u) && (p.level < 0 || level == p.level)) {
     start_ = take();
     stop_ = take();
     check_cuda(cudaEventRecord(start_, st), "event record");

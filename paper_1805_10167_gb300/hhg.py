@@ -68,6 +68,9 @@ _SIGS = {
     "hhg_set_coefficient": [_P, _P, _P],
     "hhg_from_canonical": [_P, C.c_int32, C.c_int32, _P, _P, _P],
     "hhg_to_canonical": [_P, C.c_int32, C.c_int32, _P, _P, _P],
+    "hhg_dof_coords": [_P, C.c_int32, _P, _P],
+    "hhg_sync": [_P, _P],
+    "hhg_debug_wait_limit": [_P, C.c_int32, C.c_int64],
     "hhg_apply": [_P, C.c_int32, C.c_int32, _P, _P, _P],
     "hhg_residual": [_P, C.c_int32, C.c_int32, _P, _P, _P, _P, _P],
     "hhg_assign": [_P, C.c_int32, C.c_int32, C.c_double, _P, C.c_double, _P, _P, _P],
@@ -202,6 +205,15 @@ class Mesh:
 
     def to_canonical(self, level, src, dst, prec=F64, stream=None):
         _check(lib.hhg_to_canonical(self.h, level, prec, _ptr(src), _ptr(dst), _stream(stream)))
+
+    def sync(self, stream=None):
+        _check(lib.hhg_sync(self.h, _stream(stream)))
+
+    def debug_wait_limit(self, extra_arrivals, max_polls=0):
+        _check(lib.hhg_debug_wait_limit(self.h, extra_arrivals, max_polls))
+
+    def dof_coords(self, level, xy_dev, stream=None):
+        _check(lib.hhg_dof_coords(self.h, level, _ptr(xy_dev), _stream(stream)))
 
     def apply(self, level, x, y, prec=F64, stream=None):
         _check(lib.hhg_apply(self.h, level, prec, _ptr(x), _ptr(y), _stream(stream)))

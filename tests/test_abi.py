@@ -74,3 +74,39 @@ def test_invalid_batch_rejected_on_host():
     with pytest.raises(hhg.HHGError) as e:
         hhg.Batch([good], [11])
     assert e.value.status == hhg.ERR_ARG
+
+
+NOALLOC_PROG = r"""
+#include <cstdio>
+#include "noalloc.h"
+using namespace hhg;
+static int rejects(int64_t len) {
+  try { noalloc_ctas(len); } catch (const std::invalid_argument&) { return 1; }
+  return 0;
+}
+int main() {
+  const int64_t lim = kNoallocMaxSlots;
+  std::printf("%lld %d %d %d %d %d %d %d\n", (long long)lim, noalloc_ctas(0), noalloc_ctas(1),
+              noalloc_ctas(kNoallocSlotsPerCta), noalloc_ctas(kNoallocSlotsPerCta + 1),
+              noalloc_ctas(lim), rejects(lim), rejects(lim + 1));
+  return 0;
+}
+"""
+
+
+def test_noalloc_scratch_limit_boundary(tmp_path):
+    """hhg_dot_noalloc's static array holds 2^14 partial sums of 2^14 slots
+    each: a level vector of exactly 2^28 slots fits (2^14 CTAs), one slot
+    more is rejected (host logic of csrc/noalloc.h, compiled with g++)."""
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    src = tmp_path / "noalloc_limit.cpp"
+    src.write_text(NOALLOC_PROG)
+    exe = tmp_path / "noalloc_limit"
+    subprocess.run([gxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_1805_10167_gb300", "csrc"),
+                    str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert [int(v) for v in out] == [2 ** 28, 0, 1, 1, 2, 2 ** 14, 0, 1]

@@ -54,6 +54,48 @@ def test_cnn_forward_parity(vark, path):
     P.close()
 
 
+@pytest.mark.parametrize("path", ["mma_sync", "tcgen05"])
+def test_cnn_forward_parity_level9(path):
+    """The network kernel's level-9 tile grid (each face lattice 513 x 513,
+    output tiles cut by the face diagonal and a ragged last tile column)
+    against the FP64 oracle on sampled faces of the unit square with the
+    random-field coefficient."""
+    torch = pytest.importorskip("torch")
+    from oracle import mesh as om
+    from paper_1805_10167_gb300 import hhg
+    L = 9
+    xy, tri = inputs.unit_square_mesh()
+    lv = om.Level(om.MacroMesh(xy, tri), L)
+    k_dev = inputs.grf_coefficient(inputs.element_centroids(xy, tri, L, device="cuda"), seed=42)
+    k = k_dev.cpu().numpy()           # the same seeded field for both sides
+    g = hhg.Mesh(xy, tri, L)
+    g.set_coefficient(k_dev)
+    p = _weights(3)
+    g.learned_set_weights(learned.flatten(p).astype(np.float32))
+    code = {"mma_sync": hhg.TC_MMA_SYNC, "tcgen05": hhg.TC_TCGEN05}[path]
+    assert g.learned_tensor_path(code) == code
+    I = g.info(L)
+    s = np.random.default_rng(11).standard_normal(lv.n)
+    s32 = torch.zeros(I.vec_len, dtype=torch.float32, device="cuda")
+    g.from_canonical(L, torch.tensor(s, dtype=torch.float32, device="cuda"), s32, prec=1)
+    d = torch.zeros(I.vec_len, dtype=torch.float32, device="cuda")
+    g.learned_apply(L, s32, d=d, prec=1)
+    out = torch.zeros(I.n_nodes, dtype=torch.float32, device="cuda")
+    g.to_canonical(L, d, out, prec=1)
+    got = out.double().cpu().numpy()
+    images = learned.face_images(lv, s.astype(np.float32).astype(np.float64), k)
+    worst = 0.0
+    for f in (0, 3, 6):
+        X, M, Mi, G, sig = images[f]
+        want, _ = learned.forward(p, X, M, Mi)
+        ok = Mi > 0
+        e = np.abs(got[G[ok]] - sig * want[ok]).max() / np.abs(sig * want[ok]).max()
+        worst = max(worst, e)
+    print(f"CNN forward level 9 ({path}) BF16 vs FP64 oracle: max-norm relative error {worst:.3e}")
+    assert worst < BF16_TOL
+    g.close()
+
+
 def _cots(xy, tri, f):
     v0, v1, v2 = xy[tri[f]]
     def cot(a, b, c):

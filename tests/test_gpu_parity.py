@@ -47,6 +47,46 @@ def test_canonical_roundtrip_and_ghost_copies(pairs, name, L):
                 assert h[base + j * S + i] == c[G[f][j, i]]
 
 
+@pytest.mark.parametrize("name,L", CASES)
+def test_dof_coords_parity(pairs, name, L):
+    """hhg_dof_coords against the oracle's Level.coords (Sec. 3.1 face and
+    edge frames) on every level: both halves through hhg_to_canonical, and
+    every face slot (ghost copies included) against the oracle's owner
+    coordinates via the face's id table."""
+    torch = pytest.importorskip("torch")
+    P = pairs(name, L)
+    for l in range(L + 1):
+        I = P.info(l)
+        n = I.vec_len
+        xy = torch.full((2 * n,), float("nan"), dtype=torch.float64, device="cuda")
+        P.g.dof_coords(l, xy)
+        want = P.H.levels[l].coords
+        got_x = P.from_dev(l, xy[:n])
+        got_y = P.from_dev(l, xy[n:])
+        assert np.abs(got_x - want[:, 0]).max() <= 1e-15
+        assert np.abs(got_y - want[:, 1]).max() <= 1e-15
+        h = xy.cpu().numpy()
+        N, S = I.N, I.row_stride
+        for f, G in enumerate(P.H.levels[l].face_ids):
+            base = I.f_off + f * I.face_stride
+            jj, ii = np.nonzero(G >= 0)
+            slots = base + jj * S + ii
+            assert np.abs(h[slots] - want[G[jj, ii], 0]).max() <= 1e-15
+            assert np.abs(h[n + slots] - want[G[jj, ii], 1]).max() <= 1e-15
+            # a copy equals its owner's slot bit for bit (corner v0 = vertex slot)
+            assert h[base] == h[I.v_off + P.M.tri[f][0]]
+
+
+def test_dof_coords_rejects_bad_arguments(pairs):
+    P = pairs("square", 1)
+    with pytest.raises(P.hhg.HHGError) as e:
+        P.g.dof_coords(1, None)
+    assert e.value.status == P.hhg.ERR_ARG
+    with pytest.raises(P.hhg.HHGError) as e:
+        P.g.dof_coords(2, P.new(1))
+    assert e.value.status == P.hhg.ERR_ARG
+
+
 # ------------------------------------------------------------------ operator
 @pytest.mark.parametrize("name,L", CASES)
 @pytest.mark.parametrize("vark", [False, True])
