@@ -417,6 +417,51 @@ hhg_status hhg_sync(hhg_mesh mesh, void* stream);
  * drops captured graphs.  HHG_ERR_ARG for extra_arrivals < 0. */
 hhg_status hhg_debug_wait_limit(hhg_mesh mesh, int32_t extra_arrivals, int64_t max_polls);
 
+/* P2 elements and p-multigrid (Sec. 4.1 P2 elements; Sec. 4.2 stencils of
+ * vertex DoFs and of horizontal, vertical and diagonal edge DoFs; Sec. 4.3
+ * p-refinement between P1 and P2 on one geometric level).  P2 on level L
+ * has one unknown per micro-vertex and per micro-edge midpoint of the
+ * level-L mesh: the lattice points of level L + 1.  A P2 vector of level L
+ * is therefore a level-(L+1) level vector of doubles (hhg_info of level
+ * L + 1: layout, ghost copies, canonical order via hhg_from_canonical /
+ * hhg_to_canonical at level L + 1).  The operator is the P2 stiffness matrix
+ * of -div(grad u) (coefficient k = 1; HHG_ERR_ARG after hhg_set_coefficient
+ * with a field); Dirichlet DoFs as for P1 (the level + 1 lattice points on
+ * Dirichlet macro-edges and vertices).  level must be in 1 .. max_level - 1.
+ * The first smoothing call on a level builds its macro-edge colour tables
+ * (synchronous, allocates once).  FP64. */
+typedef struct {
+  int32_t nu1, nu2;       /* P2 Gauss-Seidel sweeps before / after (2, 2)    */
+  int32_t nu1c, nu2c;     /* the coarse P1 V(nu1c, nu2c) cycle (3, 3)        */
+  int32_t max_iter;       /* hhg_p2_solve: cycles (100)                      */
+  double tol;             /* hhg_p2_solve: ||r|| <= tol ||r0|| (1e-10)        */
+} hhg_p2_opts;
+/* y = A2 x on free DoFs, 0 on Dirichlet DoFs. */
+hhg_status hhg_p2_apply(hhg_mesh mesh, int32_t level, const double* x, double* y, void* stream);
+/* r = b - A2 x (0 on Dirichlet); norm_dev (may be NULL): ||r||_2 over free DoFs. */
+hhg_status hhg_p2_residual(hhg_mesh mesh, int32_t level, const double* x, const double* b, double* r,
+                           double* norm_dev, void* stream);
+/* `sweeps` colour-ordered Gauss-Seidel sweeps in place (HHG_GS_FWD: free
+ * macro-vertices, macro-edge point colours (greedy, canonical order), face
+ * micro-vertex points by the level-L colour (i/2 + 2 (j/2)) mod 3 = 0, 1, 2,
+ * then horizontal, vertical, diagonal edge points; HHG_GS_BWD the exact
+ * reverse).  Asynchronous after the colour tables exist. */
+hhg_status hhg_p2_smooth(hhg_mesh mesh, int32_t level, double* x, const double* b, int32_t smoother,
+                         int32_t sweeps, void* stream);
+/* One p-multigrid cycle: nu1 forward sweeps, P2 residual, restriction by the
+ * transpose of the P1 -> P2 embedding (linear interpolation, i.e. the P1
+ * restriction from level L + 1 to L), one P1 V(nu1c, nu2c) cycle on level L
+ * from zero, prolongation and correction, nu2 backward sweeps.  opts may be
+ * NULL.  Uses the library's level-L and level-(L+1) workspaces. */
+hhg_status hhg_p2_cycle(hhg_mesh mesh, int32_t level, double* x, const double* b, const hhg_p2_opts* opts,
+                        void* stream);
+/* p-multigrid cycles from the guess in x until ||b - A2 x|| <= tol ||b - A2 x0||
+ * (free DoFs); synchronous, one 8-byte readback per cycle, the cycle and
+ * residual replayed as a CUDA graph from their third use on.  Errors as
+ * for hhg_solve. */
+hhg_status hhg_p2_solve(hhg_mesh mesh, int32_t level, double* x, const double* b, const hhg_p2_opts* opts,
+                        hhg_solve_report* rep, void* stream);
+
 /* Message of the last failed call on this thread ('\0'-terminated, truncated
  * to n bytes).  Returns the full message length. */
 size_t hhg_last_error(char* buf, size_t n);

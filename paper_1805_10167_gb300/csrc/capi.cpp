@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -528,6 +529,113 @@ hhg_status hhg_debug_wait_limit(hhg_mesh mesh, int32_t extra_arrivals, int64_t m
     m.dbg_bar_extra = (unsigned)extra_arrivals;
     m.dbg_bar_polls = extra_arrivals > 0 && max_polls > 0 ? (long long)max_polls : 0;
     hhg::graphs_clear(m);
+    return HHG_OK;
+  });
+}
+
+// ---------------------------------------------------------------- P2
+static void p2_vec_args(const hhg::Mesh& m, int level, std::initializer_list<std::pair<const void*, const char*>> v) {
+  if (level < 1 || level + 1 > m.max_level) throw ArgError("P2 level must be in 1 .. max_level - 1");
+  for (const auto& a : v) need_vec(a.first, a.second);
+}
+
+static hhg_p2_opts p2_defaults(const hhg_p2_opts* o) {
+  hhg_p2_opts d{2, 2, 3, 3, 100, 1e-10};
+  if (o) d = *o;
+  if (d.nu1 < 0 || d.nu2 < 0 || d.nu1c < 0 || d.nu2c < 0 || d.max_iter < 0 || !(d.tol >= 0.0))
+    throw ArgError("bad P2 options");
+  return d;
+}
+
+hhg_status hhg_p2_apply(hhg_mesh mesh, int32_t level, const double* x, double* y, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    p2_vec_args(m, level, {{x, "x"}, {y, "y"}});
+    hhg::p2_apply(m, level, x, y, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_p2_residual(hhg_mesh mesh, int32_t level, const double* x, const double* b, double* r,
+                           double* norm_dev, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    p2_vec_args(m, level, {{x, "x"}, {b, "b"}, {r, "r"}});
+    hhg::p2_residual(m, level, x, b, r, norm_dev, S(stream));
+    if (norm_dev) hhg::sqrt_scalar(norm_dev, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_p2_smooth(hhg_mesh mesh, int32_t level, double* x, const double* b, int32_t smoother,
+                         int32_t sweeps, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    p2_vec_args(m, level, {{x, "x"}, {b, "b"}});
+    if (smoother != HHG_GS_FWD && smoother != HHG_GS_BWD) throw ArgError("P2 smoother: HHG_GS_FWD or HHG_GS_BWD");
+    if (sweeps < 0) throw ArgError("sweeps < 0");
+    hhg::p2_smooth(m, level, x, b, smoother == HHG_GS_FWD, sweeps, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_p2_cycle(hhg_mesh mesh, int32_t level, double* x, const double* b, const hhg_p2_opts* opts,
+                        void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    p2_vec_args(m, level, {{x, "x"}, {b, "b"}});
+    const hhg_p2_opts o = p2_defaults(opts);
+    hhg::p2_cycle(m, level, x, b, o.nu1, o.nu2, o.nu1c, o.nu2c, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_p2_solve(hhg_mesh mesh, int32_t level, double* x, const double* b, const hhg_p2_opts* opts,
+                        hhg_solve_report* rep, void* stream) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    p2_vec_args(m, level, {{x, "x"}, {b, "b"}});
+    const hhg_p2_opts o = p2_defaults(opts);
+    cudaStream_t st = S(stream);
+    double* r = (double*)m.levels[level + 1].r[0];
+    double* nrm = m.scalars;
+    hhg::p2_edge_colours(m, level);   // colour tables first (synchronous, before any capture)
+    hhg::p2_residual(m, level, x, b, r, nrm, st);
+    const double r0 = std::sqrt(read_scalar(nrm, st));
+    double rn = r0;
+    int it = 0;
+    hhg_status status = std::isfinite(r0) ? HHG_OK : HHG_ERR_NAN;
+    auto record = [&](int k, double v) {
+      if (rep && rep->history && k < rep->history_cap) rep->history[k] = v;
+    };
+    record(0, r0);
+    while (status == HHG_OK && rn > o.tol * r0 && r0 > 0.0) {
+      if (it >= o.max_iter) {
+        status = HHG_ERR_NOT_CONVERGED;
+        break;
+      }
+      const hhg::GraphKey key{7, (uint64_t)level, (uint64_t)o.nu1, (uint64_t)o.nu2,
+                              ((uint64_t)o.nu1c << 32) | (uint64_t)o.nu2c, 0, hhg::key_ptr(x), hhg::key_ptr(b)};
+      hhg::graphed(m, key, st, [&](cudaStream_t s) {
+        hhg::p2_cycle(m, level, x, b, o.nu1, o.nu2, o.nu1c, o.nu2c, s);
+        hhg::p2_residual(m, level, x, b, r, nrm, s);
+      });
+      ++it;
+      rn = std::sqrt(read_scalar(nrm, st));
+      record(it, rn);
+      if (!std::isfinite(rn)) status = HHG_ERR_NAN;
+    }
+    if (device_timed_out(m, st)) status = HHG_ERR_TIMEOUT;
+    if (rep) {
+      rep->iterations = it;
+      rep->status = status;
+      rep->r0 = r0;
+      rep->r_final = rn;
+      rep->smoother_used = HHG_SMOOTH_GS;
+    }
+    if (status == HHG_ERR_TIMEOUT) return fail(status, "a device-side wait gave up");
+    if (status == HHG_ERR_NAN) return fail(status, "non-finite residual norm");
+    if (status == HHG_ERR_NOT_CONVERGED) return fail(status, "max_iter reached");
     return HHG_OK;
   });
 }

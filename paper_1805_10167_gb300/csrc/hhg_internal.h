@@ -205,6 +205,7 @@ struct LevelData {
 };
 
 struct Learned;
+struct P2Data;
 struct KrylovSpace;
 struct GraphCache;
 
@@ -212,6 +213,7 @@ struct Mesh {
   int nv = 0, ne = 0, nf = 0, max_level = 0;
   Learned* learned = nullptr;       // learned-smoother weights and optimiser state
   KrylovSpace* krylov = nullptr;    // FGMRES basis vectors
+  P2Data* p2 = nullptr;             // P2 stencil weights and colour tables (p2.cu)
   GraphCache* graphs = nullptr;     // captured launch sequences (graph.cpp)
   std::vector<FaceRec> h_faces;
   std::vector<EdgeRec> h_edges;
@@ -357,6 +359,16 @@ void learned_grad(Mesh& m, int B, const float* X_dev, const float* S_dev, const 
 void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr, uint64_t seed,
                    float* loss_hist, cudaStream_t st);
 void krylov_free(Mesh& m);
+// P2 elements on level L (unknowns: the level-(L+1) lattice) and p-multigrid
+void p2_setup(Mesh& m);
+void p2_free(Mesh& m);
+int p2_edge_colours(const Mesh& m, int L);
+void p2_apply(const Mesh& m, int L, const double* x, double* y, cudaStream_t st);
+void p2_residual(const Mesh& m, int L, const double* x, const double* b, double* r, double* norm2_dev,
+                 cudaStream_t st);
+void p2_smooth(const Mesh& m, int L, double* x, const double* b, bool forward, int sweeps, cudaStream_t st);
+void p2_cycle(const Mesh& m, int L, double* x, const double* b, int nu1, int nu2, int nu1c, int nu2c,
+              cudaStream_t st);
 // batched flexible CG passes over the problems (Blocks) of a merged mesh;
 // sc = 6 arrays of nb per-problem scalars (p.q, r.z, ||r||^2, q.z, ||r0||^2, threshold)
 void batch_cg_init(const Mesh& m, const double* norms, double tol, bool first, double* sc, cudaStream_t st);

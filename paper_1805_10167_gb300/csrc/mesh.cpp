@@ -354,12 +354,14 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
     m.err = (int*)dev_alloc(m, 16 * sizeof(int));
     m.gbar = (unsigned*)dev_alloc(m, kGridBarWords * sizeof(unsigned));   // zeroed
     noalloc_setup(m);
+    p2_setup(m);
     std::vector<double> k0(m.nf, 1.0);
     assemble_level0(m, k0);
     graphs_create(m);
     check_cuda(cudaDeviceSynchronize(), "mesh setup");
   } catch (...) {
     graphs_destroy(m);
+    p2_free(m);
     for (void* p : m.allocations) cudaFree(p);
     delete mp;
     throw;
@@ -373,6 +375,7 @@ void mesh_destroy_internal(Mesh* m) {
   graphs_destroy(*m);
   learned_free(*m);
   krylov_free(*m);
+  p2_free(*m);
   for (void* p : m->allocations) cudaFree(p);
   delete m;
 }

@@ -59,6 +59,11 @@ class SolveReport(C.Structure):
                 ("judge_learned", C.c_double), ("judge_gs", C.c_double)]
 
 
+class P2Opts(C.Structure):
+    _fields_ = [("nu1", C.c_int32), ("nu2", C.c_int32), ("nu1c", C.c_int32), ("nu2c", C.c_int32),
+                ("max_iter", C.c_int32), ("tol", C.c_double)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "hhg_mesh_create": [C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int32), C.c_int64,
@@ -70,6 +75,11 @@ _SIGS = {
     "hhg_to_canonical": [_P, C.c_int32, C.c_int32, _P, _P, _P],
     "hhg_dof_coords": [_P, C.c_int32, _P, _P],
     "hhg_sync": [_P, _P],
+    "hhg_p2_apply": [_P, C.c_int32, _P, _P, _P],
+    "hhg_p2_residual": [_P, C.c_int32, _P, _P, _P, _P, _P],
+    "hhg_p2_smooth": [_P, C.c_int32, _P, _P, C.c_int32, C.c_int32, _P],
+    "hhg_p2_cycle": [_P, C.c_int32, _P, _P, C.POINTER(P2Opts), _P],
+    "hhg_p2_solve": [_P, C.c_int32, _P, _P, C.POINTER(P2Opts), C.POINTER(SolveReport), _P],
     "hhg_debug_wait_limit": [_P, C.c_int32, C.c_int64],
     "hhg_apply": [_P, C.c_int32, C.c_int32, _P, _P, _P],
     "hhg_residual": [_P, C.c_int32, C.c_int32, _P, _P, _P, _P, _P],
@@ -205,6 +215,33 @@ class Mesh:
 
     def to_canonical(self, level, src, dst, prec=F64, stream=None):
         _check(lib.hhg_to_canonical(self.h, level, prec, _ptr(src), _ptr(dst), _stream(stream)))
+
+    # ---- P2 elements and p-multigrid (vectors: level + 1 layout)
+    def p2_apply(self, level, x, y, stream=None):
+        _check(lib.hhg_p2_apply(self.h, level, _ptr(x), _ptr(y), _stream(stream)))
+
+    def p2_residual(self, level, x, b, r, norm_dev=None, stream=None):
+        _check(lib.hhg_p2_residual(self.h, level, _ptr(x), _ptr(b), _ptr(r), _ptr(norm_dev), _stream(stream)))
+
+    def p2_smooth(self, level, x, b, smoother=GS_FWD, sweeps=1, stream=None):
+        _check(lib.hhg_p2_smooth(self.h, level, _ptr(x), _ptr(b), smoother, sweeps, _stream(stream)))
+
+    def p2_cycle(self, level, x, b, nu1=2, nu2=2, nu1c=3, nu2c=3, stream=None):
+        o = P2Opts(nu1, nu2, nu1c, nu2c, 100, 1e-10)
+        _check(lib.hhg_p2_cycle(self.h, level, _ptr(x), _ptr(b), C.byref(o), _stream(stream)))
+
+    def p2_solve(self, level, x, b, nu1=2, nu2=2, nu1c=3, nu2c=3, tol=1e-10, max_iter=100, stream=None,
+                 raise_on_error=True):
+        """Returns (status, report dict)."""
+        o = P2Opts(nu1, nu2, nu1c, nu2c, max_iter, tol)
+        hist = (C.c_double * (max_iter + 1))()
+        rep = SolveReport(0, 0, 0.0, 0.0, hist, max_iter + 1, 0, 0.0, 0.0)
+        st = lib.hhg_p2_solve(self.h, level, _ptr(x), _ptr(b), C.byref(o), C.byref(rep), _stream(stream))
+        out = {"iterations": rep.iterations, "status": rep.status, "r0": rep.r0, "r_final": rep.r_final,
+               "history": [hist[i] for i in range(min(rep.iterations + 1, max_iter + 1))]}
+        if raise_on_error and st != OK:
+            raise HHGError(st, last_error())
+        return st, out
 
     def sync(self, stream=None):
         _check(lib.hhg_sync(self.h, _stream(stream)))
