@@ -399,6 +399,19 @@ hhg_status hhg_learned_train(hhg_mesh mesh, int32_t level, int32_t n_pairs, int3
                              int32_t batch, float lr, uint64_t seed, float* loss_history_host,
                              void* stream);
 
+/* Coarse tail of the V-cycle (a property of this library, not of the paper's
+ * method): below a small level the cycle's steps are latency-bound, so the
+ * levels up to a cut-off (at most 3) run as one launch of a single CTA with
+ * every level's vectors in shared memory -- the same colour-ordered
+ * Gauss-Seidel, residual, full-weighting restriction, stored-inverse level-0
+ * solve and linear prolongation, from rows assembled on the host (rebuilt by
+ * hhg_set_coefficient); results agree with the level-by-level kernels to
+ * rounding.  Used by every Gauss-Seidel V-cycle when the level-0 solve is
+ * the stored inverse and the levels fit in shared memory.  set != 0:
+ * *level is the highest level the tail may take (0 = off); on return *level
+ * is the cut-off in effect for FP64 cycles.  Synchronous. */
+hhg_status hhg_coarse_tail(hhg_mesh mesh, int32_t set, int32_t* level);
+
 /* Waits for `stream` and reports whether a bounded device-side wait of this
  * mesh's kernels gave up since the last report (HHG_ERR_TIMEOUT; the device
  * error word is then cleared and the next call runs normally).  hhg_solve

@@ -116,6 +116,10 @@ static void vcycle_level(const Mesh& m, int l, int prec, void* x, const void* b,
     coarse_solve(m, prec, b, x, st);
     return;
   }
+  if (smoother == 0 && l <= tail_level(m, prec)) {   // the rest of the cycle in one CTA
+    tail_run(m, l, prec, x, b, nu1, nu2, st);
+    return;
+  }
   const LevelData& ld = m.levels[l];
   const LevelData& lc = m.levels[l - 1];
   // smoother 1: the CNN step alone; 2: a Gauss-Seidel sweep, then the CNN
@@ -509,6 +513,22 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
     if (status == HHG_ERR_TIMEOUT) return fail(status, "a device-side wait gave up");
     if (status == HHG_ERR_NAN) return fail(status, "non-finite residual norm");
     if (status == HHG_ERR_NOT_CONVERGED) return fail(status, "max_iter reached");
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_coarse_tail(hhg_mesh mesh, int32_t set, int32_t* level) {
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    need(level, "level");
+    if (set) {
+      if (*level < 0) throw ArgError("level < 0");
+      hhg::check_cuda(cudaDeviceSynchronize(), "sync");
+      m.tail_on = *level > 0;
+      m.tail_max = *level;
+      hhg::graphs_clear(m);
+    }
+    *level = hhg::tail_level(m, 0);
     return HHG_OK;
   });
 }

@@ -186,6 +186,7 @@ struct LevelData {
   LevelView lv;
   int n_colours = 0;
   std::vector<int> colour_ptr;      // host copy: colour c = [ptr[c], ptr[c+1])
+  std::vector<int> h_colour_list;   // host copy of colour_list
   int* colour_list = nullptr;       // device: packed e * (N + 1) + t
   int64_t n_nodes = 0, n_free = 0;
   // workspaces per precision [0] = double, [1] = float
@@ -206,6 +207,7 @@ struct LevelData {
 
 struct Learned;
 struct P2Data;
+struct TailPlan;
 struct KrylovSpace;
 struct GraphCache;
 
@@ -214,6 +216,9 @@ struct Mesh {
   Learned* learned = nullptr;       // learned-smoother weights and optimiser state
   KrylovSpace* krylov = nullptr;    // FGMRES basis vectors
   P2Data* p2 = nullptr;             // P2 stencil weights and colour tables (p2.cu)
+  TailPlan* tail = nullptr;         // one-CTA coarse tail of the V-cycle (tail.cu)
+  bool tail_on = true;              // hhg_coarse_tail
+  int tail_max = 3;
   GraphCache* graphs = nullptr;     // captured launch sequences (graph.cpp)
   std::vector<FaceRec> h_faces;
   std::vector<EdgeRec> h_edges;
@@ -359,6 +364,14 @@ void learned_grad(Mesh& m, int B, const float* X_dev, const float* S_dev, const 
 void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr, uint64_t seed,
                    float* loss_hist, cudaStream_t st);
 void krylov_free(Mesh& m);
+// One-CTA coarse tail of the V-cycle: tables of levels 0..3 (k_up / k_dn: per
+// level the host element coefficients in face slot layout, empty for k = 1);
+// the level a cycle may hand over to it (0: none); the cycle from level l.
+void tail_build(Mesh& m, const std::vector<std::vector<double>>& k_up,
+                const std::vector<std::vector<double>>& k_dn);
+void tail_free(Mesh& m);
+int tail_level(const Mesh& m, int prec);
+void tail_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2, cudaStream_t st);
 // P2 elements on level L (unknowns: the level-(L+1) lattice) and p-multigrid
 void p2_setup(Mesh& m);
 void p2_free(Mesh& m);

@@ -322,6 +322,7 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
     for (int l = 0; l <= max_level; ++l) {
       LevelData& ld = m.levels[l];
       if (l >= 1) ld.colour_list = upload(m, lists[l]);
+      if (l >= 1) ld.h_colour_list = lists[l];
       for (int p = 0; p < 2; ++p) {
         const size_t bytes = (size_t)ld.lv.len * (p == 0 ? 8 : 4);
         ld.x[p] = dev_alloc(m, bytes);
@@ -357,11 +358,13 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
     p2_setup(m);
     std::vector<double> k0(m.nf, 1.0);
     assemble_level0(m, k0);
+    tail_build(m, {}, {});
     graphs_create(m);
     check_cuda(cudaDeviceSynchronize(), "mesh setup");
   } catch (...) {
     graphs_destroy(m);
     p2_free(m);
+    tail_free(m);
     for (void* p : m.allocations) cudaFree(p);
     delete mp;
     throw;
@@ -376,6 +379,7 @@ void mesh_destroy_internal(Mesh* m) {
   learned_free(*m);
   krylov_free(*m);
   p2_free(*m);
+  tail_free(*m);
   for (void* p : m->allocations) cudaFree(p);
   delete m;
 }
@@ -419,6 +423,7 @@ void set_coefficient(Mesh& m, const double* k_dev, cudaStream_t st) {
     std::vector<double> k0(m.nf, 1.0);
     check_cuda(cudaStreamSynchronize(st), "sync");
     assemble_level0(m, k0);
+    tail_build(m, {}, {});
     return;
   }
   for (int l = 0; l <= m.max_level; ++l) {
@@ -442,6 +447,16 @@ void set_coefficient(Mesh& m, const double* k_dev, cudaStream_t st) {
   for (double v : k0)
     if (!(v > 0.0) || !std::isfinite(v)) throw std::invalid_argument("coefficient must be positive and finite");
   assemble_level0(m, k0);
+  // element coefficients of the tail's levels (small) back to the host
+  std::vector<std::vector<double>> ku, kd;
+  for (int l = 0; l <= std::min(3, m.max_level); ++l) {
+    const LevelView& V = m.levels[l].lv;
+    std::vector<double> both(2 * (size_t)m.nf * V.FS);
+    check_cuda(cudaMemcpy(both.data(), m.levels[l].k[0], both.size() * 8, cudaMemcpyDeviceToHost), "k copy");
+    ku.emplace_back(both.begin(), both.begin() + (size_t)m.nf * V.FS);
+    kd.emplace_back(both.begin() + (size_t)m.nf * V.FS, both.end());
+  }
+  tail_build(m, ku, kd);
   m.vark = true;
 }
 

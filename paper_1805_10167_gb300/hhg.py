@@ -75,6 +75,7 @@ _SIGS = {
     "hhg_to_canonical": [_P, C.c_int32, C.c_int32, _P, _P, _P],
     "hhg_dof_coords": [_P, C.c_int32, _P, _P],
     "hhg_sync": [_P, _P],
+    "hhg_coarse_tail": [_P, C.c_int32, C.POINTER(C.c_int32)],
     "hhg_p2_apply": [_P, C.c_int32, _P, _P, _P],
     "hhg_p2_residual": [_P, C.c_int32, _P, _P, _P, _P, _P],
     "hhg_p2_smooth": [_P, C.c_int32, _P, _P, C.c_int32, C.c_int32, _P],
@@ -242,6 +243,13 @@ class Mesh:
         if raise_on_error and st != OK:
             raise HHGError(st, last_error())
         return st, out
+
+    def coarse_tail(self, level=None):
+        """Reads, or sets when level is given, the coarse-tail cut-off (0 = off);
+        returns the cut-off in effect for FP64 cycles."""
+        v = C.c_int32(level or 0)
+        _check(lib.hhg_coarse_tail(self.h, 0 if level is None else 1, C.byref(v)))
+        return v.value
 
     def sync(self, stream=None):
         _check(lib.hhg_sync(self.h, _stream(stream)))

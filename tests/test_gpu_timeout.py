@@ -23,6 +23,7 @@ def test_grid_barrier_timeout_is_reported_and_recovered(L):
     hhg = P.hhg
     x0, b = P.random(L), P.random(L)
     xd, bd = P.to_dev(L, x0), P.to_dev(L, b)
+    P.g.coarse_tail(0)                           # every level through the whole-sweep kernel
     P.g.sync()                                   # nothing pending
 
     P.g.debug_wait_limit(1, 2000)
