@@ -96,7 +96,8 @@ __device__ __forceinline__ bool interior_pt(int i, int j, int N) { return i >= 1
 constexpr int kPS = 24;                               // BF16 slots per point in h1, h2 records
 constexpr int kF1 = 0, kF2 = 3 * 2 * 2 * 32, kF3 = kF2 + 9 * 2 * 2 * 32;
 constexpr int kFU = kF3 + 9 * 2 * 32;                 // tcgen05 layer-2 operand, 9 x 128 words
-constexpr int kFrag = kFU + 9 * 128;                  // packed weights (uint32)
+constexpr int kF4 = kFU + 9 * 128;                    // layer 3 with the taps as GEMM columns
+constexpr int kFrag = kF4 + 2 * 2 * 32;               // packed weights (uint32)
 static_assert(kFU % 4 == 0, "the tcgen05 operand is copied as 16-byte words");
 constexpr long kUmmaPolls = 1L << 22;                 // mbarrier polls before a product is given up
 
@@ -195,7 +196,7 @@ __device__ __forceinline__ void cnn_layer1(const int (&chunk)[NC], const uint32_
 
 // Layer 2 (16 -> 16) on NC chunks of the h2 region (the last chunk may be
 // ragged: its rows past the region repeat the last point and are not stored).
-template <int NC>
+template <int NC, int NP2_ = NP2>
 __device__ __forceinline__ void cnn_layer2(const int (&chunk)[NC], __nv_bfloat16 (*h1)[kPS],
                                            __nv_bfloat16 (*h2)[kPS], const uint32_t (&bf)[9][2][2],
                                            const float (&bias)[2][2], int i0, int j0, int N, int g, int tq,
@@ -204,7 +205,7 @@ __device__ __forceinline__ void cnn_layer2(const int (&chunk)[NC], __nv_bfloat16
   float d[NC][2][4];
 #pragma unroll
   for (int u = 0; u < NC; ++u) {
-    const int qr = min(chunk[u] * 16 + lrow, NP2 - 1);
+    const int qr = min(chunk[u] * 16 + lrow, NP2_ - 1);
     const int jr = qr / I2;
     pr[u] = jr * I1 + (qr - jr * I2);                    // window origin in h1
 #pragma unroll
@@ -227,7 +228,7 @@ __device__ __forceinline__ void cnn_layer2(const int (&chunk)[NC], __nv_bfloat16
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int q = chunk[u] * 16 + g + 8 * h;
-      if (q < NP2) {
+      if (q < NP2_) {
         const int jj = q / I2, ii = q - jj * I2;
         const bool in = closed_pt(i0 - 1 + ii, j0 - 1 + jj, N);
         uint32_t* row = reinterpret_cast<uint32_t*>(&h2[q][0]);
@@ -279,19 +280,38 @@ __device__ __forceinline__ void cnn_layer3(const int (&chunk)[NC], __nv_bfloat16
   }
 }
 
+// The default network kernel: one CTA of 256 threads per 16 x 32 output tile
+// (input region 22 x 38, h1 20 x 36, h2 18 x 34 in dynamic shared memory;
+// taller tiles than the opt-in variant's recompute fewer halo points: 1.41x
+// of the outputs in layer 1 and 1.20x in layer 2 instead of 1.69x / 1.33x).
+// Layers 1 and 2 as in the helpers above.  Layer 3 (16 -> 1) turns the taps
+// into GEMM columns: D[q][t] = sum_c W3[t][c] h2[q][c] for every h2 point q
+// (one k-step, two n-blocks holding the nine taps), stored tap-major in the
+// shared memory that h1 no longer needs, and each output sums its nine
+// shifted products: d(p) = b3 + sum_t D[p + offset(t)][t] -- 2 mma per 16
+// points where the per-tap form with one useful column takes 9.
 // logk: per face slot the BF16 pair (log k of the upward, of the downward
 // micro-triangle at (i, j)), zero where a triangle does not exist; NULL for
 // k = 1.
+constexpr int BJ = 16;                                    // output rows per tile
+constexpr int BJ0 = BJ + 6, BJ1 = BJ + 4, BJ2 = BJ + 2;
+constexpr int BP0 = BJ0 * I0, BP1 = BJ1 * I1, BP2 = BJ2 * I2, BP3 = BJ * TI;
+constexpr int kBigSmem = BP0 * 8 + (BP1 + BP2) * kPS * 2;  // bytes of dynamic shared memory
+static_assert(BP1 % 16 == 0, "layer-1 region is a whole number of 16-point chunks");
+static_assert(BP2 * 9 * 4 <= BP1 * kPS * 2, "the layer-3 tap products fit where h1 was");
+
 template <typename T>
-__global__ void __launch_bounds__(TJ* TI)
+__global__ void __launch_bounds__(256, 3)
     k_cnn_smooth(LevelView L, const float* __restrict__ s, const uint32_t* __restrict__ logk,
                  const float* __restrict__ scale, const uint32_t* __restrict__ frag,
                  const float* __restrict__ wr, T* x, float* delta) {
-  __shared__ __align__(16) uint2 xin[NP0];                 // 4 BF16 channels per point
-  __shared__ __align__(16) __nv_bfloat16 h1[NP1][kPS];
-  __shared__ __align__(16) __nv_bfloat16 h2[NP2][kPS];
+  extern __shared__ __align__(128) unsigned char cnn_smem[];
+  uint2* xin = reinterpret_cast<uint2*>(cnn_smem);                           // 4 BF16 channels per point
+  __nv_bfloat16(*h1)[kPS] = reinterpret_cast<__nv_bfloat16(*)[kPS]>(cnn_smem + BP0 * 8);
+  __nv_bfloat16(*h2)[kPS] = h1 + BP1;
+  float* Dt = reinterpret_cast<float*>(cnn_smem + BP0 * 8);                 // after layer 2: D[t][q]
   const int f = blockIdx.z;
-  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
+  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * BJ;
   const int N = L.N;
   const float sig = scale[f];
   if (i0 + j0 > N || !(sig > 0.f)) return;   // tile above the triangle / zero residual (uniform per CTA)
@@ -300,7 +320,8 @@ __global__ void __launch_bounds__(TJ* TI)
   const int64_t fb = L.f_off + (int64_t)f * L.FS;
   const uint32_t* lk = logk ? logk + (int64_t)f * L.FS : nullptr;
   const int tid = threadIdx.x;
-  for (int q = tid; q < NP0; q += TJ * TI) {
+  constexpr int NT = 256;
+  for (int q = tid; q < BP0; q += NT) {
     const int jj = q / I0, ii = q - jj * I0;
     const int i = i0 - 3 + ii, j = j0 - 3 + jj;
     float a = 0.f;
@@ -314,7 +335,7 @@ __global__ void __launch_bounds__(TJ* TI)
     xin[q] = make_uint2((pack_bf16(a, 0.f) & 0xffffu) | (kk << 16), kk >> 16);
   }
   const int lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = TJ * TI / 32;
+  constexpr int NW = NT / 32;
   const int g = lane >> 2, tq = lane & 3;
   // ldmatrix row of this lane: point offset in a chunk and channel half
   const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lhalf = (lane >> 4) * 8;
@@ -331,10 +352,11 @@ __global__ void __launch_bounds__(TJ* TI)
     uint32_t* h1w = reinterpret_cast<uint32_t*>(&h1[0][0]);
     __syncthreads();
     int c = warp;
-    for (; c + NW < NP1 / 16; c += 2 * NW)
+    for (; c + NW < BP1 / 16; c += 2 * NW)
       cnn_layer1<2, kPS / 2, 4>({c, c + NW}, X, h1w, bf, bias, i0, j0, N, g, tq);
-    if (c < NP1 / 16) cnn_layer1<1, kPS / 2, 4>({c}, X, h1w, bf, bias, i0, j0, N, g, tq);
+    if (c < BP1 / 16) cnn_layer1<1, kPS / 2, 4>({c}, X, h1w, bf, bias, i0, j0, N, g, tq);
   }
+  constexpr int NC2 = (BP2 + 15) / 16;
   {
     uint32_t bf[9][2][2];
 #pragma unroll
@@ -345,22 +367,51 @@ __global__ void __launch_bounds__(TJ* TI)
         for (int h = 0; h < 2; ++h) bf[t][nb][h] = frag[kF2 + ((t * 2 + nb) * 2 + h) * 32 + lane];
     const float bias[2][2] = {{wr[ob2 + 2 * tq], wr[ob2 + 2 * tq + 1]}, {wr[ob2 + 8 + 2 * tq], wr[ob2 + 9 + 2 * tq]}};
     __syncthreads();
-    constexpr int NC2 = (NP2 + 15) / 16;
     int c = warp;
-    for (; c + NW < NC2; c += 2 * NW) cnn_layer2<2>({c, c + NW}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
-    if (c < NC2) cnn_layer2<1>({c}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
+    for (; c + NW < NC2; c += 2 * NW)
+      cnn_layer2<2, BP2>({c, c + NW}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
+    if (c < NC2) cnn_layer2<1, BP2>({c}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
   }
-  uint32_t bf[9][2];
+  {
+    uint32_t bf[2][2];
 #pragma unroll
-  for (int t = 0; t < 9; ++t)
+    for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) bf[t][h] = frag[kF3 + (t * 2 + h) * 32 + lane];
+      for (int h = 0; h < 2; ++h) bf[nb][h] = frag[kF4 + (nb * 2 + h) * 32 + lane];
+    __syncthreads();   // every warp is past layer 2: h1 becomes the tap products
+    for (int c = warp; c < NC2; c += NW) {
+      uint32_t afr[4];
+      ldsm_x4(afr, &h2[min(c * 16 + lrow, BP2 - 1)][lhalf]);
+      float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+      mma_bf16(d[0], afr, bf[0][0], bf[0][1]);
+      mma_bf16(d[1], afr, bf[1][0], bf[1][1]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = c * 16 + g + 8 * h;
+        if (q >= BP2) continue;
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb) {
+          const int t = nb * 8 + 2 * tq;
+          if (t < 9) Dt[t * BP2 + q] = d[nb][2 * h];
+          if (t + 1 < 9) Dt[(t + 1) * BP2 + q] = d[nb][2 * h + 1];
+        }
+      }
+    }
+  }
   const float b3 = wr[ob3];
   __syncthreads();
-  int c = warp;
-  for (; c + NW < NP3 / 16; c += 2 * NW)
-    cnn_layer3<2, T>({c, c + NW}, h2, bf, b3, sig, fb, S, i0, j0, N, g, tq, lrow, lhalf, x, delta);
-  if (c < NP3 / 16) cnn_layer3<1, T>({c}, h2, bf, b3, sig, fb, S, i0, j0, N, g, tq, lrow, lhalf, x, delta);
+  for (int o = tid; o < BP3; o += NT) {
+    const int ty = o / TI, tx = o - ty * TI;
+    const int i = i0 + tx, j = j0 + ty;
+    if (!interior_pt(i, j, N)) continue;
+    float acc = b3;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc += Dt[t * BP2 + (ty + t / 3) * I2 + tx + t % 3];
+    const int64_t p = fb + (int64_t)j * S + i;
+    acc *= sig;
+    if (delta) delta[p] = acc;
+    if (x) x[p] = (T)((T)x[p] + (T)acc);
+  }
 }
 
 // The network with layer 2 on tcgen05 (the opt-in variant described above):
@@ -546,7 +597,10 @@ __global__ void k_logk_pack(LevelView L, int nf, const float* __restrict__ k, ui
 //   layer 2, entry ((t * 2 + nb) * 2 + h) * 32 + lane: output channel
 //            nb * 8 + g, input channels 2 tq + 8 h, + 1 at tap t;
 //   layer 3, entry (t * 2 + h) * 32 + lane: input channels 2 tq + 8 h, + 1 at
-//            tap t for column 0 (g = 0), zero for the other columns.
+//            tap t for column 0 (g = 0), zero for the other columns;
+//   layer 3 with the taps as columns (default kernel), entry kF4 + (nb * 2 +
+//            h) * 32 + lane: tap nb * 8 + g (zero for taps 9-15), input
+//            channels 2 tq + 8 h, + 1.
 __device__ __forceinline__ float w1_at(const float* wr, int o, int k) {
   const int t = k >> 2, c = k & 3;
   return (t < 9 && c < 3) ? wr[oW1 + o * 27 + c * 9 + t] : 0.f;
@@ -583,10 +637,17 @@ __global__ void k_pack_frags(const float* __restrict__ wr, uint32_t* frag) {
       lo = wr[oW3 + c * 9 + t];
       hi = wr[oW3 + (c + 1) * 9 + t];
     }
-  } else {
+  } else if (e < kF4) {
     const int w = e - kFU, t = w >> 7, el = 2 * (w & 127);
     lo = w2_core(wr, t, el);
     hi = w2_core(wr, t, el + 1);
+  } else {   // layer 3, taps as columns: n = nb * 8 + g is tap n (< 9), k = input channel
+    const int r = (e - kF4) >> 5, h = r & 1, nb = r >> 1;
+    const int t = nb * 8 + g, c = 2 * tq + 8 * h;
+    if (t < 9) {
+      lo = wr[oW3 + c * 9 + t];
+      hi = wr[oW3 + (c + 1) * 9 + t];
+    }
   }
   frag[e] = pack_bf16(lo, hi);
 }
@@ -1031,6 +1092,15 @@ void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, 
     lk = L.logk[level];
   }
   dim3 grid((lv.N + 1 + TI - 1) / TI, (lv.N + 1 + TJ - 1) / TJ, m.nf);
+  dim3 grid16((lv.N + 1 + TI - 1) / TI, (lv.N + 1 + BJ - 1) / BJ, m.nf);
+  static bool smem_set = false;
+  if (!smem_set) {
+    check_cuda(cudaFuncSetAttribute(k_cnn_smooth<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSmem),
+               "network kernel shared memory");
+    check_cuda(cudaFuncSetAttribute(k_cnn_smooth<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSmem),
+               "network kernel shared memory");
+    smem_set = true;
+  }
   LaunchScope ls(HHG_K_OTHER, level, st);
   k_face_rms<<<m.nf, 256, 0, st>>>(m.tab, lv, s, L.scale);
   if (delta) check_cuda(cudaMemsetAsync(delta, 0, (size_t)lv.len * sizeof(float), st), "delta clear");
@@ -1040,9 +1110,9 @@ void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, 
     else
       k_cnn_smooth_tc<float><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (float*)x, delta, m.err);
   } else if (prec == 0) {
-    k_cnn_smooth<double><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (double*)x, delta);
+    k_cnn_smooth<double><<<grid16, 256, kBigSmem, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (double*)x, delta);
   } else {
-    k_cnn_smooth<float><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (float*)x, delta);
+    k_cnn_smooth<float><<<grid16, 256, kBigSmem, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (float*)x, delta);
   }
   check_cuda(cudaGetLastError(), "cnn smooth");
 }
