@@ -365,11 +365,12 @@ hhg_status hhg_learned_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const 
                              void* x, float* d, void* stream);
 /* Tensor-core path of the network kernel (not in the paper): reads it
  * (set == 0: *path is written) or sets it (set != 0: *path is an input).
- * HHG_TC_MMA_SYNC (default): all three layers on mma.sync.m16n8k16;
- * HHG_TC_TCGEN05: layer 2 (16 -> 16, 80 % of the flops) on tcgen05.mma with
- * its accumulator in tensor memory (64 columns per CTA), layers 1 and 3 on
- * mma.sync.  Both give the network's result within BF16 rounding; the
- * first is faster on GB300.  A tcgen05 product that does not complete
+ * HHG_TC_MMA_SYNC (default): all three layers on mma.sync.m16n8k16, one CTA
+ * per 16 x 32 output tile; HHG_TC_TCGEN05: layer 2 (16 -> 16, 80 % of the
+ * flops) on tcgen05.mma with its accumulators in tensor memory (128 columns
+ * per persistent CTA, three CTAs per SM), layers 1 and 3 on mma.sync.  Both
+ * give the network's result within BF16 rounding; the first is faster on
+ * GB300.  A tcgen05 product that does not complete
  * within its bounded wait sets the mesh's device error word, which the next
  * hhg_solve reports as HHG_ERR_TIMEOUT.  HHG_ERR_ARG for another value.
  * Synchronous with respect to the host. */

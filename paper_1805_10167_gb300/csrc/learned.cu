@@ -78,21 +78,14 @@ __device__ __forceinline__ bool interior_pt(int i, int j, int N) { return i >= 1
 // per point (16 channels and padding): the eight 16-byte rows that one
 // ldmatrix phase reads from consecutive points then fall in distinct banks.
 //
-// Opt-in variant (k_cnn_smooth_tc, hhg_learned_tensor_path): layer 2 on the
-// fifth-generation tensor cores, tcgen05.mma with M = 128, N = 16, K = 16 and
-// the accumulator in tensor memory.  For the rows m = 0..383 of the
-// h1-linear index (row jj * 36 + ii is h2 point (jj, ii); rows with ii >= 34
-// are computed and dropped) and each tap t, A_t is the 128 rows of h1
-// starting at m0 + jj(t) * 36 + ii(t): a shifted window of h1, which that
-// kernel stores as two planes (channels 0-7 and 8-15, 16 bytes per point)
-// so that every window is a K-major operand without swizzling; 3 row blocks
-// x 9 taps issued by one thread and committed to an mbarrier, the
-// accumulator read back by tcgen05.ld.  Its weights are packed in the
-// operand's core-matrix layout.  It gives the same results within BF16
-// rounding and is slower on GB300 (the network's time is in staging,
-// layers 1 and 3 and the epilogues; the per-tile allocation, fences and
-// commit round trip cost more than layer 2's share of the mma.sync issue).
-
+// Opt-in variant (k_cnn_smooth_tc, hhg_learned_tensor_path): the same 16 x 32
+// tiles with layer 2 on the fifth-generation tensor cores (tcgen05.mma, the
+// accumulators in tensor memory), in persistent CTAs that keep their tensor
+// memory for all their tiles; described with the kernel below.  It gives the
+// same results within BF16 rounding and is slower on GB300: the network is
+// issue-bound on staging, layer 1 and the epilogues, of which layer 2's
+// mma.sync share is small, and the commit round trip of each tile stalls the
+// CTA at a barrier (both profiles under profiles/).
 constexpr int kPS = 24;                               // BF16 slots per point in h1, h2 records
 constexpr int kF1 = 0, kF2 = 3 * 2 * 2 * 32, kF3 = kF2 + 9 * 2 * 2 * 32;
 constexpr int kFU = kF3 + 9 * 2 * 32;                 // tcgen05 layer-2 operand, 9 x 128 words
@@ -414,163 +407,215 @@ __global__ void __launch_bounds__(256, 3)
   }
 }
 
-// The network with layer 2 on tcgen05 (the opt-in variant described above):
-// one CTA per 8 x 32 tile, 64 tensor-memory columns per CTA, at least four
-// CTAs per SM (64 registers a thread).
+// The network with layer 2 on tcgen05 (hhg_learned_tensor_path): the 16 x 32
+// tiles of the default kernel, taken by persistent CTAs (three per SM) from
+// a per-level list of the tiles that meet the face triangle.  Layer 2 as
+// 6 row blocks x 9 taps of tcgen05.mma (M = 128, N = 16, K = 16): for rows
+// m = 0..767 of the h1-linear index (row jj * 36 + ii is h2 point (jj, ii);
+// rows with ii >= 34 or jj >= 18 are computed and dropped) and each tap t,
+// the A operand is the window of 128 h1 rows starting at m0 + (t / 3) 36 +
+// t % 3, h1 stored as two planes (channels 0-7 and 8-15, 16 bytes per point)
+// so that every window is a K-major operand without swizzling; the weights
+// in the operand's core-matrix layout; the accumulators in 96 of the CTA's
+// 128 tensor-memory columns (allocated once per CTA), committed to an
+// mbarrier whose wait is bounded and read back by tcgen05.ld.  Layers 1 and
+// 3 on mma.sync as in the default kernel (layer 3 with the taps as columns,
+// its products in the shared memory of the h1 planes).
+constexpr int kMB2 = 6;                                   // 128-row blocks of layer 2
+constexpr int NP1Q = 848;                                 // h1 plane length: the windows' reach, padded
+static_assert(kMB2 * 128 >= (BJ2 - 1) * I1 + I2, "layer-2 rows cover the h2 region");
+static_assert(NP1Q >= kMB2 * 128 + 2 * I1 + 2 && NP1Q >= BP1, "layer-2 windows stay inside the h1 planes");
+static_assert(BP2 * 9 * 4 <= 2 * NP1Q * 16, "the layer-3 tap products fit in the h1 planes");
+constexpr int kTcOffW = 2 * NP1Q * 16;                    // byte offsets in dynamic shared memory
+constexpr int kTcOffH2 = kTcOffW + 9 * 32 * 16;
+constexpr int kTcOffX = kTcOffH2 + BP2 * kPS * 2;
+constexpr int kTcOffBar = kTcOffX + BP0 * 8;
+constexpr int kTcSmem = kTcOffBar + 16;
+constexpr int kTcCols = 128;                              // tensor-memory columns per CTA
+
 template <typename T>
-__global__ void __launch_bounds__(TJ* TI, 4)
-    k_cnn_smooth_tc(LevelView L, const float* __restrict__ s, const uint32_t* __restrict__ logk,
-                 const float* __restrict__ scale, const uint32_t* __restrict__ frag,
-                 const float* __restrict__ wr, T* x, float* delta, int* err) {
-  __shared__ __align__(16) uint2 xin[NP0];                 // 4 BF16 channels per point
-  __shared__ __align__(128) uint4 h1p[2][NP1P];            // h1: channels 0-7 | 8-15, 16 B per point
-  __shared__ __align__(128) uint4 w2s[9 * 32];             // layer-2 weights, tcgen05 operand layout
-  __shared__ __align__(16) __nv_bfloat16 h2[NP2][kPS];
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ uint32_t tslot;
-  const int f = blockIdx.z;
-  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
+__global__ void __launch_bounds__(256, 3)
+    k_cnn_smooth_tc(LevelView L, const int* __restrict__ tiles, int ntiles, const float* __restrict__ s,
+                    const uint32_t* __restrict__ logk, const float* __restrict__ scale,
+                    const uint32_t* __restrict__ frag, const float* __restrict__ wr, T* x, float* delta, int* err) {
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  uint4(*h1p)[NP1Q] = reinterpret_cast<uint4(*)[NP1Q]>(tc_smem);    // h1: channels 0-7 | 8-15
+  uint4* w2s = reinterpret_cast<uint4*>(tc_smem + kTcOffW);          // layer-2 weights, operand layout
+  __nv_bfloat16(*h2)[kPS] = reinterpret_cast<__nv_bfloat16(*)[kPS]>(tc_smem + kTcOffH2);
+  uint2* xin = reinterpret_cast<uint2*>(tc_smem + kTcOffX);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_smem + kTcOffBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_smem + kTcOffBar + 8);
+  float* Dt = reinterpret_cast<float*>(tc_smem);                      // layer-3 tap products (after layer 2)
   const int N = L.N;
-  const float sig = scale[f];
-  if (i0 + j0 > N || !(sig > 0.f)) return;   // tile above the triangle / zero residual (uniform per CTA)
-  const float isig = 1.f / sig;
   const int64_t S = L.S;
-  const int64_t fb = L.f_off + (int64_t)f * L.FS;
-  const uint32_t* lk = logk ? logk + (int64_t)f * L.FS : nullptr;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = TJ * TI / 32;
-  if (warp == 0) {   // 64 tensor-memory columns: layer 2's three 128 x 16 accumulators
-    tmem_alloc(&tslot, 64);
+  constexpr int NT = 256, NW = NT / 32;
+  if (warp == 0) {   // the CTA's tensor-memory columns, for all its tiles
+    tmem_alloc(tslot, kTcCols);
     tmem_relinquish();
   }
   if (tid == 32) {
-    mbar_init(&mbar, 1);
+    mbar_init(mbar, 1);
     mbar_init_fence();
-  }
-  for (int q = tid; q < NP0; q += TJ * TI) {
-    const int jj = q / I0, ii = q - jj * I0;
-    const int i = i0 - 3 + ii, j = j0 - 3 + jj;
-    float a = 0.f;
-    uint32_t kk = 0u;
-    if (closed_pt(i, j, N)) {
-      const int64_t p = (int64_t)j * S + i;
-      a = s[fb + p] * isig;
-      if (lk) kk = lk[p];
-    }
-    // channels (residual, log k up | log k down, 0)
-    xin[q] = make_uint2((pack_bf16(a, 0.f) & 0xffffu) | (kk << 16), kk >> 16);
   }
   {
     const uint4* wsrc = reinterpret_cast<const uint4*>(frag + kFU);
-    for (int q = tid; q < 9 * 32; q += TJ * TI) w2s[q] = wsrc[q];
-    for (int q = tid; q < 2 * (NP1P - NP1); q += TJ * TI)   // finite values under the windows' reach
-      h1p[q / (NP1P - NP1)][NP1 + q % (NP1P - NP1)] = make_uint4(0u, 0u, 0u, 0u);
+    for (int q = tid; q < 9 * 32; q += NT) w2s[q] = wsrc[q];
   }
   const int g = lane >> 2, tq = lane & 3;
-  // ldmatrix row of this lane: point offset in a chunk and channel half
   const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lhalf = (lane >> 4) * 8;
-  {  // layer 1: 3 -> 16 (mma.sync)
-    uint32_t bf[3][2][2];
+  uint32_t bf1[3][2][2], bf4[2][2];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int nb = 0; nb < 2; ++nb)
+    for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) bf[k][nb][h] = frag[kF1 + ((k * 2 + nb) * 2 + h) * 32 + lane];
-    const float bias[2][2] = {{wr[ob1 + 2 * tq], wr[ob1 + 2 * tq + 1]}, {wr[ob1 + 8 + 2 * tq], wr[ob1 + 9 + 2 * tq]}};
-    const uint32_t* X = reinterpret_cast<const uint32_t*>(xin);
-    uint32_t* h1w = reinterpret_cast<uint32_t*>(&h1p[0][0]);
-    __syncthreads();
-    int c = warp;
-    for (; c + NW < NP1 / 16; c += 2 * NW)
-      cnn_layer1<2, 4, NP1P * 4>({c, c + NW}, X, h1w, bf, bias, i0, j0, N, g, tq);
-    if (c < NP1 / 16) cnn_layer1<1, 4, NP1P * 4>({c}, X, h1w, bf, bias, i0, j0, N, g, tq);
-  }
-  // layer 2: 16 -> 16 (tcgen05).  The generic-proxy writes of h1 and of the
-  // weights are made visible to the tensor cores' reads, then one thread
-  // issues the 27 products and commits them to the mbarrier.
-  fence_proxy_async_smem();
+      for (int h = 0; h < 2; ++h) bf1[k][nb][h] = frag[kF1 + ((k * 2 + nb) * 2 + h) * 32 + lane];
+#pragma unroll
+  for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) bf4[nb][h] = frag[kF4 + (nb * 2 + h) * 32 + lane];
+  const float bias1[2][2] = {{wr[ob1 + 2 * tq], wr[ob1 + 2 * tq + 1]}, {wr[ob1 + 8 + 2 * tq], wr[ob1 + 9 + 2 * tq]}};
+  const float b3 = wr[ob3];
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t taddr = tslot;
-  if (tid == 0) {
-    constexpr uint32_t idesc = idesc_bf16_f32(128, 16);
-#pragma unroll 1
-    for (int mb = 0; mb < kMB; ++mb)
-#pragma unroll
-      for (int t = 0; t < 9; ++t)
-        umma_bf16(taddr + 16 * mb, smem_desc_kmajor(&h1p[0][mb * 128 + (t / 3) * I1 + t % 3], NP1P * 16, 128),
-                  smem_desc_kmajor(&w2s[t * 32], 128, 256), idesc, t > 0);
-    umma_commit(&mbar);
-  }
-  uint32_t bf[9][2];   // layer-3 fragments, loaded while the products run
-#pragma unroll
-  for (int t = 0; t < 9; ++t)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) bf[t][h] = frag[kF3 + (t * 2 + h) * 32 + lane];
-  const float b3 = wr[ob3];
-  // the issuing thread waits for the products (bounded); the others wait at
-  // the CTA barrier, taking no issue slots from the SM's other CTAs
-  bool done = true;
-  if (tid == 0) {
-    done = false;
-    for (long it = 0; it < kUmmaPolls; ++it)
-      if (mbar_try_wait(&mbar, 0)) {
-        done = true;
-        break;
+  const uint32_t taddr = *tslot;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const int code = tiles[ti];
+    const int f = code >> 16, by = (code >> 8) & 255, bx = code & 255;
+    const float sig = scale[f];
+    if (!(sig > 0.f)) continue;   // zero residual on this face (uniform per CTA)
+    const float isig = 1.f / sig;
+    const int i0 = bx * TI, j0 = by * BJ;
+    const int64_t fb = L.f_off + (int64_t)f * L.FS;
+    const uint32_t* lk = logk ? logk + (int64_t)f * L.FS : nullptr;
+    for (int q = tid; q < BP0; q += NT) {
+      const int jj = q / I0, ii = q - jj * I0;
+      const int i = i0 - 3 + ii, j = j0 - 3 + jj;
+      float a = 0.f;
+      uint32_t kk = 0u;
+      if (closed_pt(i, j, N)) {
+        const int64_t p = (int64_t)j * S + i;
+        a = s[fb + p] * isig;
+        if (lk) kk = lk[p];
       }
-  }
-  if (!__syncthreads_and(done)) {
-    // the products did not complete in time: report it, wait once more
-    // (bounded) so that none is in flight, free the columns, leave the tile
-    if (tid == 0) {
-      atomicExch(err, 1);
-      for (long it = 0; it < kUmmaPolls; ++it)
-        if (mbar_try_wait(&mbar, 0)) break;
+      xin[q] = make_uint2((pack_bf16(a, 0.f) & 0xffffu) | (kk << 16), kk >> 16);
     }
+    for (int q = tid; q < 2 * (NP1Q - BP1); q += NT)   // finite values under the windows' reach
+      h1p[q / (NP1Q - BP1)][BP1 + q % (NP1Q - BP1)] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    {  // layer 1 (mma.sync) into the h1 planes
+      const uint32_t* X = reinterpret_cast<const uint32_t*>(xin);
+      uint32_t* h1w = reinterpret_cast<uint32_t*>(&h1p[0][0]);
+      int c = warp;
+      for (; c + NW < BP1 / 16; c += 2 * NW)
+        cnn_layer1<2, 4, NP1Q * 4>({c, c + NW}, X, h1w, bf1, bias1, i0, j0, N, g, tq);
+      if (c < BP1 / 16) cnn_layer1<1, 4, NP1Q * 4>({c}, X, h1w, bf1, bias1, i0, j0, N, g, tq);
+    }
+    // layer 2 (tcgen05): the generic-proxy writes of h1 are made visible to
+    // the tensor cores, one thread issues the 54 products and commits them
+    fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
-      tc_fence_after();
-      tmem_dealloc(taddr, 64);
+    tc_fence_after();
+    if (tid == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(128, 16);
+#pragma unroll 1
+      for (int mb = 0; mb < kMB2; ++mb)
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+          umma_bf16(taddr + 16 * mb, smem_desc_kmajor(&h1p[0][mb * 128 + (t / 3) * I1 + t % 3], NP1Q * 16, 128),
+                    smem_desc_kmajor(&w2s[t * 32], 128, 256), idesc, t > 0);
+      umma_commit(mbar);
     }
-    return;
-  }
-  tc_fence_after();
-  {  // accumulator rows -> bias, relu, closed-triangle mask, BF16 -> h2
-    float b2[16];
+    bool done = true;
+    if (tid == 0) {
+      done = false;
+      for (long it = 0; it < kUmmaPolls; ++it)
+        if (mbar_try_wait(mbar, phase)) {
+          done = true;
+          break;
+        }
+    }
+    if (!__syncthreads_and(done)) {   // report, wait once more (bounded), stop
+      if (tid == 0) {
+        atomicExch(err, 1);
+        for (long it = 0; it < kUmmaPolls; ++it)
+          if (mbar_try_wait(mbar, phase)) break;
+      }
+      failed = true;
+      break;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    {  // accumulator rows -> bias, relu, closed-triangle mask, BF16 -> h2
+      float b2[16];
 #pragma unroll
-    for (int o = 0; o < 16; ++o) b2[o] = wr[ob2 + o];
-    for (int u = warp; u < 4 * kMB; u += NW) {   // (row block, lane quarter); quarter = warp % 4
-      const int mb = u >> 2, qq = u & 3;
-      float v[16];
-      tmem_ld16(taddr + ((uint32_t)(qq * 32) << 16) + 16 * mb, v);
-      const int m = mb * 128 + qq * 32 + lane;
-      const int jj = m / I1, ii = m - jj * I1;
-      if (jj < J2 && ii < I2) {
-        const bool in = closed_pt(i0 - 1 + ii, j0 - 1 + jj, N);
-        uint32_t w[8];
+      for (int o = 0; o < 16; ++o) b2[o] = wr[ob2 + o];
+      for (int u = warp; u < 4 * kMB2; u += NW) {   // (row block, lane quarter); quarter = warp % 4
+        const int mb = u >> 2, qq = u & 3;
+        float v[16];
+        tmem_ld16(taddr + ((uint32_t)(qq * 32) << 16) + 16 * mb, v);
+        const int m = mb * 128 + qq * 32 + lane;
+        const int jj = m / I1, ii = m - jj * I1;
+        if (jj < BJ2 && ii < I2) {
+          const bool in = closed_pt(i0 - 1 + ii, j0 - 1 + jj, N);
+          uint32_t w[8];
 #pragma unroll
-        for (int o = 0; o < 8; ++o) w[o] = relu_pack(v[2 * o] + b2[2 * o], v[2 * o + 1] + b2[2 * o + 1], in);
-        uint4* dst = reinterpret_cast<uint4*>(&h2[jj * I2 + ii][0]);
-        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          for (int o = 0; o < 8; ++o) w[o] = relu_pack(v[2 * o] + b2[2 * o], v[2 * o + 1] + b2[2 * o + 1], in);
+          uint4* dst = reinterpret_cast<uint4*>(&h2[jj * I2 + ii][0]);
+          dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        }
       }
     }
+    tc_fence_before();
+    __syncthreads();   // h2 complete; the products are done with the h1 planes
+    constexpr int NC2 = (BP2 + 15) / 16;
+    for (int c = warp; c < NC2; c += NW) {   // layer 3: taps as columns
+      uint32_t afr[4];
+      ldsm_x4(afr, &h2[min(c * 16 + lrow, BP2 - 1)][lhalf]);
+      float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+      mma_bf16(d[0], afr, bf4[0][0], bf4[0][1]);
+      mma_bf16(d[1], afr, bf4[1][0], bf4[1][1]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = c * 16 + g + 8 * h;
+        if (q >= BP2) continue;
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb) {
+          const int t = nb * 8 + 2 * tq;
+          if (t < 9) Dt[t * BP2 + q] = d[nb][2 * h];
+          if (t + 1 < 9) Dt[(t + 1) * BP2 + q] = d[nb][2 * h + 1];
+        }
+      }
+    }
+    __syncthreads();
+    for (int o = tid; o < BP3; o += NT) {
+      const int ty = o / TI, tx = o - ty * TI;
+      const int i = i0 + tx, j = j0 + ty;
+      if (!interior_pt(i, j, N)) continue;
+      float acc = b3;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) acc += Dt[t * BP2 + (ty + t / 3) * I2 + tx + t % 3];
+      const int64_t p = fb + (int64_t)j * S + i;
+      acc *= sig;
+      if (delta) delta[p] = acc;
+      if (x) x[p] = (T)((T)x[p] + (T)acc);
+    }
+    __syncthreads();   // shared memory is reused by the next tile
   }
+  (void)failed;
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(taddr, 64);
+    tmem_dealloc(taddr, kTcCols);
   }
-  // layer 3: 16 -> 1 (mma.sync)
-  int c = warp;
-  for (; c + NW < NP3 / 16; c += 2 * NW)
-    cnn_layer3<2, T>({c, c + NW}, h2, bf, b3, sig, fb, S, i0, j0, N, g, tq, lrow, lhalf, x, delta);
-  if (c < NP3 / 16) cnn_layer3<1, T>({c}, h2, bf, b3, sig, fb, S, i0, j0, N, g, tq, lrow, lhalf, x, delta);
 }
 
 // Log-coefficient pairs of one level for the smoother's input channels:
@@ -1006,6 +1051,8 @@ struct Learned {
   int tensor_path = 0;          // 0: mma.sync network, 1: layer 2 on tcgen05
   std::vector<uint32_t*> logk;  // per level: log-coefficient pairs (k_logk_pack)
   std::vector<int> logk_ver;    // Mesh::k_version they were made from
+  std::vector<int*> tiles;      // per level: the tcgen05 kernel's tile list (face, tile row, tile column)
+  std::vector<int> ntiles;
   int step = 0;
   bool trained = false;
 };
@@ -1031,6 +1078,7 @@ void learned_free(Mesh& m) {
   for (float* p : {L->w, L->wr, L->g, L->m, L->v, L->scale}) cudaFree(p);
   cudaFree(L->frag);
   for (uint32_t* p : L->logk) cudaFree(p);
+  for (int* p : L->tiles) cudaFree(p);
   delete L;
   m.learned = nullptr;
 }
@@ -1099,16 +1147,41 @@ void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, 
                "network kernel shared memory");
     check_cuda(cudaFuncSetAttribute(k_cnn_smooth<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSmem),
                "network kernel shared memory");
+    check_cuda(cudaFuncSetAttribute(k_cnn_smooth_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem),
+               "network kernel shared memory");
+    check_cuda(cudaFuncSetAttribute(k_cnn_smooth_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem),
+               "network kernel shared memory");
     smem_set = true;
   }
   LaunchScope ls(HHG_K_OTHER, level, st);
   k_face_rms<<<m.nf, 256, 0, st>>>(m.tab, lv, s, L.scale);
   if (delta) check_cuda(cudaMemsetAsync(delta, 0, (size_t)lv.len * sizeof(float), st), "delta clear");
   if (L.tensor_path == 1) {
+    // the tiles of the level that meet a face triangle, made once per level
+    if ((int)L.tiles.size() < (int)m.levels.size()) {
+      L.tiles.resize(m.levels.size(), nullptr);
+      L.ntiles.resize(m.levels.size(), 0);
+    }
+    if (!L.tiles[level]) {
+      std::vector<int> tl;
+      for (int f = 0; f < m.nf; ++f)
+        for (int by = 0; by * BJ <= lv.N; ++by)
+          for (int bx = 0; bx * TI + by * BJ <= lv.N; ++bx) tl.push_back((f << 16) | (by << 8) | bx);
+      check_cuda(cudaMalloc(&L.tiles[level], tl.size() * sizeof(int)), "tile list");
+      check_cuda(cudaMemcpy(L.tiles[level], tl.data(), tl.size() * sizeof(int), cudaMemcpyHostToDevice), "tile list");
+      L.ntiles[level] = (int)tl.size();
+    }
+    int dev = 0, sms = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const int nt = L.ntiles[level];
+    const int ctas = std::max(1, std::min(nt, 3 * sms));
     if (prec == 0)
-      k_cnn_smooth_tc<double><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (double*)x, delta, m.err);
+      k_cnn_smooth_tc<double><<<ctas, 256, kTcSmem, st>>>(lv, L.tiles[level], nt, s, lk, L.scale, L.frag, L.wr,
+                                                           (double*)x, delta, m.err);
     else
-      k_cnn_smooth_tc<float><<<grid, TJ * TI, 0, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (float*)x, delta, m.err);
+      k_cnn_smooth_tc<float><<<ctas, 256, kTcSmem, st>>>(lv, L.tiles[level], nt, s, lk, L.scale, L.frag, L.wr,
+                                                          (float*)x, delta, m.err);
   } else if (prec == 0) {
     k_cnn_smooth<double><<<grid16, 256, kBigSmem, st>>>(lv, s, lk, L.scale, L.frag, L.wr, (double*)x, delta);
   } else {
