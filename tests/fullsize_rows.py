@@ -63,3 +63,47 @@ def row_weights(xy, tri, N, f, i, j, k_patch=None):
 def patch_element_ids(N, f, i, j):
     """Canonical element ids (6,) of the PATCH triangles of point (i, j) of face f."""
     return np.array([f * N * N + element_index(N, kind, i + da, j + db) for kind, da, db in PATCH])
+
+
+# ------------------------------------------------------------------ P2
+# P2 on level L: lattice point (I, J) of level L + 1; the level-L triangles
+# holding it and their six nodes (v0, v1, v2, m01, m12, m02) relative to the
+# triangle origin (2a, 2b), in the order of oracle.p2.
+P2_UP = [(0, 0), (2, 0), (0, 2), (1, 0), (1, 1), (0, 1)]
+P2_DN = [(2, 0), (0, 2), (2, 2), (1, 1), (1, 2), (2, 1)]
+
+
+def p2_patch(I, J):
+    """(kind, a, b) of the level-L triangles holding lattice point (I, J)."""
+    if I % 2 == 0 and J % 2 == 0:
+        a, b = I // 2, J // 2
+        return [("up", a, b), ("up", a - 1, b), ("up", a, b - 1), ("dn", a - 1, b), ("dn", a, b - 1),
+                ("dn", a - 1, b - 1)]
+    if J % 2 == 0:                              # horizontal micro-edge midpoint
+        return [("up", (I - 1) // 2, J // 2), ("dn", (I - 1) // 2, J // 2 - 1)]
+    if I % 2 == 0:                              # vertical
+        return [("up", I // 2, (J - 1) // 2), ("dn", I // 2 - 1, (J - 1) // 2)]
+    return [("up", (I - 1) // 2, (J - 1) // 2), ("dn", (I - 1) // 2, (J - 1) // 2)]   # diagonal
+
+
+def p2_row(xy, tri, N1, f, I, J):
+    """{(dI, dJ): weight} with (A2 x)_p = sum w x[p + (dI, dJ)] for the
+    face-interior point p = (I, J) of the level-(L+1) lattice (N1 = 2^(L+1)
+    intervals), from the oracle's P2 element matrices on the triangles
+    holding p, placed relative to p (the matrices do not change under
+    translation)."""
+    from oracle import p2
+    v0, v1, v2 = (np.asarray(xy[v], dtype=np.float64) for v in tri[f])
+    nodes, X = [], []
+    for kind, a, b in p2_patch(I, J):
+        pts = [(2 * a + dx, 2 * b + dy) for dx, dy in (P2_UP if kind == "up" else P2_DN)]
+        nodes.append(pts)
+        X.append([((p[0] - I) / N1) * (v1 - v0) + ((p[1] - J) / N1) * (v2 - v0) for p in pts[:3]])
+    K = p2.element_stiffness(np.array(X))
+    w = {}
+    for t, pts in enumerate(nodes):
+        c = pts.index((I, J))
+        for n, p in enumerate(pts):
+            key = (p[0] - I, p[1] - J)
+            w[key] = w.get(key, 0.0) + K[t, c, n]
+    return w

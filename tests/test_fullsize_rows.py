@@ -52,3 +52,28 @@ def test_element_numbering_matches_oracle_level():
             for a in range(N - 1 - b):
                 e = f * N * N + fr.element_index(N, "dn", a, b)
                 assert list(lv.elements[e]) == [G[v[1], v[0]] for v in fr.tri_vertices("dn", a, b)]
+
+
+@pytest.mark.parametrize("name,L", [("annulus", 2), ("random", 2)])
+def test_p2_rows_equal_assembled_matrix(name, L):
+    """The one-row P2 helper equals the rows of the oracle's assembled P2
+    matrix at every face-interior lattice point (all four point types)."""
+    from oracle import p2
+    from oracle import mesh as om
+    xy, tri = (inputs.annulus_mesh(32, 2) if name == "annulus" else inputs.random_square_mesh(5, 9))
+    M = om.MacroMesh(xy, tri)
+    P = p2.P2Level(M, L)
+    A = p2.assemble(P).tocsr()
+    N1 = P.lat.N
+    for f, G in enumerate(P.lat.face_ids):
+        for J in range(1, N1 - 1):
+            for I in range(1, N1 - J):
+                w = fr.p2_row(xy, M.tri, N1, f, I, J)
+                row = A[G[J, I]]
+                got = {}
+                for (dI, dJ), v in w.items():
+                    q = G[J + dJ, I + dI]
+                    got[q] = got.get(q, 0.0) + v
+                for q, v in zip(row.indices, row.data):
+                    assert abs(got.pop(q, 0.0) - v) <= 1e-12 * abs(row.data).max()
+                assert all(abs(v) <= 1e-12 * abs(row.data).max() for v in got.values())
