@@ -317,11 +317,15 @@ hhg_status hhg_batch_tune(hhg_batch batch, void* stream);
 /* Solve every problem: x[p], b[p] are DEVICE arrays of n_nodes(p) doubles in
  * problem p's canonical order (x: initial guess with Dirichlet values in,
  * solution out).  `x` and `b` themselves are HOST arrays of n pointers.
- * opts->mode HHG_SOLVE_IR (default: FP32 V-cycles inside FP64 refinement) or
- * HHG_SOLVE_MG (FP64 V-cycles); every problem iterates until its own
- * ||b - A x|| <= tol ||b - A x0||.  reps: NULL or n reports (history unused;
- * iterations = the outer iteration at which that problem met its tolerance).
- * Synchronous. */
+ * opts->mode HHG_SOLVE_FPCG (default: flexible CG preconditioned by one FP32
+ * V-cycle, per-problem step lengths, each problem frozen once it meets its
+ * tolerance, confirmed by its true FP64 residual), HHG_SOLVE_IR (FP32 V-cycles
+ * inside FP64 refinement) or HHG_SOLVE_MG (FP64 V-cycles); opts NULL: FPCG,
+ * V(3,3), 1e-10, 100 iterations.  Every problem iterates until its own
+ * ||b - A x|| <= tol ||b - A x0||; a level group whose problems have all met
+ * their tolerance stops iterating (its problems keep that iterate).  reps:
+ * NULL or n reports (history unused; iterations = the outer iteration at which
+ * that problem met its tolerance).  Synchronous. */
 hhg_status hhg_batch_solve(hhg_batch batch, double* const* x, const double* const* b,
                            const hhg_solve_opts* opts, hhg_solve_report* reps, void* stream);
 

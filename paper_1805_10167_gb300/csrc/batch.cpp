@@ -128,7 +128,8 @@ struct Batch {
   std::vector<BatchGroup> groups;
   cudaEvent_t fork = nullptr;
   cudaStream_t capture = nullptr;   // graphs are captured here (the legacy stream cannot capture)
-  cudaGraphExec_t graph = nullptr;
+  // captured iterations, one per set of active groups (bit g: group g iterates)
+  std::map<uint32_t, cudaGraphExec_t> graphs;
   int graph_mode = -1, graph_nu1 = -1, graph_nu2 = -1;
   double* h_norms = nullptr;   // pinned: squared norms of all problems, group-major
   std::vector<int> norm_off;   // offset of each group in h_norms
@@ -233,7 +234,7 @@ Batch* batch_create(int n, const double* const* xy, const int64_t* nv, const int
 void batch_destroy(Batch* B) {
   if (!B) return;
   cudaDeviceSynchronize();
-  if (B->graph) cudaGraphExecDestroy(B->graph);
+  for (auto& kv : B->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& g : B->groups) {
     mesh_destroy_internal(g.m);
     cudaStreamDestroy(g.st);
@@ -270,10 +271,8 @@ void batch_tune(Batch& B, cudaStream_t st) {
     for (int l = 2; l <= g.level; ++l) {
       tune_face_sweep(*g.m, l, 1, st);
     }
-  if (B.graph) {
-    cudaGraphExecDestroy(B.graph);   // tasks changed: capture again
-    B.graph = nullptr;
-  }
+  for (auto& kv : B.graphs) cudaGraphExecDestroy(kv.second);   // tasks changed: capture again
+  B.graphs.clear();
 }
 
 // One outer iteration of group g on its stream: inner V-cycle on A d = r,
@@ -347,10 +346,13 @@ static void group_iteration(const BatchGroup& g, int mode, int nu1, int nu2) {
 
 // iteration: one outer iteration of every group; else the initial (or, for
 // the flexible CG, a restarting) true residual and its norms.
+// active: bit g set = group g takes part (a group whose problems have all met
+// their tolerance is left out of the outer iterations).
 static void fork_join(Batch& B, cudaStream_t st, int mode, int nu1, int nu2, bool iteration, double tol = 0.0,
-                      bool first = true) {
+                      bool first = true, uint32_t active = ~0u) {
   check_cuda(cudaEventRecord(B.fork, st), "fork");
   for (size_t gi = 0; gi < B.groups.size(); ++gi) {
+    if (!(active >> gi & 1u)) continue;
     BatchGroup& g = B.groups[gi];
     check_cuda(cudaStreamWaitEvent(g.st, B.fork, 0), "wait fork");
     if (iteration) {
@@ -425,10 +427,17 @@ void batch_solve(Batch& B, double* const* x, const double* const* b, const hhg_s
     }
     return ok;
   };
-  if (B.graph && (B.graph_mode != o.mode || B.graph_nu1 != o.nu1 || B.graph_nu2 != o.nu2)) {
-    cudaGraphExecDestroy(B.graph);
-    B.graph = nullptr;
+  if (!B.graphs.empty() && (B.graph_mode != o.mode || B.graph_nu1 != o.nu1 || B.graph_nu2 != o.nu2)) {
+    for (auto& kv : B.graphs) cudaGraphExecDestroy(kv.second);
+    B.graphs.clear();
   }
+  // groups with a problem that has not met its tolerance yet
+  auto active_groups = [&]() {
+    uint32_t mask = 0;
+    for (int p = 0; p < n; ++p)
+      if (done_at[p] < 0) mask |= 1u << B.probs[p].group;
+    return mask;
+  };
   for (;;) {
     if (all_done() || status != HHG_OK) {
       if (o.mode != HHG_SOLVE_FPCG || status != HHG_OK) break;
@@ -445,22 +454,26 @@ void batch_solve(Batch& B, double* const* x, const double* const* b, const hhg_s
       status = HHG_ERR_NOT_CONVERGED;
       break;
     }
-    if (!B.graph && it == 0) {
+    const uint32_t mask = active_groups();
+    if (B.graphs.empty() && it == 0) {
       // first iteration runs directly (sets kernel attributes), then is captured
-      fork_join(B, st, o.mode, o.nu1, o.nu2, true);
+      fork_join(B, st, o.mode, o.nu1, o.nu2, true, 0.0, true, mask);
     } else {
-      if (!B.graph) {
+      auto gi = B.graphs.find(mask);
+      if (gi == B.graphs.end()) {
         cudaGraph_t graph;
+        cudaGraphExec_t exec;
         check_cuda(cudaStreamBeginCapture(B.capture, cudaStreamCaptureModeThreadLocal), "begin capture");
-        fork_join(B, B.capture, o.mode, o.nu1, o.nu2, true);
+        fork_join(B, B.capture, o.mode, o.nu1, o.nu2, true, 0.0, true, mask);
         check_cuda(cudaStreamEndCapture(B.capture, &graph), "end capture");
-        check_cuda(cudaGraphInstantiate(&B.graph, graph, 0), "instantiate");
+        check_cuda(cudaGraphInstantiate(&exec, graph, 0), "instantiate");
         cudaGraphDestroy(graph);
+        gi = B.graphs.emplace(mask, exec).first;
         B.graph_mode = o.mode;
         B.graph_nu1 = o.nu1;
         B.graph_nu2 = o.nu2;
       }
-      check_cuda(cudaGraphLaunch(B.graph, st), "graph launch");
+      check_cuda(cudaGraphLaunch(gi->second, st), "graph launch");
     }
     check_cuda(cudaStreamSynchronize(st), "sync");
     ++it;

@@ -116,7 +116,9 @@ static void vcycle_level(const Mesh& m, int l, int prec, void* x, const void* b,
     coarse_solve(m, prec, b, x, st);
     return;
   }
-  if (smoother == 0 && l <= tail_level(m, prec)) {   // the rest of the cycle in one CTA
+  // the rest of the cycle in one CTA where every level below is Gauss-Seidel
+  // (the learned smoothers use it on levels with N >= 8 only)
+  if ((smoother == 0 || m.levels[l].lv.N < 8) && l <= tail_level(m, prec)) {
     tail_run(m, l, prec, x, b, nu1, nu2, st);
     return;
   }
@@ -749,7 +751,7 @@ hhg_status hhg_batch_solve(hhg_batch batch, double* const* x, const double* cons
     if (!batch || !batch->b) throw ArgError("NULL batch");
     need(x, "x");
     need(b, "b");
-    hhg_solve_opts o{HHG_SOLVE_IR, 3, 3, 100, 1e-10, HHG_SMOOTH_GS, 20};
+    hhg_solve_opts o{HHG_SOLVE_FPCG, 3, 3, 100, 1e-10, HHG_SMOOTH_GS, 20};
     if (opts) o = *opts;
     if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 0 || !(o.tol >= 0.0)) throw ArgError("bad solve options");
     if (o.mode != HHG_SOLVE_MG && o.mode != HHG_SOLVE_IR && o.mode != HHG_SOLVE_FPCG) throw ArgError("bad solve mode");

@@ -399,7 +399,7 @@ class Batch:
     def tune(self, stream=None):
         _check(lib.hhg_batch_tune(self.h, _stream(stream)))
 
-    def solve(self, xs, bs, mode=SOLVE_IR, nu1=3, nu2=3, tol=1e-10, max_iter=100, stream=None,
+    def solve(self, xs, bs, mode=SOLVE_FPCG, nu1=3, nu2=3, tol=1e-10, max_iter=100, stream=None,
               raise_on_error=True):
         """xs, bs: per-problem device vectors in canonical order.  Returns
         (status, list of per-problem report dicts)."""
