@@ -1084,10 +1084,18 @@ void learned_free(Mesh& m) {
   m.learned = nullptr;
 }
 
-static void load_constants(Learned& L, cudaStream_t st) {
-  check_cuda(cudaMemcpyToSymbolAsync(cW, L.wr, kNP * sizeof(float), 0, cudaMemcpyDeviceToDevice, st), "weights to constant bank");
+// The smoother kernels' tensor-core operands from the rounded weights; made
+// whenever the weights change (the smoother reads them in place, so graphs
+// that replay it see new weights without capturing again).
+static void pack_frags(Learned& L, cudaStream_t st) {
   k_pack_frags<<<(kFrag + 127) / 128, 128, 0, st>>>(L.wr, L.frag);
   check_cuda(cudaGetLastError(), "pack weight fragments");
+}
+
+// The training kernels read the weights from the process-wide constant bank.
+static void load_constants(Learned& L, cudaStream_t st) {
+  check_cuda(cudaMemcpyToSymbolAsync(cW, L.wr, kNP * sizeof(float), 0, cudaMemcpyDeviceToDevice, st), "weights to constant bank");
+  pack_frags(L, st);
 }
 
 void learned_set_weights(Mesh& m, const float* w_host, cudaStream_t st) {
@@ -1095,6 +1103,7 @@ void learned_set_weights(Mesh& m, const float* w_host, cudaStream_t st) {
   check_cuda(cudaMemcpyAsync(L.w, w_host, kNP * sizeof(float), cudaMemcpyHostToDevice, st), "weights upload");
   k_round_bf16<<<(kNP + 255) / 256, 256, 0, st>>>(L.w, L.wr, kNP);
   check_cuda(cudaGetLastError(), "round");
+  pack_frags(L, st);
   check_cuda(cudaMemsetAsync(L.m, 0, kNP * sizeof(float), st), "adam m");
   check_cuda(cudaMemsetAsync(L.v, 0, kNP * sizeof(float), st), "adam v");
   L.step = 0;
@@ -1123,7 +1132,6 @@ int learned_tensor_path(Mesh& m, int set, int path) {
 void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, float* delta, cudaStream_t st) {
   if (!m.learned) throw std::invalid_argument("learned smoother has no weights");
   Learned& L = *m.learned;
-  load_constants(L, st);
   const LevelView& lv = m.levels[level].lv;
   const uint32_t* lk = nullptr;
   if (m.vark) {   // log k pairs of the level, made once per coefficient
@@ -1359,6 +1367,7 @@ void learned_train(Mesh& m, int l, int n_pairs, int epochs, int batch, float lr,
     }
     if (loss_hist) loss_hist[ep] = (float)(ep_loss / ((double)nb * batch));
   }
+  pack_frags(L, st);   // the smoother's operands from the trained weights
   L.trained = true;
   for (void* p : {(void*)b, (void*)x, (void*)X, (void*)E, (void*)K, (void*)crops, (void*)work, (void*)loss})
     cudaFree(p);
