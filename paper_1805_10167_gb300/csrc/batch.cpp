@@ -431,7 +431,9 @@ void batch_solve(Batch& B, double* const* x, const double* const* b, const hhg_s
     for (auto& kv : B.graphs) cudaGraphExecDestroy(kv.second);
     B.graphs.clear();
   }
-  // groups with a problem that has not met its tolerance yet
+  // groups with a problem that has not met its tolerance yet (levels 1..10:
+  // at most ten groups, one bit each)
+  static_assert(sizeof(uint32_t) * 8 >= 10, "one mask bit per level group");
   auto active_groups = [&]() {
     uint32_t mask = 0;
     for (int p = 0; p < n; ++p)

@@ -484,7 +484,6 @@ __global__ void __launch_bounds__(256, 3)
   tc_fence_after();
   const uint32_t taddr = *tslot;
   uint32_t phase = 0;
-  bool failed = false;
   for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
     const int code = tiles[ti];
     const int f = code >> 16, by = (code >> 8) & 255, bx = code & 255;
@@ -548,7 +547,6 @@ __global__ void __launch_bounds__(256, 3)
         for (long it = 0; it < kUmmaPolls; ++it)
           if (mbar_try_wait(mbar, phase)) break;
       }
-      failed = true;
       break;
     }
     phase ^= 1u;
@@ -610,7 +608,6 @@ __global__ void __launch_bounds__(256, 3)
     }
     __syncthreads();   // shared memory is reused by the next tile
   }
-  (void)failed;
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -1150,17 +1147,15 @@ void learned_apply(const Mesh& m, int level, int prec, const float* s, void* x, 
   }
   dim3 grid((lv.N + 1 + TI - 1) / TI, (lv.N + 1 + TJ - 1) / TJ, m.nf);
   dim3 grid16((lv.N + 1 + TI - 1) / TI, (lv.N + 1 + BJ - 1) / BJ, m.nf);
-  static bool smem_set = false;
-  if (!smem_set) {
-    check_cuda(cudaFuncSetAttribute(k_cnn_smooth<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSmem),
+  // dynamic shared memory above 48 KB (a per-device function attribute; cheap to set)
+  if (L.tensor_path == 1) {
+    check_cuda(cudaFuncSetAttribute(prec == 0 ? (const void*)k_cnn_smooth_tc<double> : (const void*)k_cnn_smooth_tc<float>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem),
                "network kernel shared memory");
-    check_cuda(cudaFuncSetAttribute(k_cnn_smooth<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSmem),
+  } else {
+    check_cuda(cudaFuncSetAttribute(prec == 0 ? (const void*)k_cnn_smooth<double> : (const void*)k_cnn_smooth<float>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSmem),
                "network kernel shared memory");
-    check_cuda(cudaFuncSetAttribute(k_cnn_smooth_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem),
-               "network kernel shared memory");
-    check_cuda(cudaFuncSetAttribute(k_cnn_smooth_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem),
-               "network kernel shared memory");
-    smem_set = true;
   }
   LaunchScope ls(HHG_K_OTHER, level, st);
   k_face_rms<<<m.nf, 256, 0, st>>>(m.tab, lv, s, L.scale);
