@@ -59,7 +59,9 @@ typedef enum {
   HHG_ERR_NOT_CONVERGED = 5,  /* max_iter reached; x holds the last iterate */
   HHG_ERR_NAN = 6,            /* non-finite residual norm */
   HHG_ERR_TIMEOUT = 7,        /* a bounded device-side wait ran out */
-  HHG_ERR_BREAKDOWN = 8       /* Krylov breakdown */
+  HHG_ERR_BREAKDOWN = 8,      /* Krylov breakdown */
+  HHG_ERR_BOUNDS = 9          /* an index check failed (bounds-checking build, or a
+                                 host-built table); the message names the site */
 } hhg_status;
 
 typedef enum { HHG_F64 = 0, HHG_F32 = 1 } hhg_prec;
@@ -142,6 +144,10 @@ typedef struct {
  * of 2^max_level + 1 values in shared memory); HHG_ERR_OOM. */
 hhg_status hhg_mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
                            const uint8_t* dirichlet_vertex, int32_t max_level, hhg_mesh* out);
+/* Frees the mesh and everything it allocated.  Synchronous.  In the
+ * bounds-checking build, returns HHG_ERR_BOUNDS when an index check failed
+ * since the last hhg_sync / hhg_solve report (the mesh is freed all the same);
+ * NULL is a no-op. */
 hhg_status hhg_mesh_destroy(hhg_mesh mesh);
 hhg_status hhg_mesh_info(hhg_mesh mesh, int32_t level, hhg_info* out);
 
@@ -419,7 +425,11 @@ hhg_status hhg_coarse_tail(hhg_mesh mesh, int32_t set, int32_t* level);
 
 /* Waits for `stream` and reports whether a bounded device-side wait of this
  * mesh's kernels gave up since the last report (HHG_ERR_TIMEOUT; the device
- * error word is then cleared and the next call runs normally).  hhg_solve
+ * error word is then cleared and the next call runs normally) or, in the
+ * bounds-checking build libhhg_checked.so, whether a device-side index check
+ * failed (HHG_ERR_BOUNDS; the message names the kind of index and its value;
+ * the access went to a valid index instead, so results are wrong but the
+ * context stays usable).  hhg_solve
  * and hhg_batch_solve report this themselves; the asynchronous calls
  * (hhg_smooth, hhg_vcycle, ...) leave it to this call.  Synchronous. */
 hhg_status hhg_sync(hhg_mesh mesh, void* stream);

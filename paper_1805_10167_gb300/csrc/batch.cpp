@@ -494,17 +494,25 @@ void batch_solve(Batch& B, double* const* x, const double* const* b, const hhg_s
     }
   }
   check_cuda(cudaStreamSynchronize(st), "sync");
+  // the groups' device error words (bit 0: a bounded wait gave up; bit 1: an
+  // index check of the bounds-checking build failed), cleared once read
   int err = 0;
   for (auto& g : B.groups) {
     int e = 0;
     check_cuda(cudaMemcpy(&e, g.m->err, sizeof(int), cudaMemcpyDeviceToHost), "err readback");
+    if (e) {
+      check_cuda(cudaMemset(g.m->err, 0, 4 * sizeof(int)), "err clear");
+      check_cuda(cudaMemset(g.m->gbar, 0, kGridBarWords * sizeof(unsigned)), "grid barrier reset");
+    }
     err |= e;
   }
-  if (err) status = HHG_ERR_TIMEOUT;
+  const bool dev_failed = err != 0;
+  if (err & 2) status = HHG_ERR_BOUNDS;
+  else if (err) status = HHG_ERR_TIMEOUT;
   if (reps)
     for (int p = 0; p < n; ++p) {
       reps[p].iterations = done_at[p] >= 0 ? done_at[p] : it;
-      reps[p].status = done_at[p] >= 0 && status != HHG_ERR_TIMEOUT ? HHG_OK : status;
+      reps[p].status = done_at[p] >= 0 && !dev_failed ? HHG_OK : status;
       reps[p].r0 = r0[p];
       reps[p].r_final = r[p];
     }

@@ -43,6 +43,8 @@ hhg_status guarded(F&& f) {
     return fail(HHG_ERR_OOM, "device or host allocation failed");
   } catch (const std::invalid_argument& e) {
     return fail(HHG_ERR_ARG, e.what());
+  } catch (const std::logic_error& e) {
+    return fail(HHG_ERR_BOUNDS, e.what());
   } catch (const hhg::MeshError& e) {
     return fail(HHG_ERR_MESH, e.what());
   } catch (const hhg::SolveStatus& e) {
@@ -77,20 +79,34 @@ void need_vec(const void* p, const char* name) {
   if ((uintptr_t)p % 16 != 0) throw ArgError(std::string(name) + " is not 16-byte aligned");
 }
 
-// Reads the device error word (and clears it); a bounded wait that gave up
-// is reported as HHG_ERR_TIMEOUT.
-bool device_timed_out(const hhg::Mesh& m, cudaStream_t st) {
-  int e = 0;
-  hhg::check_cuda(cudaMemcpyAsync(&e, m.err, sizeof(int), cudaMemcpyDeviceToHost, st), "err readback");
+// Reads the device error word (and clears it).  Bit 0: a bounded wait gave
+// up (HHG_ERR_TIMEOUT).  Bit 1: an index check of the bounds-checking build
+// failed (HHG_ERR_BOUNDS; words 1..3 hold the site and the value, copied into
+// *msg).  HHG_OK when neither is set.
+hhg_status device_error(const hhg::Mesh& m, cudaStream_t st, std::string* msg) {
+  int e[4] = {0, 0, 0, 0};
+  hhg::check_cuda(cudaMemcpyAsync(e, m.err, sizeof(e), cudaMemcpyDeviceToHost, st), "err readback");
   hhg::check_cuda(cudaStreamSynchronize(st), "sync");
-  if (e) {
-    hhg::check_cuda(cudaMemsetAsync(m.err, 0, sizeof(int), st), "err clear");
-    hhg::check_cuda(cudaMemsetAsync(m.gbar, 0, hhg::kGridBarWords * sizeof(unsigned), st), "grid barrier reset");
+  if (e[0] == 0) return HHG_OK;
+  hhg::check_cuda(cudaMemsetAsync(m.err, 0, sizeof(e), st), "err clear");
+  hhg::check_cuda(cudaMemsetAsync(m.gbar, 0, hhg::kGridBarWords * sizeof(unsigned), st), "grid barrier reset");
+  hhg::check_cuda(cudaStreamSynchronize(st), "sync");
+  if (e[0] & 2) {
+    static const char* const kSite[] = {"?", "rotated frame point", "rotated frame element", "face id or task",
+                                        "edge id or position", "vertex id", "corner or vertex-edge range"};
+    const int site = e[1] >= 1 && e[1] <= 6 ? e[1] : 0;
+    const long long v = (long long)(((uint64_t)(uint32_t)e[3] << 32) | (uint32_t)e[2]);
+    *msg = std::string("index check failed: ") + kSite[site] + " (value " + std::to_string(v) + ")";
+    return HHG_ERR_BOUNDS;
   }
-  return e != 0;
+  *msg = "a device-side wait gave up";
+  return HHG_ERR_TIMEOUT;
 }
 
 cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+// every C-ABI entry point is an NVTX range named after it
+#define HHG_ENTRY_RANGE hhg::NvtxRange hhg_entry_range_(__func__)
 
 double read_scalar(const double* dev, cudaStream_t st) {
   double h = 0.0;
@@ -112,6 +128,9 @@ namespace hhg {
 // computed here from the caller's b.
 static void vcycle_level(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2,
                          int smoother, bool bs_ready, cudaStream_t st) {
+  static const char* const kLevelRange[] = {"level 0", "level 1", "level 2", "level 3", "level 4", "level 5",
+                                             "level 6", "level 7", "level 8", "level 9", "level 10"};
+  NvtxRange range(kLevelRange[l < 0 ? 0 : (l > 10 ? 10 : l)]);
   if (l == 0) {
     coarse_solve(m, prec, b, x, st);
     return;
@@ -180,6 +199,7 @@ extern "C" {
 
 hhg_status hhg_mesh_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
                            const uint8_t* dirichlet_vertex, int32_t max_level, hhg_mesh* out) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     need(out, "out");
     *out = nullptr;
@@ -191,15 +211,24 @@ hhg_status hhg_mesh_create(const double* xy, int64_t nv, const int32_t* tri, int
 }
 
 hhg_status hhg_mesh_destroy(hhg_mesh mesh) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     if (!mesh) return HHG_OK;
+    // a failed index check not yet reported is reported here
+    int e[4] = {0, 0, 0, 0};
+    if (mesh->m->err && cudaMemcpy(e, mesh->m->err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess) e[0] = 0;
     hhg::mesh_destroy_internal(mesh->m);
     delete mesh;
+    if (e[0] & 2)
+      return fail(HHG_ERR_BOUNDS, "index check failed (site " + std::to_string(e[1]) + ", value " +
+                                      std::to_string((long long)(((uint64_t)(uint32_t)e[3] << 32) | (uint32_t)e[2])) +
+                                      ") since the last report");
     return HHG_OK;
   });
 }
 
 hhg_status hhg_mesh_info(hhg_mesh mesh, int32_t level, hhg_info* out) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -228,6 +257,7 @@ hhg_status hhg_mesh_info(hhg_mesh mesh, int32_t level, hhg_info* out) {
 }
 
 hhg_status hhg_set_coefficient(hhg_mesh mesh, const double* k_elem_dev, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::set_coefficient(get(mesh), k_elem_dev, S(stream));
     return HHG_OK;
@@ -236,6 +266,7 @@ hhg_status hhg_set_coefficient(hhg_mesh mesh, const double* k_elem_dev, void* st
 
 hhg_status hhg_from_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* src,
                               void* dst, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -249,6 +280,7 @@ hhg_status hhg_from_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const
 
 hhg_status hhg_to_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* src,
                             void* dst, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -261,6 +293,7 @@ hhg_status hhg_to_canonical(hhg_mesh mesh, int32_t level, hhg_prec prec, const v
 }
 
 hhg_status hhg_dof_coords(hhg_mesh mesh, int32_t level, double* xy_dev, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -272,6 +305,7 @@ hhg_status hhg_dof_coords(hhg_mesh mesh, int32_t level, double* xy_dev, void* st
 
 hhg_status hhg_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x, void* y,
                      void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -286,6 +320,7 @@ hhg_status hhg_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x,
 
 hhg_status hhg_residual(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x,
                         const void* b, void* r, double* norm_dev, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -302,6 +337,7 @@ hhg_status hhg_residual(hhg_mesh mesh, int32_t level, hhg_prec prec, const void*
 
 hhg_status hhg_assign(hhg_mesh mesh, int32_t level, hhg_prec prec, double alpha, const void* x1,
                       double beta, const void* x2, void* dst, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -316,6 +352,7 @@ hhg_status hhg_assign(hhg_mesh mesh, int32_t level, hhg_prec prec, double alpha,
 
 hhg_status hhg_dot(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1, const void* x2,
                    double* result_dev, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -330,6 +367,7 @@ hhg_status hhg_dot(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1, 
 
 hhg_status hhg_dot_noalloc(hhg_mesh mesh, int32_t level, hhg_prec prec, const void* x1,
                            const void* x2, double* result_dev, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -344,6 +382,7 @@ hhg_status hhg_dot_noalloc(hhg_mesh mesh, int32_t level, hhg_prec prec, const vo
 
 hhg_status hhg_restrict(hhg_mesh mesh, int32_t fine_level, hhg_prec prec, const void* r_fine,
                         void* b_coarse, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, fine_level, 1);
@@ -357,6 +396,7 @@ hhg_status hhg_restrict(hhg_mesh mesh, int32_t fine_level, hhg_prec prec, const 
 
 hhg_status hhg_prolongate_add(hhg_mesh mesh, int32_t fine_level, hhg_prec prec,
                               const void* x_coarse, void* x_fine, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, fine_level, 1);
@@ -372,6 +412,7 @@ hhg_status hhg_prolongate_add(hhg_mesh mesh, int32_t fine_level, hhg_prec prec,
 
 hhg_status hhg_smooth(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, const void* b,
                       int32_t smoother, int32_t sweeps, double omega, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level, 1);
@@ -407,6 +448,7 @@ hhg_status hhg_smooth(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
 
 hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, const void* b,
                       const hhg_vcycle_opts* opts, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -427,6 +469,7 @@ hhg_status hhg_vcycle(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
 
 hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
                      const hhg_solve_opts* opts, hhg_solve_report* rep, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -441,15 +484,17 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
       throw ArgError("bad solve mode");
     if (o.mode == HHG_SOLVE_PCG || o.mode == HHG_SOLVE_FPCG) {
       hhg::pcg_solve(m, level, x, b, o, rep, o.mode == HHG_SOLVE_FPCG, S(stream));
-      if (device_timed_out(m, S(stream))) return fail(HHG_ERR_TIMEOUT, "a device-side wait gave up");
-      return HHG_OK;
+      std::string msg;
+      const hhg_status de = device_error(m, S(stream), &msg);
+      return de == HHG_OK ? HHG_OK : fail(de, msg);
     }
     if (o.mode == HHG_SOLVE_FGMRES) {
       int used = 0;
       hhg::fgmres_solve(m, level, x, b, o, o.smoother, o.restart > 0 ? o.restart : 20, rep, &used, S(stream));
       if (rep) rep->smoother_used = used;
-      if (device_timed_out(m, S(stream))) return fail(HHG_ERR_TIMEOUT, "a device-side wait gave up");
-      return HHG_OK;
+      std::string msg;
+      const hhg_status de = device_error(m, S(stream), &msg);
+      return de == HHG_OK ? HHG_OK : fail(de, msg);
     }
     cudaStream_t st = S(stream);
     const hhg::LevelData& ld = m.levels[level];
@@ -504,7 +549,9 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
     if (cur != x)
       hhg::check_cuda(cudaMemcpyAsync(x, cur, (size_t)ld.lv.len * sizeof(double), cudaMemcpyDeviceToDevice, st),
                  "iterate copy");
-    if (device_timed_out(m, st)) status = HHG_ERR_TIMEOUT;
+    std::string dmsg;
+    const hhg_status de = device_error(m, st, &dmsg);
+    if (de != HHG_OK) status = de;
     if (rep) {
       rep->smoother_used = HHG_SMOOTH_GS;
       rep->iterations = it;
@@ -512,7 +559,7 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
       rep->r0 = r0;
       rep->r_final = r;
     }
-    if (status == HHG_ERR_TIMEOUT) return fail(status, "a device-side wait gave up");
+    if (de != HHG_OK) return fail(status, dmsg);
     if (status == HHG_ERR_NAN) return fail(status, "non-finite residual norm");
     if (status == HHG_ERR_NOT_CONVERGED) return fail(status, "max_iter reached");
     return HHG_OK;
@@ -520,6 +567,7 @@ hhg_status hhg_solve(hhg_mesh mesh, int32_t level, double* x, const double* b,
 }
 
 hhg_status hhg_coarse_tail(hhg_mesh mesh, int32_t set, int32_t* level) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     need(level, "level");
@@ -536,14 +584,17 @@ hhg_status hhg_coarse_tail(hhg_mesh mesh, int32_t set, int32_t* level) {
 }
 
 hhg_status hhg_sync(hhg_mesh mesh, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
-    if (device_timed_out(m, S(stream))) return fail(HHG_ERR_TIMEOUT, "a device-side wait gave up");
-    return HHG_OK;
+    std::string msg;
+    const hhg_status de = device_error(m, S(stream), &msg);
+    return de == HHG_OK ? HHG_OK : fail(de, msg);
   });
 }
 
 hhg_status hhg_debug_wait_limit(hhg_mesh mesh, int32_t extra_arrivals, int64_t max_polls) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     if (extra_arrivals < 0) throw ArgError("extra_arrivals < 0");
@@ -570,6 +621,7 @@ static hhg_p2_opts p2_defaults(const hhg_p2_opts* o) {
 }
 
 hhg_status hhg_p2_apply(hhg_mesh mesh, int32_t level, const double* x, double* y, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     p2_vec_args(m, level, {{x, "x"}, {y, "y"}});
@@ -580,6 +632,7 @@ hhg_status hhg_p2_apply(hhg_mesh mesh, int32_t level, const double* x, double* y
 
 hhg_status hhg_p2_residual(hhg_mesh mesh, int32_t level, const double* x, const double* b, double* r,
                            double* norm_dev, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     p2_vec_args(m, level, {{x, "x"}, {b, "b"}, {r, "r"}});
@@ -591,6 +644,7 @@ hhg_status hhg_p2_residual(hhg_mesh mesh, int32_t level, const double* x, const 
 
 hhg_status hhg_p2_smooth(hhg_mesh mesh, int32_t level, double* x, const double* b, int32_t smoother,
                          int32_t sweeps, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     p2_vec_args(m, level, {{x, "x"}, {b, "b"}});
@@ -603,6 +657,7 @@ hhg_status hhg_p2_smooth(hhg_mesh mesh, int32_t level, double* x, const double* 
 
 hhg_status hhg_p2_cycle(hhg_mesh mesh, int32_t level, double* x, const double* b, const hhg_p2_opts* opts,
                         void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     p2_vec_args(m, level, {{x, "x"}, {b, "b"}});
@@ -614,6 +669,7 @@ hhg_status hhg_p2_cycle(hhg_mesh mesh, int32_t level, double* x, const double* b
 
 hhg_status hhg_p2_solve(hhg_mesh mesh, int32_t level, double* x, const double* b, const hhg_p2_opts* opts,
                         hhg_solve_report* rep, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     p2_vec_args(m, level, {{x, "x"}, {b, "b"}});
@@ -647,7 +703,9 @@ hhg_status hhg_p2_solve(hhg_mesh mesh, int32_t level, double* x, const double* b
       record(it, rn);
       if (!std::isfinite(rn)) status = HHG_ERR_NAN;
     }
-    if (device_timed_out(m, st)) status = HHG_ERR_TIMEOUT;
+    std::string dmsg;
+    const hhg_status de = device_error(m, st, &dmsg);
+    if (de != HHG_OK) status = de;
     if (rep) {
       rep->iterations = it;
       rep->status = status;
@@ -655,7 +713,7 @@ hhg_status hhg_p2_solve(hhg_mesh mesh, int32_t level, double* x, const double* b
       rep->r_final = rn;
       rep->smoother_used = HHG_SMOOTH_GS;
     }
-    if (status == HHG_ERR_TIMEOUT) return fail(status, "a device-side wait gave up");
+    if (de != HHG_OK) return fail(status, dmsg);
     if (status == HHG_ERR_NAN) return fail(status, "non-finite residual norm");
     if (status == HHG_ERR_NOT_CONVERGED) return fail(status, "max_iter reached");
     return HHG_OK;
@@ -663,6 +721,7 @@ hhg_status hhg_p2_solve(hhg_mesh mesh, int32_t level, double* x, const double* b
 }
 
 hhg_status hhg_tune(hhg_mesh mesh, hhg_prec prec, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_prec(prec);
@@ -672,6 +731,7 @@ hhg_status hhg_tune(hhg_mesh mesh, hhg_prec prec, void* stream) {
 }
 
 hhg_status hhg_fp64_arith(hhg_mesh mesh, int32_t set, int32_t* mode) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     need(mode, "mode");
@@ -689,6 +749,7 @@ hhg_status hhg_fp64_arith(hhg_mesh mesh, int32_t set, int32_t* mode) {
 
 hhg_status hhg_sweep_config(hhg_mesh mesh, int32_t level, hhg_prec prec, int32_t set,
                             int32_t* variant, int32_t* param) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level);
@@ -710,6 +771,7 @@ hhg_status hhg_sweep_config(hhg_mesh mesh, int32_t level, hhg_prec prec, int32_t
 hhg_status hhg_batch_create(int32_t n, const double* const* xy, const int64_t* nv,
                             const int32_t* const* tri, const int64_t* nt, const int32_t* levels,
                             hhg_batch* out) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     need(out, "out");
     *out = nullptr;
@@ -720,6 +782,7 @@ hhg_status hhg_batch_create(int32_t n, const double* const* xy, const int64_t* n
 }
 
 hhg_status hhg_batch_destroy(hhg_batch batch) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     if (!batch) return HHG_OK;
     hhg::batch_destroy(batch->b);
@@ -729,6 +792,7 @@ hhg_status hhg_batch_destroy(hhg_batch batch) {
 }
 
 hhg_status hhg_batch_info(hhg_batch batch, int32_t problem, hhg_info* out) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     if (!batch || !batch->b) throw ArgError("NULL batch");
     need(out, "out");
@@ -738,6 +802,7 @@ hhg_status hhg_batch_info(hhg_batch batch, int32_t problem, hhg_info* out) {
 }
 
 hhg_status hhg_batch_tune(hhg_batch batch, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     if (!batch || !batch->b) throw ArgError("NULL batch");
     hhg::batch_tune(*batch->b, S(stream));
@@ -747,6 +812,7 @@ hhg_status hhg_batch_tune(hhg_batch batch, void* stream) {
 
 hhg_status hhg_batch_solve(hhg_batch batch, double* const* x, const double* const* b,
                            const hhg_solve_opts* opts, hhg_solve_report* reps, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     if (!batch || !batch->b) throw ArgError("NULL batch");
     need(x, "x");
@@ -761,6 +827,7 @@ hhg_status hhg_batch_solve(hhg_batch batch, double* const* x, const double* cons
 }
 
 hhg_status hhg_learned_set_weights(hhg_mesh mesh, const float* w_host, int64_t n) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     need(w_host, "w_host");
@@ -771,6 +838,7 @@ hhg_status hhg_learned_set_weights(hhg_mesh mesh, const float* w_host, int64_t n
 }
 
 hhg_status hhg_learned_get_weights(hhg_mesh mesh, float* w_host, int64_t n) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     need(w_host, "w_host");
@@ -783,6 +851,7 @@ hhg_status hhg_learned_get_weights(hhg_mesh mesh, float* w_host, int64_t n) {
 
 hhg_status hhg_learned_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const float* s,
                              void* x, float* d, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level, 1);
@@ -795,6 +864,7 @@ hhg_status hhg_learned_apply(hhg_mesh mesh, int32_t level, hhg_prec prec, const 
 }
 
 hhg_status hhg_learned_tensor_path(hhg_mesh mesh, int32_t set, int32_t* path) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     need(path, "path");
@@ -807,6 +877,7 @@ hhg_status hhg_learned_tensor_path(hhg_mesh mesh, int32_t set, int32_t* path) {
 hhg_status hhg_learned_grad(hhg_mesh mesh, int32_t n_crops, const float* X, const float* Sres,
                             const float* K, const int32_t* crops_host, float* grad_host,
                             float* loss_host, void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     need(X, "X");
@@ -824,6 +895,7 @@ hhg_status hhg_learned_grad(hhg_mesh mesh, int32_t n_crops, const float* X, cons
 hhg_status hhg_learned_train(hhg_mesh mesh, int32_t level, int32_t n_pairs, int32_t epochs,
                              int32_t batch, float lr, uint64_t seed, float* loss_history_host,
                              void* stream) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
     check_level(m, level, 6);
@@ -834,6 +906,7 @@ hhg_status hhg_learned_train(hhg_mesh mesh, int32_t level, int32_t n_pairs, int3
 }
 
 hhg_status hhg_profile_begin(uint32_t mask, int32_t level) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::profile_begin(mask, level);
     return HHG_OK;
@@ -841,6 +914,7 @@ hhg_status hhg_profile_begin(uint32_t mask, int32_t level) {
 }
 
 hhg_status hhg_profile_end(int64_t* launches, double* ms) {
+  HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::profile_end(launches, ms);
     return HHG_OK;

@@ -43,7 +43,11 @@ __global__ void __launch_bounds__(kThreadsGS)
   __shared__ int s_fail;
 
   const int4 tk = tasks[blockIdx.x];
-  const int f = tk.x, j0 = tk.y, j1 = tk.z;   // output rows [j0, j1)
+  int f = tk.x, j0 = tk.y, j1 = tk.z;   // output rows [j0, j1)
+  {
+    int s0 = 0;
+    face_task(M, L, f, s0, 0, j0, j1);
+  }
   const int N = L.N;
   const int64_t S = L.S;
   const int warp = threadIdx.x >> 5;
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(kThreadsGS)
       while (!mbar_try_wait(&bars[slot_of(r)], parity) && ++t <= kMaxTries) {
       }
     }
-    atomicExch(err, 1);
+    atomicOr(err, 1);
   }
 }
 

@@ -262,7 +262,8 @@ __device__ __forceinline__ void strip_task(const MeshTables& M, const LevelView&
                                            const T* __restrict__ b, const T* __restrict__ k, int4 tk,
                                            int lane) {
   using A = Arith<T, DF>;
-  const int f = tk.x, s = tk.y;
+  int f = tk.x, s = tk.y;
+  face_task(M, L, f, s, kStripUseful, tk.z, tk.w);
   StripArgs<T, DF> a;
   a.N = L.N;
   a.S = (int)L.S;
@@ -334,7 +335,7 @@ __device__ __forceinline__ void face_small(const MeshTables& M, const LevelView&
   }
   phase ^= 1u;
   if (!__syncthreads_and(landed)) {
-    if (threadIdx.x == 0) atomicExch(err, 1);
+    if (threadIdx.x == 0) atomicOr(err, 1);
     return;
   }
   const FaceRec& F = M.faces[f];
@@ -433,7 +434,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, GridBar& g, int* err
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c) : "memory");
     for (long long polls = 0; !g.failed && ld_acquire(c) < g.target;) {
       if (++polls > g.polls) {
-        atomicExch(err, 1);
+        atomicOr(err, 1);
         g.failed = true;
       }
     }
@@ -479,8 +480,8 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
   };
   auto edge_pre = [&](int pk, EdgePre& p) {
     if (pk < 0) return;
-    p.e = pk / (L.N + 1);
-    p.t = pk - p.e * (L.N + 1);
+    p.e = edge_id(M, pk / (L.N + 1));
+    p.t = edge_pos(M, L, pk - (pk / (L.N + 1)) * (L.N + 1));
     p.E = M.edges[p.e];
   };
   auto vertices = [&](T* x, const VertRec& V0) {

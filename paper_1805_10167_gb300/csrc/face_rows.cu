@@ -214,8 +214,9 @@ __global__ void __launch_bounds__(kRowWarps * 32)
   SqAcc<T, DF> acc;
   const int lane = threadIdx.x & 31;
   for (int wt = blockIdx.x * kRowWarps + (int)(threadIdx.x >> 5); wt < ntasks; wt += gridDim.x * kRowWarps) {
-    const int4 tk = tasks[wt];
-    const int f = tk.x, s = tk.y;
+    int4 tk = tasks[wt];
+    int f = tk.x, s = tk.y;
+    face_task(M, L, f, s, kStripCols, tk.z, tk.w);
     const int64_t fb = L.f_off + (int64_t)f * L.FS;
     RowArgs<T> a;
     a.N = L.N;

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "hhg.h"
 
@@ -116,7 +117,45 @@ struct MeshTables {
   const Corner* corners;
   const VertEdge* vedges;
   int nv, ne, nf;
+  int ncorners, nvedges;   // lengths of the corner and vertex-edge tables
+  int* err;                // the mesh's device error word (bounds-checking build)
 };
+
+// ---------------------------------------------------------------- bounds checks
+// The bounds-checking build (-DHHG_CHECK_BOUNDS, libhhg_checked.so) checks the
+// indices of the table-driven gathers and scatters (ids read from the face,
+// edge, vertex, corner and vertex-edge records, their rotated face frames,
+// positions along edges) before each access.  A failed check sets bit 1 of the
+// mesh's error word, records the site code of the first failure in err[1]
+// and its value in err[2..3] (low, high word; reported with HHG_ERR_BOUNDS),
+// and the access goes to a valid index instead, so the kernel completes.
+// Bit 0 of the error word is the bounded waits' (HHG_ERR_TIMEOUT).  The
+// normal build compiles the checks away.
+enum BoundsSite {
+  BS_FACE_FRAME = 1,   // lattice point of a rotated face frame outside the closed triangle
+  BS_ELEM_FRAME = 2,   // micro-triangle of a rotated frame outside the face
+  BS_FACE = 3,         // face id
+  BS_EDGE = 4,         // edge id or edge position
+  BS_VERTEX = 5,       // vertex id
+  BS_TABLE = 6,        // corner / vertex-edge table range
+  BS_ROW = 7           // coarse-tail row or column
+};
+
+#ifdef HHG_CHECK_BOUNDS
+__device__ __forceinline__ bool bounds_ok(const MeshTables& M, bool ok, int site, int64_t idx) {
+  if (!ok) {
+    atomicOr(M.err, 2);
+    if (atomicCAS(M.err + 1, 0, site) == 0) {
+      M.err[2] = (int)(idx & 0xffffffff);
+      M.err[3] = (int)(idx >> 32);
+    }
+  }
+  return ok;
+}
+#define HHG_BOUNDS_OK(M, ok, site, idx) ::hhg::bounds_ok((M), (ok), (site), (int64_t)(idx))
+#else
+#define HHG_BOUNDS_OK(M, ok, site, idx) true
+#endif
 
 // ---------------------------------------------------------------- indexing
 // Rotated face frame: rotation r relabels the face as (v[r], v[r+1], v[r+2]);
@@ -143,6 +182,58 @@ __host__ __device__ inline int64_t rot_dn(const LevelView& L, int rot, int ip, i
   if (rot == 0) return ip + S * jp;
   if (rot == 1) return (N - 2) + ip * (S - 1) - jp;
   return S * (N - 2) - S * ip + (1 - S) * jp;
+}
+
+// Checked forms of the table-driven indexing.  In the bounds-checking build
+// each reports a bad value (see bounds_ok) and returns an index that stays in
+// bounds instead (id 0, slot 0 of the face, an empty range); in the normal
+// build each is the plain index.
+__device__ __forceinline__ int face_id(const MeshTables& M, int f) {
+  return HHG_BOUNDS_OK(M, f >= 0 && f < M.nf, BS_FACE, f) ? f : 0;
+}
+__device__ __forceinline__ int edge_id(const MeshTables& M, int e) {
+  return HHG_BOUNDS_OK(M, e >= 0 && e < M.ne, BS_EDGE, e) ? e : 0;
+}
+__device__ __forceinline__ int vert_id(const MeshTables& M, int v) {
+  return HHG_BOUNDS_OK(M, v >= 0 && v < M.nv, BS_VERTEX, v) ? v : 0;
+}
+// position t (0..N) along an edge of lattice L
+__device__ __forceinline__ int edge_pos(const MeshTables& M, const LevelView& L, int t) {
+  return HHG_BOUNDS_OK(M, t >= 0 && t <= L.N, BS_EDGE, (int64_t)t << 32) ? t : 0;
+}
+// [b, e) inside a table of n records (corners, vertex edges)
+__device__ __forceinline__ void table_range(const MeshTables& M, int& b, int& e, int n) {
+  if (!HHG_BOUNDS_OK(M, b >= 0 && b <= e && e <= n, BS_TABLE, (int64_t)b * 65536 + e)) b = e = 0;
+}
+// face task: strip s of width w (w = 0: no strips), rows [j0, j1) of the
+// face's N + 1 rows; a bad task becomes an empty one on face 0
+__device__ __forceinline__ void face_task(const MeshTables& M, const LevelView& L, int& f, int& s, int w, int& j0,
+                                          int& j1) {
+  if (!HHG_BOUNDS_OK(M, f >= 0 && f < M.nf && s >= 0 && (int64_t)s * w <= L.N && 0 <= j0 && j0 <= j1 && j1 <= L.N + 1,
+                     BS_FACE, (int64_t)f << 32 | (int64_t)s << 16 | j0)) {
+    f = s = 0;
+    j0 = j1 = 1;
+  }
+}
+// slot of lattice point (ip, jp) of rotated frame `rot` within its face block
+__device__ __forceinline__ int64_t frame_slot(const MeshTables& M, const LevelView& L, int rot, int ip, int jp) {
+  if (!HHG_BOUNDS_OK(M, rot >= 0 && rot < 3 && ip >= 0 && jp >= 0 && ip + jp <= L.N, BS_FACE_FRAME,
+                     (int64_t)rot << 40 | (int64_t)ip << 20 | jp))
+    return 0;
+  return rot_slot(L, rot, ip, jp);
+}
+// upward / downward micro-triangle (ip, jp) of rotated frame `rot` within the coefficient arrays
+__device__ __forceinline__ int64_t frame_up(const MeshTables& M, const LevelView& L, int rot, int ip, int jp) {
+  if (!HHG_BOUNDS_OK(M, rot >= 0 && rot < 3 && ip >= 0 && jp >= 0 && ip + jp <= L.N - 1, BS_ELEM_FRAME,
+                     (int64_t)rot << 40 | (int64_t)ip << 20 | jp))
+    return 0;
+  return rot_up(L, rot, ip, jp);
+}
+__device__ __forceinline__ int64_t frame_dn(const MeshTables& M, const LevelView& L, int rot, int ip, int jp) {
+  if (!HHG_BOUNDS_OK(M, rot >= 0 && rot < 3 && ip >= 0 && jp >= 0 && ip + jp <= L.N - 2, BS_ELEM_FRAME,
+                     (int64_t)rot << 40 | (int64_t)ip << 20 | jp))
+    return 0;
+  return rot_dn(L, rot, ip, jp);
 }
 
 // ---------------------------------------------------------------- host mesh
@@ -430,6 +521,14 @@ class LaunchScope {
   cudaStream_t st_;
   cudaEvent_t start_ = nullptr, stop_ = nullptr;
 };
+// An NVTX range for the scope (shown by Nsight tools; a no-op otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 void profile_begin(uint32_t mask, int level);
 inline void check_launch(const char* what) { check_cuda(cudaGetLastError(), what); }
 

@@ -65,20 +65,20 @@ __global__ void k_ghost_fill(MeshTables M, LevelView L, T* __restrict__ v) {
       const FaceRec& F = M.faces[f];
       T val;
       if (p == 0) {
-        val = v[L.v_off + F.v[r]];
+        val = v[L.v_off + vert_id(M, F.v[r])];
       } else if (p == L.N) {
-        val = v[L.v_off + F.v[(r + 1) % 3]];
+        val = v[L.v_off + vert_id(M, F.v[(r + 1) % 3])];
       } else {
         const int t = F.aligned[r] ? p : L.N - p;
-        val = v[L.e_off + (int64_t)F.edge[r] * L.ES + t];
+        val = v[L.e_off + (int64_t)edge_id(M, F.edge[r]) * L.ES + t];
       }
-      v[L.f_off + (int64_t)f * L.FS + rot_slot(L, r, p, 0)] = val;
+      v[L.f_off + (int64_t)f * L.FS + frame_slot(M, L, r, p, 0)] = val;
     } else {
       const int e = (int)(idx - nface);
       const EdgeRec& E = M.edges[e];
       T* ve = v + L.e_off + (int64_t)e * L.ES;
-      ve[0] = v[L.v_off + E.lo];
-      ve[L.N] = v[L.v_off + E.hi];
+      ve[0] = v[L.v_off + vert_id(M, E.lo)];
+      ve[L.N] = v[L.v_off + vert_id(M, E.hi)];
     }
   }
 }
@@ -160,8 +160,8 @@ __global__ void k_edge(MeshTables M, LevelView L, const int* __restrict__ list, 
     int e, t;
     if (list) {
       const int pk = list[idx];
-      e = pk / (L.N + 1);
-      t = pk - e * (L.N + 1);
+      e = edge_id(M, pk / (L.N + 1));
+      t = edge_pos(M, L, pk - (pk / (L.N + 1)) * (L.N + 1));
     } else {
       e = (int)(idx / (L.N - 1));
       t = (int)(idx - (int64_t)e * (L.N - 1)) + 1;
@@ -270,9 +270,11 @@ __global__ void k_restrict_ve(MeshTables M, LevelView Lf, LevelView Lc, const T*
       if (!V.dirichlet) {
         val = rf[Lf.v_off + v];
         T s = T(0);
-        for (int c = V.e_begin; c < V.e_end; ++c) {
+        int eb = V.e_begin, ee = V.e_end;
+        table_range(M, eb, ee, M.nvedges);
+        for (int c = eb; c < ee; ++c) {
           const VertEdge ve = M.vedges[c];
-          s += rf[Lf.e_off + (int64_t)ve.edge * Lf.ES + (ve.is_low ? 1 : Lf.N - 1)];
+          s += rf[Lf.e_off + (int64_t)edge_id(M, ve.edge) * Lf.ES + (ve.is_low ? 1 : Lf.N - 1)];
         }
         val += T(0.5) * s;
       }
@@ -291,8 +293,8 @@ __global__ void k_restrict_ve(MeshTables M, LevelView Lf, LevelView Lc, const T*
           if (k >= E.nfaces) break;
           const EdgeSide sd = E.side[k];
           const int p = 2 * (sd.aligned ? tc : Nc - tc);
-          const T* rff = rf + Lf.f_off + (int64_t)sd.face * Lf.FS;
-          s += rff[rot_slot(Lf, sd.rot, p, 1)] + rff[rot_slot(Lf, sd.rot, p - 1, 1)];
+          const T* rff = rf + Lf.f_off + (int64_t)face_id(M, sd.face) * Lf.FS;
+          s += rff[frame_slot(M, Lf, sd.rot, p, 1)] + rff[frame_slot(M, Lf, sd.rot, p - 1, 1)];
         }
         val = re[2 * tc] + T(0.5) * s;
       }

@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(256, 3)
     }
     if (!__syncthreads_and(done)) {   // report, wait once more (bounded), stop
       if (tid == 0) {
-        atomicExch(err, 1);
+        atomicOr(err, 1);
         for (long it = 0; it < kUmmaPolls; ++it)
           if (mbar_try_wait(mbar, phase)) break;
       }

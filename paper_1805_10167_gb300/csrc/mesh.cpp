@@ -319,6 +319,8 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
     m.tab.nv = m.nv;
     m.tab.ne = m.ne;
     m.tab.nf = m.nf;
+    m.tab.ncorners = (int)m.h_corners.size();
+    m.tab.nvedges = (int)m.h_vedges.size();
     for (int l = 0; l <= max_level; ++l) {
       LevelData& ld = m.levels[l];
       if (l >= 1) ld.colour_list = upload(m, lists[l]);
@@ -353,6 +355,7 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
     m.partials = (double*)dev_alloc(m, kMaxPartials * sizeof(double));
     m.scalars = (double*)dev_alloc(m, 16 * sizeof(double));
     m.err = (int*)dev_alloc(m, 16 * sizeof(int));
+    m.tab.err = m.err;
     m.gbar = (unsigned*)dev_alloc(m, kGridBarWords * sizeof(unsigned));   // zeroed
     noalloc_setup(m);
     p2_setup(m);

@@ -326,17 +326,17 @@ __global__ void __launch_bounds__(kP2Threads)
 // Share of face f (rotation r) in the row of the side point at position p
 // (rotated frame (p, 0)); returns the sum over off-centre entries, the
 // centre weight in *wc.
-__device__ __forceinline__ double side_share(const LevelView& L, const P2Face& F, int64_t base, int r, int p,
-                                             const double* x, double* wc) {
+__device__ __forceinline__ double side_share(const MeshTables& M, const LevelView& L, const P2Face& F, int64_t base,
+                                             int r, int p, const double* x, double* wc) {
   double acc = 0.0;
   if ((p & 1) == 0) {
     *wc += F.se[r][0];
 #pragma unroll
-    for (int q = 1; q < 9; ++q) acc += F.se[r][q] * x[base + rot_slot(L, r, p + kOffSE[q].x, kOffSE[q].y)];
+    for (int q = 1; q < 9; ++q) acc += F.se[r][q] * x[base + frame_slot(M, L, r, p + kOffSE[q].x, kOffSE[q].y)];
   } else {
     *wc += F.so[r][0];
 #pragma unroll
-    for (int q = 1; q < 5; ++q) acc += F.so[r][q] * x[base + rot_slot(L, r, p + kOffSO[q].x, kOffSO[q].y)];
+    for (int q = 1; q < 5; ++q) acc += F.so[r][q] * x[base + frame_slot(M, L, r, p + kOffSO[q].x, kOffSO[q].y)];
   }
   return acc;
 }
@@ -353,8 +353,8 @@ __global__ void __launch_bounds__(kP2Threads)
     int e, t;
     if (list) {
       const int pk = list[k];
-      e = pk / (N1 + 1);
-      t = pk - e * (N1 + 1);
+      e = edge_id(M, pk / (N1 + 1));
+      t = edge_pos(M, L, pk - (pk / (N1 + 1)) * (N1 + 1));
     } else {
       e = (int)(k / (N1 - 1));
       t = (int)(k - (int64_t)e * (N1 - 1)) + 1;
@@ -369,7 +369,8 @@ __global__ void __launch_bounds__(kP2Threads)
     for (int q = 0; q < E.nfaces; ++q) {
       const EdgeSide sd = E.side[q];
       const int p = sd.aligned ? t : N1 - t;
-      ax += side_share(L, W[sd.face], L.f_off + (int64_t)sd.face * L.FS, sd.rot, p, x, &wc);
+      const int f = face_id(M, sd.face);
+      ax += side_share(M, L, W[f], L.f_off + (int64_t)f * L.FS, sd.rot, p, x, &wc);
     }
     const double xc = x[s];
     if (mode == P2_GS) out[s] = (b[s] - ax) / wc;
@@ -389,13 +390,17 @@ __global__ void __launch_bounds__(kP2Threads)
       continue;
     }
     double ax = 0.0, wc = 0.0;
-    for (int c = V.c_begin; c < V.c_end; ++c) {
+    int cb = V.c_begin, ce = V.c_end;
+    table_range(M, cb, ce, M.ncorners);
+    for (int c = cb; c < ce; ++c) {
       const Corner C = M.corners[c];
-      const P2Face& F = W[C.face];
-      const int64_t base = L.f_off + (int64_t)C.face * L.FS;
-      wc += F.co[C.rot][0];
+      const int f = face_id(M, C.face);
+      const P2Face& F = W[f];
+      const int64_t base = L.f_off + (int64_t)f * L.FS;
+      const int r = HHG_BOUNDS_OK(M, C.rot >= 0 && C.rot < 3, BS_FACE_FRAME, (int64_t)C.rot << 40) ? C.rot : 0;
+      wc += F.co[r][0];
 #pragma unroll
-      for (int q = 1; q < 5; ++q) ax += F.co[C.rot][q] * x[base + rot_slot(L, C.rot, kOffCO[q].x, kOffCO[q].y)];
+      for (int q = 1; q < 5; ++q) ax += F.co[r][q] * x[base + frame_slot(M, L, r, kOffCO[q].x, kOffCO[q].y)];
     }
     const double xc = x[s];
     if (mode == P2_GS) out[s] = (b[s] - ax) / wc;

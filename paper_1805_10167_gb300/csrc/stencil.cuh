@@ -58,19 +58,20 @@ __device__ __forceinline__ void edge_row(const MeshTables& M, const LevelView& L
   for (int s = 0; s < 2; ++s) {   // unrolled: the record stays in registers
     if (s >= E.nfaces) break;
     const EdgeSide sd = E.side[s];
-    const FaceRec& F = M.faces[sd.face];
+    const int f = face_id(M, sd.face);
+    const FaceRec& F = M.faces[f];
     const int r = sd.rot;
     const int p = sd.aligned ? t : L.N - t;
-    const T* xf = x + L.f_off + (int64_t)sd.face * L.FS;
-    const T xa = xf[rot_slot(L, r, p + 1, 0)], xb = xf[rot_slot(L, r, p - 1, 0)];
-    const T xc = xf[rot_slot(L, r, p, 1)], xd = xf[rot_slot(L, r, p - 1, 1)];
+    const T* xf = x + L.f_off + (int64_t)f * L.FS;
+    const T xa = xf[frame_slot(M, L, r, p + 1, 0)], xb = xf[frame_slot(M, L, r, p - 1, 0)];
+    const T xc = xf[frame_slot(M, L, r, p, 1)], xd = xf[frame_slot(M, L, r, p - 1, 1)];
     const T c0 = (T)F.cot[r], c1 = (T)F.cot[(r + 1) % 3], c2 = (T)F.cot[(r + 2) % 3];
     T wa, wb, wc, wd;
     if (VARK) {
-      const T* ku = k + (int64_t)sd.face * L.FS;
-      const T* kd = k + (int64_t)(M.nf + sd.face) * L.FS;
-      const T u1 = ku[rot_up(L, r, p, 0)], u0 = ku[rot_up(L, r, p - 1, 0)];
-      const T d0 = kd[rot_dn(L, r, p - 1, 0)];
+      const T* ku = k + (int64_t)f * L.FS;
+      const T* kd = k + (int64_t)(M.nf + f) * L.FS;
+      const T u1 = ku[frame_up(M, L, r, p, 0)], u0 = ku[frame_up(M, L, r, p - 1, 0)];
+      const T d0 = kd[frame_dn(M, L, r, p - 1, 0)];
       wa = T(0.5) * c2 * u1;
       wb = T(0.5) * c2 * u0;
       wc = T(0.5) * c1 * (u1 + d0);
@@ -95,15 +96,18 @@ __device__ __forceinline__ void vertex_row_warp(const MeshTables& M, const Level
                                                 const T* __restrict__ k, T& off, T& diag) {
   off = T(0);
   diag = T(0);
-  for (int c = V.c_begin + lane; c < V.c_end; c += 32) {
+  int cb = V.c_begin, ce = V.c_end;
+  table_range(M, cb, ce, M.ncorners);
+  for (int c = cb + lane; c < ce; c += 32) {
     const Corner cn = M.corners[c];
-    const FaceRec& F = M.faces[cn.face];
+    const int f = face_id(M, cn.face);
+    const FaceRec& F = M.faces[f];
     const int r = cn.rot;
-    const T* xf = x + L.f_off + (int64_t)cn.face * L.FS;
-    const T xa = xf[rot_slot(L, r, 1, 0)], xb = xf[rot_slot(L, r, 0, 1)];
+    const T* xf = x + L.f_off + (int64_t)f * L.FS;
+    const T xa = xf[frame_slot(M, L, r, 1, 0)], xb = xf[frame_slot(M, L, r, 0, 1)];
     const T c1 = (T)F.cot[(r + 1) % 3], c2 = (T)F.cot[(r + 2) % 3];
     T kk = T(1);
-    if (VARK) kk = k[(int64_t)cn.face * L.FS + rot_up(L, r, 0, 0)];
+    if (VARK) kk = k[(int64_t)f * L.FS + frame_up(M, L, r, 0, 0)];
     const T wa = T(0.5) * c2 * kk, wb = T(0.5) * c1 * kk;
     off -= wa * xa + wb * xb;
     diag += wa + wb;
@@ -126,19 +130,23 @@ __device__ __forceinline__ void vertex_gs_rec(const MeshTables& M, const LevelVi
   const int64_t s = L.v_off + v;
   const T nv = (b[s] - off) / diag;
   if (lane == 0) x[s] = nv;
-  for (int c = V.c_begin + lane; c < V.c_end; c += 32) {
+  int cb = V.c_begin, ce = V.c_end, eb = V.e_begin, ee = V.e_end;
+  table_range(M, cb, ce, M.ncorners);
+  table_range(M, eb, ee, M.nvedges);
+  for (int c = cb + lane; c < ce; c += 32) {
     const Corner cn = M.corners[c];
-    x[L.f_off + (int64_t)cn.face * L.FS + rot_slot(L, cn.rot, 0, 0)] = nv;
+    x[L.f_off + (int64_t)face_id(M, cn.face) * L.FS + frame_slot(M, L, cn.rot, 0, 0)] = nv;
   }
-  for (int c = V.e_begin + lane; c < V.e_end; c += 32) {
+  for (int c = eb + lane; c < ee; c += 32) {
     const VertEdge ve = M.vedges[c];
-    x[L.e_off + (int64_t)ve.edge * L.ES + (ve.is_low ? 0 : L.N)] = nv;
+    x[L.e_off + (int64_t)edge_id(M, ve.edge) * L.ES + (ve.is_low ? 0 : L.N)] = nv;
   }
 }
 
 template <typename T, bool VARK>
 __device__ __forceinline__ void vertex_gs(const MeshTables& M, const LevelView& L, int v, int lane,
                                           T* x, const T* __restrict__ b, const T* __restrict__ k) {
+  v = vert_id(M, v);
   const VertRec V = M.verts[v];
   vertex_gs_rec<T, VARK>(M, L, V, v, lane, x, b, k);
 }
@@ -160,13 +168,15 @@ __device__ __forceinline__ void edge_gs_rec(const MeshTables& M, const LevelView
     if (q >= E.nfaces) break;
     const EdgeSide sd = E.side[q];
     const int p = sd.aligned ? t : L.N - t;
-    x[L.f_off + (int64_t)sd.face * L.FS + rot_slot(L, sd.rot, p, 0)] = nv;
+    x[L.f_off + (int64_t)face_id(M, sd.face) * L.FS + frame_slot(M, L, sd.rot, p, 0)] = nv;
   }
 }
 
 template <typename T, bool VARK>
 __device__ __forceinline__ void edge_gs(const MeshTables& M, const LevelView& L, int e, int t, T* x,
                                         const T* __restrict__ b, const T* __restrict__ k) {
+  e = edge_id(M, e);
+  t = edge_pos(M, L, t);
   const EdgeRec E = M.edges[e];
   edge_gs_rec<T, VARK>(M, L, E, e, t, x, b, k);
 }

@@ -23,6 +23,8 @@
 #include <algorithm>
 #include <map>
 #include <set>
+#include <stdexcept>
+#include <string>
 #include <vector>
 
 #include "hhg_internal.h"
@@ -400,6 +402,17 @@ void tail_build(Mesh& m, const std::vector<std::vector<double>>& k_up,
           }
           p_ptr.push_back((int)p_cols.size());
         }
+      // every index the kernel follows stays inside its level's vectors
+      const auto in_range = [](const std::vector<int>& v, int n, const char* what) {
+        for (int q : v)
+          if (q < 0 || q >= n) throw std::logic_error(std::string("coarse tail: ") + what + " index out of range");
+      };
+      in_range(row_pt, h.n, "row");
+      in_range(cols, h.n, "column");
+      in_range(r_pt, hc.n, "restriction row");
+      in_range(r_cols, h.n, "restriction column");
+      in_range(p_pt, h.n, "prolongation row");
+      in_range(p_cols, hc.n, "prolongation column");
       d.nr = (int)r_pt.size();
       d.np = (int)p_pt.size();
       d.r_pt = up(P, r_pt);

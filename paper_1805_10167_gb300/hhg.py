@@ -5,7 +5,9 @@ library's CUDA kernels.  Vectors are passed as device pointers -- torch CUDA
 tensors (their ``data_ptr()``) or plain integers -- and streams as raw
 ``cudaStream_t`` handles (``torch.cuda.current_stream().cuda_stream``).
 There is no CPU fallback: if ``libhhg.so`` has not been built, importing this
-module raises ImportError.
+module raises ImportError.  ``HHG_LIBRARY=checked`` in the environment loads
+the bounds-checking build ``libhhg_checked.so`` instead (device-side index
+checks; a failed check is reported as ERR_BOUNDS).
 """
 from __future__ import annotations
 
@@ -15,14 +17,18 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhhg.so")
+_VARIANT = os.environ.get("HHG_LIBRARY", "")
+if _VARIANT not in ("", "checked"):
+    raise ImportError(f"HHG_LIBRARY={_VARIANT!r}: expected 'checked' or unset")
+LIB_PATH = os.path.join(_HERE, "libhhg_checked.so" if _VARIANT == "checked" else "libhhg.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} not built: run `python -m paper_1805_10167_gb300.build` "
-                      "(or __graft_entry__.build())")
+    raise ImportError(f"{LIB_PATH} not built: run `python -m paper_1805_10167_gb300.build"
+                      f"{' --checked' if _VARIANT else ''}` (or __graft_entry__.build())")
 lib = C.CDLL(LIB_PATH)
 
-OK, ERR_ARG, ERR_MESH, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_NAN, ERR_TIMEOUT, ERR_BREAKDOWN = range(9)
+(OK, ERR_ARG, ERR_MESH, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_NAN, ERR_TIMEOUT, ERR_BREAKDOWN,
+ ERR_BOUNDS) = range(10)
 F64, F32 = 0, 1
 SWEEP_RING, SWEEP_STRIP = 0, 1
 ARITH_IEEE, ARITH_DFLOAT = 0, 1
@@ -127,6 +133,11 @@ K_FACE_GS, K_FACE_ROWS, K_EDGE_VERTEX, K_TRANSFER, K_GHOST, K_OTHER, K_COUNT = r
 K_NAMES = ["face_gs", "face_rows", "edge_vertex", "transfer", "ghost", "other"]
 
 
+# index-check failures reported when a mesh was closed (bounds-checking build;
+# kept here too because a mesh closed by the garbage collector cannot raise)
+BOUNDS_FAILURES: list = []
+
+
 class HHGError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"hhg status {status}: {msg}")
@@ -194,8 +205,12 @@ class Mesh:
 
     def close(self):
         if getattr(self, "h", None):
-            lib.hhg_mesh_destroy(self.h)
-            self.h = None
+            h, self.h = self.h, None
+            st = lib.hhg_mesh_destroy(h)
+            if st == ERR_BOUNDS:     # bounds-checking build: a failure not reported before
+                msg = last_error()
+                BOUNDS_FAILURES.append(msg)
+                raise HHGError(st, msg)
 
     def __del__(self):
         try:

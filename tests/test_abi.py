@@ -33,6 +33,42 @@ def test_every_declared_symbol_is_exported():
         assert hasattr(lib, n), n
 
 
+def test_checked_build_exports_the_same_and_is_selected():
+    """libhhg_checked.so (device-side index checks) exports every declared
+    entry point, recompiles the kernels with table-driven indexing, and is
+    the library the binding loads under HHG_LIBRARY=checked."""
+    import subprocess
+    import sys
+    from paper_1805_10167_gb300 import build
+    p = os.path.join(ROOT, "paper_1805_10167_gb300", "libhhg_checked.so")
+    if not os.path.exists(p):
+        _lib_path()
+        build.build(checked=True)
+    lib = ctypes.CDLL(p)
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+    redo = {os.path.basename(s) for s in build.sources() if build.uses_checks(s)}
+    assert {"kernels.cu", "face_gs_strip.cu", "face_rows.cu", "face_gs.cu", "p2.cu"} <= redo
+    code = "from paper_1805_10167_gb300 import hhg; import os; print(os.path.basename(hhg.LIB_PATH), hhg.ERR_BOUNDS)"
+    for var, want in (("checked", "libhhg_checked.so"), ("", "libhhg.so")):
+        env = dict(os.environ, HHG_LIBRARY=var)
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr
+        assert r.stdout.split() == [want, "9"]
+
+
+def test_status_codes_match_header():
+    src = open(os.path.join(ROOT, "include", "hhg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    codes = dict((k, int(v)) for k, v in re.findall(r"\b(HHG_(?:OK|ERR_[A-Z_]+))\s*=\s*(\d+)", src))
+    _lib_path()
+    from paper_1805_10167_gb300 import hhg
+    for k, v in codes.items():
+        assert getattr(hhg, k[4:]) == v, k
+    assert codes["HHG_ERR_BOUNDS"] == 9
+
+
 def test_binding_covers_header():
     _lib_path()
     from paper_1805_10167_gb300 import hhg
