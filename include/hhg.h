@@ -490,6 +490,81 @@ hhg_status hhg_p2_cycle(hhg_mesh mesh, int32_t level, double* x, const double* b
 hhg_status hhg_p2_solve(hhg_mesh mesh, int32_t level, double* x, const double* b, const hhg_p2_opts* opts,
                         hhg_solve_report* rep, void* stream);
 
+/* Stokes flow (Sec. 5.2: isoviscous incompressible Stokes, equal-order
+ * P1-P1 elements with a Petrov-Galerkin pressure stabilisation, velocity and
+ * pressure solved together by multigrid; Sec. 4.3: an all-at-once multigrid
+ * with pointwise inexact Uzawa smoothers).  The paper fixes neither the
+ * stabilisation parameter nor the smoother; the system and smoother here:
+ *
+ *   A u_d + B_d^T p = f_d   on free velocity points (d = 1, 2)
+ *   B1 u1 + B2 u2 - C p = g on every pressure point
+ *
+ * A the P1 Laplacian (k = 1; HHG_ERR_ARG after hhg_set_coefficient with a
+ * field), B_d(q, j) = -integral phi_q d(phi_j)/dx_d, C(q, r) = delta sum_T
+ * h_T^2 integral_T grad(phi_q).grad(phi_r) with h_T the longest edge of
+ * micro-triangle T.  Velocity Dirichlet points are those of the mesh (their
+ * values in u1, u2 are data, B reads them); the pressure has no Dirichlet
+ * points.  Every vector is an FP64 level vector of `level` (hhg_info.vec_len,
+ * 16-byte aligned); the calls rewrite the ghost copies of their inputs u1,
+ * u2, p.  Uzawa step (forward): b_d = f_d - B_d^T p, nvel forward
+ * colour-ordered Gauss-Seidel sweeps of A u_d = b_d for d = 1, 2, then
+ * p += omega (B1 u1 + B2 u2 - C p - g) / s with s = diag(C + B D_A^-1 B^T)
+ * (D_A^-1 on free velocity points); backward: the pressure step first, then
+ * backward sweeps.  V-cycle: nu1 forward steps, residual, restriction
+ * (velocity as in hhg_restrict; pressure the same with no Dirichlet point),
+ * the cycle of the next coarser level from zero, prolongation and
+ * correction, nu2 backward steps; on coarse_level the correction is the
+ * stored inverse of the dense saddle-point system applied to the residual
+ * (with velocity Dirichlet conditions on the whole boundary, the constant
+ * pressure is in the null space: g must sum to zero over the pressure
+ * points, and the coarse correction is the one whose pressure sums to zero).
+ * A macro mesh whose vertices nearly all lie on the Dirichlet boundary has
+ * almost no velocity unknowns on level 0: a finer coarse_level then keeps the
+ * cycle's convergence (at most 4096 coarse unknowns). */
+typedef struct {
+  double delta;           /* stabilisation parameter (0.3)                          */
+  double omega;           /* pressure relaxation of the Uzawa step (0.4)            */
+  int32_t nvel;           /* velocity Gauss-Seidel sweeps per Uzawa step (2)        */
+  int32_t coarse_level;   /* the cycle's coarsest level, solved directly (0)        */
+} hhg_stokes_opts;
+/* Builds the stencil weights, the smoother diagonals of levels above
+ * coarse_level, the coarse inverse and the workspaces (levels coarse_level ..
+ * max_level: 15 level vectors per level at most).  opts NULL: the defaults
+ * above.  Synchronous; drops captured graphs; a second call replaces the
+ * first.  HHG_ERR_ARG for delta <= 0, omega <= 0, nvel < 1, coarse_level
+ * outside 0 .. max_level - 1, a coarse system over 4096 unknowns, or a
+ * coefficient field; HHG_ERR_OOM. */
+hhg_status hhg_stokes_setup(hhg_mesh mesh, const hhg_stokes_opts* opts);
+/* (y1, y2, yp) = the system matrix times (u1, u2, p): y_d = A u_d + B_d^T p
+ * on free velocity points (0 at Dirichlet points), yp = B1 u1 + B2 u2 - C p. */
+hhg_status hhg_stokes_apply(hhg_mesh mesh, int32_t level, const double* u1, const double* u2, const double* p,
+                            double* y1, double* y2, double* yp, void* stream);
+/* r = right-hand side - system matrix times (u1, u2, p) (velocity rows 0 at
+ * Dirichlet points); norm_dev (may be NULL): the 2-norm over free velocity
+ * rows of both components and every pressure row. */
+hhg_status hhg_stokes_residual(hhg_mesh mesh, int32_t level, const double* u1, const double* u2, const double* p,
+                               const double* f1, const double* f2, const double* g, double* r1, double* r2,
+                               double* rp, double* norm_dev, void* stream);
+/* `steps` Uzawa steps in place (forward != 0: forward order), level above
+ * coarse_level. */
+hhg_status hhg_stokes_smooth(hhg_mesh mesh, int32_t level, double* u1, double* u2, double* p, const double* f1,
+                             const double* f2, const double* g, int32_t forward, int32_t steps, void* stream);
+/* One V(nu1, nu2) cycle in place (level = coarse_level: the direct coarse
+ * correction). */
+hhg_status hhg_stokes_vcycle(hhg_mesh mesh, int32_t level, double* u1, double* u2, double* p, const double* f1,
+                             const double* f2, const double* g, int32_t nu1, int32_t nu2, void* stream);
+/* V(nu1, nu2) cycles from the guess until the residual norm (as in
+ * hhg_stokes_residual) is at most tol times the initial one; level above
+ * coarse_level.  Synchronous, one 8-byte readback per cycle, the cycle and
+ * the norm replayed as a CUDA graph from their third use on.  rep (may be
+ * NULL) as for hhg_solve.  Errors as for hhg_solve. */
+hhg_status hhg_stokes_solve(hhg_mesh mesh, int32_t level, double* u1, double* u2, double* p, const double* f1,
+                            const double* f2, const double* g, int32_t nu1, int32_t nu2, double tol,
+                            int32_t max_iter, hhg_solve_report* rep, void* stream);
+/* 1 / s (the Uzawa step's pressure scaling) on every pressure owner slot of a
+ * level above coarse_level, into s_out (a level vector; other slots 0). */
+hhg_status hhg_stokes_diag(hhg_mesh mesh, int32_t level, double* s_out, void* stream);
+
 /* Message of the last failed call on this thread ('\0'-terminated, truncated
  * to n bytes).  Returns the full message length. */
 size_t hhg_last_error(char* buf, size_t n);

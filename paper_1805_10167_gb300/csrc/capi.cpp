@@ -606,6 +606,142 @@ hhg_status hhg_debug_wait_limit(hhg_mesh mesh, int32_t extra_arrivals, int64_t m
   });
 }
 
+// ---------------------------------------------------------------- Stokes
+static hhg::StokesData* stokes_of(const hhg::Mesh& m) {
+  if (!m.stokes) throw ArgError("Stokes not set up (hhg_stokes_setup)");
+  return m.stokes;
+}
+
+static void stokes_vec_args(const hhg::Mesh& m, int level,
+                            std::initializer_list<std::pair<const void*, const char*>> v) {
+  stokes_of(m);
+  check_level(m, level);
+  for (const auto& a : v) need_vec(a.first, a.second);
+}
+
+hhg_status hhg_stokes_setup(hhg_mesh mesh, const hhg_stokes_opts* opts) {
+  HHG_ENTRY_RANGE;
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    hhg_stokes_opts o{0.3, 0.4, 2, 0};
+    if (opts) o = *opts;
+    hhg::graphs_clear(m);
+    hhg::stokes_setup(m, o.delta, o.omega, o.nvel, o.coarse_level);
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_stokes_apply(hhg_mesh mesh, int32_t level, const double* u1, const double* u2, const double* p,
+                            double* y1, double* y2, double* yp, void* stream) {
+  HHG_ENTRY_RANGE;
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    stokes_vec_args(m, level, {{u1, "u1"}, {u2, "u2"}, {p, "p"}, {y1, "y1"}, {y2, "y2"}, {yp, "yp"}});
+    hhg::stokes_apply(m, level, u1, u2, p, y1, y2, yp, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_stokes_residual(hhg_mesh mesh, int32_t level, const double* u1, const double* u2, const double* p,
+                               const double* f1, const double* f2, const double* g, double* r1, double* r2,
+                               double* rp, double* norm_dev, void* stream) {
+  HHG_ENTRY_RANGE;
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    stokes_vec_args(m, level, {{u1, "u1"}, {u2, "u2"}, {p, "p"}, {f1, "f1"}, {f2, "f2"}, {g, "g"}, {r1, "r1"},
+                               {r2, "r2"}, {rp, "rp"}});
+    hhg::stokes_residual(m, level, u1, u2, p, f1, f2, g, r1, r2, rp, norm_dev, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_stokes_smooth(hhg_mesh mesh, int32_t level, double* u1, double* u2, double* p, const double* f1,
+                             const double* f2, const double* g, int32_t forward, int32_t steps, void* stream) {
+  HHG_ENTRY_RANGE;
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    stokes_vec_args(m, level, {{u1, "u1"}, {u2, "u2"}, {p, "p"}, {f1, "f1"}, {f2, "f2"}, {g, "g"}});
+    if (steps < 0) throw ArgError("steps < 0");
+    hhg::stokes_smooth(m, level, u1, u2, p, f1, f2, g, forward != 0, steps, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_stokes_vcycle(hhg_mesh mesh, int32_t level, double* u1, double* u2, double* p, const double* f1,
+                             const double* f2, const double* g, int32_t nu1, int32_t nu2, void* stream) {
+  HHG_ENTRY_RANGE;
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    stokes_vec_args(m, level, {{u1, "u1"}, {u2, "u2"}, {p, "p"}, {f1, "f1"}, {f2, "f2"}, {g, "g"}});
+    hhg::stokes_vcycle(m, level, u1, u2, p, f1, f2, g, nu1, nu2, S(stream));
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_stokes_solve(hhg_mesh mesh, int32_t level, double* u1, double* u2, double* p, const double* f1,
+                            const double* f2, const double* g, int32_t nu1, int32_t nu2, double tol,
+                            int32_t max_iter, hhg_solve_report* rep, void* stream) {
+  HHG_ENTRY_RANGE;
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    stokes_vec_args(m, level, {{u1, "u1"}, {u2, "u2"}, {p, "p"}, {f1, "f1"}, {f2, "f2"}, {g, "g"}});
+    if (nu1 < 0 || nu2 < 0 || max_iter < 0 || !(tol >= 0.0)) throw ArgError("bad nu1, nu2, max_iter or tol");
+    if (level <= hhg::stokes_coarse_level(m)) throw ArgError("Stokes solve: level must be above coarse_level");
+    cudaStream_t st = S(stream);
+    double* nrm = m.scalars + 8;
+    hhg::stokes_norm(m, level, u1, u2, p, f1, f2, g, nrm, st);
+    const double r0 = read_scalar(nrm, st);
+    double rn = r0;
+    int it = 0;
+    hhg_status status = std::isfinite(r0) ? HHG_OK : HHG_ERR_NAN;
+    auto record = [&](int k, double v) {
+      if (rep && rep->history && k < rep->history_cap) rep->history[k] = v;
+    };
+    record(0, r0);
+    while (status == HHG_OK && rn > tol * r0 && r0 > 0.0) {
+      if (it >= max_iter) {
+        status = HHG_ERR_NOT_CONVERGED;
+        break;
+      }
+      const hhg::GraphKey key{(8ull << 56) | ((uint64_t)level << 48) | ((uint64_t)nu1 << 24) | (uint64_t)nu2,
+                              hhg::key_ptr(u1), hhg::key_ptr(u2), hhg::key_ptr(p), hhg::key_ptr(f1),
+                              hhg::key_ptr(f2), hhg::key_ptr(g), 0};
+      hhg::graphed(m, key, st, [&](cudaStream_t s) {
+        hhg::stokes_vcycle(m, level, u1, u2, p, f1, f2, g, nu1, nu2, s);
+        hhg::stokes_norm(m, level, u1, u2, p, f1, f2, g, nrm, s);
+      });
+      ++it;
+      rn = read_scalar(nrm, st);
+      record(it, rn);
+      if (!std::isfinite(rn)) status = HHG_ERR_NAN;
+    }
+    std::string dmsg;
+    const hhg_status de = device_error(m, st, &dmsg);
+    if (de != HHG_OK) status = de;
+    if (rep) {
+      rep->iterations = it;
+      rep->status = status;
+      rep->r0 = r0;
+      rep->r_final = rn;
+      rep->smoother_used = HHG_SMOOTH_GS;
+    }
+    if (de != HHG_OK) return fail(status, dmsg);
+    if (status == HHG_ERR_NAN) return fail(status, "non-finite residual norm");
+    if (status == HHG_ERR_NOT_CONVERGED) return fail(status, "max_iter reached");
+    return HHG_OK;
+  });
+}
+
+hhg_status hhg_stokes_diag(hhg_mesh mesh, int32_t level, double* s_out, void* stream) {
+  HHG_ENTRY_RANGE;
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    stokes_vec_args(m, level, {{s_out, "s_out"}});
+    hhg::stokes_diag(m, level, s_out, S(stream));
+    return HHG_OK;
+  });
+}
+
 // ---------------------------------------------------------------- P2
 static void p2_vec_args(const hhg::Mesh& m, int level, std::initializer_list<std::pair<const void*, const char*>> v) {
   if (level < 1 || level + 1 > m.max_level) throw ArgError("P2 level must be in 1 .. max_level - 1");

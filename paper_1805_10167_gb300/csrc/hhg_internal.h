@@ -298,6 +298,7 @@ struct LevelData {
 
 struct Learned;
 struct P2Data;
+struct StokesData;
 struct TailPlan;
 struct KrylovSpace;
 struct GraphCache;
@@ -307,6 +308,7 @@ struct Mesh {
   Learned* learned = nullptr;       // learned-smoother weights and optimiser state
   KrylovSpace* krylov = nullptr;    // FGMRES basis vectors
   P2Data* p2 = nullptr;             // P2 stencil weights and colour tables (p2.cu)
+  StokesData* stokes = nullptr;     // Stokes weights, smoother diagonals, workspaces (stokes.cu)
   TailPlan* tail = nullptr;         // one-CTA coarse tail of the V-cycle (tail.cu)
   bool tail_on = true;              // hhg_coarse_tail
   int tail_max = 3;
@@ -380,15 +382,16 @@ void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, c
 size_t face_gs_smem(const LevelView& L, int prec);
 void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,
                   void* work, cudaStream_t st);
-// bs_coarse (optional, FP64): also writes b_coarse / A_pp on the coarse face interiors
+// bs_coarse (optional, FP64): also writes b_coarse / A_pp on the coarse face interiors.
+// all_free (FP64): every unknown free, Dirichlet flags ignored (a pressure field)
 void restrict_op(const Mesh& m, int fine_level, int prec, const void* r_fine, void* b_coarse,
-                 cudaStream_t st, double* bs_coarse = nullptr);
+                 cudaStream_t st, double* bs_coarse = nullptr, bool all_free = false);
 // bs = b / A_pp on the face interiors of an FP64 level with k = 1
 void scale_rhs(const Mesh& m, int level, const double* b, double* bs, cudaStream_t st);
 // whether the sweeps of `level` in precision `prec` read a scaled right-hand side
 bool uses_scaled_rhs(const Mesh& m, int level, int prec);
 void prolongate_add(const Mesh& m, int fine_level, int prec, const void* x_coarse, void* x_fine,
-                    cudaStream_t st);
+                    cudaStream_t st, bool all_free = false);
 void coarse_solve(const Mesh& m, int prec, const void* b0, void* x0, cudaStream_t st);
 void zero_vec(const Mesh& m, int level, int prec, void* v, cudaStream_t st);
 void assign_op(const Mesh& m, int level, int prec, double a, const void* x1, double b,
@@ -464,6 +467,27 @@ void tail_free(Mesh& m);
 int tail_level(const Mesh& m, int prec);
 void tail_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, int nu2, cudaStream_t st);
 // P2 elements on level L (unknowns: the level-(L+1) lattice) and p-multigrid
+// canonical index of lattice point (i, j) of face f on a lattice of N intervals
+int canonical_index(const Mesh& m, int N, int f, int i, int j);
+
+// Stokes, P1-P1 PSPG, all-at-once multigrid with the inexact Uzawa smoother (stokes.cu)
+void stokes_setup(Mesh& m, double delta, double omega, int nvel, int coarse);
+void stokes_free(Mesh& m);
+void stokes_apply(const Mesh& m, int l, const double* u1, const double* u2, const double* p, double* y1, double* y2,
+                  double* yp, cudaStream_t st);
+void stokes_residual(const Mesh& m, int l, const double* u1, const double* u2, const double* p, const double* f1,
+                     const double* f2, const double* g, double* r1, double* r2, double* rp, double* norm_dev,
+                     cudaStream_t st);
+void stokes_smooth(const Mesh& m, int l, double* u1, double* u2, double* p, const double* f1, const double* f2,
+                   const double* g, bool forward, int steps, cudaStream_t st);
+void stokes_vcycle(const Mesh& m, int l, double* u1, double* u2, double* p, const double* f1, const double* f2,
+                   const double* g, int nu1, int nu2, cudaStream_t st);
+// the residual's norm (free velocity rows, every pressure row) into *norm_dev
+void stokes_norm(const Mesh& m, int l, const double* u1, const double* u2, const double* p, const double* f1,
+                 const double* f2, const double* g, double* norm_dev, cudaStream_t st);
+void stokes_diag(const Mesh& m, int l, double* s_out, cudaStream_t st);
+int stokes_coarse_level(const Mesh& m);
+
 void p2_setup(Mesh& m);
 void p2_free(Mesh& m);
 int p2_edge_colours(const Mesh& m, int L);

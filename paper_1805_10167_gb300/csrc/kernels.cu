@@ -255,7 +255,8 @@ __global__ void k_dot(MeshTables M, LevelView L, const T* __restrict__ x1,
 // --------------------------------------------------------------- transfers
 // Restriction R = P^T (full weighting) onto coarse owners; coarse Dirichlet
 // entries are 0.  Vertex and edge part: one thread per coarse unknown.
-template <typename T>
+// ALLFREE: every unknown free (a pressure field), Dirichlet flags ignored.
+template <typename T, bool ALLFREE = false>
 __global__ void k_restrict_ve(MeshTables M, LevelView Lf, LevelView Lc, const T* __restrict__ rf,
                               T* __restrict__ bc) {
   const int Nc = Lc.N;
@@ -267,7 +268,7 @@ __global__ void k_restrict_ve(MeshTables M, LevelView Lf, LevelView Lc, const T*
       const int v = (int)idx;
       const VertRec V = M.verts[v];
       T val = T(0);
-      if (!V.dirichlet) {
+      if (ALLFREE || !V.dirichlet) {
         val = rf[Lf.v_off + v];
         T s = T(0);
         int eb = V.e_begin, ee = V.e_end;
@@ -285,7 +286,7 @@ __global__ void k_restrict_ve(MeshTables M, LevelView Lf, LevelView Lc, const T*
       const int tc = (int)(q - (int64_t)e * (Nc - 1)) + 1;
       const EdgeRec E = M.edges[e];
       T val = T(0);
-      if (!E.dirichlet) {
+      if (ALLFREE || !E.dirichlet) {
         const T* re = rf + Lf.e_off + (int64_t)e * Lf.ES;
         T s = re[2 * tc - 1] + re[2 * tc + 1];
 #pragma unroll
@@ -333,7 +334,7 @@ __global__ void k_restrict_face(MeshTables M, LevelView Lf, LevelView Lc,
 
 // Prolongation and correction x_f += P x_c (linear interpolation).  Vertex
 // and edge part covers the owners and the edge end-point copies.
-template <typename T>
+template <typename T, bool ALLFREE = false>
 __global__ void k_prolong_ve(MeshTables M, LevelView Lf, LevelView Lc, const T* __restrict__ xc,
                              T* __restrict__ xf) {
   const int Nf = Lf.N;
@@ -343,13 +344,13 @@ __global__ void k_prolong_ve(MeshTables M, LevelView Lf, LevelView Lc, const T* 
        idx += (int64_t)gridDim.x * blockDim.x) {
     if (idx < M.nv) {
       const int v = (int)idx;
-      if (!M.verts[v].dirichlet) xf[Lf.v_off + v] += xc[Lc.v_off + v];
+      if (ALLFREE || !M.verts[v].dirichlet) xf[Lf.v_off + v] += xc[Lc.v_off + v];
     } else {
       const int64_t q = idx - M.nv;
       const int e = (int)(q / (Nf + 1));
       const int t = (int)(q - (int64_t)e * (Nf + 1));
       const bool interior = (t > 0 && t < Nf);
-      if (interior && M.edges[e].dirichlet) continue;
+      if (!ALLFREE && interior && M.edges[e].dirichlet) continue;
       const T* ce = xc + Lc.e_off + (int64_t)e * Lc.ES;
       const int tc = t >> 1;
       const T val = (t & 1) ? T(0.5) * (ce[tc] + ce[tc + 1]) : ce[tc];
@@ -838,11 +839,14 @@ void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, do
 }
 
 template <typename T>
-static void restrict_t(const Mesh& m, int lf, const T* rf, T* bc, cudaStream_t st, T* bsc) {
+static void restrict_t(const Mesh& m, int lf, const T* rf, T* bc, cudaStream_t st, T* bsc, bool all_free = false) {
   const LevelView& Lf = m.levels[lf].lv;
   const LevelView& Lc = m.levels[lf - 1].lv;
   const int64_t nve = m.nv + (Lc.N >= 2 ? (int64_t)m.ne * (Lc.N - 1) : 0);
-  HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "restrict ve", k_restrict_ve<T><<<blocks_for(nve, kThreads, 1024), kThreads, 0, st>>>(m.tab, Lf, Lc, rf, bc));
+  if (all_free)
+    HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "restrict ve", k_restrict_ve<T, true><<<blocks_for(nve, kThreads, 1024), kThreads, 0, st>>>(m.tab, Lf, Lc, rf, bc));
+  else
+    HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "restrict ve", k_restrict_ve<T><<<blocks_for(nve, kThreads, 1024), kThreads, 0, st>>>(m.tab, Lf, Lc, rf, bc));
   if (Lc.N >= 3) {
     const int64_t ntask = (int64_t)m.nf * (Lc.N - 2);
     HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "restrict face", k_restrict_face<T><<<blocks_for(ntask, kWarps, kMaxBlocksF), kThreads, 0, st>>>(m.tab, Lf, Lc, rf, bc, bsc));
@@ -850,8 +854,8 @@ static void restrict_t(const Mesh& m, int lf, const T* rf, T* bc, cudaStream_t s
 }
 
 void restrict_op(const Mesh& m, int fine_level, int prec, const void* r_fine, void* b_coarse,
-                 cudaStream_t st, double* bs_coarse) {
-  if (prec == 0) restrict_t(m, fine_level, (const double*)r_fine, (double*)b_coarse, st, bs_coarse);
+                 cudaStream_t st, double* bs_coarse, bool all_free) {
+  if (prec == 0) restrict_t(m, fine_level, (const double*)r_fine, (double*)b_coarse, st, bs_coarse, all_free);
   else restrict_t<float>(m, fine_level, (const float*)r_fine, (float*)b_coarse, st, nullptr);
 }
 
@@ -893,18 +897,21 @@ void scale_rhs(const Mesh& m, int level, const double* b, double* bs, cudaStream
 }
 
 template <typename T>
-static void prolong_t(const Mesh& m, int lf, const T* xc, T* xf, cudaStream_t st) {
+static void prolong_t(const Mesh& m, int lf, const T* xc, T* xf, cudaStream_t st, bool all_free = false) {
   const LevelView& Lf = m.levels[lf].lv;
   const LevelView& Lc = m.levels[lf - 1].lv;
   const int64_t nve = m.nv + (int64_t)m.ne * (Lf.N + 1);
-  HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "prolong ve", k_prolong_ve<T><<<blocks_for(nve, kThreads, 1024), kThreads, 0, st>>>(m.tab, Lf, Lc, xc, xf));
+  if (all_free)
+    HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "prolong ve", k_prolong_ve<T, true><<<blocks_for(nve, kThreads, 1024), kThreads, 0, st>>>(m.tab, Lf, Lc, xc, xf));
+  else
+    HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "prolong ve", k_prolong_ve<T><<<blocks_for(nve, kThreads, 1024), kThreads, 0, st>>>(m.tab, Lf, Lc, xc, xf));
   const int64_t ntask = (int64_t)m.nf * (Lf.N + 1);
   HHG_LAUNCH(HHG_K_TRANSFER, lf, st, "prolong face", k_prolong_face<T><<<blocks_for(ntask, kWarps, kMaxBlocksF), kThreads, 0, st>>>(m.tab, Lf, Lc, xc, xf));
 }
 
 void prolongate_add(const Mesh& m, int fine_level, int prec, const void* x_coarse, void* x_fine,
-                    cudaStream_t st) {
-  if (prec == 0) prolong_t(m, fine_level, (const double*)x_coarse, (double*)x_fine, st);
+                    cudaStream_t st, bool all_free) {
+  if (prec == 0) prolong_t(m, fine_level, (const double*)x_coarse, (double*)x_fine, st, all_free);
   else prolong_t(m, fine_level, (const float*)x_coarse, (float*)x_fine, st);
 }
 

@@ -367,6 +367,7 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
   } catch (...) {
     graphs_destroy(m);
     p2_free(m);
+    stokes_free(m);
     tail_free(m);
     for (void* p : m.allocations) cudaFree(p);
     delete mp;
@@ -382,6 +383,7 @@ void mesh_destroy_internal(Mesh* m) {
   learned_free(*m);
   krylov_free(*m);
   p2_free(*m);
+  stokes_free(*m);
   tail_free(*m);
   for (void* p : m->allocations) cudaFree(p);
   delete m;

@@ -486,4 +486,7 @@ void tail_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, i
   ghost_fill(m, l, prec, x, st);
 }
 
+// canonical index of lattice point (i, j) of face f on a lattice of N intervals
+int canonical_index(const Mesh& m, int N, int f, int i, int j) { return canon_of(m, N, f, i, j); }
+
 }  // namespace hhg

@@ -70,6 +70,10 @@ class P2Opts(C.Structure):
                 ("max_iter", C.c_int32), ("tol", C.c_double)]
 
 
+class StokesOpts(C.Structure):
+    _fields_ = [("delta", C.c_double), ("omega", C.c_double), ("nvel", C.c_int32), ("coarse_level", C.c_int32)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "hhg_mesh_create": [C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int32), C.c_int64,
@@ -87,6 +91,14 @@ _SIGS = {
     "hhg_p2_smooth": [_P, C.c_int32, _P, _P, C.c_int32, C.c_int32, _P],
     "hhg_p2_cycle": [_P, C.c_int32, _P, _P, C.POINTER(P2Opts), _P],
     "hhg_p2_solve": [_P, C.c_int32, _P, _P, C.POINTER(P2Opts), C.POINTER(SolveReport), _P],
+    "hhg_stokes_setup": [_P, C.POINTER(StokesOpts)],
+    "hhg_stokes_apply": [_P, C.c_int32] + [_P] * 7,
+    "hhg_stokes_residual": [_P, C.c_int32] + [_P] * 11,
+    "hhg_stokes_smooth": [_P, C.c_int32] + [_P] * 6 + [C.c_int32, C.c_int32, _P],
+    "hhg_stokes_vcycle": [_P, C.c_int32] + [_P] * 6 + [C.c_int32, C.c_int32, _P],
+    "hhg_stokes_solve": [_P, C.c_int32] + [_P] * 6 + [C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                                       C.POINTER(SolveReport), _P],
+    "hhg_stokes_diag": [_P, C.c_int32, _P, _P],
     "hhg_debug_wait_limit": [_P, C.c_int32, C.c_int64],
     "hhg_apply": [_P, C.c_int32, C.c_int32, _P, _P, _P],
     "hhg_residual": [_P, C.c_int32, C.c_int32, _P, _P, _P, _P, _P],
@@ -258,6 +270,42 @@ class Mesh:
         if raise_on_error and st != OK:
             raise HHGError(st, last_error())
         return st, out
+
+    # -------------------------------------------------------------- Stokes
+    def stokes_setup(self, delta=0.3, omega=0.4, nvel=2, coarse_level=0):
+        o = StokesOpts(delta, omega, nvel, coarse_level)
+        _check(lib.hhg_stokes_setup(self.h, C.byref(o)))
+
+    def stokes_apply(self, level, u1, u2, p, y1, y2, yp, stream=None):
+        _check(lib.hhg_stokes_apply(self.h, level, *(_ptr(v) for v in (u1, u2, p, y1, y2, yp)), _stream(stream)))
+
+    def stokes_residual(self, level, u1, u2, p, f1, f2, g, r1, r2, rp, norm_dev=None, stream=None):
+        _check(lib.hhg_stokes_residual(self.h, level, *(_ptr(v) for v in (u1, u2, p, f1, f2, g, r1, r2, rp)),
+                                       _ptr(norm_dev), _stream(stream)))
+
+    def stokes_smooth(self, level, u1, u2, p, f1, f2, g, forward=True, steps=1, stream=None):
+        _check(lib.hhg_stokes_smooth(self.h, level, *(_ptr(v) for v in (u1, u2, p, f1, f2, g)), int(bool(forward)),
+                                     steps, _stream(stream)))
+
+    def stokes_vcycle(self, level, u1, u2, p, f1, f2, g, nu1=2, nu2=2, stream=None):
+        _check(lib.hhg_stokes_vcycle(self.h, level, *(_ptr(v) for v in (u1, u2, p, f1, f2, g)), nu1, nu2,
+                                     _stream(stream)))
+
+    def stokes_solve(self, level, u1, u2, p, f1, f2, g, nu1=2, nu2=2, tol=1e-8, max_iter=100, stream=None,
+                     raise_on_error=True):
+        """Returns (status, report dict)."""
+        hist = (C.c_double * (max_iter + 1))()
+        rep = SolveReport(0, 0, 0.0, 0.0, hist, max_iter + 1, 0, 0.0, 0.0)
+        st = lib.hhg_stokes_solve(self.h, level, *(_ptr(v) for v in (u1, u2, p, f1, f2, g)), nu1, nu2, tol,
+                                  max_iter, C.byref(rep), _stream(stream))
+        out = {"iterations": rep.iterations, "status": rep.status, "r0": rep.r0, "r_final": rep.r_final,
+               "history": [hist[i] for i in range(min(rep.iterations + 1, max_iter + 1))]}
+        if raise_on_error and st != OK:
+            raise HHGError(st, last_error())
+        return st, out
+
+    def stokes_diag(self, level, s_out, stream=None):
+        _check(lib.hhg_stokes_diag(self.h, level, _ptr(s_out), _stream(stream)))
 
     def coarse_tail(self, level=None):
         """Reads, or sets when level is given, the coarse-tail cut-off (0 = off);

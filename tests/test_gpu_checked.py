@@ -2,8 +2,8 @@
 table-driven index: ids read from the face, edge, vertex, corner and
 vertex-edge records, their rotated face frames, positions along edges, face
 tasks) runs the parity suites of the operator, the smoothers, the
-transfers, the V-cycle and solves, P2 and the row kernels with no failed
-check and the same results as the normal build.
+transfers, the V-cycle and solves, P2, Stokes and the row kernels with no
+failed check and the same results as the normal build.
 
 The suites run in a child pytest with HHG_LIBRARY=checked; a failed check
 shows as a wrong result, as HHG_ERR_BOUNDS from hhg_sync / hhg_solve, or as
@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SUITES = ["tests/test_gpu_parity.py", "tests/test_gpu_p2.py", "tests/test_gpu_face_sweep.py",
-          "tests/test_gpu_rows.py", "tests/test_gpu_tail.py"]
+          "tests/test_gpu_rows.py", "tests/test_gpu_tail.py", "tests/test_gpu_stokes.py"]
 
 
 def test_checked_build_runs_parity_suites_clean():
