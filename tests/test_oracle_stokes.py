@@ -13,8 +13,8 @@ closed forms, invariants and brute force:
 - the exact solution is a fixed point of both Uzawa step orders;
 - a manufactured smooth solution converges at second order in the velocity
   (a dropped term or a wrong sign stops convergence);
-- the V-cycle's factor is bounded and level independent, and the solve
-  reaches the direct solution."""
+- the variable V-cycle's factor is bounded and level independent, and the
+  solve reaches the direct solution."""
 import numpy as np
 import pytest
 
@@ -173,18 +173,18 @@ def test_manufactured_solution_converges():
     assert perrs[2] < perrs[0] / 2.0, perrs
 
 
-@pytest.mark.parametrize("name", ["square", "annulus"])
-def test_vcycle_factor_bounded_and_level_independent(name):
+@pytest.mark.parametrize("name,levels,bound", [("square", (3, 4, 5, 6), 0.5), ("annulus", (3, 4), 0.6)])
+def test_vcycle_factor_bounded_and_level_independent(name, levels, bound):
     rates = []
-    for L in (3, 4) if name == "annulus" else (3, 4, 5):
+    for L in levels:
         S = hierarchy(name, L)
         f1, f2, g = random_rhs(S, L)
         lv = S.levels[L]
         u1, u2, p = np.zeros(lv.n), np.zeros(lv.n), np.zeros(lv.n)
         h = np.array(S.solve(u1, u2, p, f1, f2, g, tol=1e-8, max_iter=60))
         rates.append((h[-1] / h[0]) ** (1.0 / (len(h) - 1)))
-    assert max(rates) < 0.65, rates
-    assert max(rates) - min(rates) < 0.08, rates
+    assert max(rates) < bound, rates
+    assert max(rates) - min(rates) < 0.05, rates
 
 
 @pytest.mark.parametrize("coarse", [0, 1])
