@@ -84,14 +84,16 @@ def parse():
     ap.add_argument("--no-vark", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-p2", action="store_true")
+    ap.add_argument("--no-stokes", action="store_true")
     ap.add_argument("--learned-pairs", type=int, default=10000)
     ap.add_argument("--learned-epochs", type=int, default=12)
     ap.add_argument("--batch-size", type=int, default=64)
-    ap.add_argument("--case", default="bench", choices=["bench", "sweep", "cnn"],
+    ap.add_argument("--case", default="bench", choices=["bench", "sweep", "cnn", "stokes"],
                     help="sweep: only four forward Gauss-Seidel sweeps on --level in --prec; "
                          "cnn: only --steps applications of the learned smoother's network on "
                          "--level of the variable-coefficient annulus, timed (the small cases of "
-                         "the ncu captures under profiles/), no JSON line")
+                         "the ncu captures under profiles/), no JSON line; stokes: --warmup and --steps "
+                         "Uzawa steps on --level of the 256-face annulus, no JSON line")
     ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
     ap.add_argument("--arith", default="ieee", choices=["ieee", "dfloat"],
                     help="arithmetic of the FP64 face kernels in the sweep case")
@@ -366,6 +368,73 @@ def run_p2(args, g, info, b, dev, st, hbm_peak, n_sm, sm_mhz):
                                "frac": ach / peak, "ms_per_apply": ms,
                                "hbm_gbs": 16.0 * info.n_free / (ms / 1e3) / 1e9, "hbm_peak_gbs": hbm_peak,
                                "model": "13 FP64 instr per micro-vertex point, 7 per edge point; 16 B per point"}}
+
+
+def run_stokes(args, dev, st, hbm_peak):
+    """Stokes flow, P1-P1 with PSPG stabilisation, by the all-at-once V(2,2)
+    multigrid with the inexact Uzawa smoother (delta 0.3, omega 0.4, two
+    velocity sweeps per step, direct level-0 correction) on the 256-face
+    annulus (32 sectors x 4 rings: micro-triangles of aspect ratio about 1.4;
+    the 64 x 2 split's aspect ratio 3 slows every pointwise smoother, the P1
+    Poisson cycle included): at the paper's energy-transport size (level 6,
+    2145 unknowns per macro-face) and at level 9.  Right-hand sides: SplitMix64 seeds 71, 72,
+    73 in canonical order, g shifted to zero sum.  Reported: time to a 1e-8
+    relative residual (the cycle replayed as a captured graph), cycles,
+    factor, DoF rate over all three fields, and the roofline of the Stokes
+    face-row kernels inside the smoother (gradient rows 40 B, pressure Jacobi
+    rows 48 B per face point)."""
+    import torch
+    from paper_1805_10167_gb300 import hhg, inputs
+    xy, tri = inputs.annulus_mesh(32, 4)
+    out = {}
+    for L in (6, 9):
+        g = hhg.Mesh(xy, tri, L)
+        g.stokes_setup(0.3, 0.4, 2, 0)
+        info = g.info(L)
+        vec = lambda: torch.zeros(info.vec_len, dtype=torch.float64, device=dev)  # noqa: E731
+        rhs = []
+        for seed in (71, 72, 73):
+            c = torch.tensor(inputs.uniform_pm1(info.n_nodes, seed), dtype=torch.float64, device=dev)
+            if seed == 73:
+                c -= c.mean()
+            v = vec()
+            g.from_canonical(L, c, v, stream=st)
+            rhs.append(v)
+        u = [vec() for _ in range(3)]
+        g.stokes_solve(L, *u, *rhs, tol=1e-8, max_iter=200, stream=st)     # warm-up: graph capture
+        for v in u:
+            v.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep = g.stokes_solve(L, *u, *rhs, tol=1e-8, max_iter=200, stream=st)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        dofs = 2 * info.n_free + info.n_nodes
+        res = {"level": L, "macro_faces": info.n_faces, "dofs": dofs,
+               "seconds_to_1e-8": dt, "cycles": rep["iterations"],
+               "factor_per_cycle": (rep["r_final"] / rep["r0"]) ** (1.0 / max(1, rep["iterations"])),
+               "ms_per_cycle": 1e3 * dt / max(1, rep["iterations"]),
+               "gdofs_per_cycle": dofs * rep["iterations"] / dt / 1e9}
+        if L == 9:
+            steps = 8
+            g.stokes_smooth(L, *u, *rhs, forward=True, steps=2, stream=st)
+            torch.cuda.synchronize()
+            hhg.profile_begin(1 << hhg.K_FACE_ROWS, L)
+            g.stokes_smooth(L, *u, *rhs, forward=True, steps=steps, stream=st)
+            torch.cuda.synchronize()
+            _, kms = hhg.profile_end()
+            ms = sum(kms)
+            pts = info.n_faces * (info.N - 1) * (info.N - 2) // 2
+            ach = 88.0 * pts * steps / (ms / 1e3) / 1e9
+            res["face_rows_roofline"] = {
+                "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "ms_per_step": ms / steps,
+                "model": "per Uzawa step and face point: gradient rows read p, f1, f2 and write b1, b2 (40 B); "
+                         "pressure Jacobi rows read u1, u2, p, g, 1/s and write p (48 B)"}
+        out[f"L{L}"] = res
+        g.close()
+    out["workload"] = "annulus-32x4-256faces P1-P1 PSPG Stokes, all-at-once V(2,2), inexact Uzawa"
+    return out
 
 
 def vark_mesh(level, dev, st):
@@ -757,6 +826,7 @@ def run_ours(args):
     batch = None if args.no_batch else run_batch(args, dev, st)
     vark = None if args.no_vark else run_vark(args, dev, st)
     learned_res = None if args.no_learned else run_learned(args, dev, st)
+    stokes_res = None if args.no_stokes else run_stokes(args, dev, st, hbm_peak)
 
     fp64_probe = fp64_dgemm_probe(dev)
     cpu = None
@@ -795,7 +865,7 @@ def run_ours(args):
                                       "gpu_launches and the roofline kernel time come from this pass"},
             "roofline": roofline, "breakdown": breakdown, "fp32_vcycle": fp32_vcycle,
             "fp64_peak_probe": fp64_probe, "cpu_baseline": cpu, "time_to_tol": solve, "batch": batch,
-            "vark": vark, "learned": learned_res, "p2": p2res,
+            "vark": vark, "learned": learned_res, "p2": p2res, "stokes": stokes_res,
         }), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -859,9 +929,38 @@ def run_cnn_case(args):
     g.close()
 
 
+def run_stokes_case(args):
+    """--warmup untimed and --steps timed forward Uzawa steps of the Stokes
+    smoother on level --level of the 256-face annulus (every level vector above
+    the 129 MB L2 from level 9 on), with the per-class event timing of the
+    Stokes face-row kernels printed; no JSON line."""
+    import torch
+    from paper_1805_10167_gb300 import hhg, inputs
+    xy, tri = inputs.annulus_mesh(32, 4)
+    L = args.level
+    g = hhg.Mesh(xy, tri, L)
+    g.stokes_setup()
+    info = g.info(L)
+    gen = torch.Generator(device="cuda").manual_seed(1234)
+    v = [torch.rand(info.vec_len, dtype=torch.float64, device="cuda", generator=gen) for _ in range(6)]
+    g.stokes_smooth(L, *v, forward=True, steps=args.warmup)
+    torch.cuda.synchronize()
+    hhg.profile_begin(1 << hhg.K_FACE_ROWS, L)
+    g.stokes_smooth(L, *v, forward=True, steps=args.steps)
+    torch.cuda.synchronize()
+    _, kms = hhg.profile_end()
+    pts = info.n_faces * (info.N - 1) * (info.N - 2) // 2
+    ms = sum(kms)
+    print(f"stokes case done: face rows {ms / args.steps:.3f} ms per step, "
+          f"{88.0 * pts * args.steps / (ms / 1e3) / 1e9:.0f} GB/s algorithmic")
+    g.close()
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.case == "sweep":
+    if a.case == "stokes":
+        run_stokes_case(a)
+    elif a.case == "sweep":
         run_sweep_case(a)
     elif a.case == "cnn":
         run_cnn_case(a)

@@ -510,10 +510,13 @@ hhg_status hhg_p2_solve(hhg_mesh mesh, int32_t level, double* x, const double* b
  * colour-ordered Gauss-Seidel sweeps of A u_d = b_d for d = 1, 2, then
  * p += omega (B1 u1 + B2 u2 - C p - g) / s with s = diag(C + B D_A^-1 B^T)
  * (D_A^-1 on free velocity points); backward: the pressure step first, then
- * backward sweeps.  V-cycle: nu1 forward steps, residual, restriction
- * (velocity as in hhg_restrict; pressure the same with no Dirichlet point),
- * the cycle of the next coarser level from zero, prolongation and
- * correction, nu2 backward steps; on coarse_level the correction is the
+ * backward sweeps.  Variable V-cycle started on level top: on level l,
+ * nu1 + nu_growth (top - l) forward steps, residual, restriction (velocity
+ * as in hhg_restrict; pressure the same with no Dirichlet point), the cycle
+ * of the next coarser level from zero, prolongation and correction, nu2 +
+ * nu_growth (top - l) backward steps (with the same steps on every level
+ * the cycle's factor grows with the number of levels and exceeds 1 from
+ * about level 9); on coarse_level the correction is the
  * stored inverse of the dense saddle-point system applied to the residual
  * (with velocity Dirichlet conditions on the whole boundary, the constant
  * pressure is in the null space: g must sum to zero over the pressure
@@ -526,14 +529,15 @@ typedef struct {
   double omega;           /* pressure relaxation of the Uzawa step (0.4)            */
   int32_t nvel;           /* velocity Gauss-Seidel sweeps per Uzawa step (2)        */
   int32_t coarse_level;   /* the cycle's coarsest level, solved directly (0)        */
+  int32_t nu_growth;      /* extra Uzawa steps per level below the top, each side (2) */
 } hhg_stokes_opts;
 /* Builds the stencil weights, the smoother diagonals of levels above
  * coarse_level, the coarse inverse and the workspaces (levels coarse_level ..
  * max_level: 15 level vectors per level at most).  opts NULL: the defaults
  * above.  Synchronous; drops captured graphs; a second call replaces the
  * first.  HHG_ERR_ARG for delta <= 0, omega <= 0, nvel < 1, coarse_level
- * outside 0 .. max_level - 1, a coarse system over 4096 unknowns, or a
- * coefficient field; HHG_ERR_OOM. */
+ * outside 0 .. max_level - 1, nu_growth < 0, a coarse system over 4096
+ * unknowns, or a coefficient field; HHG_ERR_OOM. */
 hhg_status hhg_stokes_setup(hhg_mesh mesh, const hhg_stokes_opts* opts);
 /* (y1, y2, yp) = the system matrix times (u1, u2, p): y_d = A u_d + B_d^T p
  * on free velocity points (0 at Dirichlet points), yp = B1 u1 + B2 u2 - C p. */
@@ -549,8 +553,8 @@ hhg_status hhg_stokes_residual(hhg_mesh mesh, int32_t level, const double* u1, c
  * coarse_level. */
 hhg_status hhg_stokes_smooth(hhg_mesh mesh, int32_t level, double* u1, double* u2, double* p, const double* f1,
                              const double* f2, const double* g, int32_t forward, int32_t steps, void* stream);
-/* One V(nu1, nu2) cycle in place (level = coarse_level: the direct coarse
- * correction). */
+/* One variable V(nu1, nu2) cycle in place, started on `level` (level =
+ * coarse_level: the direct coarse correction). */
 hhg_status hhg_stokes_vcycle(hhg_mesh mesh, int32_t level, double* u1, double* u2, double* p, const double* f1,
                              const double* f2, const double* g, int32_t nu1, int32_t nu2, void* stream);
 /* V(nu1, nu2) cycles from the guess until the residual norm (as in

@@ -623,10 +623,10 @@ hhg_status hhg_stokes_setup(hhg_mesh mesh, const hhg_stokes_opts* opts) {
   HHG_ENTRY_RANGE;
   return guarded([&]() {
     hhg::Mesh& m = get(mesh);
-    hhg_stokes_opts o{0.3, 0.4, 2, 0};
+    hhg_stokes_opts o{0.3, 0.4, 2, 0, 2};
     if (opts) o = *opts;
     hhg::graphs_clear(m);
-    hhg::stokes_setup(m, o.delta, o.omega, o.nvel, o.coarse_level);
+    hhg::stokes_setup(m, o.delta, o.omega, o.nvel, o.coarse_level, o.nu_growth);
     return HHG_OK;
   });
 }

@@ -471,7 +471,7 @@ void tail_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, i
 int canonical_index(const Mesh& m, int N, int f, int i, int j);
 
 // Stokes, P1-P1 PSPG, all-at-once multigrid with the inexact Uzawa smoother (stokes.cu)
-void stokes_setup(Mesh& m, double delta, double omega, int nvel, int coarse);
+void stokes_setup(Mesh& m, double delta, double omega, int nvel, int coarse, int growth);
 void stokes_free(Mesh& m);
 void stokes_apply(const Mesh& m, int l, const double* u1, const double* u2, const double* p, double* y1, double* y2,
                   double* yp, cudaStream_t st);

@@ -22,10 +22,12 @@
 // library's P1 smoother on A u_d = b_d for d = 1, 2; then the Jacobi step
 // p <- p + omega (B1 u1 + B2 u2 - C p - g) / s, s = diag(C + B D_A^-1 B^T)
 // (D_A^-1 on free velocity points).  The backward step takes the pressure
-// first, then backward sweeps.  V-cycle: nu1 forward steps, residual,
-// restriction (velocity: the P1 restriction; pressure: the same without
-// Dirichlet rows), the coarse cycle from zero, prolongation and correction,
-// nu2 backward steps.  On the coarsest level of the cycle the correction is
+// first, then backward sweeps.  Variable V-cycle started on level top: on
+// level l, nu1 + growth (top - l) forward steps, residual, restriction
+// (velocity: the P1 restriction; pressure: the same without Dirichlet rows),
+// the coarse cycle from zero, prolongation and correction, nu2 + growth
+// (top - l) backward steps (with the same steps on every level the cycle's
+// factor grows with the number of levels).  On the coarsest level of the cycle the correction is
 // the dense saddle-point system's stored inverse applied to the residual
 // (bordered by the zero-sum pressure constraint when the constant pressure
 // is in the null space).
@@ -83,7 +85,7 @@ struct StokesLevel {
 
 struct StokesData {
   double delta = 0.3, omega = 0.4;
-  int nvel = 2, coarse = 0;
+  int nvel = 2, coarse = 0, growth = 2;
   StFace* faces = nullptr;                 // device, one per macro-face
   std::vector<StokesLevel> lv;
   int nc = 0;                              // coarse system size
@@ -218,7 +220,7 @@ __device__ __forceinline__ double pres_out(const StArgs& a, int64_t s, double y,
     acc += r * r;
     return r;
   }
-  return a.p[s] + a.omega * (y - a.g[s]) * a.sinv[s];
+  return fma(a.omega, (y - a.g[s]) * a.sinv[s], a.p[s]);
 }
 
 // Face-interior rows: one warp per face row, lanes along the row.
@@ -233,32 +235,54 @@ __global__ void __launch_bounds__(kStThreads)
   const int rows = N - 2;
   const int64_t ntask = rows > 0 ? (int64_t)M.nf * rows : 0;
   double acc = 0.0;
+  // Interior rows of B and B^T have a zero centre and antisymmetric
+  // neighbour pairs, C symmetric pairs (each micro-triangle around a point
+  // has its point reflection there too): one difference or sum per pair,
+  // then one product per weight -- 11 FP64 instructions per point for the
+  // gradient rows, 24 for the pressure rows, instead of 18 and 26.
+  const int64_t oe[3] = {1, S, 1 - S};   // +e of the pairs (1, 0) / (0, 1) / (1, -1)
   for (int64_t task = warp; task < ntask; task += nwarps) {
     const int f = face_id(M, (int)(task / rows));
     const int j = (int)(task - (task / rows) * rows) + 1;
     const StFace& F = W[f];
     const int64_t row = L.f_off + (int64_t)f * L.FS + (int64_t)j * S;
+    double w1[3], w2[3], wc[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (MODE == ST_GRAD) {
+        w1[k] = 0.5 * (F.op[ST_B1T].in[1 + 2 * k] - F.op[ST_B1T].in[2 + 2 * k]);
+        w2[k] = 0.5 * (F.op[ST_B2T].in[1 + 2 * k] - F.op[ST_B2T].in[2 + 2 * k]);
+      } else if (MODE == ST_PRES) {
+        w1[k] = 0.5 * (F.op[ST_B1].in[1 + 2 * k] - F.op[ST_B1].in[2 + 2 * k]);
+        w2[k] = 0.5 * (F.op[ST_B2].in[1 + 2 * k] - F.op[ST_B2].in[2 + 2 * k]);
+        wc[k] = 0.5 * (F.op[ST_C].in[1 + 2 * k] + F.op[ST_C].in[2 + 2 * k]);
+      }
+    }
+    const double wc0 = F.op[ST_C].in[0];
+    const double gs = a.sgn * a.sB;
     for (int i = 1 + lane; i <= N - 1 - j; i += 32) {
       const int64_t s = row + i;
       if (MODE == ST_GRAD) {
-        double t1 = 0.0, t2 = 0.0;
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-          const double x = a.p[s + kStIn[q].x + (int64_t)kStIn[q].y * S];
-          t1 += F.op[ST_B1T].in[q] * x;
-          t2 += F.op[ST_B2T].in[q] * x;
-        }
-        a.out1[s] = (a.base1 ? a.base1[s] : 0.0) + a.sgn * (a.sB * t1);
-        a.out2[s] = (a.base2 ? a.base2[s] : 0.0) + a.sgn * (a.sB * t2);
+        const double d0 = a.p[s + oe[0]] - a.p[s - oe[0]];
+        const double d1 = a.p[s + oe[1]] - a.p[s - oe[1]];
+        const double d2 = a.p[s + oe[2]] - a.p[s - oe[2]];
+        const double t1 = fma(w1[2], d2, fma(w1[1], d1, w1[0] * d0));
+        const double t2 = fma(w2[2], d2, fma(w2[1], d1, w2[0] * d0));
+        a.out1[s] = a.base1 ? fma(gs, t1, a.base1[s]) : gs * t1;
+        a.out2[s] = a.base2 ? fma(gs, t2, a.base2[s]) : gs * t2;
       } else if (MODE == ST_PRES) {
-        double y = 0.0, c = 0.0;
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-          const int64_t o = s + kStIn[q].x + (int64_t)kStIn[q].y * S;
-          y += F.op[ST_B1].in[q] * a.u1[o] + F.op[ST_B2].in[q] * a.u2[o];
-          c += F.op[ST_C].in[q] * a.p[o];
-        }
-        a.out1[s] = pres_out(a, s, a.sB * y - a.sC * c, acc);
+        double y = w1[0] * (a.u1[s + oe[0]] - a.u1[s - oe[0]]);
+        y = fma(w1[1], a.u1[s + oe[1]] - a.u1[s - oe[1]], y);
+        y = fma(w1[2], a.u1[s + oe[2]] - a.u1[s - oe[2]], y);
+        y = fma(w2[0], a.u2[s + oe[0]] - a.u2[s - oe[0]], y);
+        y = fma(w2[1], a.u2[s + oe[1]] - a.u2[s - oe[1]], y);
+        y = fma(w2[2], a.u2[s + oe[2]] - a.u2[s - oe[2]], y);
+        const double pc = a.p[s];
+        double c = wc0 * pc;
+        c = fma(wc[0], a.p[s + oe[0]] + a.p[s - oe[0]], c);
+        c = fma(wc[1], a.p[s + oe[1]] + a.p[s - oe[1]], c);
+        c = fma(wc[2], a.p[s + oe[2]] + a.p[s - oe[2]], c);
+        a.out1[s] = pres_out(a, s, fma(a.sB, y, -a.sC * c), acc);
       } else if (MODE == ST_SDIAG) {
         double v = a.sC * F.op[ST_C].in[0];
 #pragma unroll
@@ -815,8 +839,8 @@ void coarse_correct(const Mesh& m, int l, double* u1, double* u2, double* p, con
   ghost_fill(m, l, 0, p, st);
 }
 
-void vcycle_rec(const Mesh& m, int l, double* u1, double* u2, double* p, const double* f1, const double* f2,
-                const double* g, int nu1, int nu2, cudaStream_t st) {
+void vcycle_rec(const Mesh& m, int l, int top, double* u1, double* u2, double* p, const double* f1,
+                const double* f2, const double* g, int nu1, int nu2, cudaStream_t st) {
   const StokesData& D = *m.stokes;
   if (l <= D.coarse) {
     coarse_correct(m, l, u1, u2, p, f1, f2, g, st);
@@ -826,7 +850,8 @@ void vcycle_rec(const Mesh& m, int l, double* u1, double* u2, double* p, const d
   const StokesLevel& C = D.lv[l - 1];
   const size_t bytes = (size_t)m.levels[l].lv.len * sizeof(double);
   double *c1 = u1, *c2 = u2, *cp = p, *o1 = S.w1, *o2 = S.w2, *op = S.pn;
-  for (int s = 0; s < nu1; ++s) uzawa_step(m, l, c1, o1, c2, o2, cp, op, f1, f2, g, true, st);
+  const int extra = D.growth * (top - l);
+  for (int s = 0; s < nu1 + extra; ++s) uzawa_step(m, l, c1, o1, c2, o2, cp, op, f1, f2, g, true, st);
   residual_all(m, l, c1, c2, cp, f1, f2, g, S.r1, S.r2, S.rp, false, st);
   restrict_op(m, l, 0, S.r1, C.f1, st);
   restrict_op(m, l, 0, S.r2, C.f2, st);
@@ -834,11 +859,11 @@ void vcycle_rec(const Mesh& m, int l, double* u1, double* u2, double* p, const d
   zero_vec(m, l - 1, 0, C.u1, st);
   zero_vec(m, l - 1, 0, C.u2, st);
   zero_vec(m, l - 1, 0, C.p, st);
-  vcycle_rec(m, l - 1, C.u1, C.u2, C.p, C.f1, C.f2, C.g, nu1, nu2, st);
+  vcycle_rec(m, l - 1, top, C.u1, C.u2, C.p, C.f1, C.f2, C.g, nu1, nu2, st);
   prolongate_add(m, l, 0, C.u1, c1, st);
   prolongate_add(m, l, 0, C.u2, c2, st);
   prolongate_add(m, l, 0, C.p, cp, st, true);
-  for (int s = 0; s < nu2; ++s) uzawa_step(m, l, c1, o1, c2, o2, cp, op, f1, f2, g, false, st);
+  for (int s = 0; s < nu2 + extra; ++s) uzawa_step(m, l, c1, o1, c2, o2, cp, op, f1, f2, g, false, st);
   if (c1 != u1) check_cuda(cudaMemcpyAsync(u1, c1, bytes, cudaMemcpyDeviceToDevice, st), "copy u1");
   if (c2 != u2) check_cuda(cudaMemcpyAsync(u2, c2, bytes, cudaMemcpyDeviceToDevice, st), "copy u2");
   if (cp != p) check_cuda(cudaMemcpyAsync(p, cp, bytes, cudaMemcpyDeviceToDevice, st), "copy p");
@@ -859,9 +884,10 @@ void stokes_free(Mesh& m) {
   m.stokes = nullptr;
 }
 
-void stokes_setup(Mesh& m, double delta, double omega, int nvel, int coarse) {
-  if (!(delta > 0.0) || !(omega > 0.0) || nvel < 1 || coarse < 0 || coarse >= m.max_level)
-    throw std::invalid_argument("Stokes options: delta > 0, omega > 0, nvel >= 1, 0 <= coarse_level < max_level");
+void stokes_setup(Mesh& m, double delta, double omega, int nvel, int coarse, int growth) {
+  if (!(delta > 0.0) || !(omega > 0.0) || nvel < 1 || coarse < 0 || coarse >= m.max_level || growth < 0)
+    throw std::invalid_argument("Stokes options: delta > 0, omega > 0, nvel >= 1, 0 <= coarse_level < max_level, "
+                                "nu_growth >= 0");
   if (m.vark) throw std::invalid_argument("Stokes: constant coefficient k = 1 only");
   check_cuda(cudaDeviceSynchronize(), "sync");
   stokes_free(m);
@@ -872,6 +898,7 @@ void stokes_setup(Mesh& m, double delta, double omega, int nvel, int coarse) {
     D.omega = omega;
     D.nvel = nvel;
     D.coarse = coarse;
+    D.growth = growth;
     std::vector<StFace> w(m.nf);
     for (int f = 0; f < m.nf; ++f) w[f] = face_weights(m, m.h_faces[f]);
     D.faces = (StFace*)st_alloc(D, w.size() * sizeof(StFace));
@@ -962,7 +989,7 @@ void stokes_vcycle(const Mesh& m, int l, double* u1, double* u2, double* p, cons
   check_level_args(m, l);
   if (nu1 < 0 || nu2 < 0) throw std::invalid_argument("nu1, nu2 >= 0");
   fill_inputs(m, l, u1, u2, p, st);
-  vcycle_rec(m, l, u1, u2, p, f1, f2, g, nu1, nu2, st);
+  vcycle_rec(m, l, l, u1, u2, p, f1, f2, g, nu1, nu2, st);
 }
 
 void stokes_norm(const Mesh& m, int l, const double* u1, const double* u2, const double* p, const double* f1,

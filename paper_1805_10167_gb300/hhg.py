@@ -71,7 +71,8 @@ class P2Opts(C.Structure):
 
 
 class StokesOpts(C.Structure):
-    _fields_ = [("delta", C.c_double), ("omega", C.c_double), ("nvel", C.c_int32), ("coarse_level", C.c_int32)]
+    _fields_ = [("delta", C.c_double), ("omega", C.c_double), ("nvel", C.c_int32), ("coarse_level", C.c_int32),
+                ("nu_growth", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -272,8 +273,8 @@ class Mesh:
         return st, out
 
     # -------------------------------------------------------------- Stokes
-    def stokes_setup(self, delta=0.3, omega=0.4, nvel=2, coarse_level=0):
-        o = StokesOpts(delta, omega, nvel, coarse_level)
+    def stokes_setup(self, delta=0.3, omega=0.4, nvel=2, coarse_level=0, nu_growth=2):
+        o = StokesOpts(delta, omega, nvel, coarse_level, nu_growth)
         _check(lib.hhg_stokes_setup(self.h, C.byref(o)))
 
     def stokes_apply(self, level, u1, u2, p, y1, y2, yp, stream=None):
