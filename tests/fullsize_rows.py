@@ -107,3 +107,35 @@ def p2_row(xy, tri, N1, f, I, J):
             key = (p[0] - I, p[1] - J)
             w[key] = w.get(key, 0.0) + K[t, c, n]
     return w
+
+
+# ------------------------------------------------------------------ Stokes
+def stokes_row_weights(xy, tri, N, f, i, j, delta):
+    """Weights (7,) in NEIGH order of the face-interior point p = (i, j) of
+    face f for the Stokes operators of oracle.stokes, from the element
+    quantities of the six micro-triangles around p (placed relative to p):
+    B1, B2 (the pressure row of p over velocity neighbours), B1T, B2T (the
+    velocity row of p over pressure neighbours), C (delta h_T^2 stiffness,
+    h_T the longest edge) and A (the P1 stiffness).  Returns a dict."""
+    v0, v1, v2 = (np.asarray(xy[v], dtype=np.float64) for v in tri[f])
+    pts = [(i + di, j + dj) for di, dj in NEIGH]
+    local = {pt: m for m, pt in enumerate(pts)}
+    coords = np.array([((a - i) / N) * (v1 - v0) + ((b - j) / N) * (v2 - v0) for a, b in pts])
+    elems = np.array([[local[v] for v in tri_vertices(kind, i + da, j + db)] for kind, da, db in PATCH])
+    patch = SimpleNamespace(coords=coords, elements=elems)
+    area, G = fem.element_geometry(patch)
+    X = coords[elems]
+    e = np.stack([X[:, 1] - X[:, 0], X[:, 2] - X[:, 1], X[:, 0] - X[:, 2]], axis=1)
+    h2 = (e ** 2).sum(axis=-1).max(axis=-1)
+    K = fem.element_stiffness(patch)
+    out = {k: np.zeros(7) for k in ("B1", "B2", "B1T", "B2T", "C", "A")}
+    for t in range(6):
+        c = int(np.where(elems[t] == 0)[0][0])
+        for n in range(3):
+            m = elems[t, n]
+            for d, name in ((0, "1"), (1, "2")):
+                out["B" + name][m] += -(area[t] / 3.0) * G[t, d, n]
+                out["B" + name + "T"][m] += -(area[t] / 3.0) * G[t, d, c]
+            out["C"][m] += delta * h2[t] * K[t, c, n]
+            out["A"][m] += K[t, c, n]
+    return out

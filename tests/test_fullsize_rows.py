@@ -77,3 +77,35 @@ def test_p2_rows_equal_assembled_matrix(name, L):
                 for q, v in zip(row.indices, row.data):
                     assert abs(got.pop(q, 0.0) - v) <= 1e-12 * abs(row.data).max()
                 assert all(abs(v) <= 1e-12 * abs(row.data).max() for v in got.values())
+
+
+@pytest.mark.parametrize("name", ["annulus", "random"])
+def test_stokes_rows_equal_assembled_operators(name):
+    """The one-row Stokes helper equals the rows of the oracle's assembled
+    B1, B2, their transposes, C and A at every face-interior point of a small
+    level."""
+    from oracle import stokes
+    xy, tri = inputs.annulus_mesh(32, 4) if name == "annulus" else inputs.random_square_mesh(5, 12)
+    M = om.MacroMesh(xy, tri)
+    L, delta = 3, 0.3
+    lv = om.Level(M, L)
+    N = lv.N
+    B1, B2 = stokes.div_matrices(lv)
+    mats = {"B1": B1, "B2": B2, "B1T": B1.T.tocsr(), "B2T": B2.T.tocsr(),
+            "C": stokes.stabilisation(lv, delta), "A": fem.assemble(lv)}
+    dense = {k: v.toarray() for k, v in mats.items()}
+    worst = 0.0
+    for f in range(M.nf):
+        G = lv.face_ids[f]
+        for j in range(1, N - 1):
+            for i in range(1, N - j):
+                w = fr.stokes_row_weights(M.xy, M.tri, N, f, i, j, delta)
+                ids = [G[j + dj, i + di] for di, dj in fr.NEIGH]
+                for k, D in dense.items():
+                    row = D[G[j, i]]
+                    scale = np.abs(row).max()
+                    worst = max(worst, np.abs(row[ids] - w[k]).max() / scale)
+                    # nothing outside the 7-point stencil
+                    rest = np.delete(row, ids)
+                    assert np.abs(rest).max(initial=0.0) <= 1e-14 * scale
+    assert worst <= 1e-13
