@@ -225,11 +225,11 @@ __device__ __forceinline__ double pres_out(const StArgs& a, int64_t s, double y,
 
 // Face-interior rows: one warp per face row, lanes along the row.
 template <int MODE>
-__global__ void __launch_bounds__(kStThreads)
-    k_st_face(MeshTables M, LevelView L, const StFace* __restrict__ W, StArgs a) {
+__device__ __forceinline__ void st_face(const MeshTables& M, const LevelView& L, const StFace* __restrict__ W,
+                                        const StArgs& a, int bid, int nblk) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t warp = (bid * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)nblk * blockDim.x) >> 5;
   const int N = L.N;
   const int64_t S = L.S;
   const int rows = N - 2;
@@ -298,19 +298,18 @@ __global__ void __launch_bounds__(kStThreads)
   }
   if (MODE == ST_PRES && a.pm == SP_RES) {
     const double t = st_block_sum(acc);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = t;
+    if (threadIdx.x == 0) a.partials[bid] = t;
   }
 }
 
 // Macro-edge rows: one thread per edge point (e, t), t = 1 .. N - 1.
 template <int MODE>
-__global__ void __launch_bounds__(kStThreads)
-    k_st_edge(MeshTables M, LevelView L, const StFace* __restrict__ W, StArgs a) {
+__device__ __forceinline__ void st_edge(const MeshTables& M, const LevelView& L, const StFace* __restrict__ W,
+                                        const StArgs& a, int bid, int nblk) {
   const int N = L.N;
   const int64_t total = N >= 2 ? (int64_t)M.ne * (N - 1) : 0;
   double acc = 0.0;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t idx = bid * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)nblk * blockDim.x) {
     const int e = (int)(idx / (N - 1));
     const int t = (int)(idx - (int64_t)e * (N - 1)) + 1;
     const EdgeRec E = M.edges[e];
@@ -384,17 +383,17 @@ __global__ void __launch_bounds__(kStThreads)
   }
   if (MODE == ST_PRES && a.pm == SP_RES) {
     const double t = st_block_sum(acc);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = t;
+    if (threadIdx.x == 0) a.partials[bid] = t;
   }
 }
 
 // Macro-vertex rows: one thread per vertex.
 template <int MODE>
-__global__ void __launch_bounds__(kStThreads)
-    k_st_vertex(MeshTables M, LevelView L, const StFace* __restrict__ W, StArgs a) {
+__device__ __forceinline__ void st_vertex(const MeshTables& M, const LevelView& L, const StFace* __restrict__ W,
+                                          const StArgs& a, int bid, int nblk) {
   const int N = L.N;
   double acc = 0.0;
-  for (int vi = blockIdx.x * blockDim.x + threadIdx.x; vi < M.nv; vi += gridDim.x * blockDim.x) {
+  for (int vi = bid * blockDim.x + threadIdx.x; vi < M.nv; vi += nblk * blockDim.x) {
     const VertRec V = M.verts[vi];
     const int64_t s = L.v_off + vi;
     const bool velocity_row = MODE == ST_GRAD || MODE == ST_DINV;
@@ -474,7 +473,27 @@ __global__ void __launch_bounds__(kStThreads)
   }
   if (MODE == ST_PRES && a.pm == SP_RES) {
     const double t = st_block_sum(acc);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = t;
+    if (threadIdx.x == 0) a.partials[bid] = t;
+  }
+}
+
+// One launch for every row kind of a mode: blocks [0, bv) take the macro-
+// vertices, [bv, bv + be) the macro-edge points, the rest the face rows
+// (partial sums, where written, in that block order).
+template <int MODE>
+__global__ void __launch_bounds__(kStThreads, 4)
+    k_st_rows(MeshTables M, LevelView L, const StFace* __restrict__ W, StArgs a, int bv, int be) {
+  const int b = blockIdx.x;
+  if (b < bv) {
+    st_vertex<MODE>(M, L, W, a, b, bv);
+  } else if (b < bv + be) {
+    StArgs ae = a;
+    if (ae.partials) ae.partials += bv;
+    st_edge<MODE>(M, L, W, ae, b - bv, be);
+  } else {
+    StArgs af = a;
+    if (af.partials) af.partials += bv + be;
+    st_face<MODE>(M, L, W, af, b - bv - be, (int)gridDim.x - bv - be);
   }
 }
 
@@ -558,20 +577,8 @@ int st_rows(const Mesh& m, int l, StArgs a, cudaStream_t st) {
   const int be = st_blocks(ne_pts, kStThreads, 1024);
   const int64_t ftask = L.N >= 3 ? (int64_t)m.nf * (L.N - 2) : 0;
   const int bf = st_blocks(ftask * 32, kStThreads, 2432);
-  double* part = a.partials;
-  StArgs av = a, ae = a, af = a;
-  if (part) {
-    ae.partials = part + bv;
-    af.partials = part + bv + be;
-  }
-  HHG_LAUNCH(HHG_K_EDGE_VERTEX, l, st, "stokes vertex rows",
-             k_st_vertex<MODE><<<bv, kStThreads, 0, st>>>(m.tab, L, D.faces, av));
-  if (ne_pts > 0 || part)
-    HHG_LAUNCH(HHG_K_EDGE_VERTEX, l, st, "stokes edge rows",
-               k_st_edge<MODE><<<be, kStThreads, 0, st>>>(m.tab, L, D.faces, ae));
-  if (ftask > 0 || part)
-    HHG_LAUNCH(HHG_K_FACE_ROWS, l, st, "stokes face rows",
-               k_st_face<MODE><<<bf, kStThreads, 0, st>>>(m.tab, L, D.faces, af));
+  HHG_LAUNCH(HHG_K_FACE_ROWS, l, st, "stokes rows",
+             k_st_rows<MODE><<<bv + be + bf, kStThreads, 0, st>>>(m.tab, L, D.faces, a, bv, be));
   return bv + be + bf;
 }
 

@@ -56,10 +56,10 @@ class StokesPair:
 def pairs():
     cache = {}
 
-    def get(name, L, coarse=0):
-        if (name, L, coarse) not in cache:
-            cache[(name, L, coarse)] = StokesPair(name, L, coarse)
-        return cache[(name, L, coarse)]
+    def get(name, L, coarse=0, nvel=2):
+        if (name, L, coarse, nvel) not in cache:
+            cache[(name, L, coarse, nvel)] = StokesPair(name, L, coarse, nvel=nvel)
+        return cache[(name, L, coarse, nvel)]
     yield get
     for p in cache.values():
         p.g.close()
@@ -97,9 +97,9 @@ def test_stokes_pressure_scaling_parity(pairs, name, L):
         assert rel_err(P.from_dev(l, s), 1.0 / P.S.s[l]) <= FP64_TOL, l
 
 
-@pytest.mark.parametrize("name,L", CASES)
-def test_stokes_uzawa_steps_parity(pairs, name, L):
-    P = pairs(name, L)
+@pytest.mark.parametrize("name,L,nvel", [c + (2,) for c in CASES] + [("annulus", 3, 1), ("random5", 3, 3)])
+def test_stokes_uzawa_steps_parity(pairs, name, L, nvel):
+    P = pairs(name, L, nvel=nvel)
     f1, f2, g = P.rhs(L)
     fd = [P.to_dev(L, v) for v in (f1, f2, g)]
     for forward in (True, False):
@@ -116,9 +116,9 @@ def test_stokes_uzawa_steps_parity(pairs, name, L):
             assert rel_err(P.from_dev(L, got), want) <= FP64_TOL, forward
 
 
-@pytest.mark.parametrize("name,L", CASES)
-def test_stokes_vcycle_parity(pairs, name, L):
-    P = pairs(name, L)
+@pytest.mark.parametrize("name,L,nvel", [c + (2,) for c in CASES] + [("square", 4, 1)])
+def test_stokes_vcycle_parity(pairs, name, L, nvel):
+    P = pairs(name, L, nvel=nvel)
     f1, f2, g = P.rhs(L)
     lv = P.S.levels[L]
     u1, u2, p = (P.rng.standard_normal(lv.n) for _ in range(3))
