@@ -749,38 +749,42 @@ def run_ours(args):
     nrm_host = torch.zeros(1, dtype=torch.float64).pin_memory()
     x_hosts = [torch.empty(info.n_nodes, dtype=torch.float64).pin_memory() for _ in range(2)]
     x.zero_()
-    # Two staging vectors per direction and two copy streams: the host->device
-    # copy of step k + 1's right-hand side and the device->host copy of step
-    # k - 1's iterate run while step k computes.  Step k waits for its own
-    # upload; a staging vector is reused only after the copy that read it.
+    # Two staging vectors per direction, two device right-hand sides and two
+    # copy streams: the host->device copy of step k + 1's right-hand side and
+    # its conversion to the internal layout (into the right-hand side step k
+    # does not read), and the device->host copy of step k - 1's iterate, run
+    # while step k computes.  A buffer is reused only after the step or copy
+    # that last read it.
     up_st = torch.cuda.Stream(device=dev)
     down_st = torch.cuda.Stream(device=dev)
     stages = [torch.empty_like(b_canon), torch.empty_like(b_canon)]
     xstages = [torch.empty_like(b_canon), torch.empty_like(b_canon)]
-    copied = [torch.cuda.Event(), torch.cuda.Event()]
-    consumed = [torch.cuda.Event(), torch.cuda.Event()]
+    bdev = [b, torch.zeros_like(b)]
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    freed = [torch.cuda.Event(), torch.cuda.Event()]
     produced = [torch.cuda.Event(), torch.cuda.Event()]
     downloaded = [torch.cuda.Event(), torch.cuda.Event()]
 
     def upload(k):
         s = k % 2
-        up_st.wait_event(consumed[s])
+        up_st.wait_event(freed[s])
         with torch.cuda.stream(up_st):
             stages[s].copy_(b_host, non_blocking=True)
-        copied[s].record(up_st)
+        g.from_canonical(L, stages[s], bdev[s], stream=up_st)
+        ready[s].record(up_st)
 
     def e2e_steps(n):
-        for ev in consumed + downloaded:
+        for ev in freed + downloaded:
             ev.record(st)
         upload(0)
         for k in range(n):
             if k + 1 < n:
                 upload(k + 1)
             s = k % 2
-            st.wait_event(copied[s])
-            g.from_canonical(L, stages[s], b, stream=st)
-            consumed[s].record(st)
-            step()
+            st.wait_event(ready[s])
+            g.vcycle(L, x, bdev[s], nu1=3, nu2=3, stream=st)
+            g.residual(L, x, bdev[s], r, nrm, stream=st)
+            freed[s].record(st)
             nrm_host.copy_(nrm, non_blocking=True)
             st.wait_event(downloaded[s])
             g.to_canonical(L, x, xstages[s], stream=st)
@@ -790,8 +794,9 @@ def run_ours(args):
                 x_hosts[s].copy_(xstages[s], non_blocking=True)
             downloaded[s].record(down_st)
         st.wait_stream(down_st)
+        st.wait_stream(up_st)
 
-    e2e_steps(args.warmup)
+    e2e_steps(max(args.warmup, 6))    # each device right-hand side's cycle graph is captured on its third use
     torch.cuda.synchronize()
     barrier()
     e0.record(st)
@@ -804,11 +809,11 @@ def run_ours(args):
            "h2d_bytes_per_step": int(b_host.numel() * 8),
            "d2h_bytes_per_step": int(info.n_nodes * 8 + 8),
            "ms_per_step": ms_e2e / args.steps,
-           "pipeline": "each step: pinned host b -> device (copy stream, overlapping the previous "
-                       "step), canonical -> internal layout, V(3,3), residual norm -> pinned host, "
-                       "iterate x -> canonical order -> pinned host (second copy stream, overlapping "
-                       "the next step)"}
-    del x_hosts, xstages, stages
+           "pipeline": "each step: pinned host b -> device and canonical -> internal layout (copy "
+                       "stream, into the second device right-hand side, overlapping the previous step), "
+                       "V(3,3), residual norm -> pinned host, iterate x -> canonical order -> pinned host "
+                       "(second copy stream, overlapping the next step)"}
+    del x_hosts, xstages, stages, bdev
 
     # time to a 1e-10 relative FP64 residual: FP64 MG vs FP32-in-FP64 IR
     solve = None
