@@ -91,7 +91,9 @@ constexpr int kPS = 24;                               // BF16 slots per point in
 constexpr int kF1 = 0, kF2 = 3 * 2 * 2 * 32, kF3 = kF2 + 9 * 2 * 2 * 32;
 constexpr int kFU = kF3 + 9 * 2 * 32;                 // tcgen05 layer-2 operand, 9 x 128 words
 constexpr int kF4 = kFU + 9 * 128;                    // layer 3 with the taps as GEMM columns
-constexpr int kFrag = kF4 + 2 * 2 * 32;               // packed weights (uint32)
+constexpr int kF1E = kF4 + 2 * 2 * 32;                // layer 1, tap rows as k-steps, even window origin
+constexpr int kF1O = kF1E + 3 * 2 * 2 * 32;           // the same for odd origins (window from origin - 1)
+constexpr int kFrag = kF1O + 3 * 2 * 2 * 32;          // packed weights (uint32)
 static_assert(kFU % 4 == 0, "the tcgen05 operand is copied as 16-byte words");
 constexpr long kUmmaPolls = 1L << 22;                 // mbarrier polls before a product is given up
 
@@ -144,7 +146,7 @@ static_assert(TI % 16 == 0, "output rows are whole chunks");
 template <int NC, int QS, int P1>
 __device__ __forceinline__ void cnn_layer1(const int (&chunk)[NC], const uint32_t* X, uint32_t* h1w,
                                            const uint32_t (&bf)[3][2][2], const float (&bias)[2][2], int i0,
-                                           int j0, int N, int g, int tq) {
+                                           int j0, int N, int g, int tq, bool full) {
   int pa[NC], pb[NC];
   float d[NC][2][4];
 #pragma unroll
@@ -181,8 +183,11 @@ __device__ __forceinline__ void cnn_layer1(const int (&chunk)[NC], const uint32_
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int q = chunk[u] * 16 + g + 8 * h;
-      const int jj = q / I1, ii = q - jj * I1;
-      const bool in = closed_pt(i0 - 2 + ii, j0 - 2 + jj, N);
+      bool in = true;
+      if (!full) {   // a tile whose regions all lie in the closed triangle needs no mask
+        const int jj = q / I1, ii = q - jj * I1;
+        in = closed_pt(i0 - 2 + ii, j0 - 2 + jj, N);
+      }
       h1w[q * QS + tq] = relu_pack(d[u][0][2 * h], d[u][0][2 * h + 1], in);
       h1w[P1 + q * QS + tq] = relu_pack(d[u][1][2 * h], d[u][1][2 * h + 1], in);
     }
@@ -194,7 +199,7 @@ template <int NC, int NP2_ = NP2>
 __device__ __forceinline__ void cnn_layer2(const int (&chunk)[NC], __nv_bfloat16 (*h1)[kPS],
                                            __nv_bfloat16 (*h2)[kPS], const uint32_t (&bf)[9][2][2],
                                            const float (&bias)[2][2], int i0, int j0, int N, int g, int tq,
-                                           int lrow, int lhalf) {
+                                           int lrow, int lhalf, bool full) {
   int pr[NC];
   float d[NC][2][4];
 #pragma unroll
@@ -223,8 +228,11 @@ __device__ __forceinline__ void cnn_layer2(const int (&chunk)[NC], __nv_bfloat16
     for (int h = 0; h < 2; ++h) {
       const int q = chunk[u] * 16 + g + 8 * h;
       if (q < NP2_) {
-        const int jj = q / I2, ii = q - jj * I2;
-        const bool in = closed_pt(i0 - 1 + ii, j0 - 1 + jj, N);
+        bool in = true;
+        if (!full) {
+          const int jj = q / I2, ii = q - jj * I2;
+          in = closed_pt(i0 - 1 + ii, j0 - 1 + jj, N);
+        }
         uint32_t* row = reinterpret_cast<uint32_t*>(&h2[q][0]);
         row[tq] = relu_pack(d[u][0][2 * h], d[u][0][2 * h + 1], in);
         row[tq + 4] = relu_pack(d[u][1][2 * h], d[u][1][2 * h + 1], in);
@@ -290,9 +298,63 @@ __device__ __forceinline__ void cnn_layer3(const int (&chunk)[NC], __nv_bfloat16
 constexpr int BJ = 16;                                    // output rows per tile
 constexpr int BJ0 = BJ + 6, BJ1 = BJ + 4, BJ2 = BJ + 2;
 constexpr int BP0 = BJ0 * I0, BP1 = BJ1 * I1, BP2 = BJ2 * I2, BP3 = BJ * TI;
-constexpr int kBigSmem = BP0 * 8 + (BP1 + BP2) * kPS * 2;  // bytes of dynamic shared memory
+constexpr int kXinPts = BP0 + 8;                          // input region and a zero pad (16-byte multiple)
+constexpr int kBigSmem = kXinPts * 8 + (BP1 + BP2) * kPS * 2;  // bytes of dynamic shared memory
 static_assert(BP1 % 16 == 0, "layer-1 region is a whole number of 16-point chunks");
 static_assert(BP2 * 9 * 4 <= BP1 * kPS * 2, "the layer-3 tap products fit where h1 was");
+
+// Layer 1 (3 -> 16) of the default kernel on a pair of chunks: 16 points of
+// the h1 region with even index q (chunk cc: q = 32 cc + 2 row) and the 16 with
+// odd q, so that every A row starts at an input window origin of one parity.
+// k-step dj is tap row dj: the row's 16 BF16 (four input points x four
+// channels) are 32 contiguous bytes of the input region, read by ldmatrix
+// from the origin (even) or from one point before it (odd; its fragments
+// shift the weights by one tap).  Rows past the region repeat the last point
+// of their parity and are not stored.  xb: the input region as bytes (one
+// zero point after it: the fourth point of the last windows).
+__device__ __forceinline__ void cnn_layer1_pair(int cc, const unsigned char* xb, uint32_t* h1w,
+                                                const uint32_t (&bfe)[3][2][2], const uint32_t (&bfo)[3][2][2],
+                                                const float (&bias)[2][2], int i0, int j0, int N, int g, int tq,
+                                                int lrow, int lhalf, bool full) {
+  float d[2][2][4];
+  int a0[2];
+#pragma unroll
+  for (int par = 0; par < 2; ++par) {
+    const int qr = min(par + 2 * (cc * 16 + lrow), BP1 - 2 + par);
+    const int jr = qr / I1;
+    a0[par] = (jr * I0 + (qr - jr * I1) - par) * 8 + lhalf * 2;   // 16-byte aligned (I0 even)
+#pragma unroll
+    for (int nb = 0; nb < 2; ++nb) {
+      d[par][nb][0] = d[par][nb][2] = bias[nb][0];
+      d[par][nb][1] = d[par][nb][3] = bias[nb][1];
+    }
+  }
+#pragma unroll
+  for (int dj = 0; dj < 3; ++dj) {
+    uint32_t ae[4], ao[4];
+    ldsm_x4(ae, xb + a0[0] + dj * I0 * 8);
+    ldsm_x4(ao, xb + a0[1] + dj * I0 * 8);
+    mma_bf16(d[0][0], ae, bfe[dj][0][0], bfe[dj][0][1]);
+    mma_bf16(d[0][1], ae, bfe[dj][1][0], bfe[dj][1][1]);
+    mma_bf16(d[1][0], ao, bfo[dj][0][0], bfo[dj][0][1]);
+    mma_bf16(d[1][1], ao, bfo[dj][1][0], bfo[dj][1][1]);
+  }
+#pragma unroll
+  for (int par = 0; par < 2; ++par)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = par + 2 * (cc * 16 + g + 8 * h);
+      if (q < BP1) {
+        bool in = true;
+        if (!full) {
+          const int jj = q / I1, ii = q - jj * I1;
+          in = closed_pt(i0 - 2 + ii, j0 - 2 + jj, N);
+        }
+        h1w[q * (kPS / 2) + tq] = relu_pack(d[par][0][2 * h], d[par][0][2 * h + 1], in);
+        h1w[4 + q * (kPS / 2) + tq] = relu_pack(d[par][1][2 * h], d[par][1][2 * h + 1], in);
+      }
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256, 3)
@@ -301,9 +363,9 @@ __global__ void __launch_bounds__(256, 3)
                  const float* __restrict__ wr, T* x, float* delta) {
   extern __shared__ __align__(128) unsigned char cnn_smem[];
   uint2* xin = reinterpret_cast<uint2*>(cnn_smem);                           // 4 BF16 channels per point
-  __nv_bfloat16(*h1)[kPS] = reinterpret_cast<__nv_bfloat16(*)[kPS]>(cnn_smem + BP0 * 8);
+  __nv_bfloat16(*h1)[kPS] = reinterpret_cast<__nv_bfloat16(*)[kPS]>(cnn_smem + kXinPts * 8);
   __nv_bfloat16(*h2)[kPS] = h1 + BP1;
-  float* Dt = reinterpret_cast<float*>(cnn_smem + BP0 * 8);                 // after layer 2: D[t][q]
+  float* Dt = reinterpret_cast<float*>(cnn_smem + kXinPts * 8);             // after layer 2: D[t][q]
   const int f = blockIdx.z;
   const int i0 = blockIdx.x * TI, j0 = blockIdx.y * BJ;
   const int N = L.N;
@@ -315,12 +377,15 @@ __global__ void __launch_bounds__(256, 3)
   const uint32_t* lk = logk ? logk + (int64_t)f * L.FS : nullptr;
   const int tid = threadIdx.x;
   constexpr int NT = 256;
+  // every point of the input region in the closed triangle (then every
+  // output point is interior): no masks in the staging and the epilogues
+  const bool full = i0 >= 3 && j0 >= 3 && (i0 + TI + 2) + (j0 + BJ + 2) <= N;
   for (int q = tid; q < BP0; q += NT) {
     const int jj = q / I0, ii = q - jj * I0;
     const int i = i0 - 3 + ii, j = j0 - 3 + jj;
     float a = 0.f;
     uint32_t kk = 0u;
-    if (closed_pt(i, j, N)) {
+    if (full || closed_pt(i, j, N)) {
       const int64_t p = (int64_t)j * S + i;
       a = s[fb + p] * isig;
       if (lk) kk = lk[p];
@@ -328,27 +393,30 @@ __global__ void __launch_bounds__(256, 3)
     // channels (residual, log k up | log k down, 0)
     xin[q] = make_uint2((pack_bf16(a, 0.f) & 0xffffu) | (kk << 16), kk >> 16);
   }
+  if (tid < kXinPts - BP0) xin[BP0 + tid] = make_uint2(0u, 0u);
   const int lane = tid & 31, warp = tid >> 5;
   constexpr int NW = NT / 32;
   const int g = lane >> 2, tq = lane & 3;
   // ldmatrix row of this lane: point offset in a chunk and channel half
   const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lhalf = (lane >> 4) * 8;
   {
-    uint32_t bf[3][2][2];
+    uint32_t bfe[3][2][2], bfo[3][2][2];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) bf[k][nb][h] = frag[kF1 + ((k * 2 + nb) * 2 + h) * 32 + lane];
+        for (int h = 0; h < 2; ++h) {
+          bfe[k][nb][h] = frag[kF1E + ((k * 2 + nb) * 2 + h) * 32 + lane];
+          bfo[k][nb][h] = frag[kF1O + ((k * 2 + nb) * 2 + h) * 32 + lane];
+        }
     const float bias[2][2] = {{wr[ob1 + 2 * tq], wr[ob1 + 2 * tq + 1]}, {wr[ob1 + 8 + 2 * tq], wr[ob1 + 9 + 2 * tq]}};
-    const uint32_t* X = reinterpret_cast<const uint32_t*>(xin);
+    const unsigned char* xb = cnn_smem;
     uint32_t* h1w = reinterpret_cast<uint32_t*>(&h1[0][0]);
     __syncthreads();
-    int c = warp;
-    for (; c + NW < BP1 / 16; c += 2 * NW)
-      cnn_layer1<2, kPS / 2, 4>({c, c + NW}, X, h1w, bf, bias, i0, j0, N, g, tq);
-    if (c < BP1 / 16) cnn_layer1<1, kPS / 2, 4>({c}, X, h1w, bf, bias, i0, j0, N, g, tq);
+    constexpr int NCP = (BP1 / 2 + 15) / 16;   // chunks per parity
+    for (int cc = warp; cc < NCP; cc += NW)
+      cnn_layer1_pair(cc, xb, h1w, bfe, bfo, bias, i0, j0, N, g, tq, lrow, lhalf, full);
   }
   constexpr int NC2 = (BP2 + 15) / 16;
   {
@@ -363,8 +431,8 @@ __global__ void __launch_bounds__(256, 3)
     __syncthreads();
     int c = warp;
     for (; c + NW < NC2; c += 2 * NW)
-      cnn_layer2<2, BP2>({c, c + NW}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
-    if (c < NC2) cnn_layer2<1, BP2>({c}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf);
+      cnn_layer2<2, BP2>({c, c + NW}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf, full);
+    if (c < NC2) cnn_layer2<1, BP2>({c}, h1, h2, bf, bias, i0, j0, N, g, tq, lrow, lhalf, full);
   }
   {
     uint32_t bf[2][2];
@@ -397,7 +465,7 @@ __global__ void __launch_bounds__(256, 3)
   for (int o = tid; o < BP3; o += NT) {
     const int ty = o / TI, tx = o - ty * TI;
     const int i = i0 + tx, j = j0 + ty;
-    if (!interior_pt(i, j, N)) continue;
+    if (!full && !interior_pt(i, j, N)) continue;
     float acc = b3;
 #pragma unroll
     for (int t = 0; t < 9; ++t) acc += Dt[t * BP2 + (ty + t / 3) * I2 + tx + t % 3];
@@ -513,8 +581,8 @@ __global__ void __launch_bounds__(256, 3)
       uint32_t* h1w = reinterpret_cast<uint32_t*>(&h1p[0][0]);
       int c = warp;
       for (; c + NW < BP1 / 16; c += 2 * NW)
-        cnn_layer1<2, 4, NP1Q * 4>({c, c + NW}, X, h1w, bf1, bias1, i0, j0, N, g, tq);
-      if (c < BP1 / 16) cnn_layer1<1, 4, NP1Q * 4>({c}, X, h1w, bf1, bias1, i0, j0, N, g, tq);
+        cnn_layer1<2, 4, NP1Q * 4>({c, c + NW}, X, h1w, bf1, bias1, i0, j0, N, g, tq, false);
+      if (c < BP1 / 16) cnn_layer1<1, 4, NP1Q * 4>({c}, X, h1w, bf1, bias1, i0, j0, N, g, tq, false);
     }
     // layer 2 (tcgen05): the generic-proxy writes of h1 are made visible to
     // the tensor cores, one thread issues the 54 products and commits them
@@ -684,13 +752,20 @@ __global__ void k_pack_frags(const float* __restrict__ wr, uint32_t* frag) {
     const int w = e - kFU, t = w >> 7, el = 2 * (w & 127);
     lo = w2_core(wr, t, el);
     hi = w2_core(wr, t, el + 1);
-  } else {   // layer 3, taps as columns: n = nb * 8 + g is tap n (< 9), k = input channel
+  } else if (e < kF1E) {   // layer 3, taps as columns: n = nb * 8 + g is tap n (< 9), k = input channel
     const int r = (e - kF4) >> 5, h = r & 1, nb = r >> 1;
     const int t = nb * 8 + g, c = 2 * tq + 8 * h;
     if (t < 9) {
       lo = wr[oW3 + c * 9 + t];
       hi = wr[oW3 + (c + 1) * 9 + t];
     }
+  } else {   // layer 1 with k-step = tap row dj, k = 4 di' + c over four points of the row
+    const bool odd = e >= kF1O;
+    const int r = (e - (odd ? kF1O : kF1E)) >> 5, h = r & 1, nb = (r >> 1) & 1, dj = r >> 2;
+    const int o = nb * 8 + g, kk = 2 * tq + 8 * h;
+    const int di = (kk >> 2) - (odd ? 1 : 0), c = kk & 3;   // an odd origin's window starts one point early
+    if (di >= 0 && di < 3 && c < 3) lo = wr[oW1 + o * 27 + c * 9 + 3 * dj + di];
+    if (di >= 0 && di < 3 && c + 1 < 3) hi = wr[oW1 + o * 27 + (c + 1) * 9 + 3 * dj + di];
   }
   frag[e] = pack_bf16(lo, hi);
 }
