@@ -416,6 +416,21 @@ def run_stokes(args, dev, st, hbm_peak, n_sm, sm_mhz):
                "factor_per_cycle": (rep["r_final"] / rep["r0"]) ** (1.0 / max(1, rep["iterations"])),
                "ms_per_cycle": 1e3 * dt / max(1, rep["iterations"]),
                "gdofs_per_cycle": dofs * rep["iterations"] / dt / 1e9}
+        # FP32 variable V-cycles inside FP64 iterative refinement, same tolerance
+        for v in u:
+            v.zero_()
+        g.stokes_solve_ir(L, *u, *rhs, tol=1e-8, max_iter=200, stream=st)   # warm-up: buffers, graph capture
+        for v in u:
+            v.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep32 = g.stokes_solve_ir(L, *u, *rhs, tol=1e-8, max_iter=200, stream=st)
+        torch.cuda.synchronize()
+        dt32 = time.perf_counter() - t0
+        res["fp32_ir"] = {"seconds_to_1e-8": dt32, "steps": rep32["iterations"],
+                          "rel_residual": rep32["r_final"] / rep32["r0"],
+                          "ms_per_step": 1e3 * dt32 / max(1, rep32["iterations"]),
+                          "speedup_vs_fp64": dt / dt32}
         if L == 9:
             steps = 8
             g.stokes_smooth(L, *u, *rhs, forward=True, steps=2, stream=st)

@@ -565,6 +565,17 @@ hhg_status hhg_stokes_vcycle(hhg_mesh mesh, int32_t level, double* u1, double* u
 hhg_status hhg_stokes_solve(hhg_mesh mesh, int32_t level, double* u1, double* u2, double* p, const double* f1,
                             const double* f2, const double* g, int32_t nu1, int32_t nu2, double tol,
                             int32_t max_iter, hhg_solve_report* rep, void* stream);
+/* Mixed precision, as for HHG_SOLVE_IR: the residual of (u1, u2, p), its
+ * norm and the update stay FP64; each refinement step narrows the residual
+ * to FP32, runs one FP32 variable V(nu1, nu2) cycle on it from zero (the
+ * same cycle in FP32 arithmetic, with the FP64 coarse inverse applied to the
+ * FP32 residual) and adds the correction.  Stops when the FP64 residual norm
+ * is at most tol times the initial one.  The first call makes the FP32 level
+ * vectors (synchronous, allocates once).  Replays, errors and rep as for
+ * hhg_stokes_solve. */
+hhg_status hhg_stokes_solve_ir(hhg_mesh mesh, int32_t level, double* u1, double* u2, double* p, const double* f1,
+                               const double* f2, const double* g, int32_t nu1, int32_t nu2, double tol,
+                               int32_t max_iter, hhg_solve_report* rep, void* stream);
 /* 1 / s (the Uzawa step's pressure scaling) on every pressure owner slot of a
  * level above coarse_level, into s_out (a level vector; other slots 0). */
 hhg_status hhg_stokes_diag(hhg_mesh mesh, int32_t level, double* s_out, void* stream);

@@ -732,6 +732,61 @@ hhg_status hhg_stokes_solve(hhg_mesh mesh, int32_t level, double* u1, double* u2
   });
 }
 
+hhg_status hhg_stokes_solve_ir(hhg_mesh mesh, int32_t level, double* u1, double* u2, double* p, const double* f1,
+                            const double* f2, const double* g, int32_t nu1, int32_t nu2, double tol,
+                            int32_t max_iter, hhg_solve_report* rep, void* stream) {
+  HHG_ENTRY_RANGE;
+  return guarded([&]() {
+    hhg::Mesh& m = get(mesh);
+    stokes_vec_args(m, level, {{u1, "u1"}, {u2, "u2"}, {p, "p"}, {f1, "f1"}, {f2, "f2"}, {g, "g"}});
+    if (nu1 < 0 || nu2 < 0 || max_iter < 0 || !(tol >= 0.0)) throw ArgError("bad nu1, nu2, max_iter or tol");
+    if (level <= hhg::stokes_coarse_level(m)) throw ArgError("Stokes solve: level must be above coarse_level");
+    cudaStream_t st = S(stream);
+    double* nrm = m.scalars + 8;
+    hhg::stokes_ir_prepare(m);   // synchronous, before any capture
+    hhg::stokes_norm(m, level, u1, u2, p, f1, f2, g, nrm, st);
+    const double r0 = read_scalar(nrm, st);
+    double rn = r0;
+    int it = 0;
+    hhg_status status = std::isfinite(r0) ? HHG_OK : HHG_ERR_NAN;
+    auto record = [&](int k, double v) {
+      if (rep && rep->history && k < rep->history_cap) rep->history[k] = v;
+    };
+    record(0, r0);
+    while (status == HHG_OK && rn > tol * r0 && r0 > 0.0) {
+      if (it >= max_iter) {
+        status = HHG_ERR_NOT_CONVERGED;
+        break;
+      }
+      const hhg::GraphKey key{(9ull << 56) | ((uint64_t)level << 48) | ((uint64_t)nu1 << 24) | (uint64_t)nu2,
+                              hhg::key_ptr(u1), hhg::key_ptr(u2), hhg::key_ptr(p), hhg::key_ptr(f1),
+                              hhg::key_ptr(f2), hhg::key_ptr(g), 0};
+      hhg::graphed(m, key, st, [&](cudaStream_t s) {
+        hhg::stokes_ir_step(m, level, u1, u2, p, nu1, nu2, s);
+        hhg::stokes_norm(m, level, u1, u2, p, f1, f2, g, nrm, s);
+      });
+      ++it;
+      rn = read_scalar(nrm, st);
+      record(it, rn);
+      if (!std::isfinite(rn)) status = HHG_ERR_NAN;
+    }
+    std::string dmsg;
+    const hhg_status de = device_error(m, st, &dmsg);
+    if (de != HHG_OK) status = de;
+    if (rep) {
+      rep->iterations = it;
+      rep->status = status;
+      rep->r0 = r0;
+      rep->r_final = rn;
+      rep->smoother_used = HHG_SMOOTH_GS;
+    }
+    if (de != HHG_OK) return fail(status, dmsg);
+    if (status == HHG_ERR_NAN) return fail(status, "non-finite residual norm");
+    if (status == HHG_ERR_NOT_CONVERGED) return fail(status, "max_iter reached");
+    return HHG_OK;
+  });
+}
+
 hhg_status hhg_stokes_diag(hhg_mesh mesh, int32_t level, double* s_out, void* stream) {
   HHG_ENTRY_RANGE;
   return guarded([&]() {

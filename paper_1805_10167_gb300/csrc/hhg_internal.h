@@ -383,7 +383,7 @@ size_t face_gs_smem(const LevelView& L, int prec);
 void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,
                   void* work, cudaStream_t st);
 // bs_coarse (optional, FP64): also writes b_coarse / A_pp on the coarse face interiors.
-// all_free (FP64): every unknown free, Dirichlet flags ignored (a pressure field)
+// all_free: every unknown free, Dirichlet flags ignored (a pressure field)
 void restrict_op(const Mesh& m, int fine_level, int prec, const void* r_fine, void* b_coarse,
                  cudaStream_t st, double* bs_coarse = nullptr, bool all_free = false);
 // bs = b / A_pp on the face interiors of an FP64 level with k = 1
@@ -486,6 +486,11 @@ void stokes_vcycle(const Mesh& m, int l, double* u1, double* u2, double* p, cons
 void stokes_norm(const Mesh& m, int l, const double* u1, const double* u2, const double* p, const double* f1,
                  const double* f2, const double* g, double* norm_dev, cudaStream_t st);
 void stokes_diag(const Mesh& m, int l, double* s_out, cudaStream_t st);
+// mixed precision: the FP32 buffers (synchronous, once), and one refinement
+// step: d = one FP32 variable V-cycle on K d = r from d = 0, where r is the
+// FP64 residual left by the last stokes_norm on this level; (u, p) += d
+void stokes_ir_prepare(Mesh& m);
+void stokes_ir_step(const Mesh& m, int l, double* u1, double* u2, double* p, int nu1, int nu2, cudaStream_t st);
 int stokes_coarse_level(const Mesh& m);
 
 void p2_setup(Mesh& m);

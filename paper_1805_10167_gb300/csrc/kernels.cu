@@ -856,7 +856,7 @@ static void restrict_t(const Mesh& m, int lf, const T* rf, T* bc, cudaStream_t s
 void restrict_op(const Mesh& m, int fine_level, int prec, const void* r_fine, void* b_coarse,
                  cudaStream_t st, double* bs_coarse, bool all_free) {
   if (prec == 0) restrict_t(m, fine_level, (const double*)r_fine, (double*)b_coarse, st, bs_coarse, all_free);
-  else restrict_t<float>(m, fine_level, (const float*)r_fine, (float*)b_coarse, st, nullptr);
+  else restrict_t<float>(m, fine_level, (const float*)r_fine, (float*)b_coarse, st, nullptr, all_free);
 }
 
 // b / A_pp on the face interiors (one warp per face row), the first product
@@ -912,7 +912,7 @@ static void prolong_t(const Mesh& m, int lf, const T* xc, T* xf, cudaStream_t st
 void prolongate_add(const Mesh& m, int fine_level, int prec, const void* x_coarse, void* x_fine,
                     cudaStream_t st, bool all_free) {
   if (prec == 0) prolong_t(m, fine_level, (const double*)x_coarse, (double*)x_fine, st, all_free);
-  else prolong_t(m, fine_level, (const float*)x_coarse, (float*)x_fine, st);
+  else prolong_t(m, fine_level, (const float*)x_coarse, (float*)x_fine, st, all_free);
 }
 
 void coarse_solve(const Mesh& m, int prec, const void* b0, void* x0, cudaStream_t st) {

@@ -63,30 +63,43 @@ const int kDn[3][2] = {{1, 0}, {0, 1}, {1, 1}};
 
 }  // namespace
 
-// One operator's weights on one face (macro scale).
-struct StOp {
-  double in[7];
-  double sd[3][5];
-  double co[3][3];
+// One operator's weights on one face (macro scale), in the arithmetic type W.
+template <typename W>
+struct StOpT {
+  W in[7];
+  W sd[3][5];
+  W co[3][3];
 };
 
-struct StFace {
-  StOp op[ST_NOPS];
+template <typename W>
+struct StFaceT {
+  StOpT<W> op[ST_NOPS];
+};
+using StOp = StOpT<double>;
+using StFace = StFaceT<double>;
+
+// Level vectors of one precision.
+template <typename T>
+struct StBufs {
+  T* sinv = nullptr;                       // 1 / s on every pressure owner slot (smoothed levels)
+  T *u1 = nullptr, *u2 = nullptr, *p = nullptr;    // iterates below the top level (FP32: every level)
+  T *f1 = nullptr, *f2 = nullptr, *g = nullptr;    // right-hand sides below the top level (FP32: every level)
+  T *r1 = nullptr, *r2 = nullptr, *rp = nullptr;   // residuals
+  T *w1 = nullptr, *w2 = nullptr, *pn = nullptr;   // ping-pong partners of the iterates
+  T *b1 = nullptr, *b2 = nullptr;                  // velocity right-hand sides f_d - B_d^T p
 };
 
 struct StokesLevel {
-  double* sinv = nullptr;                  // 1 / s on every pressure owner slot (smoothed levels)
-  double *u1 = nullptr, *u2 = nullptr, *p = nullptr;   // iterates below the top level
-  double *f1 = nullptr, *f2 = nullptr, *g = nullptr;   // right-hand sides below the top level
-  double *r1 = nullptr, *r2 = nullptr, *rp = nullptr;  // residuals
-  double *w1 = nullptr, *w2 = nullptr, *pn = nullptr;  // ping-pong partners of the iterates
-  double *b1 = nullptr, *b2 = nullptr;                 // velocity right-hand sides f_d - B_d^T p
+  StBufs<double> d;
+  StBufs<float> f;                         // the FP32 cycle of the mixed-precision solve (made on first use)
 };
 
 struct StokesData {
   double delta = 0.3, omega = 0.4;
   int nvel = 2, coarse = 0, growth = 2;
   StFace* faces = nullptr;                 // device, one per macro-face
+  StFaceT<float>* faces32 = nullptr;       // the same in FP32 (made with the FP32 buffers)
+  bool f32 = false;                        // FP32 buffers made
   std::vector<StokesLevel> lv;
   int nc = 0;                              // coarse system size
   double* Minv = nullptr;                  // nc x nc, row-major
@@ -97,14 +110,16 @@ struct StokesData {
   std::vector<void*> allocs;
 };
 
-struct StArgs {
-  const double *u1, *u2, *p, *g, *sinv, *dinv;
-  const double *base1, *base2;   // ST_GRAD: out_d = base_d + sgn B_d^T p (nullptr: 0)
-  double *out1, *out2;
+template <typename T>
+struct StArgsT {
+  const T *u1, *u2, *p, *g, *sinv, *dinv;
+  const T *base1, *base2;        // ST_GRAD: out_d = base_d + sgn B_d^T p (nullptr: 0)
+  T *out1, *out2;
   double sgn, omega, sB, sC;
   int pm;                        // StPres for ST_PRES
   double* partials;              // SP_RES: per-block sums of squares
 };
+using StArgs = StArgsT<double>;
 
 namespace {
 
@@ -213,20 +228,21 @@ __device__ __forceinline__ double st_block_sum(double v) {
 }
 
 // Output of a pressure row from y = (B1 u1 + B2 u2)(q) and c = (C p)(q), both scaled.
-__device__ __forceinline__ double pres_out(const StArgs& a, int64_t s, double y, double& acc) {
+template <typename T>
+__device__ __forceinline__ T pres_out(const StArgsT<T>& a, int64_t s, T y, double& acc) {
   if (a.pm == SP_APPLY) return y;
   if (a.pm == SP_RES) {
-    const double r = a.g[s] - y;
-    acc += r * r;
+    const T r = a.g[s] - y;
+    acc += (double)r * (double)r;
     return r;
   }
-  return fma(a.omega, (y - a.g[s]) * a.sinv[s], a.p[s]);
+  return fma((T)a.omega, (y - a.g[s]) * a.sinv[s], a.p[s]);
 }
 
 // Face-interior rows: one warp per face row, lanes along the row.
-template <int MODE>
-__device__ __forceinline__ void st_face(const MeshTables& M, const LevelView& L, const StFace* __restrict__ W,
-                                        const StArgs& a, int bid, int nblk) {
+template <typename T, int MODE>
+__device__ __forceinline__ void st_face(const MeshTables& M, const LevelView& L, const StFaceT<T>* __restrict__ W,
+                                        const StArgsT<T>& a, int bid, int nblk) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (bid * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)nblk * blockDim.x) >> 5;
@@ -244,55 +260,55 @@ __device__ __forceinline__ void st_face(const MeshTables& M, const LevelView& L,
   for (int64_t task = warp; task < ntask; task += nwarps) {
     const int f = face_id(M, (int)(task / rows));
     const int j = (int)(task - (task / rows) * rows) + 1;
-    const StFace& F = W[f];
+    const StFaceT<T>& F = W[f];
     const int64_t row = L.f_off + (int64_t)f * L.FS + (int64_t)j * S;
-    double w1[3], w2[3], wc[3];
+    T w1[3], w2[3], wc[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       if (MODE == ST_GRAD) {
-        w1[k] = 0.5 * (F.op[ST_B1T].in[1 + 2 * k] - F.op[ST_B1T].in[2 + 2 * k]);
-        w2[k] = 0.5 * (F.op[ST_B2T].in[1 + 2 * k] - F.op[ST_B2T].in[2 + 2 * k]);
+        w1[k] = T(0.5) * (F.op[ST_B1T].in[1 + 2 * k] - F.op[ST_B1T].in[2 + 2 * k]);
+        w2[k] = T(0.5) * (F.op[ST_B2T].in[1 + 2 * k] - F.op[ST_B2T].in[2 + 2 * k]);
       } else if (MODE == ST_PRES) {
-        w1[k] = 0.5 * (F.op[ST_B1].in[1 + 2 * k] - F.op[ST_B1].in[2 + 2 * k]);
-        w2[k] = 0.5 * (F.op[ST_B2].in[1 + 2 * k] - F.op[ST_B2].in[2 + 2 * k]);
-        wc[k] = 0.5 * (F.op[ST_C].in[1 + 2 * k] + F.op[ST_C].in[2 + 2 * k]);
+        w1[k] = T(0.5) * (F.op[ST_B1].in[1 + 2 * k] - F.op[ST_B1].in[2 + 2 * k]);
+        w2[k] = T(0.5) * (F.op[ST_B2].in[1 + 2 * k] - F.op[ST_B2].in[2 + 2 * k]);
+        wc[k] = T(0.5) * (F.op[ST_C].in[1 + 2 * k] + F.op[ST_C].in[2 + 2 * k]);
       }
     }
-    const double wc0 = F.op[ST_C].in[0];
-    const double gs = a.sgn * a.sB;
+    const T wc0 = F.op[ST_C].in[0];
+    const T gs = (T)(a.sgn * a.sB), sB = (T)a.sB, sC = (T)a.sC;
     for (int i = 1 + lane; i <= N - 1 - j; i += 32) {
       const int64_t s = row + i;
       if (MODE == ST_GRAD) {
-        const double d0 = a.p[s + oe[0]] - a.p[s - oe[0]];
-        const double d1 = a.p[s + oe[1]] - a.p[s - oe[1]];
-        const double d2 = a.p[s + oe[2]] - a.p[s - oe[2]];
-        const double t1 = fma(w1[2], d2, fma(w1[1], d1, w1[0] * d0));
-        const double t2 = fma(w2[2], d2, fma(w2[1], d1, w2[0] * d0));
+        const T d0 = a.p[s + oe[0]] - a.p[s - oe[0]];
+        const T d1 = a.p[s + oe[1]] - a.p[s - oe[1]];
+        const T d2 = a.p[s + oe[2]] - a.p[s - oe[2]];
+        const T t1 = fma(w1[2], d2, fma(w1[1], d1, w1[0] * d0));
+        const T t2 = fma(w2[2], d2, fma(w2[1], d1, w2[0] * d0));
         a.out1[s] = a.base1 ? fma(gs, t1, a.base1[s]) : gs * t1;
         a.out2[s] = a.base2 ? fma(gs, t2, a.base2[s]) : gs * t2;
       } else if (MODE == ST_PRES) {
-        double y = w1[0] * (a.u1[s + oe[0]] - a.u1[s - oe[0]]);
+        T y = w1[0] * (a.u1[s + oe[0]] - a.u1[s - oe[0]]);
         y = fma(w1[1], a.u1[s + oe[1]] - a.u1[s - oe[1]], y);
         y = fma(w1[2], a.u1[s + oe[2]] - a.u1[s - oe[2]], y);
         y = fma(w2[0], a.u2[s + oe[0]] - a.u2[s - oe[0]], y);
         y = fma(w2[1], a.u2[s + oe[1]] - a.u2[s - oe[1]], y);
         y = fma(w2[2], a.u2[s + oe[2]] - a.u2[s - oe[2]], y);
-        const double pc = a.p[s];
-        double c = wc0 * pc;
+        const T pc = a.p[s];
+        T c = wc0 * pc;
         c = fma(wc[0], a.p[s + oe[0]] + a.p[s - oe[0]], c);
         c = fma(wc[1], a.p[s + oe[1]] + a.p[s - oe[1]], c);
         c = fma(wc[2], a.p[s + oe[2]] + a.p[s - oe[2]], c);
-        a.out1[s] = pres_out(a, s, fma(a.sB, y, -a.sC * c), acc);
+        a.out1[s] = pres_out<T>(a, s, fma(sB, y, -sC * c), acc);
       } else if (MODE == ST_SDIAG) {
-        double v = a.sC * F.op[ST_C].in[0];
+        T v = sC * F.op[ST_C].in[0];
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
-          const double b1 = a.sB * F.op[ST_B1].in[q], b2 = a.sB * F.op[ST_B2].in[q];
+          const T b1 = sB * F.op[ST_B1].in[q], b2 = sB * F.op[ST_B2].in[q];
           v += (b1 * b1 + b2 * b2) * a.dinv[s + kStIn[q].x + (int64_t)kStIn[q].y * S];
         }
-        a.out1[s] = 1.0 / v;
+        a.out1[s] = T(1) / v;
       } else {
-        a.out1[s] = 1.0 / F.op[ST_A].in[0];
+        a.out1[s] = T(1) / F.op[ST_A].in[0];
       }
     }
   }
@@ -303,9 +319,9 @@ __device__ __forceinline__ void st_face(const MeshTables& M, const LevelView& L,
 }
 
 // Macro-edge rows: one thread per edge point (e, t), t = 1 .. N - 1.
-template <int MODE>
-__device__ __forceinline__ void st_edge(const MeshTables& M, const LevelView& L, const StFace* __restrict__ W,
-                                        const StArgs& a, int bid, int nblk) {
+template <typename T, int MODE>
+__device__ __forceinline__ void st_edge(const MeshTables& M, const LevelView& L, const StFaceT<T>* __restrict__ W,
+                                        const StArgsT<T>& a, int bid, int nblk) {
   const int N = L.N;
   const int64_t total = N >= 2 ? (int64_t)M.ne * (N - 1) : 0;
   double acc = 0.0;
@@ -320,10 +336,11 @@ __device__ __forceinline__ void st_edge(const MeshTables& M, const LevelView& L,
       if (MODE == ST_GRAD) a.out2[s] = 0.0;
       continue;
     }
-    double t1 = 0.0, t2 = 0.0, y = 0.0, c = 0.0, dg = 0.0;
+    T t1 = 0, t2 = 0, y = 0, c = 0, dg = 0;
     // ST_SDIAG: assembled B weights of the centre and of the edge neighbours
     // t + 1 and t - 1 (shared by the faces), C's centre, off-edge terms
-    double bc1 = 0.0, bc2 = 0.0, bp1 = 0.0, bp2 = 0.0, bm1 = 0.0, bm2 = 0.0, v = 0.0;
+    T bc1 = 0, bc2 = 0, bp1 = 0, bp2 = 0, bm1 = 0, bm2 = 0, v = 0;
+    const T sB = (T)a.sB, sC = (T)a.sC;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (q >= E.nfaces) break;
@@ -331,12 +348,12 @@ __device__ __forceinline__ void st_edge(const MeshTables& M, const LevelView& L,
       const int f = face_id(M, sd.face);
       const int r = sd.rot;
       const int p = sd.aligned ? t : N - t;
-      const StFace& F = W[f];
+      const StFaceT<T>& F = W[f];
       const int64_t base = L.f_off + (int64_t)f * L.FS;
       if (MODE == ST_GRAD) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-          const double x = a.p[base + frame_slot(M, L, r, p + kStSd[k].x, kStSd[k].y)];
+          const T x = a.p[base + frame_slot(M, L, r, p + kStSd[k].x, kStSd[k].y)];
           t1 += F.op[ST_B1T].sd[r][k] * x;
           t2 += F.op[ST_B2T].sd[r][k] * x;
         }
@@ -351,8 +368,8 @@ __device__ __forceinline__ void st_edge(const MeshTables& M, const LevelView& L,
         bc1 += F.op[ST_B1].sd[r][0];
         bc2 += F.op[ST_B2].sd[r][0];
         // (p + 1, 0) is edge position t + 1 when the frame runs with the edge
-        const double n1a = F.op[ST_B1].sd[r][1], n1b = F.op[ST_B1].sd[r][2];
-        const double n2a = F.op[ST_B2].sd[r][1], n2b = F.op[ST_B2].sd[r][2];
+        const T n1a = F.op[ST_B1].sd[r][1], n1b = F.op[ST_B1].sd[r][2];
+        const T n2a = F.op[ST_B2].sd[r][1], n2b = F.op[ST_B2].sd[r][2];
         bp1 += sd.aligned ? n1a : n1b;
         bm1 += sd.aligned ? n1b : n1a;
         bp2 += sd.aligned ? n2a : n2b;
@@ -360,7 +377,7 @@ __device__ __forceinline__ void st_edge(const MeshTables& M, const LevelView& L,
         c += F.op[ST_C].sd[r][0];
 #pragma unroll
         for (int k = 3; k < 5; ++k) {
-          const double b1 = a.sB * F.op[ST_B1].sd[r][k], b2 = a.sB * F.op[ST_B2].sd[r][k];
+          const T b1 = sB * F.op[ST_B1].sd[r][k], b2 = sB * F.op[ST_B2].sd[r][k];
           v += (b1 * b1 + b2 * b2) * a.dinv[base + frame_slot(M, L, r, p + kStSd[k].x, kStSd[k].y)];
         }
       } else {
@@ -368,17 +385,17 @@ __device__ __forceinline__ void st_edge(const MeshTables& M, const LevelView& L,
       }
     }
     if (MODE == ST_GRAD) {
-      a.out1[s] = (a.base1 ? a.base1[s] : 0.0) + a.sgn * (a.sB * t1);
-      a.out2[s] = (a.base2 ? a.base2[s] : 0.0) + a.sgn * (a.sB * t2);
+      a.out1[s] = (a.base1 ? a.base1[s] : T(0)) + (T)a.sgn * (sB * t1);
+      a.out2[s] = (a.base2 ? a.base2[s] : T(0)) + (T)a.sgn * (sB * t2);
     } else if (MODE == ST_PRES) {
-      a.out1[s] = pres_out(a, s, a.sB * y - a.sC * c, acc);
+      a.out1[s] = pres_out<T>(a, s, sB * y - sC * c, acc);
     } else if (MODE == ST_SDIAG) {
-      const double sB2 = a.sB * a.sB;
-      v += a.sC * c + sB2 * ((bc1 * bc1 + bc2 * bc2) * a.dinv[s] + (bp1 * bp1 + bp2 * bp2) * a.dinv[s + 1] +
-                             (bm1 * bm1 + bm2 * bm2) * a.dinv[s - 1]);
-      a.out1[s] = 1.0 / v;
+      const T sB2 = sB * sB;
+      v += sC * c + sB2 * ((bc1 * bc1 + bc2 * bc2) * a.dinv[s] + (bp1 * bp1 + bp2 * bp2) * a.dinv[s + 1] +
+                           (bm1 * bm1 + bm2 * bm2) * a.dinv[s - 1]);
+      a.out1[s] = T(1) / v;
     } else {
-      a.out1[s] = 1.0 / dg;
+      a.out1[s] = T(1) / dg;
     }
   }
   if (MODE == ST_PRES && a.pm == SP_RES) {
@@ -388,9 +405,9 @@ __device__ __forceinline__ void st_edge(const MeshTables& M, const LevelView& L,
 }
 
 // Macro-vertex rows: one thread per vertex.
-template <int MODE>
-__device__ __forceinline__ void st_vertex(const MeshTables& M, const LevelView& L, const StFace* __restrict__ W,
-                                          const StArgs& a, int bid, int nblk) {
+template <typename T, int MODE>
+__device__ __forceinline__ void st_vertex(const MeshTables& M, const LevelView& L, const StFaceT<T>* __restrict__ W,
+                                          const StArgsT<T>& a, int bid, int nblk) {
   const int N = L.N;
   double acc = 0.0;
   for (int vi = bid * blockDim.x + threadIdx.x; vi < M.nv; vi += nblk * blockDim.x) {
@@ -404,17 +421,18 @@ __device__ __forceinline__ void st_vertex(const MeshTables& M, const LevelView& 
     }
     int cb = V.c_begin, ce = V.c_end;
     table_range(M, cb, ce, M.ncorners);
-    double t1 = 0.0, t2 = 0.0, y = 0.0, c = 0.0, dg = 0.0, bc1 = 0.0, bc2 = 0.0;
+    T t1 = 0, t2 = 0, y = 0, c = 0, dg = 0, bc1 = 0, bc2 = 0;
+    const T sB = (T)a.sB, sC = (T)a.sC;
     for (int ci = cb; ci < ce; ++ci) {
       const Corner cn = M.corners[ci];
       const int f = face_id(M, cn.face);
       const int r = cn.rot;
-      const StFace& F = W[f];
+      const StFaceT<T>& F = W[f];
       const int64_t base = L.f_off + (int64_t)f * L.FS;
       if (MODE == ST_GRAD) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const double x = a.p[base + frame_slot(M, L, r, kStCo[k].x, kStCo[k].y)];
+          const T x = a.p[base + frame_slot(M, L, r, kStCo[k].x, kStCo[k].y)];
           t1 += F.op[ST_B1T].co[r][k] * x;
           t2 += F.op[ST_B2T].co[r][k] * x;
         }
@@ -434,27 +452,27 @@ __device__ __forceinline__ void st_vertex(const MeshTables& M, const LevelView& 
       }
     }
     if (MODE == ST_GRAD) {
-      a.out1[s] = (a.base1 ? a.base1[s] : 0.0) + a.sgn * (a.sB * t1);
-      a.out2[s] = (a.base2 ? a.base2[s] : 0.0) + a.sgn * (a.sB * t2);
+      a.out1[s] = (a.base1 ? a.base1[s] : T(0)) + (T)a.sgn * (sB * t1);
+      a.out2[s] = (a.base2 ? a.base2[s] : T(0)) + (T)a.sgn * (sB * t2);
     } else if (MODE == ST_PRES) {
-      a.out1[s] = pres_out(a, s, a.sB * y - a.sC * c, acc);
+      a.out1[s] = pres_out<T>(a, s, sB * y - sC * c, acc);
     } else if (MODE == ST_SDIAG) {
       // the neighbours are the first points of the incident macro-edges; a
       // neighbour's weight sums the corners of the faces on both sides of
       // its edge: (1, 0) lies on side r, (0, 1) on side r + 2 of the frame
-      const double sB2 = a.sB * a.sB;
-      double v = a.sC * c + sB2 * (bc1 * bc1 + bc2 * bc2) * a.dinv[s];
+      const T sB2 = sB * sB;
+      T v = sC * c + sB2 * (bc1 * bc1 + bc2 * bc2) * a.dinv[s];
       int eb = V.e_begin, ee = V.e_end;
       table_range(M, eb, ee, M.nvedges);
       for (int k = eb; k < ee; ++k) {
         const VertEdge ve = M.vedges[k];
         const int e = edge_id(M, ve.edge);
-        double w1 = 0.0, w2 = 0.0;
+        T w1 = 0, w2 = 0;
         for (int ci = cb; ci < ce; ++ci) {
           const Corner cn = M.corners[ci];
           const int f = face_id(M, cn.face);
           const FaceRec& FR = M.faces[f];
-          const StFace& F = W[f];
+          const StFaceT<T>& F = W[f];
           if (FR.edge[cn.rot] == e) {
             w1 += F.op[ST_B1].co[cn.rot][1];
             w2 += F.op[ST_B2].co[cn.rot][1];
@@ -466,9 +484,9 @@ __device__ __forceinline__ void st_vertex(const MeshTables& M, const LevelView& 
         }
         v += sB2 * (w1 * w1 + w2 * w2) * a.dinv[L.e_off + (int64_t)e * L.ES + (ve.is_low ? 1 : N - 1)];
       }
-      a.out1[s] = 1.0 / v;
+      a.out1[s] = T(1) / v;
     } else {
-      a.out1[s] = 1.0 / dg;
+      a.out1[s] = T(1) / dg;
     }
   }
   if (MODE == ST_PRES && a.pm == SP_RES) {
@@ -480,20 +498,20 @@ __device__ __forceinline__ void st_vertex(const MeshTables& M, const LevelView& 
 // One launch for every row kind of a mode: blocks [0, bv) take the macro-
 // vertices, [bv, bv + be) the macro-edge points, the rest the face rows
 // (partial sums, where written, in that block order).
-template <int MODE>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kStThreads, 4)
-    k_st_rows(MeshTables M, LevelView L, const StFace* __restrict__ W, StArgs a, int bv, int be) {
+    k_st_rows(MeshTables M, LevelView L, const StFaceT<T>* __restrict__ W, StArgsT<T> a, int bv, int be) {
   const int b = blockIdx.x;
   if (b < bv) {
-    st_vertex<MODE>(M, L, W, a, b, bv);
+    st_vertex<T, MODE>(M, L, W, a, b, bv);
   } else if (b < bv + be) {
-    StArgs ae = a;
+    StArgsT<T> ae = a;
     if (ae.partials) ae.partials += bv;
-    st_edge<MODE>(M, L, W, ae, b - bv, be);
+    st_edge<T, MODE>(M, L, W, ae, b - bv, be);
   } else {
-    StArgs af = a;
+    StArgsT<T> af = a;
     if (af.partials) af.partials += bv + be;
-    st_face<MODE>(M, L, W, af, b - bv - be, (int)gridDim.x - bv - be);
+    st_face<T, MODE>(M, L, W, af, b - bv - be, (int)gridDim.x - bv - be);
   }
 }
 
@@ -507,18 +525,42 @@ __global__ void k_st_sum(const double* __restrict__ partials, int n, double* out
 // sc[3] = sqrt(sc[0] + sc[1] + sc[2])
 __global__ void k_st_norm(double* sc) { sc[3] = sqrt(sc[0] + sc[1] + sc[2]); }
 
+// FP64 -> FP32 copies of three level vectors, and x_d += (double) d_d for three
+__global__ void k_st_narrow(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                            const double* __restrict__ c, float* __restrict__ fa, float* __restrict__ fb,
+                            float* __restrict__ fc) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    fa[i] = (float)a[i];
+    fb[i] = (float)b[i];
+    fc[i] = (float)c[i];
+  }
+}
+__global__ void k_st_widen_add(int64_t n, double* __restrict__ a, double* __restrict__ b, double* __restrict__ c,
+                               const float* __restrict__ da, const float* __restrict__ db,
+                               const float* __restrict__ dc) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    a[i] += (double)da[i];
+    b[i] += (double)db[i];
+    c[i] += (double)dc[i];
+  }
+}
+__global__ void k_st_narrow1(int64_t n, const double* __restrict__ a, float* __restrict__ fa) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    fa[i] = (float)a[i];
+}
+
 // Coarse correction: every CTA gathers the residual (free velocity of both
 // components, then every pressure unknown) into shared memory, its warps
 // take rows of the stored inverse, and the correction is added to the
 // owner slots.
+template <typename T>
 __global__ void __launch_bounds__(kStThreads)
     k_st_coarse(int n, const double* __restrict__ Minv, const int64_t* __restrict__ slot, const int* __restrict__ comp,
-                const double* __restrict__ r1, const double* __restrict__ r2, const double* __restrict__ rp,
-                double* u1, double* u2, double* p) {
+                const T* __restrict__ r1, const T* __restrict__ r2, const T* __restrict__ rp, T* u1, T* u2, T* p) {
   extern __shared__ double sb[];
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const int cpt = comp[k];
-    sb[k] = (cpt == 0 ? r1 : (cpt == 1 ? r2 : rp))[slot[k]];
+    sb[k] = (double)(cpt == 0 ? r1 : (cpt == 1 ? r2 : rp))[slot[k]];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -529,8 +571,8 @@ __global__ void __launch_bounds__(kStThreads)
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
       const int cpt = comp[row];
-      double* dst = cpt == 0 ? u1 : (cpt == 1 ? u2 : p);
-      dst[slot[row]] += acc;
+      T* dst = cpt == 0 ? u1 : (cpt == 1 ? u2 : p);
+      dst[slot[row]] += (T)acc;
     }
   }
 }
@@ -554,9 +596,10 @@ double* st_alloc(StokesData& D, size_t bytes) {
   return (double*)p;
 }
 
-StArgs args_for(const Mesh& m, int l) {
+template <typename T>
+StArgsT<T> args_for(const Mesh& m, int l) {
   const StokesData& D = *m.stokes;
-  StArgs a{};
+  StArgsT<T> a{};
   const double N = (double)m.levels[l].lv.N;
   a.sB = 1.0 / N;
   a.sC = D.delta / (N * N);
@@ -568,8 +611,25 @@ StArgs args_for(const Mesh& m, int l) {
 // Runs the face, edge and vertex kernels of one mode on level l; returns the
 // number of partial sums written (SP_RES: vertex blocks, edge blocks, face
 // blocks, in that order).
-template <int MODE>
-int st_rows(const Mesh& m, int l, StArgs a, cudaStream_t st) {
+template <typename T>
+const StFaceT<T>* faces_of(const StokesData& D);
+template <>
+const StFaceT<double>* faces_of<double>(const StokesData& D) { return D.faces; }
+template <>
+const StFaceT<float>* faces_of<float>(const StokesData& D) { return D.faces32; }
+template <typename T>
+StBufs<T>& bufs(StokesLevel& S);
+template <>
+StBufs<double>& bufs<double>(StokesLevel& S) { return S.d; }
+template <>
+StBufs<float>& bufs<float>(StokesLevel& S) { return S.f; }
+template <typename T>
+const StBufs<T>& bufs(const StokesLevel& S) { return bufs<T>(const_cast<StokesLevel&>(S)); }
+template <typename T>
+constexpr int prec_of() { return sizeof(T) == 8 ? 0 : 1; }
+
+template <typename T, int MODE>
+int st_rows(const Mesh& m, int l, StArgsT<T> a, cudaStream_t st) {
   const StokesData& D = *m.stokes;
   const LevelView& L = m.levels[l].lv;
   const int bv = st_blocks(m.nv, kStThreads, 64);
@@ -578,38 +638,40 @@ int st_rows(const Mesh& m, int l, StArgs a, cudaStream_t st) {
   const int64_t ftask = L.N >= 3 ? (int64_t)m.nf * (L.N - 2) : 0;
   const int bf = st_blocks(ftask * 32, kStThreads, 2432);
   HHG_LAUNCH(HHG_K_FACE_ROWS, l, st, "stokes rows",
-             k_st_rows<MODE><<<bv + be + bf, kStThreads, 0, st>>>(m.tab, L, D.faces, a, bv, be));
+             k_st_rows<T, MODE><<<bv + be + bf, kStThreads, 0, st>>>(m.tab, L, faces_of<T>(D), a, bv, be));
   return bv + be + bf;
 }
 
 // out_d = base_d + sgn B_d^T p on free velocity rows (0 at Dirichlet rows)
-void grad_rows(const Mesh& m, int l, const double* p, const double* base1, const double* base2, double sgn,
-               double* out1, double* out2, cudaStream_t st) {
-  StArgs a = args_for(m, l);
+template <typename T>
+void grad_rows(const Mesh& m, int l, const T* p, const T* base1, const T* base2, double sgn, T* out1, T* out2,
+               cudaStream_t st) {
+  StArgsT<T> a = args_for<T>(m, l);
   a.p = p;
   a.base1 = base1;
   a.base2 = base2;
   a.sgn = sgn;
   a.out1 = out1;
   a.out2 = out2;
-  st_rows<ST_GRAD>(m, l, a, st);
+  st_rows<T, ST_GRAD>(m, l, a, st);
 }
 
 // pressure rows: APPLY out = B u - C p; RES out = g - (B u - C p) (and
 // *norm2 = its sum of squares); JAC out = p + omega (B u - C p - g) / s
-void pres_rows(const Mesh& m, int l, int pm, const double* u1, const double* u2, const double* p, const double* g,
-               double* out, double* norm2, cudaStream_t st) {
+template <typename T>
+void pres_rows(const Mesh& m, int l, int pm, const T* u1, const T* u2, const T* p, const T* g, T* out,
+               double* norm2, cudaStream_t st) {
   const StokesData& D = *m.stokes;
-  StArgs a = args_for(m, l);
+  StArgsT<T> a = args_for<T>(m, l);
   a.u1 = u1;
   a.u2 = u2;
   a.p = p;
   a.g = g;
   a.pm = pm;
   a.out1 = out;
-  a.sinv = D.lv[l].sinv;
+  a.sinv = bufs<T>(D.lv[l]).sinv;
   a.partials = pm == SP_RES ? m.partials : nullptr;
-  const int nb = st_rows<ST_PRES>(m, l, a, st);
+  const int nb = st_rows<T, ST_PRES>(m, l, a, st);
   if (pm == SP_RES && norm2)
     HHG_LAUNCH(HHG_K_OTHER, l, st, "stokes sum", k_st_sum<<<1, kStThreads, 0, st>>>(m.partials, nb, norm2));
 }
@@ -785,30 +847,32 @@ void check_level_args(const Mesh& m, int l) {
 
 // u_d: the velocity iterates with consistent ghost copies; on return
 // cur_d points at the buffer that holds the new iterate (the other of the pair)
-void velocity_sweeps(const Mesh& m, int l, double*& c1, double*& o1, double*& c2, double*& o2, const double* b1,
-                     const double* b2, bool forward, cudaStream_t st) {
+template <typename T>
+void velocity_sweeps(const Mesh& m, int l, T*& c1, T*& o1, T*& c2, T*& o2, const T* b1, const T* b2, bool forward,
+                     cudaStream_t st) {
   const StokesData& D = *m.stokes;
   for (int s = 0; s < D.nvel; ++s) {
-    gs_sweep(m, l, 0, c1, o1, b1, forward, st, nullptr);
+    gs_sweep(m, l, prec_of<T>(), c1, o1, b1, forward, st, nullptr);
     std::swap(c1, o1);
-    gs_sweep(m, l, 0, c2, o2, b2, forward, st, nullptr);
+    gs_sweep(m, l, prec_of<T>(), c2, o2, b2, forward, st, nullptr);
     std::swap(c2, o2);
   }
 }
 
 // One Uzawa step on level l with the iterate in (c1, c2, cp) and partners
 // (o1, o2, op); pointers follow the buffer holding the newest iterate.
-void uzawa_step(const Mesh& m, int l, double*& c1, double*& o1, double*& c2, double*& o2, double*& cp,
-                double*& op, const double* f1, const double* f2, const double* g, bool forward, cudaStream_t st) {
-  const StokesLevel& S = m.stokes->lv[l];
+template <typename T>
+void uzawa_step(const Mesh& m, int l, T*& c1, T*& o1, T*& c2, T*& o2, T*& cp, T*& op, const T* f1, const T* f2,
+                const T* g, bool forward, cudaStream_t st) {
+  const StBufs<T>& S = bufs<T>(m.stokes->lv[l]);
   auto pressure = [&]() {
-    pres_rows(m, l, SP_JAC, c1, c2, cp, g, op, nullptr, st);
-    ghost_fill(m, l, 0, op, st);
+    pres_rows<T>(m, l, SP_JAC, c1, c2, cp, g, op, nullptr, st);
+    ghost_fill(m, l, prec_of<T>(), op, st);
     std::swap(cp, op);
   };
   auto velocity = [&]() {
-    grad_rows(m, l, cp, f1, f2, -1.0, S.b1, S.b2, st);
-    velocity_sweeps(m, l, c1, o1, c2, o2, S.b1, S.b2, forward, st);
+    grad_rows<T>(m, l, cp, f1, f2, -1.0, S.b1, S.b2, st);
+    velocity_sweeps<T>(m, l, c1, o1, c2, o2, S.b1, S.b2, forward, st);
   };
   if (forward) {
     velocity();
@@ -820,57 +884,59 @@ void uzawa_step(const Mesh& m, int l, double*& c1, double*& o1, double*& c2, dou
 }
 
 // residual (r1, r2, rp) on level l; norms^2 into D.sc[0..2] when `norms`
-void residual_all(const Mesh& m, int l, const double* u1, const double* u2, const double* p, const double* f1,
-                  const double* f2, const double* g, double* r1, double* r2, double* rp, bool norms,
-                  cudaStream_t st) {
+template <typename T>
+void residual_all(const Mesh& m, int l, const T* u1, const T* u2, const T* p, const T* f1, const T* f2, const T* g,
+                  T* r1, T* r2, T* rp, bool norms, cudaStream_t st) {
   const StokesData& D = *m.stokes;
-  const StokesLevel& S = D.lv[l];
-  grad_rows(m, l, p, f1, f2, -1.0, S.b1, S.b2, st);
-  residual_op(m, l, 0, u1, S.b1, r1, norms ? D.sc : nullptr, st);
-  residual_op(m, l, 0, u2, S.b2, r2, norms ? D.sc + 1 : nullptr, st);
-  pres_rows(m, l, SP_RES, u1, u2, p, g, rp, norms ? D.sc + 2 : nullptr, st);
+  const StBufs<T>& S = bufs<T>(D.lv[l]);
+  grad_rows<T>(m, l, p, f1, f2, -1.0, S.b1, S.b2, st);
+  residual_op(m, l, prec_of<T>(), u1, S.b1, r1, norms ? D.sc : nullptr, st);
+  residual_op(m, l, prec_of<T>(), u2, S.b2, r2, norms ? D.sc + 1 : nullptr, st);
+  pres_rows<T>(m, l, SP_RES, u1, u2, p, g, rp, norms ? D.sc + 2 : nullptr, st);
 }
 
-void coarse_correct(const Mesh& m, int l, double* u1, double* u2, double* p, const double* f1, const double* f2,
-                    const double* g, cudaStream_t st) {
+template <typename T>
+void coarse_correct(const Mesh& m, int l, T* u1, T* u2, T* p, const T* f1, const T* f2, const T* g, cudaStream_t st) {
   const StokesData& D = *m.stokes;
-  const StokesLevel& S = D.lv[l];
-  residual_all(m, l, u1, u2, p, f1, f2, g, S.r1, S.r2, S.rp, false, st);
+  const StBufs<T>& S = bufs<T>(D.lv[l]);
+  residual_all<T>(m, l, u1, u2, p, f1, f2, g, S.r1, S.r2, S.rp, false, st);
   const int rows_per_cta = kStThreads / 32;
   const int grid = std::max(1, std::min(152 * 4, (D.nc + rows_per_cta - 1) / rows_per_cta));
   HHG_LAUNCH(HHG_K_OTHER, l, st, "stokes coarse",
-             k_st_coarse<<<grid, kStThreads, (size_t)D.nc * sizeof(double), st>>>(D.nc, D.Minv, D.cslot, D.ccomp,
-                                                                                  S.r1, S.r2, S.rp, u1, u2, p));
-  ghost_fill(m, l, 0, u1, st);
-  ghost_fill(m, l, 0, u2, st);
-  ghost_fill(m, l, 0, p, st);
+             k_st_coarse<T><<<grid, kStThreads, (size_t)D.nc * sizeof(double), st>>>(D.nc, D.Minv, D.cslot, D.ccomp,
+                                                                                     S.r1, S.r2, S.rp, u1, u2, p));
+  ghost_fill(m, l, prec_of<T>(), u1, st);
+  ghost_fill(m, l, prec_of<T>(), u2, st);
+  ghost_fill(m, l, prec_of<T>(), p, st);
 }
 
-void vcycle_rec(const Mesh& m, int l, int top, double* u1, double* u2, double* p, const double* f1,
-                const double* f2, const double* g, int nu1, int nu2, cudaStream_t st) {
+template <typename T>
+void vcycle_rec(const Mesh& m, int l, int top, T* u1, T* u2, T* p, const T* f1, const T* f2, const T* g, int nu1,
+                int nu2, cudaStream_t st) {
   const StokesData& D = *m.stokes;
   if (l <= D.coarse) {
-    coarse_correct(m, l, u1, u2, p, f1, f2, g, st);
+    coarse_correct<T>(m, l, u1, u2, p, f1, f2, g, st);
     return;
   }
-  const StokesLevel& S = D.lv[l];
-  const StokesLevel& C = D.lv[l - 1];
-  const size_t bytes = (size_t)m.levels[l].lv.len * sizeof(double);
-  double *c1 = u1, *c2 = u2, *cp = p, *o1 = S.w1, *o2 = S.w2, *op = S.pn;
+  const int pr = prec_of<T>();
+  const StBufs<T>& S = bufs<T>(D.lv[l]);
+  const StBufs<T>& C = bufs<T>(D.lv[l - 1]);
+  const size_t bytes = (size_t)m.levels[l].lv.len * sizeof(T);
+  T *c1 = u1, *c2 = u2, *cp = p, *o1 = S.w1, *o2 = S.w2, *op = S.pn;
   const int extra = D.growth * (top - l);
-  for (int s = 0; s < nu1 + extra; ++s) uzawa_step(m, l, c1, o1, c2, o2, cp, op, f1, f2, g, true, st);
-  residual_all(m, l, c1, c2, cp, f1, f2, g, S.r1, S.r2, S.rp, false, st);
-  restrict_op(m, l, 0, S.r1, C.f1, st);
-  restrict_op(m, l, 0, S.r2, C.f2, st);
-  restrict_op(m, l, 0, S.rp, C.g, st, nullptr, true);
-  zero_vec(m, l - 1, 0, C.u1, st);
-  zero_vec(m, l - 1, 0, C.u2, st);
-  zero_vec(m, l - 1, 0, C.p, st);
-  vcycle_rec(m, l - 1, top, C.u1, C.u2, C.p, C.f1, C.f2, C.g, nu1, nu2, st);
-  prolongate_add(m, l, 0, C.u1, c1, st);
-  prolongate_add(m, l, 0, C.u2, c2, st);
-  prolongate_add(m, l, 0, C.p, cp, st, true);
-  for (int s = 0; s < nu2 + extra; ++s) uzawa_step(m, l, c1, o1, c2, o2, cp, op, f1, f2, g, false, st);
+  for (int s = 0; s < nu1 + extra; ++s) uzawa_step<T>(m, l, c1, o1, c2, o2, cp, op, f1, f2, g, true, st);
+  residual_all<T>(m, l, c1, c2, cp, f1, f2, g, S.r1, S.r2, S.rp, false, st);
+  restrict_op(m, l, pr, S.r1, C.f1, st);
+  restrict_op(m, l, pr, S.r2, C.f2, st);
+  restrict_op(m, l, pr, S.rp, C.g, st, nullptr, true);
+  zero_vec(m, l - 1, pr, C.u1, st);
+  zero_vec(m, l - 1, pr, C.u2, st);
+  zero_vec(m, l - 1, pr, C.p, st);
+  vcycle_rec<T>(m, l - 1, top, C.u1, C.u2, C.p, C.f1, C.f2, C.g, nu1, nu2, st);
+  prolongate_add(m, l, pr, C.u1, c1, st);
+  prolongate_add(m, l, pr, C.u2, c2, st);
+  prolongate_add(m, l, pr, C.p, cp, st, true);
+  for (int s = 0; s < nu2 + extra; ++s) uzawa_step<T>(m, l, c1, o1, c2, o2, cp, op, f1, f2, g, false, st);
   if (c1 != u1) check_cuda(cudaMemcpyAsync(u1, c1, bytes, cudaMemcpyDeviceToDevice, st), "copy u1");
   if (c2 != u2) check_cuda(cudaMemcpyAsync(u2, c2, bytes, cudaMemcpyDeviceToDevice, st), "copy u2");
   if (cp != p) check_cuda(cudaMemcpyAsync(p, cp, bytes, cudaMemcpyDeviceToDevice, st), "copy p");
@@ -913,7 +979,7 @@ void stokes_setup(Mesh& m, double delta, double omega, int nvel, int coarse, int
     D.sc = st_alloc(D, 8 * sizeof(double));
     D.lv.assign(m.max_level + 1, StokesLevel{});
     for (int l = coarse; l <= m.max_level; ++l) {
-      StokesLevel& S = D.lv[l];
+      StBufs<double>& S = D.lv[l].d;
       const size_t bytes = (size_t)m.levels[l].lv.len * sizeof(double);
       S.r1 = st_alloc(D, bytes);
       S.r2 = st_alloc(D, bytes);
@@ -934,14 +1000,14 @@ void stokes_setup(Mesh& m, double delta, double omega, int nvel, int coarse, int
         S.pn = st_alloc(D, bytes);
         S.sinv = st_alloc(D, bytes);
         // 1 / A_jj on free velocity points (b1 as scratch), then s
-        StArgs a = args_for(m, l);
+        StArgs a = args_for<double>(m, l);
         a.out1 = S.b1;
-        st_rows<ST_DINV>(m, l, a, 0);
+        st_rows<double, ST_DINV>(m, l, a, 0);
         ghost_fill(m, l, 0, S.b1, 0);
-        a = args_for(m, l);
+        a = args_for<double>(m, l);
         a.dinv = S.b1;
         a.out1 = S.sinv;
-        st_rows<ST_SDIAG>(m, l, a, 0);
+        st_rows<double, ST_SDIAG>(m, l, a, 0);
         ghost_fill(m, l, 0, S.sinv, 0);
       }
     }
@@ -959,8 +1025,8 @@ void stokes_apply(const Mesh& m, int l, const double* u1, const double* u2, cons
   fill_inputs(m, l, u1, u2, p, st);
   apply_op(m, l, 0, u1, y1, st);
   apply_op(m, l, 0, u2, y2, st);
-  grad_rows(m, l, p, y1, y2, 1.0, y1, y2, st);
-  pres_rows(m, l, SP_APPLY, u1, u2, p, nullptr, yp, nullptr, st);
+  grad_rows<double>(m, l, p, y1, y2, 1.0, y1, y2, st);
+  pres_rows<double>(m, l, SP_APPLY, u1, u2, p, nullptr, yp, nullptr, st);
 }
 
 void stokes_residual(const Mesh& m, int l, const double* u1, const double* u2, const double* p, const double* f1,
@@ -969,7 +1035,7 @@ void stokes_residual(const Mesh& m, int l, const double* u1, const double* u2, c
   check_level_args(m, l);
   const StokesData& D = *m.stokes;
   fill_inputs(m, l, u1, u2, p, st);
-  residual_all(m, l, u1, u2, p, f1, f2, g, r1, r2, rp, norm_dev != nullptr, st);
+  residual_all<double>(m, l, u1, u2, p, f1, f2, g, r1, r2, rp, norm_dev != nullptr, st);
   if (norm_dev) {
     HHG_LAUNCH(HHG_K_OTHER, l, st, "stokes norm", k_st_norm<<<1, 1, 0, st>>>(D.sc));
     check_cuda(cudaMemcpyAsync(norm_dev, D.sc + 3, sizeof(double), cudaMemcpyDeviceToDevice, st), "norm copy");
@@ -982,10 +1048,10 @@ void stokes_smooth(const Mesh& m, int l, double* u1, double* u2, double* p, cons
   const StokesData& D = *m.stokes;
   if (l <= D.coarse) throw std::invalid_argument("Stokes smoother: level must be above coarse_level");
   fill_inputs(m, l, u1, u2, p, st);
-  const StokesLevel& S = D.lv[l];
+  const StBufs<double>& S = D.lv[l].d;
   const size_t bytes = (size_t)m.levels[l].lv.len * sizeof(double);
   double *c1 = u1, *c2 = u2, *cp = p, *o1 = S.w1, *o2 = S.w2, *op = S.pn;
-  for (int s = 0; s < steps; ++s) uzawa_step(m, l, c1, o1, c2, o2, cp, op, f1, f2, g, forward, st);
+  for (int s = 0; s < steps; ++s) uzawa_step<double>(m, l, c1, o1, c2, o2, cp, op, f1, f2, g, forward, st);
   if (c1 != u1) check_cuda(cudaMemcpyAsync(u1, c1, bytes, cudaMemcpyDeviceToDevice, st), "copy u1");
   if (c2 != u2) check_cuda(cudaMemcpyAsync(u2, c2, bytes, cudaMemcpyDeviceToDevice, st), "copy u2");
   if (cp != p) check_cuda(cudaMemcpyAsync(p, cp, bytes, cudaMemcpyDeviceToDevice, st), "copy p");
@@ -996,16 +1062,16 @@ void stokes_vcycle(const Mesh& m, int l, double* u1, double* u2, double* p, cons
   check_level_args(m, l);
   if (nu1 < 0 || nu2 < 0) throw std::invalid_argument("nu1, nu2 >= 0");
   fill_inputs(m, l, u1, u2, p, st);
-  vcycle_rec(m, l, l, u1, u2, p, f1, f2, g, nu1, nu2, st);
+  vcycle_rec<double>(m, l, l, u1, u2, p, f1, f2, g, nu1, nu2, st);
 }
 
 void stokes_norm(const Mesh& m, int l, const double* u1, const double* u2, const double* p, const double* f1,
                  const double* f2, const double* g, double* norm_dev, cudaStream_t st) {
   check_level_args(m, l);
   const StokesData& D = *m.stokes;
-  const StokesLevel& S = D.lv[l];
+  const StBufs<double>& S = D.lv[l].d;
   fill_inputs(m, l, u1, u2, p, st);
-  residual_all(m, l, u1, u2, p, f1, f2, g, S.r1, S.r2, S.rp, true, st);
+  residual_all<double>(m, l, u1, u2, p, f1, f2, g, S.r1, S.r2, S.rp, true, st);
   HHG_LAUNCH(HHG_K_OTHER, l, st, "stokes norm", k_st_norm<<<1, 1, 0, st>>>(D.sc));
   check_cuda(cudaMemcpyAsync(norm_dev, D.sc + 3, sizeof(double), cudaMemcpyDeviceToDevice, st), "norm copy");
 }
@@ -1016,8 +1082,68 @@ void stokes_diag(const Mesh& m, int l, double* s_out, cudaStream_t st) {
   check_level_args(m, l);
   const StokesData& D = *m.stokes;
   if (l <= D.coarse) throw std::invalid_argument("Stokes smoother diagonal: level must be above coarse_level");
-  check_cuda(cudaMemcpyAsync(s_out, D.lv[l].sinv, (size_t)m.levels[l].lv.len * sizeof(double),
+  check_cuda(cudaMemcpyAsync(s_out, D.lv[l].d.sinv, (size_t)m.levels[l].lv.len * sizeof(double),
                              cudaMemcpyDeviceToDevice, st), "diag copy");
+}
+
+// FP32 buffers of every level from coarse_level up (iterates and right-hand
+// sides on every level: the FP32 cycle starts from the refinement step's
+// residual on the top level), the FP32 weights and 1/s.
+void stokes_ir_prepare(Mesh& m) {
+  StokesData& D = data(m);
+  if (D.f32) return;
+  check_cuda(cudaDeviceSynchronize(), "sync");
+  std::vector<StFace> w(m.nf);
+  check_cuda(cudaMemcpy(w.data(), D.faces, w.size() * sizeof(StFace), cudaMemcpyDeviceToHost), "weights");
+  std::vector<StFaceT<float>> w32(m.nf);
+  for (int f = 0; f < m.nf; ++f)
+    for (int o = 0; o < ST_NOPS; ++o) {
+      const StOp& a = w[f].op[o];
+      StOpT<float>& b = w32[f].op[o];
+      for (int k = 0; k < 7; ++k) b.in[k] = (float)a.in[k];
+      for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 5; ++k) b.sd[r][k] = (float)a.sd[r][k];
+        for (int k = 0; k < 3; ++k) b.co[r][k] = (float)a.co[r][k];
+      }
+    }
+  D.faces32 = (StFaceT<float>*)st_alloc(D, w32.size() * sizeof(StFaceT<float>));
+  check_cuda(cudaMemcpy(D.faces32, w32.data(), w32.size() * sizeof(StFaceT<float>), cudaMemcpyHostToDevice),
+             "FP32 weights");
+  for (int l = D.coarse; l <= m.max_level; ++l) {
+    StBufs<float>& S = D.lv[l].f;
+    const int64_t n = m.levels[l].lv.len;
+    const size_t bytes = (size_t)n * sizeof(float);
+    for (float** v : {&S.u1, &S.u2, &S.p, &S.f1, &S.f2, &S.g, &S.r1, &S.r2, &S.rp, &S.b1, &S.b2})
+      *v = (float*)st_alloc(D, bytes);
+    if (l > D.coarse) {
+      S.w1 = (float*)st_alloc(D, bytes);
+      S.w2 = (float*)st_alloc(D, bytes);
+      S.pn = (float*)st_alloc(D, bytes);
+      S.sinv = (float*)st_alloc(D, bytes);
+      k_st_narrow1<<<st_blocks(n, kStThreads, 152 * 8), kStThreads>>>(n, D.lv[l].d.sinv, S.sinv);
+      check_launch("FP32 1/s");
+    }
+  }
+  check_cuda(cudaDeviceSynchronize(), "FP32 Stokes buffers");
+  D.f32 = true;
+}
+
+void stokes_ir_step(const Mesh& m, int l, double* u1, double* u2, double* p, int nu1, int nu2, cudaStream_t st) {
+  check_level_args(m, l);
+  const StokesData& D = *m.stokes;
+  if (!D.f32) throw std::logic_error("Stokes FP32 buffers not made");
+  const StBufs<double>& R = D.lv[l].d;
+  const StBufs<float>& F = D.lv[l].f;
+  const int64_t n = m.levels[l].lv.len;
+  const int grid = st_blocks(n, kStThreads, 152 * 8);
+  HHG_LAUNCH(HHG_K_OTHER, l, st, "stokes narrow",
+             k_st_narrow<<<grid, kStThreads, 0, st>>>(n, R.r1, R.r2, R.rp, F.f1, F.f2, F.g));
+  zero_vec(m, l, 1, F.u1, st);
+  zero_vec(m, l, 1, F.u2, st);
+  zero_vec(m, l, 1, F.p, st);
+  vcycle_rec<float>(m, l, l, F.u1, F.u2, F.p, F.f1, F.f2, F.g, nu1, nu2, st);
+  HHG_LAUNCH(HHG_K_OTHER, l, st, "stokes widen",
+             k_st_widen_add<<<grid, kStThreads, 0, st>>>(n, u1, u2, p, F.u1, F.u2, F.p));
 }
 
 }  // namespace hhg

@@ -99,6 +99,8 @@ _SIGS = {
     "hhg_stokes_vcycle": [_P, C.c_int32] + [_P] * 6 + [C.c_int32, C.c_int32, _P],
     "hhg_stokes_solve": [_P, C.c_int32] + [_P] * 6 + [C.c_int32, C.c_int32, C.c_double, C.c_int32,
                                                        C.POINTER(SolveReport), _P],
+    "hhg_stokes_solve_ir": [_P, C.c_int32] + [_P] * 6 + [C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                                          C.POINTER(SolveReport), _P],
     "hhg_stokes_diag": [_P, C.c_int32, _P, _P],
     "hhg_debug_wait_limit": [_P, C.c_int32, C.c_int64],
     "hhg_apply": [_P, C.c_int32, C.c_int32, _P, _P, _P],
@@ -299,6 +301,20 @@ class Mesh:
         rep = SolveReport(0, 0, 0.0, 0.0, hist, max_iter + 1, 0, 0.0, 0.0)
         st = lib.hhg_stokes_solve(self.h, level, *(_ptr(v) for v in (u1, u2, p, f1, f2, g)), nu1, nu2, tol,
                                   max_iter, C.byref(rep), _stream(stream))
+        out = {"iterations": rep.iterations, "status": rep.status, "r0": rep.r0, "r_final": rep.r_final,
+               "history": [hist[i] for i in range(min(rep.iterations + 1, max_iter + 1))]}
+        if raise_on_error and st != OK:
+            raise HHGError(st, last_error())
+        return st, out
+
+    def stokes_solve_ir(self, level, u1, u2, p, f1, f2, g, nu1=2, nu2=2, tol=1e-8, max_iter=100, stream=None,
+                        raise_on_error=True):
+        """FP32 variable V-cycles inside FP64 iterative refinement.  Returns
+        (status, report dict)."""
+        hist = (C.c_double * (max_iter + 1))()
+        rep = SolveReport(0, 0, 0.0, 0.0, hist, max_iter + 1, 0, 0.0, 0.0)
+        st = lib.hhg_stokes_solve_ir(self.h, level, *(_ptr(v) for v in (u1, u2, p, f1, f2, g)), nu1, nu2, tol,
+                                     max_iter, C.byref(rep), _stream(stream))
         out = {"iterations": rep.iterations, "status": rep.status, "r0": rep.r0, "r_final": rep.r_final,
                "history": [hist[i] for i in range(min(rep.iterations + 1, max_iter + 1))]}
         if raise_on_error and st != OK:

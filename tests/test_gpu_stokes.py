@@ -186,3 +186,37 @@ def test_stokes_argument_errors():
         g.stokes_vcycle(3, *v)
     assert e.value.status == hhg.ERR_ARG
     g.close()
+
+
+FP32_CYCLE_TOL = 1e-5   # one FP32 cycle against the FP64 one: FP32 roundoff (6e-8) times the cycle's growth
+
+
+@pytest.mark.parametrize("name,L,coarse", [("square", 4, 0), ("annulus", 3, 0), ("random5", 3, 1)])
+def test_stokes_mixed_precision_step_and_solve(pairs, name, L, coarse):
+    """One refinement step (FP64 residual, FP32 variable V-cycle from zero,
+    FP64 update) against the oracle's FP64 cycle from the same iterate, at the
+    stated FP32 bound; then the mixed solve reaches the FP64 tolerance 1e-10
+    with at most two steps more than the oracle's FP64 cycles."""
+    P = pairs(name, L, coarse)
+    f1, f2, g = P.rhs(L)
+    fd = [P.to_dev(L, v) for v in (f1, f2, g)]
+    lv = P.S.levels[L]
+    u1, u2, p = (P.rng.standard_normal(lv.n) for _ in range(3))
+    u1[~lv.free] = 0.0
+    u2[~lv.free] = 0.0
+    d = [P.to_dev(L, v) for v in (u1, u2, p)]
+    st, rep = P.g.stokes_solve_ir(L, *d, *fd, tol=0.0, max_iter=1, raise_on_error=False)
+    assert rep["iterations"] == 1
+    w = [u1.copy(), u2.copy(), p.copy()]
+    P.S.vcycle(L, *w, f1, f2, g, 2, 2)
+    errs = [rel_err(P.from_dev(L, got), want) for got, want in zip(d, w)]
+    print(f"{name} level {L}: one mixed-precision step against the FP64 cycle, max relative error {max(errs):.1e}")
+    assert max(errs) <= FP32_CYCLE_TOL
+    z = np.zeros(P.n(L))
+    d = [P.to_dev(L, z) for _ in range(3)]
+    st, rep = P.g.stokes_solve_ir(L, *d, *fd, tol=1e-10, max_iter=80)
+    hist = P.S.solve(*[z.copy() for _ in range(3)], f1, f2, g, tol=1e-10, max_iter=80)
+    assert rep["r_final"] <= 1e-10 * rep["r0"]
+    assert rep["iterations"] <= len(hist) - 1 + 2
+    got = [P.from_dev(L, v) for v in d]
+    assert P.S.norm(L, *P.S.residual(L, *got, f1, f2, g)) <= 1.01e-10 * hist[0]
