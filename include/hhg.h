@@ -126,7 +126,7 @@ typedef struct {
   double r_final;         /* final residual norm                             */
   double* history;        /* optional HOST array: residual norm per cycle    */
   int32_t history_cap;    /* its capacity (entries written: min(cap, it+1))   */
-  int32_t smoother_used;  /* FGMRES: smoother kept by the judge (learned ->  */
+  int32_t smoother_used;  /* FGMRES: smoother kept by the smoother judge (learned ->  */
                           /* GS when the CNN reduced the residual less)      */
   double judge_learned;   /* FGMRES judge: ||v1 - A M(v1)|| with the learned */
   double judge_gs;        /* and with the Gauss-Seidel preconditioner (0 if  */

@@ -386,7 +386,7 @@ static double host_scalar(const double* dev, cudaStream_t st) {
   return h;
 }
 
-// ||v - A z|| (FP64) for the judge
+// ||v - A z|| (FP64) for the smoother judge
 static double precond_quality(Mesh& m, int L, const double* v, const double* z, double* tmp, cudaStream_t st) {
   apply_op(m, L, 0, z, tmp, st);
   assign_op(m, L, 0, 1.0, v, -1.0, tmp, tmp, st);

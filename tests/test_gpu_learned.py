@@ -1,6 +1,6 @@
 """Learned smoother and FGMRES on the GPU against the oracle: CNN forward
 (BF16 tolerance), weight gradients on crops (BF16 tolerance), FGMRES solves
-to 1e-10, training, and the judge's fallback."""
+to 1e-10, training, and the smoother judge's fallback."""
 import numpy as np
 import pytest
 
@@ -186,11 +186,11 @@ def test_fgmres_gs_preconditioner_reaches_fp64_tolerance():
 
 def test_training_lowers_loss_and_learned_fgmres_converges():
     """Small training run (level 6): the loss falls; FGMRES with the learned
-    V-cycle reaches the FP64 tolerance; the judge's choice and the
+    V-cycle reaches the FP64 tolerance; the smoother judge's choice and the
     convergence factors are reported.  What the trained network gains over
     the method without it: a Gauss-Seidel sweep followed by the learned step
     leaves less residual in one V(1,1) than the Gauss-Seidel V(1,1) (the
-    judge's measurement), so the judge keeps it and FGMRES needs no more
+    judge's measurement), so the smoother judge keeps it and FGMRES needs no more
     steps than with Gauss-Seidel."""
     torch = pytest.importorskip("torch")
     from paper_1805_10167_gb300 import hhg
