@@ -300,24 +300,47 @@ __global__ void __launch_bounds__(kP2Threads)
         step = 2;
       }
     }
-    for (int i = i0 + step * lane; i <= N1 - 1 - j; i += 32 * step) {
-      const int64_t s = base + (int64_t)j * S + i;
-      double ax = 0.0, wc;
-      if (((i | j) & 1) == 0) {
+    // Gauss-Seidel: one point type per class, so the centre weight's
+    // reciprocal is formed once per row (an FP64 division costs as much as
+    // the stencil itself)
+    const double winv = mode == P2_GS ? 1.0 / (cls <= 2 ? F.V[0] : F.E[cls - 3][0]) : 0.0;
+    // two points per lane and pass (the same type: 32 step apart), their
+    // gathers issued together
+    const int iend = N1 - 1 - j;
+    for (int ia = i0 + step * lane; ia <= iend; ia += 64 * step) {
+      const int ib = ia + 32 * step;
+      const bool hb = ib <= iend;
+      const int64_t sa = base + (int64_t)j * S + ia, sb = hb ? base + (int64_t)j * S + ib : sa;
+      double axa = 0.0, axb = 0.0, wc;
+      if (((ia | j) & 1) == 0) {
         wc = F.V[0];
 #pragma unroll
-        for (int q = 1; q < 13; ++q) ax += F.V[q] * x[s + kOffV[q].x + (int64_t)kOffV[q].y * S];
+        for (int q = 1; q < 13; ++q) {
+          const int64_t o = kOffV[q].x + (int64_t)kOffV[q].y * S;
+          axa += F.V[q] * x[sa + o];
+          axb += F.V[q] * x[sb + o];
+        }
       } else {
-        const double* w = F.E[(i & 1) && !(j & 1) ? 0 : ((j & 1) && !(i & 1) ? 1 : 2)];
+        const double* w = F.E[(ia & 1) && !(j & 1) ? 0 : ((j & 1) && !(ia & 1) ? 1 : 2)];
         wc = w[0];
 #pragma unroll
-        for (int q = 1; q < 7; ++q) ax += w[q] * x[s + kOffE[q].x + (int64_t)kOffE[q].y * S];
+        for (int q = 1; q < 7; ++q) {
+          const int64_t o = kOffE[q].x + (int64_t)kOffE[q].y * S;
+          axa += w[q] * x[sa + o];
+          axb += w[q] * x[sb + o];
+        }
       }
-      const double xc = x[s];
-      if (mode == P2_GS) {
-        out[s] = (b[s] - ax) / wc;
-      } else {
-        out[s] = p2_out(mode, b ? b[s] : 0.0, ax + wc * xc, wc, xc);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u == 1 && !hb) break;
+        const int64_t s = u ? sb : sa;
+        const double ax = u ? axb : axa;
+        const double xc = x[s];
+        if (mode == P2_GS) {
+          out[s] = (b[s] - ax) * winv;
+        } else {
+          out[s] = p2_out(mode, b ? b[s] : 0.0, ax + wc * xc, wc, xc);
+        }
       }
     }
   }
