@@ -276,7 +276,66 @@ __device__ __forceinline__ void st_face(const MeshTables& M, const LevelView& L,
     }
     const T wc0 = F.op[ST_C].in[0];
     const T gs = (T)(a.sgn * a.sB), sB = (T)a.sB, sC = (T)a.sC;
-    for (int i = 1 + lane; i <= N - 1 - j; i += 32) {
+    // FP32: two points per lane and pass, every load of both issued before
+    // the first store (the FP32 rows are bound by memory latency, the FP64
+    // ones by the FP64 pipe)
+    constexpr int U = sizeof(T) == 4 ? 2 : 1;
+    const int iend = N - 1 - j;
+    if (U == 2 && (MODE == ST_GRAD || MODE == ST_PRES)) {
+      for (int i0 = 1 + lane; i0 <= iend; i0 += 64) {
+        int64_t sp[2];
+        bool on[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          on[u] = i0 + 32 * u <= iend;
+          sp[u] = row + (on[u] ? i0 + 32 * u : i0);
+        }
+        if (MODE == ST_GRAD) {
+          T d[2][3], bb1[2], bb2[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) d[u][k] = a.p[sp[u] + oe[k]] - a.p[sp[u] - oe[k]];
+            bb1[u] = a.base1 ? a.base1[sp[u]] : T(0);
+            bb2[u] = a.base2 ? a.base2[sp[u]] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (!on[u]) break;
+            const T t1 = fma(w1[2], d[u][2], fma(w1[1], d[u][1], w1[0] * d[u][0]));
+            const T t2 = fma(w2[2], d[u][2], fma(w2[1], d[u][1], w2[0] * d[u][0]));
+            a.out1[sp[u]] = fma(gs, t1, bb1[u]);
+            a.out2[sp[u]] = fma(gs, t2, bb2[u]);
+          }
+        } else {
+          T y[2], c[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int64_t s = sp[u];
+            T yy = w1[0] * (a.u1[s + oe[0]] - a.u1[s - oe[0]]);
+            yy = fma(w1[1], a.u1[s + oe[1]] - a.u1[s - oe[1]], yy);
+            yy = fma(w1[2], a.u1[s + oe[2]] - a.u1[s - oe[2]], yy);
+            yy = fma(w2[0], a.u2[s + oe[0]] - a.u2[s - oe[0]], yy);
+            yy = fma(w2[1], a.u2[s + oe[1]] - a.u2[s - oe[1]], yy);
+            yy = fma(w2[2], a.u2[s + oe[2]] - a.u2[s - oe[2]], yy);
+            T cc = wc0 * a.p[s];
+            cc = fma(wc[0], a.p[s + oe[0]] + a.p[s - oe[0]], cc);
+            cc = fma(wc[1], a.p[s + oe[1]] + a.p[s - oe[1]], cc);
+            cc = fma(wc[2], a.p[s + oe[2]] + a.p[s - oe[2]], cc);
+            y[u] = yy;
+            c[u] = cc;
+          }
+          T res[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) res[u] = on[u] ? pres_out<T>(a, sp[u], fma(sB, y[u], -sC * c[u]), acc) : T(0);
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (on[u]) a.out1[sp[u]] = res[u];
+        }
+      }
+      continue;
+    }
+    for (int i = 1 + lane; i <= iend; i += 32) {
       const int64_t s = row + i;
       if (MODE == ST_GRAD) {
         const T d0 = a.p[s + oe[0]] - a.p[s - oe[0]];
