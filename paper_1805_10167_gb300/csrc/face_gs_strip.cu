@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
                const T* __restrict__ bsf, const T* __restrict__ k, const int4* __restrict__ tasks, int ntasks,
                const int* __restrict__ clist, const __grid_constant__ EdgeColours cs, int small,
                const unsigned short* __restrict__ spts, int4 sptr, unsigned* bar, int* err,
-               unsigned bar_extra, long long bar_polls) {
+               unsigned bar_extra, long long bar_polls, T* xin2, T* xout2, const T* __restrict__ b2) {
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   GridBar gb = barrier_start(bar, bar_extra, bar_polls);
   const int lane = threadIdx.x & 31;
@@ -484,20 +484,32 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
     p.t = edge_pos(M, L, pk - (pk / (L.N + 1)) * (L.N + 1));
     p.E = M.edges[p.e];
   };
-  auto vertices = [&](T* x, const VertRec& V0) {
-    if (gw < M.nv) vertex_gs_rec<T, VARK>(M, L, V0, gw, lane, x, b, k);
-    for (int v = gw + nw; v < M.nv; v += nw) vertex_gs<T, VARK>(M, L, v, lane, x, b, k);
+  // a second vector (x2, b2; small levels only): every phase sweeps both,
+  // the grid barriers are shared
+  auto vertices1 = [&](T* x, const T* bb, const VertRec& V0) {
+    if (gw < M.nv) vertex_gs_rec<T, VARK>(M, L, V0, gw, lane, x, bb, k);
+    for (int v = gw + nw; v < M.nv; v += nw) vertex_gs<T, VARK>(M, L, v, lane, x, bb, k);
   };
-  auto edges = [&](T* x, int c, int pk, const EdgePre& p) {
-    if (pk >= 0) edge_gs_rec<T, VARK>(M, L, p.E, p.e, p.t, x, b, k);
+  auto vertices = [&](bool out, const VertRec& V0) {
+    vertices1(out ? xout : xin, b, V0);
+    if (xin2) vertices1(out ? xout2 : xin2, b2, V0);
+  };
+  auto edges1 = [&](T* x, const T* bb, int c, int pk, const EdgePre& p) {
+    if (pk >= 0) edge_gs_rec<T, VARK>(M, L, p.E, p.e, p.t, x, bb, k);
     for (int q = cs.ptr[c] + gt + nt; q < cs.ptr[c + 1]; q += nt) {
       const int pq = clist[q];
       const int e = pq / (L.N + 1);
-      edge_gs<T, VARK>(M, L, e, pq - e * (L.N + 1), x, b, k);
+      edge_gs<T, VARK>(M, L, e, pq - e * (L.N + 1), x, bb, k);
     }
+  };
+  auto edges = [&](bool out, int c, int pk, const EdgePre& p) {
+    edges1(out ? xout : xin, b, c, pk, p);
+    if (xin2) edges1(out ? xout2 : xin2, b2, c, pk, p);
   };
   auto faces = [&]() {
     for (int64_t q = gt; q < L.f_off; q += nt) xout[q] = xin[q];
+    if (xin2)
+      for (int64_t q = gt; q < L.f_off; q += nt) xout2[q] = xin2[q];
     if (small) {
       uint64_t* mb = reinterpret_cast<uint64_t*>(dyn_smem);
       T* sx = reinterpret_cast<T*>(dyn_smem + kSmallHeader);
@@ -509,6 +521,9 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
       __syncthreads();
       for (int f = blockIdx.x; f < M.nf; f += gridDim.x)
         face_small<T, VARK, FWD>(M, L, f, xin, xout, b, k, sx, mb, phase, spts, sptr, err);
+      if (xin2)
+        for (int f = blockIdx.x; f < M.nf; f += gridDim.x)
+          face_small<T, VARK, FWD>(M, L, f, xin2, xout2, b2, k, sx, mb, phase, spts, sptr, err);
     } else {
       // tasks handed out one at a time from a ticket counter (the strips of
       // a face differ in height, the rows of a task in length); the last
@@ -536,11 +551,11 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
   if (FWD) {
     int pk = edge_pk(0), pk_next = edge_pk(1);
     if (gw < M.nv) V0 = M.verts[gw];
-    vertices(xin, V0);
+    vertices(false, V0);
     edge_pre(pk, ep);
     grid_barrier(bar, gb, err);
     for (int c = 0; c < cs.n; ++c) {
-      edges(xin, c, pk, ep);
+      edges(false, c, pk, ep);
       pk = pk_next;
       pk_next = edge_pk(c + 2);
       edge_pre(pk, ep);
@@ -554,7 +569,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
     edge_pre(pk, ep);
     grid_barrier(bar, gb, err);
     for (int c = cs.n - 1; c >= 0; --c) {
-      edges(xout, c, pk, ep);
+      edges(true, c, pk, ep);
       pk = pk_next;
       pk_next = edge_pk(c - 2);
       edge_pre(pk, ep);
@@ -562,7 +577,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
       grid_barrier(bar, gb, err);
     }
     if (cs.n == 0 && gw < M.nv) V0 = M.verts[gw];
-    vertices(xout, V0);
+    vertices(true, V0);
   }
 }
 
@@ -595,7 +610,7 @@ std::vector<int> strip_tasks(int nf, int N, int rows_per_task) {
 
 template <typename T, bool DF, bool VARK, bool FWD, bool BS>
 static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b, const T* bs, const T* k,
-                           cudaStream_t st) {
+                           cudaStream_t st, T* xin2 = nullptr, T* xout2 = nullptr, const T* b2 = nullptr) {
   const LevelData& ld = m.levels[level];
   const SweepCfg& c = ld.sweep[sizeof(T) == 8 ? 0 : 1];
   const int small = ld.lv.N <= kSmallN ? 1 : 0;
@@ -646,24 +661,24 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
                                 (const int4*)c.tasks, c.ntasks, (const int*)ld.colour_list, cs, small,
                                 (const unsigned short*)ld.small_pts,
                                 make_int4(ld.small_ptr[0], ld.small_ptr[1], ld.small_ptr[2], ld.small_ptr[3]),
-                                m.gbar, m.err, m.dbg_bar_extra, m.dbg_bar_polls),
+                                m.gbar, m.err, m.dbg_bar_extra, m.dbg_bar_polls, xin2, xout2, b2),
              "whole sweep launch");
 }
 
 template <typename T, bool DF>
 static void sweep_dispatch(const Mesh& m, int level, T* xi, T* xo, const T* b, const T* bs, const T* k,
-                           bool forward, cudaStream_t st) {
+                           bool forward, cudaStream_t st, T* xi2 = nullptr, T* xo2 = nullptr, const T* b2 = nullptr) {
   if (m.vark) {
-    if (forward) launch_sweep_t<T, DF, true, true, false>(m, level, xi, xo, b, nullptr, k, st);
-    else launch_sweep_t<T, DF, true, false, false>(m, level, xi, xo, b, nullptr, k, st);
+    if (forward) launch_sweep_t<T, DF, true, true, false>(m, level, xi, xo, b, nullptr, k, st, xi2, xo2, b2);
+    else launch_sweep_t<T, DF, true, false, false>(m, level, xi, xo, b, nullptr, k, st, xi2, xo2, b2);
   } else if (bs) {
     if constexpr (sizeof(T) == 8) {   // FP64 only
       if (forward) launch_sweep_t<T, DF, false, true, true>(m, level, xi, xo, b, bs, nullptr, st);
       else launch_sweep_t<T, DF, false, false, true>(m, level, xi, xo, b, bs, nullptr, st);
     }
   } else {
-    if (forward) launch_sweep_t<T, DF, false, true, false>(m, level, xi, xo, b, nullptr, nullptr, st);
-    else launch_sweep_t<T, DF, false, false, false>(m, level, xi, xo, b, nullptr, nullptr, st);
+    if (forward) launch_sweep_t<T, DF, false, true, false>(m, level, xi, xo, b, nullptr, nullptr, st, xi2, xo2, b2);
+    else launch_sweep_t<T, DF, false, false, false>(m, level, xi, xo, b, nullptr, nullptr, st, xi2, xo2, b2);
   }
 }
 
@@ -682,6 +697,28 @@ void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, c
   } else {
     const float* k = m.vark ? (const float*)ld.k[1] : nullptr;
     sweep_dispatch<float, false>(m, level, (float*)xin, (float*)xout, (const float*)b, nullptr, k, forward, st);
+  }
+}
+
+// Two independent vectors (the two velocity components of a Stokes
+// smoothing step) in one whole-sweep launch on a level with N <= kSmallN:
+// both go through every phase, one set of grid barriers.
+void gs_sweep_fused2(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b, void* xin2,
+                     void* xout2, const void* b2, bool forward, cudaStream_t st) {
+  const LevelData& ld = m.levels[level];
+  if (ld.lv.N > kSmallN) throw std::logic_error("two-vector sweep: small levels only");
+  if (prec == 0) {
+    const double* k = m.vark ? (const double*)ld.k[0] : nullptr;
+    if (m.fp64_df)
+      sweep_dispatch<double, true>(m, level, (double*)xin, (double*)xout, (const double*)b, nullptr, k, forward, st,
+                                   (double*)xin2, (double*)xout2, (const double*)b2);
+    else
+      sweep_dispatch<double, false>(m, level, (double*)xin, (double*)xout, (const double*)b, nullptr, k, forward, st,
+                                    (double*)xin2, (double*)xout2, (const double*)b2);
+  } else {
+    const float* k = m.vark ? (const float*)ld.k[1] : nullptr;
+    sweep_dispatch<float, false>(m, level, (float*)xin, (float*)xout, (const float*)b, nullptr, k, forward, st,
+                                 (float*)xin2, (float*)xout2, (const float*)b2);
   }
 }
 

@@ -371,6 +371,12 @@ void gs_sweep(const Mesh& m, int level, int prec, void* xin, void* xout, const v
               bool forward, cudaStream_t st, const void* bs = nullptr);
 void face_gs3_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
                      bool forward, cudaStream_t st);
+// One sweep of each of two independent vectors with the same operator (no
+// scaled right-hand side); on small levels both in one whole-sweep launch.
+void gs_sweep2(const Mesh& m, int level, int prec, void* x1in, void* x1out, const void* b1, void* x2in,
+               void* x2out, const void* b2, bool forward, cudaStream_t st);
+void gs_sweep_fused2(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b, void* xin2,
+                     void* xout2, const void* b2, bool forward, cudaStream_t st);
 std::vector<int> face_tasks(int nf, int N, int tasks_per_face);
 std::vector<int> strip_tasks(int nf, int N, int rows_per_task);
 void face_ring_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,

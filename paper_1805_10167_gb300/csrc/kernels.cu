@@ -825,6 +825,18 @@ void gs_sweep(const Mesh& m, int level, int prec, void* xin, void* xout, const v
   if (!forward) ve_gs(m, level, prec, xout, b, false, st);
 }
 
+void gs_sweep2(const Mesh& m, int level, int prec, void* x1in, void* x1out, const void* b1, void* x2in,
+               void* x2out, const void* b2, bool forward, cudaStream_t st) {
+  const LevelView& L = m.levels[level].lv;
+  if (m.levels[level].sweep[prec].variant == SWEEP_STRIP && L.N <= kSmallN) {
+    LaunchScope ls(HHG_K_FACE_GS, level, st);
+    gs_sweep_fused2(m, level, prec, x1in, x1out, b1, x2in, x2out, b2, forward, st);
+    return;
+  }
+  gs_sweep(m, level, prec, x1in, x1out, b1, forward, st);
+  gs_sweep(m, level, prec, x2in, x2out, b2, forward, st);
+}
+
 void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,
                   void* work, cudaStream_t st) {
   const int64_t n = m.levels[level].lv.len;

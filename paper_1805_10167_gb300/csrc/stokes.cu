@@ -911,9 +911,8 @@ void velocity_sweeps(const Mesh& m, int l, T*& c1, T*& o1, T*& c2, T*& o2, const
                      cudaStream_t st) {
   const StokesData& D = *m.stokes;
   for (int s = 0; s < D.nvel; ++s) {
-    gs_sweep(m, l, prec_of<T>(), c1, o1, b1, forward, st, nullptr);
+    gs_sweep2(m, l, prec_of<T>(), c1, o1, b1, c2, o2, b2, forward, st);
     std::swap(c1, o1);
-    gs_sweep(m, l, prec_of<T>(), c2, o2, b2, forward, st, nullptr);
     std::swap(c2, o2);
   }
 }
