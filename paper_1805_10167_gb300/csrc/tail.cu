@@ -4,8 +4,8 @@
 // Gauss-Seidel sweeps, residual and transfers are a dozen dependent steps
 // over a few thousand unknowns, and each separate launch (with its grid-wide
 // barriers) costs far more than its arithmetic.  Here the whole cycle from a
-// level c <= 3 down to the level-0 solve and back up runs in ONE block (1024
-// threads in FP32, 512 in FP64): every level's x, b and r live in shared memory in canonical
+// level c <= 3 down to the level-0 solve and back up runs in ONE block of
+// 1024 threads: every level's x, b and r live in shared memory in canonical
 // order (the compact numbering of the unknowns: macro-vertices, macro-edge
 // interior points, face interior points row by row), the phases are separated
 // by __syncthreads instead of launches, and the operator, restriction and
@@ -15,11 +15,6 @@
 //          -1/2 cot(angle opposite pq) k_T       (Sec. 4.2, cotangent form),
 //   P   = linear interpolation of the nested P1 spaces, R = P^T (Sec. 4.3),
 //   level 0: the stored inverse of the level-0 matrix of every problem.
-// The rows are stored column-major with a fixed width (entry k of row q at
-// k * rows + q, shorter rows padded with zero weights on their own point), so
-// that a thread issues all loads of a row at once; a thread's first row of
-// the next phase is loaded before the current phase runs and its latency
-// overlaps the phase and the barrier.
 // The Gauss-Seidel colour sets are those of the sweep kernels (free
 // macro-vertices, the level's edge colours, face interior points by
 // (i + 2j) mod 3), in the same order, so a cycle computes the same iterate up
@@ -41,14 +36,6 @@ constexpr int kTailThreads = 1024;
 constexpr int kTailMaxLevel = 3;
 constexpr int kTailMaxSets = kMaxEdgeColours + 4;      // vertices, edge colours, three face colours
 constexpr size_t kTailSmemCap = 200 * 1024;
-constexpr int kTailPre = 6;      // entries of a Gauss-Seidel row loaded a phase ahead (interior rows have 6)
-// threads of the block, and rows per thread and phase loaded ahead (FP64
-// rows take twice the registers: half the threads, two rows each)
-template <typename T>
-struct TailCfg {
-  static constexpr int threads = sizeof(T) == 8 ? 512 : 1024;
-  static constexpr int rows = kTailThreads / threads;
-};
 }  // namespace
 
 struct TailLevelDev {
@@ -56,20 +43,21 @@ struct TailLevelDev {
   int nrow;               // free unknowns (the rows, in Gauss-Seidel colour order)
   int nsets;
   int set_ptr[kTailMaxSets + 1];
-  int set_w[kTailMaxSets];   // off-diagonal entries of the longest row of each set
   int nr, np;             // restriction rows (free points of level - 1), prolongation rows (free points)
-  int rw, pw;             // their widths
   int smem_off;           // element offset of this level's x in shared memory (b at + n, r at + 2 n)
   const int* row_pt;      // canonical index of each row
-  const int* cols;        // off-diagonal entries, entry k of row q at k * nrow + q
+  const int* row_ptr;     // off-diagonal CSR (nrow + 1)
+  const int* cols;
   const void* vals;       // T
   const void* diag;       // T: A_pp
   const void* dinv;       // T: 1 / A_pp
   const int* r_pt;        // restriction into level - 1: its canonical index,
-  const int* r_cols;      //   entries over this level's free points (k * nr + i)
+  const int* r_ptr;       //   CSR over this level's free points
+  const int* r_cols;
   const void* r_vals;
-  const int* p_pt;        // prolongation: fine free point, entries over the
-  const int* p_cols;      //   points of level - 1 (k * np + i)
+  const int* p_pt;        // prolongation: fine free point, CSR over the points
+  const int* p_ptr;       //   of level - 1
+  const int* p_cols;
   const void* p_vals;
   const int64_t* slot;    // canonical index -> slot of the level vector
 };
@@ -88,130 +76,27 @@ struct TailPlan {
 
 namespace {
 
-// The data of one operator row, loaded a phase ahead of its use.
 template <typename T>
-struct TailRow {
-  int p;                  // canonical index (-1: no row for this thread)
-  T d;                    // 1 / A_pp (Gauss-Seidel) or A_pp (residual)
-  int c[kTailPre];
-  T v[kTailPre];
-};
-
-template <typename T>
-__device__ __forceinline__ void tail_row_load(const TailLevelDev& L, int s, int row, bool resid, TailRow<T>& R) {
-  if (row >= L.set_ptr[s + 1]) {
-    R.p = -1;
-    return;
-  }
+__device__ __forceinline__ void tail_gs(const TailLevelDev& L, T* x, const T* b, bool fwd) {
   const T* vals = (const T*)L.vals;
-  R.p = __ldg(L.row_pt + row);
-  R.d = __ldg((const T*)(resid ? L.diag : L.dinv) + row);
-  const int w = L.set_w[s];
-#pragma unroll
-  for (int k = 0; k < kTailPre; ++k)
-    if (k < w) {
-      R.c[k] = __ldg(L.cols + k * L.nrow + row);
-      R.v[k] = __ldg(vals + k * L.nrow + row);
+  const T* dinv = (const T*)L.dinv;
+  for (int q = 0; q < L.nsets; ++q) {
+    const int s = fwd ? q : L.nsets - 1 - q;
+    for (int row = L.set_ptr[s] + threadIdx.x; row < L.set_ptr[s + 1]; row += kTailThreads) {
+      const int p = L.row_pt[row];
+      T acc = b[p];
+      for (int k = L.row_ptr[row]; k < L.row_ptr[row + 1]; ++k) acc -= vals[k] * x[L.cols[k]];
+      x[p] = acc * dinv[row];
     }
-}
-
-// Gauss-Seidel update of the row (x_p = (b_p - sum_q A_pq x_q) / A_pp) or
-// its residual r_p = b_p - A_pp x_p - sum_q A_pq x_q.
-template <typename T>
-__device__ __forceinline__ void tail_row_apply(const TailLevelDev& L, int s, int row, bool resid,
-                                               const TailRow<T>& R, T* x, const T* b, T* r) {
-  const int w = L.set_w[s];
-  const int p = R.p;
-  T acc = resid ? R.d * x[p] : b[p];
-#pragma unroll
-  for (int k = 0; k < kTailPre; ++k)
-    if (k < w) {
-      if (resid) acc += R.v[k] * x[R.c[k]];
-      else acc -= R.v[k] * x[R.c[k]];
-    }
-  const T* vals = (const T*)L.vals;
-  for (int k = kTailPre; k < w; ++k) {   // rows of high-degree vertices
-    const T v = __ldg(vals + k * L.nrow + row);
-    const T xq = x[__ldg(L.cols + k * L.nrow + row)];
-    if (resid) acc += v * xq;
-    else acc -= v * xq;
-  }
-  if (resid) r[p] = b[p] - acc;
-  else x[p] = acc * R.d;
-}
-
-// nsw Gauss-Seidel sweeps over the colour sets (forward or backward order)
-// and then, with resid, the residual of every row into r.  A barrier follows
-// every Gauss-Seidel phase and the last residual phase.
-template <typename T>
-__device__ void tail_smooth(const TailLevelDev& L, T* x, const T* b, T* r, int nsw, bool fwd, bool resid) {
-  constexpr int NT = TailCfg<T>::threads, NR = TailCfg<T>::rows;
-  const int ns = L.nsets;
-  const int ngs = nsw * ns;
-  const int nph = ngs + (resid ? ns : 0);
-  auto set_of = [&](int ph) {
-    if (ph >= ngs) return ph - ngs;
-    const int q = ph % ns;
-    return fwd ? q : ns - 1 - q;
-  };
-  TailRow<T> nxt[NR];
-#pragma unroll
-  for (int u = 0; u < NR; ++u) {
-    nxt[u].p = -1;
-    if (nph > 0) tail_row_load(L, set_of(0), L.set_ptr[set_of(0)] + (int)threadIdx.x + u * NT, ngs == 0, nxt[u]);
-  }
-  for (int ph = 0; ph < nph; ++ph) {
-    TailRow<T> cur[NR];
-#pragma unroll
-    for (int u = 0; u < NR; ++u) cur[u] = nxt[u];
-    const int s = set_of(ph);
-    const bool res = ph >= ngs;
-    if (ph + 1 < nph) {
-      const int s2 = set_of(ph + 1);
-#pragma unroll
-      for (int u = 0; u < NR; ++u)
-        tail_row_load(L, s2, L.set_ptr[s2] + (int)threadIdx.x + u * NT, ph + 1 >= ngs, nxt[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < NR; ++u)
-      if (cur[u].p >= 0) tail_row_apply(L, s, L.set_ptr[s] + (int)threadIdx.x + u * NT, res, cur[u], x, b, r);
-    for (int row = L.set_ptr[s] + (int)threadIdx.x + NR * NT; row < L.set_ptr[s + 1]; row += NT) {
-      TailRow<T> R;
-      tail_row_load(L, s, row, res, R);
-      tail_row_apply(L, s, row, res, R, x, b, r);
-    }
-    if (!res || ph + 1 == nph) __syncthreads();
+    __syncthreads();
   }
 }
 
-// Row i of a transfer stored column-major (entry k at k * n + i, shorter
-// rows padded with zero weights), applied to v.
 template <typename T>
-__device__ __forceinline__ T tail_transfer_row(const int* __restrict__ cols, const T* __restrict__ vals, int n,
-                                               int w, int i, const T* v) {
-  T acc = T(0);
-  for (int k0 = 0; k0 < w; k0 += 4) {
-    int c[4];
-    T a[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const bool on = k0 + k < w;
-      c[k] = on ? __ldg(cols + (k0 + k) * n + i) : 0;
-      a[k] = on ? __ldg(vals + (k0 + k) * n + i) : T(0);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (k0 + k < w) acc += a[k] * v[c[k]];
-  }
-  return acc;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(TailCfg<T>::threads, 1)
+__global__ void __launch_bounds__(kTailThreads, 1)
     k_tail(const __grid_constant__ TailDev D, const Block* __restrict__ blocks, int nblocks,
            const double* __restrict__ Ainv, const int* __restrict__ free0, T* xtop, const T* __restrict__ btop,
            int nu1, int nu2) {
-  constexpr int NT = TailCfg<T>::threads;
   extern __shared__ __align__(16) unsigned char tail_smem[];
   T* sm = reinterpret_cast<T*>(tail_smem);
   const int c = D.c;
@@ -220,7 +105,7 @@ __global__ void __launch_bounds__(TailCfg<T>::threads, 1)
     const TailLevelDev& L = D.lv[c];
     T* x = sm + L.smem_off;
     T* b = x + L.n;
-    for (int p = tid; p < L.n; p += NT) {
+    for (int p = tid; p < L.n; p += kTailThreads) {
       x[p] = xtop[L.slot[p]];
       b[p] = btop[L.slot[p]];
     }
@@ -231,13 +116,28 @@ __global__ void __launch_bounds__(TailCfg<T>::threads, 1)
     T* x = sm + L.smem_off;
     T* b = x + L.n;
     T* r = b + L.n;
-    tail_smooth<T>(L, x, b, r, nu1, true, true);
+    for (int s = 0; s < nu1; ++s) tail_gs<T>(L, x, b, true);
+    {
+      const T* vals = (const T*)L.vals;
+      const T* diag = (const T*)L.diag;
+      for (int row = tid; row < L.nrow; row += kTailThreads) {
+        const int p = L.row_pt[row];
+        T acc = diag[row] * x[p];
+        for (int k = L.row_ptr[row]; k < L.row_ptr[row + 1]; ++k) acc += vals[k] * x[L.cols[k]];
+        r[p] = b[p] - acc;
+      }
+    }
+    __syncthreads();
     const TailLevelDev& C = D.lv[l - 1];
     T* xc = sm + C.smem_off;
     T* bc = xc + C.n;
-    for (int i = tid; i < L.nr; i += NT)
-      bc[__ldg(L.r_pt + i)] = tail_transfer_row(L.r_cols, (const T*)L.r_vals, L.nr, L.rw, i, (const T*)r);
-    for (int p = tid; p < C.n; p += NT) xc[p] = T(0);
+    const T* rv = (const T*)L.r_vals;
+    for (int i = tid; i < L.nr; i += kTailThreads) {
+      T acc = T(0);
+      for (int k = L.r_ptr[i]; k < L.r_ptr[i + 1]; ++k) acc += rv[k] * r[L.r_cols[k]];
+      bc[L.r_pt[i]] = acc;
+    }
+    for (int p = tid; p < C.n; p += kTailThreads) xc[p] = T(0);
     __syncthreads();
   }
   {   // level 0: x = A0^-1 b on every problem's free macro-vertices
@@ -249,7 +149,7 @@ __global__ void __launch_bounds__(TailCfg<T>::threads, 1)
       const Block B = blocks[bk];
       const double* A = Ainv + B.a0_off;
       const int* idx = free0 + B.free0_off;
-      for (int rr = warp; rr < B.n0; rr += NT / 32) {
+      for (int rr = warp; rr < B.n0; rr += kTailThreads / 32) {
         double s = 0.0;
         for (int j = lane; j < B.n0; j += 32) s = fma(A[(int64_t)rr * B.n0 + j], (double)b0[idx[j]], s);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -264,14 +164,18 @@ __global__ void __launch_bounds__(TailCfg<T>::threads, 1)
     T* x = sm + L.smem_off;
     T* b = x + L.n;
     const T* xc = sm + C.smem_off;
-    for (int i = tid; i < L.np; i += NT)
-      x[__ldg(L.p_pt + i)] += tail_transfer_row(L.p_cols, (const T*)L.p_vals, L.np, L.pw, i, xc);
+    const T* pv = (const T*)L.p_vals;
+    for (int i = tid; i < L.np; i += kTailThreads) {
+      T acc = T(0);
+      for (int k = L.p_ptr[i]; k < L.p_ptr[i + 1]; ++k) acc += pv[k] * xc[L.p_cols[k]];
+      x[L.p_pt[i]] += acc;
+    }
     __syncthreads();
-    tail_smooth<T>(L, x, b, nullptr, nu2, false, false);
+    for (int s = 0; s < nu2; ++s) tail_gs<T>(L, x, b, false);
   }
   const TailLevelDev& L = D.lv[c];
   const T* x = sm + L.smem_off;
-  for (int row = tid; row < L.nrow; row += NT) {
+  for (int row = tid; row < L.nrow; row += kTailThreads) {
     const int p = L.row_pt[row];
     xtop[L.slot[p]] = x[p];
   }
@@ -431,38 +335,26 @@ void tail_build(Mesh& m, const std::vector<std::vector<double>>& k_up,
             edge(a, cpt, 0.5 * F.cot[1] * k);
           }
       }
-      std::vector<int> row_pt, set_ptr{0};
-      std::vector<double> diag, dinv;
-      int ew = 0;
-      for (size_t s = 0; s < sets.size(); ++s) {
-        int w = 0;
-        for (int p : sets[s]) {
+      std::vector<int> row_pt, row_ptr{0}, cols, set_ptr{0};
+      std::vector<double> vals, diag, dinv;
+      for (const auto& S : sets) {
+        for (int p : S) {
           row_pt.push_back(p);
+          for (const auto& kv : off_rows[p]) {
+            cols.push_back(kv.first);
+            vals.push_back(kv.second);
+          }
+          row_ptr.push_back((int)cols.size());
           diag.push_back(dg[p]);
           dinv.push_back(1.0 / dg[p]);
-          w = std::max(w, (int)off_rows[p].size());
         }
         set_ptr.push_back((int)row_pt.size());
-        d.set_w[s] = w;
-        ew = std::max(ew, w);
       }
-      const int nrow = (int)row_pt.size();
-      // entry k of row q at k * nrow + q; padding: weight 0 on the row's own point
-      std::vector<int> cols((size_t)ew * nrow);
-      std::vector<double> vals((size_t)ew * nrow, 0.0);
-      for (int q = 0; q < nrow; ++q) {
-        int k = 0;
-        for (const auto& kv : off_rows[row_pt[q]]) {
-          cols[(size_t)k * nrow + q] = kv.first;
-          vals[(size_t)k * nrow + q] = kv.second;
-          ++k;
-        }
-        for (; k < ew; ++k) cols[(size_t)k * nrow + q] = row_pt[q];
-      }
-      d.nrow = nrow;
+      d.nrow = (int)row_pt.size();
       d.nsets = (int)sets.size();
       for (int s = 0; s <= d.nsets; ++s) d.set_ptr[s] = set_ptr[s];
       d.row_pt = up(P, row_pt);
+      d.row_ptr = up(P, row_ptr);
       d.cols = up(P, cols);
       // transfers between level l - 1 and l: (coarse, fine) pairs of the
       // nested lattices, each counted once
@@ -481,52 +373,35 @@ void tail_build(Mesh& m, const std::vector<std::vector<double>>& k_up,
             }
           }
       const LevelHost& hc = H[l - 1];
-      // restriction rows (free coarse points) and prolongation rows (free fine
-      // points), each list of (column, weight) in ascending column order
-      std::vector<int> r_pt;
-      std::vector<std::vector<std::pair<int, double>>> rrow;
+      std::vector<int> r_pt, r_ptr{0}, r_cols;
+      std::vector<double> r_vals;
       int cur = -1;
       for (const auto& kv : pairs) {   // ordered by coarse point
         const int oc = kv.first.first, of = kv.first.second;
         if (!hc.free[oc] || !h.free[of]) continue;
         if (oc != cur) {
+          if (cur >= 0) r_ptr.push_back((int)r_cols.size());
           r_pt.push_back(oc);
-          rrow.emplace_back();
           cur = oc;
         }
-        rrow.back().push_back({of, kv.second});
+        r_cols.push_back(of);
+        r_vals.push_back(kv.second);
       }
+      if (cur >= 0) r_ptr.push_back((int)r_cols.size());
       std::vector<std::vector<std::pair<int, double>>> prow(h.n);
       for (const auto& kv : pairs)
         if (h.free[kv.first.second]) prow[kv.first.second].push_back({kv.first.first, kv.second});
-      std::vector<int> p_pt;
-      std::vector<std::vector<std::pair<int, double>>> prows;
+      std::vector<int> p_pt, p_ptr{0}, p_cols;
+      std::vector<double> p_vals;
       for (int q = 0; q < h.n; ++q)
         if (h.free[q] && !prow[q].empty()) {
           p_pt.push_back(q);
-          prows.push_back(prow[q]);
-        }
-      // column-major with the longest row's width; padding repeats the row's
-      // first column with weight 0
-      auto ell = [](const std::vector<std::vector<std::pair<int, double>>>& rows, std::vector<int>& c,
-                    std::vector<double>& v) {
-        int w = 0;
-        for (const auto& r : rows) w = std::max(w, (int)r.size());
-        const size_t n = rows.size();
-        c.assign((size_t)w * n, 0);
-        v.assign((size_t)w * n, 0.0);
-        for (size_t i = 0; i < n; ++i)
-          for (int k = 0; k < w; ++k) {
-            const bool in = k < (int)rows[i].size();
-            c[(size_t)k * n + i] = in ? rows[i][k].first : rows[i][0].first;
-            v[(size_t)k * n + i] = in ? rows[i][k].second : 0.0;
+          for (const auto& e : prow[q]) {
+            p_cols.push_back(e.first);
+            p_vals.push_back(e.second);
           }
-        return w;
-      };
-      std::vector<int> r_cols, p_cols;
-      std::vector<double> r_vals, p_vals;
-      d.rw = ell(rrow, r_cols, r_vals);
-      d.pw = ell(prows, p_cols, p_vals);
+          p_ptr.push_back((int)p_cols.size());
+        }
       // every index the kernel follows stays inside its level's vectors
       const auto in_range = [](const std::vector<int>& v, int n, const char* what) {
         for (int q : v)
@@ -541,8 +416,10 @@ void tail_build(Mesh& m, const std::vector<std::vector<double>>& k_up,
       d.nr = (int)r_pt.size();
       d.np = (int)p_pt.size();
       d.r_pt = up(P, r_pt);
+      d.r_ptr = up(P, r_ptr);
       d.r_cols = up(P, r_cols);
       d.p_pt = up(P, p_pt);
+      d.p_ptr = up(P, p_ptr);
       d.p_cols = up(P, p_cols);
       TailLevelDev d32 = d;
       d.vals = up_as<double>(P, vals);
@@ -600,11 +477,11 @@ void tail_run(const Mesh& m, int l, int prec, void* x, const void* b, int nu1, i
   const int nb = (int)m.h_blocks.size();
   if (prec == 0)
     HHG_LAUNCH(HHG_K_OTHER, l, st, "coarse tail",
-               k_tail<double><<<1, TailCfg<double>::threads, smem, st>>>(D, m.blocks, nb, m.A0inv, m.free0, (double*)x,
+               k_tail<double><<<1, kTailThreads, smem, st>>>(D, m.blocks, nb, m.A0inv, m.free0, (double*)x,
                                                               (const double*)b, nu1, nu2));
   else
     HHG_LAUNCH(HHG_K_OTHER, l, st, "coarse tail",
-               k_tail<float><<<1, TailCfg<float>::threads, smem, st>>>(D, m.blocks, nb, m.A0inv, m.free0, (float*)x,
+               k_tail<float><<<1, kTailThreads, smem, st>>>(D, m.blocks, nb, m.A0inv, m.free0, (float*)x,
                                                              (const float*)b, nu1, nu2));
   ghost_fill(m, l, prec, x, st);
 }
