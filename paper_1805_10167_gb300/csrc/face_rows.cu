@@ -39,7 +39,7 @@ constexpr int kSmallRowsN = 64;    // double-float rows from this level size up 
 constexpr int kStripCols = 96;
 constexpr unsigned kAll = 0xffffffffu;
 
-enum RowMode { R_APPLY = 0, R_RESID = 1, R_JAC = 3, R_SRES = 4, R_ADOT = 5 };   // same codes as the row kernels
+enum RowMode { R_APPLY = 0, R_RESID = 1, R_JAC = 3, R_SRES = 4, R_ADOT = 5, R_RES0 = 6 };   // same codes as the row kernels
 
 template <typename T>
 struct RowArgs {
@@ -162,6 +162,8 @@ __device__ __forceinline__ void rows_step(typename Arith<T, DF>::V (&R)[4][3], t
       } else if (MODE == R_RESID) {
         out[fb + p] = out_cast<T, DF, TO>(v);
         acc.add(v);
+      } else if (MODE == R_RES0) {
+        out[fb + p] = out_cast<T, DF, TO>(v);
       } else if (MODE == R_SRES) {
         const T vv = A::out(v);
         out[fb + p] = narrow<TO>(vv * dgi);
@@ -194,6 +196,8 @@ __device__ __forceinline__ void rows_step(typename Arith<T, DF>::V (&R)[4][3], t
         const V r = A::sub(A::in(bg[p]), ax);
         out[fb + p] = out_cast<T, DF, TO>(r);
         acc.add(r);
+      } else if (MODE == R_RES0) {
+        out[fb + p] = out_cast<T, DF, TO>(A::sub(A::in(bg[p]), ax));
       } else if (MODE == R_SRES) {
         out[fb + p] = narrow<TO>(A::out(A::sub(A::in(bg[p]), ax)) / A::out(diag));
       } else {
@@ -336,6 +340,7 @@ int face_rows(const Mesh& m, int level, int prec_in, int prec_out, int mode, con
     switch (mode) {
       case R_APPLY: launch_rows<float, float, R_APPLY, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st); return 0;
       case R_RESID: return launch_rows<float, float, R_RESID, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st);
+      case R_RES0: launch_rows<float, float, R_RES0, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st); return 0;
       case R_SRES: launch_rows<float, float, R_SRES, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st); return 0;
       default: launch_rows<float, float, R_JAC, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st); return 0;
     }
@@ -361,6 +366,7 @@ int face_rows(const Mesh& m, int level, int prec_in, int prec_out, int mode, con
     case R_RESID:
       if (x_upd) return launch_rows_f64<double, R_RESID, true>(m, level, xx, (double*)x_upd, d, o, bb, partials, omega, st);
       return launch_rows_f64<double, R_RESID, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st);
+    case R_RES0: launch_rows_f64<double, R_RES0, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st); return 0;
     case R_SRES: launch_rows<double, double, R_SRES, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st); return 0;
     default: launch_rows<double, double, R_JAC, false>(m, level, xx, nullptr, nullptr, o, bb, partials, omega, st); return 0;
   }

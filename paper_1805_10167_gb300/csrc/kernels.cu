@@ -16,7 +16,7 @@
 namespace hhg {
 
 // SRES: (b - A x) / A_pp; ADOT: A x and the partial sums of x . (A x)
-enum Mode { APPLY = 0, RESID = 1, GS = 2, JAC = 3, SRES = 4, ADOT = 5 };
+enum Mode { APPLY = 0, RESID = 1, GS = 2, JAC = 3, SRES = 4, ADOT = 5, RESID0 = 6 };   // RESID0: residual without its sum of squares
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -109,7 +109,7 @@ __global__ void k_vertex(MeshTables M, LevelView L, const T* x, TO* out, const T
     }
     if (V.dirichlet) {
       if (lane == 0) {
-        if (MODE == APPLY || MODE == RESID || MODE == SRES || MODE == ADOT) out[s] = TO(0);
+        if (MODE == APPLY || MODE == RESID || MODE == RESID0 || MODE == SRES || MODE == ADOT) out[s] = TO(0);
         if (MODE == JAC) out[s] = (TO)x[s];
       }
       continue;
@@ -133,6 +133,8 @@ __global__ void k_vertex(MeshTables M, LevelView L, const T* x, TO* out, const T
         const T r = b[s] - (diag * xv + off);
         out[s] = (TO)r;
         acc += (double)r * (double)r;
+      } else if (MODE == RESID0) {
+        out[s] = (TO)(b[s] - (diag * xv + off));
       } else if (MODE == JAC) {
         out[s] = (TO)(xv + T(omega) * (b[s] - (diag * xv + off)) / diag);
       }
@@ -178,7 +180,7 @@ __global__ void k_edge(MeshTables M, LevelView L, const int* __restrict__ list, 
       xs = MODE == GS ? T(0) : x[s];
     }
     if (E.dirichlet) {
-      if (MODE == APPLY || MODE == RESID || MODE == SRES || MODE == ADOT) out[s] = TO(0);
+      if (MODE == APPLY || MODE == RESID || MODE == RESID0 || MODE == SRES || MODE == ADOT) out[s] = TO(0);
       if (MODE == JAC) out[s] = (TO)xs;
       continue;
     }
@@ -200,6 +202,8 @@ __global__ void k_edge(MeshTables M, LevelView L, const int* __restrict__ list, 
       const T r = b[s] - (diag * xs + off);
       out[s] = (TO)r;
       acc += (double)r * (double)r;
+    } else if (MODE == RESID0) {
+      out[s] = (TO)(b[s] - (diag * xs + off));
     } else if (MODE == JAC) {
       out[s] = (TO)(xs + T(omega) * (b[s] - (diag * xs + off)) / diag);
     }
@@ -726,6 +730,14 @@ void apply_dot_op(const Mesh& m, int level, const double* x, double* y, double* 
 
 void residual_op(const Mesh& m, int level, int prec, const void* x, const void* b, void* r,
                  double* norm2_dev, cudaStream_t st) {
+  if (!norm2_dev) {   // the residual alone: no sum of squares (in FP32 its FP64 products and widenings would
+                      // take the narrow FP64 pipe)
+    if (prec == 0)
+      rows_dispatch<double, double, RESID0>(m, level, (const double*)x, (double*)r, (const double*)b, nullptr, 0.0, st);
+    else
+      rows_dispatch<float, float, RESID0>(m, level, (const float*)x, (float*)r, (const float*)b, nullptr, 0.0, st);
+    return;
+  }
   int used;
   if (prec == 0)
     used = rows_dispatch<double, double, RESID>(m, level, (const double*)x, (double*)r, (const double*)b, m.partials, 0.0, st);
