@@ -35,6 +35,7 @@ __device__ __forceinline__ TO narrow(T v) {
 }
 
 constexpr int kRowWarps = 4;
+constexpr int kRowPrefetch = 8;    // L2 prefetch distance in rows (beyond the row loaded for step t + 2)
 constexpr int kSmallRowsN = 64;    // double-float rows from this level size up (as in the sweeps)
 constexpr int kStripCols = 96;
 constexpr unsigned kAll = 0xffffffffu;
@@ -107,6 +108,10 @@ __device__ __forceinline__ TO out_cast(typename Arith<T, DF>::V v) {
   }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Per-task constants of the constant stencil in the arithmetic's type.
 template <typename V>
 struct RowConsts {
@@ -122,6 +127,13 @@ __device__ __forceinline__ void rows_step(typename Arith<T, DF>::V (&R)[4][3], t
   using V = typename A::V;
   constexpr int sc = U, sn = (U + 1) & 3, ss = (U + 3) & 3;
   ld_row<T, DF, UPD>(R[(U + 2) & 3], E[(U + 2) & 3], t + 2, a);
+  {
+    const int rp = t + 2 + kRowPrefetch;
+    if (rp <= a.j1 && a.ic <= a.N - rp) {
+      prefetch_l2(a.xg + (rp * a.S + a.ic));
+      if (bg) prefetch_l2(bg + (rp * a.S + a.ic));
+    }
+  }
   if (t < a.j0) return;
   if (t < 1 || t > a.N - 2 || max(a.ws, 1) > a.N - 1 - t) return;   // no interior point in this row
   // neighbours across lanes (all lanes take part in the shuffles)

@@ -346,8 +346,9 @@ Mesh* mesh_create_blocks(const double* xy, int64_t nv, const int32_t* tri, int64
         ld.small_ptr[3] = (int)pts.size();
         if (!pts.empty()) ld.small_pts = upload(m, pts);
       }
-      {   // row kernels: 96-column strips in blocks of about 64 rows
-        const std::vector<int> rt = row_strip_tasks(m.nf, ld.lv.N, 64);
+      {   // row kernels: 96-column strips in blocks of about 32 rows (enough tasks to fill
+          // every SM from level 9 on; 64-row blocks left the FP64 level-9 residual 24 % slower)
+        const std::vector<int> rt = row_strip_tasks(m.nf, ld.lv.N, 32);
         ld.row_tasks = upload(m, rt);
         ld.n_row_tasks = (int)(rt.size() / 4);
       }
