@@ -5,6 +5,11 @@ import numpy as np
 import pytest
 
 from gpu_support import FP64_TOL, Pair, rel_err
+
+# An FP32 residual row rounds about ten operations at 2^-24 each on terms whose
+# magnitudes sum to at most |b|_max + 2 A_pp |x|_max, a few times max |r| for
+# these random inputs: 2^-16 bounds it with room to spare.
+FP32_RES_TOL = 2.0 ** -16
 from oracle import fem
 from oracle import multigrid as mg
 
@@ -112,6 +117,19 @@ def test_residual_and_norm_parity(pairs, name, L, vark):
     want = P.H.residual(L, x, b)
     assert rel_err(P.from_dev(L, r), want) <= FP64_TOL
     assert abs(nrm.item() - mg.norm_free(P.H, L, want)) <= FP64_TOL * mg.norm_free(P.H, L, want)
+    # without a norm the library takes a kernel form that skips the sum of
+    # squares: the same residual, bit for bit
+    r_only = P.new(L)
+    P.g.residual(L, P.to_dev(L, x), P.to_dev(L, b), r_only)
+    assert torch.equal(r_only, r)
+    # and in FP32, with and without the norm, within FP32 rounding of the oracle
+    r32, r32_only = P.new(L, 1), P.new(L, 1)
+    n32 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    x32, b32 = P.to_dev(L, x, prec=1), P.to_dev(L, b, prec=1)
+    P.g.residual(L, x32, b32, r32, n32, prec=P.hhg.F32)
+    P.g.residual(L, x32, b32, r32_only, prec=P.hhg.F32)
+    assert torch.equal(r32_only, r32)
+    assert rel_err(P.from_dev(L, r32, prec=1).astype(np.float64), want) <= FP32_RES_TOL
 
 
 @pytest.mark.parametrize("name,L", CASES[:4])
