@@ -154,17 +154,13 @@ static void vcycle_level(const Mesh& m, int l, int prec, void* x, const void* b,
   }
   void* cur = x;
   void* oth = ld.w[prec];
-  for (int s = 0; s < nu1; ++s) {
-    if (learned) {
-      if (gs_first) {
-        gs_sweep(m, l, prec, cur, oth, b, true, st, nullptr);
-        std::swap(cur, oth);
-      }
-      learned_step(m, l, prec, cur, b, st);
-      continue;
+  if (!learned) gs_sweeps(m, l, prec, cur, oth, b, true, nu1, st, bs);
+  for (int s = 0; learned && s < nu1; ++s) {
+    if (gs_first) {
+      gs_sweep(m, l, prec, cur, oth, b, true, st, nullptr);
+      std::swap(cur, oth);
     }
-    gs_sweep(m, l, prec, cur, oth, b, true, st, bs);
-    std::swap(cur, oth);
+    learned_step(m, l, prec, cur, b, st);
   }
   residual_op(m, l, prec, cur, b, ld.r[prec], nullptr, st);
   const bool coarse_bs = smoother == 0 && uses_scaled_rhs(m, l - 1, prec);
@@ -172,17 +168,13 @@ static void vcycle_level(const Mesh& m, int l, int prec, void* x, const void* b,
   zero_vec(m, l - 1, prec, lc.x[prec], st);
   vcycle_level(m, l - 1, prec, lc.x[prec], lc.b[prec], nu1, nu2, smoother, coarse_bs, st);
   prolongate_add(m, l, prec, lc.x[prec], cur, st);
-  for (int s = 0; s < nu2; ++s) {
-    if (learned) {
-      if (gs_first) {
-        gs_sweep(m, l, prec, cur, oth, b, false, st, nullptr);
-        std::swap(cur, oth);
-      }
-      learned_step(m, l, prec, cur, b, st);
-      continue;
+  if (!learned) gs_sweeps(m, l, prec, cur, oth, b, false, nu2, st, bs);
+  for (int s = 0; learned && s < nu2; ++s) {
+    if (gs_first) {
+      gs_sweep(m, l, prec, cur, oth, b, false, st, nullptr);
+      std::swap(cur, oth);
     }
-    gs_sweep(m, l, prec, cur, oth, b, false, st, bs);
-    std::swap(cur, oth);
+    learned_step(m, l, prec, cur, b, st);
   }
   if (cur != x)
     check_cuda(cudaMemcpyAsync(x, cur, (size_t)ld.lv.len * (prec == 0 ? 8 : 4),
@@ -431,14 +423,10 @@ hhg_status hhg_smooth(hhg_mesh mesh, int32_t level, hhg_prec prec, void* x, cons
     }
     void* cur = x;
     void* oth = ld.w[prec];
-    for (int s = 0; s < sweeps; ++s) {
-      if (smoother == HHG_JACOBI) {
-        hhg::jacobi_sweep(m, level, prec, cur, b, omega, ld.r[prec], S(stream));
-      } else {
-        hhg::gs_sweep(m, level, prec, cur, oth, b, smoother == HHG_GS_FWD, S(stream), bs);
-        std::swap(cur, oth);
-      }
-    }
+    if (smoother == HHG_JACOBI)
+      for (int s = 0; s < sweeps; ++s) hhg::jacobi_sweep(m, level, prec, cur, b, omega, ld.r[prec], S(stream));
+    else
+      hhg::gs_sweeps(m, level, prec, cur, oth, b, smoother == HHG_GS_FWD, sweeps, S(stream), bs);
     if (cur != x)
       hhg::check_cuda(cudaMemcpyAsync(x, cur, (size_t)ld.lv.len * (prec == 0 ? 8 : 4),
                                       cudaMemcpyDeviceToDevice, S(stream)), "iterate copy");

@@ -416,13 +416,13 @@ struct GridBar {
 
 __device__ __forceinline__ GridBar barrier_start(unsigned* bar, unsigned extra, long long polls) {
   GridBar g{nullptr, 0u, 0, gridDim.x + extra, polls > 0 ? polls : kBarrierPolls, false};
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 || blockIdx.x == 0) {
     g.set = ld_acquire(bar) & 1u;
     g.cnt = bar + 4 + g.set * kGridBarSlots;
-    if (blockIdx.x == 0) {
-      unsigned* other = bar + 4 + (g.set ^ 1u) * kGridBarSlots;
-      for (int q = 0; q < kGridBarSlots; ++q) st_relaxed(other + q, 0u);
-    }
+  }
+  if (blockIdx.x == 0) {   // the threads of CTA 0 zero the other set
+    unsigned* other = bar + 4 + (g.set ^ 1u) * kGridBarSlots;
+    for (int q = threadIdx.x; q < kGridBarSlots; q += blockDim.x) st_relaxed(other + q, 0u);
   }
   return g;
 }
@@ -450,12 +450,16 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, GridBar& g, int* err
 // the colour sets, reversed for the backward sweep).  Vertices and edges are
 // updated in place, on x_in going forward and on x_out going backward; the
 // faces go from x_in to x_out, and the vertex/edge block of x_in is copied
-// to x_out along with them.  Grid barriers separate the phases.
-template <typename T, bool DF, bool VARK, bool FWD, bool BS>
+// to x_out along with them.  Grid barriers separate the phases.  SMALLK:
+// the instance for levels with N <= kSmallN (faces one CTA each in shared
+// memory), which with k = 1 may run nsw sweeps in one launch, x_in and x_out
+// trading places after each (a grid barrier between sweeps); the other
+// instances sweep the face strips, one sweep per launch.
+template <typename T, bool DF, bool VARK, bool FWD, bool BS, bool SMALLK>
 __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
     k_gs_sweep(MeshTables M, LevelView L, T* xin, T* xout, const T* __restrict__ b,
                const T* __restrict__ bsf, const T* __restrict__ k, const int4* __restrict__ tasks, int ntasks,
-               const int* __restrict__ clist, const __grid_constant__ EdgeColours cs, int small,
+               const int* __restrict__ clist, const __grid_constant__ EdgeColours cs, int nsw,
                const unsigned short* __restrict__ spts, int4 sptr, unsigned* bar, int* err,
                unsigned bar_extra, long long bar_polls, T* xin2, T* xout2, const T* __restrict__ b2) {
   extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -510,7 +514,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
     for (int64_t q = gt; q < L.f_off; q += nt) xout[q] = xin[q];
     if (xin2)
       for (int64_t q = gt; q < L.f_off; q += nt) xout2[q] = xin2[q];
-    if (small) {
+    if constexpr (SMALLK) {
       uint64_t* mb = reinterpret_cast<uint64_t*>(dyn_smem);
       T* sx = reinterpret_cast<T*>(dyn_smem + kSmallHeader);
       uint32_t phase = 0;
@@ -546,6 +550,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
       }
     }
   };
+  auto sweep = [&]() {
   VertRec V0{};
   EdgePre ep{};
   if (FWD) {
@@ -579,6 +584,23 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(T) == 4 ? 6 : 4)
     if (cs.n == 0 && gw < M.nv) V0 = M.verts[gw];
     vertices(true, V0);
   }
+  };
+  if constexpr (SMALLK && !VARK) {
+    for (int sw = 0; sw < nsw; ++sw) {
+      if (sw > 0) {
+        T* t = xin;
+        xin = xout;
+        xout = t;
+        t = xin2;
+        xin2 = xout2;
+        xout2 = t;
+        grid_barrier(bar, gb, err);
+      }
+      sweep();
+    }
+  } else {
+    sweep();
+  }
 }
 
 }  // namespace
@@ -608,28 +630,26 @@ std::vector<int> strip_tasks(int nf, int N, int rows_per_task) {
   return out;
 }
 
-template <typename T, bool DF, bool VARK, bool FWD, bool BS>
-static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b, const T* bs, const T* k,
-                           cudaStream_t st, T* xin2 = nullptr, T* xout2 = nullptr, const T* b2 = nullptr) {
+template <typename T, bool DF, bool VARK, bool FWD, bool BS, bool SMALLK>
+static void launch_sweep_k(const Mesh& m, int level, T* xin, T* xout, const T* b, const T* bs, const T* k,
+                           cudaStream_t st, T* xin2, T* xout2, const T* b2, int nsw) {
   const LevelData& ld = m.levels[level];
   const SweepCfg& c = ld.sweep[sizeof(T) == 8 ? 0 : 1];
-  const int small = ld.lv.N <= kSmallN ? 1 : 0;
-  const size_t smem = small ? kSmallHeader + 2 * (size_t)(ld.lv.N + 1) * ld.lv.S * sizeof(T) : 0;
+  const size_t smem = SMALLK ? kSmallHeader + 2 * (size_t)(ld.lv.N + 1) * ld.lv.S * sizeof(T) : 0;
   // CTAs per SM of this instance for each level (the shared memory of the
   // small-level face phase depends on N only; the same on every device of a run)
   static int resident_at[32] = {0};
   const int lvl = std::min(level, 31);
   static size_t configured = 48 * 1024;   // largest dynamic shared memory enabled for this instance
+  auto kern = k_gs_sweep<T, DF, VARK, FWD, BS, SMALLK>;
   if (smem > configured) {
-    check_cuda(cudaFuncSetAttribute(k_gs_sweep<T, DF, VARK, FWD, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem),
+    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "whole sweep shared memory");
     configured = smem;
   }
   if (resident_at[lvl] == 0) {
     int r = 0;
-    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_gs_sweep<T, DF, VARK, FWD, BS>, kStripWarps * 32, smem),
-               "sweep occupancy");
+    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, kStripWarps * 32, smem), "sweep occupancy");
     if (r < 1) throw std::runtime_error("whole-sweep kernel cannot be resident");
     resident_at[lvl] = r;
   }
@@ -638,7 +658,7 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
   check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
   check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
   // enough CTAs for the widest phase, never more than are resident at once
-  int64_t want = std::max<int64_t>(small ? m.nf : (c.ntasks + kStripWarps - 1) / kStripWarps,
+  int64_t want = std::max<int64_t>(SMALLK ? m.nf : (c.ntasks + kStripWarps - 1) / kStripWarps,
                                    (m.nv + kStripWarps - 1) / kStripWarps);
   want = std::max<int64_t>(want, (ld.lv.f_off + kStripWarps * 32 - 1) / (kStripWarps * 32));
   want = std::max<int64_t>(want, 1);
@@ -646,6 +666,9 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
   EdgeColours cs{};
   cs.n = ld.n_colours;
   if (cs.n > kMaxEdgeColours) throw std::runtime_error("too many edge colours for the whole-sweep kernel");
+  // grid barriers of the launch: cs.n + 1 per sweep and one between sweeps
+  if (nsw < 1 || (nsw > 1 && (!SMALLK || VARK)) || nsw * (cs.n + 2) - 1 > kGridBarSlots)
+    throw std::logic_error("whole sweep: sweep count out of range");
   for (int q = 0; q <= cs.n; ++q) cs.ptr[q] = ld.colour_ptr.empty() ? 0 : ld.colour_ptr[q];
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);
@@ -657,46 +680,59 @@ static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  check_cuda(cudaLaunchKernelEx(&cfg, k_gs_sweep<T, DF, VARK, FWD, BS>, m.tab, ld.lv, xin, xout, b, bs, k,
-                                (const int4*)c.tasks, c.ntasks, (const int*)ld.colour_list, cs, small,
-                                (const unsigned short*)ld.small_pts,
+  check_cuda(cudaLaunchKernelEx(&cfg, kern, m.tab, ld.lv, xin, xout, b, bs, k, (const int4*)c.tasks, c.ntasks,
+                                (const int*)ld.colour_list, cs, nsw, (const unsigned short*)ld.small_pts,
                                 make_int4(ld.small_ptr[0], ld.small_ptr[1], ld.small_ptr[2], ld.small_ptr[3]),
                                 m.gbar, m.err, m.dbg_bar_extra, m.dbg_bar_polls, xin2, xout2, b2),
              "whole sweep launch");
 }
 
+template <typename T, bool DF, bool VARK, bool FWD, bool BS>
+static void launch_sweep_t(const Mesh& m, int level, T* xin, T* xout, const T* b, const T* bs, const T* k,
+                           cudaStream_t st, T* xin2 = nullptr, T* xout2 = nullptr, const T* b2 = nullptr,
+                           int nsw = 1) {
+  if (m.levels[level].lv.N <= kSmallN)
+    launch_sweep_k<T, DF, VARK, FWD, false, true>(m, level, xin, xout, b, nullptr, k, st, xin2, xout2, b2, nsw);
+  else
+    launch_sweep_k<T, DF, VARK, FWD, BS, false>(m, level, xin, xout, b, bs, k, st, xin2, xout2, b2, nsw);
+}
+
 template <typename T, bool DF>
 static void sweep_dispatch(const Mesh& m, int level, T* xi, T* xo, const T* b, const T* bs, const T* k,
-                           bool forward, cudaStream_t st, T* xi2 = nullptr, T* xo2 = nullptr, const T* b2 = nullptr) {
+                           bool forward, cudaStream_t st, T* xi2 = nullptr, T* xo2 = nullptr, const T* b2 = nullptr,
+                           int nsw = 1) {
   if (m.vark) {
-    if (forward) launch_sweep_t<T, DF, true, true, false>(m, level, xi, xo, b, nullptr, k, st, xi2, xo2, b2);
-    else launch_sweep_t<T, DF, true, false, false>(m, level, xi, xo, b, nullptr, k, st, xi2, xo2, b2);
+    if (forward) launch_sweep_t<T, DF, true, true, false>(m, level, xi, xo, b, nullptr, k, st, xi2, xo2, b2, nsw);
+    else launch_sweep_t<T, DF, true, false, false>(m, level, xi, xo, b, nullptr, k, st, xi2, xo2, b2, nsw);
   } else if (bs) {
     if constexpr (sizeof(T) == 8) {   // FP64 only
       if (forward) launch_sweep_t<T, DF, false, true, true>(m, level, xi, xo, b, bs, nullptr, st);
       else launch_sweep_t<T, DF, false, false, true>(m, level, xi, xo, b, bs, nullptr, st);
     }
   } else {
-    if (forward) launch_sweep_t<T, DF, false, true, false>(m, level, xi, xo, b, nullptr, nullptr, st, xi2, xo2, b2);
-    else launch_sweep_t<T, DF, false, false, false>(m, level, xi, xo, b, nullptr, nullptr, st, xi2, xo2, b2);
+    if (forward) launch_sweep_t<T, DF, false, true, false>(m, level, xi, xo, b, nullptr, nullptr, st, xi2, xo2, b2, nsw);
+    else launch_sweep_t<T, DF, false, false, false>(m, level, xi, xo, b, nullptr, nullptr, st, xi2, xo2, b2, nsw);
   }
 }
 
 // bs: the face part of b / A_pp (scale_rhs) for the strip kernel of an FP64
 // level with k = 1 and N > kSmallN, or nullptr
 void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
-                    const void* bs, bool forward, cudaStream_t st) {
+                    const void* bs, bool forward, cudaStream_t st, int nsw) {
   const LevelData& ld = m.levels[level];
   if (prec == 0) {
     const double* k = m.vark ? (const double*)ld.k[0] : nullptr;
     const double* bsd = (!m.vark && ld.lv.N > kSmallN) ? (const double*)bs : nullptr;
     if (m.fp64_df)
-      sweep_dispatch<double, true>(m, level, (double*)xin, (double*)xout, (const double*)b, bsd, k, forward, st);
+      sweep_dispatch<double, true>(m, level, (double*)xin, (double*)xout, (const double*)b, bsd, k, forward, st,
+                                   nullptr, nullptr, nullptr, nsw);
     else
-      sweep_dispatch<double, false>(m, level, (double*)xin, (double*)xout, (const double*)b, bsd, k, forward, st);
+      sweep_dispatch<double, false>(m, level, (double*)xin, (double*)xout, (const double*)b, bsd, k, forward, st,
+                                    nullptr, nullptr, nullptr, nsw);
   } else {
     const float* k = m.vark ? (const float*)ld.k[1] : nullptr;
-    sweep_dispatch<float, false>(m, level, (float*)xin, (float*)xout, (const float*)b, nullptr, k, forward, st);
+    sweep_dispatch<float, false>(m, level, (float*)xin, (float*)xout, (const float*)b, nullptr, k, forward, st,
+                                 nullptr, nullptr, nullptr, nsw);
   }
 }
 
@@ -704,21 +740,21 @@ void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, c
 // smoothing step) in one whole-sweep launch on a level with N <= kSmallN:
 // both go through every phase, one set of grid barriers.
 void gs_sweep_fused2(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b, void* xin2,
-                     void* xout2, const void* b2, bool forward, cudaStream_t st) {
+                     void* xout2, const void* b2, bool forward, cudaStream_t st, int nsw) {
   const LevelData& ld = m.levels[level];
   if (ld.lv.N > kSmallN) throw std::logic_error("two-vector sweep: small levels only");
   if (prec == 0) {
     const double* k = m.vark ? (const double*)ld.k[0] : nullptr;
     if (m.fp64_df)
       sweep_dispatch<double, true>(m, level, (double*)xin, (double*)xout, (const double*)b, nullptr, k, forward, st,
-                                   (double*)xin2, (double*)xout2, (const double*)b2);
+                                   (double*)xin2, (double*)xout2, (const double*)b2, nsw);
     else
       sweep_dispatch<double, false>(m, level, (double*)xin, (double*)xout, (const double*)b, nullptr, k, forward, st,
-                                    (double*)xin2, (double*)xout2, (const double*)b2);
+                                    (double*)xin2, (double*)xout2, (const double*)b2, nsw);
   } else {
     const float* k = m.vark ? (const float*)ld.k[1] : nullptr;
     sweep_dispatch<float, false>(m, level, (float*)xin, (float*)xout, (const float*)b, nullptr, k, forward, st,
-                                 (float*)xin2, (float*)xout2, (const float*)b2);
+                                 (float*)xin2, (float*)xout2, (const float*)b2, nsw);
   }
 }
 

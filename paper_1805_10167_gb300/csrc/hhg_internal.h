@@ -263,8 +263,10 @@ struct EdgeColours {
 // Device state of the whole-sweep kernel (32-bit words): [0] which of the
 // two barrier-counter sets the next launch uses, [1] face-task ticket,
 // [2] finished-warp count, [3] unused, then two sets of kGridBarSlots
-// arrival counters (one per grid barrier of a launch).
-constexpr int kGridBarSlots = kMaxEdgeColours + 1;
+// arrival counters (one per grid barrier of a launch).  On levels with
+// N <= kSmallN one launch runs up to kMaxFusedSweeps consecutive sweeps.
+constexpr int kMaxFusedSweeps = 3;
+constexpr int kGridBarSlots = kMaxFusedSweeps * (kMaxEdgeColours + 2);
 constexpr int kGridBarWords = 4 + 2 * kGridBarSlots;
 
 // Level-0 blocks of at most kDirectMaxN0 unknowns are solved by a stored inverse.
@@ -371,20 +373,27 @@ void gs_sweep(const Mesh& m, int level, int prec, void* xin, void* xout, const v
               bool forward, cudaStream_t st, const void* bs = nullptr);
 void face_gs3_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
                      bool forward, cudaStream_t st);
-// One sweep of each of two independent vectors with the same operator (no
-// scaled right-hand side); on small levels both in one whole-sweep launch.
-void gs_sweep2(const Mesh& m, int level, int prec, void* x1in, void* x1out, const void* b1, void* x2in,
-               void* x2out, const void* b2, bool forward, cudaStream_t st);
+// nsw sweeps of each of two independent vectors with the same operator (no
+// scaled right-hand side), ping-ponging between x?in and x?out; on small
+// levels both vectors and up to kMaxFusedSweeps sweeps in one launch.  On
+// return x1in / x2in point at the result.
+void gs_sweep2(const Mesh& m, int level, int prec, void*& x1in, void*& x1out, const void* b1, void*& x2in,
+               void*& x2out, const void* b2, bool forward, int nsw, cudaStream_t st);
 void gs_sweep_fused2(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b, void* xin2,
-                     void* xout2, const void* b2, bool forward, cudaStream_t st);
+                     void* xout2, const void* b2, bool forward, cudaStream_t st, int nsw);
 std::vector<int> face_tasks(int nf, int N, int tasks_per_face);
 std::vector<int> strip_tasks(int nf, int N, int rows_per_task);
 void face_ring_launch(const Mesh& m, int level, int prec, const void* xin, void* xout, const void* b,
                       bool forward, const int4* tasks, int ntasks, cudaStream_t st);
 // One whole Gauss-Seidel sweep (vertices, edge colours, faces) in one
-// cooperative launch (the STRIP variant).
+// cooperative launch (the STRIP variant); with nsw > 1 (levels with
+// N <= kSmallN, k = 1) nsw sweeps alternating xin -> xout, xout -> xin, ...
 void gs_sweep_fused(const Mesh& m, int level, int prec, void* xin, void* xout, const void* b,
-                    const void* bs, bool forward, cudaStream_t st);
+                    const void* bs, bool forward, cudaStream_t st, int nsw = 1);
+// nsw sweeps ping-ponging between cur and oth (up to kMaxFusedSweeps per
+// launch where gs_sweep_fused allows it); on return cur points at the result.
+void gs_sweeps(const Mesh& m, int level, int prec, void*& cur, void*& oth, const void* b, bool forward, int nsw,
+               cudaStream_t st, const void* bs);
 size_t face_gs_smem(const LevelView& L, int prec);
 void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,
                   void* work, cudaStream_t st);

@@ -837,16 +837,42 @@ void gs_sweep(const Mesh& m, int level, int prec, void* xin, void* xout, const v
   if (!forward) ve_gs(m, level, prec, xout, b, false, st);
 }
 
-void gs_sweep2(const Mesh& m, int level, int prec, void* x1in, void* x1out, const void* b1, void* x2in,
-               void* x2out, const void* b2, bool forward, cudaStream_t st) {
-  const LevelView& L = m.levels[level].lv;
-  if (m.levels[level].sweep[prec].variant == SWEEP_STRIP && L.N <= kSmallN) {
-    LaunchScope ls(HHG_K_FACE_GS, level, st);
-    gs_sweep_fused2(m, level, prec, x1in, x1out, b1, x2in, x2out, b2, forward, st);
-    return;
+void gs_sweep2(const Mesh& m, int level, int prec, void*& x1in, void*& x1out, const void* b1, void*& x2in,
+               void*& x2out, const void* b2, bool forward, int nsw, cudaStream_t st) {
+  const bool fuse = m.levels[level].sweep[prec].variant == SWEEP_STRIP && m.levels[level].lv.N <= kSmallN;
+  const int per_launch = m.vark ? 1 : kMaxFusedSweeps;
+  while (nsw > 0) {
+    const int k = fuse ? std::min(nsw, per_launch) : 1;
+    if (fuse) {
+      LaunchScope ls(HHG_K_FACE_GS, level, st);
+      gs_sweep_fused2(m, level, prec, x1in, x1out, b1, x2in, x2out, b2, forward, st, k);
+    } else {
+      gs_sweep(m, level, prec, x1in, x1out, b1, forward, st);
+      gs_sweep(m, level, prec, x2in, x2out, b2, forward, st);
+    }
+    if (k % 2) {
+      std::swap(x1in, x1out);
+      std::swap(x2in, x2out);
+    }
+    nsw -= k;
   }
-  gs_sweep(m, level, prec, x1in, x1out, b1, forward, st);
-  gs_sweep(m, level, prec, x2in, x2out, b2, forward, st);
+}
+
+void gs_sweeps(const Mesh& m, int level, int prec, void*& cur, void*& oth, const void* b, bool forward, int nsw,
+               cudaStream_t st, const void* bs) {
+  const bool fuse = m.levels[level].sweep[prec].variant == SWEEP_STRIP && m.levels[level].lv.N <= kSmallN;
+  const int per_launch = m.vark ? 1 : kMaxFusedSweeps;
+  while (nsw > 0) {
+    const int k = fuse ? std::min(nsw, per_launch) : 1;
+    if (fuse) {
+      LaunchScope ls(HHG_K_FACE_GS, level, st);
+      gs_sweep_fused(m, level, prec, cur, oth, b, bs, forward, st, k);
+    } else {
+      gs_sweep(m, level, prec, cur, oth, b, forward, st, bs);
+    }
+    if (k % 2) std::swap(cur, oth);
+    nsw -= k;
+  }
 }
 
 void jacobi_sweep(const Mesh& m, int level, int prec, void* x, const void* b, double omega,

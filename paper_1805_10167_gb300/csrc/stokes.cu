@@ -910,11 +910,12 @@ template <typename T>
 void velocity_sweeps(const Mesh& m, int l, T*& c1, T*& o1, T*& c2, T*& o2, const T* b1, const T* b2, bool forward,
                      cudaStream_t st) {
   const StokesData& D = *m.stokes;
-  for (int s = 0; s < D.nvel; ++s) {
-    gs_sweep2(m, l, prec_of<T>(), c1, o1, b1, c2, o2, b2, forward, st);
-    std::swap(c1, o1);
-    std::swap(c2, o2);
-  }
+  void *a1 = c1, *p1 = o1, *a2 = c2, *p2 = o2;
+  gs_sweep2(m, l, prec_of<T>(), a1, p1, b1, a2, p2, b2, forward, D.nvel, st);
+  c1 = (T*)a1;
+  o1 = (T*)p1;
+  c2 = (T*)a2;
+  o2 = (T*)p2;
 }
 
 // One Uzawa step on level l with the iterate in (c1, c2, cp) and partners
