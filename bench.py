@@ -42,7 +42,7 @@ FP64_OPS_PER_CLK_SM = 2           # FP64 add/mul/fma per clock per SM (cross-che
 # dram__bytes_read.sum + dram__bytes_write.sum of one level-9 launch of the
 # FP64 face sweep (annulus, 128 faces), per (kernel variant, split), from the
 # ncu captures summarised under profiles/; None until captured
-TRAFFIC_L9 = {(1, 32): 391.266560e6 + 113.123072e6}   # k_gs_sweep<double, 0, 0, 1, 1>, default split
+TRAFFIC_L9 = {(1, 32): 391.016448e6 + 113.307136e6}   # k_gs_sweep<double, 0, 0, 1, 1, 0>, default split
 
 
 # ------------------------------------------------------------------ ranks
